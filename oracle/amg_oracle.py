@@ -1,0 +1,299 @@
+"""Plain FP64 CPU oracle of the AMG multilevel-correction eigensolver's solve phase.
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or run this module.  It shares no
+code with the CUDA path: it parses the hierarchy blob itself and uses NumPy /
+SciPy library primitives (sparse matrix products, dense Cholesky, LAPACK's
+symmetric-definite eigensolver) as single steps.
+
+It computes, in float64 and in the paper's order:
+
+* ``amg``            AMG(k, b, x0, m): m V-cycles for A_k x = b from the initial
+                     guess x0 (Algorithm 3.1, Eqs. Linear_Equation and
+                     inexact_inverse_iter; one V-cycle by default, Sec. 4.1).
+                     Each V-cycle smooths with point l1-Jacobi (one sweep before
+                     and one after the coarse correction; the paper uses
+                     Gauss-Seidel, this solver fixes l1-Jacobi), restricts with
+                     I_k^{k+1} = (I_{k+1}^k)^T, solves the coarsest level exactly
+                     with a Cholesky factor of A_n and prolongates with
+                     I_{k+1}^k (Sec. 2.3).
+* ``correction``     AMGCorrection(n, k, {lambda_j, u_j}) (Algorithm 3.1): the
+                     inexact inverse iteration of step 1, the augmented pencil
+                     (A_{n,k}, M_{n,k}) on V_n + span(V) of step 2, its q smallest
+                     eigenpairs normalised x^T M_{n,k} x = 1 and the recombination
+                     u_j = I_n^k x_j(1:d_n) + V x_j(d_n+1:d_n+q).
+* ``solve``          the AMG Eigenvalue Solver (Algorithm 3.2): the eigenproblem
+                     on level n1 (the coarsest level with at least q+q_extra
+                     dofs, n1 = n by default, Sec. 4.1), then for k = n1-1..1
+                     the prolongation u_k = I_{k+1}^k u_{k+1} and p_k corrections
+                     (p_k = 1 on intermediate levels; on the finest level until the
+                     residual test passes or max_corrections, p_1 <= 20, Sec. 4.1).
+
+Levels are 0-based here: level 0 is the paper's finest level 1, level n-1 its
+coarsest level n.
+
+Readings of the paper taken here (they are listed with the rest of the design):
+* the right-hand side of the AMG call is lambda_j M_k u_j (Eq. Linear_Equation;
+  the shorthand AMG(k, lambda u, u, m) drops M);
+* I_k^n is the restriction chain R_{n-1}...R_k and I_n^k the prolongation chain;
+* the coarsest-level solve inside a V-cycle is exact (Cholesky of A_n);
+* the stopping test is the relative residual
+  max_j ||A u_j - lambda_j M u_j||_2 / (|lambda_j| ||M u_j||_2) <= tol, because the
+  paper's total error e_l needs reference eigenvalues;
+* "select the desired eigenpairs" means the q + q_extra smallest Ritz values;
+* each output vector is signed so that its largest-magnitude entry (lowest
+  index on ties) is positive.
+"""
+from __future__ import annotations
+
+import dataclasses
+import struct
+from typing import List, Optional
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+MAGIC = b"AMGEIGH1"
+
+
+# --------------------------------------------------------------------------
+# hierarchy
+
+
+@dataclasses.dataclass
+class OracleHierarchy:
+    A: List[sp.csr_matrix]
+    M: List[sp.csr_matrix]
+    P: List[sp.csr_matrix]  # P[l] = I_{l+1}^l, N_l x N_{l+1}
+    R: List[sp.csr_matrix]  # R[l] = P[l]^T
+    dinv: List[np.ndarray]  # 1 / sum_j |a_ij|  (l1-Jacobi), levels 0..n-2
+    An: np.ndarray  # dense coarsest A
+    Mn: np.ndarray  # dense coarsest M
+    An_chol: tuple  # scipy cho_factor of An
+
+    @property
+    def n_levels(self) -> int:
+        return len(self.A)
+
+    @property
+    def sizes(self) -> List[int]:
+        return [a.shape[0] for a in self.A]
+
+
+def read_blob(blob: bytes) -> OracleHierarchy:
+    """Parse and validate a hierarchy blob (layout documented by its writer)."""
+    if len(blob) < 24 or len(blob) % 8 or blob[:8] != MAGIC:
+        raise ValueError("not a hierarchy blob")
+    words = np.frombuffer(blob[:-8], dtype="<u8")
+    (stored,) = struct.unpack("<Q", blob[-8:])
+    if int(words.sum(dtype=np.uint64)) != stored:
+        raise ValueError("hierarchy blob checksum mismatch")
+    version, n = struct.unpack_from("<II", blob, 8)
+    if version != 1 or n < 1:
+        raise ValueError("unsupported hierarchy blob")
+    off = 16
+    rows = struct.unpack_from(f"<{n}Q", blob, off)
+    off += 8 * n
+    nnz = struct.unpack_from(f"<{n}Q", blob, off)
+    off += 8 * n
+    nnzp = struct.unpack_from(f"<{n - 1}Q", blob, off) if n > 1 else ()
+    off += 8 * (n - 1)
+    off += (-off) % 8
+
+    def take(count, dt):
+        nonlocal off
+        itemsize = np.dtype(dt).itemsize
+        end = off + count * itemsize
+        if end > len(blob) - 8:
+            raise ValueError("truncated hierarchy blob")
+        arr = np.frombuffer(blob, dtype=dt, count=count, offset=off)
+        off = end + ((-end) % 8)
+        return arr
+
+    A, M, P = [], [], []
+    for l in range(n):
+        rp = take(rows[l] + 1, "<i4")
+        ci = take(nnz[l], "<i4")
+        av = take(nnz[l], "<f8")
+        mv = take(nnz[l], "<f8")
+        shape = (rows[l], rows[l])
+        A.append(sp.csr_matrix((av, ci, rp), shape=shape))
+        M.append(sp.csr_matrix((mv, ci, rp), shape=shape))
+    for l in range(n - 1):
+        rp = take(rows[l] + 1, "<i4")
+        ci = take(nnzp[l], "<i4")
+        pv = take(nnzp[l], "<f8")
+        P.append(sp.csr_matrix((pv, ci, rp), shape=(rows[l], rows[l + 1])))
+    if off != len(blob) - 8:
+        raise ValueError("trailing bytes in hierarchy blob")
+    R = [p.T.tocsr() for p in P]
+    dinv = [1.0 / np.asarray(abs(a).sum(axis=1)).ravel() for a in A[:-1]]
+    An = A[-1].toarray()
+    Mn = M[-1].toarray()
+    return OracleHierarchy(A, M, P, R, dinv, An, Mn, sla.cho_factor(An, lower=True))
+
+
+# --------------------------------------------------------------------------
+# AMG linear solver (Algorithm 3.1 step 1)
+
+
+def jacobi_l1(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """One point l1-Jacobi sweep x <- x + D^-1 (b - A_l x), D = diag(sum_j |a_ij|)."""
+    d = h.dinv[l] if x.ndim == 1 else h.dinv[l][:, None]
+    return x + d * (b - h.A[l] @ x)
+
+
+def vcycle(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray, pre: int = 1, post: int = 1) -> np.ndarray:
+    """One V-cycle for A_l x = b from the initial guess x."""
+    if l == h.n_levels - 1:
+        return sla.cho_solve(h.An_chol, b)
+    for _ in range(pre):
+        x = jacobi_l1(h, l, b, x)
+    r = b - h.A[l] @ x
+    bc = h.R[l] @ r
+    xc = vcycle(h, l + 1, bc, np.zeros_like(bc), pre, post)
+    x = x + h.P[l] @ xc
+    for _ in range(post):
+        x = jacobi_l1(h, l, b, x)
+    return x
+
+
+def amg(h: OracleHierarchy, k: int, b: np.ndarray, x0: np.ndarray, m: int = 1, pre: int = 1, post: int = 1):
+    """AMG(k, b, x0, m): m V-cycles on level k from the initial guess x0."""
+    x = x0
+    for _ in range(m):
+        x = vcycle(h, k, b, x, pre, post)
+    return x
+
+
+# --------------------------------------------------------------------------
+# transfers between level k and the coarsest level
+
+
+def restrict_to_coarsest(h: OracleHierarchy, k: int, X: np.ndarray) -> np.ndarray:
+    """I_k^n X = R_{n-1} ... R_k X (0-based: R[n-2] ... R[k])."""
+    for l in range(k, h.n_levels - 1):
+        X = h.R[l] @ X
+    return X
+
+
+def prolong_from_coarsest(h: OracleHierarchy, k: int, Xc: np.ndarray) -> np.ndarray:
+    """I_n^k Xc = P_k ... P_{n-1} Xc (0-based: P[k] ... P[n-2])."""
+    for l in range(h.n_levels - 2, k - 1, -1):
+        Xc = h.P[l] @ Xc
+    return Xc
+
+
+# --------------------------------------------------------------------------
+# correction step (Algorithm 3.1)
+
+
+@dataclasses.dataclass
+class Options:
+    max_corrections: int = 20
+    v_cycles: int = 1
+    pre_sweeps: int = 1
+    post_sweeps: int = 1
+    q_extra: int = 0
+    fixed_corrections: int = 0  # > 0: run exactly this many finest-level corrections
+
+
+def augmented_pencil(h: OracleHierarchy, k: int, V: np.ndarray):
+    """(A_{n,k}, M_{n,k}) of Algorithm 3.1 step 2 on V_n + span(V)."""
+    AV = h.A[k] @ V
+    MV = h.M[k] @ V
+    CA = restrict_to_coarsest(h, k, AV)
+    CM = restrict_to_coarsest(h, k, MV)
+    Ahat = np.block([[h.An, CA], [CA.T, V.T @ AV]])
+    Mhat = np.block([[h.Mn, CM], [CM.T, V.T @ MV]])
+    return Ahat, Mhat
+
+
+def smallest_pairs(Ahat: np.ndarray, Mhat: np.ndarray, count: int):
+    """The `count` smallest eigenpairs of A x = mu M x with x^T M x = 1 (LAPACK)."""
+    mu, X = sla.eigh(Ahat, Mhat, subset_by_index=[0, count - 1])
+    return mu, X
+
+
+def correction(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
+    """One AMGCorrection(n, k, {lambda_j, u_j}) step; returns (lambda, U)."""
+    qt = U.shape[1]
+    b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
+    V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps)
+    Ahat, Mhat = augmented_pencil(h, k, V)
+    mu, X = smallest_pairs(Ahat, Mhat, qt)
+    dn = h.sizes[-1]
+    U_new = prolong_from_coarsest(h, k, X[:dn]) + V @ X[dn:]
+    return mu, U_new
+
+
+# --------------------------------------------------------------------------
+# solver (Algorithm 3.2)
+
+
+def relres(h: OracleHierarchy, lam: np.ndarray, U: np.ndarray, k: int = 0) -> np.ndarray:
+    """||A u_j - lambda_j M u_j||_2 / (|lambda_j| ||M u_j||_2) per column."""
+    AU = h.A[k] @ U
+    MU = h.M[k] @ U
+    return np.linalg.norm(AU - MU * lam[None, :], axis=0) / (np.abs(lam) * np.linalg.norm(MU, axis=0))
+
+
+def initial_level(h: OracleHierarchy, qt: int) -> int:
+    """n1: the coarsest level with at least qt dofs."""
+    for l in range(h.n_levels - 1, -1, -1):
+        if h.sizes[l] >= qt:
+            return l
+    raise ValueError("q + q_extra exceeds the finest dimension")
+
+
+def sign_normalise(U: np.ndarray) -> np.ndarray:
+    idx = np.argmax(np.abs(U), axis=0)
+    s = np.sign(U[idx, np.arange(U.shape[1])])
+    s[s == 0] = 1.0
+    return U * s[None, :]
+
+
+@dataclasses.dataclass
+class Info:
+    corrections: int  # finest-level corrections performed
+    converged: bool
+    relres: np.ndarray  # final relative residuals (q columns)
+    history: list  # eigenvalue estimates after each finest-level correction
+    n1: int
+
+
+def solve(h: OracleHierarchy, q: int, tol: float = 1e-10, opts: Options = Options()):
+    """Algorithm 3.2.  Returns (lambda[q] ascending, U[N_0, q], Info)."""
+    qt = q + opts.q_extra
+    n1 = initial_level(h, qt)
+    An1 = h.A[n1].toarray()
+    Mn1 = h.M[n1].toarray()
+    lam, U = smallest_pairs(An1, Mn1, qt)
+    for k in range(n1 - 1, 0, -1):
+        U = h.P[k] @ U
+        lam, U = correction(h, k, lam, U, opts)
+    history = []
+    done = 0
+    converged = False
+    if n1 > 0:
+        U = h.P[0] @ U
+        while True:
+            rr = relres(h, lam, U)[:q]
+            if opts.fixed_corrections > 0:
+                if done == opts.fixed_corrections:
+                    converged = bool(np.max(rr) <= tol)
+                    break
+            else:
+                if np.max(rr) <= tol:
+                    converged = True
+                    break
+                if done == opts.max_corrections:
+                    break
+            lam, U = correction(h, 0, lam, U, opts)
+            done += 1
+            history.append(lam[:q].copy())
+    rr = relres(h, lam, U)[:q]
+    if n1 == 0:
+        converged = bool(np.max(rr) <= tol)
+    return lam[:q].copy(), sign_normalise(U[:, :q]), Info(done, converged, rr, history, n1)

@@ -1,0 +1,200 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the dense
+generalized eigensolution (the plain definition of the fixed point), closed-form
+continuum eigenvalues, linear-algebra identities of the V-cycle and of the
+Rayleigh-Ritz step (Sec. 3: the pencil is the Galerkin projection on
+V_n + span(V)), and invariants of the output.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spl
+
+from oracle import amg_oracle as O
+from paper_1503_08462_gb300.inputs import hierarchy, meshes
+
+from helpers import dense_pairs, eig_rel_tol, lam_max, m_subspace_angle, problem_and_blob
+
+
+def _oh(kind="square", size=32, cap=50, seed=1):
+    p, blob, _ = problem_and_blob(kind, size, cap, seed)
+    return p, O.read_blob(blob)
+
+
+# ---------------------------------------------------------------- V-cycle
+
+
+def _vcycle_matrix(oh, l=0):
+    n = oh.sizes[l]
+    return np.stack([O.vcycle(oh, l, e, np.zeros(n)) for e in np.eye(n)], axis=1)
+
+
+def test_vcycle_is_symmetric_and_contracting():
+    """V(1,1) with the same symmetric smoother before and after and R = P^T is
+    a symmetric operator B, and the error propagation I - BA contracts in the
+    A-norm.  A transposed transfer, a missing sweep or a sign error breaks one
+    of these."""
+    p, oh = _oh("square", 16, 20)
+    B = _vcycle_matrix(oh)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    A = oh.A[0].toarray()
+    L = np.linalg.cholesky(A)
+    E = np.eye(A.shape[0]) - B @ A
+    rho = np.linalg.norm(L.T @ E @ np.linalg.inv(L.T), 2)  # A-norm of I - BA
+    assert rho < 0.7, rho
+
+
+def test_vcycle_two_level_dense():
+    """A two-level cycle equals the dense formula S (I - P A_c^-1 P^T A) S' ..."""
+    p = meshes.square_2d(8)
+    h = hierarchy.build_for_problem(p, coarse_cap=25, max_levels=2)
+    oh = O.read_blob(hierarchy.to_blob(h))
+    assert oh.n_levels == 2
+    A = oh.A[0].toarray()
+    P = oh.P[0].toarray()
+    D = np.diag(np.abs(A).sum(axis=1))
+    Ac_inv = np.linalg.inv(P.T @ A @ P)
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(A.shape[0])
+    x0 = rng.standard_normal(A.shape[0])
+    x1 = x0 + np.linalg.solve(D, b - A @ x0)
+    x2 = x1 + P @ Ac_inv @ P.T @ (b - A @ x1)
+    x3 = x2 + np.linalg.solve(D, b - A @ x2)
+    got = O.amg(oh, 0, b, x0, 1)
+    assert np.allclose(got, x3, rtol=1e-12, atol=1e-12 * np.abs(x3).max())
+
+
+def test_amg_iteration_solves_linear_system():
+    p, oh = _oh("lshape", 16, 60)
+    A = oh.A[0]
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal((A.shape[0], 2))
+    x = np.zeros_like(b)
+    xs = np.column_stack([spl.spsolve(A.tocsc(), b[:, j]) for j in range(2)])
+    x = O.amg(oh, 0, b, x, 60)
+    assert np.abs(x - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+def test_l1_jacobi_reduces_energy_error():
+    """The l1 diagonal dominates A (2D - A is SPD), so each sweep is an A-norm contraction."""
+    p, oh = _oh("checker", 16, 30, seed=3)
+    A = oh.A[0]
+    rng = np.random.default_rng(1)
+    e = rng.standard_normal(A.shape[0])
+    for _ in range(5):
+        e_new = O.jacobi_l1(oh, 0, np.zeros_like(e), e)
+        assert e_new @ (A @ e_new) < e @ (A @ e)
+        e = e_new
+
+
+# ---------------------------------------------------------------- Rayleigh-Ritz
+
+
+def _chain_dense(oh, k):
+    """I_n^k as a dense matrix (product of the prolongations)."""
+    Pc = np.eye(oh.sizes[-1])
+    for l in range(oh.n_levels - 2, k - 1, -1):
+        Pc = oh.P[l] @ Pc
+    return np.asarray(Pc)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_pencil_is_galerkin_projection(k):
+    """(A_{n,k}, M_{n,k}) equals B^T (A_k, M_k) B with B = [I_n^k, V]."""
+    p, oh = _oh("square", 16, 20)
+    rng = np.random.default_rng(5)
+    V = rng.standard_normal((oh.sizes[k], 3))
+    Ahat, Mhat = O.augmented_pencil(oh, k, V)
+    Bm = np.hstack([_chain_dense(oh, k), V])
+    for hat, mat in ((Ahat, oh.A[k]), (Mhat, oh.M[k])):
+        ref = Bm.T @ (mat @ Bm)
+        assert np.abs(hat - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_exact_eigenpairs_are_a_fixed_point():
+    p, oh = _oh("square", 32, 50)
+    lam, U = dense_pairs(p, 6)
+    mu, U1 = O.correction(oh, 0, lam, U)
+    assert np.allclose(mu, lam, rtol=1e-11)
+    assert m_subspace_angle(U1[:, :4], U[:, :4], oh.M[0]) < 1e-8
+
+
+def test_rayleigh_ritz_is_basis_invariant():
+    """Replacing V by V Q (Q invertible) leaves the Ritz pairs unchanged."""
+    p, oh = _oh("square", 16, 20)
+    rng = np.random.default_rng(11)
+    V = rng.standard_normal((oh.sizes[0], 4))
+    Q = rng.standard_normal((4, 4)) + 4 * np.eye(4)
+    res = []
+    for W in (V, V @ Q):
+        Ahat, Mhat = O.augmented_pencil(oh, 0, W)
+        mu, X = O.smallest_pairs(Ahat, Mhat, 4)
+        dn = oh.sizes[-1]
+        res.append((mu, O.prolong_from_coarsest(oh, 0, X[:dn]) + W @ X[dn:]))
+    assert np.allclose(res[0][0], res[1][0], rtol=1e-12)
+    assert m_subspace_angle(res[0][1], res[1][1], oh.M[0]) < 1e-10
+
+
+# ---------------------------------------------------------------- full solver
+
+
+# tol: the relative-residual floor of FP64 grows with the coefficient contrast
+# (rounding in A u is ~1e-16 ||A|| ||u||); the 10^(+-3) checkerboard sits near 1e-10.
+@pytest.mark.parametrize("kind,size,cap,seed,q,qe,tol", [("square", 32, 50, 1, 4, 2, 1e-10),
+                                                       ("lshape", 16, 60, 2, 6, 2, 1e-10),
+                                                       ("checker", 32, 60, 3, 5, 2, 2e-9),
+                                                       ("cube", 8, 40, 4, 4, 2, 1e-10)])
+def test_converged_solve_matches_dense_definition(kind, size, cap, seed, q, qe, tol):
+    """Pin 1: the converged iteration reproduces the q smallest dense eigenpairs."""
+    p, oh = _oh(kind, size, cap, seed)
+    lam, U, info = O.solve(oh, q, tol=tol, opts=O.Options(q_extra=qe, max_corrections=100))
+    assert info.converged, info.relres
+    lam_ex, U_ex = dense_pairs(p, q)
+    assert np.all(np.abs(lam - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
+    # compare invariant subspaces (clusters handled by comparing spans)
+    assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
+    # invariants: U^T M U = I, residual, sign convention
+    G = U.T @ (oh.M[0] @ U)
+    assert np.abs(G - np.eye(q)).max() < 1e-11
+    assert np.all(info.relres <= tol)
+    idx = np.argmax(np.abs(U), axis=0)
+    assert np.all(U[idx, np.arange(q)] > 0)
+
+
+def test_ritz_values_are_upper_bounds_and_converge():
+    """Every Ritz value bounds the exact eigenvalue from above (Courant-Fischer)
+    and the total error e_l falls geometrically (Sec. 4.1 ratio)."""
+    p, oh = _oh("square", 32, 50)
+    q = 4
+    lam_ex, _ = dense_pairs(p, q)
+    _, _, info = O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=2, fixed_corrections=8))
+    errs = []
+    for est in info.history:
+        assert np.all(est >= lam_ex * (1 - 1e-12))
+        errs.append(np.sum(est - lam_ex))
+    ratio = (errs[-1] / errs[0]) ** (1.0 / (len(errs) - 1))
+    assert ratio < 0.35, ratio
+
+
+def test_single_level_hierarchy_is_dense_solve():
+    p = meshes.square_2d(8)
+    oh = O.read_blob(hierarchy.to_blob(hierarchy.build_for_problem(p, coarse_cap=1000)))
+    lam, U, info = O.solve(oh, 3)
+    lam_ex, U_ex = dense_pairs(p, 3)
+    assert np.allclose(lam, lam_ex, rtol=1e-13)
+    assert info.corrections == 0 and info.n1 == 0
+
+
+def test_closed_form_unit_square():
+    """The converged solver approaches pi^2 (2, 5, 5, 8) at O(h^2) (Example 1)."""
+    exact = np.pi ** 2 * np.array([2.0, 5.0, 5.0, 8.0])
+    errs = []
+    for m in (8, 16, 32):
+        p = meshes.square_2d(m, seed=1)
+        oh = O.read_blob(hierarchy.to_blob(hierarchy.build_for_problem(p, coarse_cap=20)))
+        lam, _, info = O.solve(oh, 4, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=60))
+        assert info.converged
+        errs.append(np.mean(np.abs(lam - exact) / exact))
+    slope = np.polyfit(np.log([1 / 8, 1 / 16, 1 / 32]), np.log(errs), 1)[0]
+    assert 1.7 < slope < 2.4, slope
