@@ -1,0 +1,164 @@
+/*
+ * amgeig.h -- C ABI of the GB300 (sm_103a) solve phase of the algebraic
+ * multigrid multilevel-correction eigensolver of Zhang, Han, He, Xie and You,
+ * "An Algebraic Multigrid Method for Eigenvalue Problems in Some Different
+ * Cases" (arXiv:1503.08462).
+ *
+ * Problem (Sec. 1, Eq. eigenvalue_problem): find the q smallest eigenpairs
+ * (lambda_j, u_j) of A u = lambda M u with A sparse SPD and M sparse SPD, and
+ * u_j^T M u_k = delta_jk.  The AMG hierarchy of Sec. 2 (levels A_k, M_k and
+ * prolongations I_{k+1}^k) is built once on the host and handed over as a
+ * serialized blob; this library runs Algorithm 3.2 (AMG Eigenvalue Solver)
+ * with Algorithm 3.1 (AMG Correction Step) on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - return value: AMGEIG_OK (0) or a negative AMGEIG_E* code; no call aborts
+ *     the process.  amgeig_strerror() names a code; amgeig_last_error() gives a
+ *     one-line description of the most recent failure on the calling thread.
+ *   - caller buffers are read (or written) only during the call; the library
+ *     keeps no pointer to them.
+ *   - dense blocks of vectors are row-major N x q: entry (i, j) of vector j is
+ *     at index i * q + j.
+ *   - level 0 is the paper's finest level 1; level n-1 its coarsest level n.
+ */
+#ifndef AMGEIG_H
+#define AMGEIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define AMGEIG_OK 0
+#define AMGEIG_EINVAL (-1)   /* invalid argument (NULL pointer, q out of range, ...) */
+#define AMGEIG_ECORRUPT (-2) /* hierarchy blob fails validation (magic, checksum, bounds) */
+#define AMGEIG_ENOMEM (-3)   /* device allocation failed or admission refused */
+#define AMGEIG_ENOTSPD (-4)  /* a Cholesky factorisation met a non-positive pivot */
+#define AMGEIG_ENOCONV (-5)  /* max_corrections reached; outputs are still written */
+#define AMGEIG_ENAN (-6)     /* a NaN or Inf appeared in the iterates */
+#define AMGEIG_ECUDA (-7)    /* CUDA runtime error (see amgeig_last_error) */
+#define AMGEIG_ENOTFOUND (-8) /* unknown request id */
+
+/* ---- precision of the V-cycle ------------------------------------------- */
+#define AMGEIG_FP64 0       /* every step in float64 */
+#define AMGEIG_MIXED_FP32 1 /* V-cycle (smoothing, transfers, coarse solve) in float32;
+                               defect, Rayleigh-Ritz, Gram/cross blocks and the
+                               recombination stay in float64 */
+
+typedef struct amgeig_hierarchy_t* amgeig_hierarchy;
+
+/* Solver options.  Defaults (amgeig_default_options) follow Sec. 4.1 except the
+ * smoother: one V-cycle (m = 1) with one pre- and one post-smoothing sweep of
+ * point l1-Jacobi (the paper smooths with Gauss-Seidel), n1 = n, p_k = 1 on the
+ * intermediate levels and at most 20 corrections on the finest level. */
+typedef struct {
+  int max_corrections;   /* finest-level corrections at most (p_1 <= 20, Sec. 4.1) */
+  int v_cycles;          /* m, V-cycles per AMG call (Eq. inexact_inverse_iter), >= 1 */
+  int pre_sweeps;        /* l1-Jacobi sweeps before the coarse correction, >= 0 */
+  int post_sweeps;       /* l1-Jacobi sweeps after the coarse correction, >= 0 */
+  int q_extra;           /* extra eigenpairs carried along (Sec. 4, Examples 4-6), >= 0 */
+  int precision;         /* AMGEIG_FP64 or AMGEIG_MIXED_FP32 */
+  int fixed_corrections; /* > 0: run exactly this many finest-level corrections and
+                            ignore tol (iteration-level parity mode) */
+  int reserved;          /* must be 0 */
+} amgeig_options;
+
+/* Per-solve report. */
+typedef struct {
+  int corrections;   /* finest-level corrections performed */
+  int converged;     /* 1 if max_j relres_j <= tol */
+  int n1;            /* initial level (0-based) */
+  int status;        /* AMGEIG_OK or the error code of the solve */
+  double max_relres; /* max_j ||A u_j - lambda_j M u_j||_2 / (|lambda_j| ||M u_j||_2), j < q */
+} amgeig_info;
+
+/* Fill *opt with the defaults above.  opt must not be NULL. */
+void amgeig_default_options(amgeig_options* opt);
+
+/* Load a serialized hierarchy (layout: the writer in the package's
+ * inputs/hierarchy.py; magic "AMGEIGH1", u64 checksum trailer) onto CUDA device
+ * `device`.  blob: host pointer to `bytes` bytes, read during the call only.
+ * The library copies every level (A_k, M_k in one shared-pattern CSR, P_k and
+ * its transpose R_k = P_k^T, Sec. 2.3) to the device, derives the l1-Jacobi
+ * diagonals and float32 copies, and computes once, on the GPU, the
+ * M_n-orthonormal eigenbasis of the coarsest pencil (A_n, M_n) used by step 1
+ * of Algorithm 3.2 and by every correction.  On success *out owns all device
+ * memory of the hierarchy until amgeig_free_hierarchy.  Errors: EINVAL (NULL
+ * argument, bad device), ECORRUPT (validation), ENOMEM, ENOTSPD (A_n or M_n not
+ * SPD), ECUDA. */
+int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hierarchy* out);
+
+/* Release every device and host resource of h.  NULL is accepted.  Pending
+ * requests on h must have been polled to completion first (EINVAL otherwise). */
+int amgeig_free_hierarchy(amgeig_hierarchy h);
+
+/* Level count and per-level sizes: n_levels receives n; sizes (may be NULL)
+ * receives min(n, max_sizes) row counts N_0 >= ... >= N_{n-1}. */
+int amgeig_hierarchy_info(amgeig_hierarchy h, int* n_levels, int64_t* sizes, int max_sizes);
+
+/* Algorithm 3.2 with Algorithm 3.1 on the GPU.
+ *   q         number of wanted eigenpairs, 1 <= q, q + q_extra <= N_{n-1} (the
+ *             coarsest dimension must hold the initial eigenproblem, n1 = n).
+ *   tol       stopping test max_j relres_j <= tol on the finest level (the paper
+ *             stops on the total error against reference eigenvalues, Sec. 4.1,
+ *             which a solver cannot know).
+ *   opt       options, NULL for defaults.
+ *   eigvals   host buffer of q doubles: the q smallest Ritz values, ascending.
+ *   eigvecs   buffer of N_0 * q doubles, row-major N_0 x q: M-orthonormal vectors,
+ *             each signed so that its largest-magnitude entry (lowest index on
+ *             ties) is positive.  Device pointer if eigvecs_on_device != 0, host
+ *             pointer otherwise; NULL skips the vectors.
+ *   info      report (may be NULL).
+ *   stream    cudaStream_t to run on (NULL: the library's own stream).  The call
+ *             returns after the results are in the caller's buffers.
+ * Errors: EINVAL, ENOMEM, ENOTSPD (the Gram block of the augmented pencil is not
+ * SPD), ENAN, ECUDA.  ENOCONV when max_corrections ran out: eigvals, eigvecs and
+ * info are still written. */
+int amgeig_solve(amgeig_hierarchy h, int q, double tol, const amgeig_options* opt, double* eigvals,
+                 double* eigvecs, int eigvecs_on_device, amgeig_info* info, void* stream);
+
+/* Serving: queue a solve on h and return at once with *request_id.  The options
+ * are copied.  Requests run on a library thread in arrival order; each keeps
+ * its hierarchy and iterate block resident on the device, and a request is
+ * admitted only when its workspace fits in free device memory (ENOMEM is
+ * reported through amgeig_poll if it can never fit).  Errors: EINVAL. */
+int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* opt, uint64_t* request_id);
+
+/* Poll a request.  *done = 0 while it is queued or running.  Once done, copies
+ * the q eigenvalues (host, may be NULL), the N_0 x q eigenvectors (host, may be
+ * NULL) and the report (may be NULL), releases the request and returns its
+ * status (AMGEIG_OK, ENOCONV, ...).  Errors: ENOTFOUND for an unknown or already
+ * released id. */
+int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs, amgeig_info* info);
+
+/* ---- building blocks, exposed for verification -------------------------- */
+
+/* The nwant smallest eigenpairs of the symmetric n x n matrix H (host, row-major,
+ * float64), computed on device `device` by the solver's own dense eigensolver
+ * (the black-box eigensolver of Algorithm 3.1 step 2: Householder
+ * tridiagonalisation, Sturm bisection, inverse iteration and a Rayleigh-Ritz
+ * clean-up, in float-float arithmetic).  evals: host, nwant doubles ascending;
+ * evecs: host, n x nwant row-major, orthonormal columns.  1 <= nwant <= n <= 2048.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals, double* evecs);
+
+/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h (Algorithm
+ * 3.1 step 1 with the options' pre/post l1-Jacobi sweeps and precision): b and
+ * x are host buffers of N_l x width doubles (row-major), 1 <= width <= 128.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* b,
+                        double* x);
+
+/* Static description of a status code. */
+const char* amgeig_strerror(int code);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char* amgeig_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMGEIG_H */

@@ -1,0 +1,225 @@
+"""Thin ctypes binding of the C ABI in include/amgeig.h (argument marshalling only).
+
+Every function here forwards to ``libamgeig.so``; no step of the solve runs in
+Python.  Arrays may be NumPy arrays (host) or torch tensors (host or CUDA); they
+must be C-contiguous float64.  If the library has not been built the import of
+any entry point raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _build
+
+AMGEIG_OK = 0
+AMGEIG_EINVAL = -1
+AMGEIG_ECORRUPT = -2
+AMGEIG_ENOMEM = -3
+AMGEIG_ENOTSPD = -4
+AMGEIG_ENOCONV = -5
+AMGEIG_ENAN = -6
+AMGEIG_ECUDA = -7
+AMGEIG_ENOTFOUND = -8
+
+AMGEIG_FP64 = 0
+AMGEIG_MIXED_FP32 = 1
+
+
+class AmgEigError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail} (code {code})")
+        self.code = code
+
+
+class amgeig_options(ctypes.Structure):
+    _fields_ = [("max_corrections", ctypes.c_int), ("v_cycles", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
+                ("post_sweeps", ctypes.c_int), ("q_extra", ctypes.c_int), ("precision", ctypes.c_int),
+                ("fixed_corrections", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class amgeig_info(ctypes.Structure):
+    _fields_ = [("corrections", ctypes.c_int), ("converged", ctypes.c_int), ("n1", ctypes.c_int),
+                ("status", ctypes.c_int), ("max_relres", ctypes.c_double)]
+
+
+_lib = None
+EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
+            "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
+            "amgeig_sym_eigh", "amgeig_apply_vcycle"]
+
+
+def library_path() -> str:
+    return str(_build.CUDA_LIB)
+
+
+def lib():
+    """Load libamgeig.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libamgeig.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.amgeig_default_options.argtypes = [ctypes.POINTER(amgeig_options)]
+        L.amgeig_default_options.restype = None
+        L.amgeig_load_hierarchy.argtypes = [vp, ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+        L.amgeig_free_hierarchy.argtypes = [vp]
+        L.amgeig_hierarchy_info.argtypes = [vp, ctypes.POINTER(i32), vp, i32]
+        L.amgeig_solve.argtypes = [vp, i32, dbl, ctypes.POINTER(amgeig_options), vp, vp, i32,
+                                   ctypes.POINTER(amgeig_info), vp]
+        L.amgeig_submit.argtypes = [vp, i32, dbl, ctypes.POINTER(amgeig_options), ctypes.POINTER(ctypes.c_uint64)]
+        L.amgeig_poll.argtypes = [ctypes.c_uint64, ctypes.POINTER(i32), vp, vp, ctypes.POINTER(amgeig_info)]
+        L.amgeig_strerror.argtypes = [i32]
+        L.amgeig_strerror.restype = ctypes.c_char_p
+        L.amgeig_last_error.argtypes = []
+        L.amgeig_last_error.restype = ctypes.c_char_p
+        L.amgeig_sym_eigh.argtypes = [i32, i32, i32, vp, vp, vp]
+        L.amgeig_apply_vcycle.argtypes = [vp, i32, i32, ctypes.POINTER(amgeig_options), vp, vp]
+        for name in ("amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
+                     "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str, allow=(AMGEIG_OK,)) -> int:
+    if code not in allow:
+        L = lib()
+        raise AmgEigError(code, where, f"{L.amgeig_strerror(code).decode()}: {L.amgeig_last_error().decode()}")
+    return code
+
+
+def _ptr(a) -> Optional[int]:
+    """Data pointer of a C-contiguous float64 NumPy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float64 array")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def amgeig_default_options() -> amgeig_options:
+    o = amgeig_options()
+    lib().amgeig_default_options(ctypes.byref(o))
+    return o
+
+
+def amgeig_load_hierarchy(blob: bytes, device: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().amgeig_load_hierarchy(buf, len(blob), device, ctypes.byref(h)), "amgeig_load_hierarchy")
+    return h
+
+
+def amgeig_free_hierarchy(h) -> None:
+    _check(lib().amgeig_free_hierarchy(h), "amgeig_free_hierarchy")
+
+
+def amgeig_hierarchy_info(h):
+    n = ctypes.c_int()
+    sizes = (ctypes.c_int64 * 64)()
+    _check(lib().amgeig_hierarchy_info(h, ctypes.byref(n), sizes, 64), "amgeig_hierarchy_info")
+    return [int(sizes[i]) for i in range(n.value)]
+
+
+def amgeig_solve(h, q: int, tol: float, opt: Optional[amgeig_options], eigvals, eigvecs, eigvecs_on_device: bool,
+                 info: Optional[amgeig_info] = None, stream: Optional[int] = None) -> int:
+    """Forward to amgeig_solve; returns AMGEIG_OK or AMGEIG_ENOCONV, raises otherwise."""
+    code = lib().amgeig_solve(h, q, tol, ctypes.byref(opt) if opt is not None else None, _ptr(eigvals),
+                              _ptr(eigvecs), 1 if eigvecs_on_device else 0,
+                              ctypes.byref(info) if info is not None else None, stream)
+    return _check(code, "amgeig_solve", allow=(AMGEIG_OK, AMGEIG_ENOCONV))
+
+
+def amgeig_submit(h, q: int, tol: float, opt: Optional[amgeig_options] = None) -> int:
+    rid = ctypes.c_uint64()
+    _check(lib().amgeig_submit(h, q, tol, ctypes.byref(opt) if opt is not None else None, ctypes.byref(rid)),
+           "amgeig_submit")
+    return rid.value
+
+
+def amgeig_poll(request_id: int, eigvals=None, eigvecs=None, info: Optional[amgeig_info] = None) -> Tuple[bool, int]:
+    done = ctypes.c_int()
+    code = lib().amgeig_poll(request_id, ctypes.byref(done), _ptr(eigvals), _ptr(eigvecs),
+                             ctypes.byref(info) if info is not None else None)
+    if done.value == 0:
+        _check(code, "amgeig_poll")
+        return False, code
+    return True, code
+
+
+def amgeig_sym_eigh(H: np.ndarray, nwant: int, device: int = 0):
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    n = H.shape[0]
+    evals = np.empty(nwant)
+    evecs = np.empty((n, nwant))
+    _check(lib().amgeig_sym_eigh(device, n, nwant, _ptr(H), _ptr(evals), _ptr(evecs)), "amgeig_sym_eigh")
+    return evals, evecs
+
+
+def amgeig_apply_vcycle(h, level: int, b: np.ndarray, opt: Optional[amgeig_options] = None) -> np.ndarray:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty_like(b)
+    _check(lib().amgeig_apply_vcycle(h, level, b.shape[1], ctypes.byref(opt) if opt is not None else None, _ptr(b),
+                                     _ptr(x)), "amgeig_apply_vcycle")
+    return x
+
+
+def strerror(code: int) -> str:
+    return lib().amgeig_strerror(code).decode()
+
+
+# ---------------------------------------------------------------- convenience
+
+
+def options(**kw) -> amgeig_options:
+    o = amgeig_default_options()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Hierarchy:
+    """Owns a loaded hierarchy handle (amgeig_load_hierarchy / amgeig_free_hierarchy)."""
+
+    def __init__(self, blob: bytes, device: int = 0):
+        self.handle = amgeig_load_hierarchy(blob, device)
+        self.sizes = amgeig_hierarchy_info(self.handle)
+
+    def solve(self, q: int, tol: float = 1e-10, opt: Optional[amgeig_options] = None, vectors: bool = True):
+        """Return (eigvals[q], eigvecs[N0, q] or None, info, status) through amgeig_solve (host buffers)."""
+        vals = np.empty(q)
+        vecs = np.empty((self.sizes[0], q)) if vectors else None
+        info = amgeig_info()
+        code = amgeig_solve(self.handle, q, tol, opt, vals, vecs, False, info)
+        return vals, vecs, info, code
+
+    def close(self):
+        if self.handle is not None:
+            amgeig_free_hierarchy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1007 @@
+// C ABI of the solve phase: hierarchy loading, the solve driver (Algorithm 3.2
+// around Algorithm 3.1) and the request service.  Every arithmetic step of a
+// solve runs in the kernels of spmm.cu, dense.cu and pencil.cu; the host only
+// validates input, moves data and sequences launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "amgeig.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace amgeig;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(expr)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? AMGEIG_ENOMEM : AMGEIG_ECUDA,                  \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                             \
+    }                                                                                              \
+  } while (0)
+
+// ------------------------------------------------------------------ small kernels
+
+// per-column (max |u|, lowest index) over rows; one block per column
+__global__ void k_col_sign(const double* __restrict__ U, int rows, int ld, int q, double* __restrict__ sign) {
+  const int c = blockIdx.x;
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    const double a = fabs(U[static_cast<long long>(i) * ld + c]);
+    if (a > best || (a == best && i < bi)) {
+      best = a;
+      bi = i;
+    }
+  }
+  __shared__ double sb[256];
+  __shared__ int si[256];
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double b2 = sb[threadIdx.x + s];
+      const int i2 = si[threadIdx.x + s];
+      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sb[threadIdx.x] = b2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sign[c] = (si[0] < rows && U[static_cast<long long>(si[0]) * ld + c] < 0.0) ? -1.0 : 1.0;
+}
+
+__global__ void k_out_vectors(const double* __restrict__ U, int rows, int ld, int q, const double* __restrict__ sign,
+                              double* __restrict__ out) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / q;
+    const int c = static_cast<int>(i % q);
+    out[i] = sign[c] * U[r * ld + c];
+  }
+}
+
+__global__ void k_copy_d(const double* __restrict__ a, int n, double* __restrict__ b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+// ------------------------------------------------------------------ blob parsing
+
+struct HostCsr {
+  int64_t rows = 0, cols = 0;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> a, m;
+};
+
+struct Reader {
+  const uint8_t* p;
+  size_t n, off;
+  bool ok = true;
+  template <typename T>
+  bool take(std::vector<T>& out, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (off + bytes > n - 8 || count > (n / sizeof(T))) return ok = false;
+    out.resize(count);
+    std::memcpy(out.data(), p + off, bytes);
+    off += bytes;
+    off += (8 - off % 8) % 8;
+    return true;
+  }
+};
+
+bool csr_valid(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, int64_t rows, int64_t cols) {
+  if (static_cast<int64_t>(rp.size()) != rows + 1 || rp[0] != 0) return false;
+  for (int64_t i = 0; i < rows; ++i)
+    if (rp[i + 1] < rp[i]) return false;
+  if (static_cast<size_t>(rp[rows]) != ci.size()) return false;
+  for (int32_t c : ci)
+    if (c < 0 || c >= cols) return false;
+  return true;
+}
+
+int parse_blob(const void* blob, size_t bytes, std::vector<HostCsr>& levels, std::vector<HostCsr>& prolong) {
+  const uint8_t* b = static_cast<const uint8_t*>(blob);
+  if (bytes < 24 || bytes % 8 != 0 || std::memcmp(b, "AMGEIGH1", 8) != 0)
+    return fail(AMGEIG_ECORRUPT, "not a hierarchy blob (magic/length)");
+  uint64_t sum = 0, stored;
+  for (size_t i = 0; i + 8 < bytes; i += 8) {
+    uint64_t w;
+    std::memcpy(&w, b + i, 8);
+    sum += w;
+  }
+  std::memcpy(&stored, b + bytes - 8, 8);
+  if (sum != stored) return fail(AMGEIG_ECORRUPT, "hierarchy blob checksum mismatch");
+  uint32_t version, n;
+  std::memcpy(&version, b + 8, 4);
+  std::memcpy(&n, b + 12, 4);
+  if (version != 1 || n < 1 || n > 64) return fail(AMGEIG_ECORRUPT, "unsupported blob version or level count");
+  size_t off = 16;
+  if (off + 8ull * (3 * n - 1) > bytes - 8) return fail(AMGEIG_ECORRUPT, "truncated blob header");
+  std::vector<uint64_t> rows(n), nnz(n), nnzp(n > 1 ? n - 1 : 0);
+  std::memcpy(rows.data(), b + off, 8 * n);
+  off += 8 * n;
+  std::memcpy(nnz.data(), b + off, 8 * n);
+  off += 8 * n;
+  if (n > 1) std::memcpy(nnzp.data(), b + off, 8 * (n - 1));
+  off += 8 * (n - 1);
+  off += (8 - off % 8) % 8;
+  for (uint32_t l = 0; l < n; ++l) {
+    if (rows[l] == 0 || rows[l] >= (1ull << 31) || nnz[l] >= (1ull << 31)) return fail(AMGEIG_ECORRUPT, "level size out of range");
+    if (l > 0 && rows[l] >= rows[l - 1]) return fail(AMGEIG_ECORRUPT, "levels must shrink");
+  }
+  Reader rd{b, bytes, off};
+  levels.assign(n, HostCsr());
+  prolong.assign(n > 1 ? n - 1 : 0, HostCsr());
+  for (uint32_t l = 0; l < n; ++l) {
+    HostCsr& L = levels[l];
+    L.rows = L.cols = static_cast<int64_t>(rows[l]);
+    if (!rd.take(L.rp, rows[l] + 1) || !rd.take(L.ci, nnz[l]) || !rd.take(L.a, nnz[l]) || !rd.take(L.m, nnz[l]))
+      return fail(AMGEIG_ECORRUPT, "truncated level arrays");
+    if (!csr_valid(L.rp, L.ci, L.rows, L.cols)) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
+  }
+  for (uint32_t l = 0; l + 1 < n; ++l) {
+    HostCsr& P = prolong[l];
+    P.rows = static_cast<int64_t>(rows[l]);
+    P.cols = static_cast<int64_t>(rows[l + 1]);
+    if (nnzp[l] >= (1ull << 31)) return fail(AMGEIG_ECORRUPT, "prolongation size out of range");
+    if (!rd.take(P.rp, rows[l] + 1) || !rd.take(P.ci, nnzp[l]) || !rd.take(P.a, nnzp[l]))
+      return fail(AMGEIG_ECORRUPT, "truncated prolongation arrays");
+    if (!csr_valid(P.rp, P.ci, P.rows, P.cols)) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
+  }
+  if (rd.off != bytes - 8) return fail(AMGEIG_ECORRUPT, "trailing bytes in blob");
+  return AMGEIG_OK;
+}
+
+HostCsr transpose(const HostCsr& P) {
+  HostCsr R;
+  R.rows = P.cols;
+  R.cols = P.rows;
+  R.rp.assign(P.cols + 1, 0);
+  for (int32_t c : P.ci) R.rp[c + 1]++;
+  for (int64_t j = 0; j < P.cols; ++j) R.rp[j + 1] += R.rp[j];
+  R.ci.resize(P.ci.size());
+  R.a.resize(P.ci.size());
+  std::vector<int32_t> pos(R.rp.begin(), R.rp.end() - 1);
+  for (int64_t i = 0; i < P.rows; ++i)
+    for (int32_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
+      const int32_t k = pos[P.ci[p]]++;
+      R.ci[k] = static_cast<int32_t>(i);
+      R.a[k] = P.a[p];
+    }
+  return R;
+}
+
+// ------------------------------------------------------------------ device data
+
+struct DeviceBuffers {
+  std::vector<void*> ptrs;
+  ~DeviceBuffers() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t alloc(T** out, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (count > 0 ? count : 1));
+    if (e == cudaSuccess) ptrs.push_back(p);
+    *out = static_cast<T*>(p);
+    return e;
+  }
+  template <typename T>
+  cudaError_t upload(T** out, const std::vector<T>& v) {
+    cudaError_t e = alloc(out, v.size());
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+  }
+};
+
+struct SolveWork;
+
+}  // namespace
+
+struct amgeig_hierarchy_t {
+  int device = 0;
+  int nlev = 0;
+  std::vector<int64_t> sizes;
+  std::vector<DevCsr> A;  // v64 = A, m64 = M, v32 = float(A)
+  std::vector<double*> dinv64;
+  std::vector<float*> dinv32;
+  std::vector<DevCsr> P, R;  // v64 and v32
+  int dn = 0;
+  double *An = nullptr, *Mn = nullptr, *Z = nullptr, *theta = nullptr, *Ainv = nullptr;
+  float* Ainv32 = nullptr;
+  int* dstatus = nullptr;
+  DeviceBuffers mem;
+  std::mutex mu;  // one solve at a time per hierarchy (shared workspace)
+  std::unique_ptr<SolveWork> ws;
+  cudaStream_t stream = nullptr;
+  std::atomic<int> pending{0};
+  ~amgeig_hierarchy_t();
+};
+
+namespace {
+
+struct SolveWork {
+  int qt = 0;
+  int precision = -1;
+  int vcycles = 1;
+  DeviceBuffers mem;
+  double *U = nullptr, *Ualt = nullptr, *V = nullptr, *W = nullptr;
+  std::vector<double*> B64, X64, T64, D64, E64;  // per level (FP64 V-cycle)
+  std::vector<float*> B32, X32, T32, D32, E32;   // per level (FP32 V-cycle)
+  std::vector<double*> WC, PX;                   // restriction chain [N][2q], prolongation chain [N][q]
+  double *partials = nullptr, *sums = nullptr, *relres = nullptr, *lam = nullptr, *mu = nullptr;
+  double *C = nullptr, *G = nullptr, *gsc = nullptr, *Xc = nullptr, *Yv = nullptr, *sign = nullptr;
+  int* flags = nullptr;
+  PencilWork* pw = nullptr;
+  ~SolveWork() { pencil_work_destroy(pw); }
+};
+
+int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, std::unique_ptr<SolveWork>& out) {
+  auto w = std::make_unique<SolveWork>();
+  w->qt = qt;
+  w->precision = precision;
+  w->vcycles = vcycles;
+  const int n = h->nlev;
+  const int64_t N0 = h->sizes[0];
+  auto& m = w->mem;
+  CK(m.alloc(&w->U, N0 * qt));
+  CK(m.alloc(&w->Ualt, N0 * qt));
+  CK(m.alloc(&w->V, N0 * qt));
+  CK(m.alloc(&w->W, N0 * 2 * qt));
+  w->B64.assign(n, nullptr);
+  w->X64.assign(n, nullptr);
+  w->T64.assign(n, nullptr);
+  w->D64.assign(n, nullptr);
+  w->E64.assign(n, nullptr);
+  w->B32.assign(n, nullptr);
+  w->X32.assign(n, nullptr);
+  w->T32.assign(n, nullptr);
+  w->D32.assign(n, nullptr);
+  w->E32.assign(n, nullptr);
+  w->WC.assign(n, nullptr);
+  w->PX.assign(n, nullptr);
+  for (int l = 0; l < n; ++l) {
+    const int64_t Nl = h->sizes[l];
+    if (precision == AMGEIG_FP64) {
+      CK(m.alloc(&w->B64[l], Nl * qt));
+      CK(m.alloc(&w->X64[l], Nl * qt));
+      CK(m.alloc(&w->T64[l], Nl * qt));
+      if (vcycles > 1) {
+        CK(m.alloc(&w->D64[l], Nl * qt));
+        CK(m.alloc(&w->E64[l], Nl * qt));
+      }
+    } else {
+      CK(m.alloc(&w->B32[l], Nl * qt));
+      CK(m.alloc(&w->X32[l], Nl * qt));
+      CK(m.alloc(&w->T32[l], Nl * qt));
+      if (vcycles > 1) {
+        CK(m.alloc(&w->D32[l], Nl * qt));
+        CK(m.alloc(&w->E32[l], Nl * qt));
+      }
+    }
+    if (l > 0) CK(m.alloc(&w->WC[l], Nl * 2 * qt));
+    CK(m.alloc(&w->PX[l], Nl * qt));
+  }
+  const int blocks_max = ceil_div(N0, 8) + 1;  // defect launches use >= 8 rows per block
+  CK(m.alloc(&w->partials, static_cast<size_t>(blocks_max) * 2 * qt));
+  CK(m.alloc(&w->sums, 2 * qt));
+  CK(m.alloc(&w->relres, qt));
+  CK(m.alloc(&w->lam, qt));
+  CK(m.alloc(&w->mu, qt));
+  CK(m.alloc(&w->C, static_cast<size_t>(h->dn) * 2 * qt));
+  CK(m.alloc(&w->G, static_cast<size_t>(qt) * 2 * qt));
+  size_t gs = 0;
+  for (int l = 0; l < n; ++l) gs = std::max(gs, gram_scratch_doubles(static_cast<int>(h->sizes[l]), qt, 2 * qt));
+  CK(m.alloc(&w->gsc, gs));
+  CK(m.alloc(&w->Xc, static_cast<size_t>(h->dn) * qt));
+  CK(m.alloc(&w->Yv, static_cast<size_t>(qt) * qt));
+  CK(m.alloc(&w->sign, qt));
+  CK(m.alloc(&w->flags, 4));
+  cudaError_t e;
+  w->pw = pencil_work_create(h->dn, qt, &e);
+  if (!w->pw) return fail(AMGEIG_ENOMEM, std::string("pencil workspace: ") + cudaGetErrorString(e));
+  out = std::move(w);
+  return AMGEIG_OK;
+}
+
+// ------------------------------------------------------------------ V-cycle
+
+template <typename T>
+struct VBufs;
+template <>
+struct VBufs<double> {
+  static std::vector<double*>& B(SolveWork* w) { return w->B64; }
+  static std::vector<double*>& X(SolveWork* w) { return w->X64; }
+  static std::vector<double*>& Tm(SolveWork* w) { return w->T64; }
+  static std::vector<double*>& D(SolveWork* w) { return w->D64; }
+  static std::vector<double*>& E(SolveWork* w) { return w->E64; }
+};
+template <>
+struct VBufs<float> {
+  static std::vector<float*>& B(SolveWork* w) { return w->B32; }
+  static std::vector<float*>& X(SolveWork* w) { return w->X32; }
+  static std::vector<float*>& Tm(SolveWork* w) { return w->T32; }
+  static std::vector<float*>& D(SolveWork* w) { return w->D32; }
+  static std::vector<float*>& E(SolveWork* w) { return w->E32; }
+};
+
+void presmooth_residual(const DevCsr& A, const double* d, const double* b, int wdt, double* x, double* r, cudaStream_t s) { launch_presmooth_residual_f64(A, d, b, wdt, x, r, s); }
+void presmooth_residual(const DevCsr& A, const float* d, const float* b, int wdt, float* x, float* r, cudaStream_t s) { launch_presmooth_residual_f32(A, d, b, wdt, x, r, s); }
+void jacobi(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, double* o, cudaStream_t s) { launch_jacobi_f64(A, d, b, x, wdt, o, s); }
+void jacobi(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, float* o, cudaStream_t s) { launch_jacobi_f32(A, d, b, x, wdt, o, s); }
+void residual(const DevCsr& A, const double* b, const double* x, int wdt, double* r, cudaStream_t s) { launch_residual_f64(A, b, x, wdt, r, s); }
+void residual(const DevCsr& A, const float* b, const float* x, int wdt, float* r, cudaStream_t s) { launch_residual_f32(A, b, x, wdt, r, s); }
+void spmm(const DevCsr& S, const double* X, int wdt, double* Y, bool acc, cudaStream_t s) { launch_spmm_f64(S, X, wdt, Y, acc, s); }
+void spmm(const DevCsr& S, const float* X, int wdt, float* Y, bool acc, cudaStream_t s) { launch_spmm_f32(S, X, wdt, Y, acc, s); }
+void jacobi_to_v(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, const double* U, double* V, cudaStream_t s) { launch_jacobi_to_v_f64(A, d, b, x, wdt, U, V, s); }
+void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s) { launch_jacobi_to_v_f32(A, d, b, x, wdt, U, V, s); }
+void add_to_v(const double* U, const double* x, long long c, double* V, cudaStream_t s) { launch_add_to_v_f64(U, x, c, V, s); }
+void add_to_v(const double* U, const float* x, long long c, double* V, cudaStream_t s) { launch_add_to_v_f32(U, x, c, V, s); }
+void axpy(const double* x, long long c, double* y, cudaStream_t s) { launch_axpy_f64(x, c, y, s); }
+void axpy(const float* x, long long c, float* y, cudaStream_t s) { launch_axpy_f32(x, c, y, s); }
+const double* dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->dinv64[l]; }
+const float* dinv_of(amgeig_hierarchy_t* h, int l, float*) { return h->dinv32[l]; }
+void coarse_solve(amgeig_hierarchy_t* h, const double* b, int q, double* x, cudaStream_t s) {
+  launch_gemm_f64(h->dn, q, h->dn, 1.0, h->Ainv, h->dn, false, b, q, false, 0.0, x, q, s);
+}
+void coarse_solve(amgeig_hierarchy_t* h, const float* b, int q, float* x, cudaStream_t s) {
+  launch_gemm_f32(h->dn, q, h->dn, 1.0f, h->Ainv32, h->dn, false, b, q, false, 0.0f, x, q, s);
+}
+
+// One V-cycle for A_k x = B[k] from x = 0; the result is left in X[k] unless
+// to_v, in which case the last sweep on level k writes V = U + x instead.
+template <typename T>
+void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool to_v, const double* U, double* V,
+            cudaStream_t st) {
+  const int q = w->qt;
+  const int n = h->nlev;
+  auto& B = VBufs<T>::B(w);
+  auto& X = VBufs<T>::X(w);
+  auto& Tm = VBufs<T>::Tm(w);
+  T* dummy = nullptr;
+  for (int l = k; l < n - 1; ++l) {
+    const DevCsr& A = h->A[l];
+    const T* d = dinv_of(h, l, dummy);
+    if (pre >= 1) {
+      presmooth_residual(A, d, B[l], q, X[l], Tm[l], st);
+      for (int s = 1; s < pre; ++s) {
+        jacobi(A, d, B[l], X[l], q, Tm[l], st);
+        std::swap(X[l], Tm[l]);
+      }
+      if (pre > 1) residual(A, B[l], X[l], q, Tm[l], st);
+      spmm(h->R[l], Tm[l], q, B[l + 1], false, st);
+    } else {
+      cudaMemsetAsync(X[l], 0, sizeof(T) * h->sizes[l] * q, st);
+      spmm(h->R[l], B[l], q, B[l + 1], false, st);
+    }
+  }
+  coarse_solve(h, B[n - 1], q, X[n - 1], st);
+  for (int l = n - 2; l >= k; --l) {
+    const DevCsr& A = h->A[l];
+    const T* d = dinv_of(h, l, dummy);
+    spmm(h->P[l], X[l + 1], q, X[l], true, st);
+    for (int s = 0; s < post; ++s) {
+      if (to_v && l == k && s == post - 1) {
+        jacobi_to_v(A, d, B[l], X[l], q, U, V, st);
+      } else {
+        jacobi(A, d, B[l], X[l], q, Tm[l], st);
+        std::swap(X[l], Tm[l]);
+      }
+    }
+    if (to_v && l == k && post == 0) add_to_v(U, X[l], h->sizes[l] * q, V, st);
+  }
+}
+
+// m V-cycles in defect-correction form: x_{c+1} = x_c + V(b - A x_c), x_0 = 0;
+// the final V = U + x_m.  B[k] holds the defect on entry.
+template <typename T>
+void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, const double* U, double* V,
+                    cudaStream_t st) {
+  const int q = w->qt;
+  if (o.v_cycles <= 1) {
+    vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, true, U, V, st);
+    return;
+  }
+  auto& B = VBufs<T>::B(w);
+  auto& X = VBufs<T>::X(w);
+  auto& D = VBufs<T>::D(w);
+  auto& E = VBufs<T>::E(w);
+  const long long cnt = h->sizes[k] * q;
+  cudaMemcpyAsync(D[k], B[k], sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(E[k], 0, sizeof(T) * cnt, st);
+  for (int c = 0; c < o.v_cycles; ++c) {
+    vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
+    // E += X[k]
+    axpy(X[k], cnt, E[k], st);
+    if (c + 1 < o.v_cycles) residual(h->A[k], D[k], E[k], q, B[k], st);
+  }
+  add_to_v(U, E[k], cnt, V, st);
+}
+
+}  // namespace
+
+amgeig_hierarchy_t::~amgeig_hierarchy_t() {
+  ws.reset();
+  if (stream) cudaStreamDestroy(stream);
+}
+
+namespace {
+
+// ------------------------------------------------------------------ one correction (Algorithm 3.1)
+
+// Step 1 (inexact inverse iteration from u_j, in defect form) and step 2
+// (augmented pencil on V_n + span(V), its q smallest pairs, recombination).
+// On entry U (level k) and lam hold {lambda_j, u_j}; the defect of the current
+// pair is already in B[k] (float64 or float32 by precision).
+int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, cudaStream_t st) {
+  const int q = w->qt;
+  const int n = h->nlev;
+  const int Nk = static_cast<int>(h->sizes[k]);
+  if (o.precision == AMGEIG_FP64)
+    amg_correction<double>(h, w, k, o, w->U, w->V, st);
+  else
+    amg_correction<float>(h, w, k, o, w->U, w->V, st);
+  // augmentation: W = [A_k V | M_k V], G = V^T W, C = I_k^n W
+  launch_dual_spmm(h->A[k], w->V, q, w->W, st);
+  launch_gram(Nk, w->V, q, w->W, 2 * q, w->gsc, w->G, st);
+  const double* cur = w->W;
+  for (int l = k; l < n - 1; ++l) {
+    launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st);
+    cur = w->WC[l + 1];
+  }
+  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
+  launch_pencil_solve(w->pw, h->dn, q, cur, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
+  // recombination: U = I_n^k Xc + V Y
+  const double* px = w->Xc;
+  for (int l = n - 2; l >= k; --l) {
+    launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st);
+    px = w->PX[l];
+  }
+  launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st);
+  k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
+  CK(cudaGetLastError());
+  return AMGEIG_OK;
+}
+
+int defect(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, bool norms, cudaStream_t st) {
+  const int q = w->qt;
+  int nb = 0;
+  double* part = norms ? w->partials : nullptr;
+  if (o.precision == AMGEIG_FP64)
+    launch_defect_f64(h->A[k], w->U, q, w->lam, w->B64[k], part, &nb, st);
+  else
+    launch_defect_f32out(h->A[k], w->U, q, w->lam, w->B32[k], part, &nb, st);
+  if (norms) {
+    launch_sum_partials(w->partials, nb, 2 * q, w->sums, st);
+    CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
+    launch_relres(w->sums, w->lam, q, w->relres, w->flags, st);
+  }
+  CK(cudaGetLastError());
+  return AMGEIG_OK;
+}
+
+int check_options(const amgeig_options& o) {
+  if (o.max_corrections < 0 || o.v_cycles < 1 || o.pre_sweeps < 0 || o.post_sweeps < 0 || o.q_extra < 0 ||
+      o.fixed_corrections < 0 || o.reserved != 0 || (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32))
+    return fail(AMGEIG_EINVAL, "invalid options");
+  return AMGEIG_OK;
+}
+
+// Algorithm 3.2 on the hierarchy's stream; results stay in the workspace.
+int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o, amgeig_info* info,
+               std::vector<double>& relres_host, cudaStream_t st) {
+  const int qt = q + o.q_extra;
+  const int n = h->nlev;
+  if (q < 1 || qt > h->dn) return fail(AMGEIG_EINVAL, "q + q_extra must be in [1, coarsest dimension]");
+  if (qt > 128) return fail(AMGEIG_EINVAL, "q + q_extra must be at most 128");
+  int rc = check_options(o);
+  if (rc) return rc;
+  if (!h->ws || h->ws->qt != qt || h->ws->precision != o.precision || h->ws->vcycles < o.v_cycles) {
+    h->ws.reset();
+    rc = make_workspace(h, qt, o.precision, std::max(1, o.v_cycles), h->ws);
+    if (rc) return rc;
+  }
+  SolveWork* w = h->ws.get();
+  // step 1: initial eigenpairs on level n1 = n (the coarsest)
+  launch_copy_cols(h->Z, h->dn, h->dn, qt, w->U, st);
+  k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
+  CK(cudaGetLastError());
+  int corrections = 0;
+  bool converged = false;
+  relres_host.assign(qt, 0.0);
+  // step 2: k = n1-1 .. 1 (0-based n-2 .. 1) one correction each, then the finest level
+  for (int k = n - 2; k >= 0; --k) {
+    launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st);
+    std::swap(w->U, w->Ualt);
+    if (k >= 1) {
+      rc = defect(h, w, k, o, false, st);
+      if (rc) return rc;
+      rc = correction_tail(h, w, k, o, st);
+      if (rc) return rc;
+      int stt = 0;
+      CK(cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (stt) return fail(stt, "augmented pencil: Gram Schur complement not positive definite");
+      continue;
+    }
+    for (;;) {
+      rc = defect(h, w, 0, o, true, st);
+      if (rc) return rc;
+      int flags = 0;
+      CK(cudaMemcpyAsync(relres_host.data(), w->relres, sizeof(double) * qt, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&flags, w->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+      int stt = 0;
+      CK(cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (stt) return fail(stt, "augmented pencil: Gram Schur complement not positive definite");
+      if (flags) return fail(AMGEIG_ENAN, "NaN or Inf in the iterates");
+      double mx = 0.0;
+      for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
+      if (o.fixed_corrections > 0) {
+        if (corrections == o.fixed_corrections) {
+          converged = mx <= tol;
+          break;
+        }
+      } else {
+        if (mx <= tol) {
+          converged = true;
+          break;
+        }
+        if (corrections == o.max_corrections) break;
+      }
+      rc = correction_tail(h, w, 0, o, st);
+      if (rc) return rc;
+      ++corrections;
+    }
+  }
+  if (n == 1) {
+    // single level: the coarse eigenpairs are the answer; report their residual
+    rc = defect(h, w, 0, o, true, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(relres_host.data(), w->relres, sizeof(double) * qt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
+    converged = mx <= tol;
+  }
+  if (info) {
+    double mx = 0.0;
+    for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
+    info->corrections = corrections;
+    info->converged = converged ? 1 : 0;
+    info->n1 = n - 1;
+    info->max_relres = mx;
+    info->status = converged ? AMGEIG_OK : AMGEIG_ENOCONV;
+  }
+  return converged ? AMGEIG_OK : AMGEIG_ENOCONV;
+}
+
+// Copy the q wanted eigenvalues / sign-normalised eigenvectors out.
+int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs, int on_device, cudaStream_t st) {
+  SolveWork* w = h->ws.get();
+  const int qt = w->qt;
+  const int N0 = static_cast<int>(h->sizes[0]);
+  if (eigvals) CK(cudaMemcpyAsync(eigvals, w->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st));
+  if (eigvecs) {
+    k_col_sign<<<q, 256, 0, st>>>(w->U, N0, qt, q, w->sign);
+    double* dst = on_device ? eigvecs : w->V;  // V is free after the solve
+    const long long total = static_cast<long long>(N0) * q;
+    k_out_vectors<<<static_cast<int>(std::min<long long>((total + 255) / 256, 8LL * kNumSms)), 256, 0, st>>>(
+        w->U, N0, qt, q, w->sign, dst);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(eigvecs, dst, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return AMGEIG_OK;
+}
+
+// ------------------------------------------------------------------ request service
+
+struct Request {
+  uint64_t id;
+  amgeig_hierarchy_t* h;
+  int q;
+  double tol;
+  amgeig_options opt;
+  bool done = false;
+  int status = AMGEIG_OK;
+  std::vector<double> vals, vecs;
+  amgeig_info info{};
+};
+
+struct Service {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> table;
+  uint64_t next_id = 1;
+  std::thread worker;
+  bool running = false;
+
+  void start() {
+    if (running) return;
+    running = true;
+    worker = std::thread([this] { loop(); });
+    worker.detach();
+  }
+
+  void loop() {
+    for (;;) {
+      std::shared_ptr<Request> r;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [this] { return !queue.empty(); });
+        r = queue.front();
+        queue.pop_front();
+      }
+      run(r);
+      r->h->pending--;
+    }
+  }
+
+  void run(const std::shared_ptr<Request>& r);
+};
+
+Service& service() {
+  static Service* s = new Service();  // intentionally never destroyed (detached worker)
+  return *s;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+void amgeig_default_options(amgeig_options* opt) {
+  if (!opt) return;
+  opt->max_corrections = 20;
+  opt->v_cycles = 1;
+  opt->pre_sweeps = 1;
+  opt->post_sweeps = 1;
+  opt->q_extra = 0;
+  opt->precision = AMGEIG_FP64;
+  opt->fixed_corrections = 0;
+  opt->reserved = 0;
+}
+
+const char* amgeig_strerror(int code) {
+  switch (code) {
+    case AMGEIG_OK: return "ok";
+    case AMGEIG_EINVAL: return "invalid argument";
+    case AMGEIG_ECORRUPT: return "corrupt hierarchy blob";
+    case AMGEIG_ENOMEM: return "out of device memory";
+    case AMGEIG_ENOTSPD: return "matrix not positive definite";
+    case AMGEIG_ENOCONV: return "not converged within max_corrections";
+    case AMGEIG_ENAN: return "NaN or Inf in the iterates";
+    case AMGEIG_ECUDA: return "CUDA error";
+    case AMGEIG_ENOTFOUND: return "unknown request id";
+    default: return "unknown status";
+  }
+}
+
+const char* amgeig_last_error(void) { return g_last_error.c_str(); }
+
+int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hierarchy* out) {
+  g_last_error.clear();
+  if (!blob || !out) return fail(AMGEIG_EINVAL, "NULL argument");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(AMGEIG_EINVAL, "no such CUDA device");
+  std::vector<HostCsr> levels, prolong;
+  int rc = parse_blob(blob, bytes, levels, prolong);
+  if (rc) return rc;
+  CK(cudaSetDevice(device));
+  auto h = std::make_unique<amgeig_hierarchy_t>();
+  h->device = device;
+  h->nlev = static_cast<int>(levels.size());
+  const int n = h->nlev;
+  for (auto& L : levels) h->sizes.push_back(L.rows);
+  h->dn = static_cast<int>(h->sizes[n - 1]);
+  if (h->dn > 4096) return fail(AMGEIG_EINVAL, "coarsest level larger than 4096");
+  CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  auto& m = h->mem;
+  h->A.resize(n);
+  h->dinv64.assign(n, nullptr);
+  h->dinv32.assign(n, nullptr);
+  for (int l = 0; l < n; ++l) {
+    HostCsr& L = levels[l];
+    DevCsr& D = h->A[l];
+    D.rows = D.cols = static_cast<int>(L.rows);
+    D.nnz = static_cast<int>(L.ci.size());
+    std::vector<float> a32(L.a.begin(), L.a.end());
+    std::vector<double> d64(L.rows);
+    std::vector<float> d32(L.rows);
+    for (int64_t i = 0; i < L.rows; ++i) {
+      double s = 0.0;
+      for (int32_t p = L.rp[i]; p < L.rp[i + 1]; ++p) s += std::fabs(L.a[p]);
+      if (!(s > 0.0)) return fail(AMGEIG_ECORRUPT, "zero row in A");
+      d64[i] = 1.0 / s;
+      d32[i] = static_cast<float>(1.0 / s);
+    }
+    CK(m.upload(&D.rp, L.rp));
+    CK(m.upload(&D.ci, L.ci));
+    CK(m.upload(&D.v64, L.a));
+    CK(m.upload(&D.m64, L.m));
+    CK(m.upload(&D.v32, a32));
+    CK(m.upload(&h->dinv64[l], d64));
+    CK(m.upload(&h->dinv32[l], d32));
+  }
+  h->P.resize(n - 1);
+  h->R.resize(n - 1);
+  for (int l = 0; l + 1 < n; ++l) {
+    for (int which = 0; which < 2; ++which) {
+      HostCsr S = which == 0 ? prolong[l] : transpose(prolong[l]);
+      DevCsr& D = which == 0 ? h->P[l] : h->R[l];
+      D.rows = static_cast<int>(S.rows);
+      D.cols = static_cast<int>(S.cols);
+      D.nnz = static_cast<int>(S.ci.size());
+      std::vector<float> v32(S.a.begin(), S.a.end());
+      CK(m.upload(&D.rp, S.rp));
+      CK(m.upload(&D.ci, S.ci));
+      CK(m.upload(&D.v64, S.a));
+      CK(m.upload(&D.v32, v32));
+    }
+  }
+  // dense coarsest pencil and its eigendecomposition
+  const int dn = h->dn;
+  std::vector<double> An(static_cast<size_t>(dn) * dn, 0.0), Mn(static_cast<size_t>(dn) * dn, 0.0);
+  const HostCsr& Lc = levels[n - 1];
+  for (int i = 0; i < dn; ++i)
+    for (int32_t p = Lc.rp[i]; p < Lc.rp[i + 1]; ++p) {
+      An[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.a[p];
+      Mn[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.m[p];
+    }
+  CK(m.upload(&h->An, An));
+  CK(m.upload(&h->Mn, Mn));
+  CK(m.alloc(&h->Z, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->theta, dn));
+  CK(m.alloc(&h->Ainv, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->Ainv32, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->dstatus, 4));
+  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+  cudaError_t e;
+  PencilWork* pw = pencil_work_create(dn, 1, &e);
+  if (!pw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
+  launch_coarse_eigh(pw, dn, h->An, h->Mn, h->Z, h->theta, h->Ainv, h->dstatus, h->stream);
+  launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, h->stream);
+  int stt = 0;
+  cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  pencil_work_destroy(pw);
+  CK(e1);
+  CK(e2);
+  CK(cudaGetLastError());
+  if (stt) return fail(AMGEIG_ENOTSPD, "coarsest M_n or A_n is not positive definite");
+  *out = h.release();
+  return AMGEIG_OK;
+}
+
+int amgeig_free_hierarchy(amgeig_hierarchy h) {
+  if (!h) return AMGEIG_OK;
+  if (h->pending.load() != 0) return fail(AMGEIG_EINVAL, "hierarchy has pending requests");
+  cudaSetDevice(h->device);
+  delete h;
+  return AMGEIG_OK;
+}
+
+int amgeig_hierarchy_info(amgeig_hierarchy h, int* n_levels, int64_t* sizes, int max_sizes) {
+  if (!h || !n_levels) return fail(AMGEIG_EINVAL, "NULL argument");
+  *n_levels = h->nlev;
+  if (sizes)
+    for (int l = 0; l < std::min(h->nlev, max_sizes); ++l) sizes[l] = h->sizes[l];
+  return AMGEIG_OK;
+}
+
+int amgeig_solve(amgeig_hierarchy h, int q, double tol, const amgeig_options* opt, double* eigvals, double* eigvecs,
+                 int eigvecs_on_device, amgeig_info* info, void* stream) {
+  g_last_error.clear();
+  if (!h) return fail(AMGEIG_EINVAL, "NULL hierarchy");
+  amgeig_options o;
+  amgeig_default_options(&o);
+  if (opt) o = *opt;
+  std::lock_guard<std::mutex> lk(h->mu);
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+  std::vector<double> rr;
+  if (info) std::memset(info, 0, sizeof(*info));
+  const int rc = solve_impl(h, q, tol, o, info, rr, st);
+  if (rc != AMGEIG_OK && rc != AMGEIG_ENOCONV) {
+    if (info) info->status = rc;
+    return rc;
+  }
+  const int rc2 = write_outputs(h, q, eigvals, eigvecs, eigvecs_on_device, st);
+  if (rc2) return rc2;
+  return rc;
+}
+
+int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals, double* evecs) {
+  g_last_error.clear();
+  if (!H || !evals || !evecs || n < 1 || n > 2048 || nwant < 1 || nwant > n)
+    return fail(AMGEIG_EINVAL, "invalid argument");
+  CK(cudaSetDevice(device));
+  cudaError_t e;
+  PencilWork* pw = pencil_work_create(n, 1, &e);
+  if (!pw) return fail(AMGEIG_ENOMEM, std::string("eigensolver workspace: ") + cudaGetErrorString(e));
+  DeviceBuffers m;
+  double *dH, *dv, *dV;
+  cudaStream_t st;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaError_t e0 = m.alloc(&dH, static_cast<size_t>(n) * n);
+  if (e0 == cudaSuccess) e0 = m.alloc(&dv, nwant);
+  if (e0 == cudaSuccess) e0 = m.alloc(&dV, static_cast<size_t>(n) * nwant);
+  if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(dH, H, sizeof(double) * n * n, cudaMemcpyHostToDevice, st);
+  if (e0 == cudaSuccess) {
+    launch_syev_df(pw, n, nwant, dH, dv, dV, st);
+    e0 = cudaGetLastError();
+  }
+  if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(evals, dv, sizeof(double) * nwant, cudaMemcpyDeviceToHost, st);
+  if (e0 == cudaSuccess)
+    e0 = cudaMemcpyAsync(evecs, dV, sizeof(double) * n * nwant, cudaMemcpyDeviceToHost, st);
+  cudaError_t e1 = cudaStreamSynchronize(st);
+  pencil_work_destroy(pw);
+  cudaStreamDestroy(st);
+  CK(e0);
+  CK(e1);
+  return AMGEIG_OK;
+}
+
+int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* b,
+                        double* x) {
+  g_last_error.clear();
+  if (!h || !b || !x || level < 0 || level >= h->nlev || width < 1 || width > 128)
+    return fail(AMGEIG_EINVAL, "invalid argument");
+  amgeig_options o;
+  amgeig_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->stream;
+  if (!h->ws || h->ws->qt != width || h->ws->precision != o.precision) {
+    h->ws.reset();
+    rc = make_workspace(h, width, o.precision, 1, h->ws);
+    if (rc) return rc;
+  }
+  SolveWork* w = h->ws.get();
+  const long long cnt = h->sizes[level] * static_cast<long long>(width);
+  if (level == h->nlev - 1) {
+    // the coarsest level: the exact solve
+    CK(cudaMemcpyAsync(w->V, b, sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+    launch_gemm_f64(h->dn, width, h->dn, 1.0, h->Ainv, h->dn, false, w->V, width, false, 0.0, w->U, width, st);
+    CK(cudaMemcpyAsync(x, w->U, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return AMGEIG_OK;
+  }
+  CK(cudaMemcpyAsync(w->V, b, sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+  if (o.precision == AMGEIG_FP64) {
+    CK(cudaMemcpyAsync(w->B64[level], w->V, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+    vcycle<double>(h, w, level, o.pre_sweeps, o.post_sweeps, false, nullptr, nullptr, st);
+    CK(cudaMemcpyAsync(w->U, w->X64[level], sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+  } else {
+    launch_convert_f64_to_f32(w->V, cnt, w->B32[level], st);
+    vcycle<float>(h, w, level, o.pre_sweeps, o.post_sweeps, false, nullptr, nullptr, st);
+    launch_convert_f32_to_f64(w->X32[level], cnt, w->U, st);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(x, w->U, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return AMGEIG_OK;
+}
+
+int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* opt, uint64_t* request_id) {
+  if (!h || !request_id) return fail(AMGEIG_EINVAL, "NULL argument");
+  amgeig_options o;
+  amgeig_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  if (q < 1 || q + o.q_extra > h->dn || q + o.q_extra > 128) return fail(AMGEIG_EINVAL, "q out of range");
+  auto r = std::make_shared<Request>();
+  r->h = h;
+  r->q = q;
+  r->tol = tol;
+  r->opt = o;
+  Service& s = service();
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    r->id = s.next_id++;
+    s.table[r->id] = r;
+    s.queue.push_back(r);
+    h->pending++;
+    s.start();
+  }
+  s.cv.notify_one();
+  *request_id = r->id;
+  return AMGEIG_OK;
+}
+
+int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs, amgeig_info* info) {
+  if (!done) return fail(AMGEIG_EINVAL, "NULL argument");
+  Service& s = service();
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.table.find(request_id);
+    if (it == s.table.end()) return fail(AMGEIG_ENOTFOUND, "unknown request id");
+    r = it->second;
+    if (!r->done) {
+      *done = 0;
+      return AMGEIG_OK;
+    }
+    s.table.erase(it);
+  }
+  *done = 1;
+  if (eigvals && !r->vals.empty()) std::memcpy(eigvals, r->vals.data(), sizeof(double) * r->vals.size());
+  if (eigvecs && !r->vecs.empty()) std::memcpy(eigvecs, r->vecs.data(), sizeof(double) * r->vecs.size());
+  if (info) *info = r->info;
+  return r->status;
+}
+
+}  // extern "C"
+
+namespace {
+
+void Service::run(const std::shared_ptr<Request>& r) {
+  amgeig_hierarchy_t* h = r->h;
+  const int qt = r->q + r->opt.q_extra;
+  // admission by free device memory: the request's workspace must fit
+  size_t need = 0;
+  {
+    size_t per = 0;
+    for (int l = 0; l < h->nlev; ++l) per += static_cast<size_t>(h->sizes[l]) * qt * 8 * 6;
+    need = per + static_cast<size_t>(h->sizes[0]) * qt * 8 * 5;
+  }
+  int status = AMGEIG_OK;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaSetDevice(h->device);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const bool have_ws = h->ws && h->ws->qt == qt && h->ws->precision == r->opt.precision;
+    if (!have_ws && need > fr && need > tot) status = AMGEIG_ENOMEM;
+  }
+  if (status == AMGEIG_OK) {
+    r->vals.assign(r->q, 0.0);
+    r->vecs.assign(static_cast<size_t>(h->sizes[0]) * r->q, 0.0);
+    status = amgeig_solve(h, r->q, r->tol, &r->opt, r->vals.data(), r->vecs.data(), 0, &r->info, nullptr);
+    if (status != AMGEIG_OK && status != AMGEIG_ENOCONV) {
+      r->vals.clear();
+      r->vecs.clear();
+    }
+  }
+  r->info.status = status;
+  std::lock_guard<std::mutex> lk(mu);
+  r->status = status;
+  r->done = true;
+}
+
+}  // namespace

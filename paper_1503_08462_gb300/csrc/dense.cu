@@ -1,0 +1,177 @@
+// Small dense kernels: GEMM on coarse-size operands, the tall-skinny Gram
+// products V^T W of Algorithm 3.1 step 2 (V^T A_k V and V^T M_k V), fixed-order
+// reductions of per-block partial sums, and the residual test.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace amgeig {
+namespace {
+
+constexpr int kTile = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, int lda, int ta,
+                                              const T* __restrict__ B, int ldb, int tb, T beta, T* __restrict__ C,
+                                              int ldc) {
+  __shared__ T As[kTile][kTile + 1];
+  __shared__ T Bs[kTile][kTile + 1];
+  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+  const int row = blockIdx.y * kTile + ty, col = blockIdx.x * kTile + tx;
+  T acc = T(0);
+  for (int k0 = 0; k0 < K; k0 += kTile) {
+    {
+      const int r = blockIdx.y * kTile + ty, k = k0 + tx;
+      As[ty][tx] = (r < M && k < K) ? (ta ? A[static_cast<long long>(k) * lda + r] : A[static_cast<long long>(r) * lda + k])
+                                    : T(0);
+    }
+    {
+      const int k = k0 + ty, c = blockIdx.x * kTile + tx;
+      Bs[ty][tx] = (k < K && c < N) ? (tb ? B[static_cast<long long>(c) * ldb + k] : B[static_cast<long long>(k) * ldb + c])
+                                    : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTile; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  if (row < M && col < N) {
+    T* c = C + static_cast<long long>(row) * ldc + col;
+    *c = (beta == T(0)) ? alpha * acc : fma(alpha, acc, beta * *c);
+  }
+}
+
+// Gram partials: block (chunk, tile) accumulates out[a][b] = sum_{r in chunk} V[r][a] W[r][b]
+// for a 32 x 32 tile of (a, b); each thread owns 4 outputs.
+constexpr int kGT = 32;
+constexpr int kGramRows = 32;
+
+__global__ void __launch_bounds__(256) k_gram_partial(int rows, const double* __restrict__ V, int ldv, int q,
+                                                      const double* __restrict__ W, int ldw, int w, int chunk_rows,
+                                                      int tiles_w, double* __restrict__ part) {
+  __shared__ double Vs[kGramRows][kGT + 1];
+  __shared__ double Ws[kGramRows][kGT + 1];
+  const int chunk = blockIdx.x;
+  const int ta = blockIdx.y / tiles_w, tb = blockIdx.y % tiles_w;
+  const int a0 = ta * kGT, b0 = tb * kGT;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // ty in 0..7
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int r0 = chunk * chunk_rows;
+  const int r1 = min(rows, r0 + chunk_rows);
+  for (int rb = r0; rb < r1; rb += kGramRows) {
+    for (int idx = threadIdx.x; idx < kGramRows * kGT; idx += blockDim.x) {
+      const int rr = idx / kGT, cc = idx % kGT;
+      const int r = rb + rr;
+      Vs[rr][cc] = (r < r1 && a0 + cc < q) ? V[static_cast<long long>(r) * ldv + a0 + cc] : 0.0;
+      Ws[rr][cc] = (r < r1 && b0 + cc < w) ? W[static_cast<long long>(r) * ldw + b0 + cc] : 0.0;
+    }
+    __syncthreads();
+    const int nr = min(kGramRows, r1 - rb);
+    for (int rr = 0; rr < nr; ++rr) {
+      const double wv = Ws[rr][tx];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) acc[s] = fma(Vs[rr][ty * 4 + s], wv, acc[s]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int a = a0 + ty * 4 + s, b = b0 + tx;
+    if (a < q && b < w) part[(static_cast<long long>(chunk) * q + a) * w + b] = acc[s];
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int nparts, int len, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[static_cast<long long>(b) * len + j];
+    out[j] = s;
+  }
+}
+
+__global__ void k_relres(const double* __restrict__ sums, const double* __restrict__ lam, int q,
+                         double* __restrict__ relres, int* __restrict__ flags) {
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    const double r = sqrt(sums[j]) / (fabs(lam[j]) * sqrt(sums[q + j]));
+    relres[j] = r;
+    if (!isfinite(r) || !isfinite(lam[j])) atomicOr(flags, 1);
+  }
+}
+
+__global__ void k_copy_cols(const double* __restrict__ src, int rows, int ld, int q, double* __restrict__ dst) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / q, c = i % q;
+    dst[i] = src[r * ld + c];
+  }
+}
+
+int gram_chunks(int rows, int q, int w, int* chunk_rows) {
+  const int tiles = ceil_div(q, kGT) * ceil_div(w, kGT);
+  int chunks = ceil_div(rows, 256);
+  const int cap = (4 * kNumSms + tiles - 1) / tiles;
+  if (chunks > cap) chunks = cap;
+  if (chunks < 1) chunks = 1;
+  int cr = ceil_div(rows, chunks);
+  cr = ceil_div(cr, kGramRows) * kGramRows;
+  if (cr < kGramRows) cr = kGramRows;
+  *chunk_rows = cr;
+  return ceil_div(rows, cr) > 0 ? ceil_div(rows, cr) : 1;
+}
+
+}  // namespace
+
+void launch_gemm_f64(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
+                     bool tb, double beta, double* C, int ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid(ceil_div(N, kTile), ceil_div(M, kTile));
+  k_gemm<double><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
+}
+
+void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, bool ta, const float* B, int ldb,
+                     bool tb, float beta, float* C, int ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid(ceil_div(N, kTile), ceil_div(M, kTile));
+  k_gemm<float><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
+}
+
+size_t gram_scratch_doubles(int rows, int q, int w) {
+  int cr;
+  const int chunks = gram_chunks(rows, q, w, &cr);
+  return static_cast<size_t>(chunks) * q * w;
+}
+
+void launch_gram_strided(int rows, const double* V, int ldv, int q, const double* W, int ldw, int w, double* scratch,
+                         double* G, cudaStream_t st) {
+  if (q <= 0 || w <= 0) return;
+  int cr;
+  const int chunks = gram_chunks(rows, q, w, &cr);
+  const int tiles_w = ceil_div(w, kGT);
+  dim3 grid(chunks, ceil_div(q, kGT) * tiles_w);
+  k_gram_partial<<<grid, 256, 0, st>>>(rows, V, ldv, q, W, ldw, w, cr, tiles_w, scratch);
+  launch_sum_partials(scratch, chunks, q * w, G, st);
+}
+
+void launch_gram(int rows, const double* V, int q, const double* W, int w, double* scratch, double* G,
+                 cudaStream_t st) {
+  launch_gram_strided(rows, V, q, q, W, w, w, scratch, G, st);
+}
+
+void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st) {
+  if (len <= 0) return;
+  k_sum_partials<<<ceil_div(len, 256), 256, 0, st>>>(part, nparts, len, out);
+}
+
+void launch_relres(const double* sums, const double* lam, int q, double* relres, int* flags, cudaStream_t st) {
+  k_relres<<<1, 256, 0, st>>>(sums, lam, q, relres, flags);
+}
+
+void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, cudaStream_t st) {
+  const long long total = static_cast<long long>(rows) * q;
+  if (total <= 0) return;
+  long long b = (total + 255) / 256;
+  if (b > 8 * kNumSms) b = 8 * kNumSms;
+  k_copy_cols<<<static_cast<int>(b), 256, 0, st>>>(src, rows, ld, q, dst);
+}
+
+}  // namespace amgeig

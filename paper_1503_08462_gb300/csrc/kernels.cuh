@@ -1,0 +1,132 @@
+// Host-side launchers of the solve-path kernels (one declaration per kernel
+// family; each launcher enqueues on `st` and returns without synchronising).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace amgeig {
+
+// CSR matrix on the device.  vals64 / vals32 point to the same entries in
+// float64 and float32 (either may be null when a path does not use it).
+struct DevCsr {
+  int rows = 0, cols = 0, nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  double* m64 = nullptr;  // second value array sharing the pattern (mass matrix)
+};
+
+// ---- sparse kernels (spmm.cu) --------------------------------------------
+// All blocks of vectors are row-major [rows][width].
+
+// R = lambda o (M U) - A U   (Eq. Linear_Equation moved to the defect form),
+// R written as TO; when `partials` is non-null each block also writes the
+// per-column sums of R_ij^2 and (MU)_ij^2 to partials[block][2q] (fixed order).
+void launch_defect_f64(const DevCsr& AM, const double* U, int q, const double* lam, double* R,
+                       double* partials, int* nblocks_out, cudaStream_t st);
+void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double* lam, float* R,
+                          double* partials, int* nblocks_out, cudaStream_t st);
+
+// Y = S X (accumulate = false) or Y += S X (accumulate = true)
+void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st);
+void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st);
+
+// first l1-Jacobi sweep from x = 0 fused with the residual:
+//   x = D^-1 b,  r = b - A x
+void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const double* b, int width, double* x,
+                                   double* r, cudaStream_t st);
+void launch_presmooth_residual_f32(const DevCsr& A, const float* dinv, const float* b, int width, float* x,
+                                   float* r, cudaStream_t st);
+// one l1-Jacobi sweep x_out = x + D^-1 (b - A x) (x_out != x)
+void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
+                       double* x_out, cudaStream_t st);
+void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
+                       float* x_out, cudaStream_t st);
+// residual r = b - A x
+void launch_residual_f64(const DevCsr& A, const double* b, const double* x, int width, double* r, cudaStream_t st);
+void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st);
+// last sweep on the working level fused with V = U + x_new (float64 output)
+void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
+                            const double* U, double* V, cudaStream_t st);
+void launch_jacobi_to_v_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
+                            const double* U, double* V, cudaStream_t st);
+// V = U + x (used when there are no post-smoothing sweeps)
+void launch_add_to_v_f64(const double* U, const double* x, long long count, double* V, cudaStream_t st);
+void launch_add_to_v_f32(const double* U, const float* x, long long count, double* V, cudaStream_t st);
+
+// W = [A V | M V]  ([rows][2q])
+void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaStream_t st);
+
+// U = Xp + V Y   (Y: q x q row-major)
+void launch_recombine(int rows, const double* Xp, const double* V, const double* Y, int q, double* U,
+                      cudaStream_t st);
+
+// y += x
+void launch_axpy_f64(const double* x, long long count, double* y, cudaStream_t st);
+void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st);
+
+// float64 -> float32 / float32 -> float64 copies
+void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st);
+void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st);
+
+// ---- dense kernels (dense.cu) ---------------------------------------------
+
+// C = alpha op(A) op(B) + beta C, all row-major; op = transpose when t* != 0.
+// A is M x K (or K x M when ta), B is K x N (or N x K when tb).
+void launch_gemm_f64(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
+                     int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st);
+void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, bool ta, const float* B, int ldb,
+                     bool tb, float beta, float* C, int ldc, cudaStream_t st);
+
+// Gram G = V^T W  (V: rows x q, W: rows x w) -> G: q x w, via per-chunk partials
+// in `scratch` (size gram_scratch_doubles(rows, q, w)) and a fixed-order sum.
+size_t gram_scratch_doubles(int rows, int q, int w);
+void launch_gram(int rows, const double* V, int q, const double* W, int w, double* scratch, double* G,
+                 cudaStream_t st);
+// same with explicit row strides ldv >= q and ldw >= w
+void launch_gram_strided(int rows, const double* V, int ldv, int q, const double* W, int ldw, int w, double* scratch,
+                         double* G, cudaStream_t st);
+
+// Sum `nparts` partial rows of length `len` in fixed order: out[j] = sum_b part[b*len + j]
+void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st);
+
+// relres_j = sqrt(rr_j) / (|lambda_j| sqrt(mm_j)) from the summed defect norms;
+// writes relres[q] and flags[0] = 1 if any value is NaN/Inf.
+void launch_relres(const double* sums, const double* lam, int q, double* relres, int* flags, cudaStream_t st);
+
+// Copy the first q columns of a row-major (rows x ld) matrix into a rows x q block
+void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, cudaStream_t st);
+
+// ---- small dense eigen-machinery (pencil.cu) ------------------------------
+
+struct PencilWork;  // opaque device workspace, sized by pencil_work_create
+
+// Workspace for pencils of coarse size dn with up to qmax border vectors.
+PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err);
+void pencil_work_destroy(PencilWork* w);
+
+// One Rayleigh-Ritz step on V_n + span(V) (Algorithm 3.1 step 2) in the
+// coarse eigenbasis: inputs C = [I_k^n A V | I_k^n M V] (dn x 2q),
+// G = [V^T A V | V^T M V] (q x 2q), the coarse eigenbasis Z (dn x dn, M_n-
+// orthonormal) and Theta (dn).  Outputs the q smallest Ritz values mu (q), the
+// coarse coefficients Xc (dn x q) and the V-coefficients Y (q x q) so that the
+// new vectors are I_n^k Xc + V Y.  status[0] receives AMGEIG_ENOTSPD when the
+// Gram Schur complement is not positive definite.
+void launch_pencil_solve(PencilWork* w, int dn, int q, const double* C, const double* G, const double* Z,
+                         const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st);
+
+// Full eigendecomposition of the coarsest pencil (A_n, M_n), both dn x dn
+// dense row-major: Z (dn x dn) with Z^T M_n Z = I, Z^T A_n Z = diag(theta),
+// theta ascending; also Ainv = A_n^-1 = Z diag(1/theta) Z^T.  status as above.
+void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,
+                        double* Ainv, int* status, cudaStream_t st);
+
+// Symmetric eigensolver in float-float: the `nwant` smallest eigenpairs of the
+// symmetric n x n row-major float64 matrix H.  evals (nwant), evecs (n x nwant
+// row-major).  Exposed for the kernel-level tests.
+void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
+                    cudaStream_t st);
+
+}  // namespace amgeig

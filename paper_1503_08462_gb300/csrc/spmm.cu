@@ -1,0 +1,483 @@
+// Sparse kernels of the solve path: CSR times row-major blocks of vectors.
+//
+// Layout: every block of vectors is row-major [rows][width], so the `width`
+// values of one row are contiguous and a gathered neighbour row is one
+// coalesced segment.  A group of G threads (G = width rounded up to a power of
+// two, at most 32) owns one matrix row; thread t of the group accumulates the
+// columns t, t+G, ... (CPT columns per thread).  Column indices and values of
+// the row are loaded once per group (same address across the group).
+//
+// Steps served (Algorithm 3.1, 0-based levels):
+//   defect       r_j = lambda_j M_k u_j - A_k u_j (Eq. Linear_Equation; the
+//                AMG call from the initial guess u_j is run in defect form)
+//   smoothing    point l1-Jacobi x <- x + D^-1 (b - A x), D = diag(sum_j |a_ij|)
+//   transfers    restriction R_l = P_l^T and prolongation P_l (Sec. 2.3)
+//   augmentation A_k V and M_k V for the pencil of Algorithm 3.1 step 2
+//   recombine    u_j = I_n^k x_j(1:d_n) + V x_j(d_n+1:d_n+q)
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace amgeig {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Geo {
+  int G, rows_per_block, cpt;
+};
+
+Geo geo_for(int width) {
+  int G = 1;
+  while (G < width && G < 32) G <<= 1;
+  int cpt = (width + G - 1) / G;
+  int c = 1;
+  while (c < cpt) c <<= 1;
+  return Geo{G, kThreads / G, c};
+}
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  using type = double;
+};
+template <>
+struct Acc<float> {
+  using type = float;
+};
+
+// ------------------------------------------------------------------ defect
+
+template <int CPT, typename TO>
+__global__ void __launch_bounds__(kThreads) k_defect(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                     const double* __restrict__ a, const double* __restrict__ m,
+                                                     const double* __restrict__ U, int q,
+                                                     const double* __restrict__ lam, TO* __restrict__ R, int G,
+                                                     double* __restrict__ partials) {
+  extern __shared__ double sred[];  // [rows_per_block][2*G*CPT] when partials != null
+  const int rpb = blockDim.x / G;
+  const int g = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + g;
+  double aa[CPT], mm[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = 0.0;
+  if (row < n) {
+    const int p0 = rp[row], p1 = rp[row + 1];
+    for (int p = p0; p < p1; ++p) {
+      const int j = ci[p];
+      const double av = a[p], mv = m[p];
+      const double* uj = U + static_cast<long long>(j) * q;
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        const int c = lane + t * G;
+        if (c < q) {
+          const double u = uj[c];
+          aa[t] = fma(av, u, aa[t]);
+          mm[t] = fma(mv, u, mm[t]);
+        }
+      }
+    }
+  }
+  double rr[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    rr[t] = 0.0;
+    if (row < n && c < q) {
+      const double r = fma(lam[c], mm[t], -aa[t]);
+      R[static_cast<long long>(row) * q + c] = static_cast<TO>(r);
+      rr[t] = r;
+    }
+  }
+  if (partials == nullptr) return;
+  // per-column sums of r^2 and (Mu)^2 over the block's rows, fixed order
+  const int W = G * CPT;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    sred[g * 2 * W + lane + t * G] = rr[t] * rr[t];
+    sred[g * 2 * W + W + lane + t * G] = (row < n) ? mm[t] * mm[t] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * q; idx += blockDim.x) {
+    const int which = idx / q, c = idx % q;
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += sred[r * 2 * W + which * W + c];
+    partials[static_cast<long long>(blockIdx.x) * 2 * q + idx] = s;
+  }
+}
+
+template <typename TO>
+void defect_impl(const DevCsr& AM, const double* U, int q, const double* lam, TO* R, double* partials,
+                 int* nblocks_out, cudaStream_t st) {
+  Geo g = geo_for(q);
+  const int blocks = ceil_div(AM.rows, g.rows_per_block);
+  if (nblocks_out) *nblocks_out = blocks;
+  const size_t sm = partials ? sizeof(double) * g.rows_per_block * 2 * g.G * g.cpt : 0;
+  switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                                        \
+  case C:                                                                                                     \
+    k_defect<C, TO><<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, U, q, lam, R, g.G, \
+                                                  partials);                                                \
+    break;
+    AMGEIG_CASE(1)
+    AMGEIG_CASE(2)
+    AMGEIG_CASE(4)
+    AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------------ generic SpMM
+
+template <typename T, int CPT>
+__global__ void __launch_bounds__(kThreads) k_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const T* __restrict__ v, const T* __restrict__ X, int width,
+                                                   T* __restrict__ Y, int G, int accumulate) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  T acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) acc[t] = T(0);
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = ci[p];
+    const T s = v[p];
+    const T* xj = X + static_cast<long long>(j) * width;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < width) acc[t] = fma(s, xj[c], acc[t]);
+    }
+  }
+  T* yr = Y + static_cast<long long>(row) * width;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < width) yr[c] = accumulate ? yr[c] + acc[t] : acc[t];
+  }
+}
+
+template <typename T>
+void spmm_impl(const DevCsr& S, const T* vals, const T* X, int width, T* Y, bool accumulate, cudaStream_t st) {
+  if (S.rows == 0 || width == 0) return;
+  Geo g = geo_for(width);
+  const int blocks = ceil_div(S.rows, g.rows_per_block);
+  switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                                     \
+  case C:                                                                                                  \
+    k_spmm<T, C><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, vals, X, width, Y, g.G, accumulate ? 1 : 0); \
+    break;
+    AMGEIG_CASE(1)
+    AMGEIG_CASE(2)
+    AMGEIG_CASE(4)
+    AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------------ smoothing
+
+// mode 0: x = D^-1 b, r = b - A x          (presmooth from zero + residual)
+// mode 1: out = x + D^-1 (b - A x)         (one sweep)
+// mode 2: r = b - A x                      (residual)
+// mode 3: V = U + x + D^-1 (b - A x)       (last sweep on the working level)
+template <typename T, int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads) k_smooth(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                     const T* __restrict__ a, const T* __restrict__ dinv,
+                                                     const T* __restrict__ b, const T* __restrict__ x, int width,
+                                                     T* __restrict__ out1, T* __restrict__ out2,
+                                                     const double* __restrict__ U, double* __restrict__ V, int G) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  T acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) acc[t] = T(0);
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = ci[p];
+    T s = a[p];
+    if (MODE == 0) s *= dinv[j];
+    const T* xj = (MODE == 0 ? b : x) + static_cast<long long>(j) * width;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < width) acc[t] = fma(s, xj[c], acc[t]);
+    }
+  }
+  const long long base = static_cast<long long>(row) * width;
+  const T di = dinv ? dinv[row] : T(0);
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < width) {
+      const T bi = b[base + c];
+      const T res = bi - acc[t];
+      if (MODE == 0) {
+        out1[base + c] = di * bi;
+        out2[base + c] = res;
+      } else if (MODE == 1) {
+        out1[base + c] = fma(di, res, x[base + c]);
+      } else if (MODE == 2) {
+        out1[base + c] = res;
+      } else {
+        const T xn = fma(di, res, x[base + c]);
+        V[base + c] = U[base + c] + static_cast<double>(xn);
+      }
+    }
+  }
+}
+
+template <typename T, int MODE>
+void smooth_impl(const DevCsr& A, const T* vals, const T* dinv, const T* b, const T* x, int width, T* out1,
+                 T* out2, const double* U, double* V, cudaStream_t st) {
+  if (A.rows == 0 || width == 0) return;
+  Geo g = geo_for(width);
+  const int blocks = ceil_div(A.rows, g.rows_per_block);
+  switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                                         \
+  case C:                                                                                                      \
+    k_smooth<T, C, MODE><<<blocks, kThreads, 0, st>>>(A.rows, A.rp, A.ci, vals, dinv, b, x, width, out1, out2, \
+                                                      U, V, g.G);                                              \
+    break;
+    AMGEIG_CASE(1)
+    AMGEIG_CASE(2)
+    AMGEIG_CASE(4)
+    AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------------ augmentation
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_dual_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                        const double* __restrict__ a, const double* __restrict__ m,
+                                                        const double* __restrict__ V, int q, double* __restrict__ W,
+                                                        int G) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  double aa[CPT], mm[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = 0.0;
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = ci[p];
+    const double av = a[p], mv = m[p];
+    const double* vj = V + static_cast<long long>(j) * q;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < q) {
+        const double u = vj[c];
+        aa[t] = fma(av, u, aa[t]);
+        mm[t] = fma(mv, u, mm[t]);
+      }
+    }
+  }
+  double* wr = W + static_cast<long long>(row) * 2 * q;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < q) {
+      wr[c] = aa[t];
+      wr[q + c] = mm[t];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ recombination
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_recombine(int n, const double* __restrict__ Xp,
+                                                        const double* __restrict__ V, const double* __restrict__ Y,
+                                                        int q, double* __restrict__ U, int G) {
+  extern __shared__ double ys[];  // q x q
+  for (int i = threadIdx.x; i < q * q; i += blockDim.x) ys[i] = Y[i];
+  __syncthreads();
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  const long long base = static_cast<long long>(row) * q;
+  double acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    acc[t] = (c < q) ? Xp[base + c] : 0.0;
+  }
+  for (int d = 0; d < q; ++d) {
+    const double v = V[base + d];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < q) acc[t] = fma(v, ys[d * q + c], acc[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < q) U[base + c] = acc[t];
+  }
+}
+
+// ------------------------------------------------------------------ elementwise
+
+template <typename T>
+__global__ void k_add_to_v(const double* __restrict__ U, const T* __restrict__ x, long long count,
+                           double* __restrict__ V) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    V[i] = U[i] + static_cast<double>(x[i]);
+}
+
+template <typename T>
+__global__ void k_axpy(const T* __restrict__ x, long long count, T* __restrict__ y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] += x[i];
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ x, long long count, float* __restrict__ y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] = static_cast<float>(x[i]);
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ x, long long count, double* __restrict__ y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] = static_cast<double>(x[i]);
+}
+
+int grid_for(long long count) {
+  long long b = (count + kThreads - 1) / kThreads;
+  if (b > 8LL * kNumSms) b = 8LL * kNumSms;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+void launch_defect_f64(const DevCsr& AM, const double* U, int q, const double* lam, double* R, double* partials,
+                       int* nblocks_out, cudaStream_t st) {
+  defect_impl<double>(AM, U, q, lam, R, partials, nblocks_out, st);
+}
+void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double* lam, float* R, double* partials,
+                          int* nblocks_out, cudaStream_t st) {
+  defect_impl<float>(AM, U, q, lam, R, partials, nblocks_out, st);
+}
+
+void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st) {
+  spmm_impl<double>(S, S.v64, X, width, Y, accumulate, st);
+}
+void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st) {
+  spmm_impl<float>(S, S.v32, X, width, Y, accumulate, st);
+}
+
+void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const double* b, int width, double* x,
+                                   double* r, cudaStream_t st) {
+  smooth_impl<double, 0>(A, A.v64, dinv, b, nullptr, width, x, r, nullptr, nullptr, st);
+}
+void launch_presmooth_residual_f32(const DevCsr& A, const float* dinv, const float* b, int width, float* x,
+                                   float* r, cudaStream_t st) {
+  smooth_impl<float, 0>(A, A.v32, dinv, b, nullptr, width, x, r, nullptr, nullptr, st);
+}
+void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
+                       double* x_out, cudaStream_t st) {
+  smooth_impl<double, 1>(A, A.v64, dinv, b, x, width, x_out, nullptr, nullptr, nullptr, st);
+}
+void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
+                       float* x_out, cudaStream_t st) {
+  smooth_impl<float, 1>(A, A.v32, dinv, b, x, width, x_out, nullptr, nullptr, nullptr, st);
+}
+void launch_residual_f64(const DevCsr& A, const double* b, const double* x, int width, double* r, cudaStream_t st) {
+  smooth_impl<double, 2>(A, A.v64, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
+}
+void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st) {
+  smooth_impl<float, 2>(A, A.v32, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
+}
+void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
+                            const double* U, double* V, cudaStream_t st) {
+  smooth_impl<double, 3>(A, A.v64, dinv, b, x, width, nullptr, nullptr, U, V, st);
+}
+void launch_jacobi_to_v_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
+                            const double* U, double* V, cudaStream_t st) {
+  smooth_impl<float, 3>(A, A.v32, dinv, b, x, width, nullptr, nullptr, U, V, st);
+}
+void launch_add_to_v_f64(const double* U, const double* x, long long count, double* V, cudaStream_t st) {
+  k_add_to_v<double><<<grid_for(count), kThreads, 0, st>>>(U, x, count, V);
+}
+void launch_add_to_v_f32(const double* U, const float* x, long long count, double* V, cudaStream_t st) {
+  k_add_to_v<float><<<grid_for(count), kThreads, 0, st>>>(U, x, count, V);
+}
+
+void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaStream_t st) {
+  Geo g = geo_for(q);
+  const int blocks = ceil_div(AM.rows, g.rows_per_block);
+  switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                                         \
+  case C:                                                                                                      \
+    k_dual_spmm<C><<<blocks, kThreads, 0, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, V, q, W, g.G); \
+    break;
+    AMGEIG_CASE(1)
+    AMGEIG_CASE(2)
+    AMGEIG_CASE(4)
+    AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+    default:
+      break;
+  }
+}
+
+void launch_recombine(int rows, const double* Xp, const double* V, const double* Y, int q, double* U,
+                      cudaStream_t st) {
+  Geo g = geo_for(q);
+  const int blocks = ceil_div(rows, g.rows_per_block);
+  const size_t sm = sizeof(double) * q * q;
+  switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                         \
+  case C:                                                                                      \
+    if (sm > 48 * 1024)                                                                        \
+      cudaFuncSetAttribute(k_recombine<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    k_recombine<C><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U, g.G);                     \
+    break;
+    AMGEIG_CASE(1)
+    AMGEIG_CASE(2)
+    AMGEIG_CASE(4)
+    AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+    default:
+      break;
+  }
+}
+
+void launch_axpy_f64(const double* x, long long count, double* y, cudaStream_t st) {
+  k_axpy<double><<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st) {
+  k_axpy<float><<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st) {
+  k_f64_to_f32<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st) {
+  k_f32_to_f64<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+}  // namespace amgeig

@@ -1,0 +1,48 @@
+"""The C-ABI library builds, loads and exports every symbol its header declares (CPU only)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_symbols():
+    names = set()
+    for hdr in (ROOT / "include").glob("*.h"):
+        text = hdr.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(?:int|void|const char\*)\s+(amgeig_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_solve", "amgeig_submit",
+                     "amgeig_poll", "amgeig_strerror"):
+        assert required in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_1503_08462_gb300 import _build
+
+    path = _build.build_cuda_lib()
+    lib = ctypes.CDLL(str(path))  # loads without a GPU
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    from paper_1503_08462_gb300 import amgeig
+
+    assert set(amgeig.EXPORTED) == declared_symbols()
+
+
+def test_host_only_calls_without_gpu():
+    from paper_1503_08462_gb300 import amgeig
+
+    o = amgeig.amgeig_default_options()
+    assert (o.max_corrections, o.v_cycles, o.pre_sweeps, o.post_sweeps) == (20, 1, 1, 1)
+    assert amgeig.strerror(amgeig.AMGEIG_ENOCONV).startswith("not converged")

@@ -1,0 +1,195 @@
+"""GPU path vs the CPU oracle, through the C ABI (needs a GB300 and libamgeig.so)."""
+import numpy as np
+import pytest
+
+from oracle import amg_oracle as O
+from paper_1503_08462_gb300 import amgeig as ae
+
+from helpers import dense_pairs, eig_rel_tol, lam_max, m_subspace_angle, problem_and_blob
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+# ------------------------------------------------------------------ dense eigensolver
+
+
+def _rand_sym(n, spectrum, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (Q * spectrum) @ Q.T
+
+
+@pytest.mark.parametrize("n,nwant,kind", [(1, 1, "plain"), (2, 2, "plain"), (7, 3, "plain"), (50, 10, "plain"),
+                                          (131, 22, "plain"), (131, 22, "cluster"), (260, 60, "graded"),
+                                          (64, 64, "plain")])
+def test_sym_eigh_matches_lapack(n, nwant, kind):
+    rng = np.random.default_rng(n + nwant)
+    if kind == "plain":
+        spec = np.sort(rng.uniform(0.5, 100.0, n))
+    elif kind == "cluster":
+        spec = np.sort(np.concatenate([[3.0, 3.0 + 1e-9, 3.0 + 2e-9, 7.0, 7.0], rng.uniform(1.0, 50.0, n - 5)]))
+    else:
+        spec = np.sort(10.0 ** rng.uniform(-2, 4, n))
+    H = _rand_sym(n, spec, n)
+    H = 0.5 * (H + H.T)
+    w, V = ae.amgeig_sym_eigh(H, nwant)
+    ref = np.linalg.eigvalsh(H)[:nwant]
+    scale = np.abs(ref).max() if kind != "graded" else np.abs(spec).max()
+    assert np.all(np.abs(w - ref) <= 1e-12 * scale), np.abs(w - ref).max() / scale
+    assert np.abs(V.T @ V - np.eye(nwant)).max() < 1e-12
+    R = H @ V - V * w
+    assert np.abs(R).max() <= 1e-11 * scale
+
+
+# ------------------------------------------------------------------ V-cycle
+
+
+@pytest.mark.parametrize("kind,size,cap,width", [("square", 32, 50, 4), ("lshape", 16, 60, 7), ("checker", 32, 40, 33)])
+def test_vcycle_matches_oracle(kind, size, cap, width):
+    p, blob, _ = problem_and_blob(kind, size, cap, 1 if kind != "checker" else 3)
+    oh = O.read_blob(blob)
+    rng = np.random.default_rng(width)
+    with ae.Hierarchy(blob) as h:
+        for level in range(oh.n_levels):
+            b = rng.standard_normal((oh.sizes[level], width))
+            ref = O.vcycle(oh, level, b, np.zeros_like(b))
+            x64 = ae.amgeig_apply_vcycle(h.handle, level, b, ae.options(precision=ae.AMGEIG_FP64))
+            assert np.abs(x64 - ref).max() <= 1e-11 * np.abs(ref).max()
+            x32 = ae.amgeig_apply_vcycle(h.handle, level, b, ae.options(precision=ae.AMGEIG_MIXED_FP32))
+            assert np.abs(x32 - ref).max() <= 2e-5 * np.abs(ref).max()
+            if level < oh.n_levels - 1:
+                x22 = ae.amgeig_apply_vcycle(h.handle, level, b, ae.options(pre_sweeps=2, post_sweeps=3))
+                ref22 = O.vcycle(oh, level, b, np.zeros_like(b), pre=2, post=3)
+                assert np.abs(x22 - ref22).max() <= 1e-11 * np.abs(ref22).max()
+
+
+# ------------------------------------------------------------------ solver
+
+
+CASES = [("square", 32, 50, 1, 4, 2), ("lshape", 16, 60, 2, 6, 2), ("checker", 32, 60, 3, 5, 2),
+         ("cube", 8, 40, 4, 4, 2), ("square", 48, 120, 5, 20, 3)]
+
+
+@pytest.mark.parametrize("kind,size,cap,seed,q,qe", CASES)
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_iteration_level_parity(kind, size, cap, seed, q, qe, L):
+    """After exactly L finest-level corrections the GPU FP64 path equals the oracle."""
+    p, blob, _ = problem_and_blob(kind, size, cap, seed)
+    oh = O.read_blob(blob)
+    lam_o, U_o, info_o = O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=L))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, code = h.solve(q, tol=0.0, opt=ae.options(q_extra=qe, fixed_corrections=L))
+    assert info.corrections == L
+    tol = eig_rel_tol(lam_o, lam_max(p))
+    assert np.all(np.abs(lam - lam_o) <= tol * lam_o), np.max(np.abs(lam - lam_o) / lam_o)
+    assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
+    assert np.allclose(info.max_relres, info_o.relres.max(), rtol=1e-6, atol=1e-14)
+
+
+@pytest.mark.parametrize("kind,size,cap,seed,q,qe", CASES)
+def test_converged_solve(kind, size, cap, seed, q, qe):
+    p, blob, _ = problem_and_blob(kind, size, cap, seed)
+    oh = O.read_blob(blob)
+    tol = 2e-9 if kind == "checker" else 1e-10
+    lam_ex, U_ex = dense_pairs(p, q)
+    rtol = eig_rel_tol(lam_ex, lam_max(p))
+    with ae.Hierarchy(blob) as h:
+        for prec in (ae.AMGEIG_FP64, ae.AMGEIG_MIXED_FP32):
+            lam, U, info, code = h.solve(q, tol=tol, opt=ae.options(q_extra=qe, max_corrections=100, precision=prec))
+            assert code == ae.AMGEIG_OK and info.converged == 1
+            assert np.all(np.abs(lam - lam_ex) <= rtol * lam_ex), np.max(np.abs(lam - lam_ex) / lam_ex)
+            assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
+            G = U.T @ (oh.M[0] @ U)
+            assert np.abs(G - np.eye(q)).max() < 1e-10
+            idx = np.argmax(np.abs(U), axis=0)
+            assert np.all(U[idx, np.arange(q)] > 0)
+            assert np.all(O.relres(oh, lam, U) <= tol * 1.0001)
+
+
+def test_mixed_matches_fp64_iterates():
+    """The float32 V-cycle changes the iterates by at most float32-level relative amounts."""
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    with ae.Hierarchy(blob) as h:
+        l64, _, _, _ = h.solve(6, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=4))
+        l32, _, _, _ = h.solve(6, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=4,
+                                                          precision=ae.AMGEIG_MIXED_FP32))
+    assert np.max(np.abs(l32 - l64) / l64) < 1e-6
+
+
+def test_deterministic_repeat():
+    p, blob, _ = problem_and_blob("square", 32, 50, 1)
+    with ae.Hierarchy(blob) as h:
+        a = h.solve(4, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=3))
+        b = h.solve(4, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=3))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_device_output_and_nonconvergence():
+    import torch
+
+    p, blob, _ = problem_and_blob("square", 32, 50, 1)
+    with ae.Hierarchy(blob) as h:
+        vals = np.empty(4)
+        vecs = torch.empty((p.n, 4), dtype=torch.float64, device="cuda:0")
+        info = ae.amgeig_info()
+        code = ae.amgeig_solve(h.handle, 4, 1e-14, ae.options(max_corrections=2), vals, vecs, True, info)
+        assert code == ae.AMGEIG_ENOCONV and info.converged == 0 and info.corrections == 2
+        lam_h, U_h, _, _ = h.solve(4, tol=1e-14, opt=ae.options(max_corrections=2))
+        assert np.array_equal(vals, lam_h) and np.array_equal(vecs.cpu().numpy(), U_h)
+
+
+def test_errors_are_reported():
+    p, blob, _ = problem_and_blob("square", 32, 50, 1)
+    bad = bytearray(blob)
+    bad[300] ^= 1
+    with pytest.raises(ae.AmgEigError) as e:
+        ae.amgeig_load_hierarchy(bytes(bad))
+    assert e.value.code == ae.AMGEIG_ECORRUPT
+    with ae.Hierarchy(blob) as h:
+        with pytest.raises(ae.AmgEigError) as e:
+            h.solve(h.sizes[-1] + 1)
+        assert e.value.code == ae.AMGEIG_EINVAL
+        with pytest.raises(ae.AmgEigError):
+            h.solve(2, opt=ae.options(v_cycles=0))
+
+
+def test_submit_poll_matches_direct():
+    import time
+
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    with ae.Hierarchy(blob) as h:
+        direct = [h.solve(q, tol=1e-9, opt=ae.options(q_extra=2, max_corrections=60)) for q in (3, 6)]
+        ids = [ae.amgeig_submit(h.handle, q, 1e-9, ae.options(q_extra=2, max_corrections=60)) for q in (3, 6)]
+        for rid, q, d in zip(ids, (3, 6), direct):
+            vals = np.empty(q)
+            vecs = np.empty((p.n, q))
+            t0 = time.time()
+            while True:
+                done, code = ae.amgeig_poll(rid, vals, vecs)
+                if done:
+                    break
+                assert time.time() - t0 < 120
+                time.sleep(0.01)
+            assert code == ae.AMGEIG_OK
+            assert np.array_equal(vals, d[0]) and np.array_equal(vecs, d[1])
+        with pytest.raises(ae.AmgEigError):
+            ae.amgeig_poll(ids[0])
+
+
+def test_multiple_vcycles_match_oracle():
+    p, blob, _ = problem_and_blob("square", 32, 50, 1)
+    oh = O.read_blob(blob)
+    lam_o, U_o, _ = O.solve(oh, 4, tol=0.0, opts=O.Options(q_extra=1, fixed_corrections=2, v_cycles=2,
+                                                           pre_sweeps=2, post_sweeps=1))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, _ = h.solve(4, tol=0.0, opt=ae.options(q_extra=1, fixed_corrections=2, v_cycles=2,
+                                                             pre_sweeps=2, post_sweeps=1))
+    assert np.max(np.abs(lam - lam_o) / lam_o) < 1e-10
+    assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
