@@ -152,6 +152,32 @@ int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals
 int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* b,
                         double* x);
 
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Per kernel class totals recorded while profiling is enabled. */
+typedef struct {
+  char name[24];    /* kernel class: defect, smooth, transfer, coarse_solve, augment,
+                       gram, pencil, recombine, other */
+  int64_t launches; /* timed launch scopes */
+  int64_t kernels;  /* kernels inside those scopes */
+  double total_ms;  /* sum of CUDA-event durations, recorded on the launching stream */
+  double bytes;     /* algorithmic HBM bytes of those launches (each operand moved once) */
+  double flops;     /* algorithmic floating-point operations of those launches */
+} amgeig_prof_entry;
+
+/* Enable (1; clears the table) or disable (0) CUDA-event timing of every launch
+ * of this library in this process.  Timing adds two event records per launch.
+ * Returns AMGEIG_OK. */
+int amgeig_profile_enable(int enable);
+
+/* Synchronise on the recorded events and write up to max_entries per-class
+ * totals (classes with no launches are skipped) into out; *n_entries receives
+ * the count.  Errors: EINVAL, ECUDA. */
+int amgeig_profile_read(amgeig_prof_entry* out, int max_entries, int* n_entries);
+
+/* Cumulative number of kernels this library has launched in this process. */
+uint64_t amgeig_kernel_launches(void);
+
 /* Static description of a status code. */
 const char* amgeig_strerror(int code);
 

@@ -21,6 +21,7 @@
 #include "amgeig.h"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.cuh"
 
 using namespace amgeig;
 
@@ -368,10 +369,10 @@ void axpy(const float* x, long long c, float* y, cudaStream_t s) { launch_axpy_f
 const double* dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->dinv64[l]; }
 const float* dinv_of(amgeig_hierarchy_t* h, int l, float*) { return h->dinv32[l]; }
 void coarse_solve(amgeig_hierarchy_t* h, const double* b, int q, double* x, cudaStream_t s) {
-  launch_gemm_f64(h->dn, q, h->dn, 1.0, h->Ainv, h->dn, false, b, q, false, 0.0, x, q, s);
+  launch_gemm_f64(h->dn, q, h->dn, 1.0, h->Ainv, h->dn, false, b, q, false, 0.0, x, q, s, P_COARSE);
 }
 void coarse_solve(amgeig_hierarchy_t* h, const float* b, int q, float* x, cudaStream_t s) {
-  launch_gemm_f32(h->dn, q, h->dn, 1.0f, h->Ainv32, h->dn, false, b, q, false, 0.0f, x, q, s);
+  launch_gemm_f32(h->dn, q, h->dn, 1.0f, h->Ainv32, h->dn, false, b, q, false, 0.0f, x, q, s, P_COARSE);
 }
 
 // One V-cycle for A_k x = B[k] from x = 0; the result is left in X[k] unless
@@ -484,7 +485,10 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     px = w->PX[l];
   }
   launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st);
-  k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
+  {
+    ProfScope ps(st, P_OTHER, 16.0 * q, 0.0);
+    k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
+  }
   CK(cudaGetLastError());
   return AMGEIG_OK;
 }
@@ -530,7 +534,10 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   SolveWork* w = h->ws.get();
   // step 1: initial eigenpairs on level n1 = n (the coarsest)
   launch_copy_cols(h->Z, h->dn, h->dn, qt, w->U, st);
-  k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
+  {
+    ProfScope ps(st, P_OTHER, 16.0 * qt, 0.0);
+    k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
+  }
   CK(cudaGetLastError());
   int corrections = 0;
   bool converged = false;
@@ -609,9 +616,10 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
   const int N0 = static_cast<int>(h->sizes[0]);
   if (eigvals) CK(cudaMemcpyAsync(eigvals, w->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st));
   if (eigvecs) {
-    k_col_sign<<<q, 256, 0, st>>>(w->U, N0, qt, q, w->sign);
     double* dst = on_device ? eigvecs : w->V;  // V is free after the solve
     const long long total = static_cast<long long>(N0) * q;
+    ProfScope ps(st, P_OTHER, 8.0 * N0 * qt + 16.0 * total, 0.0, 2);
+    k_col_sign<<<q, 256, 0, st>>>(w->U, N0, qt, q, w->sign);
     k_out_vectors<<<static_cast<int>(std::min<long long>((total + 255) / 256, 8LL * kNumSms)), 256, 0, st>>>(
         w->U, N0, qt, q, w->sign, dst);
     CK(cudaGetLastError());

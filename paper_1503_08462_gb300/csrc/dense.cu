@@ -3,6 +3,7 @@
 // reductions of per-block partial sums, and the residual test.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace amgeig {
 namespace {
@@ -122,15 +123,17 @@ int gram_chunks(int rows, int q, int w, int* chunk_rows) {
 }  // namespace
 
 void launch_gemm_f64(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
-                     bool tb, double beta, double* C, int ldc, cudaStream_t st) {
+                     bool tb, double beta, double* C, int ldc, cudaStream_t st, int cls) {
   if (M <= 0 || N <= 0) return;
+  ProfScope ps(st, cls, 8.0 * (1.0 * M * K + 1.0 * K * N + (beta != 0.0 ? 2.0 : 1.0) * M * N), 2.0 * M * N * K);
   dim3 grid(ceil_div(N, kTile), ceil_div(M, kTile));
   k_gemm<double><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
 }
 
 void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, bool ta, const float* B, int ldb,
-                     bool tb, float beta, float* C, int ldc, cudaStream_t st) {
+                     bool tb, float beta, float* C, int ldc, cudaStream_t st, int cls) {
   if (M <= 0 || N <= 0) return;
+  ProfScope ps(st, cls, 4.0 * (1.0 * M * K + 1.0 * K * N + (beta != 0.0f ? 2.0 : 1.0) * M * N), 2.0 * M * N * K);
   dim3 grid(ceil_div(N, kTile), ceil_div(M, kTile));
   k_gemm<float><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
 }
@@ -148,6 +151,7 @@ void launch_gram_strided(int rows, const double* V, int ldv, int q, const double
   const int chunks = gram_chunks(rows, q, w, &cr);
   const int tiles_w = ceil_div(w, kGT);
   dim3 grid(chunks, ceil_div(q, kGT) * tiles_w);
+  ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks * q * w, 2.0 * rows * q * w);
   k_gram_partial<<<grid, 256, 0, st>>>(rows, V, ldv, q, W, ldw, w, cr, tiles_w, scratch);
   launch_sum_partials(scratch, chunks, q * w, G, st);
 }
@@ -159,16 +163,19 @@ void launch_gram(int rows, const double* V, int q, const double* W, int w, doubl
 
 void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st) {
   if (len <= 0) return;
+  ProfScope ps(st, P_OTHER, 8.0 * (nparts + 1.0) * len, 1.0 * nparts * len);
   k_sum_partials<<<ceil_div(len, 256), 256, 0, st>>>(part, nparts, len, out);
 }
 
 void launch_relres(const double* sums, const double* lam, int q, double* relres, int* flags, cudaStream_t st) {
+  ProfScope ps(st, P_DEFECT, 32.0 * q, 4.0 * q);
   k_relres<<<1, 256, 0, st>>>(sums, lam, q, relres, flags);
 }
 
 void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, cudaStream_t st) {
   const long long total = static_cast<long long>(rows) * q;
   if (total <= 0) return;
+  ProfScope ps(st, P_OTHER, 16.0 * total, 0.0);
   long long b = (total + 255) / 256;
   if (b > 8 * kNumSms) b = 8 * kNumSms;
   k_copy_cols<<<static_cast<int>(b), 256, 0, st>>>(src, rows, ld, q, dst);

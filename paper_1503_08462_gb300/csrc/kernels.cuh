@@ -75,10 +75,11 @@ void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaS
 
 // C = alpha op(A) op(B) + beta C, all row-major; op = transpose when t* != 0.
 // A is M x K (or K x M when ta), B is K x N (or N x K when tb).
+// cls: the profiler class the launch is accounted to (prof.cuh; 8 = other)
 void launch_gemm_f64(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
-                     int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st);
+                     int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st, int cls = 8);
 void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, bool ta, const float* B, int ldb,
-                     bool tb, float beta, float* C, int ldc, cudaStream_t st);
+                     bool tb, float beta, float* C, int ldc, cudaStream_t st, int cls = 8);
 
 // Gram G = V^T W  (V: rows x q, W: rows x w) -> G: q x w, via per-chunk partials
 // in `scratch` (size gram_scratch_doubles(rows, q, w)) and a fixed-order sum.

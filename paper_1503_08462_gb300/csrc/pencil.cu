@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace amgeig {
 
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
     }
     const df sigma = block_reduce_df(a, red, &sc[0]);
     const df x0 = W[(k + 1) * N + k];
+    __syncthreads();  // every thread has read x0 before thread 0 overwrites it with v0
     if (sigma.hi == 0.f) {
       if (tid == 0) {
         tau[k] = df{0.f, 0.f};
@@ -824,6 +826,7 @@ void pencil_work_destroy(PencilWork* w) {
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
                     cudaStream_t st) {
   const size_t sm = syev_smem(n, nwant);
+  ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
   cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
   k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, H, evals, evecs, w->W, w->tau, w->dd, w->ee, w->fac, w->Zt,
                                        w->rr, w->perm);
@@ -832,6 +835,9 @@ void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* ev
 void launch_pencil_solve(PencilWork* w, int dn, int q, const double* C, const double* G, const double* Z,
                          const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st) {
   const int n = dn + q;
+  // three kernels launched here; the GEMM, Gram and eigensolver launchers count their own
+  ProfScope ps(st, P_PENCIL, 8.0 * (1.0 * dn * dn * 2 + 2.0 * dn * q + 2.0 * q * q + 1.0 * n * n + 1.0 * dn * q), 0.0,
+               3);
   // K | B = Z^T [C_A | C_M]
   launch_gemm_f64(dn, 2 * q, dn, 1.0, Z, dn, true, C, 2 * q, false, 0.0, w->KB, 2 * q, st);
   k_build_y3<<<ceil_div(static_cast<long long>(dn) * q, 256), 256, 0, st>>>(dn, q, w->KB, theta, w->Y3);
@@ -847,6 +853,7 @@ void launch_pencil_solve(PencilWork* w, int dn, int q, const double* C, const do
 
 void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,
                         double* Ainv, int* status, cudaStream_t st) {
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 0.0, 7);
   // M_n = L L^T
   k_chol<<<1, 1024, 0, st>>>(dn, Mn, w->Lm, status);
   // Hs = L^-1 A_n L^-T : X = L^-1 A_n ; Hs = L^-1 X^T

@@ -1,0 +1,115 @@
+// Launch counter and event-based per-class timing (see prof.cuh).
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "amgeig.h"
+#include "prof.cuh"
+
+namespace amgeig {
+namespace {
+
+struct Rec {
+  int cls;
+  double bytes, flops;
+  int kernels;
+  cudaEvent_t e0, e1;
+};
+
+struct Profiler {
+  std::atomic<unsigned long long> launches{0};
+  std::atomic<bool> on{false};
+  std::mutex mu;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_next = 0;
+
+  cudaEvent_t take() {
+    if (pool_next == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[pool_next++];
+  }
+};
+
+Profiler& prof() {
+  static Profiler* p = new Profiler();
+  return *p;
+}
+
+const char* kNames[P_COUNT] = {"defect", "smooth", "transfer", "coarse_solve", "augment",
+                               "gram", "pencil", "recombine", "other"};
+
+}  // namespace
+
+thread_local int g_depth = 0;  // nested scopes only count launches; the outermost one is timed
+
+ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels) : st_(st), slot_(-1) {
+  Profiler& p = prof();
+  p.launches += static_cast<unsigned long long>(kernels);
+  if (g_depth++ > 0) return;
+  if (!p.on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(p.mu);
+  Rec r{cls, bytes, flops, kernels, p.take(), p.take()};
+  if (!r.e0 || !r.e1) return;
+  cudaEventRecord(r.e0, st);
+  slot_ = static_cast<int>(p.recs.size());
+  p.recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  --g_depth;
+  if (slot_ < 0) return;
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (slot_ < static_cast<int>(p.recs.size())) cudaEventRecord(p.recs[slot_].e1, st_);
+}
+
+}  // namespace amgeig
+
+using namespace amgeig;
+
+extern "C" {
+
+int amgeig_profile_enable(int enable) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (enable) {
+    p.recs.clear();
+    p.pool_next = 0;
+  }
+  p.on.store(enable != 0);
+  return AMGEIG_OK;
+}
+
+int amgeig_profile_read(amgeig_prof_entry* out, int max_entries, int* n_entries) {
+  if (!out || !n_entries || max_entries < 0) return AMGEIG_EINVAL;
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  amgeig_prof_entry tab[P_COUNT];
+  std::memset(tab, 0, sizeof(tab));
+  for (int c = 0; c < P_COUNT; ++c) std::strncpy(tab[c].name, kNames[c], sizeof(tab[c].name) - 1);
+  for (const Rec& r : p.recs) {
+    if (cudaEventSynchronize(r.e1) != cudaSuccess) return AMGEIG_ECUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return AMGEIG_ECUDA;
+    amgeig_prof_entry& t = tab[r.cls];
+    t.launches += 1;
+    t.kernels += r.kernels;
+    t.total_ms += ms;
+    t.bytes += r.bytes;
+    t.flops += r.flops;
+  }
+  int n = 0;
+  for (int c = 0; c < P_COUNT && n < max_entries; ++c)
+    if (tab[c].launches > 0) out[n++] = tab[c];
+  *n_entries = n;
+  return AMGEIG_OK;
+}
+
+uint64_t amgeig_kernel_launches(void) { return prof().launches.load(); }
+
+}  // extern "C"

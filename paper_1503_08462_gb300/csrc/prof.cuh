@@ -1,0 +1,40 @@
+// Launch accounting and optional per-kernel-class CUDA-event timing.
+//
+// Every launcher wraps its kernel(s) in a ProfScope.  The scope always adds
+// its kernel count to a process-wide launch counter; when profiling is
+// enabled it also records CUDA events before and after the launch on the
+// launching stream, together with the algorithmic bytes and flops of that
+// launch, so that achieved GB/s and FLOP/s per kernel class can be computed
+// from the event times.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace amgeig {
+
+enum ProfClass {
+  P_DEFECT = 0,   // lambda M u - A u (+ residual norms)
+  P_SMOOTH,       // l1-Jacobi sweeps and residuals of the V-cycle
+  P_TRANSFER,     // restriction / prolongation SpMM (V-cycle, chains, nested phase)
+  P_COARSE,       // coarsest-level solve of the V-cycle
+  P_AUGMENT,      // [A V | M V]
+  P_GRAM,         // V^T [A V | M V]
+  P_PENCIL,       // reduced pencil and its float-float eigensolve
+  P_RECOMBINE,    // I_n^k Xc + V Y
+  P_OTHER,        // copies, conversions, sign normalisation
+  P_COUNT
+};
+
+class ProfScope {
+ public:
+  ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels = 1);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int slot_;
+};
+
+}  // namespace amgeig

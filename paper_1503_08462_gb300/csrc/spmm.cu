@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace amgeig {
 namespace {
@@ -115,6 +116,8 @@ void defect_impl(const DevCsr& AM, const double* U, int q, const double* lam, TO
   Geo g = geo_for(q);
   const int blocks = ceil_div(AM.rows, g.rows_per_block);
   if (nblocks_out) *nblocks_out = blocks;
+  const double N = AM.rows, nnz = AM.nnz;
+  ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + sizeof(TO) * N * q, 4.0 * nnz * q);
   const size_t sm = partials ? sizeof(double) * g.rows_per_block * 2 * g.G * g.cpt : 0;
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                                        \
@@ -169,6 +172,10 @@ void spmm_impl(const DevCsr& S, const T* vals, const T* X, int width, T* Y, bool
   if (S.rows == 0 || width == 0) return;
   Geo g = geo_for(width);
   const int blocks = ceil_div(S.rows, g.rows_per_block);
+  const double t = sizeof(T);
+  ProfScope ps(st, P_TRANSFER,
+               4.0 * (S.rows + 1) + (4.0 + t) * S.nnz + t * S.cols * width + t * S.rows * width * (accumulate ? 2 : 1),
+               2.0 * S.nnz * width);
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                                     \
   case C:                                                                                                  \
@@ -244,6 +251,12 @@ void smooth_impl(const DevCsr& A, const T* vals, const T* dinv, const T* b, cons
   if (A.rows == 0 || width == 0) return;
   Geo g = geo_for(width);
   const int blocks = ceil_div(A.rows, g.rows_per_block);
+  const double t = sizeof(T), N = A.rows;
+  // vector traffic per mode: 0 reads b, writes x and r; 1 reads b, x, writes out;
+  // 2 reads b, x, writes r; 3 reads b, x, U and writes V (float64)
+  const double vec = (MODE == 3) ? (2.0 * t + 16.0) * N * width : 3.0 * t * N * width;
+  ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + (4.0 + t) * A.nnz + (MODE == 2 ? 0.0 : t * N) + vec,
+               2.0 * A.nnz * width);
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                                         \
   case C:                                                                                                      \
@@ -419,15 +432,19 @@ void launch_jacobi_to_v_f32(const DevCsr& A, const float* dinv, const float* b, 
   smooth_impl<float, 3>(A, A.v32, dinv, b, x, width, nullptr, nullptr, U, V, st);
 }
 void launch_add_to_v_f64(const double* U, const double* x, long long count, double* V, cudaStream_t st) {
+  ProfScope ps(st, P_SMOOTH, 24.0 * count, 1.0 * count);
   k_add_to_v<double><<<grid_for(count), kThreads, 0, st>>>(U, x, count, V);
 }
 void launch_add_to_v_f32(const double* U, const float* x, long long count, double* V, cudaStream_t st) {
+  ProfScope ps(st, P_SMOOTH, 20.0 * count, 1.0 * count);
   k_add_to_v<float><<<grid_for(count), kThreads, 0, st>>>(U, x, count, V);
 }
 
 void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaStream_t st) {
   Geo g = geo_for(q);
   const int blocks = ceil_div(AM.rows, g.rows_per_block);
+  const double N = AM.rows, nnz = AM.nnz;
+  ProfScope ps(st, P_AUGMENT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 16.0 * N * q, 4.0 * nnz * q);
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                                         \
   case C:                                                                                                      \
@@ -448,6 +465,7 @@ void launch_recombine(int rows, const double* Xp, const double* V, const double*
   Geo g = geo_for(q);
   const int blocks = ceil_div(rows, g.rows_per_block);
   const size_t sm = sizeof(double) * q * q;
+  ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                         \
   case C:                                                                                      \
@@ -466,17 +484,21 @@ void launch_recombine(int rows, const double* Xp, const double* V, const double*
 }
 
 void launch_axpy_f64(const double* x, long long count, double* y, cudaStream_t st) {
+  ProfScope ps(st, P_SMOOTH, 24.0 * count, 1.0 * count);
   k_axpy<double><<<grid_for(count), kThreads, 0, st>>>(x, count, y);
 }
 void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st) {
+  ProfScope ps(st, P_SMOOTH, 12.0 * count, 1.0 * count);
   k_axpy<float><<<grid_for(count), kThreads, 0, st>>>(x, count, y);
 }
 
 void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
   k_f64_to_f32<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
 }
 
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
   k_f32_to_f64<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
 }
 

@@ -13,7 +13,7 @@ def declared_symbols():
     for hdr in (ROOT / "include").glob("*.h"):
         text = hdr.read_text()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(?:int|void|const char\*)\s+(amgeig_\w+)\s*\(", text):
+        for m in re.finditer(r"\b(?:int|void|const char\*|uint64_t)\s+(amgeig_\w+)\s*\(", text):
             names.add(m.group(1))
     return names
 
