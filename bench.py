@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Eigenpairs/s of the AMG multilevel-correction eigensolver's solve phase on GB300.
+
+One step = one complete solve (Algorithm 3.2 with Algorithm 3.1: coarse
+eigenproblem, nested prolongations with one correction per level, finest-level
+corrections until the relative residual test passes) of the synthetic workload
+through the C ABI.  `value` is eigenpairs/s over the timed steps with the
+hierarchy already resident in HBM; `e2e` is the same metric through the same
+API with host buffers: load of the hierarchy blob from pinned host memory,
+solve, and the copy of eigenvalues and eigenvectors back to pinned host memory
+inside the timed region.
+
+Default workload: 2D P1 FE Laplace on the L-shape (-1,1)^2 minus [0,1)x(-1,0],
+h = 1/512, N = 784,385, q = 20, mixed precision (float32 V-cycle, float64
+defect / Rayleigh-Ritz / recombination).  Its accuracy is checked against the
+float64 path converged on the same hierarchy.
+
+Multi-GPU: the solve does not shard; with --gpus N each rank runs an independent
+replica of the workload ("replicas only"), value sums the ranks' solves.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
+
+WORKLOADS = {
+    # name: (builder, kwargs, q, q_extra, coarse_cap, tol)
+    "lshape_h512_q20": ("lshape_2d", dict(m_half=512, seed=2), 20, 4, 400, 1e-7),
+    "square_h32_q4": ("square_2d", dict(m=32, seed=1), 4, 2, 50, 1e-9),
+    "checker_h1024_q50": ("square_2d", dict(m=1024, checker=4, seed=3), 50, 6, 400, 1e-6),
+    "cube_m128_q10": ("cube_3d", dict(m=128, seed=4), 10, 4, 400, 1e-7),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def build_workload(name):
+    from paper_1503_08462_gb300.inputs import hierarchy, meshes
+
+    builder, kw, q, qe, cap, tol = WORKLOADS[name]
+    t0 = time.perf_counter()
+    p = getattr(meshes, builder)(**kw)
+    blob, h = hierarchy.problem_blob(p, coarse_cap=cap)
+    log(f"[bench] {name}: N={p.n} levels={h.sizes} op.complexity={h.operator_complexity():.2f} "
+        f"blob={len(blob) / 1e6:.1f} MB setup={time.perf_counter() - t0:.1f}s")
+    return p, blob, h, q, qe, tol
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(blob, q, qe, n_corr, sample_corr=2):
+    """The CPU oracle on the same hierarchy, single thread: the nested phase plus
+    `sample_corr` finest-level corrections, scaled to `n_corr` corrections."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import amg_oracle as O
+
+    oh = O.read_blob(blob)
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1))
+        t1 = time.perf_counter()
+        O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1 + sample_corr))
+        t2 = time.perf_counter()
+    per_corr = (t2 - t1 - (t1 - t0)) / sample_corr
+    nested = (t1 - t0) - per_corr
+    est = nested + n_corr * per_corr
+    return q / est, est, nested, per_corr, (t2 - t0)
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle (as it stands) on this workload, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p, blob, h, q, qe, tol = build_workload(args.workload)
+    n_corr = args.reference_corrections
+    vals = []
+    t_all = 0.0
+    for i in range(args.warmup + args.steps):
+        v, est, nested, per_corr, wall = oracle_sample(blob, q, qe, n_corr)
+        t_all += wall
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": "eigenpairs/s", "value": value, "unit": "eigenpairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": p.n, "q": q, "q_extra": qe, "levels": h.sizes},
+        "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: nested phase + 2 finest corrections of the FP64 oracle, scaled to "
+                                   f"{n_corr} corrections"},
+        "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lshape_h512_q20", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-corrections", type=int, default=12)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1503_08462_gb300 import amgeig as ae
+
+    p, blob, hinfo, q, qe, tol = build_workload(args.workload)
+    prec = ae.AMGEIG_MIXED_FP32 if args.precision == "mixed" else ae.AMGEIG_FP64
+    opt = ae.options(q_extra=qe, max_corrections=60, precision=prec)
+    h = ae.Hierarchy(blob, device=local)
+    N0 = h.sizes[0]
+    stream = torch.cuda.Stream(device=local)
+    vals = np.empty(q)
+    vecs = torch.empty((N0, q), dtype=torch.float64, device=f"cuda:{local}")
+    info = ae.amgeig_info()
+
+    # reference accuracy: the float64 path converged tightly on the same hierarchy
+    ref = np.empty(q)
+    info_ref = ae.amgeig_info()
+    ae.amgeig_solve(h.handle, q, 1e-10, ae.options(q_extra=qe, max_corrections=80), ref, None, False, info_ref,
+                    stream.cuda_stream)
+
+    def step():
+        return ae.amgeig_solve(h.handle, q, tol, opt, vals, vecs, True, info, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        step()
+    rel_err = float(np.max(np.abs(vals - ref) / np.abs(ref)))
+    corrections = info.corrections
+
+    launches0 = ae.amgeig_kernel_launches()
+    ae.amgeig_profile_enable(True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            code = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = ae.amgeig_profile_read()
+    ae.amgeig_profile_enable(False)
+    launches = ae.amgeig_kernel_launches() - launches0
+    if dist is not None:
+        t = torch.tensor([ms_total], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = world * q * args.steps / (ms_total / 1e3)
+
+    # end to end through the public API with host buffers
+    blob_pinned = torch.frombuffer(bytearray(blob), dtype=torch.uint8).pin_memory()
+    vals_h = torch.empty(q, dtype=torch.float64).pin_memory()
+    vecs_h = torch.empty((N0, q), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hh = ae.lib()
+        import ctypes
+
+        handle = ctypes.c_void_p()
+        rc = hh.amgeig_load_hierarchy(ctypes.c_void_p(blob_pinned.data_ptr()), len(blob), local,
+                                      ctypes.byref(handle))
+        ae._check(rc, "amgeig_load_hierarchy")
+        ae.amgeig_solve(handle, q, tol, opt, vals_h, vecs_h, False, None, None)
+        ae.amgeig_free_hierarchy(handle)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = world * q / e2e_s
+
+    # roofline of the dominant kernel class
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    name, d = dom
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    t_s = d["total_ms"] / 1e3
+    gbs = d["bytes"] / t_s / 1e9
+    tfl = d["flops"] / t_s / 1e12
+    per_launch_ms = d["total_ms"] / d["launches"]
+    if d["flops"] / (FP64_PEAK_TFLOPS * 1e12) > d["bytes"] / (hbm_peak * 1e9):
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2070 MHz (derived)",
+                "ms_per_launch": per_launch_ms}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "kernel": name, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "ms_per_launch": per_launch_ms}
+    kernels = {k: {"launches": v["launches"], "kernels": v["kernels"], "ms": round(v["total_ms"], 3),
+                   "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
+                   "GB/s": round(v["bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1),
+                   "TFLOP/s": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 4)} for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, est, nested, per_corr, wall_c = oracle_sample(blob, q, qe, corrections)
+            cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"FP64 oracle, 1 thread: nested phase ({nested:.1f}s) + 2 finest corrections "
+                             f"({per_corr:.1f}s each) measured, scaled to the {corrections} corrections of this run"}
+        except Exception as exc:  # the baseline must not hide the GPU result
+            cpu = {"value": None, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {
+            "metric": "eigenpairs/s", "value": value, "unit": "eigenpairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32" if prec == ae.AMGEIG_MIXED_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N0, "q": q, "q_extra": qe, "levels": h.sizes,
+                       "precision": args.precision, "tol_relres": tol, "corrections": corrections,
+                       "rel_eig_err_vs_fp64": rel_err, "fp64_corrections": info_ref.corrections,
+                       "l2": "inputs larger than L2 (hierarchy + blocks > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": len(blob),
+                    "d2h_bytes_per_step": 8 * q + 8 * N0 * q},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "status": code,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -41,6 +41,11 @@ class amgeig_options(ctypes.Structure):
                 ("fixed_corrections", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class amgeig_prof_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("kernels", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 class amgeig_info(ctypes.Structure):
     _fields_ = [("corrections", ctypes.c_int), ("converged", ctypes.c_int), ("n1", ctypes.c_int),
                 ("status", ctypes.c_int), ("max_relres", ctypes.c_double)]
@@ -49,7 +54,8 @@ class amgeig_info(ctypes.Structure):
 _lib = None
 EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
-            "amgeig_sym_eigh", "amgeig_apply_vcycle"]
+            "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_profile_enable", "amgeig_profile_read",
+            "amgeig_kernel_launches"]
 
 
 def library_path() -> str:
@@ -80,8 +86,13 @@ def lib():
         L.amgeig_last_error.restype = ctypes.c_char_p
         L.amgeig_sym_eigh.argtypes = [i32, i32, i32, vp, vp, vp]
         L.amgeig_apply_vcycle.argtypes = [vp, i32, i32, ctypes.POINTER(amgeig_options), vp, vp]
+        L.amgeig_profile_enable.argtypes = [i32]
+        L.amgeig_profile_read.argtypes = [ctypes.POINTER(amgeig_prof_entry), i32, ctypes.POINTER(i32)]
+        L.amgeig_kernel_launches.argtypes = []
+        L.amgeig_kernel_launches.restype = ctypes.c_uint64
         for name in ("amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
-                     "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle"):
+                     "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle",
+                     "amgeig_profile_enable", "amgeig_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -174,6 +185,23 @@ def amgeig_apply_vcycle(h, level: int, b: np.ndarray, opt: Optional[amgeig_optio
     _check(lib().amgeig_apply_vcycle(h, level, b.shape[1], ctypes.byref(opt) if opt is not None else None, _ptr(b),
                                      _ptr(x)), "amgeig_apply_vcycle")
     return x
+
+
+def amgeig_profile_enable(enable: bool) -> None:
+    _check(lib().amgeig_profile_enable(1 if enable else 0), "amgeig_profile_enable")
+
+
+def amgeig_profile_read():
+    """Per kernel class totals: {name: dict(launches, kernels, total_ms, bytes, flops)}."""
+    buf = (amgeig_prof_entry * 16)()
+    n = ctypes.c_int()
+    _check(lib().amgeig_profile_read(buf, 16, ctypes.byref(n)), "amgeig_profile_read")
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, kernels=buf[i].kernels, total_ms=buf[i].total_ms,
+                                       bytes=buf[i].bytes, flops=buf[i].flops) for i in range(n.value)}
+
+
+def amgeig_kernel_launches() -> int:
+    return int(lib().amgeig_kernel_launches())
 
 
 def strerror(code: int) -> str:

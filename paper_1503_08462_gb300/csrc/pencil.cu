@@ -457,13 +457,21 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
           df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
           if (b0 < nwant) {
             const df apq = Hq[a0 * NW + b0];
-            if (apq.hi != 0.f) {
-              const df app = Hq[a0 * NW + a0], aqq = Hq[b0 * NW + b0];
-              // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1))
+            const df app = Hq[a0 * NW + a0], aqq = Hq[b0 * NW + b0];
+            // skip entries already below the float-float resolution of the diagonal
+            const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
+            if (fabsf(apq.hi) > thr) {
+              // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
+              // and t = 1 / (2 theta) once theta^2 would leave the float range
               const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
-              const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
-              df tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
-              if (df_lt0(th)) tt = df_neg(tt);
+              df tt;
+              if (fabsf(th.hi) > 1.0e12f) {
+                tt = df_div(df{0.5f, 0.f}, th);
+              } else {
+                const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
+                tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
+                if (df_lt0(th)) tt = df_neg(tt);
+              }
               cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
               sn = df_mul(tt, cs);
             }
