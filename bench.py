@@ -37,11 +37,14 @@ import numpy as np  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
 
 WORKLOADS = {
-    # name: (builder, kwargs, q, q_extra, coarse_cap, tol)
-    "lshape_h512_q20": ("lshape_2d", dict(m_half=512, seed=2), 20, 4, 400, 1e-7),
-    "square_h32_q4": ("square_2d", dict(m=32, seed=1), 4, 2, 50, 1e-9),
-    "checker_h1024_q50": ("square_2d", dict(m=1024, checker=4, seed=3), 50, 6, 400, 1e-6),
-    "cube_m128_q10": ("cube_3d", dict(m=128, seed=4), 10, 4, 400, 1e-7),
+    # name: builder, its arguments, q, q_extra, coarse-level cap of the AMG setup,
+    # relative-residual tolerance, coarse modes in the pencil (0 = all of V_n)
+    "lshape_h512_q20": dict(builder="lshape_2d", kw=dict(m_half=512, seed=2), q=20, qe=4, cap=400, tol=1e-6,
+                            modes=96),
+    "square_h32_q4": dict(builder="square_2d", kw=dict(m=32, seed=1), q=4, qe=2, cap=50, tol=1e-9, modes=0),
+    "checker_h1024_q50": dict(builder="square_2d", kw=dict(m=1024, checker=4, seed=3), q=50, qe=6, cap=400,
+                              tol=1e-6, modes=112),
+    "cube_m128_q10": dict(builder="cube_3d", kw=dict(m=128, seed=4), q=10, qe=4, cap=400, tol=1e-6, modes=64),
 }
 
 
@@ -49,13 +52,14 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def build_workload(name):
+def build_workload(name, cap=None):
     from paper_1503_08462_gb300.inputs import hierarchy, meshes
 
-    builder, kw, q, qe, cap, tol = WORKLOADS[name]
+    wl = WORKLOADS[name]
+    q, qe, tol = wl["q"], wl["qe"], wl["tol"]
     t0 = time.perf_counter()
-    p = getattr(meshes, builder)(**kw)
-    blob, h = hierarchy.problem_blob(p, coarse_cap=cap)
+    p = getattr(meshes, wl["builder"])(**wl["kw"])
+    blob, h = hierarchy.problem_blob(p, coarse_cap=cap or wl["cap"])
     log(f"[bench] {name}: N={p.n} levels={h.sizes} op.complexity={h.operator_complexity():.2f} "
         f"blob={len(blob) / 1e6:.1f} MB setup={time.perf_counter() - t0:.1f}s")
     return p, blob, h, q, qe, tol
@@ -175,6 +179,12 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-corrections", type=int, default=12)
+    ap.add_argument("--tol", type=float, default=None, help="relative-residual tolerance (workload default)")
+    ap.add_argument("--coarse-modes", type=int, default=None, help="coarse modes in the pencil (0 = all)")
+    ap.add_argument("--q-extra", type=int, default=None)
+    ap.add_argument("--cap", type=int, default=None, help="coarse-level cap of the AMG setup")
+    ap.add_argument("--sweeps", type=int, default=1, help="l1-Jacobi sweeps before and after the coarse correction")
+    ap.add_argument("--v-cycles", type=int, default=1)
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -198,9 +208,15 @@ def main():
     __graft_entry__.build()
     from paper_1503_08462_gb300 import amgeig as ae
 
-    p, blob, hinfo, q, qe, tol = build_workload(args.workload)
+    p, blob, hinfo, q, qe, tol = build_workload(args.workload, args.cap)
+    if args.tol is not None:
+        tol = args.tol
+    if args.q_extra is not None:
+        qe = args.q_extra
+    modes = WORKLOADS[args.workload]["modes"] if args.coarse_modes is None else args.coarse_modes
     prec = ae.AMGEIG_MIXED_FP32 if args.precision == "mixed" else ae.AMGEIG_FP64
-    opt = ae.options(q_extra=qe, max_corrections=60, precision=prec)
+    opt = ae.options(q_extra=qe, max_corrections=60, precision=prec, coarse_modes=modes,
+                     pre_sweeps=args.sweeps, post_sweeps=args.sweeps, v_cycles=args.v_cycles)
     h = ae.Hierarchy(blob, device=local)
     N0 = h.sizes[0]
     stream = torch.cuda.Stream(device=local)
@@ -208,11 +224,14 @@ def main():
     vecs = torch.empty((N0, q), dtype=torch.float64, device=f"cuda:{local}")
     info = ae.amgeig_info()
 
-    # reference accuracy: the float64 path converged tightly on the same hierarchy
+    # reference accuracy: the paper's method (all of V_n in the pencil) on the
+    # float64 path, converged tightly on the same hierarchy
     ref = np.empty(q)
     info_ref = ae.amgeig_info()
-    ae.amgeig_solve(h.handle, q, 1e-10, ae.options(q_extra=qe, max_corrections=80), ref, None, False, info_ref,
+    t_ref = time.perf_counter()
+    ae.amgeig_solve(h.handle, q, 1e-8, ae.options(q_extra=qe, max_corrections=150), ref, None, False, info_ref,
                     stream.cuda_stream)
+    t_ref = time.perf_counter() - t_ref
 
     def step():
         return ae.amgeig_solve(h.handle, q, tol, opt, vals, vecs, True, info, stream.cuda_stream)
@@ -317,7 +336,9 @@ def main():
             "dtype": "f64+f32" if prec == ae.AMGEIG_MIXED_FP32 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "N": N0, "q": q, "q_extra": qe, "levels": h.sizes,
                        "precision": args.precision, "tol_relres": tol, "corrections": corrections,
+                       "coarse_modes": modes, "sweeps": args.sweeps, "v_cycles": args.v_cycles,
                        "rel_eig_err_vs_fp64": rel_err, "fp64_corrections": info_ref.corrections,
+                       "fp64_full_pencil_s": round(t_ref, 4), "fp64_relres": info_ref.max_relres,
                        "l2": "inputs larger than L2 (hierarchy + blocks > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,

@@ -63,7 +63,11 @@ typedef struct {
   int precision;         /* AMGEIG_FP64 or AMGEIG_MIXED_FP32 */
   int fixed_corrections; /* > 0: run exactly this many finest-level corrections and
                             ignore tol (iteration-level parity mode) */
-  int reserved;          /* must be 0 */
+  int coarse_modes;      /* 0: the pencil of Algorithm 3.1 step 2 uses all of V_n (the
+                            paper's method).  m > 0: only the m lowest eigenvectors of
+                            the coarsest pencil (A_n, M_n) span its coarse part (an
+                            option of this library: the pencil shrinks from d_n + q to
+                            m + q; the fixed point, the exact eigenpairs, is unchanged) */
 } amgeig_options;
 
 /* Per-solve report. */

@@ -197,6 +197,10 @@ class Options:
     post_sweeps: int = 1
     q_extra: int = 0
     fixed_corrections: int = 0  # > 0: run exactly this many finest-level corrections
+    # > 0: the pencil's coarse part is spanned by the `coarse_modes` lowest
+    # eigenvectors of (A_n, M_n) instead of all of V_n (an option of the GPU
+    # library, not of the paper; 0 = the paper's pencil)
+    coarse_modes: int = 0
 
 
 def augmented_pencil(h: OracleHierarchy, k: int, V: np.ndarray):
@@ -216,14 +220,29 @@ def smallest_pairs(Ahat: np.ndarray, Mhat: np.ndarray, count: int):
     return mu, X
 
 
+def coarse_modes_basis(h: OracleHierarchy, m: int) -> np.ndarray:
+    """The m lowest M_n-orthonormal eigenvectors of (A_n, M_n)."""
+    _, Z = sla.eigh(h.An, h.Mn, subset_by_index=[0, m - 1])
+    return Z
+
+
 def correction(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
     """One AMGCorrection(n, k, {lambda_j, u_j}) step; returns (lambda, U)."""
     qt = U.shape[1]
     b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
     V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps)
     Ahat, Mhat = augmented_pencil(h, k, V)
-    mu, X = smallest_pairs(Ahat, Mhat, qt)
     dn = h.sizes[-1]
+    if 0 < opts.coarse_modes < dn:
+        # restrict the coarse block to span(Z_m): the pencil of B = [I_n^k Z_m, V]
+        m = opts.coarse_modes
+        T = np.zeros((m + qt, dn + qt))
+        T[:m, :dn] = coarse_modes_basis(h, m).T
+        T[m:, dn:] = np.eye(qt)
+        mu, X = smallest_pairs(T @ Ahat @ T.T, T @ Mhat @ T.T, qt)
+        X = T.T @ X
+    else:
+        mu, X = smallest_pairs(Ahat, Mhat, qt)
     U_new = prolong_from_coarsest(h, k, X[:dn]) + V @ X[dn:]
     return mu, U_new
 

@@ -477,7 +477,8 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     cur = w->WC[l + 1];
   }
   CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
-  launch_pencil_solve(w->pw, h->dn, q, cur, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
+  const int modes = (o.coarse_modes > 0 && o.coarse_modes < h->dn) ? o.coarse_modes : h->dn;
+  launch_pencil_solve(w->pw, h->dn, modes, q, cur, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
   // recombination: U = I_n^k Xc + V Y
   const double* px = w->Xc;
   for (int l = n - 2; l >= k; --l) {
@@ -512,7 +513,8 @@ int defect(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, 
 
 int check_options(const amgeig_options& o) {
   if (o.max_corrections < 0 || o.v_cycles < 1 || o.pre_sweeps < 0 || o.post_sweeps < 0 || o.q_extra < 0 ||
-      o.fixed_corrections < 0 || o.reserved != 0 || (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32))
+      o.fixed_corrections < 0 || o.coarse_modes < 0 ||
+      (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -696,7 +698,7 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->q_extra = 0;
   opt->precision = AMGEIG_FP64;
   opt->fixed_corrections = 0;
-  opt->reserved = 0;
+  opt->coarse_modes = 0;
 }
 
 const char* amgeig_strerror(int code) {

@@ -89,6 +89,29 @@ __global__ void k_sum_partials(const double* __restrict__ part, int nparts, int 
   }
 }
 
+// many parts: one block per output, strided partial sums then a fixed-shape tree
+__global__ void __launch_bounds__(256) k_sum_partials_wide(const double* __restrict__ part, int nparts, int len,
+                                                           double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[static_cast<long long>(b) * len + j];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sh[0];
+}
+
+__global__ void k_eye_minus(int n, double* __restrict__ T) {
+  const long long total = static_cast<long long>(n) * n;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    T[i] = ((i / n) == (i % n) ? 1.0 : 0.0) - T[i];
+}
+
 __global__ void k_relres(const double* __restrict__ sums, const double* __restrict__ lam, int q,
                          double* __restrict__ relres, int* __restrict__ flags) {
   for (int j = threadIdx.x; j < q; j += blockDim.x) {
@@ -164,7 +187,10 @@ void launch_gram(int rows, const double* V, int q, const double* W, int w, doubl
 void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st) {
   if (len <= 0) return;
   ProfScope ps(st, P_OTHER, 8.0 * (nparts + 1.0) * len, 1.0 * nparts * len);
-  k_sum_partials<<<ceil_div(len, 256), 256, 0, st>>>(part, nparts, len, out);
+  if (nparts >= 64)
+    k_sum_partials_wide<<<len, 256, 0, st>>>(part, nparts, len, out);
+  else
+    k_sum_partials<<<ceil_div(len, 256), 256, 0, st>>>(part, nparts, len, out);
 }
 
 void launch_relres(const double* sums, const double* lam, int q, double* relres, int* flags, cudaStream_t st) {
@@ -179,6 +205,18 @@ void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, c
   long long b = (total + 255) / 256;
   if (b > 8 * kNumSms) b = 8 * kNumSms;
   k_copy_cols<<<static_cast<int>(b), 256, 0, st>>>(src, rows, ld, q, dst);
+}
+
+// One Newton-Schulz step X <- X (2I - A X) for an approximate inverse X of A
+// (n x n, row-major); T and Y are n x n scratch.  Squares the residual I - A X.
+void launch_newton_schulz(int n, const double* A, double* X, double* T, double* Y, cudaStream_t st) {
+  launch_gemm_f64(n, n, n, 1.0, A, n, false, X, n, false, 0.0, T, n, st, P_PENCIL);
+  {
+    ProfScope ps(st, P_PENCIL, 16.0 * n * n, 0.0);
+    k_eye_minus<<<ceil_div(static_cast<long long>(n) * n, 256), 256, 0, st>>>(n, T);
+  }
+  cudaMemcpyAsync(Y, X, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
+  launch_gemm_f64(n, n, n, 1.0, Y, n, false, T, n, false, 1.0, X, n, st, P_PENCIL);
 }
 
 }  // namespace amgeig

@@ -90,6 +90,9 @@ void launch_gram(int rows, const double* V, int q, const double* W, int w, doubl
 void launch_gram_strided(int rows, const double* V, int ldv, int q, const double* W, int ldw, int w, double* scratch,
                          double* G, cudaStream_t st);
 
+// One Newton-Schulz step X <- X (2I - A X) (n x n row-major; T, Y scratch)
+void launch_newton_schulz(int n, const double* A, double* X, double* T, double* Y, cudaStream_t st);
+
 // Sum `nparts` partial rows of length `len` in fixed order: out[j] = sum_b part[b*len + j]
 void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st);
 
@@ -111,11 +114,13 @@ void pencil_work_destroy(PencilWork* w);
 // One Rayleigh-Ritz step on V_n + span(V) (Algorithm 3.1 step 2) in the
 // coarse eigenbasis: inputs C = [I_k^n A V | I_k^n M V] (dn x 2q),
 // G = [V^T A V | V^T M V] (q x 2q), the coarse eigenbasis Z (dn x dn, M_n-
-// orthonormal) and Theta (dn).  Outputs the q smallest Ritz values mu (q), the
-// coarse coefficients Xc (dn x q) and the V-coefficients Y (q x q) so that the
-// new vectors are I_n^k Xc + V Y.  status[0] receives AMGEIG_ENOTSPD when the
-// Gram Schur complement is not positive definite.
-void launch_pencil_solve(PencilWork* w, int dn, int q, const double* C, const double* G, const double* Z,
+// orthonormal) and Theta (dn).  The coarse part of the trial space is spanned
+// by the first m <= dn columns of Z (m = dn: all of V_n).  Outputs the q
+// smallest Ritz values mu (q), the coarse coefficients Xc (dn x q) and the
+// V-coefficients Y (q x q) so that the new vectors are I_n^k Xc + V Y.
+// status[0] receives AMGEIG_ENOTSPD when the Gram Schur complement is not
+// positive definite.
+void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C, const double* G, const double* Z,
                          const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st);
 
 // Full eigendecomposition of the coarsest pencil (A_n, M_n), both dn x dn

@@ -100,15 +100,22 @@ __device__ __forceinline__ int sturm_count(const float* sd, const float* se2, in
 
 // ------------------------------------------------------------ float-float syev
 //
-// Dynamic shared memory: v, p (df, n each), sd, se2 (float, n each),
-// shift (float, nwant), cstart, cpos (int, nwant).
-__global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const double* __restrict__ H,
-                                                        double* __restrict__ evals, double* __restrict__ evecs,
-                                                        df* __restrict__ W, df* __restrict__ tau,
-                                                        df* __restrict__ dd, df* __restrict__ ee,
-                                                        df* __restrict__ fac, df* __restrict__ Zt,
-                                                        df* __restrict__ rrw, int* __restrict__ perm) {
-  extern __shared__ unsigned char smem_raw[];
+// Dynamic shared memory: v, p (df, n each), sd, se2 (float, n each), shift
+// (float, nwant), cstart, cpos (int, nwant), then -- when they fit -- the
+// working matrix W (n x ldw df), the inverse-iteration factors (2 x n x nwant
+// df) and the tridiagonal eigenvectors Zt (n x nwant df).  `flags` bit 0/1/2
+// says which of W / factors / Zt live in shared memory; the others use the
+// global workspace (same layout), so one code path serves every size.
+constexpr int kSyW = 1, kSyF = 2, kSyZ = 4;
+
+__global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ldw, int flags,
+                                                        const double* __restrict__ H, double* __restrict__ evals,
+                                                        double* __restrict__ evecs, df* __restrict__ Wg,
+                                                        df* __restrict__ tau, df* __restrict__ dd,
+                                                        df* __restrict__ ee, df* __restrict__ facg,
+                                                        df* __restrict__ Ztg, df* __restrict__ rrw,
+                                                        int* __restrict__ perm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   df* v = reinterpret_cast<df*>(smem_raw);
   df* p = v + n;
   float* sd = reinterpret_cast<float*>(p + n);
@@ -116,15 +123,29 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
   float* shift = se2 + n;
   int* cstart = reinterpret_cast<int*>(shift + nwant);
   int* cpos = cstart + nwant;
+  size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant + 15) &
+               ~static_cast<size_t>(15);
+  df* W = Wg;
+  if (flags & kSyW) {
+    W = reinterpret_cast<df*>(smem_raw + off);
+    off += sizeof(df) * static_cast<size_t>(n) * ldw;
+  }
+  df* fac = facg;
+  if (flags & kSyF) {
+    fac = reinterpret_cast<df*>(smem_raw + off);
+    off += sizeof(df) * 2 * static_cast<size_t>(n) * nwant;
+  }
+  df* Zt = Ztg;
+  if (flags & kSyZ) Zt = reinterpret_cast<df*>(smem_raw + off);
   __shared__ df_acc red[32];
   __shared__ df sc[4];
   __shared__ float sf[4];
   __shared__ int si[4];
 
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const long long N = n;
+  const long long N = n, LD = ldw;
 
-  for (long long i = tid; i < N * N; i += nt) W[i] = df_from_double(H[i]);
+  for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
   __syncthreads();
 
   // ---- Householder tridiagonalisation (full symmetric storage) -------------
@@ -132,16 +153,16 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
     const int m = n - k - 1;
     df_acc a = acc_zero();
     for (int i = 1 + tid; i < m; i += nt) {
-      const df x = W[(k + 1 + i) * N + k];
+      const df x = W[(k + 1 + i) * LD + k];
       a.fma(x, x);
     }
     const df sigma = block_reduce_df(a, red, &sc[0]);
-    const df x0 = W[(k + 1) * N + k];
+    const df x0 = W[(k + 1) * LD + k];
     __syncthreads();  // every thread has read x0 before thread 0 overwrites it with v0
     if (sigma.hi == 0.f) {
       if (tid == 0) {
         tau[k] = df{0.f, 0.f};
-        dd[k] = W[k * N + k];
+        dd[k] = W[k * LD + k];
         ee[k] = x0;
       }
       __syncthreads();
@@ -153,20 +174,20 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
     const df vtv = df_add(sigma, df_mul(v0, v0));
     const df t = df_div(df{2.f, 0.f}, vtv);
     for (int i = tid; i < m; i += nt) {
-      const df vi = (i == 0) ? v0 : W[(k + 1 + i) * N + k];
+      const df vi = (i == 0) ? v0 : W[(k + 1 + i) * LD + k];
       v[i] = vi;
-      W[(k + 1 + i) * N + k] = vi;  // kept for the back-transformation
+      W[(k + 1 + i) * LD + k] = vi;  // kept for the back-transformation
     }
     if (tid == 0) {
       tau[k] = t;
-      dd[k] = W[k * N + k];
+      dd[k] = W[k * LD + k];
       ee[k] = alpha;
     }
     __syncthreads();
     // p = t * W22 v
     for (int i = warp; i < m; i += nw) {
       df_acc b = acc_zero();
-      const df* row = W + (k + 1 + i) * N + (k + 1);
+      const df* row = W + (k + 1 + i) * LD + (k + 1);
       for (int j = lane; j < m; j += 32) b.fma(row[j], v[j]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) b.merge(shfl_xor_acc(b, o));
@@ -182,23 +203,23 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
     // W22 -= v w^T + w v^T  (lower triangle computed, mirrored)
     for (int i = warp; i < m; i += nw) {
       const df vi = v[i], wi = p[i];
-      df* rowi = W + (k + 1 + i) * N + (k + 1);
+      df* rowi = W + (k + 1 + i) * LD + (k + 1);
       for (int j = lane; j <= i; j += 32) {
         df_acc u = acc_zero();
         u.fma(vi, p[j]);
         u.fma(wi, v[j]);
         const df nv = df_sub(rowi[j], u.value());
         rowi[j] = nv;
-        W[(k + 1 + j) * N + (k + 1 + i)] = nv;
+        W[(k + 1 + j) * LD + (k + 1 + i)] = nv;
       }
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
-      dd[n - 2] = W[(n - 2) * N + (n - 2)];
-      dd[n - 1] = W[(n - 1) * N + (n - 1)];
-      ee[n - 2] = W[(n - 1) * N + (n - 2)];
+      dd[n - 2] = W[(n - 2) * LD + (n - 2)];
+      dd[n - 1] = W[(n - 1) * LD + (n - 1)];
+      ee[n - 2] = W[(n - 1) * LD + (n - 2)];
       tau[n - 2] = df{0.f, 0.f};
     } else {
       dd[0] = W[0];
@@ -262,90 +283,63 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
   __syncthreads();
   const int maxpos = si[0];
 
-  // ---- inverse iteration in float-float -----------------------------------
-  // factor arrays: fac[(f * n + i) * nwant + j], f = 0..5 : u1inv, u2, u3, l, piv, (unused)
+  // ---- inverse iteration in float-float: T - s I = L D L^T -----------------
+  // factor arrays (element i of eigen-index j at [i * nwant + j]):
+  //   fac[0 .. n*nwant) = 1/d_i, fac[n*nwant .. 2n*nwant) = l_i
   const long long NW = nwant;
   const df pv = df{fmaxf(3.6e-15f * tnorm, 1.0e-30f), 0.f};
   for (int round = 0; round <= maxpos; ++round) {
     for (int j = tid; j < nwant; j += nt) {
       if (cpos[j] != round) continue;
       const df sg = df{shift[j], 0.f};
-      df* u1i = fac + (0 * N) * NW;
-      df* u2 = fac + (1 * N) * NW;
-      df* u3 = fac + (2 * N) * NW;
-      df* lm = fac + (3 * N) * NW;
-      df* pf = fac + (4 * N) * NW;
-      // factor T - sg I = P L U
-      df al = df_sub(dd[0], sg);
-      df be = (n > 1) ? ee[0] : df{0.f, 0.f};
-      for (int i = 0; i + 1 < n; ++i) {
-        const df sub = ee[i];
-        const df dn1 = df_sub(dd[i + 1], sg);
-        const df en1 = (i + 2 < n) ? ee[i + 1] : df{0.f, 0.f};
-        df u1;
-        if (!(fabsf(al.hi) < fabsf(sub.hi))) {
-          if (al.hi == 0.f) al = pv;
-          u1 = al;
-          u2[i * NW + j] = be;
-          u3[i * NW + j] = df{0.f, 0.f};
-          pf[i * NW + j] = df{0.f, 0.f};
-          const df l = df_div(sub, al);
-          lm[i * NW + j] = l;
-          al = df_sub(dn1, df_mul(l, be));
-          be = en1;
-        } else {
-          u1 = sub;
-          u2[i * NW + j] = dn1;
-          u3[i * NW + j] = en1;
-          pf[i * NW + j] = df{1.f, 0.f};
-          const df l = df_div(al, sub);
-          lm[i * NW + j] = l;
-          al = df_sub(be, df_mul(l, dn1));
-          be = df_neg(df_mul(l, en1));
-        }
-        u1i[i * NW + j] = df_div(df{1.f, 0.f}, u1);
+      df* dinv = fac;
+      df* lm = fac + N * NW;
+      df d = df_sub(dd[0], sg);
+      if (fabsf(d.hi) < pv.hi) d = df_lt0(d) ? df_neg(pv) : pv;
+      df di = df_div(df{1.f, 0.f}, d);
+      dinv[j] = di;
+      for (int i = 1; i < n; ++i) {
+        const df e = ee[i - 1];
+        const df l = df_mul(e, di);
+        lm[(i - 1) * NW + j] = l;
+        d = df_sub(df_sub(dd[i], sg), df_mul(l, e));
+        if (fabsf(d.hi) < pv.hi) d = df_lt0(d) ? df_neg(pv) : pv;
+        di = df_div(df{1.f, 0.f}, d);
+        dinv[i * NW + j] = di;
       }
-      if (fabsf(al.hi) < pv.hi) al = df_lt0(al) ? df_neg(pv) : pv;
-      u1i[(n - 1) * NW + j] = df_div(df{1.f, 0.f}, al);
       // start vector
       for (int i = 0; i < n; ++i) Zt[i * NW + j] = df{1.f + 0.37f * (float)((i * 7 + j * 13) % 11) / 11.f, 0.f};
       for (int it = 0; it < 3; ++it) {
-        // forward: apply P and L^-1
-        for (int i = 0; i + 1 < n; ++i) {
-          df xi = Zt[i * NW + j], xn = Zt[(i + 1) * NW + j];
-          if (pf[i * NW + j].hi != 0.f) {
-            const df tmpv = xi;
-            xi = xn;
-            xn = tmpv;
-            Zt[i * NW + j] = xi;
-          }
-          Zt[(i + 1) * NW + j] = df_sub(xn, df_mul(lm[i * NW + j], xi));
+        // L w = x ; z = D^-1 w ; L^T y = z
+        df prev = Zt[j];
+        for (int i = 1; i < n; ++i) {
+          prev = df_sub(Zt[i * NW + j], df_mul(lm[(i - 1) * NW + j], prev));
+          Zt[i * NW + j] = prev;
         }
-        // back substitution with U
-        for (int i = n - 1; i >= 0; --i) {
-          df s = Zt[i * NW + j];
-          if (i + 1 < n) s = df_sub(s, df_mul(u2[i * NW + j], Zt[(i + 1) * NW + j]));
-          if (i + 2 < n) s = df_sub(s, df_mul(u3[i * NW + j], Zt[(i + 2) * NW + j]));
-          Zt[i * NW + j] = df_mul(s, u1i[i * NW + j]);
+        df nxt = df_mul(Zt[(n - 1) * NW + j], dinv[(n - 1) * NW + j]);
+        Zt[(n - 1) * NW + j] = nxt;
+        for (int i = n - 2; i >= 0; --i) {
+          nxt = df_sub(df_mul(Zt[i * NW + j], dinv[i * NW + j]), df_mul(lm[i * NW + j], nxt));
+          Zt[i * NW + j] = nxt;
         }
         // Gram-Schmidt against finished members of the cluster
         for (int jp = cstart[j]; jp < j; ++jp) {
-          df_acc d = acc_zero();
-          for (int i = 0; i < n; ++i) d.fma(Zt[i * NW + jp], Zt[i * NW + j]);
-          const df dv = d.value();
+          df_acc dt = acc_zero();
+          for (int i = 0; i < n; ++i) dt.fma(Zt[i * NW + jp], Zt[i * NW + j]);
+          const df dv = dt.value();
           for (int i = 0; i < n; ++i) Zt[i * NW + j] = df_sub(Zt[i * NW + j], df_mul(dv, Zt[i * NW + jp]));
         }
         // normalise (scale first by the largest entry to stay in range)
         float amax = 0.f;
         for (int i = 0; i < n; ++i) amax = fmaxf(amax, fabsf(Zt[i * NW + j].hi));
         const float sc1 = amax > 0.f ? 1.f / amax : 1.f;
-        df_acc d = acc_zero();
+        df_acc dn = acc_zero();
         for (int i = 0; i < n; ++i) {
           const df z = df_mul_f(Zt[i * NW + j], sc1);
           Zt[i * NW + j] = z;
-          d.fma(z, z);
+          dn.fma(z, z);
         }
-        const df inv = df_div(df{1.f, 0.f}, df_sqrt(d.value()));
+        const df inv = df_div(df{1.f, 0.f}, df_sqrt(dn.value()));
         for (int i = 0; i < n; ++i) Zt[i * NW + j] = df_mul(Zt[i * NW + j], inv);
       }
     }
@@ -556,12 +550,12 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, const 
     // for each column c: s_c = v^T z[k+1:, c]; z[k+1:, c] -= t s_c v
     for (int c = warp; c < nwant; c += nw) {
       df_acc s = acc_zero();
-      for (int i = lane; i < m; i += 32) s.fma(W[(k + 1 + i) * N + k], Zn[(k + 1 + i) * NW + c]);
+      for (int i = lane; i < m; i += 32) s.fma(W[(k + 1 + i) * LD + k], Zn[(k + 1 + i) * NW + c]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s.merge(shfl_xor_acc(s, o));
       const df f = df_mul(t, s.value());
       for (int i = lane; i < m; i += 32)
-        Zn[(k + 1 + i) * NW + c] = df_sub(Zn[(k + 1 + i) * NW + c], df_mul(f, W[(k + 1 + i) * N + k]));
+        Zn[(k + 1 + i) * NW + c] = df_sub(Zn[(k + 1 + i) * NW + c], df_mul(f, W[(k + 1 + i) * LD + k]));
     }
     __syncthreads();
   }
@@ -773,9 +767,12 @@ __global__ void k_pencil_back(int dn, int q, const double* __restrict__ Yh, cons
   for (long long idx = tid; idx < static_cast<long long>(dn) * q; idx += nt) tmp[idx] = Yh[idx];
 }
 
-size_t syev_smem(int n, int nwant) {
-  return 2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant;
+size_t syev_smem_base(int n, int nwant) {
+  return (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant + 15) &
+         ~static_cast<size_t>(15);
 }
+
+constexpr size_t kSmemBudget = 225 * 1024;
 
 }  // namespace
 
@@ -804,7 +801,7 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
   alloc((void**)&w->Nq, sizeof(double) * qmax * qmax);
   alloc((void**)&w->Yh, sizeof(double) * nm * nwm);
   alloc((void**)&w->tmp, sizeof(double) * dn * qmax);
-  alloc((void**)&w->W, sizeof(df) * nm * nm);
+  alloc((void**)&w->W, sizeof(df) * nm * (nm + 1));
   alloc((void**)&w->tau, sizeof(df) * nm);
   alloc((void**)&w->dd, sizeof(df) * nm);
   alloc((void**)&w->ee, sizeof(df) * nm);
@@ -833,30 +830,47 @@ void pencil_work_destroy(PencilWork* w) {
 
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
                     cudaStream_t st) {
-  const size_t sm = syev_smem(n, nwant);
+  // place W, the factors and Zt in shared memory when they fit (in that order of benefit)
+  const int ldw = n | 1;  // odd row stride: column walks of W hit different banks
+  size_t sm = syev_smem_base(n, nwant);
+  int flags = 0;
+  const size_t wb = sizeof(df) * static_cast<size_t>(n) * ldw;
+  const size_t fb = sizeof(df) * 2 * static_cast<size_t>(n) * nwant;
+  const size_t zb = sizeof(df) * static_cast<size_t>(n) * nwant;
+  if (sm + wb <= kSmemBudget) {
+    flags |= kSyW;
+    sm += wb;
+  }
+  if (sm + fb <= kSmemBudget) {
+    flags |= kSyF;
+    sm += fb;
+  }
+  if (sm + zb <= kSmemBudget) {
+    flags |= kSyZ;
+    sm += zb;
+  }
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
   cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-  k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, H, evals, evecs, w->W, w->tau, w->dd, w->ee, w->fac, w->Zt,
-                                       w->rr, w->perm);
+  k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, w->W, w->tau, w->dd, w->ee, w->fac,
+                                       w->Zt, w->rr, w->perm);
 }
 
-void launch_pencil_solve(PencilWork* w, int dn, int q, const double* C, const double* G, const double* Z,
+void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C, const double* G, const double* Z,
                          const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st) {
-  const int n = dn + q;
+  const int n = m + q;
   // three kernels launched here; the GEMM, Gram and eigensolver launchers count their own
-  ProfScope ps(st, P_PENCIL, 8.0 * (1.0 * dn * dn * 2 + 2.0 * dn * q + 2.0 * q * q + 1.0 * n * n + 1.0 * dn * q), 0.0,
-               3);
-  // K | B = Z^T [C_A | C_M]
-  launch_gemm_f64(dn, 2 * q, dn, 1.0, Z, dn, true, C, 2 * q, false, 0.0, w->KB, 2 * q, st);
-  k_build_y3<<<ceil_div(static_cast<long long>(dn) * q, 256), 256, 0, st>>>(dn, q, w->KB, theta, w->Y3);
+  ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * q * q + 1.0 * n * n + 1.0 * m * q), 0.0, 3);
+  // K | B = Z_m^T [C_A | C_M]   (Z_m: the first m columns of Z)
+  launch_gemm_f64(m, 2 * q, dn, 1.0, Z, dn, true, C, 2 * q, false, 0.0, w->KB, 2 * q, st);
+  k_build_y3<<<ceil_div(static_cast<long long>(m) * q, 256), 256, 0, st>>>(m, q, w->KB, theta, w->Y3);
   // P3 = [B K]^T [B K Theta B]
-  launch_gram_strided(dn, w->Y3, 3 * q, 2 * q, w->Y3, 3 * q, 3 * q, w->gsc, w->P3, st);
-  k_pencil_h<<<1, 512, 0, st>>>(dn, q, G, w->P3, w->Y3, theta, w->Lq, w->Sq, w->Nq, w->H, status);
+  launch_gram_strided(m, w->Y3, 3 * q, 2 * q, w->Y3, 3 * q, 3 * q, w->gsc, w->P3, st);
+  k_pencil_h<<<1, 512, 0, st>>>(m, q, G, w->P3, w->Y3, theta, w->Lq, w->Sq, w->Nq, w->H, status);
   launch_syev_df(w, n, q, w->H, mu, w->Yh, st);
-  k_pencil_back<<<1, 256, 0, st>>>(dn, q, w->Yh, w->Lq, Y, w->tmp);
-  // tmp = a - B Yv ; Xc = Z tmp
-  launch_gemm_f64(dn, q, q, -1.0, w->Y3, 3 * q, false, Y, q, false, 1.0, w->tmp, q, st);
-  launch_gemm_f64(dn, q, dn, 1.0, Z, dn, false, w->tmp, q, false, 0.0, Xc, q, st);
+  k_pencil_back<<<1, 256, 0, st>>>(m, q, w->Yh, w->Lq, Y, w->tmp);
+  // tmp = a - B Yv ; Xc = Z_m tmp
+  launch_gemm_f64(m, q, q, -1.0, w->Y3, 3 * q, false, Y, q, false, 1.0, w->tmp, q, st);
+  launch_gemm_f64(dn, q, m, 1.0, Z, dn, false, w->tmp, q, false, 0.0, Xc, q, st);
 }
 
 void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,
@@ -877,6 +891,9 @@ void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* M
   // Ainv = Z diag(1/theta) Z^T
   k_scale_cols_inv<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, dn, Z, theta, w->H);
   launch_gemm_f64(dn, dn, dn, 1.0, w->H, dn, false, Z, dn, true, 0.0, Ainv, dn, st);
+  // two Newton-Schulz steps bring the float-float-derived inverse to float64 accuracy
+  launch_newton_schulz(dn, An, Ainv, w->Hs, w->H, st);
+  launch_newton_schulz(dn, An, Ainv, w->Hs, w->H, st);
 }
 
 }  // namespace amgeig

@@ -74,7 +74,7 @@ def test_vcycle_matches_oracle(kind, size, cap, width):
 
 
 CASES = [("square", 32, 50, 1, 4, 2), ("lshape", 16, 60, 2, 6, 2), ("checker", 32, 60, 3, 5, 2),
-         ("cube", 8, 40, 4, 4, 2), ("square", 48, 120, 5, 20, 3)]
+         ("cube", 8, 40, 4, 4, 2), ("square", 48, 120, 5, 20, 4)]
 
 
 @pytest.mark.parametrize("kind,size,cap,seed,q,qe", CASES)
@@ -97,12 +97,14 @@ def test_iteration_level_parity(kind, size, cap, seed, q, qe, L):
 def test_converged_solve(kind, size, cap, seed, q, qe):
     p, blob, _ = problem_and_blob(kind, size, cap, seed)
     oh = O.read_blob(blob)
-    tol = 2e-9 if kind == "checker" else 1e-10
+    # relative-residual floor: ~1e-10 for the coefficient jump; the q = 20 case converges
+    # its last pair more slowly (tighter tolerances need many more corrections)
+    tol = 2e-9 if kind == "checker" else (1e-9 if q >= 20 else 1e-10)
     lam_ex, U_ex = dense_pairs(p, q)
     rtol = eig_rel_tol(lam_ex, lam_max(p))
     with ae.Hierarchy(blob) as h:
         for prec in (ae.AMGEIG_FP64, ae.AMGEIG_MIXED_FP32):
-            lam, U, info, code = h.solve(q, tol=tol, opt=ae.options(q_extra=qe, max_corrections=100, precision=prec))
+            lam, U, info, code = h.solve(q, tol=tol, opt=ae.options(q_extra=qe, max_corrections=150, precision=prec))
             assert code == ae.AMGEIG_OK and info.converged == 1
             assert np.all(np.abs(lam - lam_ex) <= rtol * lam_ex), np.max(np.abs(lam - lam_ex) / lam_ex)
             assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
@@ -191,5 +193,17 @@ def test_multiple_vcycles_match_oracle():
     with ae.Hierarchy(blob) as h:
         lam, U, info, _ = h.solve(4, tol=0.0, opt=ae.options(q_extra=1, fixed_corrections=2, v_cycles=2,
                                                              pre_sweeps=2, post_sweeps=1))
+    assert np.max(np.abs(lam - lam_o) / lam_o) < 1e-10
+    assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
+
+
+@pytest.mark.parametrize("L", [1, 3])
+def test_coarse_modes_parity(L):
+    """The truncated coarse space (coarse_modes option) matches the oracle's same option."""
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    oh = O.read_blob(blob)
+    lam_o, U_o, _ = O.solve(oh, 6, tol=0.0, opts=O.Options(q_extra=2, fixed_corrections=L, coarse_modes=16))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, _ = h.solve(6, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=L, coarse_modes=16))
     assert np.max(np.abs(lam - lam_o) / lam_o) < 1e-10
     assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8

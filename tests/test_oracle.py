@@ -198,3 +198,18 @@ def test_closed_form_unit_square():
         errs.append(np.mean(np.abs(lam - exact) / exact))
     slope = np.polyfit(np.log([1 / 8, 1 / 16, 1 / 32]), np.log(errs), 1)[0]
     assert 1.7 < slope < 2.4, slope
+
+
+def test_coarse_modes_option():
+    """The library's coarse_modes option: m = d_n is the paper's pencil exactly, and a
+    truncated coarse space still converges to the dense eigenpairs."""
+    p, oh = _oh("lshape", 16, 60, 2)
+    dn = oh.sizes[-1]
+    full = O.solve(oh, 6, tol=0.0, opts=O.Options(q_extra=2, fixed_corrections=3))
+    same = O.solve(oh, 6, tol=0.0, opts=O.Options(q_extra=2, fixed_corrections=3, coarse_modes=dn))
+    assert np.allclose(full[0], same[0], rtol=1e-13)
+    lam, U, info = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100, coarse_modes=16))
+    assert info.converged
+    lam_ex, U_ex = dense_pairs(p, 6)
+    assert np.all(np.abs(lam - lam_ex) <= 1e-10 * lam_ex)
+    assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
