@@ -473,7 +473,7 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
   launch_gram(Nk, w->V, q, w->W, 2 * q, w->gsc, w->G, st);
   const double* cur = w->W;
   for (int l = k; l < n - 1; ++l) {
-    launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st);
+    launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st, P_CHAIN);
     cur = w->WC[l + 1];
   }
   CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
@@ -482,7 +482,7 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
   // recombination: U = I_n^k Xc + V Y
   const double* px = w->Xc;
   for (int l = n - 2; l >= k; --l) {
-    launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st);
+    launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st, P_CHAIN);
     px = w->PX[l];
   }
   launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st);
@@ -546,7 +546,7 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   relres_host.assign(qt, 0.0);
   // step 2: k = n1-1 .. 1 (0-based n-2 .. 1) one correction each, then the finest level
   for (int k = n - 2; k >= 0; --k) {
-    launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st);
+    launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st, P_CHAIN);
     std::swap(w->U, w->Ualt);
     if (k >= 1) {
       rc = defect(h, w, k, o, false, st);

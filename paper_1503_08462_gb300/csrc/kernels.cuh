@@ -30,7 +30,8 @@ void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double
                           double* partials, int* nblocks_out, cudaStream_t st);
 
 // Y = S X (accumulate = false) or Y += S X (accumulate = true)
-void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st);
+void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st,
+                     int cls = 2);
 void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st);
 
 // first l1-Jacobi sweep from x = 0 fused with the residual:

@@ -41,7 +41,7 @@ Profiler& prof() {
 }
 
 const char* kNames[P_COUNT] = {"defect", "smooth", "transfer", "coarse_solve", "augment",
-                               "gram", "pencil", "recombine", "other"};
+                               "gram", "pencil", "recombine", "other", "chain"};
 
 }  // namespace
 

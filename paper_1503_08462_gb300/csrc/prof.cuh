@@ -22,6 +22,7 @@ enum ProfClass {
   P_PENCIL,       // reduced pencil and its float-float eigensolve
   P_RECOMBINE,    // I_n^k Xc + V Y
   P_OTHER,        // copies, conversions, sign normalisation
+  P_CHAIN,        // float64 transfer chains: I_k^n [AV | MV], I_n^k Xc, nested prolongation
   P_COUNT
 };
 

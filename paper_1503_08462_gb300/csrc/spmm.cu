@@ -168,12 +168,13 @@ __global__ void __launch_bounds__(kThreads) k_spmm(int n, const int* __restrict_
 }
 
 template <typename T>
-void spmm_impl(const DevCsr& S, const T* vals, const T* X, int width, T* Y, bool accumulate, cudaStream_t st) {
+void spmm_impl(const DevCsr& S, const T* vals, const T* X, int width, T* Y, bool accumulate, cudaStream_t st,
+               int cls = P_TRANSFER) {
   if (S.rows == 0 || width == 0) return;
   Geo g = geo_for(width);
   const int blocks = ceil_div(S.rows, g.rows_per_block);
   const double t = sizeof(T);
-  ProfScope ps(st, P_TRANSFER,
+  ProfScope ps(st, cls,
                4.0 * (S.rows + 1) + (4.0 + t) * S.nnz + t * S.cols * width + t * S.rows * width * (accumulate ? 2 : 1),
                2.0 * S.nnz * width);
   switch (g.cpt) {
@@ -394,8 +395,9 @@ void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double
   defect_impl<float>(AM, U, q, lam, R, partials, nblocks_out, st);
 }
 
-void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st) {
-  spmm_impl<double>(S, S.v64, X, width, Y, accumulate, st);
+void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st,
+                     int cls) {
+  spmm_impl<double>(S, S.v64, X, width, Y, accumulate, st, cls);
 }
 void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st) {
   spmm_impl<float>(S, S.v32, X, width, Y, accumulate, st);
