@@ -156,6 +156,27 @@ int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals
 int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* b,
                         double* x);
 
+/* Allocation-free form of amgeig_sym_eigh, for callers that cannot allocate
+ * device memory when they need it (work inside a foreign memory pool, code that
+ * must not synchronise the device as cudaFree does, hosts whose allocator
+ * belongs to another runtime).  The paper has no counterpart: it treats the
+ * small eigenproblems as a black box.
+ *   n, nwant  1 <= nwant <= n, n <= 128, nwant <= 64 (EINVAL beyond).
+ *   H         device pointer, n x n row-major float64, symmetric.
+ *   evals     device pointer, nwant doubles (ascending).
+ *   evecs     device pointer, n x nwant row-major float64.
+ *   stream    cudaStream_t (NULL: the legacy default stream).
+ * The call only enqueues work on `stream` (no synchronisation, no cudaMalloc,
+ * cudaFree or allocating library call).  Its scratch is one file-scope device
+ * array of 512 KiB that every GPU loading the library holds until exit; the
+ * first call on a device looks the array's device address up with
+ * cudaGetSymbolAddress, so make that first call outside any stream capture.
+ * All calls share the array and it keeps the last call's contents (the solver
+ * writes every scratch element before reading it); calls that overlap on the
+ * GPU race on it and must be serialised by the caller.
+ * Errors: EINVAL, ECUDA. */
+int amgeig_sym_eigh_noalloc(int n, int nwant, const double* H, double* evals, double* evecs, void* stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Per kernel class totals recorded while profiling is enabled. */

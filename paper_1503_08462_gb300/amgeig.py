@@ -55,7 +55,7 @@ _lib = None
 EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
             "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_profile_enable", "amgeig_profile_read",
-            "amgeig_kernel_launches"]
+            "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc"]
 
 
 def library_path() -> str:
@@ -88,6 +88,8 @@ def lib():
         L.amgeig_apply_vcycle.argtypes = [vp, i32, i32, ctypes.POINTER(amgeig_options), vp, vp]
         L.amgeig_profile_enable.argtypes = [i32]
         L.amgeig_profile_read.argtypes = [ctypes.POINTER(amgeig_prof_entry), i32, ctypes.POINTER(i32)]
+        L.amgeig_sym_eigh_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
+        L.amgeig_sym_eigh_noalloc.restype = i32
         L.amgeig_kernel_launches.argtypes = []
         L.amgeig_kernel_launches.restype = ctypes.c_uint64
         for name in ("amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
@@ -177,6 +179,14 @@ def amgeig_sym_eigh(H: np.ndarray, nwant: int, device: int = 0):
     evecs = np.empty((n, nwant))
     _check(lib().amgeig_sym_eigh(device, n, nwant, _ptr(H), _ptr(evals), _ptr(evecs)), "amgeig_sym_eigh")
     return evals, evecs
+
+
+def amgeig_sym_eigh_noalloc(H, evals, evecs, stream: Optional[int] = None) -> None:
+    """Device-pointer form without allocation: H (n x n), evals (nwant), evecs (n x nwant) CUDA float64 tensors."""
+    n = H.shape[0]
+    nwant = evals.shape[0]
+    _check(lib().amgeig_sym_eigh_noalloc(n, nwant, _ptr(H), _ptr(evals), _ptr(evecs), stream),
+           "amgeig_sym_eigh_noalloc")
 
 
 def amgeig_apply_vcycle(h, level: int, b: np.ndarray, opt: Optional[amgeig_options] = None) -> np.ndarray:

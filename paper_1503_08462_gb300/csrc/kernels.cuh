@@ -136,4 +136,10 @@ void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* M
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
                     cudaStream_t st);
 
+// The same eigensolver on caller-provided workspace (device pointers sized as in
+// pencil_work_create for nmax >= n + 1 and nwant_max >= nwant); enqueues only.
+struct df;
+void launch_syev_df_into(int n, int nwant, const double* H, double* evals, double* evecs, df* W, df* tau, df* dd,
+                         df* ee, df* fac, df* Zt, df* rr, int* perm, cudaStream_t st);
+
 }  // namespace amgeig

@@ -855,6 +855,31 @@ void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* ev
                                        w->Zt, w->rr, w->perm);
 }
 
+void launch_syev_df_into(int n, int nwant, const double* H, double* evals, double* evecs, df* W, df* tau, df* dd,
+                         df* ee, df* fac, df* Zt, df* rr, int* perm, cudaStream_t st) {
+  const int ldw = n | 1;
+  size_t sm = syev_smem_base(n, nwant);
+  int flags = 0;
+  const size_t wb = sizeof(df) * static_cast<size_t>(n) * ldw;
+  const size_t fb = sizeof(df) * 2 * static_cast<size_t>(n) * nwant;
+  const size_t zb = sizeof(df) * static_cast<size_t>(n) * nwant;
+  if (sm + wb <= kSmemBudget) {
+    flags |= kSyW;
+    sm += wb;
+  }
+  if (sm + fb <= kSmemBudget) {
+    flags |= kSyF;
+    sm += fb;
+  }
+  if (sm + zb <= kSmemBudget) {
+    flags |= kSyZ;
+    sm += zb;
+  }
+  ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
+  cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+  k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, W, tau, dd, ee, fac, Zt, rr, perm);
+}
+
 void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C, const double* G, const double* Z,
                          const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st) {
   const int n = m + q;
