@@ -249,6 +249,7 @@ namespace {
 
 struct SolveWork {
   int qt = 0;
+  int ld32 = 0;  // row stride of the float32 V-cycle blocks: qt rounded up to a multiple of 4
   int precision = -1;
   int vcycles = 1;
   DeviceBuffers mem;
@@ -266,6 +267,7 @@ struct SolveWork {
 int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, std::unique_ptr<SolveWork>& out) {
   auto w = std::make_unique<SolveWork>();
   w->qt = qt;
+  w->ld32 = (qt + 3) & ~3;
   w->precision = precision;
   w->vcycles = vcycles;
   const int n = h->nlev;
@@ -298,12 +300,12 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
         CK(m.alloc(&w->E64[l], Nl * qt));
       }
     } else {
-      CK(m.alloc(&w->B32[l], Nl * qt));
-      CK(m.alloc(&w->X32[l], Nl * qt));
-      CK(m.alloc(&w->T32[l], Nl * qt));
+      CK(m.alloc(&w->B32[l], Nl * w->ld32));
+      CK(m.alloc(&w->X32[l], Nl * w->ld32));
+      CK(m.alloc(&w->T32[l], Nl * w->ld32));
       if (vcycles > 1) {
-        CK(m.alloc(&w->D32[l], Nl * qt));
-        CK(m.alloc(&w->E32[l], Nl * qt));
+        CK(m.alloc(&w->D32[l], Nl * w->ld32));
+        CK(m.alloc(&w->E32[l], Nl * w->ld32));
       }
     }
     if (l > 0) CK(m.alloc(&w->WC[l], Nl * 2 * qt));
@@ -360,10 +362,10 @@ void residual(const DevCsr& A, const double* b, const double* x, int wdt, double
 void residual(const DevCsr& A, const float* b, const float* x, int wdt, float* r, cudaStream_t s) { launch_residual_f32(A, b, x, wdt, r, s); }
 void spmm(const DevCsr& S, const double* X, int wdt, double* Y, bool acc, cudaStream_t s) { launch_spmm_f64(S, X, wdt, Y, acc, s); }
 void spmm(const DevCsr& S, const float* X, int wdt, float* Y, bool acc, cudaStream_t s) { launch_spmm_f32(S, X, wdt, Y, acc, s); }
-void jacobi_to_v(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, const double* U, double* V, cudaStream_t s) { launch_jacobi_to_v_f64(A, d, b, x, wdt, U, V, s); }
-void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s) { launch_jacobi_to_v_f32(A, d, b, x, wdt, U, V, s); }
-void add_to_v(const double* U, const double* x, long long c, double* V, cudaStream_t s) { launch_add_to_v_f64(U, x, c, V, s); }
-void add_to_v(const double* U, const float* x, long long c, double* V, cudaStream_t s) { launch_add_to_v_f32(U, x, c, V, s); }
+void jacobi_to_v(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, const double* U, double* V, cudaStream_t s, int) { launch_jacobi_to_v_f64(A, d, b, x, wdt, U, V, s); }
+void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv) { launch_jacobi_to_v_f32(A, d, b, x, wdt, U, V, s, qv); }
+void add_to_v(const double* U, const double* x, int rows, int q, int, double* V, cudaStream_t s) { launch_add_to_v_f64(U, x, static_cast<long long>(rows) * q, V, s); }
+void add_to_v(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t s) { launch_add_to_v_f32_strided(U, x, rows, q, ldx, V, s); }
 void axpy(const double* x, long long c, double* y, cudaStream_t s) { launch_axpy_f64(x, c, y, s); }
 void axpy(const float* x, long long c, float* y, cudaStream_t s) { launch_axpy_f32(x, c, y, s); }
 const double* dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->dinv64[l]; }
@@ -377,10 +379,13 @@ void coarse_solve(amgeig_hierarchy_t* h, const float* b, int q, float* x, cudaSt
 
 // One V-cycle for A_k x = B[k] from x = 0; the result is left in X[k] unless
 // to_v, in which case the last sweep on level k writes V = U + x instead.
+int width_of(SolveWork* w, double*) { return w->qt; }
+int width_of(SolveWork* w, float*) { return w->ld32; }
+
 template <typename T>
 void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool to_v, const double* U, double* V,
             cudaStream_t st) {
-  const int q = w->qt;
+  const int q = width_of(w, static_cast<T*>(nullptr));
   const int n = h->nlev;
   auto& B = VBufs<T>::B(w);
   auto& X = VBufs<T>::X(w);
@@ -409,13 +414,13 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
     spmm(h->P[l], X[l + 1], q, X[l], true, st);
     for (int s = 0; s < post; ++s) {
       if (to_v && l == k && s == post - 1) {
-        jacobi_to_v(A, d, B[l], X[l], q, U, V, st);
+        jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt);
       } else {
         jacobi(A, d, B[l], X[l], q, Tm[l], st);
         std::swap(X[l], Tm[l]);
       }
     }
-    if (to_v && l == k && post == 0) add_to_v(U, X[l], h->sizes[l] * q, V, st);
+    if (to_v && l == k && post == 0) add_to_v(U, X[l], static_cast<int>(h->sizes[l]), w->qt, q, V, st);
   }
 }
 
@@ -433,16 +438,17 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
   auto& X = VBufs<T>::X(w);
   auto& D = VBufs<T>::D(w);
   auto& E = VBufs<T>::E(w);
-  const long long cnt = h->sizes[k] * q;
+  const int wd = width_of(w, static_cast<T*>(nullptr));
+  const long long cnt = h->sizes[k] * wd;
   cudaMemcpyAsync(D[k], B[k], sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(E[k], 0, sizeof(T) * cnt, st);
   for (int c = 0; c < o.v_cycles; ++c) {
     vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
     // E += X[k]
     axpy(X[k], cnt, E[k], st);
-    if (c + 1 < o.v_cycles) residual(h->A[k], D[k], E[k], q, B[k], st);
+    if (c + 1 < o.v_cycles) residual(h->A[k], D[k], E[k], wd, B[k], st);
   }
-  add_to_v(U, E[k], cnt, V, st);
+  add_to_v(U, E[k], static_cast<int>(h->sizes[k]), q, wd, V, st);
 }
 
 }  // namespace
@@ -470,7 +476,10 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     amg_correction<float>(h, w, k, o, w->U, w->V, st);
   // augmentation: W = [A_k V | M_k V], G = V^T W, C = I_k^n W
   launch_dual_spmm(h->A[k], w->V, q, w->W, st);
-  launch_gram(Nk, w->V, q, w->W, 2 * q, w->gsc, w->G, st);
+  // the mixed path forms the Gram blocks and the recombination in float-float
+  // (48-bit significand on the float32 pipes); the float64 path in float64
+  const bool dfa = o.precision != AMGEIG_FP64;
+  launch_gram(Nk, w->V, q, w->W, 2 * q, w->gsc, w->G, st, dfa);
   const double* cur = w->W;
   for (int l = k; l < n - 1; ++l) {
     launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st, P_CHAIN);
@@ -485,7 +494,7 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st, P_CHAIN);
     px = w->PX[l];
   }
-  launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st);
+  launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st, dfa);
   {
     ProfScope ps(st, P_OTHER, 16.0 * q, 0.0);
     k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
@@ -501,7 +510,7 @@ int defect(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, 
   if (o.precision == AMGEIG_FP64)
     launch_defect_f64(h->A[k], w->U, q, w->lam, w->B64[k], part, &nb, st);
   else
-    launch_defect_f32out(h->A[k], w->U, q, w->lam, w->B32[k], part, &nb, st);
+    launch_defect_f32out(h->A[k], w->U, q, w->lam, w->B32[k], w->ld32, part, &nb, st);
   if (norms) {
     launch_sum_partials(w->partials, nb, 2 * q, w->sums, st);
     CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
@@ -917,9 +926,9 @@ int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_o
     vcycle<double>(h, w, level, o.pre_sweeps, o.post_sweeps, false, nullptr, nullptr, st);
     CK(cudaMemcpyAsync(w->U, w->X64[level], sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
   } else {
-    launch_convert_f64_to_f32(w->V, cnt, w->B32[level], st);
+    launch_f64_to_f32_pad(w->V, static_cast<int>(h->sizes[level]), width, w->ld32, w->B32[level], st);
     vcycle<float>(h, w, level, o.pre_sweeps, o.post_sweeps, false, nullptr, nullptr, st);
-    launch_convert_f32_to_f64(w->X32[level], cnt, w->U, st);
+    launch_f32_to_f64_unpad(w->X32[level], static_cast<int>(h->sizes[level]), width, w->ld32, w->U, st);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(x, w->U, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));

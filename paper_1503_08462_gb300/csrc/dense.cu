@@ -1,6 +1,8 @@
 // Small dense kernels: GEMM on coarse-size operands, the tall-skinny Gram
 // products V^T W of Algorithm 3.1 step 2 (V^T A_k V and V^T M_k V), fixed-order
 // reductions of per-block partial sums, and the residual test.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "prof.cuh"
@@ -46,38 +48,59 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, cons
 constexpr int kGT = 32;
 constexpr int kGramRows = 32;
 
+template <bool DF>
 __global__ void __launch_bounds__(256) k_gram_partial(int rows, const double* __restrict__ V, int ldv, int q,
                                                       const double* __restrict__ W, int ldw, int w, int chunk_rows,
                                                       int tiles_w, double* __restrict__ part) {
-  __shared__ double Vs[kGramRows][kGT + 1];
-  __shared__ double Ws[kGramRows][kGT + 1];
+  // float64 operands; DF = true stages them as float-float pairs and accumulates
+  // the products on the float32 pipes with compensated (two-sum) accumulation
+  using Stage = typename std::conditional<DF, df, double>::type;
+  __shared__ Stage Vs[kGramRows][kGT + 1];
+  __shared__ Stage Ws[kGramRows][kGT + 1];
   const int chunk = blockIdx.x;
   const int ta = blockIdx.y / tiles_w, tb = blockIdx.y % tiles_w;
   const int a0 = ta * kGT, b0 = tb * kGT;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // ty in 0..7
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  df_acc facc[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) facc[s] = acc_zero();
   const int r0 = chunk * chunk_rows;
   const int r1 = min(rows, r0 + chunk_rows);
   for (int rb = r0; rb < r1; rb += kGramRows) {
     for (int idx = threadIdx.x; idx < kGramRows * kGT; idx += blockDim.x) {
       const int rr = idx / kGT, cc = idx % kGT;
       const int r = rb + rr;
-      Vs[rr][cc] = (r < r1 && a0 + cc < q) ? V[static_cast<long long>(r) * ldv + a0 + cc] : 0.0;
-      Ws[rr][cc] = (r < r1 && b0 + cc < w) ? W[static_cast<long long>(r) * ldw + b0 + cc] : 0.0;
+      const double vv = (r < r1 && a0 + cc < q) ? V[static_cast<long long>(r) * ldv + a0 + cc] : 0.0;
+      const double ww = (r < r1 && b0 + cc < w) ? W[static_cast<long long>(r) * ldw + b0 + cc] : 0.0;
+      if constexpr (DF) {
+        Vs[rr][cc] = df_from_double(vv);
+        Ws[rr][cc] = df_from_double(ww);
+      } else {
+        Vs[rr][cc] = vv;
+        Ws[rr][cc] = ww;
+      }
     }
     __syncthreads();
     const int nr = min(kGramRows, r1 - rb);
     for (int rr = 0; rr < nr; ++rr) {
-      const double wv = Ws[rr][tx];
+      const Stage wv = Ws[rr][tx];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) acc[s] = fma(Vs[rr][ty * 4 + s], wv, acc[s]);
+      for (int s = 0; s < 4; ++s) {
+        if constexpr (DF)
+          facc[s].fma(Vs[rr][ty * 4 + s], wv);
+        else
+          acc[s] = fma(Vs[rr][ty * 4 + s], wv, acc[s]);
+      }
     }
     __syncthreads();
   }
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int a = a0 + ty * 4 + s, b = b0 + tx;
-    if (a < q && b < w) part[(static_cast<long long>(chunk) * q + a) * w + b] = acc[s];
+    double val = acc[s];
+    if constexpr (DF) val = df_to_double(facc[s].value());
+    if (a < q && b < w) part[(static_cast<long long>(chunk) * q + a) * w + b] = val;
   }
 }
 
@@ -168,20 +191,23 @@ size_t gram_scratch_doubles(int rows, int q, int w) {
 }
 
 void launch_gram_strided(int rows, const double* V, int ldv, int q, const double* W, int ldw, int w, double* scratch,
-                         double* G, cudaStream_t st) {
+                         double* G, cudaStream_t st, bool df_arith) {
   if (q <= 0 || w <= 0) return;
   int cr;
   const int chunks = gram_chunks(rows, q, w, &cr);
   const int tiles_w = ceil_div(w, kGT);
   dim3 grid(chunks, ceil_div(q, kGT) * tiles_w);
   ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks * q * w, 2.0 * rows * q * w);
-  k_gram_partial<<<grid, 256, 0, st>>>(rows, V, ldv, q, W, ldw, w, cr, tiles_w, scratch);
+  if (df_arith)
+    k_gram_partial<true><<<grid, 256, 0, st>>>(rows, V, ldv, q, W, ldw, w, cr, tiles_w, scratch);
+  else
+    k_gram_partial<false><<<grid, 256, 0, st>>>(rows, V, ldv, q, W, ldw, w, cr, tiles_w, scratch);
   launch_sum_partials(scratch, chunks, q * w, G, st);
 }
 
 void launch_gram(int rows, const double* V, int q, const double* W, int w, double* scratch, double* G,
-                 cudaStream_t st) {
-  launch_gram_strided(rows, V, q, q, W, w, w, scratch, G, st);
+                 cudaStream_t st, bool df_arith) {
+  launch_gram_strided(rows, V, q, q, W, w, w, scratch, G, st, df_arith);
 }
 
 void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st) {

@@ -26,7 +26,8 @@ struct DevCsr {
 // per-column sums of R_ij^2 and (MU)_ij^2 to partials[block][2q] (fixed order).
 void launch_defect_f64(const DevCsr& AM, const double* U, int q, const double* lam, double* R,
                        double* partials, int* nblocks_out, cudaStream_t st);
-void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double* lam, float* R,
+// float32 output with row stride ldr >= q; columns q..ldr-1 are written as zero
+void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double* lam, float* R, int ldr,
                           double* partials, int* nblocks_out, cudaStream_t st);
 
 // Y = S X (accumulate = false) or Y += S X (accumulate = true)
@@ -51,18 +52,25 @@ void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int wi
 // last sweep on the working level fused with V = U + x_new (float64 output)
 void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
                             const double* U, double* V, cudaStream_t st);
+// float32 variant: b and x have row stride `width` (a multiple of 4 when padded),
+// U and V have row stride qv <= width
 void launch_jacobi_to_v_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                            const double* U, double* V, cudaStream_t st);
+                            const double* U, double* V, cudaStream_t st, int qv);
 // V = U + x (used when there are no post-smoothing sweeps)
 void launch_add_to_v_f64(const double* U, const double* x, long long count, double* V, cudaStream_t st);
 void launch_add_to_v_f32(const double* U, const float* x, long long count, double* V, cudaStream_t st);
+// V = U + x with x of row stride ldx >= q (rows x q)
+void launch_add_to_v_f32_strided(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t st);
+// padded float32 copies: dst (rows x ld) = src (rows x q), zero padding; and back
+void launch_f64_to_f32_pad(const double* src, int rows, int q, int ld, float* dst, cudaStream_t st);
+void launch_f32_to_f64_unpad(const float* src, int rows, int q, int ld, double* dst, cudaStream_t st);
 
 // W = [A V | M V]  ([rows][2q])
 void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaStream_t st);
 
-// U = Xp + V Y   (Y: q x q row-major)
+// U = Xp + V Y   (Y: q x q row-major); df_arith as for the Gram
 void launch_recombine(int rows, const double* Xp, const double* V, const double* Y, int q, double* U,
-                      cudaStream_t st);
+                      cudaStream_t st, bool df_arith = false);
 
 // y += x
 void launch_axpy_f64(const double* x, long long count, double* y, cudaStream_t st);
@@ -85,11 +93,13 @@ void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, 
 // Gram G = V^T W  (V: rows x q, W: rows x w) -> G: q x w, via per-chunk partials
 // in `scratch` (size gram_scratch_doubles(rows, q, w)) and a fixed-order sum.
 size_t gram_scratch_doubles(int rows, int q, int w);
+// df_arith: products and sums in float-float on the float32 pipes (48-bit
+// significand, compensated accumulation) instead of float64 FMA.
 void launch_gram(int rows, const double* V, int q, const double* W, int w, double* scratch, double* G,
-                 cudaStream_t st);
+                 cudaStream_t st, bool df_arith = false);
 // same with explicit row strides ldv >= q and ldw >= w
 void launch_gram_strided(int rows, const double* V, int ldv, int q, const double* W, int ldw, int w, double* scratch,
-                         double* G, cudaStream_t st);
+                         double* G, cudaStream_t st, bool df_arith = false);
 
 // One Newton-Schulz step X <- X (2I - A X) (n x n row-major; T, Y scratch)
 void launch_newton_schulz(int n, const double* A, double* X, double* T, double* Y, cudaStream_t st);

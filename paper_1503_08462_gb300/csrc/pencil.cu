@@ -70,23 +70,6 @@ namespace {
 
 // ------------------------------------------------------------ block helpers
 
-__device__ df block_reduce_df(df_acc a, df_acc* red, df* out) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) a.merge(shfl_xor_acc(a, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    df_acc b = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : acc_zero();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) b.merge(shfl_xor_acc(b, o));
-    if (threadIdx.x == 0) *out = b.value();
-  }
-  __syncthreads();
-  df r = *out;
-  __syncthreads();
-  return r;
-}
-
 __device__ __forceinline__ int sturm_count(const float* sd, const float* se2, int n, float x, float pivmin) {
   float qv = sd[0] - x;
   int cnt = qv < 0.f;
@@ -101,7 +84,8 @@ __device__ __forceinline__ int sturm_count(const float* sd, const float* se2, in
 // ------------------------------------------------------------ float-float syev
 //
 // Dynamic shared memory: v, p (df, n each), sd, se2 (float, n each), shift
-// (float, nwant), cstart, cpos (int, nwant), then -- when they fit -- the
+// (float, nwant), cstart, cpos (int, nwant), d, e, tau (df, n each), then --
+// when they fit -- the
 // working matrix W (n x ldw df), the inverse-iteration factors (2 x n x nwant
 // df) and the tridiagonal eigenvectors Zt (n x nwant df).  `flags` bit 0/1/2
 // says which of W / factors / Zt live in shared memory; the others use the
@@ -111,8 +95,8 @@ constexpr int kSyW = 1, kSyF = 2, kSyZ = 4;
 __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ldw, int flags,
                                                         const double* __restrict__ H, double* __restrict__ evals,
                                                         double* __restrict__ evecs, df* __restrict__ Wg,
-                                                        df* __restrict__ tau, df* __restrict__ dd,
-                                                        df* __restrict__ ee, df* __restrict__ facg,
+                                                        df* __restrict__ tau_g, df* __restrict__ dd_g,
+                                                        df* __restrict__ ee_g, df* __restrict__ facg,
                                                         df* __restrict__ Ztg, df* __restrict__ rrw,
                                                         int* __restrict__ perm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -123,7 +107,8 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   float* shift = se2 + n;
   int* cstart = reinterpret_cast<int*>(shift + nwant);
   int* cpos = cstart + nwant;
-  size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant + 15) &
+  size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
+                3 * sizeof(df) * n + 15) &
                ~static_cast<size_t>(15);
   df* W = Wg;
   if (flags & kSyW) {
@@ -138,33 +123,49 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   df* Zt = Ztg;
   if (flags & kSyZ) Zt = reinterpret_cast<df*>(smem_raw + off);
   __shared__ df_acc red[32];
-  __shared__ df sc[4];
   __shared__ float sf[4];
   __shared__ int si[4];
 
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const long long N = n, LD = ldw;
+  // the tridiagonal (d, e) and the Householder scalars live in shared memory
+  df* dd = reinterpret_cast<df*>(cpos + nwant);
+  df* ee = dd + n;
+  df* tau = ee + n;
+  __shared__ df_acc red_sig[32], red_vp[32];
 
   for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
   __syncthreads();
+  // sigma partials of column 0 (rows 2..n-1)
+  {
+    df_acc a = acc_zero();
+    for (int i = 2 + warp; i < n; i += nw)
+      if (lane == 0) a.fma(W[i * LD], W[i * LD]);
+    if (lane == 0) red_sig[warp] = a;
+  }
+  __syncthreads();
 
   // ---- Householder tridiagonalisation (full symmetric storage) -------------
+  // Four barriers per step: the norm of the next column and v^T p are formed
+  // from per-warp partial sums written in the preceding phase.
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
-    df_acc a = acc_zero();
-    for (int i = 1 + tid; i < m; i += nt) {
-      const df x = W[(k + 1 + i) * LD + k];
-      a.fma(x, x);
-    }
-    const df sigma = block_reduce_df(a, red, &sc[0]);
+    df_acc sa = acc_zero();
+    for (int w2 = 0; w2 < nw; ++w2) sa.merge(red_sig[w2]);
+    const df sigma = sa.value();
     const df x0 = W[(k + 1) * LD + k];
-    __syncthreads();  // every thread has read x0 before thread 0 overwrites it with v0
     if (sigma.hi == 0.f) {
       if (tid == 0) {
         tau[k] = df{0.f, 0.f};
         dd[k] = W[k * LD + k];
         ee[k] = x0;
       }
+      // partials of the next column, unchanged by this step
+      __syncthreads();
+      df_acc a = acc_zero();
+      for (int i = k + 3 + warp; i < n; i += nw)
+        if (lane == 0) a.fma(W[i * LD + k + 1], W[i * LD + k + 1]);
+      if (lane == 0) red_sig[warp] = a;
       __syncthreads();
       continue;
     }
@@ -173,47 +174,84 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     const df v0 = df_sub(x0, alpha);
     const df vtv = df_add(sigma, df_mul(v0, v0));
     const df t = df_div(df{2.f, 0.f}, vtv);
-    for (int i = tid; i < m; i += nt) {
-      const df vi = (i == 0) ? v0 : W[(k + 1 + i) * LD + k];
-      v[i] = vi;
-      W[(k + 1 + i) * LD + k] = vi;  // kept for the back-transformation
-    }
+    for (int i = tid; i < m; i += nt) v[i] = (i == 0) ? v0 : W[(k + 1 + i) * LD + k];
     if (tid == 0) {
       tau[k] = t;
       dd[k] = W[k * LD + k];
       ee[k] = alpha;
     }
-    __syncthreads();
-    // p = t * W22 v
-    for (int i = warp; i < m; i += nw) {
-      df_acc b = acc_zero();
-      const df* row = W + (k + 1 + i) * LD + (k + 1);
-      for (int j = lane; j < m; j += 32) b.fma(row[j], v[j]);
+    __syncthreads();  // (1) v complete
+    // p = t * W22 v, and per-warp partials of v^T p; column k keeps v for the back-transformation
+    {
+      df_acc pv = acc_zero();
+      for (int i = warp; i < m; i += nw) {
+        df_acc b0 = acc_zero(), b1 = acc_zero();
+        const df* row = W + (k + 1 + i) * LD + (k + 1);
+        int j = lane;
+        for (; j + 32 < m; j += 64) {
+          const df r0 = row[j], r1 = row[j + 32];
+          const df v0j = v[j], v1j = v[j + 32];
+          b0.fma(r0, v0j);
+          b1.fma(r1, v1j);
+        }
+        if (j < m) b0.fma(row[j], v[j]);
+        b0.merge(b1);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) b.merge(shfl_xor_acc(b, o));
-      if (lane == 0) p[i] = df_mul(t, b.value());
-    }
-    __syncthreads();
-    df_acc c = acc_zero();
-    for (int i = tid; i < m; i += nt) c.fma(v[i], p[i]);
-    const df vp = block_reduce_df(c, red, &sc[1]);
-    const df kc = df_mul(df_mul_f(t, 0.5f), vp);
-    for (int i = tid; i < m; i += nt) p[i] = df_sub(p[i], df_mul(kc, v[i]));  // w
-    __syncthreads();
-    // W22 -= v w^T + w v^T  (lower triangle computed, mirrored)
-    for (int i = warp; i < m; i += nw) {
-      const df vi = v[i], wi = p[i];
-      df* rowi = W + (k + 1 + i) * LD + (k + 1);
-      for (int j = lane; j <= i; j += 32) {
-        df_acc u = acc_zero();
-        u.fma(vi, p[j]);
-        u.fma(wi, v[j]);
-        const df nv = df_sub(rowi[j], u.value());
-        rowi[j] = nv;
-        W[(k + 1 + j) * LD + (k + 1 + i)] = nv;
+        for (int o = 16; o > 0; o >>= 1) b0.merge(shfl_xor_acc(b0, o));
+        if (lane == 0) {
+          const df pi = df_mul(t, b0.value());
+          p[i] = pi;
+          pv.fma(v[i], pi);
+        }
       }
+      if (lane == 0) red_vp[warp] = pv;
+      for (int i = tid; i < m; i += nt) W[(k + 1 + i) * LD + k] = v[i];
     }
-    __syncthreads();
+    __syncthreads();  // (2) p and v^T p partials complete
+    {
+      df_acc c = acc_zero();
+      for (int w2 = 0; w2 < nw; ++w2) c.merge(red_vp[w2]);
+      const df kc = df_mul(df_mul_f(t, 0.5f), c.value());
+      for (int i = tid; i < m; i += nt) p[i] = df_sub(p[i], df_mul(kc, v[i]));  // w
+    }
+    __syncthreads();  // (3) w complete
+    // W22 -= v w^T + w v^T (lower triangle computed, mirrored); lane 0 of each
+    // row also accumulates the next column's norm (rows 2.. of the trailing block)
+    {
+      df_acc sg = acc_zero();
+      for (int i = warp; i < m; i += nw) {
+        const df vi = v[i], wi = p[i];
+        df* rowi = W + (k + 1 + i) * LD + (k + 1);
+        int j = lane;
+        for (; j + 32 <= i; j += 64) {
+          const df a0 = rowi[j], a1 = rowi[j + 32];
+          const df pj0 = p[j], vj0 = v[j], pj1 = p[j + 32], vj1 = v[j + 32];
+          df_acc u0 = acc_zero(), u1 = acc_zero();
+          u0.fma(vi, pj0);
+          u1.fma(vi, pj1);
+          u0.fma(wi, vj0);
+          u1.fma(wi, vj1);
+          const df n0 = df_sub(a0, u0.value());
+          const df n1 = df_sub(a1, u1.value());
+          rowi[j] = n0;
+          rowi[j + 32] = n1;
+          W[(k + 1 + j) * LD + (k + 1 + i)] = n0;
+          W[(k + 1 + j + 32) * LD + (k + 1 + i)] = n1;
+          if (j == 0 && i >= 2) sg.fma(n0, n0);
+        }
+        if (j <= i) {
+          df_acc u0 = acc_zero();
+          u0.fma(vi, p[j]);
+          u0.fma(wi, v[j]);
+          const df n0 = df_sub(rowi[j], u0.value());
+          rowi[j] = n0;
+          W[(k + 1 + j) * LD + (k + 1 + i)] = n0;
+          if (j == 0 && i >= 2) sg.fma(n0, n0);
+        }
+      }
+      if (lane == 0) red_sig[warp] = sg;
+    }
+    __syncthreads();  // (4) trailing block and next-column partials complete
   }
   if (tid == 0) {
     if (n >= 2) {
@@ -258,7 +296,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     float lo = gl, hi = gu;
     for (int it = 0; it < 80; ++it) {
       const float mid = 0.5f * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
+      if (mid <= lo || mid >= hi || hi - lo <= 2.0e-7f * tnorm) break;
       if (sturm_count(sd, se2, n, mid, pivmin) > j) hi = mid; else lo = mid;
     }
     shift[j] = 0.5f * (lo + hi);
@@ -768,7 +806,8 @@ __global__ void k_pencil_back(int dn, int q, const double* __restrict__ Yh, cons
 }
 
 size_t syev_smem_base(int n, int nwant) {
-  return (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant + 15) &
+  return (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
+          3 * sizeof(df) * n + 15) &
          ~static_cast<size_t>(15);
 }
 

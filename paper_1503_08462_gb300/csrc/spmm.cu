@@ -55,8 +55,8 @@ template <int CPT, typename TO>
 __global__ void __launch_bounds__(kThreads) k_defect(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                      const double* __restrict__ a, const double* __restrict__ m,
                                                      const double* __restrict__ U, int q,
-                                                     const double* __restrict__ lam, TO* __restrict__ R, int G,
-                                                     double* __restrict__ partials) {
+                                                     const double* __restrict__ lam, TO* __restrict__ R, int ldr,
+                                                     int G, double* __restrict__ partials) {
   extern __shared__ double sred[];  // [rows_per_block][2*G*CPT] when partials != null
   const int rpb = blockDim.x / G;
   const int g = threadIdx.x / G;
@@ -89,10 +89,12 @@ __global__ void __launch_bounds__(kThreads) k_defect(int n, const int* __restric
     rr[t] = 0.0;
     if (row < n && c < q) {
       const double r = fma(lam[c], mm[t], -aa[t]);
-      R[static_cast<long long>(row) * q + c] = static_cast<TO>(r);
+      R[static_cast<long long>(row) * ldr + c] = static_cast<TO>(r);
       rr[t] = r;
     }
   }
+  if (row < n)
+    for (int c = q + lane; c < ldr; c += G) R[static_cast<long long>(row) * ldr + c] = TO(0);
   if (partials == nullptr) return;
   // per-column sums of r^2 and (Mu)^2 over the block's rows, fixed order
   const int W = G * CPT;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_defect(int n, const int* __restric
 }
 
 template <typename TO>
-void defect_impl(const DevCsr& AM, const double* U, int q, const double* lam, TO* R, double* partials,
+void defect_impl(const DevCsr& AM, const double* U, int q, const double* lam, TO* R, int ldr, double* partials,
                  int* nblocks_out, cudaStream_t st) {
   Geo g = geo_for(q);
   const int blocks = ceil_div(AM.rows, g.rows_per_block);
@@ -122,8 +124,8 @@ void defect_impl(const DevCsr& AM, const double* U, int q, const double* lam, TO
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                                        \
   case C:                                                                                                     \
-    k_defect<C, TO><<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, U, q, lam, R, g.G, \
-                                                  partials);                                                \
+    k_defect<C, TO><<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, U, q, lam, R, ldr, \
+                                                  g.G, partials);                                           \
     break;
     AMGEIG_CASE(1)
     AMGEIG_CASE(2)
@@ -274,6 +276,102 @@ void smooth_impl(const DevCsr& A, const T* vals, const T* dinv, const T* b, cons
   }
 }
 
+// ------------------------------------------------------------------ float32, 16-byte vectors
+//
+// The float32 V-cycle works on blocks whose row stride is a multiple of 4, so
+// each thread moves one float4 (16 bytes) per gathered row: a row group is
+// G = width/4 threads (rounded up to a power of two), and a warp serves
+// 32/G rows at once, keeping more independent gathers in flight.
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __restrict__ rp,
+                                                        const int* __restrict__ ci, const float* __restrict__ a,
+                                                        const float* __restrict__ dinv,
+                                                        const float4* __restrict__ b, const float4* __restrict__ x,
+                                                        int w4, float4* __restrict__ out1, float4* __restrict__ out2,
+                                                        const double* __restrict__ U, double* __restrict__ V, int qv,
+                                                        int G) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  for (int c4 = lane; c4 < w4; c4 += G) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int p0 = rp[row], p1 = rp[row + 1];
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) {
+      const int j = ci[p];
+      float s = a[p];
+      if (MODE == 0) s *= dinv[j];
+      const float4 xv = (MODE == 0 ? b : x)[static_cast<long long>(j) * w4 + c4];
+      acc.x = fmaf(s, xv.x, acc.x);
+      acc.y = fmaf(s, xv.y, acc.y);
+      acc.z = fmaf(s, xv.z, acc.z);
+      acc.w = fmaf(s, xv.w, acc.w);
+    }
+    const long long o = static_cast<long long>(row) * w4 + c4;
+    const float4 bi = b[o];
+    const float4 res = make_float4(bi.x - acc.x, bi.y - acc.y, bi.z - acc.z, bi.w - acc.w);
+    const float di = dinv ? dinv[row] : 0.f;
+    if (MODE == 0) {
+      out1[o] = make_float4(di * bi.x, di * bi.y, di * bi.z, di * bi.w);
+      out2[o] = res;
+    } else if (MODE == 2) {
+      out1[o] = res;
+    } else {
+      const float4 xi = x[o];
+      const float4 xn = make_float4(fmaf(di, res.x, xi.x), fmaf(di, res.y, xi.y), fmaf(di, res.z, xi.z),
+                                    fmaf(di, res.w, xi.w));
+      if (MODE == 1) {
+        out1[o] = xn;
+      } else {
+        const long long vb = static_cast<long long>(row) * qv + 4 * c4;
+        const float xs[4] = {xn.x, xn.y, xn.z, xn.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (4 * c4 + k < qv) V[vb + k] = U[vb + k] + static_cast<double>(xs[k]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_spmm_f4(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                      const float* __restrict__ v, const float4* __restrict__ X,
+                                                      int w4, float4* __restrict__ Y, int G, int accumulate) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  for (int c4 = lane; c4 < w4; c4 += G) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int p0 = rp[row], p1 = rp[row + 1];
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) {
+      const float s = v[p];
+      const float4 xv = X[static_cast<long long>(ci[p]) * w4 + c4];
+      acc.x = fmaf(s, xv.x, acc.x);
+      acc.y = fmaf(s, xv.y, acc.y);
+      acc.z = fmaf(s, xv.z, acc.z);
+      acc.w = fmaf(s, xv.w, acc.w);
+    }
+    const long long o = static_cast<long long>(row) * w4 + c4;
+    if (accumulate) {
+      const float4 y = Y[o];
+      acc.x += y.x;
+      acc.y += y.y;
+      acc.z += y.z;
+      acc.w += y.w;
+    }
+    Y[o] = acc;
+  }
+}
+
+int group_for_f4(int w4) {
+  int G = 1;
+  while (G < w4 && G < 32) G <<= 1;
+  return G;
+}
+
 // ------------------------------------------------------------------ augmentation
 
 template <int CPT>
@@ -349,6 +447,53 @@ __global__ void __launch_bounds__(kThreads) k_recombine(int n, const double* __r
   }
 }
 
+// float-float variant: the block's V rows and Y are staged as float-float
+// pairs in shared memory (each converted once), products accumulate with
+// compensated float32 arithmetic
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_recombine_df(int n, const double* __restrict__ Xp,
+                                                           const double* __restrict__ V,
+                                                           const double* __restrict__ Y, int q,
+                                                           double* __restrict__ U, int G) {
+  extern __shared__ df dsm[];  // Y (q x q) then V rows (rpb x q)
+  df* ys = dsm;
+  df* vs = dsm + q * q;
+  const int rpb = blockDim.x / G;
+  for (int i = threadIdx.x; i < q * q; i += blockDim.x) ys[i] = df_from_double(Y[i]);
+  const long long row0 = static_cast<long long>(blockIdx.x) * rpb;
+  for (int i = threadIdx.x; i < rpb * q; i += blockDim.x) {
+    const long long r = row0 + i / q;
+    vs[i] = (r < n) ? df_from_double(V[r * q + i % q]) : df{0.f, 0.f};
+  }
+  __syncthreads();
+  const int g = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const long long row = row0 + g;
+  if (row >= n) return;
+  const long long base = row * q;
+  df_acc acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    acc[t] = acc_zero();
+    if (c < q) acc[t].add(df_from_double(Xp[base + c]));
+  }
+  const df* vr = vs + g * q;
+  for (int d = 0; d < q; ++d) {
+    const df v = vr[d];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < q) acc[t].fma(v, ys[d * q + c]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < q) U[base + c] = df_to_double(acc[t].value());
+  }
+}
+
 // ------------------------------------------------------------------ elementwise
 
 template <typename T>
@@ -378,6 +523,31 @@ __global__ void k_f32_to_f64(const float* __restrict__ x, long long count, doubl
     y[i] = static_cast<double>(x[i]);
 }
 
+__global__ void k_add_to_v_strided(const double* __restrict__ U, const float* __restrict__ x, int rows, int q, int ldx,
+                                   double* __restrict__ V) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    V[i] = U[i] + static_cast<double>(x[(i / q) * ldx + i % q]);
+}
+
+__global__ void k_pad_f64_to_f32(const double* __restrict__ src, int rows, int q, int ld, float* __restrict__ dst) {
+  const long long total = static_cast<long long>(rows) * ld;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / ld;
+    const int c = static_cast<int>(i % ld);
+    dst[i] = c < q ? static_cast<float>(src[r * q + c]) : 0.f;
+  }
+}
+
+__global__ void k_unpad_f32_to_f64(const float* __restrict__ src, int rows, int q, int ld, double* __restrict__ dst) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    dst[i] = static_cast<double>(src[(i / q) * ld + i % q]);
+}
+
 int grid_for(long long count) {
   long long b = (count + kThreads - 1) / kThreads;
   if (b > 8LL * kNumSms) b = 8LL * kNumSms;
@@ -388,11 +558,11 @@ int grid_for(long long count) {
 
 void launch_defect_f64(const DevCsr& AM, const double* U, int q, const double* lam, double* R, double* partials,
                        int* nblocks_out, cudaStream_t st) {
-  defect_impl<double>(AM, U, q, lam, R, partials, nblocks_out, st);
+  defect_impl<double>(AM, U, q, lam, R, q, partials, nblocks_out, st);
 }
-void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double* lam, float* R, double* partials,
-                          int* nblocks_out, cudaStream_t st) {
-  defect_impl<float>(AM, U, q, lam, R, partials, nblocks_out, st);
+void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double* lam, float* R, int ldr,
+                          double* partials, int* nblocks_out, cudaStream_t st) {
+  defect_impl<float>(AM, U, q, lam, R, ldr, partials, nblocks_out, st);
 }
 
 void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st,
@@ -400,7 +570,17 @@ void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, boo
   spmm_impl<double>(S, S.v64, X, width, Y, accumulate, st, cls);
 }
 void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st) {
-  spmm_impl<float>(S, S.v32, X, width, Y, accumulate, st);
+  if (width % 4 != 0 || S.rows == 0) {
+    spmm_impl<float>(S, S.v32, X, width, Y, accumulate, st);
+    return;
+  }
+  const int w4 = width / 4, G = group_for_f4(w4);
+  ProfScope ps(st, P_TRANSFER,
+               4.0 * (S.rows + 1) + 8.0 * S.nnz + 4.0 * S.cols * width + 4.0 * S.rows * width * (accumulate ? 2 : 1),
+               2.0 * S.nnz * width);
+  k_spmm_f4<<<ceil_div(S.rows, kThreads / G), kThreads, 0, st>>>(
+      S.rows, S.rp, S.ci, S.v32, reinterpret_cast<const float4*>(X), w4, reinterpret_cast<float4*>(Y), G,
+      accumulate ? 1 : 0);
 }
 
 void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const double* b, int width, double* x,
@@ -409,6 +589,16 @@ void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const do
 }
 void launch_presmooth_residual_f32(const DevCsr& A, const float* dinv, const float* b, int width, float* x,
                                    float* r, cudaStream_t st) {
+  if (width % 4 == 0 && A.rows > 0) {
+    const int w4 = width / 4, G = group_for_f4(w4);
+    const double N = A.rows;
+    const double vec = 12.0 * N * width;
+    ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
+    k_smooth_f4<0><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
+        A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), nullptr, w4,
+        reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r), nullptr, nullptr, 0, G);
+    return;
+  }
   smooth_impl<float, 0>(A, A.v32, dinv, b, nullptr, width, x, r, nullptr, nullptr, st);
 }
 void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
@@ -417,12 +607,32 @@ void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, con
 }
 void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
                        float* x_out, cudaStream_t st) {
+  if (width % 4 == 0 && A.rows > 0) {
+    const int w4 = width / 4, G = group_for_f4(w4);
+    const double N = A.rows;
+    const double vec = 12.0 * N * width;
+    ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
+    k_smooth_f4<1><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
+        A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
+        reinterpret_cast<float4*>(x_out), nullptr, nullptr, nullptr, 0, G);
+    return;
+  }
   smooth_impl<float, 1>(A, A.v32, dinv, b, x, width, x_out, nullptr, nullptr, nullptr, st);
 }
 void launch_residual_f64(const DevCsr& A, const double* b, const double* x, int width, double* r, cudaStream_t st) {
   smooth_impl<double, 2>(A, A.v64, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
 }
 void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st) {
+  if (width % 4 == 0 && A.rows > 0) {
+    const int w4 = width / 4, G = group_for_f4(w4);
+    const double N = A.rows;
+    const double vec = 12.0 * N * width;
+    ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 0.0 + vec, 2.0 * A.nnz * width);
+    k_smooth_f4<2><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
+        A.rows, A.rp, A.ci, A.v32, nullptr, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
+        reinterpret_cast<float4*>(r), nullptr, nullptr, nullptr, 0, G);
+    return;
+  }
   smooth_impl<float, 2>(A, A.v32, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
 }
 void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
@@ -430,8 +640,19 @@ void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b
   smooth_impl<double, 3>(A, A.v64, dinv, b, x, width, nullptr, nullptr, U, V, st);
 }
 void launch_jacobi_to_v_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                            const double* U, double* V, cudaStream_t st) {
+                            const double* U, double* V, cudaStream_t st, int qv) {
+  if (width % 4 == 0 && A.rows > 0) {
+    const int w4 = width / 4, G = group_for_f4(w4);
+    const double N = A.rows;
+    const double vec = (2.0 * 4 + 16.0) * N * width;
+    ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
+    k_smooth_f4<3><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
+        A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
+        nullptr, nullptr, U, V, qv, G);
+    return;
+  }
   smooth_impl<float, 3>(A, A.v32, dinv, b, x, width, nullptr, nullptr, U, V, st);
+  (void)qv;
 }
 void launch_add_to_v_f64(const double* U, const double* x, long long count, double* V, cudaStream_t st) {
   ProfScope ps(st, P_SMOOTH, 24.0 * count, 1.0 * count);
@@ -463,11 +684,30 @@ void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaS
 }
 
 void launch_recombine(int rows, const double* Xp, const double* V, const double* Y, int q, double* U,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool df_arith) {
   Geo g = geo_for(q);
   const int blocks = ceil_div(rows, g.rows_per_block);
-  const size_t sm = sizeof(double) * q * q;
   ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
+  if (df_arith) {
+    const size_t sm = sizeof(df) * (static_cast<size_t>(q) * q + static_cast<size_t>(g.rows_per_block) * q);
+    switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                            \
+  case C:                                                                                         \
+    if (sm > 48 * 1024)                                                                           \
+      cudaFuncSetAttribute(k_recombine_df<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    k_recombine_df<C><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U, g.G);                     \
+    break;
+      AMGEIG_CASE(1)
+      AMGEIG_CASE(2)
+      AMGEIG_CASE(4)
+      AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+      default:
+        break;
+    }
+    return;
+  }
+  const size_t sm = sizeof(double) * q * q;
   switch (g.cpt) {
 #define AMGEIG_CASE(C)                                                                         \
   case C:                                                                                      \
@@ -502,6 +742,25 @@ void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaS
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st) {
   ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
   k_f32_to_f64<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+void launch_add_to_v_f32_strided(const double* U, const float* x, int rows, int q, int ldx, double* V,
+                                 cudaStream_t st) {
+  const long long count = static_cast<long long>(rows) * q;
+  ProfScope ps(st, P_SMOOTH, 20.0 * count, 1.0 * count);
+  k_add_to_v_strided<<<grid_for(count), kThreads, 0, st>>>(U, x, rows, q, ldx, V);
+}
+
+void launch_f64_to_f32_pad(const double* src, int rows, int q, int ld, float* dst, cudaStream_t st) {
+  const long long count = static_cast<long long>(rows) * ld;
+  ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
+  k_pad_f64_to_f32<<<grid_for(count), kThreads, 0, st>>>(src, rows, q, ld, dst);
+}
+
+void launch_f32_to_f64_unpad(const float* src, int rows, int q, int ld, double* dst, cudaStream_t st) {
+  const long long count = static_cast<long long>(rows) * q;
+  ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
+  k_unpad_f32_to_f64<<<grid_for(count), kThreads, 0, st>>>(src, rows, q, ld, dst);
 }
 
 }  // namespace amgeig
