@@ -35,7 +35,10 @@
 
 namespace amgeig {
 
-constexpr int kSyThreads = 1024;
+#ifndef AMGEIG_SY_THREADS
+#define AMGEIG_SY_THREADS 1024
+#endif
+constexpr int kSyThreads = AMGEIG_SY_THREADS;
 
 struct PencilWork {
   int dn = 0, qmax = 0, nmax = 0;
@@ -150,8 +153,9 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   // from per-warp partial sums written in the preceding phase.
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
-    df_acc sa = acc_zero();
-    for (int w2 = 0; w2 < nw; ++w2) sa.merge(red_sig[w2]);
+    df_acc sa = lane < nw ? red_sig[lane] : acc_zero();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sa.merge(shfl_xor_acc(sa, o));
     const df sigma = sa.value();
     const df x0 = W[(k + 1) * LD + k];
     if (sigma.hi == 0.f) {
@@ -209,8 +213,9 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     }
     __syncthreads();  // (2) p and v^T p partials complete
     {
-      df_acc c = acc_zero();
-      for (int w2 = 0; w2 < nw; ++w2) c.merge(red_vp[w2]);
+      df_acc c = lane < nw ? red_vp[lane] : acc_zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c.merge(shfl_xor_acc(c, o));
       const df kc = df_mul(df_mul_f(t, 0.5f), c.value());
       for (int i = tid; i < m; i += nt) p[i] = df_sub(p[i], df_mul(kc, v[i]));  // w
     }
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     float lo = gl, hi = gu;
     for (int it = 0; it < 80; ++it) {
       const float mid = 0.5f * (lo + hi);
-      if (mid <= lo || mid >= hi || hi - lo <= 2.0e-7f * tnorm) break;
+      if (mid <= lo || mid >= hi) break;
       if (sturm_count(sd, se2, n, mid, pivmin) > j) hi = mid; else lo = mid;
     }
     shift[j] = 0.5f * (lo + hi);
