@@ -42,7 +42,7 @@ WORKLOADS = {
     # name: builder, its arguments, q, q_extra, coarse-level cap of the AMG setup,
     # relative-residual tolerance, coarse modes in the pencil (0 = all of V_n)
     "lshape_h512_q20": dict(builder="lshape_2d", kw=dict(m_half=512, seed=2), q=20, qe=4, cap=400, tol=1e-5,
-                            modes=96),
+                            modes=64),
     "square_h32_q4": dict(builder="square_2d", kw=dict(m=32, seed=1), q=4, qe=2, cap=50, tol=1e-9, modes=0),
     "checker_h1024_q50": dict(builder="square_2d", kw=dict(m=1024, checker=4, seed=3), q=50, qe=6, cap=400,
                               tol=1e-6, modes=112),

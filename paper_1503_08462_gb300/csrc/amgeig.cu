@@ -363,9 +363,10 @@ void residual(const DevCsr& A, const float* b, const float* x, int wdt, float* r
 void spmm(const DevCsr& S, const double* X, int wdt, double* Y, bool acc, cudaStream_t s) { launch_spmm_f64(S, X, wdt, Y, acc, s); }
 void spmm(const DevCsr& S, const float* X, int wdt, float* Y, bool acc, cudaStream_t s) { launch_spmm_f32(S, X, wdt, Y, acc, s); }
 void jacobi_to_v(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, const double* U, double* V, cudaStream_t s, int) { launch_jacobi_to_v_f64(A, d, b, x, wdt, U, V, s); }
-void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv) { launch_jacobi_to_v_f32(A, d, b, x, wdt, U, V, s, qv); }
+// the float32 V-cycle belongs to the mixed path, whose U and V are float-float
+void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv) { launch_jacobi_to_vdf_f32(A, d, b, x, wdt, reinterpret_cast<const float2*>(U), reinterpret_cast<float2*>(V), s, qv); }
 void add_to_v(const double* U, const double* x, int rows, int q, int, double* V, cudaStream_t s) { launch_add_to_v_f64(U, x, static_cast<long long>(rows) * q, V, s); }
-void add_to_v(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t s) { launch_add_to_v_f32_strided(U, x, rows, q, ldx, V, s); }
+void add_to_v(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t s) { launch_add_to_vdf(reinterpret_cast<const float2*>(U), x, rows, q, ldx, reinterpret_cast<float2*>(V), s); }
 void axpy(const double* x, long long c, double* y, cudaStream_t s) { launch_axpy_f64(x, c, y, s); }
 void axpy(const float* x, long long c, float* y, cudaStream_t s) { launch_axpy_f32(x, c, y, s); }
 const double* dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->dinv64[l]; }
@@ -466,35 +467,53 @@ namespace {
 // (augmented pencil on V_n + span(V), its q smallest pairs, recombination).
 // On entry U (level k) and lam hold {lambda_j, u_j}; the defect of the current
 // pair is already in B[k] (float64 or float32 by precision).
+float2* as_df(double* p) { return reinterpret_cast<float2*>(p); }
+
 int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, cudaStream_t st) {
   const int q = w->qt;
   const int n = h->nlev;
   const int Nk = static_cast<int>(h->sizes[k]);
-  if (o.precision == AMGEIG_FP64)
-    amg_correction<double>(h, w, k, o, w->U, w->V, st);
-  else
-    amg_correction<float>(h, w, k, o, w->U, w->V, st);
-  // augmentation: W = [A_k V | M_k V], G = V^T W, C = I_k^n W
-  launch_dual_spmm(h->A[k], w->V, q, w->W, st);
-  // the mixed path forms the Gram blocks and the recombination in float-float
-  // (48-bit significand on the float32 pipes); the float64 path in float64
-  const bool dfa = o.precision != AMGEIG_FP64;
-  launch_gram(Nk, w->V, q, w->W, 2 * q, w->gsc, w->G, st, dfa);
-  const double* cur = w->W;
-  for (int l = k; l < n - 1; ++l) {
-    launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st, P_CHAIN);
-    cur = w->WC[l + 1];
-  }
-  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
   const int modes = (o.coarse_modes > 0 && o.coarse_modes < h->dn) ? o.coarse_modes : h->dn;
-  launch_pencil_solve(w->pw, h->dn, modes, q, cur, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
-  // recombination: U = I_n^k Xc + V Y
-  const double* px = w->Xc;
-  for (int l = n - 2; l >= k; --l) {
-    launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st, P_CHAIN);
-    px = w->PX[l];
+  if (o.precision == AMGEIG_FP64) {
+    amg_correction<double>(h, w, k, o, w->U, w->V, st);
+    // augmentation: W = [A_k V | M_k V], G = V^T W, C = I_k^n W
+    launch_dual_spmm(h->A[k], w->V, q, w->W, st);
+    launch_gram(Nk, w->V, q, w->W, 2 * q, w->gsc, w->G, st, false);
+    const double* cur = w->W;
+    for (int l = k; l < n - 1; ++l) {
+      launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st, P_CHAIN);
+      cur = w->WC[l + 1];
+    }
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
+    launch_pencil_solve(w->pw, h->dn, modes, q, cur, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
+    // recombination: U = I_n^k Xc + V Y
+    const double* px = w->Xc;
+    for (int l = n - 2; l >= k; --l) {
+      launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st, P_CHAIN);
+      px = w->PX[l];
+    }
+    launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st, false);
+  } else {
+    // mixed path: float32 V-cycle; U, V, W and the chains in float-float
+    amg_correction<float>(h, w, k, o, w->U, w->V, st);
+    launch_dual_spmm_df(h->A[k], as_df(w->V), q, as_df(w->W), st);
+    launch_gram_df(Nk, as_df(w->V), q, as_df(w->W), 2 * q, w->gsc, w->G, st);
+    const float2* cur = as_df(w->W);
+    for (int l = k; l < n - 1; ++l) {
+      launch_spmm_df(h->R[l], cur, 2 * q, as_df(w->WC[l + 1]), false, st, P_CHAIN);
+      cur = as_df(w->WC[l + 1]);
+    }
+    launch_df_to_f64(cur, static_cast<long long>(h->dn) * 2 * q, w->C, st);
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
+    launch_pencil_solve(w->pw, h->dn, modes, q, w->C, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
+    launch_f64_to_df(w->Xc, static_cast<long long>(h->dn) * q, as_df(w->PX[n - 1]), st);
+    const float2* px = as_df(w->PX[n - 1]);
+    for (int l = n - 2; l >= k; --l) {
+      launch_spmm_df(h->P[l], px, q, as_df(w->PX[l]), false, st, P_CHAIN);
+      px = as_df(w->PX[l]);
+    }
+    launch_recombine_df(Nk, px, as_df(w->V), w->Yv, q, as_df(w->U), st);
   }
-  launch_recombine(Nk, px, w->V, w->Yv, q, w->U, st, dfa);
   {
     ProfScope ps(st, P_OTHER, 16.0 * q, 0.0);
     k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
@@ -510,7 +529,7 @@ int defect(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, 
   if (o.precision == AMGEIG_FP64)
     launch_defect_f64(h->A[k], w->U, q, w->lam, w->B64[k], part, &nb, st);
   else
-    launch_defect_f32out(h->A[k], w->U, q, w->lam, w->B32[k], w->ld32, part, &nb, st);
+    launch_defect_df(h->A[k], as_df(w->U), q, w->lam, w->B32[k], w->ld32, part, &nb, st);
   if (norms) {
     launch_sum_partials(w->partials, nb, 2 * q, w->sums, st);
     CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
@@ -544,7 +563,10 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   }
   SolveWork* w = h->ws.get();
   // step 1: initial eigenpairs on level n1 = n (the coarsest)
-  launch_copy_cols(h->Z, h->dn, h->dn, qt, w->U, st);
+  if (o.precision == AMGEIG_FP64)
+    launch_copy_cols(h->Z, h->dn, h->dn, qt, w->U, st);
+  else
+    launch_cols_to_df(h->Z, h->dn, h->dn, qt, as_df(w->U), st);
   {
     ProfScope ps(st, P_OTHER, 16.0 * qt, 0.0);
     k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
@@ -555,7 +577,10 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   relres_host.assign(qt, 0.0);
   // step 2: k = n1-1 .. 1 (0-based n-2 .. 1) one correction each, then the finest level
   for (int k = n - 2; k >= 0; --k) {
-    launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st, P_CHAIN);
+    if (o.precision == AMGEIG_FP64)
+      launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st, P_CHAIN);
+    else
+      launch_spmm_df(h->P[k], as_df(w->U), qt, as_df(w->Ualt), false, st, P_CHAIN);
     std::swap(w->U, w->Ualt);
     if (k >= 1) {
       rc = defect(h, w, k, o, false, st);
@@ -627,12 +652,18 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
   const int N0 = static_cast<int>(h->sizes[0]);
   if (eigvals) CK(cudaMemcpyAsync(eigvals, w->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st));
   if (eigvecs) {
-    double* dst = on_device ? eigvecs : w->V;  // V is free after the solve
+    const double* src = w->U;
+    if (w->precision != AMGEIG_FP64) {
+      // float-float iterate -> float64 (V is free after the solve)
+      launch_df_to_f64(as_df(w->U), static_cast<long long>(N0) * qt, w->V, st);
+      src = w->V;
+    }
+    double* dst = on_device ? eigvecs : w->Ualt;  // Ualt is free after the solve
     const long long total = static_cast<long long>(N0) * q;
     ProfScope ps(st, P_OTHER, 8.0 * N0 * qt + 16.0 * total, 0.0, 2);
-    k_col_sign<<<q, 256, 0, st>>>(w->U, N0, qt, q, w->sign);
+    k_col_sign<<<q, 256, 0, st>>>(src, N0, qt, q, w->sign);
     k_out_vectors<<<static_cast<int>(std::min<long long>((total + 255) / 256, 8LL * kNumSms)), 256, 0, st>>>(
-        w->U, N0, qt, q, w->sign, dst);
+        src, N0, qt, q, w->sign, dst);
     CK(cudaGetLastError());
     if (!on_device) CK(cudaMemcpyAsync(eigvecs, dst, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
   }
@@ -770,6 +801,15 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
     CK(m.upload(&D.v64, L.a));
     CK(m.upload(&D.m64, L.m));
     CK(m.upload(&D.v32, a32));
+    std::vector<float2> a2(L.a.size()), m2(L.m.size());
+    for (size_t i = 0; i < L.a.size(); ++i) {
+      const float hi = static_cast<float>(L.a[i]);
+      a2[i] = make_float2(hi, static_cast<float>(L.a[i] - static_cast<double>(hi)));
+      const float mh = static_cast<float>(L.m[i]);
+      m2[i] = make_float2(mh, static_cast<float>(L.m[i] - static_cast<double>(mh)));
+    }
+    CK(m.upload(&D.d2, a2));
+    CK(m.upload(&D.m2, m2));
     CK(m.upload(&h->dinv64[l], d64));
     CK(m.upload(&h->dinv32[l], d32));
   }
@@ -783,10 +823,16 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
       D.cols = static_cast<int>(S.cols);
       D.nnz = static_cast<int>(S.ci.size());
       std::vector<float> v32(S.a.begin(), S.a.end());
+      std::vector<float2> v2(S.a.size());
+      for (size_t i = 0; i < S.a.size(); ++i) {
+        const float hi = static_cast<float>(S.a[i]);
+        v2[i] = make_float2(hi, static_cast<float>(S.a[i] - static_cast<double>(hi)));
+      }
       CK(m.upload(&D.rp, S.rp));
       CK(m.upload(&D.ci, S.ci));
       CK(m.upload(&D.v64, S.a));
       CK(m.upload(&D.v32, v32));
+      CK(m.upload(&D.d2, v2));
     }
   }
   // dense coarsest pencil and its eigendecomposition

@@ -16,6 +16,8 @@ struct DevCsr {
   double* v64 = nullptr;
   float* v32 = nullptr;
   double* m64 = nullptr;  // second value array sharing the pattern (mass matrix)
+  float2* d2 = nullptr;   // v64 as float-float pairs (hi, lo)
+  float2* m2 = nullptr;   // m64 as float-float pairs
 };
 
 // ---- sparse kernels (spmm.cu) --------------------------------------------
@@ -79,6 +81,28 @@ void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st)
 // float64 -> float32 / float32 -> float64 copies
 void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st);
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st);
+
+// ---- float-float kernels of the mixed path (spmm_df.cu) -------------------
+// Blocks are float2 (hi, lo) pairs, row-major like the float64 blocks.
+void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* lam, float* R, int ldr,
+                      double* partials, int* nblocks_out, cudaStream_t st);
+void launch_dual_spmm_df(const DevCsr& AM, const float2* V, int q, float2* W, cudaStream_t st);
+void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool accumulate, cudaStream_t st,
+                    int cls);
+void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
+                         cudaStream_t st);
+size_t gram_df_scratch_doubles(int rows, int q, int w);
+void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, double* scratch, double* G,
+                    cudaStream_t st);
+void launch_f64_to_df(const double* x, long long count, float2* y, cudaStream_t st);
+void launch_df_to_f64(const float2* x, long long count, double* y, cudaStream_t st);
+void launch_cols_to_df(const double* src, int rows, int ld, int q, float2* dst, cudaStream_t st);
+// last float32 sweep on the working level fused with V = U + x (U, V float-float,
+// row stride qv; b and x row stride width)
+void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
+                              const float2* U, float2* V, cudaStream_t st, int qv);
+// V = U + x (U, V float-float rows x q; x float32 with row stride ldx)
+void launch_add_to_vdf(const float2* U, const float* x, int rows, int q, int ldx, float2* V, cudaStream_t st);
 
 // ---- dense kernels (dense.cu) ---------------------------------------------
 

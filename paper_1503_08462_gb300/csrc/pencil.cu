@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   __syncthreads();
   // clusters of nearly equal shifts are iterated in rounds with Gram-Schmidt
   if (tid == 0) {
-    const float ctol = 1.0e-5f * tnorm;
+    const float ctol = 1.0e-3f * tnorm;
     int maxpos = 0;
     for (int j = 0; j < nwant; ++j) {
       if (j > 0 && shift[j] - shift[j - 1] <= ctol) {
@@ -389,201 +389,220 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     __syncthreads();
   }
 
-  // ---- Rayleigh-Ritz clean-up on span(Zt): S = Z^T Z, Hq = Z^T T Z ---------
-  df* S = rrw;
-  df* Hq = rrw + NW * NW;
-  df* Qm = rrw + 2 * NW * NW;
-  df* Xm = rrw + 3 * NW * NW;
-  for (int idx = tid; idx < nwant * nwant; idx += nt) {
-    const int a0 = idx / nwant, b0 = idx % nwant;
-    if (b0 < a0) continue;
-    df_acc s = acc_zero(), h = acc_zero();
-    for (int i = 0; i < n; ++i) {
-      const df za = Zt[i * NW + a0];
-      const df zb = Zt[i * NW + b0];
-      s.fma(za, zb);
-      df_acc tz = acc_zero();
-      tz.fma(dd[i], zb);
-      if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + b0]);
-      if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + b0]);
-      h.fma(za, tz.value());
-    }
-    S[a0 * NW + b0] = S[b0 * NW + a0] = s.value();
-    Hq[a0 * NW + b0] = Hq[b0 * NW + a0] = h.value();
-  }
-  __syncthreads();
-  // Cholesky S = L L^T in place (lower), right-looking
-  for (int kk = 0; kk < nwant; ++kk) {
-    if (tid == 0) S[kk * NW + kk] = df_sqrt(S[kk * NW + kk]);
-    __syncthreads();
-    const df piv = S[kk * NW + kk];
-    for (int i = kk + 1 + tid; i < nwant; i += nt) S[i * NW + kk] = df_div(S[i * NW + kk], piv);
-    __syncthreads();
-    for (int idx = tid; idx < (nwant - kk - 1) * (nwant - kk - 1); idx += nt) {
-      const int i = kk + 1 + idx / (nwant - kk - 1), jj = kk + 1 + idx % (nwant - kk - 1);
-      if (jj <= i) S[i * NW + jj] = df_sub(S[i * NW + jj], df_mul(S[i * NW + kk], S[jj * NW + kk]));
-    }
-    __syncthreads();
-  }
-  // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int col = tid; col < nwant; col += nt) {
-      for (int i = 0; i < nwant; ++i) {
-        df s = (pass == 0) ? Hq[i * NW + col] : Xm[col * NW + i];
-        for (int kk = 0; kk < i; ++kk)
-          s = df_sub(s, df_mul(S[i * NW + kk], (pass == 0) ? Xm[kk * NW + col] : Qm[kk * NW + col]));
-        const df r = df_div(s, S[i * NW + i]);
-        if (pass == 0) Xm[i * NW + col] = r; else Qm[i * NW + col] = r;
-      }
-    }
-    __syncthreads();
-  }
-  // Qm now holds C (symmetric); move it to Hq and set Qm = I
-  for (int idx = tid; idx < nwant * nwant; idx += nt) {
-    const int a0 = idx / nwant, b0 = idx % nwant;
-    const df cab = Qm[a0 * NW + b0], cba = Qm[b0 * NW + a0];
-    Hq[idx] = df_mul_f(df_add(cab, cba), 0.5f);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < nwant * nwant; idx += nt) Qm[idx] = df{(idx / nwant == idx % nwant) ? 1.f : 0.f, 0.f};
-  __syncthreads();
-  // parallel cyclic Jacobi (round-robin pairing) on C, accumulating Q
-  {
-    const int np = (nwant + 1) & ~1;  // even player count; index nwant is a dummy
-    for (int sweep = 0; sweep < 12; ++sweep) {
-      // convergence test: largest off-diagonal entry against the largest diagonal one
-      float off = 0.f, dia = 0.f;
-      for (int idx = tid; idx < nwant * nwant; idx += nt) {
-        const int a0 = idx / nwant, b0 = idx % nwant;
-        const float x = fabsf(Hq[idx].hi);
-        if (a0 == b0) dia = fmaxf(dia, x); else off = fmaxf(off, x);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
-        dia = fmaxf(dia, __shfl_xor_sync(0xffffffffu, dia, o));
-      }
-      if (lane == 0) {
-        red[warp].s = off;
-        red[warp].c = dia;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        float o2 = 0.f, d2 = 0.f;
-        for (int w2 = 0; w2 < nw; ++w2) {
-          o2 = fmaxf(o2, red[w2].s);
-          d2 = fmaxf(d2, red[w2].c);
-        }
-        sf[0] = o2;
-        sf[1] = d2;
-      }
-      __syncthreads();
-      const float offmax = sf[0], diamax = sf[1];
-      __syncthreads();
-      if (!(offmax > 1.0e-15f * fmaxf(diamax, 1.0e-30f))) break;
-      for (int r = 0; r < np - 1; ++r) {
-        // pair t: players (a, b) of the round-robin schedule
-        for (int t = tid; t < np / 2; t += nt) {
-          int a0 = (t == 0) ? 0 : 1 + (t - 1 + r) % (np - 1);
-          int b0 = 1 + (np - 2 - t + r) % (np - 1);
-          if (a0 > b0) {
-            const int tmpi = a0;
-            a0 = b0;
-            b0 = tmpi;
-          }
-          df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
-          if (b0 < nwant) {
-            const df apq = Hq[a0 * NW + b0];
-            const df app = Hq[a0 * NW + a0], aqq = Hq[b0 * NW + b0];
-            // skip entries already below the float-float resolution of the diagonal
-            const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
-            if (fabsf(apq.hi) > thr) {
-              // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
-              // and t = 1 / (2 theta) once theta^2 would leave the float range
-              const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
-              df tt;
-              if (fabsf(th.hi) > 1.0e12f) {
-                tt = df_div(df{0.5f, 0.f}, th);
-              } else {
-                const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
-                tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
-                if (df_lt0(th)) tt = df_neg(tt);
-              }
-              cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
-              sn = df_mul(tt, cs);
-            }
-          }
-          // stash rotation in Xm row 0..np/2 (cols 0..3)
-          Xm[t * 4 + 0] = cs;
-          Xm[t * 4 + 1] = sn;
-          reinterpret_cast<int*>(&Xm[t * 4 + 2])[0] = a0;
-          reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
-        }
-        __syncthreads();
-        // rows: C <- J^T C
-        for (int idx = tid; idx < (np / 2) * nwant; idx += nt) {
-          const int t = idx / nwant, col = idx % nwant;
-          const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-          const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-          if (b0 >= nwant) continue;
-          const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-          const df x = Hq[a0 * NW + col], y = Hq[b0 * NW + col];
-          Hq[a0 * NW + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          Hq[b0 * NW + col] = df_add(df_mul(sn, x), df_mul(cs, y));
-        }
-        __syncthreads();
-        // columns: C <- C J, Q <- Q J
-        for (int idx = tid; idx < (np / 2) * nwant; idx += nt) {
-          const int t = idx / nwant, row = idx % nwant;
-          const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-          const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-          if (b0 >= nwant) continue;
-          const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-          df x = Hq[row * NW + a0], y = Hq[row * NW + b0];
-          Hq[row * NW + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          Hq[row * NW + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-          x = Qm[row * NW + a0];
-          y = Qm[row * NW + b0];
-          Qm[row * NW + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          Qm[row * NW + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-        }
-        __syncthreads();
-      }
-    }
-  }
-  // order eigenvalues ascending (selection by rank; ties broken by index)
-  for (int j = tid; j < nwant; j += nt) {
-    const df lj = Hq[j * NW + j];
-    int rank = 0;
-    for (int i = 0; i < nwant; ++i) {
-      const df li = Hq[i * NW + i];
-      const df dlt = df_sub(li, lj);
-      if (df_lt0(dlt) || ((dlt.hi == 0.f && dlt.lo == 0.f) && i < j)) ++rank;
-    }
-    perm[rank] = j;
-  }
-  __syncthreads();
-  // Xm = L^-T Q  (back substitution per column)
-  for (int col = tid; col < nwant; col += nt) {
-    for (int i = nwant - 1; i >= 0; --i) {
-      df s = Qm[i * NW + col];
-      for (int kk = i + 1; kk < nwant; ++kk) s = df_sub(s, df_mul(S[kk * NW + i], Xm[kk * NW + col]));
-      Xm[i * NW + col] = df_div(s, S[i * NW + i]);
-    }
-  }
-  __syncthreads();
-  // tridiagonal eigenvectors Zt <- Zt Xm, written in sorted order into Qm-free
-  // storage: reuse fac (no longer needed) as the new block
   df* Zn = fac;
-  for (long long idx = tid; idx < N * NW; idx += nt) {
-    const int i = static_cast<int>(idx / NW), c = static_cast<int>(idx % NW);
-    const int src = perm[c];
-    df_acc s = acc_zero();
-    for (int kk = 0; kk < nwant; ++kk) s.fma(Zt[i * NW + kk], Xm[kk * NW + src]);
-    Zn[idx] = s.value();
+  if (maxpos == 0) {
+    // no two shifts within the cluster tolerance: the vectors are accurate
+    // individually (error ~ 48-bit rounding x ||T|| / gap <= 4e-12); their
+    // Rayleigh quotients are the eigenvalues, already in ascending order
+    for (long long idx = tid; idx < N * NW; idx += nt) Zn[idx] = Zt[idx];
+    for (int j = tid; j < nwant; j += nt) {
+      df_acc h = acc_zero();
+      for (int i = 0; i < n; ++i) {
+        df_acc tz = acc_zero();
+        tz.fma(dd[i], Zt[i * NW + j]);
+        if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + j]);
+        if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + j]);
+        h.fma(Zt[i * NW + j], tz.value());
+      }
+      evals[j] = df_to_double(h.value());
+    }
+    __syncthreads();
+  } else {
+    // ---- Rayleigh-Ritz clean-up on span(Zt): S = Z^T Z, Hq = Z^T T Z ---------
+    df* S = rrw;
+    df* Hq = rrw + NW * NW;
+    df* Qm = rrw + 2 * NW * NW;
+    df* Xm = rrw + 3 * NW * NW;
+    for (int idx = tid; idx < nwant * nwant; idx += nt) {
+      const int a0 = idx / nwant, b0 = idx % nwant;
+      if (b0 < a0) continue;
+      df_acc s = acc_zero(), h = acc_zero();
+      for (int i = 0; i < n; ++i) {
+        const df za = Zt[i * NW + a0];
+        const df zb = Zt[i * NW + b0];
+        s.fma(za, zb);
+        df_acc tz = acc_zero();
+        tz.fma(dd[i], zb);
+        if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + b0]);
+        if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + b0]);
+        h.fma(za, tz.value());
+      }
+      S[a0 * NW + b0] = S[b0 * NW + a0] = s.value();
+      Hq[a0 * NW + b0] = Hq[b0 * NW + a0] = h.value();
+    }
+    __syncthreads();
+    // Cholesky S = L L^T in place (lower), right-looking
+    for (int kk = 0; kk < nwant; ++kk) {
+      if (tid == 0) S[kk * NW + kk] = df_sqrt(S[kk * NW + kk]);
+      __syncthreads();
+      const df piv = S[kk * NW + kk];
+      for (int i = kk + 1 + tid; i < nwant; i += nt) S[i * NW + kk] = df_div(S[i * NW + kk], piv);
+      __syncthreads();
+      for (int idx = tid; idx < (nwant - kk - 1) * (nwant - kk - 1); idx += nt) {
+        const int i = kk + 1 + idx / (nwant - kk - 1), jj = kk + 1 + idx % (nwant - kk - 1);
+        if (jj <= i) S[i * NW + jj] = df_sub(S[i * NW + jj], df_mul(S[i * NW + kk], S[jj * NW + kk]));
+      }
+      __syncthreads();
+    }
+    // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int col = tid; col < nwant; col += nt) {
+        for (int i = 0; i < nwant; ++i) {
+          df s = (pass == 0) ? Hq[i * NW + col] : Xm[col * NW + i];
+          for (int kk = 0; kk < i; ++kk)
+            s = df_sub(s, df_mul(S[i * NW + kk], (pass == 0) ? Xm[kk * NW + col] : Qm[kk * NW + col]));
+          const df r = df_div(s, S[i * NW + i]);
+          if (pass == 0) Xm[i * NW + col] = r; else Qm[i * NW + col] = r;
+        }
+      }
+      __syncthreads();
+    }
+    // Qm now holds C (symmetric); move it to Hq and set Qm = I
+    for (int idx = tid; idx < nwant * nwant; idx += nt) {
+      const int a0 = idx / nwant, b0 = idx % nwant;
+      const df cab = Qm[a0 * NW + b0], cba = Qm[b0 * NW + a0];
+      Hq[idx] = df_mul_f(df_add(cab, cba), 0.5f);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nwant * nwant; idx += nt) Qm[idx] = df{(idx / nwant == idx % nwant) ? 1.f : 0.f, 0.f};
+    __syncthreads();
+    // parallel cyclic Jacobi (round-robin pairing) on C, accumulating Q
+    {
+      const int np = (nwant + 1) & ~1;  // even player count; index nwant is a dummy
+      for (int sweep = 0; sweep < 12; ++sweep) {
+        // convergence test: largest off-diagonal entry against the largest diagonal one
+        float off = 0.f, dia = 0.f;
+        for (int idx = tid; idx < nwant * nwant; idx += nt) {
+          const int a0 = idx / nwant, b0 = idx % nwant;
+          const float x = fabsf(Hq[idx].hi);
+          if (a0 == b0) dia = fmaxf(dia, x); else off = fmaxf(off, x);
+        }
+  #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+          dia = fmaxf(dia, __shfl_xor_sync(0xffffffffu, dia, o));
+        }
+        if (lane == 0) {
+          red[warp].s = off;
+          red[warp].c = dia;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          float o2 = 0.f, d2 = 0.f;
+          for (int w2 = 0; w2 < nw; ++w2) {
+            o2 = fmaxf(o2, red[w2].s);
+            d2 = fmaxf(d2, red[w2].c);
+          }
+          sf[0] = o2;
+          sf[1] = d2;
+        }
+        __syncthreads();
+        const float offmax = sf[0], diamax = sf[1];
+        __syncthreads();
+        if (!(offmax > 1.0e-15f * fmaxf(diamax, 1.0e-30f))) break;
+        for (int r = 0; r < np - 1; ++r) {
+          // pair t: players (a, b) of the round-robin schedule
+          for (int t = tid; t < np / 2; t += nt) {
+            int a0 = (t == 0) ? 0 : 1 + (t - 1 + r) % (np - 1);
+            int b0 = 1 + (np - 2 - t + r) % (np - 1);
+            if (a0 > b0) {
+              const int tmpi = a0;
+              a0 = b0;
+              b0 = tmpi;
+            }
+            df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
+            if (b0 < nwant) {
+              const df apq = Hq[a0 * NW + b0];
+              const df app = Hq[a0 * NW + a0], aqq = Hq[b0 * NW + b0];
+              // skip entries already below the float-float resolution of the diagonal
+              const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
+              if (fabsf(apq.hi) > thr) {
+                // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
+                // and t = 1 / (2 theta) once theta^2 would leave the float range
+                const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
+                df tt;
+                if (fabsf(th.hi) > 1.0e12f) {
+                  tt = df_div(df{0.5f, 0.f}, th);
+                } else {
+                  const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
+                  tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
+                  if (df_lt0(th)) tt = df_neg(tt);
+                }
+                cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
+                sn = df_mul(tt, cs);
+              }
+            }
+            // stash rotation in Xm row 0..np/2 (cols 0..3)
+            Xm[t * 4 + 0] = cs;
+            Xm[t * 4 + 1] = sn;
+            reinterpret_cast<int*>(&Xm[t * 4 + 2])[0] = a0;
+            reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
+          }
+          __syncthreads();
+          // rows: C <- J^T C
+          for (int idx = tid; idx < (np / 2) * nwant; idx += nt) {
+            const int t = idx / nwant, col = idx % nwant;
+            const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
+            const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
+            if (b0 >= nwant) continue;
+            const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+            const df x = Hq[a0 * NW + col], y = Hq[b0 * NW + col];
+            Hq[a0 * NW + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
+            Hq[b0 * NW + col] = df_add(df_mul(sn, x), df_mul(cs, y));
+          }
+          __syncthreads();
+          // columns: C <- C J, Q <- Q J
+          for (int idx = tid; idx < (np / 2) * nwant; idx += nt) {
+            const int t = idx / nwant, row = idx % nwant;
+            const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
+            const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
+            if (b0 >= nwant) continue;
+            const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+            df x = Hq[row * NW + a0], y = Hq[row * NW + b0];
+            Hq[row * NW + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+            Hq[row * NW + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+            x = Qm[row * NW + a0];
+            y = Qm[row * NW + b0];
+            Qm[row * NW + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+            Qm[row * NW + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+          }
+          __syncthreads();
+        }
+      }
+    }
+    // order eigenvalues ascending (selection by rank; ties broken by index)
+    for (int j = tid; j < nwant; j += nt) {
+      const df lj = Hq[j * NW + j];
+      int rank = 0;
+      for (int i = 0; i < nwant; ++i) {
+        const df li = Hq[i * NW + i];
+        const df dlt = df_sub(li, lj);
+        if (df_lt0(dlt) || ((dlt.hi == 0.f && dlt.lo == 0.f) && i < j)) ++rank;
+      }
+      perm[rank] = j;
+    }
+    __syncthreads();
+    // Xm = L^-T Q  (back substitution per column)
+    for (int col = tid; col < nwant; col += nt) {
+      for (int i = nwant - 1; i >= 0; --i) {
+        df s = Qm[i * NW + col];
+        for (int kk = i + 1; kk < nwant; ++kk) s = df_sub(s, df_mul(S[kk * NW + i], Xm[kk * NW + col]));
+        Xm[i * NW + col] = df_div(s, S[i * NW + i]);
+      }
+    }
+    __syncthreads();
+    // tridiagonal eigenvectors Zt <- Zt Xm, written in sorted order into Qm-free
+    // storage: reuse fac (no longer needed) as the new block
+    for (long long idx = tid; idx < N * NW; idx += nt) {
+      const int i = static_cast<int>(idx / NW), c = static_cast<int>(idx % NW);
+      const int src = perm[c];
+      df_acc s = acc_zero();
+      for (int kk = 0; kk < nwant; ++kk) s.fma(Zt[i * NW + kk], Xm[kk * NW + src]);
+      Zn[idx] = s.value();
+    }
+    __syncthreads();
+    for (int c = tid; c < nwant; c += nt) evals[c] = df_to_double(Hq[perm[c] * NW + perm[c]]);
   }
-  __syncthreads();
-  for (int c = tid; c < nwant; c += nt) evals[c] = df_to_double(Hq[perm[c] * NW + perm[c]]);
 
   // ---- back-transformation y = H_0 H_1 ... H_{n-3} z ------------------------
   for (int k = n - 3; k >= 0; --k) {

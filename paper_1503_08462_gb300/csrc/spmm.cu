@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
                                                         const float4* __restrict__ b, const float4* __restrict__ x,
                                                         int w4, float4* __restrict__ out1, float4* __restrict__ out2,
                                                         const double* __restrict__ U, double* __restrict__ V, int qv,
-                                                        int G) {
+                                                        int G, const float2* __restrict__ U2 = nullptr,
+                                                        float2* __restrict__ V2 = nullptr) {
   const int rpb = blockDim.x / G;
   const int lane = threadIdx.x % G;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
@@ -324,12 +325,23 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
                                     fmaf(di, res.w, xi.w));
       if (MODE == 1) {
         out1[o] = xn;
-      } else {
+      } else if (MODE == 3) {
         const long long vb = static_cast<long long>(row) * qv + 4 * c4;
         const float xs[4] = {xn.x, xn.y, xn.z, xn.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (4 * c4 + k < qv) V[vb + k] = U[vb + k] + static_cast<double>(xs[k]);
+      } else {
+        // MODE 4: float-float V = U + x
+        const long long vb = static_cast<long long>(row) * qv + 4 * c4;
+        const float xs[4] = {xn.x, xn.y, xn.z, xn.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (4 * c4 + k < qv) {
+            const float2 u = U2[vb + k];
+            const df r = df_add(df{u.x, u.y}, df{xs[k], 0.f});
+            V2[vb + k] = make_float2(r.hi, r.lo);
+          }
       }
     }
   }
@@ -761,6 +773,35 @@ void launch_f32_to_f64_unpad(const float* src, int rows, int q, int ld, double* 
   const long long count = static_cast<long long>(rows) * q;
   ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
   k_unpad_f32_to_f64<<<grid_for(count), kThreads, 0, st>>>(src, rows, q, ld, dst);
+}
+
+void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
+                              const float2* U, float2* V, cudaStream_t st, int qv) {
+  if (A.rows == 0) return;
+  const int w4 = width / 4, G = group_for_f4(w4);
+  const double N = A.rows;
+  ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + (2.0 * 4 + 16.0) * N * width,
+               2.0 * A.nnz * width);
+  k_smooth_f4<4><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
+      A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
+      nullptr, nullptr, nullptr, nullptr, qv, G, U, V);
+}
+
+__global__ void k_add_to_vdf(const float2* __restrict__ U, const float* __restrict__ x, int rows, int q, int ldx,
+                             float2* __restrict__ V) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float2 u = U[i];
+    const df r = df_add(df{u.x, u.y}, df{x[(i / q) * ldx + i % q], 0.f});
+    V[i] = make_float2(r.hi, r.lo);
+  }
+}
+
+void launch_add_to_vdf(const float2* U, const float* x, int rows, int q, int ldx, float2* V, cudaStream_t st) {
+  const long long count = static_cast<long long>(rows) * q;
+  ProfScope ps(st, P_SMOOTH, 20.0 * count, 1.0 * count);
+  k_add_to_vdf<<<grid_for(count), kThreads, 0, st>>>(U, x, rows, q, ldx, V);
 }
 
 }  // namespace amgeig

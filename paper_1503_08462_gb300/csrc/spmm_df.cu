@@ -1,0 +1,424 @@
+// Float-float ("df") sparse kernels of the mixed-precision path.
+//
+// In the mixed path the iterate blocks U, V, W = [AV | MV] and the transfer
+// chains are stored as float-float pairs (float2: hi, lo; 48-bit significand)
+// and every product accumulates with the compensated scheme of common.cuh on
+// the float32 pipes.  The matrix values are split into float-float pairs once,
+// at load.  This replaces float64 FMA, which issues at 1/59 of the float32 rate
+// on this GPU, for the defect (Eq. Linear_Equation), the augmentation products
+// A_k V, M_k V (Algorithm 3.1 step 2), the restriction / prolongation chains
+// I_k^n, I_n^k and the recombination.  Rounding: ~2^-48 relative per
+// operation; the cancellation in lambda M u - A u raises the floor of the
+// relative residual to ~2^-48 lambda_max / lambda (float64: 2^-53 times the same).
+#include "common.cuh"
+#include "kernels.cuh"
+#include "prof.cuh"
+
+namespace amgeig {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ df ld2(const float2* p, long long i) {
+  const float2 v = p[i];
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ void st2(float2* p, long long i, df v) { p[i] = make_float2(v.hi, v.lo); }
+
+struct Geo {
+  int G, rows_per_block, cpt;
+};
+
+Geo geo_for(int width) {
+  int G = 1;
+  while (G < width && G < 32) G <<= 1;
+  int cpt = (width + G - 1) / G;
+  int c = 1;
+  while (c < cpt) c <<= 1;
+  return Geo{G, kThreads / G, c};
+}
+
+// ---------------------------------------------------------------- defect
+// R = lambda o (M U) - A U, rounded to float32 with row stride ldr (zero padding),
+// per-block sums of r^2 and (Mu)^2 in float64 (fixed order)
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                        const float2* __restrict__ a, const float2* __restrict__ m,
+                                                        const float2* __restrict__ U, int q,
+                                                        const double* __restrict__ lam, float* __restrict__ R,
+                                                        int ldr, int G, double* __restrict__ partials) {
+  extern __shared__ double sred[];
+  const int rpb = blockDim.x / G;
+  const int g = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + g;
+  df_acc aa[CPT], mm[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
+  if (row < n) {
+    const int p0 = rp[row], p1 = rp[row + 1];
+    for (int p = p0; p < p1; ++p) {
+      const int j = ci[p];
+      const df av = ld2(a, p), mv = ld2(m, p);
+      const long long base = static_cast<long long>(j) * q;
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        const int c = lane + t * G;
+        if (c < q) {
+          const df u = ld2(U, base + c);
+          aa[t].fma(av, u);
+          mm[t].fma(mv, u);
+        }
+      }
+    }
+  }
+  double rr[CPT], m2[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    rr[t] = 0.0;
+    m2[t] = 0.0;
+    if (row < n && c < q) {
+      const df mu = mm[t].value();
+      const df r = df_sub(df_mul(df_from_double(lam[c]), mu), aa[t].value());
+      const float rf = df_float(r);
+      R[static_cast<long long>(row) * ldr + c] = rf;
+      rr[t] = static_cast<double>(rf) * static_cast<double>(rf);
+      const double md = df_to_double(mu);
+      m2[t] = md * md;
+    }
+  }
+  if (row < n)
+    for (int c = q + lane; c < ldr; c += G) R[static_cast<long long>(row) * ldr + c] = 0.f;
+  if (partials == nullptr) return;
+  const int W = G * CPT;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    sred[g * 2 * W + lane + t * G] = rr[t];
+    sred[g * 2 * W + W + lane + t * G] = m2[t];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * q; idx += blockDim.x) {
+    const int which = idx / q, c = idx % q;
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += sred[r * 2 * W + which * W + c];
+    partials[static_cast<long long>(blockIdx.x) * 2 * q + idx] = s;
+  }
+}
+
+// ---------------------------------------------------------------- W = [A V | M V]
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_dual_spmm_df(int n, const int* __restrict__ rp,
+                                                           const int* __restrict__ ci, const float2* __restrict__ a,
+                                                           const float2* __restrict__ m,
+                                                           const float2* __restrict__ V, int q,
+                                                           float2* __restrict__ W, int G) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  df_acc aa[CPT], mm[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = ci[p];
+    const df av = ld2(a, p), mv = ld2(m, p);
+    const long long base = static_cast<long long>(j) * q;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < q) {
+        const df v = ld2(V, base + c);
+        aa[t].fma(av, v);
+        mm[t].fma(mv, v);
+      }
+    }
+  }
+  const long long o = static_cast<long long>(row) * 2 * q;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < q) {
+      st2(W, o + c, aa[t].value());
+      st2(W, o + q + c, mm[t].value());
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Y (+)= S X
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_spmm_df(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                      const float2* __restrict__ v, const float2* __restrict__ X,
+                                                      int width, float2* __restrict__ Y, int G, int accumulate) {
+  const int rpb = blockDim.x / G;
+  const int lane = threadIdx.x % G;
+  const int row = blockIdx.x * rpb + threadIdx.x / G;
+  if (row >= n) return;
+  df_acc acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) acc[t] = acc_zero();
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const df s = ld2(v, p);
+    const long long base = static_cast<long long>(ci[p]) * width;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < width) acc[t].fma(s, ld2(X, base + c));
+    }
+  }
+  const long long o = static_cast<long long>(row) * width;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < width) {
+      if (accumulate) acc[t].add(ld2(Y, o + c));
+      st2(Y, o + c, acc[t].value());
+    }
+  }
+}
+
+// ---------------------------------------------------------------- U = Xp + V Y
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) k_recombine_df2(int n, const float2* __restrict__ Xp,
+                                                            const float2* __restrict__ V,
+                                                            const double* __restrict__ Y, int q,
+                                                            float2* __restrict__ U, int G) {
+  extern __shared__ df dsm[];  // Y (q x q) then the block's V rows
+  df* ys = dsm;
+  df* vs = dsm + q * q;
+  const int rpb = blockDim.x / G;
+  for (int i = threadIdx.x; i < q * q; i += blockDim.x) ys[i] = df_from_double(Y[i]);
+  const long long row0 = static_cast<long long>(blockIdx.x) * rpb;
+  for (int i = threadIdx.x; i < rpb * q; i += blockDim.x) {
+    const long long r = row0 + i / q;
+    vs[i] = (r < n) ? ld2(V, r * q + i % q) : df{0.f, 0.f};
+  }
+  __syncthreads();
+  const int g = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const long long row = row0 + g;
+  if (row >= n) return;
+  const long long base = row * q;
+  df_acc acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    acc[t] = acc_zero();
+    if (c < q) acc[t].add(ld2(Xp, base + c));
+  }
+  const df* vr = vs + g * q;
+  for (int d = 0; d < q; ++d) {
+    const df v = vr[d];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < q) acc[t].fma(v, ys[d * q + c]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c = lane + t * G;
+    if (c < q) st2(U, base + c, acc[t].value());
+  }
+}
+
+// ---------------------------------------------------------------- Gram V^T W (df inputs)
+constexpr int kGT = 32;
+constexpr int kGramRows = 32;
+
+__global__ void __launch_bounds__(256) k_gram_df(int rows, const float2* __restrict__ V, int q,
+                                                 const float2* __restrict__ W, int w, int chunk_rows, int tiles_w,
+                                                 double* __restrict__ part) {
+  __shared__ df Vs[kGramRows][kGT + 1];
+  __shared__ df Ws[kGramRows][kGT + 1];
+  const int chunk = blockIdx.x;
+  const int ta = blockIdx.y / tiles_w, tb = blockIdx.y % tiles_w;
+  const int a0 = ta * kGT, b0 = tb * kGT;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  df_acc acc[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc[s] = acc_zero();
+  const int r0 = chunk * chunk_rows;
+  const int r1 = min(rows, r0 + chunk_rows);
+  for (int rb = r0; rb < r1; rb += kGramRows) {
+    for (int idx = threadIdx.x; idx < kGramRows * kGT; idx += blockDim.x) {
+      const int rr = idx / kGT, cc = idx % kGT;
+      const int r = rb + rr;
+      Vs[rr][cc] = (r < r1 && a0 + cc < q) ? ld2(V, static_cast<long long>(r) * q + a0 + cc) : df{0.f, 0.f};
+      Ws[rr][cc] = (r < r1 && b0 + cc < w) ? ld2(W, static_cast<long long>(r) * w + b0 + cc) : df{0.f, 0.f};
+    }
+    __syncthreads();
+    const int nr = min(kGramRows, r1 - rb);
+    for (int rr = 0; rr < nr; ++rr) {
+      const df wv = Ws[rr][tx];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) acc[s].fma(Vs[rr][ty * 4 + s], wv);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int a = a0 + ty * 4 + s, b = b0 + tx;
+    if (a < q && b < w) part[(static_cast<long long>(chunk) * q + a) * w + b] = df_to_double(acc[s].value());
+  }
+}
+
+int gram_chunks_df(int rows, int q, int w, int* chunk_rows) {
+  const int tiles = ceil_div(q, kGT) * ceil_div(w, kGT);
+  int chunks = ceil_div(rows, 256);
+  const int cap = (4 * kNumSms + tiles - 1) / tiles;
+  if (chunks > cap) chunks = cap;
+  if (chunks < 1) chunks = 1;
+  int cr = ceil_div(rows, chunks);
+  cr = ceil_div(cr, kGramRows) * kGramRows;
+  if (cr < kGramRows) cr = kGramRows;
+  *chunk_rows = cr;
+  return ceil_div(rows, cr) > 0 ? ceil_div(rows, cr) : 1;
+}
+
+// ---------------------------------------------------------------- conversions
+__global__ void k_f64_to_df(const double* __restrict__ x, long long count, float2* __restrict__ y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const df d = df_from_double(x[i]);
+    y[i] = make_float2(d.hi, d.lo);
+  }
+}
+
+__global__ void k_df_to_f64(const float2* __restrict__ x, long long count, double* __restrict__ y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float2 v = x[i];
+    y[i] = static_cast<double>(v.x) + static_cast<double>(v.y);
+  }
+}
+
+// first columns of a row-major (rows x ld) float64 matrix into a rows x q df block
+__global__ void k_cols_to_df(const double* __restrict__ src, int rows, int ld, int q, float2* __restrict__ dst) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const df d = df_from_double(src[(i / q) * ld + i % q]);
+    dst[i] = make_float2(d.hi, d.lo);
+  }
+}
+
+int grid_for(long long count) {
+  long long b = (count + kThreads - 1) / kThreads;
+  if (b > 8LL * kNumSms) b = 8LL * kNumSms;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+#define AMGEIG_DISPATCH(cpt, KERNEL, ...) \
+  switch (cpt) {                          \
+    case 1:                               \
+      KERNEL<1> __VA_ARGS__;              \
+      break;                              \
+    case 2:                               \
+      KERNEL<2> __VA_ARGS__;              \
+      break;                              \
+    case 4:                               \
+      KERNEL<4> __VA_ARGS__;              \
+      break;                              \
+    case 8:                               \
+      KERNEL<8> __VA_ARGS__;              \
+      break;                              \
+    default:                              \
+      break;                              \
+  }
+
+}  // namespace
+
+void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* lam, float* R, int ldr,
+                      double* partials, int* nblocks_out, cudaStream_t st) {
+  Geo g = geo_for(q);
+  const int blocks = ceil_div(AM.rows, g.rows_per_block);
+  if (nblocks_out) *nblocks_out = blocks;
+  const size_t sm = partials ? sizeof(double) * g.rows_per_block * 2 * g.G * g.cpt : 0;
+  const double N = AM.rows, nnz = AM.nnz;
+  ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 4.0 * N * ldr, 4.0 * nnz * q);
+  AMGEIG_DISPATCH(g.cpt, k_defect_df,
+                  <<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, U, q, lam, R, ldr, g.G,
+                                                 partials))
+}
+
+void launch_dual_spmm_df(const DevCsr& AM, const float2* V, int q, float2* W, cudaStream_t st) {
+  Geo g = geo_for(q);
+  const int blocks = ceil_div(AM.rows, g.rows_per_block);
+  const double N = AM.rows, nnz = AM.nnz;
+  ProfScope ps(st, P_AUGMENT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 16.0 * N * q, 4.0 * nnz * q);
+  AMGEIG_DISPATCH(g.cpt, k_dual_spmm_df,
+                  <<<blocks, kThreads, 0, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, V, q, W, g.G))
+}
+
+void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool accumulate, cudaStream_t st,
+                    int cls) {
+  if (S.rows == 0 || width == 0) return;
+  Geo g = geo_for(width);
+  const int blocks = ceil_div(S.rows, g.rows_per_block);
+  ProfScope ps(st, cls,
+               4.0 * (S.rows + 1) + 12.0 * S.nnz + 8.0 * S.cols * width + 8.0 * S.rows * width * (accumulate ? 2 : 1),
+               2.0 * S.nnz * width);
+  AMGEIG_DISPATCH(g.cpt, k_spmm_df,
+                  <<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.d2, X, width, Y, g.G, accumulate ? 1 : 0))
+}
+
+void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
+                         cudaStream_t st) {
+  Geo g = geo_for(q);
+  const int blocks = ceil_div(rows, g.rows_per_block);
+  ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
+  const size_t sm = sizeof(df) * (static_cast<size_t>(q) * q + static_cast<size_t>(g.rows_per_block) * q);
+  switch (g.cpt) {
+#define AMGEIG_CASE(C)                                                                              \
+  case C:                                                                                           \
+    if (sm > 48 * 1024)                                                                             \
+      cudaFuncSetAttribute(k_recombine_df2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    k_recombine_df2<C><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U, g.G);                      \
+    break;
+    AMGEIG_CASE(1)
+    AMGEIG_CASE(2)
+    AMGEIG_CASE(4)
+    AMGEIG_CASE(8)
+#undef AMGEIG_CASE
+    default:
+      break;
+  }
+}
+
+size_t gram_df_scratch_doubles(int rows, int q, int w) {
+  int cr;
+  return static_cast<size_t>(gram_chunks_df(rows, q, w, &cr)) * q * w;
+}
+
+void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, double* scratch, double* G,
+                    cudaStream_t st) {
+  if (q <= 0 || w <= 0) return;
+  int cr;
+  const int chunks = gram_chunks_df(rows, q, w, &cr);
+  const int tiles_w = ceil_div(w, kGT);
+  dim3 grid(chunks, ceil_div(q, kGT) * tiles_w);
+  ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks * q * w, 2.0 * rows * q * w);
+  k_gram_df<<<grid, 256, 0, st>>>(rows, V, q, W, w, cr, tiles_w, scratch);
+  launch_sum_partials(scratch, chunks, q * w, G, st);
+}
+
+void launch_f64_to_df(const double* x, long long count, float2* y, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 16.0 * count, 0.0);
+  k_f64_to_df<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+void launch_df_to_f64(const float2* x, long long count, double* y, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 16.0 * count, 0.0);
+  k_df_to_f64<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+void launch_cols_to_df(const double* src, int rows, int ld, int q, float2* dst, cudaStream_t st) {
+  const long long total = static_cast<long long>(rows) * q;
+  ProfScope ps(st, P_OTHER, 16.0 * total, 0.0);
+  k_cols_to_df<<<grid_for(total), kThreads, 0, st>>>(src, rows, ld, q, dst);
+}
+
+}  // namespace amgeig
