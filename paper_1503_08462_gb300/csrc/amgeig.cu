@@ -320,7 +320,10 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->C, static_cast<size_t>(h->dn) * 2 * qt));
   CK(m.alloc(&w->G, static_cast<size_t>(qt) * 2 * qt));
   size_t gs = 0;
-  for (int l = 0; l < n; ++l) gs = std::max(gs, gram_scratch_doubles(static_cast<int>(h->sizes[l]), qt, 2 * qt));
+  for (int l = 0; l < n; ++l) {
+    gs = std::max(gs, gram_scratch_doubles(static_cast<int>(h->sizes[l]), qt, 2 * qt));
+    gs = std::max(gs, gram_df_scratch_doubles(static_cast<int>(h->sizes[l]), qt, 2 * qt));
+  }
   CK(m.alloc(&w->gsc, gs));
   CK(m.alloc(&w->Xc, static_cast<size_t>(h->dn) * qt));
   CK(m.alloc(&w->Yv, static_cast<size_t>(qt) * qt));

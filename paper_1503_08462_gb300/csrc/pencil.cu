@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   __syncthreads();
   // clusters of nearly equal shifts are iterated in rounds with Gram-Schmidt
   if (tid == 0) {
-    const float ctol = 1.0e-3f * tnorm;
+    const float ctol = 1.0e-4f * tnorm;
     int maxpos = 0;
     for (int j = 0; j < nwant; ++j) {
       if (j > 0 && shift[j] - shift[j - 1] <= ctol) {
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   df* Zn = fac;
   if (maxpos == 0) {
     // no two shifts within the cluster tolerance: the vectors are accurate
-    // individually (error ~ 48-bit rounding x ||T|| / gap <= 4e-12); their
+    // individually (error ~ 48-bit rounding x ||T|| / gap <= 4e-11); their
     // Rayleigh quotients are the eigenvalues, already in ascending order
     for (long long idx = tid; idx < N * NW; idx += nt) Zn[idx] = Zt[idx];
     for (int j = tid; j < nwant; j += nt) {

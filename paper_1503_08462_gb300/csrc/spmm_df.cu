@@ -47,15 +47,24 @@ __global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __rest
                                                         const float2* __restrict__ U, int q,
                                                         const double* __restrict__ lam, float* __restrict__ R,
                                                         int ldr, int G, double* __restrict__ partials) {
+  // grid-stride over row groups; each thread keeps its columns' sums of r^2 and
+  // (Mu)^2 in registers, so a block writes one row of partials
   extern __shared__ double sred[];
   const int rpb = blockDim.x / G;
   const int g = threadIdx.x / G;
   const int lane = threadIdx.x % G;
-  const int row = blockIdx.x * rpb + g;
-  df_acc aa[CPT], mm[CPT];
+  double rr[CPT], m2[CPT];
+  df lamc[CPT];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
-  if (row < n) {
+  for (int t = 0; t < CPT; ++t) {
+    rr[t] = m2[t] = 0.0;
+    const int c = lane + t * G;
+    lamc[t] = c < q ? df_from_double(lam[c]) : df{0.f, 0.f};
+  }
+  for (int row = blockIdx.x * rpb + g; row < n; row += gridDim.x * rpb) {
+    df_acc aa[CPT], mm[CPT];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
     const int p0 = rp[row], p1 = rp[row + 1];
     for (int p = p0; p < p1; ++p) {
       const int j = ci[p];
@@ -71,25 +80,21 @@ __global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __rest
         }
       }
     }
-  }
-  double rr[CPT], m2[CPT];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) {
-    const int c = lane + t * G;
-    rr[t] = 0.0;
-    m2[t] = 0.0;
-    if (row < n && c < q) {
-      const df mu = mm[t].value();
-      const df r = df_sub(df_mul(df_from_double(lam[c]), mu), aa[t].value());
-      const float rf = df_float(r);
-      R[static_cast<long long>(row) * ldr + c] = rf;
-      rr[t] = static_cast<double>(rf) * static_cast<double>(rf);
-      const double md = df_to_double(mu);
-      m2[t] = md * md;
+    for (int t = 0; t < CPT; ++t) {
+      const int c = lane + t * G;
+      if (c < q) {
+        const df mu = mm[t].value();
+        const df r = df_sub(df_mul(lamc[t], mu), aa[t].value());
+        const float rf = df_float(r);
+        R[static_cast<long long>(row) * ldr + c] = rf;
+        rr[t] = fma(static_cast<double>(rf), static_cast<double>(rf), rr[t]);
+        const double md = df_to_double(mu);
+        m2[t] = fma(md, md, m2[t]);
+      }
     }
-  }
-  if (row < n)
     for (int c = q + lane; c < ldr; c += G) R[static_cast<long long>(row) * ldr + c] = 0.f;
+  }
   if (partials == nullptr) return;
   const int W = G * CPT;
 #pragma unroll
@@ -225,14 +230,100 @@ __global__ void __launch_bounds__(kThreads) k_recombine_df2(int n, const float2*
 }
 
 // ---------------------------------------------------------------- Gram V^T W (df inputs)
-constexpr int kGT = 32;
-constexpr int kGramRows = 32;
+// G = V^T [A V | M V] (q x 2q).  Both halves are symmetric, so only the pairs
+// a <= b of each half are formed: np = q (q + 1) pairs.  A block stages a slab
+// of rows of V and W in shared memory; thread t owns pairs t, t + blockDim, ...
+constexpr int kGramRows = 16;
+constexpr int kGramThreads = 320;
+constexpr int kGramMaxPairs = 4;  // pairs per thread: q (q+1) <= 4 * 320 -> q <= 35
 
+__device__ __forceinline__ void pair_of(int idx, int q, int* half, int* a, int* b) {
+  // idx in [0, q(q+1)): half = idx / T, then the (a, b) with a <= b of the upper triangle
+  const int T = q * (q + 1) / 2;
+  *half = idx >= T;
+  int r = idx - (*half) * T;
+  int row = 0;
+  while (r >= q - row) {
+    r -= q - row;
+    ++row;
+  }
+  *a = row;
+  *b = row + r;
+}
+
+__global__ void __launch_bounds__(kGramThreads) k_gram_df_sym(int rows, const float2* __restrict__ V, int q,
+                                                              const float2* __restrict__ W, int chunk_rows,
+                                                              double* __restrict__ part) {
+  extern __shared__ df gsm[];
+  df* Vs = gsm;                  // kGramRows x q
+  df* Ws = gsm + kGramRows * q;  // kGramRows x 2q
+  const int np = q * (q + 1);
+  int pa[kGramMaxPairs], pb[kGramMaxPairs];
+  df_acc acc[kGramMaxPairs];
+#pragma unroll
+  for (int s = 0; s < kGramMaxPairs; ++s) {
+    const int idx = threadIdx.x + s * blockDim.x;
+    acc[s] = acc_zero();
+    pa[s] = -1;
+    pb[s] = 0;
+    if (idx < np) {
+      int half, a, b;
+      pair_of(idx, q, &half, &a, &b);
+      pa[s] = a;
+      pb[s] = b + half * q;
+    }
+  }
+  const int r0 = blockIdx.x * chunk_rows;
+  const int r1 = min(rows, r0 + chunk_rows);
+  for (int rb = r0; rb < r1; rb += kGramRows) {
+    const int nr = min(kGramRows, r1 - rb);
+    for (int i = threadIdx.x; i < nr * q; i += blockDim.x) Vs[i] = ld2(V, static_cast<long long>(rb) * q + i);
+    for (int i = threadIdx.x; i < nr * 2 * q; i += blockDim.x)
+      Ws[i] = ld2(W, static_cast<long long>(rb) * 2 * q + i);
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+#pragma unroll
+      for (int s = 0; s < kGramMaxPairs; ++s)
+        if (pa[s] >= 0) acc[s].fma(Vs[rr * q + pa[s]], Ws[rr * 2 * q + pb[s]]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < kGramMaxPairs; ++s) {
+    const int idx = threadIdx.x + s * blockDim.x;
+    if (idx < np) part[static_cast<long long>(blockIdx.x) * np + idx] = df_to_double(acc[s].value());
+  }
+}
+
+// G (q x 2q) from the summed pairs, mirrored
+__global__ void k_gram_unpack(const double* __restrict__ sums, int q, double* __restrict__ G) {
+  const int np = q * (q + 1);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < np; idx += gridDim.x * blockDim.x) {
+    int half, a, b;
+    pair_of(idx, q, &half, &a, &b);
+    const double v = sums[idx];
+    G[a * 2 * q + half * q + b] = v;
+    G[b * 2 * q + half * q + a] = v;
+  }
+}
+
+int gram_chunks_df(int rows, int* chunk_rows) {
+  int chunks = ceil_div(rows, 512);
+  if (chunks > 4 * kNumSms) chunks = 4 * kNumSms;
+  if (chunks < 1) chunks = 1;
+  int cr = ceil_div(rows, chunks);
+  cr = ceil_div(cr, kGramRows) * kGramRows;
+  *chunk_rows = cr;
+  return ceil_div(rows, cr) > 0 ? ceil_div(rows, cr) : 1;
+}
+
+// general (non-symmetric-friendly) fallback for q > 35: 32 x 32 output tiles
+constexpr int kGT = 32;
 __global__ void __launch_bounds__(256) k_gram_df(int rows, const float2* __restrict__ V, int q,
                                                  const float2* __restrict__ W, int w, int chunk_rows, int tiles_w,
                                                  double* __restrict__ part) {
-  __shared__ df Vs[kGramRows][kGT + 1];
-  __shared__ df Ws[kGramRows][kGT + 1];
+  __shared__ df Vs[32][kGT + 1];
+  __shared__ df Ws[32][kGT + 1];
   const int chunk = blockIdx.x;
   const int ta = blockIdx.y / tiles_w, tb = blockIdx.y % tiles_w;
   const int a0 = ta * kGT, b0 = tb * kGT;
@@ -242,15 +333,15 @@ __global__ void __launch_bounds__(256) k_gram_df(int rows, const float2* __restr
   for (int s = 0; s < 4; ++s) acc[s] = acc_zero();
   const int r0 = chunk * chunk_rows;
   const int r1 = min(rows, r0 + chunk_rows);
-  for (int rb = r0; rb < r1; rb += kGramRows) {
-    for (int idx = threadIdx.x; idx < kGramRows * kGT; idx += blockDim.x) {
+  for (int rb = r0; rb < r1; rb += 32) {
+    for (int idx = threadIdx.x; idx < 32 * kGT; idx += blockDim.x) {
       const int rr = idx / kGT, cc = idx % kGT;
       const int r = rb + rr;
       Vs[rr][cc] = (r < r1 && a0 + cc < q) ? ld2(V, static_cast<long long>(r) * q + a0 + cc) : df{0.f, 0.f};
       Ws[rr][cc] = (r < r1 && b0 + cc < w) ? ld2(W, static_cast<long long>(r) * w + b0 + cc) : df{0.f, 0.f};
     }
     __syncthreads();
-    const int nr = min(kGramRows, r1 - rb);
+    const int nr = min(32, r1 - rb);
     for (int rr = 0; rr < nr; ++rr) {
       const df wv = Ws[rr][tx];
 #pragma unroll
@@ -263,19 +354,6 @@ __global__ void __launch_bounds__(256) k_gram_df(int rows, const float2* __restr
     const int a = a0 + ty * 4 + s, b = b0 + tx;
     if (a < q && b < w) part[(static_cast<long long>(chunk) * q + a) * w + b] = df_to_double(acc[s].value());
   }
-}
-
-int gram_chunks_df(int rows, int q, int w, int* chunk_rows) {
-  const int tiles = ceil_div(q, kGT) * ceil_div(w, kGT);
-  int chunks = ceil_div(rows, 256);
-  const int cap = (4 * kNumSms + tiles - 1) / tiles;
-  if (chunks > cap) chunks = cap;
-  if (chunks < 1) chunks = 1;
-  int cr = ceil_div(rows, chunks);
-  cr = ceil_div(cr, kGramRows) * kGramRows;
-  if (cr < kGramRows) cr = kGramRows;
-  *chunk_rows = cr;
-  return ceil_div(rows, cr) > 0 ? ceil_div(rows, cr) : 1;
 }
 
 // ---------------------------------------------------------------- conversions
@@ -334,7 +412,8 @@ int grid_for(long long count) {
 void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* lam, float* R, int ldr,
                       double* partials, int* nblocks_out, cudaStream_t st) {
   Geo g = geo_for(q);
-  const int blocks = ceil_div(AM.rows, g.rows_per_block);
+  int blocks = ceil_div(AM.rows, g.rows_per_block);
+  if (blocks > 8 * kNumSms) blocks = 8 * kNumSms;
   if (nblocks_out) *nblocks_out = blocks;
   const size_t sm = partials ? sizeof(double) * g.rows_per_block * 2 * g.G * g.cpt : 0;
   const double N = AM.rows, nnz = AM.nnz;
@@ -390,14 +469,26 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
 
 size_t gram_df_scratch_doubles(int rows, int q, int w) {
   int cr;
-  return static_cast<size_t>(gram_chunks_df(rows, q, w, &cr)) * q * w;
+  const size_t chunks = static_cast<size_t>(gram_chunks_df(rows, &cr));
+  // symmetric kernel: chunks x q(q+1) partials + q(q+1) sums; tiled kernel: chunks x q x w
+  return chunks * q * w + static_cast<size_t>(q) * (q + 1);
 }
 
 void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, double* scratch, double* G,
                     cudaStream_t st) {
   if (q <= 0 || w <= 0) return;
   int cr;
-  const int chunks = gram_chunks_df(rows, q, w, &cr);
+  const int chunks = gram_chunks_df(rows, &cr);
+  if (w == 2 * q && q * (q + 1) <= kGramMaxPairs * kGramThreads) {
+    const int np = q * (q + 1);
+    ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks * np, 1.0 * rows * np * 2.0);
+    const size_t sm = sizeof(df) * kGramRows * 3 * q;
+    k_gram_df_sym<<<chunks, kGramThreads, sm, st>>>(rows, V, q, W, cr, scratch);
+    double* sums = scratch + static_cast<size_t>(chunks) * np;
+    launch_sum_partials(scratch, chunks, np, sums, st);
+    k_gram_unpack<<<ceil_div(np, 256), 256, 0, st>>>(sums, q, G);
+    return;
+  }
   const int tiles_w = ceil_div(w, kGT);
   dim3 grid(chunks, ceil_div(q, kGT) * tiles_w);
   ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks * q * w, 2.0 * rows * q * w);
