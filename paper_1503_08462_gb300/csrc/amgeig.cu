@@ -45,35 +45,62 @@ int fail(int code, const std::string& msg) {
 
 // ------------------------------------------------------------------ small kernels
 
-// per-column (max |u|, lowest index) over rows; one block per column
-__global__ void k_col_sign(const double* __restrict__ U, int rows, int ld, int q, double* __restrict__ sign) {
-  const int c = blockIdx.x;
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    const double a = fabs(U[static_cast<long long>(i) * ld + c]);
-    if (a > best || (a == best && i < bi)) {
-      best = a;
-      bi = i;
-    }
-  }
-  __shared__ double sb[256];
-  __shared__ int si[256];
-  sb[threadIdx.x] = best;
-  si[threadIdx.x] = bi;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      const double b2 = sb[threadIdx.x + s];
-      const int i2 = si[threadIdx.x + s];
-      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
-        sb[threadIdx.x] = b2;
-        si[threadIdx.x] = i2;
+// per-column (max |u|, lowest index) over rows, stage 1: each block scans a slab
+// of rows for all q columns (coalesced along the row) and writes its best entry
+// per column; stage 2 picks the best slab per column and the sign
+__global__ void k_col_best(const double* __restrict__ U, int rows, int ld, int q, int slab, double* __restrict__ bval,
+                           int* __restrict__ bidx) {
+  __shared__ double sb[8][32];
+  __shared__ int si[8][32];
+  const int r0 = blockIdx.x * slab, r1 = min(rows, r0 + slab);
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32, nwarp = blockDim.x / 32;
+  for (int c0 = 0; c0 < q; c0 += 32) {  // uniform trip count: barriers below are reached by all
+    const int c = c0 + lane;
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    if (c < q) {
+      for (int i = r0 + wid; i < r1; i += nwarp) {
+        const double a = fabs(U[static_cast<long long>(i) * ld + c]);
+        if (a > best || (a == best && i < bi)) {
+          best = a;
+          bi = i;
+        }
       }
+    }
+    sb[wid][lane] = best;
+    si[wid][lane] = bi;
+    __syncthreads();
+    if (wid == 0 && c < q) {
+      for (int w = 1; w < nwarp; ++w) {
+        const double b2 = sb[w][lane];
+        const int i2 = si[w][lane];
+        if (b2 > best || (b2 == best && i2 < bi)) {
+          best = b2;
+          bi = i2;
+        }
+      }
+      bval[static_cast<long long>(blockIdx.x) * q + c] = best;
+      bidx[static_cast<long long>(blockIdx.x) * q + c] = bi;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) sign[c] = (si[0] < rows && U[static_cast<long long>(si[0]) * ld + c] < 0.0) ? -1.0 : 1.0;
+}
+
+__global__ void k_col_sign2(const double* __restrict__ U, int ld, int q, int nslabs, const double* __restrict__ bval,
+                            const int* __restrict__ bidx, double* __restrict__ sign) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= q) return;
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int s = 0; s < nslabs; ++s) {
+    const double b2 = bval[static_cast<long long>(s) * q + c];
+    const int i2 = bidx[static_cast<long long>(s) * q + c];
+    if (b2 > best || (b2 == best && i2 < bi)) {
+      best = b2;
+      bi = i2;
+    }
+  }
+  sign[c] = (bi != 0x7fffffff && U[static_cast<long long>(bi) * ld + c] < 0.0) ? -1.0 : 1.0;
 }
 
 __global__ void k_out_vectors(const double* __restrict__ U, int rows, int ld, int q, const double* __restrict__ sign,
@@ -663,8 +690,15 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
     }
     double* dst = on_device ? eigvecs : w->Ualt;  // Ualt is free after the solve
     const long long total = static_cast<long long>(N0) * q;
-    ProfScope ps(st, P_OTHER, 8.0 * N0 * qt + 16.0 * total, 0.0, 2);
-    k_col_sign<<<q, 256, 0, st>>>(src, N0, qt, q, w->sign);
+    ProfScope ps(st, P_OTHER, 8.0 * N0 * qt + 16.0 * total, 0.0, 3);
+    {
+      const int slab = 4096, nslabs = ceil_div(N0, slab);
+      // the slab results live in W, free after the solve (nslabs * q <= N0 * 2q)
+      double* bval = w->W;
+      int* bidx = reinterpret_cast<int*>(w->W + static_cast<size_t>(nslabs) * q);
+      k_col_best<<<nslabs, 256, 0, st>>>(src, N0, qt, q, slab, bval, bidx);
+      k_col_sign2<<<ceil_div(q, 128), 128, 0, st>>>(src, qt, q, nslabs, bval, bidx, w->sign);
+    }
     k_out_vectors<<<static_cast<int>(std::min<long long>((total + 255) / 256, 8LL * kNumSms)), 256, 0, st>>>(
         src, N0, qt, q, w->sign, dst);
     CK(cudaGetLastError());

@@ -29,13 +29,18 @@ struct Geo {
   int G, rows_per_block, cpt;
 };
 
+// G lanes per row with CPT = ceil(width / G) <= 8 columns each: about three
+// columns per lane gives each thread independent accumulation chains and cuts
+// the redundant index / value loads of a 32-lane row group
 Geo geo_for(int width) {
   int G = 1;
-  while (G < width && G < 32) G <<= 1;
+  while (G * 2 <= width / 3 && G < 32) G <<= 1;
   int cpt = (width + G - 1) / G;
-  int c = 1;
-  while (c < cpt) c <<= 1;
-  return Geo{G, kThreads / G, c};
+  while (cpt > 8) {
+    G <<= 1;
+    cpt = (width + G - 1) / G;
+  }
+  return Geo{G, kThreads / G, cpt};
 }
 
 // ---------------------------------------------------------------- defect
@@ -397,8 +402,20 @@ int grid_for(long long count) {
     case 2:                               \
       KERNEL<2> __VA_ARGS__;              \
       break;                              \
+    case 3:                               \
+      KERNEL<3> __VA_ARGS__;              \
+      break;                              \
     case 4:                               \
       KERNEL<4> __VA_ARGS__;              \
+      break;                              \
+    case 5:                               \
+      KERNEL<5> __VA_ARGS__;              \
+      break;                              \
+    case 6:                               \
+      KERNEL<6> __VA_ARGS__;              \
+      break;                              \
+    case 7:                               \
+      KERNEL<7> __VA_ARGS__;              \
       break;                              \
     case 8:                               \
       KERNEL<8> __VA_ARGS__;              \
@@ -459,7 +476,11 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
     break;
     AMGEIG_CASE(1)
     AMGEIG_CASE(2)
+    AMGEIG_CASE(3)
     AMGEIG_CASE(4)
+    AMGEIG_CASE(5)
+    AMGEIG_CASE(6)
+    AMGEIG_CASE(7)
     AMGEIG_CASE(8)
 #undef AMGEIG_CASE
     default:
