@@ -167,8 +167,9 @@ void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* M
 // Symmetric eigensolver in float-float: the `nwant` smallest eigenpairs of the
 // symmetric n x n row-major float64 matrix H.  evals (nwant), evecs (n x nwant
 // row-major).  Exposed for the kernel-level tests.
+// skip (device, may be null): when *skip != 0 at run time the kernel returns at once
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
-                    cudaStream_t st);
+                    cudaStream_t st, const int* skip = nullptr);
 
 // The same eigensolver on caller-provided workspace (device pointers sized as in
 // pencil_work_create for nmax >= n + 1 and nwant_max >= nwant); enqueues only.

@@ -67,6 +67,11 @@ struct PencilWork {
   // coarse decomposition
   double* Lm = nullptr;  // dn x dn
   double* Hs = nullptr;  // dn x dn
+  // structured Rayleigh quotient iteration
+  double* sr_mu = nullptr;  // qmax
+  double* sr_X = nullptr;   // nmax x qmax
+  int* sr_conv = nullptr;   // qmax
+  int* sr_flag = nullptr;   // 1
 };
 
 namespace {
@@ -101,7 +106,8 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
                                                         df* __restrict__ tau_g, df* __restrict__ dd_g,
                                                         df* __restrict__ ee_g, df* __restrict__ facg,
                                                         df* __restrict__ Ztg, df* __restrict__ rrw,
-                                                        int* __restrict__ perm) {
+                                                        int* __restrict__ perm, const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;  // the structured fast path already produced the pairs
   extern __shared__ __align__(16) unsigned char smem_raw[];
   df* v = reinterpret_cast<df*>(smem_raw);
   df* p = v + n;
@@ -624,6 +630,328 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   for (long long idx = tid; idx < N * NW; idx += nt) evecs[idx] = df_to_double(Zn[idx]);
 }
 
+// ------------------------------------------------------------ structured Rayleigh quotient iteration
+//
+// Fast path for the reduced pencil H = [[Theta, F], [F^T, T]] (Theta diagonal,
+// m x m; border q): Rayleigh quotient iteration for each wanted pair in its
+// own block, with (H - s I) y = x solved through the Schur complement
+//   S(s) = T - s I - F^T (Theta - s I)^-1 F   (q x q, Gaussian elimination with
+// partial pivoting), starting from the current iterates written in the basis
+// of H (column j of V is [B e_j; L^T e_j] there).  k_srqi_check then accepts
+// the result only if every iteration converged, the vectors are mutually
+// orthogonal, and Sylvester's inertia of H - s* I just above the largest value
+// counts exactly q eigenvalues below (inertia(Theta - s) + inertia(S(s)),
+// Haynsworth), i.e. the pairs found are the q smallest; otherwise the dense
+// float-float eigensolver runs.  Golub & Van Loan 8.2.3 (RQI), 4.4 (inertia).
+constexpr int kSrqiThreads = 256;
+constexpr int kSrqiMaxQ = 64;
+constexpr int kSrqiMaxIt = 8;
+
+// Solve S y = r in place (S: q x (q+1) augmented, row-major, shared) by GEPP;
+// the solution is left in column q.
+__device__ void gepp_solve(df* S, int q, int* piv_shared) {
+  const int ld = q + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < q; ++k) {
+    if (tid < 32) {
+      float best = -1.f;
+      int bi = k;
+      for (int i = k + tid; i < q; i += 32) {
+        const float a = fabsf(S[i * ld + k].hi);
+        if (a > best) {
+          best = a;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (b2 > best || (b2 == best && i2 < bi)) {
+          best = b2;
+          bi = i2;
+        }
+      }
+      if (tid == 0) *piv_shared = bi;
+    }
+    __syncthreads();
+    const int pr = *piv_shared;
+    if (pr != k)
+      for (int j = k + tid; j <= q; j += nt) {
+        const df t = S[k * ld + j];
+        S[k * ld + j] = S[pr * ld + j];
+        S[pr * ld + j] = t;
+      }
+    __syncthreads();
+    df pivv = S[k * ld + k];
+    if (fabsf(pivv.hi) < 1.0e-30f) pivv = df{1.0e-30f, 0.f};
+    const df rinv = df_div(df{1.f, 0.f}, pivv);
+    const int rows = q - k - 1, cols = q - k;  // columns k+1..q
+    for (int idx = tid; idx < rows * cols; idx += nt) {
+      const int i = k + 1 + idx / cols, j = k + 1 + idx % cols;
+      const df l = df_mul(S[i * ld + k], rinv);
+      S[i * ld + j] = df_sub(S[i * ld + j], df_mul(l, S[k * ld + j]));
+    }
+    __syncthreads();
+  }
+  // back substitution by warp 0
+  if (tid < 32) {
+    for (int i = q - 1; i >= 0; --i) {
+      df_acc a = acc_zero();
+      for (int j = i + 1 + tid; j < q; j += 32) a.fma(S[i * ld + j], S[j * ld + q]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a.merge(shfl_xor_acc(a, o));
+      if (tid == 0) {
+        df pivv = S[i * ld + i];
+        if (fabsf(pivv.hi) < 1.0e-30f) pivv = df{1.0e-30f, 0.f};
+        S[i * ld + q] = df_div(df_sub(S[i * ld + q], a.value()), pivv);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+__device__ df block_sum_df(df_acc a, df_acc* red, df* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a.merge(shfl_xor_acc(a, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    df_acc b = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : acc_zero();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b.merge(shfl_xor_acc(b, o));
+    if (threadIdx.x == 0) *out = b.value();
+  }
+  __syncthreads();
+  const df r = *out;
+  __syncthreads();
+  return r;
+}
+
+// x^T H x with H = [[Theta, F], [F^T, T]]; hx receives H x
+__device__ df rayleigh(const df* th, const df* F, const df* T, const df* x, df* hx, int m, int q, df_acc* red,
+                       df* out) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < m + q; i += nt) {
+    df_acc a = acc_zero();
+    if (i < m) {
+      a.fma(th[i], x[i]);
+      for (int c = 0; c < q; ++c) a.fma(F[i * q + c], x[m + c]);
+    } else {
+      const int r = i - m;
+      for (int k = 0; k < m; ++k) a.fma(F[k * q + r], x[k]);
+      for (int c = 0; c < q; ++c) a.fma(T[r * q + c], x[m + c]);
+    }
+    hx[i] = a.value();
+  }
+  __syncthreads();
+  df_acc a = acc_zero();
+  for (int i = tid; i < m + q; i += nt) a.fma(x[i], hx[i]);
+  return block_sum_df(a, red, out);
+}
+
+__global__ void __launch_bounds__(kSrqiThreads) k_srqi(int m, int q, const double* __restrict__ H,
+                                                       const double* __restrict__ Y3,
+                                                       const double* __restrict__ Lq, double* __restrict__ mu,
+                                                       double* __restrict__ X, int* __restrict__ conv) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  const int n = m + q;
+  df* th = reinterpret_cast<df*>(sraw);
+  df* F = th + m;          // m x q
+  df* T = F + m * q;       // q x q
+  df* S = T + q * q;       // q x (q+1)
+  df* x = S + q * (q + 1); // n
+  df* y = x + n;           // n
+  df* dinv = y + n;        // m
+  __shared__ df_acc red[32];
+  __shared__ df outv;
+  __shared__ int piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int j = blockIdx.x;
+  const long long N = n;
+  for (int i = tid; i < m; i += nt) th[i] = df_from_double(H[i * N + i]);
+  for (int idx = tid; idx < m * q; idx += nt) {
+    const int i = idx / q, c = idx % q;
+    F[idx] = df_from_double(H[i * N + m + c]);
+  }
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, b = idx % q;
+    T[idx] = df_from_double(H[(m + a) * N + m + b]);
+  }
+  // start: column j of V in the basis of H
+  for (int i = tid; i < n; i += nt) {
+    double v;
+    if (i < m) {
+      v = Y3[i * 3LL * q + j];
+    } else {
+      const int a = i - m;
+      v = a <= j ? Lq[j * q + a] : 0.0;
+    }
+    x[i] = df_from_double(v);
+  }
+  __syncthreads();
+  {
+    df_acc a = acc_zero();
+    for (int i = tid; i < n; i += nt) a.fma(x[i], x[i]);
+    const df nrm = df_sqrt(block_sum_df(a, red, &outv));
+    const df inv = df_div(df{1.f, 0.f}, nrm);
+    for (int i = tid; i < n; i += nt) x[i] = df_mul(x[i], inv);
+    __syncthreads();
+  }
+  df sg = rayleigh(th, F, T, x, y, m, q, red, &outv);
+  int ok = 0;
+  for (int it = 0; it < kSrqiMaxIt; ++it) {
+    // Schur complement S(s) and its right-hand side
+    const float pvf = 1.0e-30f;
+    for (int i = tid; i < m; i += nt) {
+      df d = df_sub(th[i], sg);
+      if (fabsf(d.hi) < pvf) d = df{pvf, 0.f};
+      dinv[i] = df_div(df{1.f, 0.f}, d);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < q * (q + 1); idx += nt) {
+      const int a = idx / (q + 1), b = idx % (q + 1);
+      df_acc acc = acc_zero();
+      if (b < q) {
+        acc.add(T[a * q + b]);
+        if (a == b) acc.add(df_neg(sg));
+        for (int i = 0; i < m; ++i) acc.fma(df_neg(df_mul(F[i * q + a], dinv[i])), F[i * q + b]);
+      } else {
+        acc.add(x[m + a]);
+        for (int i = 0; i < m; ++i) acc.fma(df_neg(df_mul(F[i * q + a], dinv[i])), x[i]);
+      }
+      S[idx] = acc.value();
+    }
+    __syncthreads();
+    gepp_solve(S, q, &piv);
+    for (int i = tid; i < n; i += nt) {
+      if (i < m) {
+        df_acc acc = acc_zero();
+        acc.add(x[i]);
+        for (int c = 0; c < q; ++c) acc.fma(df_neg(F[i * q + c]), S[c * (q + 1) + q]);
+        y[i] = df_mul(dinv[i], acc.value());
+      } else {
+        y[i] = S[(i - m) * (q + 1) + q];
+      }
+    }
+    __syncthreads();
+    // normalise (scaled by the largest entry first)
+    {
+      float amax = 0.f;
+      for (int i = tid; i < n; i += nt) amax = fmaxf(amax, fabsf(y[i].hi));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      __shared__ float wmax[32];
+      if ((tid & 31) == 0) wmax[tid >> 5] = amax;
+      __syncthreads();
+      float gmax = 0.f;
+      for (int w2 = 0; w2 < (nt >> 5); ++w2) gmax = fmaxf(gmax, wmax[w2]);
+      const float sc = gmax > 0.f ? 1.f / gmax : 1.f;
+      df_acc a = acc_zero();
+      for (int i = tid; i < n; i += nt) {
+        const df z = df_mul_f(y[i], sc);
+        y[i] = z;
+        a.fma(z, z);
+      }
+      const df nrm = df_sqrt(block_sum_df(a, red, &outv));
+      const df inv = df_div(df{1.f, 0.f}, nrm);
+      for (int i = tid; i < n; i += nt) x[i] = df_mul(y[i], inv);
+      __syncthreads();
+    }
+    const df sn = rayleigh(th, F, T, x, y, m, q, red, &outv);
+    const df dlt = df_abs(df_sub(sn, sg));
+    sg = sn;
+    if (it >= 1 && dlt.hi <= 4.0e-14f * fabsf(sn.hi)) {
+      ok = 1;
+      break;
+    }
+  }
+  for (int i = tid; i < n; i += nt) X[i * static_cast<long long>(q) + j] = df_to_double(x[i]);
+  if (tid == 0) {
+    mu[j] = df_to_double(sg);
+    conv[j] = ok;
+  }
+}
+
+// Accept the fast path (flag[0] = 1) or leave it to the dense solver (flag[0] = 0).
+// On acceptance writes the sorted pairs to evals / evecs (n x q).  Sg: q x q scratch.
+__global__ void __launch_bounds__(256) k_srqi_check(int m, int q, const double* __restrict__ H,
+                                                    const double* __restrict__ mu, const double* __restrict__ X,
+                                                    const int* __restrict__ conv, double* __restrict__ Sg,
+                                                    double* __restrict__ evals, double* __restrict__ evecs,
+                                                    int* __restrict__ flag) {
+  __shared__ int okf, negs, theta_cnt;
+  __shared__ int perm[kSrqiMaxQ];
+  __shared__ double sstar;
+  const int n = m + q, tid = threadIdx.x, nt = blockDim.x;
+  const long long N = n;
+  if (tid == 0) {
+    okf = 1;
+    negs = 0;
+    double mx = mu[0];
+    for (int i = 1; i < q; ++i) mx = fmax(mx, mu[i]);
+    sstar = mx + 1.0e-9 * fabs(mx) + 1.0e-300;
+    int cnt = 0;
+    for (int i = 0; i < m; ++i)
+      if (H[i * N + i] < sstar) ++cnt;
+    theta_cnt = cnt;
+  }
+  __syncthreads();
+  for (int j = tid; j < q; j += nt)
+    if (!conv[j]) okf = 0;
+  // the computed vectors must be mutually orthogonal (distinct eigenvectors)
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, b = idx % q;
+    if (b <= a) continue;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i)
+      s = fma(X[i * static_cast<long long>(q) + a], X[i * static_cast<long long>(q) + b], s);
+    if (fabs(s) > 1.0e-6) okf = 0;
+  }
+  __syncthreads();
+  if (!okf) {
+    if (tid == 0) flag[0] = 0;
+    return;
+  }
+  // Sylvester inertia of H - s* I: theta_cnt + negative pivots of LDL^T(S(s*))
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, b = idx % q;
+    double acc = H[(m + a) * N + m + b] - (a == b ? sstar : 0.0);
+    for (int i = 0; i < m; ++i) acc -= H[i * N + m + a] * H[i * N + m + b] / (H[i * N + i] - sstar);
+    Sg[idx] = acc;
+  }
+  __syncthreads();
+  for (int k = 0; k < q; ++k) {
+    double piv = Sg[k * q + k];
+    if (fabs(piv) < 1.0e-300) piv = -1.0e-300;
+    if (tid == 0 && piv < 0.0) ++negs;
+    const int r = q - k - 1;
+    for (int idx = tid; idx < r * r; idx += nt) {
+      const int i = k + 1 + idx / r, jj = k + 1 + idx % r;
+      Sg[i * q + jj] -= Sg[i * q + k] * Sg[k * q + jj] / piv;
+    }
+    __syncthreads();
+  }
+  if (theta_cnt + negs != q) {
+    if (tid == 0) flag[0] = 0;
+    return;
+  }
+  for (int j = tid; j < q; j += nt) {
+    int r = 0;
+    for (int i = 0; i < q; ++i)
+      if (mu[i] < mu[j] || (mu[i] == mu[j] && i < j)) ++r;
+    perm[r] = j;
+  }
+  __syncthreads();
+  for (int c = tid; c < q; c += nt) evals[c] = mu[perm[c]];
+  for (long long idx = tid; idx < N * q; idx += nt) {
+    const int i = static_cast<int>(idx / q), c = static_cast<int>(idx % q);
+    evecs[idx] = X[i * static_cast<long long>(q) + perm[c]];
+  }
+  if (tid == 0) flag[0] = 1;
+}
+
 // ------------------------------------------------------------ small FP64 kernels
 
 // Cholesky of a symmetric positive definite n x n row-major matrix into L
@@ -874,6 +1202,10 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
   alloc((void**)&w->perm, sizeof(int) * nwm);
   alloc((void**)&w->Lm, sizeof(double) * dn * dn);
   alloc((void**)&w->Hs, sizeof(double) * dn * dn);
+  alloc((void**)&w->sr_mu, sizeof(double) * qmax);
+  alloc((void**)&w->sr_X, sizeof(double) * nm * qmax);
+  alloc((void**)&w->sr_conv, sizeof(int) * qmax);
+  alloc((void**)&w->sr_flag, sizeof(int));
   if (err) *err = e;
   if (e != cudaSuccess) {
     pencil_work_destroy(w);
@@ -885,14 +1217,15 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
 void pencil_work_destroy(PencilWork* w) {
   if (!w) return;
   void* ptrs[] = {w->KB, w->Y3, w->P3, w->gsc, w->H, w->Lq, w->Sq, w->Nq, w->Yh, w->tmp, w->W,
-                  w->tau, w->dd, w->ee, w->fac, w->Zt, w->rr, w->perm, w->Lm, w->Hs};
+                  w->tau, w->dd, w->ee, w->fac, w->Zt, w->rr, w->perm, w->Lm, w->Hs,
+                  w->sr_mu, w->sr_X, w->sr_conv, w->sr_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete w;
 }
 
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
-                    cudaStream_t st) {
+                    cudaStream_t st, const int* skip) {
   // place W, the factors and Zt in shared memory when they fit (in that order of benefit)
   const int ldw = n | 1;  // odd row stride: column walks of W hit different banks
   size_t sm = syev_smem_base(n, nwant);
@@ -915,7 +1248,7 @@ void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* ev
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
   cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
   k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, w->W, w->tau, w->dd, w->ee, w->fac,
-                                       w->Zt, w->rr, w->perm);
+                                       w->Zt, w->rr, w->perm, skip);
 }
 
 void launch_syev_df_into(int n, int nwant, const double* H, double* evals, double* evecs, df* W, df* tau, df* dd,
@@ -940,21 +1273,32 @@ void launch_syev_df_into(int n, int nwant, const double* H, double* evals, doubl
   }
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
   cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-  k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, W, tau, dd, ee, fac, Zt, rr, perm);
+  k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, W, tau, dd, ee, fac, Zt, rr, perm,
+                                       nullptr);
 }
 
 void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C, const double* G, const double* Z,
                          const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st) {
   const int n = m + q;
-  // three kernels launched here; the GEMM, Gram and eigensolver launchers count their own
-  ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * q * q + 1.0 * n * n + 1.0 * m * q), 0.0, 3);
+  // five kernels launched here; the GEMM, Gram and eigensolver launchers count their own
+  ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * q * q + 1.0 * n * n + 1.0 * m * q), 0.0, 5);
   // K | B = Z_m^T [C_A | C_M]   (Z_m: the first m columns of Z)
   launch_gemm_f64(m, 2 * q, dn, 1.0, Z, dn, true, C, 2 * q, false, 0.0, w->KB, 2 * q, st);
   k_build_y3<<<ceil_div(static_cast<long long>(m) * q, 256), 256, 0, st>>>(m, q, w->KB, theta, w->Y3);
   // P3 = [B K]^T [B K Theta B]
   launch_gram_strided(m, w->Y3, 3 * q, 2 * q, w->Y3, 3 * q, 3 * q, w->gsc, w->P3, st);
   k_pencil_h<<<1, 512, 0, st>>>(m, q, G, w->P3, w->Y3, theta, w->Lq, w->Sq, w->Nq, w->H, status);
-  launch_syev_df(w, n, q, w->H, mu, w->Yh, st);
+  // structured Rayleigh quotient iteration, checked by inertia; the dense
+  // float-float solver runs only when the check rejects it
+  const size_t srs = sizeof(df) * (2.0 * m + 1.0 * m * q + 2.0 * q * q + q + 2.0 * n);
+  const int* skip = nullptr;
+  if (q <= kSrqiMaxQ && srs <= 200 * 1024) {
+    if (srs > 48 * 1024) cudaFuncSetAttribute(k_srqi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)srs);
+    k_srqi<<<q, kSrqiThreads, srs, st>>>(m, q, w->H, w->Y3, w->Lq, w->sr_mu, w->sr_X, w->sr_conv);
+    k_srqi_check<<<1, 256, 0, st>>>(m, q, w->H, w->sr_mu, w->sr_X, w->sr_conv, w->Sq, mu, w->Yh, w->sr_flag);
+    skip = w->sr_flag;
+  }
+  launch_syev_df(w, n, q, w->H, mu, w->Yh, st, skip);
   k_pencil_back<<<1, 256, 0, st>>>(m, q, w->Yh, w->Lq, Y, w->tmp);
   // tmp = a - B Yv ; Xc = Z_m tmp
   launch_gemm_f64(m, q, q, -1.0, w->Y3, 3 * q, false, Y, q, false, 1.0, w->tmp, q, st);
