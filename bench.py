@@ -345,6 +345,7 @@ def main():
                        "coarse_modes": modes, "sweeps": args.sweeps, "v_cycles": args.v_cycles,
                        "rel_eig_err_vs_fp64": rel_err, "fp64_corrections": info_ref.corrections,
                        "fp64_full_pencil_s": round(t_ref, 4), "fp64_relres": info_ref.max_relres,
+                       "dense_fallbacks": info.dense_fallbacks,
                        "l2": "inputs larger than L2 (hierarchy + blocks > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,

@@ -77,6 +77,8 @@ typedef struct {
   int n1;            /* initial level (0-based) */
   int status;        /* AMGEIG_OK or the error code of the solve */
   double max_relres; /* max_j ||A u_j - lambda_j M u_j||_2 / (|lambda_j| ||M u_j||_2), j < q */
+  int dense_fallbacks; /* corrections (all levels) whose small pencil needed the dense eigensolver
+                          because the Rayleigh quotient iteration's result failed its check */
 } amgeig_info;
 
 /* Fill *opt with the defaults above.  opt must not be NULL. */

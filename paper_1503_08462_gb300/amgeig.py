@@ -48,7 +48,7 @@ class amgeig_prof_entry(ctypes.Structure):
 
 class amgeig_info(ctypes.Structure):
     _fields_ = [("corrections", ctypes.c_int), ("converged", ctypes.c_int), ("n1", ctypes.c_int),
-                ("status", ctypes.c_int), ("max_relres", ctypes.c_double)]
+                ("status", ctypes.c_int), ("max_relres", ctypes.c_double), ("dense_fallbacks", ctypes.c_int)]
 
 
 _lib = None

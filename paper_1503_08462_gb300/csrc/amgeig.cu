@@ -263,6 +263,7 @@ struct amgeig_hierarchy_t {
   int dn = 0;
   double *An = nullptr, *Mn = nullptr, *Z = nullptr, *theta = nullptr, *Ainv = nullptr;
   float* Ainv32 = nullptr;
+  float2* Zdf = nullptr;  // Z as float-float pairs
   int* dstatus = nullptr;
   DeviceBuffers mem;
   std::mutex mu;  // one solve at a time per hierarchy (shared workspace)
@@ -287,6 +288,7 @@ struct SolveWork {
   double *partials = nullptr, *sums = nullptr, *relres = nullptr, *lam = nullptr, *mu = nullptr;
   double *C = nullptr, *G = nullptr, *gsc = nullptr, *Xc = nullptr, *Yv = nullptr, *sign = nullptr;
   int* flags = nullptr;
+  int* nfallback = nullptr;  // corrections that needed the dense eigensolver
   PencilWork* pw = nullptr;
   ~SolveWork() { pencil_work_destroy(pw); }
 };
@@ -356,6 +358,7 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->Yv, static_cast<size_t>(qt) * qt));
   CK(m.alloc(&w->sign, qt));
   CK(m.alloc(&w->flags, 4));
+  CK(m.alloc(&w->nfallback, 1));
   cudaError_t e;
   w->pw = pencil_work_create(h->dn, qt, &e);
   if (!w->pw) return fail(AMGEIG_ENOMEM, std::string("pencil workspace: ") + cudaGetErrorString(e));
@@ -402,10 +405,10 @@ void axpy(const float* x, long long c, float* y, cudaStream_t s) { launch_axpy_f
 const double* dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->dinv64[l]; }
 const float* dinv_of(amgeig_hierarchy_t* h, int l, float*) { return h->dinv32[l]; }
 void coarse_solve(amgeig_hierarchy_t* h, const double* b, int q, double* x, cudaStream_t s) {
-  launch_gemm_f64(h->dn, q, h->dn, 1.0, h->Ainv, h->dn, false, b, q, false, 0.0, x, q, s, P_COARSE);
+  launch_dense_apply(h->dn, q, h->Ainv, b, x, s, P_COARSE);
 }
 void coarse_solve(amgeig_hierarchy_t* h, const float* b, int q, float* x, cudaStream_t s) {
-  launch_gemm_f32(h->dn, q, h->dn, 1.0f, h->Ainv32, h->dn, false, b, q, false, 0.0f, x, q, s, P_COARSE);
+  launch_dense_apply(h->dn, q, h->Ainv32, b, x, s, P_COARSE);
 }
 
 // One V-cycle for A_k x = B[k] from x = 0; the result is left in X[k] unless
@@ -515,7 +518,8 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
       cur = w->WC[l + 1];
     }
     CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
-    launch_pencil_solve(w->pw, h->dn, modes, q, cur, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
+    launch_pencil_solve(w->pw, h->dn, modes, q, cur, nullptr, w->G, h->Zdf, h->theta, w->mu, w->Xc, nullptr, w->Yv,
+                        h->dstatus, st, w->nfallback);
     // recombination: U = I_n^k Xc + V Y
     const double* px = w->Xc;
     for (int l = n - 2; l >= k; --l) {
@@ -533,10 +537,9 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
       launch_spmm_df(h->R[l], cur, 2 * q, as_df(w->WC[l + 1]), false, st, P_CHAIN);
       cur = as_df(w->WC[l + 1]);
     }
-    launch_df_to_f64(cur, static_cast<long long>(h->dn) * 2 * q, w->C, st);
     CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
-    launch_pencil_solve(w->pw, h->dn, modes, q, w->C, w->G, h->Z, h->theta, w->mu, w->Xc, w->Yv, h->dstatus, st);
-    launch_f64_to_df(w->Xc, static_cast<long long>(h->dn) * q, as_df(w->PX[n - 1]), st);
+    launch_pencil_solve(w->pw, h->dn, modes, q, nullptr, cur, w->G, h->Zdf, h->theta, w->mu, w->Xc,
+                        as_df(w->PX[n - 1]), w->Yv, h->dstatus, st, w->nfallback);
     const float2* px = as_df(w->PX[n - 1]);
     for (int l = n - 2; l >= k; --l) {
       launch_spmm_df(h->P[l], px, q, as_df(w->PX[l]), false, st, P_CHAIN);
@@ -601,6 +604,7 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
     ProfScope ps(st, P_OTHER, 16.0 * qt, 0.0);
     k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
   }
+  CK(cudaMemsetAsync(w->nfallback, 0, sizeof(int), st));
   CK(cudaGetLastError());
   int corrections = 0;
   bool converged = false;
@@ -666,6 +670,10 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   if (info) {
     double mx = 0.0;
     for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
+    int nfb = 0;
+    CK(cudaMemcpyAsync(&nfb, w->nfallback, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    info->dense_fallbacks = nfb;
     info->corrections = corrections;
     info->converged = converged ? 1 : 0;
     info->n1 = n - 1;
@@ -894,6 +902,8 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   if (!pw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
   launch_coarse_eigh(pw, dn, h->An, h->Mn, h->Z, h->theta, h->Ainv, h->dstatus, h->stream);
   launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, h->stream);
+  CK(m.alloc(&h->Zdf, static_cast<size_t>(dn) * dn));
+  launch_f64_to_df(h->Z, static_cast<long long>(dn) * dn, h->Zdf, h->stream);
   int stt = 0;
   cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e2 = cudaStreamSynchronize(h->stream);

@@ -94,6 +94,15 @@ __device__ __forceinline__ df df_div(df a, df b) {
   return df_add(q, df{q3, 0.f});
 }
 
+// 1 / b: the float32 reciprocal refined by one Newton step in float-float,
+// r <- r + r (1 - b r); the relative error squares (2^-24 -> ~2^-48).  Cheaper
+// than df_div's three corrections, for the latency-bound pivots and shifts.
+__device__ __forceinline__ df df_recip(df b) {
+  const float r = __frcp_rn(b.hi);
+  const df e = df_sub(df{1.f, 0.f}, df_mul_f(b, r));
+  return df_add(df{r, 0.f}, df_mul_f(e, r));
+}
+
 __device__ __forceinline__ df df_sqrt(df a) {
   if (a.hi <= 0.f) return df{0.f, 0.f};
   float s = __fsqrt_rn(a.hi);

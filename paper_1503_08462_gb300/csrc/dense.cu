@@ -1,6 +1,7 @@
 // Small dense kernels: GEMM on coarse-size operands, the tall-skinny Gram
 // products V^T W of Algorithm 3.1 step 2 (V^T A_k V and V^T M_k V), fixed-order
 // reductions of per-block partial sums, and the residual test.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -41,6 +42,28 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, cons
     T* c = C + static_cast<long long>(row) * ldc + col;
     *c = (beta == T(0)) ? alpha * acc : fma(alpha, acc, beta * *c);
   }
+}
+
+// x = A b for a dense n x n row-major A and an n x w row-major block b: each
+// thread owns one output, rows_per_block rows per block; four independent
+// accumulators break the FMA dependency chain.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply(int n, int w, const T* __restrict__ A, const T* __restrict__ b,
+                                                     T* __restrict__ x, int rows_per_block) {
+  const int rl = threadIdx.x / w, c = threadIdx.x % w;
+  const int r = blockIdx.x * rows_per_block + rl;
+  if (rl >= rows_per_block || r >= n) return;
+  const T* a = A + static_cast<long long>(r) * n;
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int k = 0;
+  for (; k + 4 <= n; k += 4) {
+    s0 = fma(a[k], b[static_cast<long long>(k) * w + c], s0);
+    s1 = fma(a[k + 1], b[static_cast<long long>(k + 1) * w + c], s1);
+    s2 = fma(a[k + 2], b[static_cast<long long>(k + 2) * w + c], s2);
+    s3 = fma(a[k + 3], b[static_cast<long long>(k + 3) * w + c], s3);
+  }
+  for (; k < n; ++k) s0 = fma(a[k], b[static_cast<long long>(k) * w + c], s0);
+  x[static_cast<long long>(r) * w + c] = (s0 + s1) + (s2 + s3);
 }
 
 // Gram partials: block (chunk, tile) accumulates out[a][b] = sum_{r in chunk} V[r][a] W[r][b]
@@ -182,6 +205,23 @@ void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, 
   ProfScope ps(st, cls, 4.0 * (1.0 * M * K + 1.0 * K * N + (beta != 0.0f ? 2.0 : 1.0) * M * N), 2.0 * M * N * K);
   dim3 grid(ceil_div(N, kTile), ceil_div(M, kTile));
   k_gemm<float><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
+}
+
+template <typename T>
+void launch_dense_apply_t(int n, int w, const T* A, const T* b, T* x, cudaStream_t st, int cls) {
+  if (n <= 0 || w <= 0) return;
+  ProfScope ps(st, cls, sizeof(T) * (1.0 * n * n + 2.0 * n * w), 2.0 * n * n * w);
+  // float64 issues slowly on this part: fewer rows per block spread it over more SMs
+  const int cap = std::is_same<T, double>::value ? 2 : 8;
+  const int rpb = std::max(1, std::min(cap, 256 / w));
+  k_dense_apply<T><<<ceil_div(n, rpb), rpb * w, 0, st>>>(n, w, A, b, x, rpb);
+}
+
+void launch_dense_apply(int n, int w, const double* A, const double* b, double* x, cudaStream_t st, int cls) {
+  launch_dense_apply_t(n, w, A, b, x, st, cls);
+}
+void launch_dense_apply(int n, int w, const float* A, const float* b, float* x, cudaStream_t st, int cls) {
+  launch_dense_apply_t(n, w, A, b, x, st, cls);
 }
 
 size_t gram_scratch_doubles(int rows, int q, int w) {

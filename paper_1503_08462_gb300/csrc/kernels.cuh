@@ -109,6 +109,9 @@ void launch_add_to_vdf(const float2* U, const float* x, int rows, int q, int ldx
 // C = alpha op(A) op(B) + beta C, all row-major; op = transpose when t* != 0.
 // A is M x K (or K x M when ta), B is K x N (or N x K when tb).
 // cls: the profiler class the launch is accounted to (prof.cuh; 8 = other)
+// x = A b, A dense n x n row-major, b and x n x w row-major (w <= 256)
+void launch_dense_apply(int n, int w, const double* A, const double* b, double* x, cudaStream_t st, int cls);
+void launch_dense_apply(int n, int w, const float* A, const float* b, float* x, cudaStream_t st, int cls);
 void launch_gemm_f64(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
                      int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st, int cls = 8);
 void launch_gemm_f32(int M, int N, int K, float alpha, const float* A, int lda, bool ta, const float* B, int ldb,
@@ -147,16 +150,19 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err);
 void pencil_work_destroy(PencilWork* w);
 
 // One Rayleigh-Ritz step on V_n + span(V) (Algorithm 3.1 step 2) in the
-// coarse eigenbasis: inputs C = [I_k^n A V | I_k^n M V] (dn x 2q),
-// G = [V^T A V | V^T M V] (q x 2q), the coarse eigenbasis Z (dn x dn, M_n-
-// orthonormal) and Theta (dn).  The coarse part of the trial space is spanned
-// by the first m <= dn columns of Z (m = dn: all of V_n).  Outputs the q
-// smallest Ritz values mu (q), the coarse coefficients Xc (dn x q) and the
-// V-coefficients Y (q x q) so that the new vectors are I_n^k Xc + V Y.
-// status[0] receives AMGEIG_ENOTSPD when the Gram Schur complement is not
-// positive definite.
-void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C, const double* G, const double* Z,
-                         const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st);
+// coarse eigenbasis: inputs C = [I_k^n A V | I_k^n M V] (dn x 2q, float64 in
+// C64 or float-float in Cdf, the other null), G = [V^T A V | V^T M V] (q x 2q),
+// the coarse eigenbasis Z (dn x dn, M_n-orthonormal, as float-float pairs Zdf)
+// and Theta (dn).  The coarse part of the trial space is spanned by the first
+// m <= dn columns of Z (m = dn: all of V_n).  Outputs the q smallest Ritz
+// values mu (q), the coarse coefficients Xc (dn x q; also as float-float pairs
+// in Xcdf when non-null) and the V-coefficients Y (q x q) so that the new
+// vectors are I_n^k Xc + V Y.  status[0] receives AMGEIG_ENOTSPD when the Gram
+// Schur complement is not positive definite.  nfallback (device, may be null)
+// is incremented when the dense eigensolver had to run.
+void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64, const float2* Cdf,
+                         const double* G, const float2* Zdf, const double* theta, double* mu, double* Xc,
+                         float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback = nullptr);
 
 // Full eigendecomposition of the coarsest pencil (A_n, M_n), both dn x dn
 // dense row-major: Z (dn x dn) with Z^T M_n Z = I, Z^T A_n Z = diag(theta),

@@ -8,17 +8,18 @@
 //   H = Y Theta Y^T, Z = L^-T Y.  Then Z^T M_n Z = I and Z^T A_n Z = Theta, which
 //   gives step 1 of Algorithm 3.2 (the q smallest columns of Z) and the exact
 //   coarsest-level solve A_n^-1 = Z Theta^-1 Z^T of the V-cycle.
-// * Each correction's pencil is written in the basis [I_n^k Z, V].  With
-//   K = Z^T I_k^n A_k V, B = Z^T I_k^n M_k V (d_n x q), the M-part becomes
-//   [[I, B], [B^T, V^T M V]]; eliminating B (block Gram-Schmidt of V against the
-//   coarse space, in float64 on q x q and d_n x q data) and factoring the Schur
-//   complement S = V^T M V - B^T B = L L^T reduces the pencil to the standard
-//   symmetric problem
-//       H = [[Theta, F], [F^T, T]],  F = (K - Theta B) L^-T,
-//       T = L^-1 (V^T A V - B^T K - K^T B + B^T Theta B) L^-T,
-//   whose eigenvectors y = [a; b] map back to x = [Z (a - B L^-T b); L^-T b].
-//   This is the same Rayleigh-Ritz problem (its eigenvalues are those of the
-//   pencil), only better conditioned.
+// * Each correction's pencil is written in the basis [I_n^k Z_m, V - I_n^k Z_m B]
+//   (block Gram-Schmidt of V against the first m coarse modes) with
+//   K = Z_m^T I_k^n A_k V, B = Z_m^T I_k^n M_k V: it becomes
+//       At = [[Theta, K - Theta B], [., V^T A V - B^T K - K^T B + B^T Theta B]],
+//       Mt = [[I, 0], [0, S]],   S = V^T M V - B^T B,
+//   whose eigenvectors [a; b] map back to x = I_n^k Z_m (a - B b) + V b.  The
+//   q wanted pairs come from a structured Rayleigh quotient iteration checked by
+//   Sylvester's inertia; when the check fails, S = L L^T reduces the pencil to
+//   the standard symmetric matrix H = [[Theta, F], [F^T, T]], F = (K - Theta B)
+//   L^-T, T = L^-1 (...) L^-T, solved by the dense eigensolver below.  Both are
+//   the same Rayleigh-Ritz problem (same eigenvalues as the paper's pencil),
+//   only better conditioned, and everything runs in float-float.
 // * The symmetric eigenproblem is solved in float-float (48-bit significand)
 //   by one 1024-thread block: Householder tridiagonalisation, bisection with
 //   Sturm counts for the wanted eigenvalues (float32), inverse iteration with
@@ -42,18 +43,15 @@ constexpr int kSyThreads = AMGEIG_SY_THREADS;
 
 struct PencilWork {
   int dn = 0, qmax = 0, nmax = 0;
-  // pencil stage
-  double* KB = nullptr;   // dn x 2q   Z^T C
-  double* Y3 = nullptr;   // dn x 3q   [B | K | Theta B]
-  double* P3 = nullptr;   // 2q x 3q   [B K]^T [B K Theta B]
-  double* gsc = nullptr;  // gram scratch
-  size_t gsc_doubles = 0;
-  double* H = nullptr;    // nmax x nmax
-  double* Lq = nullptr;   // q x q   Cholesky factor of the Schur complement
-  double* Sq = nullptr;   // q x q   scratch
-  double* Nq = nullptr;   // q x q   scratch
-  double* Yh = nullptr;   // nmax x q eigenvectors of H
-  double* tmp = nullptr;  // dn x q
+  // Rayleigh-Ritz pencil (float-float)
+  df* KB = nullptr;   // dn x 2q   Z_m^T C = [K | B]
+  df* Ft = nullptr;   // dn x q    K - Theta B
+  df* Tt = nullptr;   // q x q
+  df* St = nullptr;   // q x q     Schur complement of the Gram matrix
+  df* Lq = nullptr;   // q x q     its Cholesky factor (fallback)
+  df* Xq = nullptr;   // q x q     scratch (fallback)
+  double* H = nullptr;   // nmax x nmax standard form (fallback)
+  double* Yh = nullptr;  // nmax x q eigenvectors [a; b]
   // float-float eigensolver
   df* W = nullptr;     // nmax x nmax
   df* tau = nullptr;   // nmax
@@ -630,39 +628,97 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   for (long long idx = tid; idx < N * NW; idx += nt) evecs[idx] = df_to_double(Zn[idx]);
 }
 
-// ------------------------------------------------------------ structured Rayleigh quotient iteration
+// ------------------------------------------------------------ Rayleigh-Ritz pencil
 //
-// Fast path for the reduced pencil H = [[Theta, F], [F^T, T]] (Theta diagonal,
-// m x m; border q): Rayleigh quotient iteration for each wanted pair in its
-// own block, with (H - s I) y = x solved through the Schur complement
-//   S(s) = T - s I - F^T (Theta - s I)^-1 F   (q x q, Gaussian elimination with
-// partial pivoting), starting from the current iterates written in the basis
-// of H (column j of V is [B e_j; L^T e_j] there).  k_srqi_check then accepts
-// the result only if every iteration converged, the vectors are mutually
-// orthogonal, and Sylvester's inertia of H - s* I just above the largest value
-// counts exactly q eigenvalues below (inertia(Theta - s) + inertia(S(s)),
-// Haynsworth), i.e. the pairs found are the q smallest; otherwise the dense
-// float-float eigensolver runs.  Golub & Van Loan 8.2.3 (RQI), 4.4 (inertia).
-constexpr int kSrqiThreads = 256;
+// The pencil of Algorithm 3.1 step 2 in the basis [Phi, V - Phi B], Phi =
+// I_n^k Z_m (M-orthonormal coarse modes), K = Phi^T A V, B = Phi^T M V:
+//     At = [[Theta, Ft], [Ft^T, Tt]],   Mt = [[I, 0], [0, S]],
+//     Ft = K - Theta B,   Tt = V^T A V - B^T K - K^T B + B^T Theta B,
+//     S  = V^T M V - B^T B   (the Gram matrix of V after block Gram-Schmidt
+//                             against the coarse space).
+// An eigenvector [a; b] (M-normalised) gives the new vector Phi (a - B b) + V b.
+//
+// Fast path: a Rayleigh quotient iteration per wanted pair (one block each),
+// started from the columns of V (column j is [B e_j; e_j] in this basis), with
+// (At - s Mt) y = Mt x solved through the q x q Schur complement
+// S(s) = Tt - s S - Ft^T (Theta - s)^-1 Ft (Gaussian elimination with partial
+// pivoting), all in float-float.  k_srqi_check accepts the result only if every
+// iteration converged, the vectors are mutually Mt-orthogonal to 1e-6, S is
+// positive definite, and Sylvester's inertia of At - s* Mt just above the
+// largest value (inertia of Theta - s* plus that of S(s*), Haynsworth) counts
+// exactly q eigenvalues below, i.e. the pairs found are the q smallest.
+// Otherwise the fallback forms the standard matrix H (Cholesky of S) and runs
+// the dense float-float eigensolver.  Golub & Van Loan 8.2.3 (RQI), 4.4
+// (inertia), 8.7 (symmetric-definite pencils).
+constexpr int kPenThreads = 256;
+constexpr int kSrqiThreads = 1024;  // one block per pair: the whole SM for its latency-bound steps
 constexpr int kSrqiMaxQ = 64;
 constexpr int kSrqiMaxIt = 8;
+constexpr int kStdMaxQ = 128;  // largest border the solver accepts (q + q_extra)
 
-// Solve S y = r in place (S: q x (q+1) augmented, row-major, shared) by GEPP;
-// the solution is left in column q.
-__device__ void gepp_solve(df* S, int q, int* piv_shared) {
+__device__ __forceinline__ df to_df(double v) { return df_from_double(v); }
+__device__ __forceinline__ df to_df(float2 v) { return df{v.x, v.y}; }
+
+// sum_i a[i sa] b[i sb] (i < len) in float-float with four interleaved
+// accumulators: independent chains keep the float32 pipes busy in these
+// latency-bound single-block kernels
+__device__ __forceinline__ df_acc dot4(const df* a, int sa, const df* b, int sb, int len) {
+  df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
+  int i = 0;
+  for (; i + 4 <= len; i += 4) {
+    c0.fma(a[i * sa], b[i * sb]);
+    c1.fma(a[(i + 1) * sa], b[(i + 1) * sb]);
+    c2.fma(a[(i + 2) * sa], b[(i + 2) * sb]);
+    c3.fma(a[(i + 3) * sa], b[(i + 3) * sb]);
+  }
+  for (; i < len; ++i) c0.fma(a[i * sa], b[i * sb]);
+  c0.merge(c1);
+  c2.merge(c3);
+  c0.merge(c2);
+  return c0;
+}
+
+// the same with weights: sum_i a[i sa] w[i] b[i sb]
+__device__ __forceinline__ df_acc dot4w(const df* a, int sa, const df* w, const df* b, int sb, int len) {
+  df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
+  int i = 0;
+  for (; i + 4 <= len; i += 4) {
+    c0.fma(df_mul(a[i * sa], w[i]), b[i * sb]);
+    c1.fma(df_mul(a[(i + 1) * sa], w[i + 1]), b[(i + 1) * sb]);
+    c2.fma(df_mul(a[(i + 2) * sa], w[i + 2]), b[(i + 2) * sb]);
+    c3.fma(df_mul(a[(i + 3) * sa], w[i + 3]), b[(i + 3) * sb]);
+  }
+  for (; i < len; ++i) c0.fma(df_mul(a[i * sa], w[i]), b[i * sb]);
+  c0.merge(c1);
+  c2.merge(c3);
+  c0.merge(c2);
+  return c0;
+}
+
+// Solve S y = r (S: q x (q+1) augmented, row-major, shared) by Gauss-Jordan
+// elimination with partial pivoting, by the whole block: per column, warp 0
+// picks the pivot among the rows not yet used and every thread then updates
+// elements of the other rows (two barriers per column, no back substitution).
+// Pivot rows are marked in `used` instead of swapped; their order is kept in
+// prow.  The solution goes to sol.  prow, used (q ints), rinv (1) and sol (q)
+// live in shared memory.
+__device__ void gj_solve(df* S, int q, int* prow, int* used, df* rinv_s, df* sol) {
   const int ld = q + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < q; i += nt) used[i] = 0;
+  __syncthreads();
   for (int k = 0; k < q; ++k) {
     if (tid < 32) {
       float best = -1.f;
-      int bi = k;
-      for (int i = k + tid; i < q; i += 32) {
-        const float a = fabsf(S[i * ld + k].hi);
-        if (a > best) {
-          best = a;
-          bi = i;
+      int bi = q;
+      for (int i = tid; i < q; i += 32)
+        if (!used[i]) {
+          const float a = fabsf(S[i * ld + k].hi);
+          if (a > best) {
+            best = a;
+            bi = i;
+          }
         }
-      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
@@ -672,44 +728,136 @@ __device__ void gepp_solve(df* S, int q, int* piv_shared) {
           bi = i2;
         }
       }
-      if (tid == 0) *piv_shared = bi;
+      if (tid == 0) {
+        prow[k] = bi;
+        used[bi] = 1;
+        df pv = S[bi * ld + k];
+        if (fabsf(pv.hi) < 1.0e-30f) pv = df{1.0e-30f, 0.f};
+        *rinv_s = df_div(df{1.f, 0.f}, pv);
+      }
     }
     __syncthreads();
-    const int pr = *piv_shared;
-    if (pr != k)
-      for (int j = k + tid; j <= q; j += nt) {
-        const df t = S[k * ld + j];
-        S[k * ld + j] = S[pr * ld + j];
-        S[pr * ld + j] = t;
-      }
-    __syncthreads();
-    df pivv = S[k * ld + k];
-    if (fabsf(pivv.hi) < 1.0e-30f) pivv = df{1.0e-30f, 0.f};
-    const df rinv = df_div(df{1.f, 0.f}, pivv);
-    const int rows = q - k - 1, cols = q - k;  // columns k+1..q
-    for (int idx = tid; idx < rows * cols; idx += nt) {
-      const int i = k + 1 + idx / cols, j = k + 1 + idx % cols;
+    const int p = prow[k];
+    const df rinv = *rinv_s;
+    const int cols = q - k;  // columns k+1..q
+    for (int e = tid; e < q * cols; e += nt) {
+      const int i = e / cols, j = k + 1 + e % cols;
+      if (i == p) continue;
       const df l = df_mul(S[i * ld + k], rinv);
-      S[i * ld + j] = df_sub(S[i * ld + j], df_mul(l, S[k * ld + j]));
+      S[i * ld + j] = df_sub(S[i * ld + j], df_mul(l, S[p * ld + j]));
     }
     __syncthreads();
   }
-  // back substitution by warp 0
-  if (tid < 32) {
-    for (int i = q - 1; i >= 0; --i) {
-      df_acc a = acc_zero();
-      for (int j = i + 1 + tid; j < q; j += 32) a.fma(S[i * ld + j], S[j * ld + q]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a.merge(shfl_xor_acc(a, o));
-      if (tid == 0) {
-        df pivv = S[i * ld + i];
-        if (fabsf(pivv.hi) < 1.0e-30f) pivv = df{1.0e-30f, 0.f};
-        S[i * ld + q] = df_div(df_sub(S[i * ld + q], a.value()), pivv);
-      }
-      __syncwarp();
-    }
+  for (int k = tid; k < q; k += nt) {
+    const int p = prow[k];
+    df pv = S[p * ld + k];
+    if (fabsf(pv.hi) < 1.0e-30f) pv = df{1.0e-30f, 0.f};
+    sol[k] = df_div(S[p * ld + q], pv);
   }
   __syncthreads();
+}
+
+// Gauss-Jordan with partial pivoting for q <= 31 and a 1024-thread block: the
+// thread (i, j) = (tid / 32, tid % 32) keeps element (i, j) of the augmented
+// q x (q+1) matrix in registers, so warp i holds row i.  Per column k: the
+// pivot row p (chosen by a shared atomic max over |a_ik| while column k was
+// updated) is scaled by 1 / a_pk inside its warp and published in shared
+// memory; every other row takes its multiplier a_ik from lane k by a shuffle
+// and subtracts a_ik * (scaled pivot row).  Two barriers per column, no
+// integer division, no back substitution: x_k ends in column q of row p_k.
+// S is read from shared memory (row stride q + 1); the solution goes to sol.
+struct GjShared {
+  unsigned long long key[2];
+  df prowv[33];
+  int kof[32];
+};
+
+__device__ __forceinline__ unsigned long long pivot_key(float a, int i) {
+  // |a| >= 0: its bits order like its value; ties go to the smaller row
+  return (static_cast<unsigned long long>(__float_as_uint(a)) << 32) | static_cast<unsigned>(31 - i);
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src) {
+  return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+__device__ void gj_solve_reg(const df* S, int q, GjShared* g, df* sol) {
+  const int tid = threadIdx.x;
+  const int i = tid >> 5, j = tid & 31;
+  const bool live = i < q && j <= q;
+  df v = live ? S[i * (q + 1) + j] : df{0.f, 0.f};
+  if (tid == 0) g->key[0] = 0ull;
+  __syncthreads();
+  if (live && j == 0) atomicMax(&g->key[0], pivot_key(fabsf(v.hi), i));
+  unsigned used = 0u;
+  __syncthreads();
+  for (int k = 0; k < q; ++k) {
+    const int p = 31 - static_cast<int>(g->key[k & 1] & 0xffffffffull);
+    if (i == p) {
+      df pk = shfl_df(v, k);
+      if (fabsf(pk.hi) < 1.0e-30f) pk = df{1.0e-30f, 0.f};
+      v = (j == k) ? df{1.f, 0.f} : df_mul(v, df_recip(pk));
+      if (j <= q) g->prowv[j] = v;
+    }
+    if (tid == 0) {
+      g->key[(k + 1) & 1] = 0ull;
+      g->kof[p] = k;
+    }
+    used |= 1u << p;
+    __syncthreads();
+    if (i < q && i != p) {
+      const df l = shfl_df(v, k);
+      if (j <= q && j > k) {
+        v = df_sub(v, df_mul(l, g->prowv[j]));
+        if (j == k + 1 && !((used >> i) & 1u)) atomicMax(&g->key[(k + 1) & 1], pivot_key(fabsf(v.hi), i));
+      }
+    }
+    __syncthreads();
+  }
+  if (live && j == q) sol[g->kof[i]] = v;
+  __syncthreads();
+}
+
+// Inertia by symmetric elimination without pivoting (LDL^T) of two q x q
+// matrices at once (q <= 31, 1024 threads): thread (i, j) keeps element (i, j)
+// of both in registers; per step k warp k scales its row by 1 / d_k and
+// publishes it, and rows i > k subtract a_ik times it.  Counts the negative
+// (or zero) pivots of A into *negs and flags a non-positive pivot of B in
+// *nonpd (both shared, initialised by the caller).
+struct LdlShared {
+  df ra[32], rb[32];
+};
+
+__device__ void ldl_inertia_reg(const df* A, const df* B, int q, LdlShared* g, int* negs, int* nonpd) {
+  const int tid = threadIdx.x;
+  const int i = tid >> 5, j = tid & 31;
+  const bool live = i < q && j < q;
+  df a = live ? A[i * q + j] : df{0.f, 0.f};
+  df b = live ? B[i * q + j] : df{0.f, 0.f};
+  for (int k = 0; k < q; ++k) {
+    if (i == k) {
+      df da = shfl_df(a, k), db = shfl_df(b, k);
+      if (j == 0) {
+        if (df_lt0(da) || da.hi == 0.f) ++*negs;
+        if (!(db.hi > 0.f)) *nonpd = 1;
+      }
+      if (da.hi == 0.f) da = df{-1.0e-30f, 0.f};
+      if (!(db.hi > 0.f)) db = df{1.f, 0.f};
+      if (j < q) {
+        g->ra[j] = df_mul(a, df_recip(da));
+        g->rb[j] = df_mul(b, df_recip(db));
+      }
+    }
+    __syncthreads();
+    if (i > k && i < q) {
+      const df la = shfl_df(a, k), lb = shfl_df(b, k);
+      if (j > k && j < q) {
+        a = df_sub(a, df_mul(la, g->ra[j]));
+        b = df_sub(b, df_mul(lb, g->rb[j]));
+      }
+    }
+    __syncthreads();
+  }
 }
 
 __device__ df block_sum_df(df_acc a, df_acc* red, df* out) {
@@ -729,211 +877,356 @@ __device__ df block_sum_df(df_acc a, df_acc* red, df* out) {
   return r;
 }
 
-// x^T H x with H = [[Theta, F], [F^T, T]]; hx receives H x
-__device__ df rayleigh(const df* th, const df* F, const df* T, const df* x, df* hx, int m, int q, df_acc* red,
-                       df* out) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < m + q; i += nt) {
-    df_acc a = acc_zero();
+// KB = Z_m^T C (m x 2q, float-float): K = KB[:, :q], B = KB[:, q:].  One block
+// per column of C; the block's four thread groups split the d_n-long sums.
+template <typename TC>
+__global__ void __launch_bounds__(kPenThreads) k_kb(int dn, int m, int q, const float2* __restrict__ Zdf,
+                                                    const TC* __restrict__ C, df* __restrict__ KB) {
+  extern __shared__ __align__(16) unsigned char kraw[];
+  df* col = reinterpret_cast<df*>(kraw);  // dn
+  __shared__ df_acc part[4][64];
+  const int c = blockIdx.x, tid = threadIdx.x;
+  const int q2 = 2 * q;
+  for (int l = tid; l < dn; l += blockDim.x) col[l] = to_df(C[static_cast<long long>(l) * q2 + c]);
+  __syncthreads();
+  const int il = tid & 63, g = tid >> 6;
+  for (int i0 = 0; i0 < m; i0 += 64) {
+    const int i = i0 + il;
+    df_acc a = acc_zero(), a2 = acc_zero();
     if (i < m) {
-      a.fma(th[i], x[i]);
-      for (int c = 0; c < q; ++c) a.fma(F[i * q + c], x[m + c]);
+      int l = g;
+      for (; l + 4 < dn; l += 8) {
+        a.fma(to_df(Zdf[static_cast<long long>(l) * dn + i]), col[l]);
+        a2.fma(to_df(Zdf[static_cast<long long>(l + 4) * dn + i]), col[l + 4]);
+      }
+      if (l < dn) a.fma(to_df(Zdf[static_cast<long long>(l) * dn + i]), col[l]);
+    }
+    a.merge(a2);
+    part[g][il] = a;
+    __syncthreads();
+    if (g == 0 && i < m) {
+      df_acc s = part[0][il];
+      s.merge(part[1][il]);
+      s.merge(part[2][il]);
+      s.merge(part[3][il]);
+      KB[static_cast<long long>(i) * q2 + c] = s.value();
+    }
+    __syncthreads();
+  }
+}
+
+// Ft (m x q), Tt, S (q x q), float-float; block a computes column a of Ft and
+// row a of Tt and S.  G = [V^T A V | V^T M V] (q x 2q) is symmetrised.
+__global__ void __launch_bounds__(kPenThreads) k_blocks(int m, int q, const df* __restrict__ KB,
+                                                        const double* __restrict__ G, const double* __restrict__ th,
+                                                        df* __restrict__ Ft, df* __restrict__ Tt, df* __restrict__ St) {
+  __shared__ df_acc pt[8][32], ps[8][32];
+  const int a = blockIdx.x, tid = threadIdx.x;
+  const int q2 = 2 * q;
+  for (int i = tid; i < m; i += blockDim.x) {
+    const df k = KB[static_cast<long long>(i) * q2 + a], b = KB[static_cast<long long>(i) * q2 + q + a];
+    Ft[static_cast<long long>(i) * q + a] = df_sub(k, df_mul(to_df(th[i]), b));
+  }
+  const int lane = tid & 31, g = tid >> 5;
+  for (int b0 = 0; b0 < q; b0 += 32) {
+    const int b = b0 + lane;
+    df_acc at = acc_zero(), as = acc_zero();
+    if (b < q)
+      for (int i = g; i < m; i += 8) {
+        const long long r = static_cast<long long>(i) * q2;
+        const df ka = KB[r + a], ba = KB[r + q + a], kb = KB[r + b], bb = KB[r + q + b];
+        const df fb = df_sub(kb, df_mul(to_df(th[i]), bb));  // (K - Theta B)_ib
+        at.fma(ba, fb);
+        at.fma(ka, bb);
+        as.fma(ba, bb);
+      }
+    pt[g][lane] = at;
+    ps[g][lane] = as;
+    __syncthreads();
+    if (g == 0 && b < q) {
+      df_acc t = pt[0][lane], s = ps[0][lane];
+      for (int h = 1; h < 8; ++h) {
+        t.merge(pt[h][lane]);
+        s.merge(ps[h][lane]);
+      }
+      const double ga = 0.5 * (G[a * static_cast<long long>(q2) + b] + G[b * static_cast<long long>(q2) + a]);
+      const double gm =
+          0.5 * (G[a * static_cast<long long>(q2) + q + b] + G[b * static_cast<long long>(q2) + q + a]);
+      Tt[a * q + b] = df_sub(to_df(ga), t.value());
+      St[a * q + b] = df_sub(to_df(gm), s.value());
+    }
+    __syncthreads();
+  }
+}
+
+// x^T At x for x = [x1; x2] (m + q)
+__device__ df pencil_rq(const df* th, const df* F, const df* T, const df* x, int m, int q, df_acc* red, df* out) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  df_acc a = acc_zero();
+  for (int i = tid; i < m + q; i += nt) {
+    if (i < m) {
+      const df fx = dot4(F + i * q, 1, x + m, 1, q).value();
+      // x1_i (theta_i x1_i + 2 (Ft x2)_i)
+      a.fma(x[i], df_add(df_mul(th[i], x[i]), df_add(fx, fx)));
     } else {
       const int r = i - m;
-      for (int k = 0; k < m; ++k) a.fma(F[k * q + r], x[k]);
-      for (int c = 0; c < q; ++c) a.fma(T[r * q + c], x[m + c]);
+      a.fma(x[i], dot4(T + r * q, 1, x + m, 1, q).value());
     }
-    hx[i] = a.value();
   }
-  __syncthreads();
-  df_acc a = acc_zero();
-  for (int i = tid; i < m + q; i += nt) a.fma(x[i], hx[i]);
   return block_sum_df(a, red, out);
 }
 
-__global__ void __launch_bounds__(kSrqiThreads) k_srqi(int m, int q, const double* __restrict__ H,
-                                                       const double* __restrict__ Y3,
-                                                       const double* __restrict__ Lq, double* __restrict__ mu,
-                                                       double* __restrict__ X, int* __restrict__ conv) {
+// x = y / ||y||_Mt (y is first scaled by a power of two near 1 / max |y_i|).  sy: q scratch.
+__device__ void mt_normalise(const df* S, df* y, df* x, df* sy, int m, int q, df_acc* red, df* out) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int n = m + q;
+  float amax = 0.f;
+  for (int i = tid; i < n; i += nt) amax = fmaxf(amax, fabsf(y[i].hi));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  __shared__ float wmax[32];
+  if ((tid & 31) == 0) wmax[tid >> 5] = amax;
+  __syncthreads();
+  float gmax = (tid & 31) < (nt >> 5) ? wmax[tid & 31] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  // power-of-two scale keeps the scaling exact
+  const float sc = gmax > 0.f ? exp2f(-floorf(log2f(gmax))) : 1.f;
+  for (int i = tid; i < n; i += nt) y[i] = df{y[i].hi * sc, y[i].lo * sc};
+  __syncthreads();
+  for (int a = tid; a < q; a += nt) sy[a] = dot4(S + a * q, 1, y + m, 1, q).value();
+  __syncthreads();
+  df_acc acc = acc_zero();
+  for (int i = tid; i < n; i += nt) acc.fma(y[i], i < m ? y[i] : sy[i - m]);
+  const df nrm = df_sqrt(block_sum_df(acc, red, out));
+  const df inv = df_recip(nrm);
+  for (int i = tid; i < n; i += nt) x[i] = df_mul(y[i], inv);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSrqiThreads) k_srqi(int m, int q, const double* __restrict__ thg,
+                                                      const df* __restrict__ KB, const df* __restrict__ Ftg,
+                                                      const df* __restrict__ Ttg, const df* __restrict__ Stg,
+                                                      double* __restrict__ mu, double* __restrict__ X,
+                                                      int* __restrict__ conv) {
   extern __shared__ __align__(16) unsigned char sraw[];
   const int n = m + q;
   df* th = reinterpret_cast<df*>(sraw);
-  df* F = th + m;          // m x q
-  df* T = F + m * q;       // q x q
-  df* S = T + q * q;       // q x (q+1)
-  df* x = S + q * (q + 1); // n
-  df* y = x + n;           // n
-  df* dinv = y + n;        // m
+  df* dv = th + m;          // m: 1 / (theta_i - s)
+  df* F = dv + m;           // m x q
+  df* DF = F + m * q;       // m x q: (Theta - s)^-1 Ft
+  df* T = DF + m * q;       // q x q
+  df* S = T + q * q;        // q x q
+  df* Sc = S + q * q;       // q x (q+1)
+  df* x = Sc + q * (q + 1); // n
+  df* y = x + n;            // n
+  df* sx = y + n;           // q
   __shared__ df_acc red[32];
   __shared__ df outv;
-  __shared__ int piv;
+  __shared__ int prow[kSrqiMaxQ], used[kSrqiMaxQ];
+  __shared__ df ysol[kSrqiMaxQ], rinv;
+  __shared__ GjShared gj;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int j = blockIdx.x;
-  const long long N = n;
-  for (int i = tid; i < m; i += nt) th[i] = df_from_double(H[i * N + i]);
-  for (int idx = tid; idx < m * q; idx += nt) {
-    const int i = idx / q, c = idx % q;
-    F[idx] = df_from_double(H[i * N + m + c]);
-  }
+  const int q2 = 2 * q;
+  for (int i = tid; i < m; i += nt) th[i] = to_df(thg[i]);
+  for (int idx = tid; idx < m * q; idx += nt) F[idx] = Ftg[idx];
   for (int idx = tid; idx < q * q; idx += nt) {
-    const int a = idx / q, b = idx % q;
-    T[idx] = df_from_double(H[(m + a) * N + m + b]);
+    T[idx] = Ttg[idx];
+    S[idx] = Stg[idx];
   }
-  // start: column j of V in the basis of H
-  for (int i = tid; i < n; i += nt) {
-    double v;
-    if (i < m) {
-      v = Y3[i * 3LL * q + j];
-    } else {
-      const int a = i - m;
-      v = a <= j ? Lq[j * q + a] : 0.0;
-    }
-    x[i] = df_from_double(v);
-  }
+  // start: column j of V, i.e. [B e_j; e_j]
+  for (int i = tid; i < n; i += nt)
+    y[i] = i < m ? KB[static_cast<long long>(i) * q2 + q + j] : df{(i - m) == j ? 1.f : 0.f, 0.f};
   __syncthreads();
-  {
-    df_acc a = acc_zero();
-    for (int i = tid; i < n; i += nt) a.fma(x[i], x[i]);
-    const df nrm = df_sqrt(block_sum_df(a, red, &outv));
-    const df inv = df_div(df{1.f, 0.f}, nrm);
-    for (int i = tid; i < n; i += nt) x[i] = df_mul(x[i], inv);
-    __syncthreads();
-  }
-  df sg = rayleigh(th, F, T, x, y, m, q, red, &outv);
+  mt_normalise(S, y, x, sx, m, q, red, &outv);
+  df sg = pencil_rq(th, F, T, x, m, q, red, &outv);
   int ok = 0;
   for (int it = 0; it < kSrqiMaxIt; ++it) {
-    // Schur complement S(s) and its right-hand side
-    const float pvf = 1.0e-30f;
+    // S x2 for the right-hand side
+    for (int a = tid; a < q; a += nt) sx[a] = dot4(S + a * q, 1, x + m, 1, q).value();
     for (int i = tid; i < m; i += nt) {
       df d = df_sub(th[i], sg);
-      if (fabsf(d.hi) < pvf) d = df{pvf, 0.f};
-      dinv[i] = df_div(df{1.f, 0.f}, d);
+      if (fabsf(d.hi) < 1.0e-30f) d = df{1.0e-30f, 0.f};
+      dv[i] = df_recip(d);
     }
     __syncthreads();
+    for (int idx = tid; idx < m * q; idx += nt) DF[idx] = df_mul(dv[idx / q], F[idx]);
+    __syncthreads();
+    // Schur complement S(s) (symmetric: upper triangle, mirrored below) and
+    // right-hand side S x2 - Ft^T (Theta - s)^-1 x1
     for (int idx = tid; idx < q * (q + 1); idx += nt) {
       const int a = idx / (q + 1), b = idx % (q + 1);
+      if (b < a) continue;
       df_acc acc = acc_zero();
       if (b < q) {
         acc.add(T[a * q + b]);
-        if (a == b) acc.add(df_neg(sg));
-        for (int i = 0; i < m; ++i) acc.fma(df_neg(df_mul(F[i * q + a], dinv[i])), F[i * q + b]);
+        acc.fma(df_neg(sg), S[a * q + b]);
+        acc.add(df_neg(dot4(F + a, q, DF + b, q, m).value()));
       } else {
-        acc.add(x[m + a]);
-        for (int i = 0; i < m; ++i) acc.fma(df_neg(df_mul(F[i * q + a], dinv[i])), x[i]);
+        acc.add(sx[a]);
+        acc.add(df_neg(dot4(DF + a, q, x, 1, m).value()));
       }
-      S[idx] = acc.value();
+      Sc[idx] = acc.value();
     }
     __syncthreads();
-    gepp_solve(S, q, &piv);
+    for (int idx = tid; idx < q * q; idx += nt) {
+      const int a = idx / q, b = idx % q;
+      if (b < a) Sc[a * (q + 1) + b] = Sc[b * (q + 1) + a];
+    }
+    __syncthreads();
+    if (q <= 31 && nt == 1024)
+      gj_solve_reg(Sc, q, &gj, ysol);
+    else
+      gj_solve(Sc, q, prow, used, &rinv, ysol);
+    // y2 = solution, y1 = (Theta - s)^-1 (x1 - Ft y2)
     for (int i = tid; i < n; i += nt) {
       if (i < m) {
-        df_acc acc = acc_zero();
-        acc.add(x[i]);
-        for (int c = 0; c < q; ++c) acc.fma(df_neg(F[i * q + c]), S[c * (q + 1) + q]);
-        y[i] = df_mul(dinv[i], acc.value());
+        y[i] = df_mul(dv[i], df_sub(x[i], dot4(F + i * q, 1, ysol, 1, q).value()));
       } else {
-        y[i] = S[(i - m) * (q + 1) + q];
+        y[i] = ysol[i - m];
       }
     }
     __syncthreads();
-    // normalise (scaled by the largest entry first)
-    {
-      float amax = 0.f;
-      for (int i = tid; i < n; i += nt) amax = fmaxf(amax, fabsf(y[i].hi));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      __shared__ float wmax[32];
-      if ((tid & 31) == 0) wmax[tid >> 5] = amax;
-      __syncthreads();
-      float gmax = 0.f;
-      for (int w2 = 0; w2 < (nt >> 5); ++w2) gmax = fmaxf(gmax, wmax[w2]);
-      const float sc = gmax > 0.f ? 1.f / gmax : 1.f;
-      df_acc a = acc_zero();
-      for (int i = tid; i < n; i += nt) {
-        const df z = df_mul_f(y[i], sc);
-        y[i] = z;
-        a.fma(z, z);
-      }
-      const df nrm = df_sqrt(block_sum_df(a, red, &outv));
-      const df inv = df_div(df{1.f, 0.f}, nrm);
-      for (int i = tid; i < n; i += nt) x[i] = df_mul(y[i], inv);
-      __syncthreads();
-    }
-    const df sn = rayleigh(th, F, T, x, y, m, q, red, &outv);
+    mt_normalise(S, y, x, sx, m, q, red, &outv);
+    const df sn = pencil_rq(th, F, T, x, m, q, red, &outv);
     const df dlt = df_abs(df_sub(sn, sg));
     sg = sn;
-    if (it >= 1 && dlt.hi <= 4.0e-14f * fabsf(sn.hi)) {
-      ok = 1;
+    // RQI converges cubically: a step that moves the quotient by d (relative)
+    // started from a vector with angle error ~sqrt(d), so the vector it
+    // produced is accurate to ~d^(3/2): d <= 1e-10 gives working precision
+    if (it >= 1 && dlt.hi <= 1.0e-10f * fabsf(sn.hi)) {
+      ok = it + 1;
       break;
     }
   }
   for (int i = tid; i < n; i += nt) X[i * static_cast<long long>(q) + j] = df_to_double(x[i]);
   if (tid == 0) {
     mu[j] = df_to_double(sg);
-    conv[j] = ok;
+    conv[j] = ok;  // iterations taken when converged, 0 otherwise
   }
 }
 
-// Accept the fast path (flag[0] = 1) or leave it to the dense solver (flag[0] = 0).
-// On acceptance writes the sorted pairs to evals / evecs (n x q).  Sg: q x q scratch.
-__global__ void __launch_bounds__(256) k_srqi_check(int m, int q, const double* __restrict__ H,
-                                                    const double* __restrict__ mu, const double* __restrict__ X,
-                                                    const int* __restrict__ conv, double* __restrict__ Sg,
-                                                    double* __restrict__ evals, double* __restrict__ evecs,
-                                                    int* __restrict__ flag) {
-  __shared__ int okf, negs, theta_cnt;
+// Accept the fast path (flag[0] = 1) or leave it to the dense solver (flag[0] =
+// 0).  On acceptance writes the ascending values to evals and the vectors [a; b]
+// ((m + q) x q) to evecs, made Mt-orthonormal to second order by the first-order
+// Lowdin correction X (I - E / 2), E = X^T Mt X - I (the overlaps of vectors of
+// nearly equal values are only accurate to residual / gap).
+__global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const double* __restrict__ thg,
+                                                            const df* __restrict__ Ftg, const df* __restrict__ Ttg,
+                                                            const df* __restrict__ Stg,
+                                                            const double* __restrict__ mu,
+                                                            const double* __restrict__ Xg,
+                                                            const int* __restrict__ conv,
+                                                            double* __restrict__ evals, double* __restrict__ evecs,
+                                                            int* __restrict__ flag) {
+  extern __shared__ __align__(16) unsigned char craw[];
+  const int n = m + q;
+  df* X = reinterpret_cast<df*>(craw);  // n x q
+  df* SX = X + n * q;                   // q x q: S X2
+  df* Sc = SX + q * q;                  // q x q: S(s*)
+  df* Sl = Sc + q * q;                  // q x q: copy of S for its LDL^T
+  df* Ov = Sl + q * q;                  // q x q: X^T Mt X - I
+  df* dv = Ov + q * q;                  // m: 1 / (theta_i - s*)
+  df* F = dv + m;                       // m x q
+  __shared__ int okf, negs, nonpd, theta_cnt;
   __shared__ int perm[kSrqiMaxQ];
-  __shared__ double sstar;
-  const int n = m + q, tid = threadIdx.x, nt = blockDim.x;
-  const long long N = n;
+  __shared__ df sstar;
+  __shared__ LdlShared lsh;
+  __shared__ float omax;
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
     okf = 1;
     negs = 0;
+    nonpd = 0;
+    omax = 0.f;
     double mx = mu[0];
     for (int i = 1; i < q; ++i) mx = fmax(mx, mu[i]);
-    sstar = mx + 1.0e-9 * fabs(mx) + 1.0e-300;
-    int cnt = 0;
-    for (int i = 0; i < m; ++i)
-      if (H[i * N + i] < sstar) ++cnt;
-    theta_cnt = cnt;
+    sstar = to_df(mx + 1.0e-9 * fabs(mx) + 1.0e-300);
   }
+  for (int idx = tid; idx < n * q; idx += nt) X[idx] = to_df(Xg[idx]);
+  for (int idx = tid; idx < q * q; idx += nt) Sl[idx] = Stg[idx];
+  for (int idx = tid; idx < m * q; idx += nt) F[idx] = Ftg[idx];
   __syncthreads();
+  if (tid < 32) {
+    const double ss = df_to_double(sstar);
+    int cnt = 0;
+    for (int i = tid; i < m; i += 32) cnt += thg[i] < ss;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (tid == 0) theta_cnt = cnt;
+  }
   for (int j = tid; j < q; j += nt)
     if (!conv[j]) okf = 0;
-  // the computed vectors must be mutually orthogonal (distinct eigenvectors)
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, j = idx % q;
+    SX[idx] = dot4(Sl + a * q, 1, X + m * q + j, q, q).value();
+  }
+  for (int i = tid; i < m; i += nt) {
+    df d = df_sub(to_df(thg[i]), sstar);
+    if (fabsf(d.hi) < 1.0e-30f) d = df{-1.0e-30f, 0.f};
+    dv[i] = df_div(df{1.f, 0.f}, d);
+  }
+  __syncthreads();
+  // Mt-overlaps X^T Mt X - I (upper triangle computed, mirrored)
   for (int idx = tid; idx < q * q; idx += nt) {
     const int a = idx / q, b = idx % q;
-    if (b <= a) continue;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i)
-      s = fma(X[i * static_cast<long long>(q) + a], X[i * static_cast<long long>(q) + b], s);
-    if (fabs(s) > 1.0e-6) okf = 0;
+    if (b < a) continue;
+    df_acc s = dot4(X + a, q, X + b, q, m);
+    s.merge(dot4(X + m * q + a, q, SX + b, q, q));
+    if (a == b) s.add(df{-1.f, 0.f});
+    const df v = s.value();
+    Ov[a * q + b] = v;
+    Ov[b * q + a] = v;
+    const float f = fabsf(df_float(v));
+    atomicMax(reinterpret_cast<int*>(&omax), __float_as_int(f));  // f >= 0 (NaN sorts above)
   }
+  // Schur complement at s*: Tt - s* S - Ft^T (Theta - s*)^-1 Ft (upper triangle, mirrored)
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, b = idx % q;
+    if (b < a) continue;
+    df_acc acc = acc_zero();
+    acc.add(Ttg[idx]);
+    acc.fma(df_neg(sstar), Sl[idx]);
+    acc.add(df_neg(dot4w(F + a, q, dv, F + b, q, m).value()));
+    Sc[idx] = acc.value();
+  }
+  __syncthreads();
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, b = idx % q;
+    if (b < a) Sc[idx] = Sc[b * q + a];
+  }
+  __syncthreads();
+  if (!(omax <= 1.0e-6f)) okf = 0;  // also rejects NaN
   __syncthreads();
   if (!okf) {
     if (tid == 0) flag[0] = 0;
     return;
   }
-  // Sylvester inertia of H - s* I: theta_cnt + negative pivots of LDL^T(S(s*))
-  for (int idx = tid; idx < q * q; idx += nt) {
-    const int a = idx / q, b = idx % q;
-    double acc = H[(m + a) * N + m + b] - (a == b ? sstar : 0.0);
-    for (int i = 0; i < m; ++i) acc -= H[i * N + m + a] * H[i * N + m + b] / (H[i * N + i] - sstar);
-    Sg[idx] = acc;
-  }
-  __syncthreads();
-  for (int k = 0; k < q; ++k) {
-    double piv = Sg[k * q + k];
-    if (fabs(piv) < 1.0e-300) piv = -1.0e-300;
-    if (tid == 0 && piv < 0.0) ++negs;
-    const int r = q - k - 1;
-    for (int idx = tid; idx < r * r; idx += nt) {
-      const int i = k + 1 + idx / r, jj = k + 1 + idx % r;
-      Sg[i * q + jj] -= Sg[i * q + k] * Sg[k * q + jj] / piv;
+  // LDL^T of S(s*) (negative pivots) and of S (must be positive definite)
+  if (q <= 31 && nt == 1024)
+    ldl_inertia_reg(Sc, Sl, q, &lsh, &negs, &nonpd);
+  else
+    for (int k = 0; k < q; ++k) {
+      const df pc = Sc[k * q + k], pl = Sl[k * q + k];
+      if (tid == 0) {
+        if (df_lt0(pc) || pc.hi == 0.f) ++negs;
+        if (!(pl.hi > 0.f)) nonpd = 1;
+      }
+      const df ic = df_recip((pc.hi == 0.f) ? df{-1.0e-30f, 0.f} : pc);
+      const df il = df_recip((pl.hi > 0.f) ? pl : df{1.f, 0.f});
+      const int r = q - k - 1;
+      __syncthreads();
+      for (int idx = tid; idx < 2 * r * r; idx += nt) {
+        const int which = idx / (r * r), e = idx % (r * r);
+        const int i = k + 1 + e / r, jj = k + 1 + e % r;
+        df* Mx = which ? Sl : Sc;
+        const df fac = df_mul(Mx[i * q + k], which ? il : ic);
+        Mx[i * q + jj] = df_sub(Mx[i * q + jj], df_mul(fac, Mx[k * q + jj]));
+      }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  if (theta_cnt + negs != q) {
+  if (nonpd || theta_cnt + negs != q) {
     if (tid == 0) flag[0] = 0;
     return;
   }
@@ -945,11 +1238,161 @@ __global__ void __launch_bounds__(256) k_srqi_check(int m, int q, const double* 
   }
   __syncthreads();
   for (int c = tid; c < q; c += nt) evals[c] = mu[perm[c]];
-  for (long long idx = tid; idx < N * q; idx += nt) {
-    const int i = static_cast<int>(idx / q), c = static_cast<int>(idx % q);
-    evecs[idx] = X[i * static_cast<long long>(q) + perm[c]];
+  for (int idx = tid; idx < n * q; idx += nt) {
+    const int i = idx / q, c = idx % q, b = perm[c];
+    const df corr = dot4(X + i * q, 1, Ov + b, q, q).value();
+    evecs[idx] = df_to_double(df_sub(X[i * q + b], df{0.5f * corr.hi, 0.5f * corr.lo}));
   }
   if (tid == 0) flag[0] = 1;
+}
+
+// Fallback: H = [[Theta, Ft L^-T], [L^-1 Ft^T, L^-1 Tt L^-T]] with S = L L^T
+// (float-float Cholesky; status = ENOTSPD when S is not positive definite).
+__global__ void __launch_bounds__(512) k_std_form(int m, int q, const double* __restrict__ thg,
+                                                  const df* __restrict__ Ft, const df* __restrict__ Tt,
+                                                  const df* __restrict__ St, df* __restrict__ L, df* __restrict__ Xs,
+                                                  double* __restrict__ H, int* status, const int* skip,
+                                                  int* nfallback) {
+  if (skip && *skip) return;
+  if (threadIdx.x == 0 && nfallback) atomicAdd(nfallback, 1);
+  extern __shared__ __align__(16) unsigned char fraw[];
+  df* Ls = reinterpret_cast<df*>(fraw);  // q x q
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int n = m + q;
+  const long long N = n;
+  if (tid == 0) bad = 0;
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int r = idx / q, c = idx % q;
+    Ls[idx] = c <= r ? St[idx] : df{0.f, 0.f};
+  }
+  __syncthreads();
+  for (int k = 0; k < q; ++k) {
+    if (tid == 0) {
+      const df d = Ls[k * q + k];
+      if (!(d.hi > 0.f)) {
+        bad = 1;
+        Ls[k * q + k] = df{1.f, 0.f};
+      } else {
+        Ls[k * q + k] = df_sqrt(d);
+      }
+    }
+    __syncthreads();
+    const df inv = df_div(df{1.f, 0.f}, Ls[k * q + k]);
+    for (int i = k + 1 + tid; i < q; i += nt) Ls[i * q + k] = df_mul(Ls[i * q + k], inv);
+    __syncthreads();
+    const int r = q - k - 1;
+    for (int idx = tid; idx < r * r; idx += nt) {
+      const int i = k + 1 + idx / r, j = k + 1 + idx % r;
+      if (j <= i) Ls[i * q + j] = df_sub(Ls[i * q + j], df_mul(Ls[i * q + k], Ls[j * q + k]));
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0 && status) status[0] = AMGEIG_ENOTSPD;
+    return;
+  }
+  for (int idx = tid; idx < q * q; idx += nt) L[idx] = Ls[idx];
+  // Xs = L^-1 Tt (columns in parallel; each thread reads back only what it wrote)
+  for (int c = tid; c < q; c += nt)
+    for (int i = 0; i < q; ++i) {
+      df_acc s = acc_zero();
+      s.add(Tt[i * q + c]);
+      for (int k = 0; k < i; ++k) s.fma(df_neg(Ls[i * q + k]), Xs[k * q + c]);
+      Xs[i * q + c] = df_div(s.value(), Ls[i * q + i]);
+    }
+  __syncthreads();
+  // T = L^-1 Xs^T, written (symmetrised below) into H's lower-right block
+  for (int c = tid; c < q; c += nt)
+    for (int i = 0; i < q; ++i) {
+      df_acc s = acc_zero();
+      s.add(Xs[c * q + i]);
+      for (int k = 0; k < i; ++k) s.fma(df_neg(Ls[i * q + k]), to_df(H[(m + k) * N + m + c]));
+      H[(m + i) * N + m + c] = df_to_double(df_div(s.value(), Ls[i * q + i]));
+    }
+  for (long long idx = tid; idx < static_cast<long long>(m) * m; idx += nt) {
+    const int r = static_cast<int>(idx / m), c = static_cast<int>(idx % m);
+    H[r * N + c] = (r == c) ? thg[r] : 0.0;
+  }
+  // F rows: f_i = L^-1 Ft_i^T
+  for (int r = tid; r < m; r += nt) {
+    df f[kStdMaxQ];
+    for (int i = 0; i < q; ++i) {
+      df_acc s = acc_zero();
+      s.add(Ft[r * q + i]);
+      for (int k = 0; k < i; ++k) s.fma(df_neg(Ls[i * q + k]), f[k]);
+      f[i] = df_div(s.value(), Ls[i * q + i]);
+      const double v = df_to_double(f[i]);
+      H[r * N + m + i] = v;
+      H[(m + i) * N + r] = v;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const int a = idx / q, b = idx % q;
+    if (b <= a) continue;
+    const double v = 0.5 * (H[(m + a) * N + m + b] + H[(m + b) * N + m + a]);
+    H[(m + a) * N + m + b] = v;
+    H[(m + b) * N + m + a] = v;
+  }
+}
+
+// Fallback back-map: b = L^-T b_std in place (rows m.. of evecs, n x q).
+__global__ void k_std_back(int m, int q, const df* __restrict__ L, double* __restrict__ evecs, const int* skip) {
+  if (skip && *skip) return;
+  const int c = threadIdx.x;
+  if (c >= q) return;
+  df b[kStdMaxQ];
+  for (int i = q - 1; i >= 0; --i) {
+    df_acc s = acc_zero();
+    s.add(to_df(evecs[(m + i) * static_cast<long long>(q) + c]));
+    for (int k = i + 1; k < q; ++k) s.fma(df_neg(L[k * q + i]), b[k]);
+    b[i] = df_div(s.value(), L[i * q + i]);
+  }
+  for (int i = 0; i < q; ++i) evecs[(m + i) * static_cast<long long>(q) + c] = df_to_double(b[i]);
+}
+
+// Xc = Z_m (a - B b) (d_n x q) and Y = b (q x q) from evecs = [a; b].  Every
+// block forms a - B b in shared memory (b staged there first), then its share
+// of the rows of Xc.
+__global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, const float2* __restrict__ Zdf,
+                                                    const df* __restrict__ KB, const double* __restrict__ evecs,
+                                                    double* __restrict__ Xc, float2* __restrict__ Xc2,
+                                                    double* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char xraw[];
+  df* bs = reinterpret_cast<df*>(xraw);  // q x q
+  df* tmp = bs + q * q;                  // m x q
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int q2 = 2 * q;
+  for (int idx = tid; idx < q * q; idx += nt) {
+    const double v = evecs[static_cast<long long>(m) * q + idx];
+    bs[idx] = to_df(v);
+    if (blockIdx.x == 0) Y[idx] = v;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * q; idx += nt) {
+    const int i = idx / q, j = idx % q;
+    const df* Bi = KB + static_cast<long long>(i) * q2 + q;
+    tmp[idx] = df_sub(to_df(evecs[idx]), dot4(Bi, 1, bs + j, q, q).value());
+  }
+  __syncthreads();
+  const int rows = (dn + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rows, r1 = min(dn, r0 + rows);
+  for (int idx = tid; idx < (r1 - r0) * q; idx += nt) {
+    const int l = r0 + idx / q, j = idx % q;
+    const float2* zl = Zdf + static_cast<long long>(l) * dn;
+    df_acc s0 = acc_zero(), s1 = acc_zero();
+    int i = 0;
+    for (; i + 2 <= m; i += 2) {
+      s0.fma(to_df(zl[i]), tmp[i * q + j]);
+      s1.fma(to_df(zl[i + 1]), tmp[(i + 1) * q + j]);
+    }
+    if (i < m) s0.fma(to_df(zl[i]), tmp[i * q + j]);
+    s0.merge(s1);
+    const df v = s0.value();
+    Xc[static_cast<long long>(l) * q + j] = df_to_double(v);
+    if (Xc2) Xc2[static_cast<long long>(l) * q + j] = make_float2(v.hi, v.lo);
+  }
 }
 
 // ------------------------------------------------------------ small FP64 kernels
@@ -1038,125 +1481,6 @@ __global__ void k_scale_cols_inv(int rows, int cols, const double* __restrict__ 
     out[i] = Z[i] / th[i % cols];
 }
 
-// Y3 = [B | K | Theta B] from KB = [K | B] (dn x 2q)
-__global__ void k_build_y3(int dn, int q, const double* __restrict__ KB, const double* __restrict__ th,
-                           double* __restrict__ Y3) {
-  const long long total = static_cast<long long>(dn) * q;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int r = static_cast<int>(i / q), c = static_cast<int>(i % q);
-    const double K = KB[r * 2LL * q + c], B = KB[r * 2LL * q + q + c];
-    Y3[r * 3LL * q + c] = B;
-    Y3[r * 3LL * q + q + c] = K;
-    Y3[r * 3LL * q + 2 * q + c] = th[r] * B;
-  }
-}
-
-// Assemble H from the float64 pieces (one block):
-//   S = G_M - B^T B, L = chol(S), N = G_A - B^T K - K^T B + B^T Theta B,
-//   T = L^-1 N L^-T, F = (K - Theta B) L^-T, H = [[Theta, F], [F^T, T]].
-__global__ void k_pencil_h(int dn, int q, const double* __restrict__ G, const double* __restrict__ P3,
-                           const double* __restrict__ Y3, const double* __restrict__ th, double* __restrict__ Lq,
-                           double* __restrict__ Sq, double* __restrict__ Nq, double* __restrict__ H, int* status) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int n = dn + q;
-  const long long ld3 = 3LL * q;
-  for (int idx = tid; idx < q * q; idx += nt) {
-    const int a = idx / q, b = idx % q;
-    const double gm = 0.5 * (G[a * 2LL * q + q + b] + G[b * 2LL * q + q + a]);
-    const double ga = 0.5 * (G[a * 2LL * q + b] + G[b * 2LL * q + a]);
-    const double btb = 0.5 * (P3[a * ld3 + b] + P3[b * ld3 + a]);
-    const double btk_ab = P3[a * ld3 + q + b], btk_ba = P3[b * ld3 + q + a];
-    const double btthb = 0.5 * (P3[a * ld3 + 2 * q + b] + P3[b * ld3 + 2 * q + a]);
-    Sq[idx] = gm - btb;
-    Nq[idx] = ga - btk_ab - btk_ba + btthb;
-  }
-  __syncthreads();
-  // Cholesky of Sq into Lq
-  for (int idx = tid; idx < q * q; idx += nt) {
-    const int r = idx / q, c = idx % q;
-    Lq[idx] = (c <= r) ? Sq[idx] : 0.0;
-  }
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int k = 0; k < q; ++k) {
-    if (tid == 0) {
-      const double d = Lq[k * q + k];
-      if (!(d > 0.0)) {
-        bad = 1;
-        Lq[k * q + k] = 1.0;
-      } else {
-        Lq[k * q + k] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    const double piv = Lq[k * q + k];
-    for (int i = k + 1 + tid; i < q; i += nt) Lq[i * q + k] /= piv;
-    __syncthreads();
-    const int m = q - k - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-      if (j <= i) Lq[i * q + j] -= Lq[i * q + k] * Lq[j * q + k];
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    if (tid == 0 && status) status[0] = AMGEIG_ENOTSPD;
-    return;
-  }
-  // X = L^-1 N  (columns), then T = L^-1 X^T  (N symmetric)
-  for (int c = tid; c < q; c += nt) {
-    for (int i = 0; i < q; ++i) {
-      double s = Nq[i * q + c];
-      for (int k = 0; k < i; ++k) s -= Lq[i * q + k] * Sq[k * q + c];
-      Sq[i * q + c] = s / Lq[i * q + i];
-    }
-  }
-  __syncthreads();
-  for (int c = tid; c < q; c += nt) {
-    for (int i = 0; i < q; ++i) {
-      double s = Sq[c * q + i];  // X^T(i, c) = X(c, i)
-      for (int k = 0; k < i; ++k) s -= Lq[i * q + k] * Nq[k * q + c];
-      Nq[i * q + c] = s / Lq[i * q + i];
-    }
-  }
-  __syncthreads();
-  const long long Nn = n;
-  for (long long idx = tid; idx < static_cast<long long>(dn) * dn; idx += nt) {
-    const int r = static_cast<int>(idx / dn), c = static_cast<int>(idx % dn);
-    H[r * Nn + c] = (r == c) ? th[r] : 0.0;
-  }
-  // F rows: f_i = L^-1 (K_i - theta_i B_i)^T
-  for (int r = tid; r < dn; r += nt) {
-    for (int i = 0; i < q; ++i) {
-      double s = Y3[r * ld3 + q + i] - th[r] * Y3[r * ld3 + i];
-      for (int k = 0; k < i; ++k) s -= Lq[i * q + k] * H[r * Nn + dn + k];
-      const double f = s / Lq[i * q + i];
-      H[r * Nn + dn + i] = f;
-      H[(dn + i) * Nn + r] = f;
-    }
-  }
-  for (int idx = tid; idx < q * q; idx += nt) {
-    const int a = idx / q, b = idx % q;
-    H[(dn + a) * Nn + dn + b] = 0.5 * (Nq[a * q + b] + Nq[b * q + a]);
-  }
-}
-
-// Yv = L^-T b (b = Yh[dn:, :]), tmp = a (Yh[:dn, :]) -- one block
-__global__ void k_pencil_back(int dn, int q, const double* __restrict__ Yh, const double* __restrict__ Lq,
-                              double* __restrict__ Yv, double* __restrict__ tmp) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int c = tid; c < q; c += nt) {
-    for (int i = q - 1; i >= 0; --i) {
-      double s = Yh[(dn + i) * static_cast<long long>(q) + c];
-      for (int k = i + 1; k < q; ++k) s -= Lq[k * q + i] * Yv[k * q + c];
-      Yv[i * q + c] = s / Lq[i * q + i];
-    }
-  }
-  for (long long idx = tid; idx < static_cast<long long>(dn) * q; idx += nt) tmp[idx] = Yh[idx];
-}
-
 size_t syev_smem_base(int n, int nwant) {
   return (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
           3 * sizeof(df) * n + 15) &
@@ -1177,21 +1501,18 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
   w->nwant_max = dn > qmax ? dn : qmax;
   const long long nm = w->nmax;
   const long long nwm = w->nwant_max;
-  w->gsc_doubles = gram_scratch_doubles(dn, 2 * qmax, 3 * qmax);
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 8);
   };
-  alloc((void**)&w->KB, sizeof(double) * dn * 2 * qmax);
-  alloc((void**)&w->Y3, sizeof(double) * dn * 3 * qmax);
-  alloc((void**)&w->P3, sizeof(double) * 6 * qmax * qmax);
-  alloc((void**)&w->gsc, sizeof(double) * w->gsc_doubles);
+  alloc((void**)&w->KB, sizeof(df) * dn * 2 * qmax);
+  alloc((void**)&w->Ft, sizeof(df) * dn * qmax);
+  alloc((void**)&w->Tt, sizeof(df) * qmax * qmax);
+  alloc((void**)&w->St, sizeof(df) * qmax * qmax);
+  alloc((void**)&w->Lq, sizeof(df) * qmax * qmax);
+  alloc((void**)&w->Xq, sizeof(df) * qmax * qmax);
   alloc((void**)&w->H, sizeof(double) * nm * nm);
-  alloc((void**)&w->Lq, sizeof(double) * qmax * qmax);
-  alloc((void**)&w->Sq, sizeof(double) * qmax * qmax);
-  alloc((void**)&w->Nq, sizeof(double) * qmax * qmax);
   alloc((void**)&w->Yh, sizeof(double) * nm * nwm);
-  alloc((void**)&w->tmp, sizeof(double) * dn * qmax);
   alloc((void**)&w->W, sizeof(df) * nm * (nm + 1));
   alloc((void**)&w->tau, sizeof(df) * nm);
   alloc((void**)&w->dd, sizeof(df) * nm);
@@ -1216,9 +1537,8 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
 
 void pencil_work_destroy(PencilWork* w) {
   if (!w) return;
-  void* ptrs[] = {w->KB, w->Y3, w->P3, w->gsc, w->H, w->Lq, w->Sq, w->Nq, w->Yh, w->tmp, w->W,
-                  w->tau, w->dd, w->ee, w->fac, w->Zt, w->rr, w->perm, w->Lm, w->Hs,
-                  w->sr_mu, w->sr_X, w->sr_conv, w->sr_flag};
+  void* ptrs[] = {w->KB, w->Ft, w->Tt, w->St, w->Lq, w->Xq, w->H, w->Yh, w->W, w->tau, w->dd, w->ee,
+                  w->fac, w->Zt, w->rr, w->perm, w->Lm, w->Hs, w->sr_mu, w->sr_X, w->sr_conv, w->sr_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete w;
@@ -1277,32 +1597,48 @@ void launch_syev_df_into(int n, int nwant, const double* H, double* evals, doubl
                                        nullptr);
 }
 
-void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C, const double* G, const double* Z,
-                         const double* theta, double* mu, double* Xc, double* Y, int* status, cudaStream_t st) {
+void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64, const float2* Cdf,
+                         const double* G, const float2* Zdf, const double* theta, double* mu, double* Xc,
+                         float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback) {
   const int n = m + q;
-  // five kernels launched here; the GEMM, Gram and eigensolver launchers count their own
-  ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * q * q + 1.0 * n * n + 1.0 * m * q), 0.0, 5);
-  // K | B = Z_m^T [C_A | C_M]   (Z_m: the first m columns of Z)
-  launch_gemm_f64(m, 2 * q, dn, 1.0, Z, dn, true, C, 2 * q, false, 0.0, w->KB, 2 * q, st);
-  k_build_y3<<<ceil_div(static_cast<long long>(m) * q, 256), 256, 0, st>>>(m, q, w->KB, theta, w->Y3);
-  // P3 = [B K]^T [B K Theta B]
-  launch_gram_strided(m, w->Y3, 3 * q, 2 * q, w->Y3, 3 * q, 3 * q, w->gsc, w->P3, st);
-  k_pencil_h<<<1, 512, 0, st>>>(m, q, G, w->P3, w->Y3, theta, w->Lq, w->Sq, w->Nq, w->H, status);
+  auto smem_attr = [](const void* f, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  const size_t kbs = sizeof(df) * dn;
+  const size_t srs = sizeof(df) * (2.0 * m + 2.0 * m * q + 3.0 * q * q + 2.0 * q + 2.0 * n);
+  const size_t chs = sizeof(df) * (1.0 * n * q + 4.0 * q * q + m + 1.0 * m * q);
+  const size_t fs = sizeof(df) * q * q;
+  const size_t xs = sizeof(df) * (1.0 * m * q + 1.0 * q * q);
+  const bool fast = q <= kSrqiMaxQ && srs <= 200 * 1024 && chs <= 200 * 1024;
+  // kernels launched here; the dense eigensolver's launcher counts its own
+  ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * m * q + 3.0 * q * q + 1.0 * n * q), 0.0,
+               fast ? 7 : 5);
+  if (Cdf) {
+    smem_attr((const void*)k_kb<float2>, kbs);
+    k_kb<float2><<<2 * q, kPenThreads, kbs, st>>>(dn, m, q, Zdf, Cdf, w->KB);
+  } else {
+    smem_attr((const void*)k_kb<double>, kbs);
+    k_kb<double><<<2 * q, kPenThreads, kbs, st>>>(dn, m, q, Zdf, C64, w->KB);
+  }
+  k_blocks<<<q, kPenThreads, 0, st>>>(m, q, w->KB, G, theta, w->Ft, w->Tt, w->St);
   // structured Rayleigh quotient iteration, checked by inertia; the dense
   // float-float solver runs only when the check rejects it
-  const size_t srs = sizeof(df) * (2.0 * m + 1.0 * m * q + 2.0 * q * q + q + 2.0 * n);
   const int* skip = nullptr;
-  if (q <= kSrqiMaxQ && srs <= 200 * 1024) {
-    if (srs > 48 * 1024) cudaFuncSetAttribute(k_srqi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)srs);
-    k_srqi<<<q, kSrqiThreads, srs, st>>>(m, q, w->H, w->Y3, w->Lq, w->sr_mu, w->sr_X, w->sr_conv);
-    k_srqi_check<<<1, 256, 0, st>>>(m, q, w->H, w->sr_mu, w->sr_X, w->sr_conv, w->Sq, mu, w->Yh, w->sr_flag);
+  if (fast) {
+    smem_attr((const void*)k_srqi, srs);
+    smem_attr((const void*)k_srqi_check, chs);
+    k_srqi<<<q, kSrqiThreads, srs, st>>>(m, q, theta, w->KB, w->Ft, w->Tt, w->St, w->sr_mu, w->sr_X, w->sr_conv);
+    k_srqi_check<<<1, kSrqiThreads, chs, st>>>(m, q, theta, w->Ft, w->Tt, w->St, w->sr_mu, w->sr_X, w->sr_conv, mu,
+                                              w->Yh, w->sr_flag);
     skip = w->sr_flag;
   }
+  smem_attr((const void*)k_std_form, fs);
+  k_std_form<<<1, 512, fs, st>>>(m, q, theta, w->Ft, w->Tt, w->St, w->Lq, w->Xq, w->H, status, skip, nfallback);
   launch_syev_df(w, n, q, w->H, mu, w->Yh, st, skip);
-  k_pencil_back<<<1, 256, 0, st>>>(m, q, w->Yh, w->Lq, Y, w->tmp);
-  // tmp = a - B Yv ; Xc = Z_m tmp
-  launch_gemm_f64(m, q, q, -1.0, w->Y3, 3 * q, false, Y, q, false, 1.0, w->tmp, q, st);
-  launch_gemm_f64(dn, q, m, 1.0, Z, dn, false, w->tmp, q, false, 0.0, Xc, q, st);
+  k_std_back<<<1, kStdMaxQ, 0, st>>>(m, q, w->Lq, w->Yh, skip);
+  // Xc = Z_m (a - B b), Y = b
+  smem_attr((const void*)k_xc, xs);
+  k_xc<<<16, kPenThreads, xs, st>>>(dn, m, q, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
 }
 
 void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,

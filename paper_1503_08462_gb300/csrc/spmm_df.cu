@@ -10,6 +10,8 @@
 // I_k^n, I_n^k and the recombination.  Rounding: ~2^-48 relative per
 // operation; the cancellation in lambda M u - A u raises the floor of the
 // relative residual to ~2^-48 lambda_max / lambda (float64: 2^-53 times the same).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "prof.cuh"
@@ -45,24 +47,26 @@ Geo geo_for(int width) {
 
 // ---------------------------------------------------------------- defect
 // R = lambda o (M U) - A U, rounded to float32 with row stride ldr (zero padding),
-// per-block sums of r^2 and (Mu)^2 in float64 (fixed order)
+// per-block sums of r^2 and (Mu)^2 (fixed order).  The sums accumulate in
+// float-float: float64 arithmetic here, once per row and column, cost more
+// than the whole sparse product on this GPU.
 template <int CPT>
-__global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(kThreads, 4) k_defect_df(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                         const float2* __restrict__ a, const float2* __restrict__ m,
                                                         const float2* __restrict__ U, int q,
                                                         const double* __restrict__ lam, float* __restrict__ R,
                                                         int ldr, int G, double* __restrict__ partials) {
   // grid-stride over row groups; each thread keeps its columns' sums of r^2 and
   // (Mu)^2 in registers, so a block writes one row of partials
-  extern __shared__ double sred[];
+  extern __shared__ df_acc sred[];
   const int rpb = blockDim.x / G;
   const int g = threadIdx.x / G;
   const int lane = threadIdx.x % G;
-  double rr[CPT], m2[CPT];
+  df_acc rr[CPT], m2[CPT];
   df lamc[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
-    rr[t] = m2[t] = 0.0;
+    rr[t] = m2[t] = acc_zero();
     const int c = lane + t * G;
     lamc[t] = c < q ? df_from_double(lam[c]) : df{0.f, 0.f};
   }
@@ -71,6 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __rest
 #pragma unroll
     for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
     const int p0 = rp[row], p1 = rp[row + 1];
+#pragma unroll 4
     for (int p = p0; p < p1; ++p) {
       const int j = ci[p];
       const df av = ld2(a, p), mv = ld2(m, p);
@@ -93,9 +98,8 @@ __global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __rest
         const df r = df_sub(df_mul(lamc[t], mu), aa[t].value());
         const float rf = df_float(r);
         R[static_cast<long long>(row) * ldr + c] = rf;
-        rr[t] = fma(static_cast<double>(rf), static_cast<double>(rf), rr[t]);
-        const double md = df_to_double(mu);
-        m2[t] = fma(md, md, m2[t]);
+        rr[t].fma(df{rf, 0.f}, df{rf, 0.f});
+        m2[t].fma(mu, mu);
       }
     }
     for (int c = q + lane; c < ldr; c += G) R[static_cast<long long>(row) * ldr + c] = 0.f;
@@ -110,9 +114,9 @@ __global__ void __launch_bounds__(kThreads) k_defect_df(int n, const int* __rest
   __syncthreads();
   for (int idx = threadIdx.x; idx < 2 * q; idx += blockDim.x) {
     const int which = idx / q, c = idx % q;
-    double s = 0.0;
-    for (int r = 0; r < rpb; ++r) s += sred[r * 2 * W + which * W + c];
-    partials[static_cast<long long>(blockIdx.x) * 2 * q + idx] = s;
+    df_acc s = acc_zero();
+    for (int r = 0; r < rpb; ++r) s.merge(sred[r * 2 * W + which * W + c]);
+    partials[static_cast<long long>(blockIdx.x) * 2 * q + idx] = df_to_double(s.value());
   }
 }
 
@@ -234,6 +238,45 @@ __global__ void __launch_bounds__(kThreads) k_recombine_df2(int n, const float2*
   }
 }
 
+// Row-per-thread form for q <= Q <= 32: each thread keeps all Q accumulators of
+// its row in registers, so one V value feeds Q compensated products and the
+// rows of Y (zero-padded to Q columns, shared) are read as 16-byte broadcasts.
+template <int Q>
+__global__ void __launch_bounds__(kThreads) k_recombine_rows(int n, const float2* __restrict__ Xp,
+                                                             const float2* __restrict__ V,
+                                                             const double* __restrict__ Y, int q,
+                                                             float2* __restrict__ U) {
+  __shared__ __align__(16) float2 ys[Q * Q];
+  for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+    const int d = i / Q, c = i % Q;
+    const df v = (d < q && c < q) ? df_from_double(Y[d * q + c]) : df{0.f, 0.f};
+    ys[i] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  const long long row = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const long long base = row * q;
+  df_acc acc[Q];
+#pragma unroll
+  for (int c = 0; c < Q; ++c) {
+    acc[c] = acc_zero();
+    if (c < q) acc[c].add(ld2(Xp, base + c));
+  }
+  for (int d = 0; d < q; ++d) {
+    const df v = ld2(V, base + d);
+    const float4* yr = reinterpret_cast<const float4*>(ys + d * Q);
+#pragma unroll
+    for (int c = 0; c < Q; c += 2) {
+      const float4 y2 = yr[c / 2];
+      acc[c].fma(v, df{y2.x, y2.y});
+      acc[c + 1].fma(v, df{y2.z, y2.w});
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < Q; ++c)
+    if (c < q) st2(U, base + c, acc[c].value());
+}
+
 // ---------------------------------------------------------------- Gram V^T W (df inputs)
 // G = V^T [A V | M V] (q x 2q).  Both halves are symmetric, so only the pairs
 // a <= b of each half are formed: np = q (q + 1) pairs.  A block stages a slab
@@ -297,6 +340,86 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_df_sym(int rows, const fl
   for (int s = 0; s < kGramMaxPairs; ++s) {
     const int idx = threadIdx.x + s * blockDim.x;
     if (idx < np) part[static_cast<long long>(blockIdx.x) * np + idx] = df_to_double(acc[s].value());
+  }
+}
+
+// Register-tiled form of the same product for q <= 32: thread (g, t) owns the
+// 4 x 4 output tile t of the upper triangle of one half (tiles (ta, tb) with
+// ta <= tb, both halves: ntiles = T (T + 1), T = ceil(q / 4)) and accumulates
+// rows g, g + rg, ... of each staged slab; 8 float-float loads feed 16
+// compensated products.  The rg partial tiles are merged in a fixed order and
+// written in the pair layout of k_gram_df_sym.
+constexpr int kGtThreads = 256;
+
+__global__ void __launch_bounds__(kGtThreads) k_gram_df_tiled(int rows, const float2* __restrict__ V, int q,
+                                                              const float2* __restrict__ W, int chunk_rows,
+                                                              int T, int rg, int slab, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char graw[];
+  const int qp = 4 * T;
+  float2* Vs = reinterpret_cast<float2*>(graw);  // slab x qp
+  float2* Ws = Vs + slab * qp;                   // slab x 2 qp
+  const int ntiles = T * (T + 1);
+  const int tid = threadIdx.x;
+  const int t = tid % ntiles, g = tid / ntiles;
+  const bool active = g < rg;
+  // tile t -> half, (ta, tb) with ta <= tb
+  const int half = t >= T * (T + 1) / 2;
+  int r = t - half * (T * (T + 1) / 2), ta = 0;
+  while (r >= T - ta) {
+    r -= T - ta;
+    ++ta;
+  }
+  const int tb = ta + r;
+  // staging roles, fixed per thread: (row offset, padded column) of V and of W
+  const int vstep = blockDim.x / qp, vr0 = tid / qp, vc = tid % qp;
+  const int wstep = blockDim.x / (2 * qp), wr0 = tid / (2 * qp), wc = tid % (2 * qp);
+  const int whh = wc / qp, wcc = wc % qp;
+  df_acc acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = acc_zero();
+  const int r0 = blockIdx.x * chunk_rows;
+  const int r1 = min(rows, r0 + chunk_rows);
+  for (int rb = r0; rb < r1; rb += slab) {
+    const int nr = min(slab, r1 - rb);
+    if (vr0 < vstep)
+      for (int rr = vr0; rr < nr; rr += vstep)
+        Vs[rr * qp + vc] = vc < q ? V[static_cast<long long>(rb + rr) * q + vc] : make_float2(0.f, 0.f);
+    if (wr0 < wstep)
+      for (int rr = wr0; rr < nr; rr += wstep)
+        Ws[rr * 2 * qp + wc] = wcc < q ? W[static_cast<long long>(rb + rr) * 2 * q + whh * q + wcc]
+                                       : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (active)
+      for (int rr = g; rr < nr; rr += rg) {
+        const float4* vp = reinterpret_cast<const float4*>(Vs + rr * qp + 4 * ta);
+        const float4* wp = reinterpret_cast<const float4*>(Ws + rr * 2 * qp + half * qp + 4 * tb);
+        const float4 v01 = vp[0], v23 = vp[1], w01 = wp[0], w23 = wp[1];
+        const df v[4] = {df{v01.x, v01.y}, df{v01.z, v01.w}, df{v23.x, v23.y}, df{v23.z, v23.w}};
+        const df w[4] = {df{w01.x, w01.y}, df{w01.z, w01.w}, df{w23.x, w23.y}, df{w23.z, w23.w}};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i * 4 + j].fma(v[i], w[j]);
+      }
+    __syncthreads();
+  }
+  // merge the rg row groups (shared memory reused; fixed order)
+  df_acc* red = reinterpret_cast<df_acc*>(graw);  // rg x ntiles x 16
+  if (active)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) red[(g * ntiles + t) * 16 + i] = acc[i];
+  __syncthreads();
+  if (g == 0) {
+    const int np = q * (q + 1);
+    const int Tq = q * (q + 1) / 2;
+    for (int i = 0; i < 16; ++i) {
+      const int a = 4 * ta + i / 4, b = 4 * tb + i % 4;
+      if (a >= q || b >= q || a > b) continue;
+      df_acc s = red[t * 16 + i];
+      for (int h = 1; h < rg; ++h) s.merge(red[(h * ntiles + t) * 16 + i]);
+      const int idx = half * Tq + a * q - a * (a - 1) / 2 + (b - a);
+      part[static_cast<long long>(blockIdx.x) * np + idx] = df_to_double(s.value());
+    }
   }
 }
 
@@ -429,10 +552,11 @@ int grid_for(long long count) {
 void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* lam, float* R, int ldr,
                       double* partials, int* nblocks_out, cudaStream_t st) {
   Geo g = geo_for(q);
+  // one wave: four resident blocks per SM (the kernel's launch bound), grid-stride beyond
   int blocks = ceil_div(AM.rows, g.rows_per_block);
-  if (blocks > 8 * kNumSms) blocks = 8 * kNumSms;
+  if (blocks > 4 * kNumSms) blocks = 4 * kNumSms;
   if (nblocks_out) *nblocks_out = blocks;
-  const size_t sm = partials ? sizeof(double) * g.rows_per_block * 2 * g.G * g.cpt : 0;
+  const size_t sm = partials ? sizeof(df_acc) * g.rows_per_block * 2 * g.G * g.cpt : 0;
   const double N = AM.rows, nnz = AM.nnz;
   ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 4.0 * N * ldr, 4.0 * nnz * q);
   AMGEIG_DISPATCH(g.cpt, k_defect_df,
@@ -463,6 +587,20 @@ void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool
 
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
                          cudaStream_t st) {
+  if (rows <= 0 || q <= 0) return;
+  if (q <= 32) {
+    ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
+    const int blocks = ceil_div(rows, kThreads);
+    if (q <= 8)
+      k_recombine_rows<8><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    else if (q <= 16)
+      k_recombine_rows<16><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    else if (q <= 24)
+      k_recombine_rows<24><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    else
+      k_recombine_rows<32><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    return;
+  }
   Geo g = geo_for(q);
   const int blocks = ceil_div(rows, g.rows_per_block);
   ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
@@ -500,6 +638,30 @@ void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, do
   if (q <= 0 || w <= 0) return;
   int cr;
   const int chunks = gram_chunks_df(rows, &cr);
+  if (w == 2 * q && q <= 32) {
+    const int T = (q + 3) / 4, ntiles = T * (T + 1);
+    const int rg = kGtThreads / ntiles;
+    // up to 8 rows per group, staged slab within 40 KB of shared memory
+    const int rpg = std::max(1, std::min(8, 40960 / (rg * 96 * T)));
+    const int slab = rg * rpg;
+    int chunks2 = ceil_div(rows, slab);
+    if (chunks2 > 3 * kNumSms) chunks2 = 3 * kNumSms;
+    int cr2 = ceil_div(ceil_div(rows, chunks2), slab) * slab;
+    chunks2 = ceil_div(rows, cr2);
+    if (chunks2 > chunks) chunks2 = chunks;  // scratch is sized for gram_chunks_df
+    cr2 = ceil_div(ceil_div(rows, chunks2), slab) * slab;
+    chunks2 = ceil_div(rows, cr2);
+    const int np = q * (q + 1);
+    ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks2 * np, 1.0 * rows * np * 2.0);
+    const size_t stage = sizeof(float2) * slab * 3 * 4 * T;
+    const size_t merge = sizeof(df_acc) * rg * ntiles * 16;
+    const size_t sm = stage > merge ? stage : merge;
+    k_gram_df_tiled<<<chunks2, kGtThreads, sm, st>>>(rows, V, q, W, cr2, T, rg, slab, scratch);
+    double* sums = scratch + static_cast<size_t>(chunks2) * np;
+    launch_sum_partials(scratch, chunks2, np, sums, st);
+    k_gram_unpack<<<ceil_div(np, 256), 256, 0, st>>>(sums, q, G);
+    return;
+  }
   if (w == 2 * q && q * (q + 1) <= kGramMaxPairs * kGramThreads) {
     const int np = q * (q + 1);
     ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks * np, 1.0 * rows * np * 2.0);
