@@ -41,7 +41,7 @@ FP64_CLASSES = {"defect", "augment", "gram", "recombine", "chain"}
 WORKLOADS = {
     # name: builder, its arguments, q, q_extra, coarse-level cap of the AMG setup,
     # relative-residual tolerance, coarse modes in the pencil (0 = all of V_n)
-    "lshape_h512_q20": dict(builder="lshape_2d", kw=dict(m_half=512, seed=2), q=20, qe=4, cap=400, tol=1e-5,
+    "lshape_h512_q20": dict(builder="lshape_2d", kw=dict(m_half=512, seed=2), q=20, qe=4, cap=400, tol=1e-4,
                             modes=64),
     "square_h32_q4": dict(builder="square_2d", kw=dict(m=32, seed=1), q=4, qe=2, cap=50, tol=1e-9, modes=0),
     "checker_h1024_q50": dict(builder="square_2d", kw=dict(m=1024, checker=4, seed=3), q=50, qe=6, cap=400,
@@ -52,6 +52,18 @@ WORKLOADS = {
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def replica_max(dist, seconds_or_ms, device):
+    """Max over ranks of one timing (replicas only: the ranks share no data, this
+    all-reduce of a scalar is the only collective).  dist is None on one process."""
+    if dist is None:
+        return float(seconds_or_ms)
+    import torch
+
+    t = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def build_workload(name, cap=None):
@@ -186,7 +198,7 @@ def main():
     ap.add_argument("--q-extra", type=int, default=None)
     ap.add_argument("--cap", type=int, default=None, help="coarse-level cap of the AMG setup")
     ap.add_argument("--sweeps", type=int, default=1, help="l1-Jacobi sweeps before and after the coarse correction")
-    ap.add_argument("--v-cycles", type=int, default=1)
+    ap.add_argument("--v-cycles", type=int, default=2, help="V-cycles per correction (AMG iteration steps m)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -265,10 +277,7 @@ def main():
     prof = ae.amgeig_profile_read()
     ae.amgeig_profile_enable(False)
     launches = ae.amgeig_kernel_launches() - launches0
-    if dist is not None:
-        t = torch.tensor([ms_total], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = replica_max(dist, ms_total, f"cuda:{local}")
     ms_per_step = ms_total / args.steps
     value = world * q * args.steps / (ms_total / 1e3)
 
@@ -289,7 +298,7 @@ def main():
         ae._check(rc, "amgeig_load_hierarchy")
         ae.amgeig_solve(handle, q, tol, opt, vals_h, vecs_h, False, None, None)
         ae.amgeig_free_hierarchy(handle)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = replica_max(dist, (time.perf_counter() - t0) / e2e_steps, f"cuda:{local}")
     e2e_value = world * q / e2e_s
 
     # roofline of the dominant kernel class (the pencil's eigensolver is latency-bound;

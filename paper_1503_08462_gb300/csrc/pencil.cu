@@ -69,7 +69,7 @@ struct PencilWork {
   double* sr_mu = nullptr;  // qmax
   double* sr_X = nullptr;   // nmax x qmax
   int* sr_conv = nullptr;   // qmax
-  int* sr_flag = nullptr;   // 1
+  int* sr_flag = nullptr;   // 4: accepted, reason of a rejection, inertia count, q
 };
 
 namespace {
@@ -757,15 +757,16 @@ __device__ void gj_solve(df* S, int q, int* prow, int* used, df* rinv_s, df* sol
   __syncthreads();
 }
 
-// Gauss-Jordan with partial pivoting for q <= 31 and a 1024-thread block: the
-// thread (i, j) = (tid / 32, tid % 32) keeps element (i, j) of the augmented
-// q x (q+1) matrix in registers, so warp i holds row i.  Per column k: the
+// Gauss-Jordan with partial pivoting for q + nrhs <= 32 and a 1024-thread
+// block: the thread (i, j) = (tid / 32, tid % 32) keeps element (i, j) of the
+// augmented q x (q + nrhs) matrix in registers, so warp i holds row i.  Per column k: the
 // pivot row p (chosen by a shared atomic max over |a_ik| while column k was
 // updated) is scaled by 1 / a_pk inside its warp and published in shared
 // memory; every other row takes its multiplier a_ik from lane k by a shuffle
 // and subtracts a_ik * (scaled pivot row).  Two barriers per column, no
-// integer division, no back substitution: x_k ends in column q of row p_k.
-// S is read from shared memory (row stride q + 1); the solution goes to sol.
+// integer division, no back substitution: x_k ends in the right-hand-side
+// columns of row p_k.  S is read from shared memory (row stride lds); solution
+// r goes to sol[r * ldsol + k].
 struct GjShared {
   unsigned long long key[2];
   df prowv[33];
@@ -781,11 +782,12 @@ __device__ __forceinline__ df shfl_df(df v, int src) {
   return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
 
-__device__ void gj_solve_reg(const df* S, int q, GjShared* g, df* sol) {
+__device__ void gj_solve_reg(const df* S, int q, int nrhs, int lds, GjShared* g, df* sol, int ldsol) {
   const int tid = threadIdx.x;
   const int i = tid >> 5, j = tid & 31;
-  const bool live = i < q && j <= q;
-  df v = live ? S[i * (q + 1) + j] : df{0.f, 0.f};
+  const int ncol = q + nrhs;
+  const bool live = i < q && j < ncol;
+  df v = live ? S[i * lds + j] : df{0.f, 0.f};
   if (tid == 0) g->key[0] = 0ull;
   __syncthreads();
   if (live && j == 0) atomicMax(&g->key[0], pivot_key(fabsf(v.hi), i));
@@ -797,7 +799,7 @@ __device__ void gj_solve_reg(const df* S, int q, GjShared* g, df* sol) {
       df pk = shfl_df(v, k);
       if (fabsf(pk.hi) < 1.0e-30f) pk = df{1.0e-30f, 0.f};
       v = (j == k) ? df{1.f, 0.f} : df_mul(v, df_recip(pk));
-      if (j <= q) g->prowv[j] = v;
+      if (j < ncol) g->prowv[j] = v;
     }
     if (tid == 0) {
       g->key[(k + 1) & 1] = 0ull;
@@ -807,14 +809,14 @@ __device__ void gj_solve_reg(const df* S, int q, GjShared* g, df* sol) {
     __syncthreads();
     if (i < q && i != p) {
       const df l = shfl_df(v, k);
-      if (j <= q && j > k) {
+      if (j < ncol && j > k) {
         v = df_sub(v, df_mul(l, g->prowv[j]));
         if (j == k + 1 && !((used >> i) & 1u)) atomicMax(&g->key[(k + 1) & 1], pivot_key(fabsf(v.hi), i));
       }
     }
     __syncthreads();
   }
-  if (live && j == q) sol[g->kof[i]] = v;
+  if (live && j >= q) sol[(j - q) * ldsol + g->kof[i]] = v;
   __syncthreads();
 }
 
@@ -1041,6 +1043,7 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi(int m, int q, const doubl
   __syncthreads();
   mt_normalise(S, y, x, sx, m, q, red, &outv);
   df sg = pencil_rq(th, F, T, x, m, q, red, &outv);
+  const df sg0 = sg;  // reported when the iteration fails: it places the pair for the repair
   int ok = 0;
   for (int it = 0; it < kSrqiMaxIt; ++it) {
     // S x2 for the right-hand side
@@ -1076,7 +1079,7 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi(int m, int q, const doubl
     }
     __syncthreads();
     if (q <= 31 && nt == 1024)
-      gj_solve_reg(Sc, q, &gj, ysol);
+      gj_solve_reg(Sc, q, 1, q + 1, &gj, ysol, q);
     else
       gj_solve(Sc, q, prow, used, &rinv, ysol);
     // y2 = solution, y1 = (Theta - s)^-1 (x1 - Ft y2)
@@ -1102,73 +1105,47 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi(int m, int q, const doubl
   }
   for (int i = tid; i < n; i += nt) X[i * static_cast<long long>(q) + j] = df_to_double(x[i]);
   if (tid == 0) {
-    mu[j] = df_to_double(sg);
+    mu[j] = df_to_double(ok ? sg : sg0);
     conv[j] = ok;  // iterations taken when converged, 0 otherwise
   }
 }
 
 // Accept the fast path (flag[0] = 1) or leave it to the dense solver (flag[0] =
-// 0).  On acceptance writes the ascending values to evals and the vectors [a; b]
+// 0).  Vectors of nearly equal values come out of the iteration only accurate
+// to residual / gap, and two iterations may even find the same pair; such
+// clusters (chains of sorted neighbours whose Mt-overlap exceeds 1e-9, at most
+// kMaxCluster vectors) are repaired by Rayleigh-Ritz on the cluster's span --
+// after two steps of block inverse iteration from the starting vectors when
+// the cluster holds duplicates.  The result is accepted only if every
+// iteration converged, all vectors are Mt-orthogonal to 1e-6 afterwards, S is
+// positive definite and the inertia count just above the largest value is q.
+// On acceptance writes the ascending values to evals and the vectors [a; b]
 // ((m + q) x q) to evecs, made Mt-orthonormal to second order by the first-order
-// Lowdin correction X (I - E / 2), E = X^T Mt X - I (the overlaps of vectors of
-// nearly equal values are only accurate to residual / gap).
-__global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const double* __restrict__ thg,
-                                                            const df* __restrict__ Ftg, const df* __restrict__ Ttg,
-                                                            const df* __restrict__ Stg,
-                                                            const double* __restrict__ mu,
-                                                            const double* __restrict__ Xg,
-                                                            const int* __restrict__ conv,
-                                                            double* __restrict__ evals, double* __restrict__ evecs,
-                                                            int* __restrict__ flag) {
-  extern __shared__ __align__(16) unsigned char craw[];
-  const int n = m + q;
-  df* X = reinterpret_cast<df*>(craw);  // n x q
-  df* SX = X + n * q;                   // q x q: S X2
-  df* Sc = SX + q * q;                  // q x q: S(s*)
-  df* Sl = Sc + q * q;                  // q x q: copy of S for its LDL^T
-  df* Ov = Sl + q * q;                  // q x q: X^T Mt X - I
-  df* dv = Ov + q * q;                  // m: 1 / (theta_i - s*)
-  df* F = dv + m;                       // m x q
-  __shared__ int okf, negs, nonpd, theta_cnt;
-  __shared__ int perm[kSrqiMaxQ];
-  __shared__ df sstar;
-  __shared__ LdlShared lsh;
-  __shared__ float omax;
+// Lowdin correction X (I - E / 2), E = X^T Mt X - I.
+constexpr int kMaxCluster = 4;
+constexpr int kRepairRounds = 8;
+constexpr float kRepairResidual = 1.0e-12f;  // relative residual of a repaired pair
+
+struct CheckShared {
+  int okf, negs, nonpd, theta_cnt, nclus;
+  int perm[kSrqiMaxQ];
+  int cstart[kSrqiMaxQ + 1];  // clusters: members perm[cstart[c] .. cstart[c+1])
+  df muS[kSrqiMaxQ];
+  df sstar, shift;
+  float res;
+  float omax;
+  int good[kSrqiMaxQ];  // columns accepted so far (the repaired block is kept Mt-orthogonal to them)
+  df Ac[kMaxCluster * kMaxCluster], Mc[kMaxCluster * kMaxCluster], Wc[kMaxCluster * kMaxCluster];
+  df evc[kMaxCluster];
+  GjShared gj;
+  LdlShared lsh;
+};
+
+// Mt-overlaps Ov = X^T Mt X - I (upper triangle computed, mirrored); omax = max |Ov| off the diagonal
+__device__ void check_overlaps(const df* X, const df* SX, df* Ov, int m, int q, CheckShared* c) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    okf = 1;
-    negs = 0;
-    nonpd = 0;
-    omax = 0.f;
-    double mx = mu[0];
-    for (int i = 1; i < q; ++i) mx = fmax(mx, mu[i]);
-    sstar = to_df(mx + 1.0e-9 * fabs(mx) + 1.0e-300);
-  }
-  for (int idx = tid; idx < n * q; idx += nt) X[idx] = to_df(Xg[idx]);
-  for (int idx = tid; idx < q * q; idx += nt) Sl[idx] = Stg[idx];
-  for (int idx = tid; idx < m * q; idx += nt) F[idx] = Ftg[idx];
+  if (tid == 0) c->omax = 0.f;
   __syncthreads();
-  if (tid < 32) {
-    const double ss = df_to_double(sstar);
-    int cnt = 0;
-    for (int i = tid; i < m; i += 32) cnt += thg[i] < ss;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (tid == 0) theta_cnt = cnt;
-  }
-  for (int j = tid; j < q; j += nt)
-    if (!conv[j]) okf = 0;
-  for (int idx = tid; idx < q * q; idx += nt) {
-    const int a = idx / q, j = idx % q;
-    SX[idx] = dot4(Sl + a * q, 1, X + m * q + j, q, q).value();
-  }
-  for (int i = tid; i < m; i += nt) {
-    df d = df_sub(to_df(thg[i]), sstar);
-    if (fabsf(d.hi) < 1.0e-30f) d = df{-1.0e-30f, 0.f};
-    dv[i] = df_div(df{1.f, 0.f}, d);
-  }
-  __syncthreads();
-  // Mt-overlaps X^T Mt X - I (upper triangle computed, mirrored)
   for (int idx = tid; idx < q * q; idx += nt) {
     const int a = idx / q, b = idx % q;
     if (b < a) continue;
@@ -1179,15 +1156,535 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const
     Ov[a * q + b] = v;
     Ov[b * q + a] = v;
     const float f = fabsf(df_float(v));
-    atomicMax(reinterpret_cast<int*>(&omax), __float_as_int(f));  // f >= 0 (NaN sorts above)
+    if (a != b) atomicMax(reinterpret_cast<int*>(&c->omax), __float_as_int(f));  // f >= 0 (NaN sorts above)
   }
-  // Schur complement at s*: Tt - s* S - Ft^T (Theta - s*)^-1 Ft (upper triangle, mirrored)
+  __syncthreads();
+}
+
+// SX = S X2 for all columns
+__device__ void check_sx(const df* S, const df* X, df* SX, int m, int q) {
+  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+    const int a = idx / q, j = idx % q;
+    SX[idx] = dot4(S + a * q, 1, X + m * q + j, q, q).value();
+  }
+  __syncthreads();
+}
+
+// Yb (n x c, column stride 1, row stride kMaxCluster) -> AY = At Yb, MY = Mt Yb
+__device__ void pencil_apply(const df* th, const df* F, const df* T, const df* S, const df* Yb, df* AY, df* MY,
+                             int m, int q, int c) {
+  const int n = m + q;
+  constexpr int L = kMaxCluster;
+  for (int idx = threadIdx.x; idx < n * c; idx += blockDim.x) {
+    const int i = idx / c, r = idx % c;
+    if (i < m) {
+      const df fy = dot4(F + i * q, 1, Yb + m * L + r, L, q).value();
+      AY[i * L + r] = df_add(df_mul(th[i], Yb[i * L + r]), fy);
+      MY[i * L + r] = Yb[i * L + r];
+    } else {
+      const int a = i - m;
+      df_acc t = dot4(F + a, q, Yb + r, L, m);
+      t.merge(dot4(T + a * q, 1, Yb + m * L + r, L, q));
+      AY[i * L + r] = t.value();
+      MY[i * L + r] = dot4(S + a * q, 1, Yb + m * L + r, L, q).value();
+    }
+  }
+  __syncthreads();
+}
+
+// c x c symmetric-definite Rayleigh-Ritz by one thread: M = L L^T, C = L^-1 A L^-T,
+// cyclic Jacobi on C (one exact rotation for c = 2), W <- L^-T W; values ascending.
+__device__ void small_rr(df* A, df* M, df* W, df* ev, int c) {
+  constexpr int L = kMaxCluster;
+  // Cholesky of M in place (lower)
+  for (int k = 0; k < c; ++k) {
+    df d = M[k * L + k];
+    for (int t = 0; t < k; ++t) d = df_sub(d, df_mul(M[k * L + t], M[k * L + t]));
+    d = df_sqrt(d.hi > 0.f ? d : df{1.0e-30f, 0.f});
+    M[k * L + k] = d;
+    const df id = df_recip(d);
+    for (int i = k + 1; i < c; ++i) {
+      df s = M[i * L + k];
+      for (int t = 0; t < k; ++t) s = df_sub(s, df_mul(M[i * L + t], M[k * L + t]));
+      M[i * L + k] = df_mul(s, id);
+    }
+  }
+  // C = L^-1 A L^-T (A symmetric; rows then columns)
+  for (int j = 0; j < c; ++j)
+    for (int i = 0; i < c; ++i) {
+      df s = A[i * L + j];
+      for (int t = 0; t < i; ++t) s = df_sub(s, df_mul(M[i * L + t], A[t * L + j]));
+      A[i * L + j] = df_div(s, M[i * L + i]);
+    }
+  for (int i = 0; i < c; ++i)
+    for (int j = 0; j < c; ++j) {
+      df s = A[i * L + j];
+      for (int t = 0; t < j; ++t) s = df_sub(s, df_mul(M[j * L + t], A[i * L + t]));
+      A[i * L + j] = df_div(s, M[j * L + j]);
+    }
+  for (int i = 0; i < c; ++i)
+    for (int j = 0; j < c; ++j) W[i * L + j] = df{i == j ? 1.f : 0.f, 0.f};
+  const int sweeps = c == 2 ? 1 : 6;
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int p = 0; p < c; ++p)
+      for (int r = p + 1; r < c; ++r) {
+        const df apr = df_mul_f(df_add(A[p * L + r], A[r * L + p]), 0.5f);
+        const df dif = df_sub(A[r * L + r], A[p * L + p]);
+        if (fabsf(apr.hi) <= 1.0e-30f * fabsf(dif.hi) || apr.hi == 0.f) continue;
+        // t = sign(th) / (|th| + sqrt(th^2 + 1)), th = (a_rr - a_pp) / (2 a_pr);
+        // t = 1 / (2 th) once th^2 would leave the float range
+        const df th = df_div(dif, df_add(apr, apr));
+        df t;
+        if (fabsf(th.hi) > 1.0e15f) {
+          t = df_recip(df_add(th, th));
+        } else {
+          const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
+          t = df_recip(df_add(df_abs(th), rt));
+          if (df_lt0(th)) t = df_neg(t);
+        }
+        const df cs = df_recip(df_sqrt(df_add(df_mul(t, t), df{1.f, 0.f})));
+        const df sn = df_mul(t, cs);
+        for (int k = 0; k < c; ++k) {  // columns p, r of A
+          const df akp = A[k * L + p], akr = A[k * L + r];
+          A[k * L + p] = df_sub(df_mul(cs, akp), df_mul(sn, akr));
+          A[k * L + r] = df_add(df_mul(sn, akp), df_mul(cs, akr));
+        }
+        for (int k = 0; k < c; ++k) {  // rows p, r of A
+          const df apk = A[p * L + k], ark = A[r * L + k];
+          A[p * L + k] = df_sub(df_mul(cs, apk), df_mul(sn, ark));
+          A[r * L + k] = df_add(df_mul(sn, apk), df_mul(cs, ark));
+        }
+        for (int k = 0; k < c; ++k) {
+          const df wkp = W[k * L + p], wkr = W[k * L + r];
+          W[k * L + p] = df_sub(df_mul(cs, wkp), df_mul(sn, wkr));
+          W[k * L + r] = df_add(df_mul(sn, wkp), df_mul(cs, wkr));
+        }
+      }
+  // W <- L^-T W
+  for (int j = 0; j < c; ++j)
+    for (int i = c - 1; i >= 0; --i) {
+      df s = W[i * L + j];
+      for (int t = i + 1; t < c; ++t) s = df_sub(s, df_mul(M[t * L + i], W[t * L + j]));
+      W[i * L + j] = df_div(s, M[i * L + i]);
+    }
+  // ascending order (selection sort of columns)
+  for (int i = 0; i < c; ++i) ev[i] = A[i * L + i];
+  for (int i = 0; i < c; ++i) {
+    int b = i;
+    for (int j = i + 1; j < c; ++j)
+      if (df_lt0(df_sub(ev[j], ev[b]))) b = j;
+    if (b != i) {
+      const df e = ev[i];
+      ev[i] = ev[b];
+      ev[b] = e;
+      for (int k = 0; k < c; ++k) {
+        const df w = W[k * L + i];
+        W[k * L + i] = W[k * L + b];
+        W[k * L + b] = w;
+      }
+    }
+  }
+}
+
+// columns of Yb (n x c, row stride kMaxCluster) scaled by powers of two to max |.| ~ 1
+__device__ void block_scale(df* Yb, int n, int c) {
+  constexpr int L = kMaxCluster;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int r = 0; r < c; ++r) {
+      float amax = 0.f;
+      for (int i = lane; i < n; i += 32) amax = fmaxf(amax, fabsf(Yb[i * L + r].hi));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      const float sc = amax > 0.f ? exp2f(-floorf(log2f(amax))) : 1.f;
+      for (int i = lane; i < n; i += 32) Yb[i * L + r] = df{Yb[i * L + r].hi * sc, Yb[i * L + r].lo * sc};
+    }
+  }
+  __syncthreads();
+}
+
+// Yb <- Yb - X_good (X_good^T Mt Yb), twice (the accepted columns of X are
+// Mt-orthonormal to working accuracy).  MY, tmp: n x L scratch; coef: q x L.
+__device__ void block_deflate(const df* X, const df* S, df* Yb, df* MY, df* tmp, const int* good, df* coef, int m,
+                              int q, int c) {
+  constexpr int L = kMaxCluster;
+  const int n = m + q, tid = threadIdx.x, nt = blockDim.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int idx = tid; idx < n * c; idx += nt) {
+      const int i = idx / c, r = idx % c;
+      MY[i * L + r] = i < m ? Yb[i * L + r] : dot4(S + (i - m) * q, 1, Yb + m * L + r, L, q).value();
+    }
+    __syncthreads();
+    for (int idx = tid; idx < q * c; idx += nt) {
+      const int j = idx / c, r = idx % c;
+      coef[j * L + r] = good[j] ? dot4(X + j, q, MY + r, L, n).value() : df{0.f, 0.f};
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * c; idx += nt) {
+      const int i = idx / c, r = idx % c;
+      // skip the other columns outright: an unconverged one may hold NaN
+      df_acc a0 = acc_zero(), a1 = acc_zero();
+      int j = 0;
+      for (; j + 2 <= q; j += 2) {
+        if (good[j]) a0.fma(X[i * q + j], coef[j * L + r]);
+        if (good[j + 1]) a1.fma(X[i * q + j + 1], coef[(j + 1) * L + r]);
+      }
+      if (j < q && good[j]) a0.fma(X[i * q + j], coef[j * L + r]);
+      a0.merge(a1);
+      tmp[i * L + r] = df_sub(Yb[i * L + r], a0.value());
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * c; idx += nt) Yb[(idx / c) * L + idx % c] = tmp[(idx / c) * L + idx % c];
+    __syncthreads();
+  }
+}
+
+// Mt-orthonormalise the block: G = Yb^T Mt Yb = L L^T, Yb <- Yb L^-T (Cholesky-QR)
+__device__ void block_cholqr(const df* th, const df* F, const df* T, const df* S, df* Yb, df* AY, df* MY,
+                             CheckShared* c, int m, int q, int cs) {
+  constexpr int L = kMaxCluster;
+  const int n = m + q, tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * cs; idx += nt) {
+    const int i = idx / cs, r = idx % cs;
+    MY[i * L + r] = i < m ? Yb[i * L + r] : dot4(S + (i - m) * q, 1, Yb + m * L + r, L, q).value();
+  }
+  __syncthreads();
+  for (int idx = tid; idx < cs * cs; idx += nt) {
+    const int a = idx / cs, b = idx % cs;
+    c->Mc[a * L + b] = dot4(Yb + a, L, MY + b, L, n).value();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < cs; ++k) {  // Cholesky in place (lower); L^-T goes to Wc
+      df d = c->Mc[k * L + k];
+      for (int t = 0; t < k; ++t) d = df_sub(d, df_mul(c->Mc[k * L + t], c->Mc[k * L + t]));
+      d = df_sqrt(d.hi > 0.f ? d : df{1.0e-30f, 0.f});
+      c->Mc[k * L + k] = d;
+      const df id = df_recip(d);
+      for (int i = k + 1; i < cs; ++i) {
+        df t2 = c->Mc[i * L + k];
+        for (int t = 0; t < k; ++t) t2 = df_sub(t2, df_mul(c->Mc[i * L + t], c->Mc[k * L + t]));
+        c->Mc[i * L + k] = df_mul(t2, id);
+      }
+    }
+    for (int j = 0; j < cs; ++j)
+      for (int i = cs - 1; i >= 0; --i) {
+        df t2 = df{i == j ? 1.f : 0.f, 0.f};
+        for (int t = i + 1; t < cs; ++t) t2 = df_sub(t2, df_mul(c->Mc[t * L + i], c->Wc[t * L + j]));
+        c->Wc[i * L + j] = df_div(t2, c->Mc[i * L + i]);
+      }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * cs; idx += nt) {
+    const int i = idx / cs, r = idx % cs;
+    df_acc t2 = acc_zero();
+    for (int t = 0; t <= r; ++t) t2.fma(Yb[i * L + t], c->Wc[t * L + r]);
+    AY[i * L + r] = t2.value();
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * cs; idx += nt) Yb[(idx / cs) * L + idx % cs] = AY[(idx / cs) * L + idx % cs];
+  __syncthreads();
+}
+
+// Largest relative residual ||At y - mu Mt y|| / (|mu| ||Mt y||) of the Ritz pairs
+// (Yb W_r, ev_r), r < cs, from AY = At Yb and MY = Mt Yb; one warp per pair.
+// Result in *res (shared).
+__device__ void ritz_residual(const df* AY, const df* MY, const df* W, const df* ev, int n, int cs, float* res) {
+  constexpr int L = kMaxCluster;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) *res = 0.f;
+  __syncthreads();
+  if (w < cs) {
+    float rr = 0.f, mm = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      df_acc a = acc_zero(), b = acc_zero();
+      for (int t = 0; t < cs; ++t) {
+        a.fma(AY[i * L + t], W[t * L + w]);
+        b.fma(MY[i * L + t], W[t * L + w]);
+      }
+      const df my = b.value();
+      const float e = df_float(df_sub(a.value(), df_mul(ev[w], my)));
+      rr = fmaf(e, e, rr);
+      mm = fmaf(my.hi, my.hi, mm);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      mm += __shfl_xor_sync(0xffffffffu, mm, o);
+    }
+    if (lane == 0) {
+      const float rel = sqrtf(rr) / (fabsf(ev[w].hi) * sqrtf(mm));
+      atomicMax(reinterpret_cast<int*>(res), __float_as_int(rel == rel ? rel : 3.0e38f));
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const double* __restrict__ thg,
+                                                            const df* __restrict__ KB, const df* __restrict__ Ftg,
+                                                            const df* __restrict__ Ttg, const df* __restrict__ Stg,
+                                                            const double* __restrict__ mu,
+                                                            const double* __restrict__ Xg,
+                                                            const int* __restrict__ conv,
+                                                            double* __restrict__ evals, double* __restrict__ evecs,
+                                                            int* __restrict__ flag) {
+  extern __shared__ __align__(16) unsigned char craw[];
+  constexpr int L = kMaxCluster;
+  const int n = m + q;
+  df* X = reinterpret_cast<df*>(craw);  // n x q
+  df* SX = X + n * q;                   // q x q: S X2
+  df* Sc = SX + q * q;                  // q x q: S(s*)
+  df* Sl = Sc + q * q;                  // q x q: S
+  df* Ov = Sl + q * q;                  // q x q: X^T Mt X - I
+  df* T = Ov + q * q;                   // q x q: Tt
+  df* dv = T + q * q;                   // m: 1 / (theta_i - shift)
+  df* th = dv + m;                      // m
+  df* F = th + m;                       // m x q
+  df* Sa = F + m * q;                   // q x (q + L): augmented Schur complement of the repair
+  df* Yb = Sa + q * (q + L);            // n x L
+  df* AY = Yb + n * L;                  // n x L
+  df* MY = AY + n * L;                  // n x L
+  df* ys = MY + n * L;                  // L x q
+  __shared__ CheckShared c;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    c.okf = 1;
+    c.negs = 0;
+    c.nonpd = 0;
+  }
+  for (int idx = tid; idx < n * q; idx += nt) X[idx] = to_df(Xg[idx]);
+  for (int idx = tid; idx < q * q; idx += nt) {
+    Sl[idx] = Stg[idx];
+    T[idx] = Ttg[idx];
+  }
+  for (int idx = tid; idx < m * q; idx += nt) F[idx] = Ftg[idx];
+  for (int i = tid; i < m; i += nt) th[i] = to_df(thg[i]);
+  for (int j = tid; j < q; j += nt) c.muS[j] = to_df(mu[j]);
+  __syncthreads();
+  check_sx(Sl, X, SX, m, q);
+  check_overlaps(X, SX, Ov, m, q, &c);
+  // sort by value (a NaN from a diverged iteration sorts last), then chain
+  // sorted neighbours with large overlaps into clusters
+  for (int j = tid; j < q; j += nt) {
+    const double vj = mu[j] == mu[j] ? mu[j] : HUGE_VAL;
+    int r = 0;
+    for (int i = 0; i < q; ++i) {
+      const double vi = mu[i] == mu[i] ? mu[i] : HUGE_VAL;
+      if (vi < vj || (vi == vj && i < j)) ++r;
+    }
+    c.perm[r] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nc = 0, bad = 0;
+    c.cstart[0] = 0;
+    for (int r = 1; r <= q; ++r) {
+      // an iteration that did not converge joins its sorted neighbours' cluster
+      const bool join = r < q && (fabsf(df_float(Ov[c.perm[r - 1] * q + c.perm[r]])) > 1.0e-9f ||
+                                  !conv[c.perm[r - 1]] || !conv[c.perm[r]]);
+      if (!join) {
+        const int size = r - c.cstart[nc];
+        if (size > L || (size > 1 && q + size > 32) || (size == 1 && !conv[c.perm[r - 1]])) bad = 1;
+        c.cstart[++nc] = r;
+      }
+    }
+    c.nclus = nc;
+    if (bad) c.okf = 0;
+  }
+  __syncthreads();
+  if (!c.okf) {
+    if (tid == 0) {
+      flag[0] = 0;
+      flag[1] = 1;  // a cluster larger than kMaxCluster, or an unconverged singleton
+    }
+    return;
+  }
+  bool repaired = false;
+  for (int r = tid; r < q; r += nt) c.good[r] = 1;
+  __syncthreads();
+  if (tid == 0)
+    for (int cl = 0; cl < c.nclus; ++cl)
+      if (c.cstart[cl + 1] - c.cstart[cl] > 1)
+        for (int r = c.cstart[cl]; r < c.cstart[cl + 1]; ++r) c.good[c.perm[r]] = 0;
+  __syncthreads();
+  for (int cl = 0; cl < c.nclus; ++cl) {
+    const int c0 = c.cstart[cl], cs = c.cstart[cl + 1] - c0;
+    if (cs < 2) continue;
+    repaired = true;
+    // duplicates (overlap > 0.5) or an unconverged member: restart from the
+    // starting vectors [B e_j; e_j]
+    bool dup = false;
+    for (int r = 0; r < cs; ++r) {
+      if (!conv[c.perm[c0 + r]]) dup = true;
+      if (r + 1 < cs && fabsf(df_float(Ov[c.perm[c0 + r] * q + c.perm[c0 + r + 1]])) > 0.5f) dup = true;
+    }
+    for (int idx = tid; idx < n * cs; idx += nt) {
+      const int i = idx / cs, r = idx % cs, j = c.perm[c0 + r];
+      Yb[i * L + r] = dup ? (i < m ? KB[static_cast<long long>(i) * 2 * q + q + j]
+                                   : df{(i - m) == j ? 1.f : 0.f, 0.f})
+                          : X[i * q + j];
+    }
+    __syncthreads();
+    // the block only has to find what the accepted vectors do not span:
+    // project them out (Mt inner product) and re-normalise
+    block_deflate(X, Sl, Yb, MY, AY, c.good, ys, m, q, cs);
+    block_cholqr(th, F, T, Sl, Yb, AY, MY, &c, m, q, cs);
+    if (dup) {
+      // shift: the mean Rayleigh quotient of the block (inside the cluster)
+      pencil_apply(th, F, T, Sl, Yb, AY, MY, m, q, cs);
+      for (int idx = tid; idx < 2 * cs; idx += nt) {
+        const int which = idx / cs, r = idx % cs;
+        (which ? c.Mc : c.Ac)[r] = dot4(Yb + r, L, (which ? MY : AY) + r, L, n).value();
+      }
+      __syncthreads();
+      if (tid == 0) {
+        df sum = df{0.f, 0.f};
+        for (int r = 0; r < cs; ++r) sum = df_add(sum, df_div(c.Ac[r], c.Mc[r]));
+        c.shift = df_div(sum, df{static_cast<float>(cs), 0.f});
+      }
+      __syncthreads();
+    }
+    // block inverse iteration, the shift moved to the mean Ritz value after each
+    // step, until the Ritz values settle (at most kRepairRounds steps)
+    for (int round = 0; dup && round < kRepairRounds; ++round) {
+      // (At - s Mt) Y = Mt Yb through the Schur complement at s, all columns at
+      // once; s sits 2^-30 (relative) off the mean Ritz value so that a cluster
+      // of equal values cannot make the solve exactly singular
+      const df sh = df_add(c.shift, df_mul_f(df_abs(c.shift), 9.313225746154785e-10f));
+      for (int i = tid; i < m; i += nt) {
+        df d = df_sub(th[i], sh);
+        if (fabsf(d.hi) < 1.0e-30f) d = df{1.0e-30f, 0.f};
+        dv[i] = df_recip(d);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < q * (q + cs); idx += nt) {
+        const int a = idx / (q + cs), b = idx % (q + cs);
+        df_acc acc = acc_zero();
+        if (b < q) {
+          acc.add(T[a * q + b]);
+          acc.fma(df_neg(sh), Sl[a * q + b]);
+          acc.add(df_neg(dot4w(F + a, q, dv, F + b, q, m).value()));
+        } else {
+          const int r = b - q;
+          acc.add(dot4(Sl + a * q, 1, Yb + m * L + r, L, q).value());
+          acc.add(df_neg(dot4w(F + a, q, dv, Yb + r, L, m).value()));
+        }
+        Sa[a * (q + L) + b] = acc.value();
+      }
+      __syncthreads();
+      gj_solve_reg(Sa, q, cs, q + L, &c.gj, ys, q);
+      for (int idx = tid; idx < n * cs; idx += nt) {
+        const int i = idx / cs, r = idx % cs;
+        Yb[i * L + r] = i < m ? df_mul(dv[i], df_sub(Yb[i * L + r], dot4(F + i * q, 1, ys + r * q, 1, q).value()))
+                              : ys[r * q + (i - m)];
+      }
+      __syncthreads();
+      block_scale(Yb, n, cs);
+      block_deflate(X, Sl, Yb, MY, AY, c.good, ys, m, q, cs);
+      block_cholqr(th, F, T, Sl, Yb, AY, MY, &c, m, q, cs);
+      pencil_apply(th, F, T, Sl, Yb, AY, MY, m, q, cs);
+      for (int idx = tid; idx < 2 * cs * cs; idx += nt) {
+        const int which = idx / (cs * cs), e = idx % (cs * cs), a = e / cs, b = e % cs;
+        const df v = dot4(Yb + a, L, (which ? MY : AY) + b, L, n).value();
+        (which ? c.Mc : c.Ac)[a * L + b] = v;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        small_rr(c.Ac, c.Mc, c.Wc, c.evc, cs);
+        df sum = df{0.f, 0.f};
+        for (int r = 0; r < cs; ++r) sum = df_add(sum, c.evc[r]);
+        c.shift = df_div(sum, df{static_cast<float>(cs), 0.f});
+      }
+      __syncthreads();
+      ritz_residual(AY, MY, c.Wc, c.evc, n, cs, &c.res);
+      if (c.res <= kRepairResidual) break;
+    }
+    // Rayleigh-Ritz on span(Yb)
+    pencil_apply(th, F, T, Sl, Yb, AY, MY, m, q, cs);
+    for (int idx = tid; idx < 2 * cs * cs; idx += nt) {
+      const int which = idx / (cs * cs), e = idx % (cs * cs), a = e / cs, b = e % cs;
+      const df v = dot4(Yb + a, L, (which ? MY : AY) + b, L, n).value();
+      (which ? c.Mc : c.Ac)[a * L + b] = v;
+    }
+    __syncthreads();
+    if (tid == 0) small_rr(c.Ac, c.Mc, c.Wc, c.evc, cs);
+    __syncthreads();
+    // the repaired pairs must be eigenpairs of the pencil to working accuracy
+    ritz_residual(AY, MY, c.Wc, c.evc, n, cs, &c.res);
+    if (!(c.res <= kRepairResidual)) {
+      if (tid == 0) {
+        flag[0] = 0;
+        flag[1] = 5;  // a cluster repair did not converge
+        flag[2] = __float_as_int(c.res);
+        flag[3] = cs;
+      }
+      return;
+    }
+    // new vectors Yb W into the cluster's columns (in the cluster's sorted order)
+    for (int idx = tid; idx < n * cs; idx += nt) {
+      const int i = idx / cs, r = idx % cs, j = c.perm[c0 + r];
+      df_acc s2 = acc_zero();
+      for (int t = 0; t < cs; ++t) s2.fma(Yb[i * L + t], c.Wc[t * L + r]);
+      X[i * q + j] = s2.value();
+    }
+    for (int r = tid; r < cs; r += nt) {
+      c.muS[c.perm[c0 + r]] = c.evc[r];
+      c.good[c.perm[c0 + r]] = 1;
+    }
+    __syncthreads();
+  }
+  if (repaired) {
+    check_sx(Sl, X, SX, m, q);
+    check_overlaps(X, SX, Ov, m, q, &c);
+  }
+  if (!(c.omax <= 1.0e-6f)) {  // also rejects NaN
+    if (tid == 0) {
+      flag[0] = 0;
+      flag[1] = 2;  // vectors not orthogonal after the cluster repairs
+      int ba = 0, bb = 0;
+      float bv = -1.f;
+      for (int a = 0; a < q && bv == bv; ++a)
+        for (int b = a + 1; b < q; ++b) {
+          const float v = fabsf(df_float(Ov[a * q + b]));
+          if (!(v <= bv)) {
+            bv = v;
+            ba = a;
+            bb = b;
+            if (v != v) break;  // the first NaN
+          }
+        }
+      flag[2] = ba * 64 + bb;  // the worst pair
+      flag[3] = __float_as_int(bv);
+    }
+    return;
+  }
+  // inertia just above the largest value
+  if (tid == 0) {
+    df mx = c.muS[0];
+    for (int i = 1; i < q; ++i)
+      if (df_lt0(df_sub(mx, c.muS[i]))) mx = c.muS[i];
+    c.sstar = df_add(mx, df_mul_f(df_abs(mx), 1.0e-9f));
+  }
+  __syncthreads();
+  if (tid < 32) {
+    int cnt = 0;
+    for (int i = tid; i < m; i += 32) cnt += df_lt0(df_sub(th[i], c.sstar));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (tid == 0) c.theta_cnt = cnt;
+  }
+  for (int i = tid; i < m; i += nt) {
+    df d = df_sub(th[i], c.sstar);
+    if (fabsf(d.hi) < 1.0e-30f) d = df{-1.0e-30f, 0.f};
+    dv[i] = df_recip(d);
+  }
+  __syncthreads();
   for (int idx = tid; idx < q * q; idx += nt) {
     const int a = idx / q, b = idx % q;
     if (b < a) continue;
     df_acc acc = acc_zero();
-    acc.add(Ttg[idx]);
-    acc.fma(df_neg(sstar), Sl[idx]);
+    acc.add(T[idx]);
+    acc.fma(df_neg(c.sstar), Sl[idx]);
     acc.add(df_neg(dot4w(F + a, q, dv, F + b, q, m).value()));
     Sc[idx] = acc.value();
   }
@@ -1197,21 +1694,15 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const
     if (b < a) Sc[idx] = Sc[b * q + a];
   }
   __syncthreads();
-  if (!(omax <= 1.0e-6f)) okf = 0;  // also rejects NaN
-  __syncthreads();
-  if (!okf) {
-    if (tid == 0) flag[0] = 0;
-    return;
-  }
   // LDL^T of S(s*) (negative pivots) and of S (must be positive definite)
   if (q <= 31 && nt == 1024)
-    ldl_inertia_reg(Sc, Sl, q, &lsh, &negs, &nonpd);
+    ldl_inertia_reg(Sc, Sl, q, &c.lsh, &c.negs, &c.nonpd);
   else
     for (int k = 0; k < q; ++k) {
       const df pc = Sc[k * q + k], pl = Sl[k * q + k];
       if (tid == 0) {
-        if (df_lt0(pc) || pc.hi == 0.f) ++negs;
-        if (!(pl.hi > 0.f)) nonpd = 1;
+        if (df_lt0(pc) || pc.hi == 0.f) ++c.negs;
+        if (!(pl.hi > 0.f)) c.nonpd = 1;
       }
       const df ic = df_recip((pc.hi == 0.f) ? df{-1.0e-30f, 0.f} : pc);
       const df il = df_recip((pl.hi > 0.f) ? pl : df{1.f, 0.f});
@@ -1226,24 +1717,36 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const
       }
       __syncthreads();
     }
-  if (nonpd || theta_cnt + negs != q) {
-    if (tid == 0) flag[0] = 0;
+  __syncthreads();
+  if (c.nonpd || c.theta_cnt + c.negs != q) {
+    if (tid == 0) {
+      flag[0] = 0;
+      flag[1] = c.nonpd ? 3 : 4;  // S not positive definite / not the q smallest
+      flag[2] = c.theta_cnt + c.negs;
+      flag[3] = q;
+    }
     return;
   }
+  // final order by the (possibly repaired) values
   for (int j = tid; j < q; j += nt) {
     int r = 0;
-    for (int i = 0; i < q; ++i)
-      if (mu[i] < mu[j] || (mu[i] == mu[j] && i < j)) ++r;
-    perm[r] = j;
+    for (int i = 0; i < q; ++i) {
+      const df d = df_sub(c.muS[i], c.muS[j]);
+      if (df_lt0(d) || (d.hi == 0.f && d.lo == 0.f && i < j)) ++r;
+    }
+    c.perm[r] = j;  // all values are finite here (the overlap test rejects NaN)
   }
   __syncthreads();
-  for (int c = tid; c < q; c += nt) evals[c] = mu[perm[c]];
+  for (int r = tid; r < q; r += nt) evals[r] = df_to_double(c.muS[c.perm[r]]);
   for (int idx = tid; idx < n * q; idx += nt) {
-    const int i = idx / q, c = idx % q, b = perm[c];
+    const int i = idx / q, r = idx % q, b = c.perm[r];
     const df corr = dot4(X + i * q, 1, Ov + b, q, q).value();
     evecs[idx] = df_to_double(df_sub(X[i * q + b], df{0.5f * corr.hi, 0.5f * corr.lo}));
   }
-  if (tid == 0) flag[0] = 1;
+  if (tid == 0) {
+    flag[0] = 1;
+    flag[1] = 0;
+  }
 }
 
 // Fallback: H = [[Theta, Ft L^-T], [L^-1 Ft^T, L^-1 Tt L^-T]] with S = L L^T
@@ -1526,7 +2029,7 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
   alloc((void**)&w->sr_mu, sizeof(double) * qmax);
   alloc((void**)&w->sr_X, sizeof(double) * nm * qmax);
   alloc((void**)&w->sr_conv, sizeof(int) * qmax);
-  alloc((void**)&w->sr_flag, sizeof(int));
+  alloc((void**)&w->sr_flag, 4 * sizeof(int));
   if (err) *err = e;
   if (e != cudaSuccess) {
     pencil_work_destroy(w);
@@ -1606,10 +2109,11 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   };
   const size_t kbs = sizeof(df) * dn;
   const size_t srs = sizeof(df) * (2.0 * m + 2.0 * m * q + 3.0 * q * q + 2.0 * q + 2.0 * n);
-  const size_t chs = sizeof(df) * (1.0 * n * q + 4.0 * q * q + m + 1.0 * m * q);
+  const size_t chs = sizeof(df) * (1.0 * n * q + 5.0 * q * q + 2.0 * m + 1.0 * m * q + 1.0 * q * (q + kMaxCluster) +
+                                    3.0 * n * kMaxCluster + 1.0 * kMaxCluster * q);
   const size_t fs = sizeof(df) * q * q;
   const size_t xs = sizeof(df) * (1.0 * m * q + 1.0 * q * q);
-  const bool fast = q <= kSrqiMaxQ && srs <= 200 * 1024 && chs <= 200 * 1024;
+  const bool fast = q <= kSrqiMaxQ && srs <= 200 * 1024 && chs <= 220 * 1024;
   // kernels launched here; the dense eigensolver's launcher counts its own
   ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * m * q + 3.0 * q * q + 1.0 * n * q), 0.0,
                fast ? 7 : 5);
@@ -1628,8 +2132,8 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
     smem_attr((const void*)k_srqi, srs);
     smem_attr((const void*)k_srqi_check, chs);
     k_srqi<<<q, kSrqiThreads, srs, st>>>(m, q, theta, w->KB, w->Ft, w->Tt, w->St, w->sr_mu, w->sr_X, w->sr_conv);
-    k_srqi_check<<<1, kSrqiThreads, chs, st>>>(m, q, theta, w->Ft, w->Tt, w->St, w->sr_mu, w->sr_X, w->sr_conv, mu,
-                                              w->Yh, w->sr_flag);
+    k_srqi_check<<<1, kSrqiThreads, chs, st>>>(m, q, theta, w->KB, w->Ft, w->Tt, w->St, w->sr_mu, w->sr_X,
+                                               w->sr_conv, mu, w->Yh, w->sr_flag);
     skip = w->sr_flag;
   }
   smem_attr((const void*)k_std_form, fs);
