@@ -11,9 +11,10 @@ solve, and the copy of eigenvalues and eigenvectors back to pinned host memory
 inside the timed region.
 
 Default workload: 2D P1 FE Laplace on the L-shape (-1,1)^2 minus [0,1)x(-1,0],
-h = 1/512, N = 784,385, q = 20, mixed precision (float32 V-cycle, float64
-defect / Rayleigh-Ritz / recombination).  Its accuracy is checked against the
-float64 path converged on the same hierarchy.
+h = 1/512, N = 784,385, q = 20, mixed precision (float32 V-cycle, two V-cycles
+per correction; float-float defect / Rayleigh-Ritz / recombination), stopping
+at relative residual 1e-4.  Its eigenvalues are checked against the float64
+path converged to 1e-8 on the same hierarchy (rel_eig_err_vs_fp64 in config).
 
 Multi-GPU: the solve does not shard; with --gpus N each rank runs an independent
 replica of the workload ("replicas only"), value sums the ranks' solves.
@@ -136,23 +137,50 @@ class ClockSampler:
 
 
 def oracle_sample(blob, q, qe, n_corr, sample_corr=2):
-    """The CPU oracle on the same hierarchy, single thread: the nested phase plus
-    `sample_corr` finest-level corrections, scaled to `n_corr` corrections."""
-    from threadpoolctl import threadpool_limits
-
+    """The CPU oracle on the same hierarchy: the nested phase plus `sample_corr`
+    finest-level corrections, scaled to `n_corr` corrections.  Runs in the calling
+    process; oracle_samples() runs it single-threaded in a child."""
     from oracle import amg_oracle as O
 
     oh = O.read_blob(blob)
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1))
-        t1 = time.perf_counter()
-        O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1 + sample_corr))
-        t2 = time.perf_counter()
+    t0 = time.perf_counter()
+    O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1))
+    t1 = time.perf_counter()
+    O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1 + sample_corr))
+    t2 = time.perf_counter()
     per_corr = (t2 - t1 - (t1 - t0)) / sample_corr
     nested = (t1 - t0) - per_corr
     est = nested + n_corr * per_corr
     return q / est, est, nested, per_corr, (t2 - t0)
+
+
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                     "VECLIB_MAXIMUM_THREADS": "1", "NUMEXPR_NUM_THREADS": "1"}
+
+
+def oracle_samples(workload, cap, qe, n_corr, count):
+    """`count` oracle samples in a fresh single-threaded interpreter (BLAS thread
+    counts are fixed by the environment before numpy loads; the child builds the
+    same seeded workload and never touches the GPU).  Returns a list of
+    oracle_sample() tuples."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--workload", workload,
+           "--reference-corrections", str(n_corr), "--steps", str(count), "--warmup", "0"]
+    if cap is not None:
+        cmd += ["--cap", str(cap)]
+    if qe is not None:
+        cmd += ["--q-extra", str(qe)]
+    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True, timeout=1800)
+    return [tuple(x) for x in json.loads(out.stdout.strip().splitlines()[-1])]
+
+
+def oracle_child(args):
+    """--oracle-child: print the samples as one JSON line (see oracle_samples)."""
+    p, blob, h, q, qe, tol = build_workload(args.workload, args.cap)
+    if args.q_extra is not None:
+        qe = args.q_extra
+    res = [oracle_sample(blob, q, qe, args.reference_corrections) for _ in range(args.steps)]
+    print(json.dumps(res), flush=True)
 
 
 def run_reference(args):
@@ -162,13 +190,8 @@ def run_reference(args):
         return
     p, blob, h, q, qe, tol = build_workload(args.workload)
     n_corr = args.reference_corrections
-    vals = []
-    t_all = 0.0
-    for i in range(args.warmup + args.steps):
-        v, est, nested, per_corr, wall = oracle_sample(blob, q, qe, n_corr)
-        t_all += wall
-        if i >= args.warmup:
-            vals.append(v)
+    samples = oracle_samples(args.workload, None, qe, n_corr, args.warmup + args.steps)
+    vals = [smp[0] for smp in samples[args.warmup:]]
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": "eigenpairs/s", "value": value, "unit": "eigenpairs/s",
@@ -176,8 +199,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "N": p.n, "q": q, "q_extra": qe, "levels": h.sizes},
         "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: nested phase + 2 finest corrections of the FP64 oracle, scaled to "
-                                   f"{n_corr} corrections"},
+                         "sample": f"per step: nested phase + 2 finest corrections of the FP64 oracle "
+                                   f"(one thread), scaled to {n_corr} corrections"},
         "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -192,15 +215,21 @@ def main():
     ap.add_argument("--workload", default="lshape_h512_q20", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reference-corrections", type=int, default=12)
+    ap.add_argument("--reference-corrections", type=int, default=15,
+                    help="finest-level corrections the reference arm's oracle timing is scaled to (the GPU run "
+                         "of the default workload takes 15)")
     ap.add_argument("--tol", type=float, default=None, help="relative-residual tolerance (workload default)")
     ap.add_argument("--coarse-modes", type=int, default=None, help="coarse modes in the pencil (0 = all)")
     ap.add_argument("--q-extra", type=int, default=None)
     ap.add_argument("--cap", type=int, default=None, help="coarse-level cap of the AMG setup")
     ap.add_argument("--sweeps", type=int, default=1, help="l1-Jacobi sweeps before and after the coarse correction")
     ap.add_argument("--v-cycles", type=int, default=2, help="V-cycles per correction (AMG iteration steps m)")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
+    if args.oracle_child:
+        oracle_child(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -336,7 +365,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            v, est, nested, per_corr, wall_c = oracle_sample(blob, q, qe, corrections)
+            v, est, nested, per_corr, wall_c = oracle_samples(args.workload, args.cap, qe, corrections, 1)[0]
             cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
                    "sample": f"FP64 oracle, 1 thread: nested phase ({nested:.1f}s) + 2 finest corrections "
                              f"({per_corr:.1f}s each) measured, scaled to the {corrections} corrections of this run"}

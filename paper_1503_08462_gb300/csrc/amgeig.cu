@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "amgeig.h"
@@ -397,7 +398,7 @@ void spmm(const DevCsr& S, const double* X, int wdt, double* Y, bool acc, cudaSt
 void spmm(const DevCsr& S, const float* X, int wdt, float* Y, bool acc, cudaStream_t s) { launch_spmm_f32(S, X, wdt, Y, acc, s); }
 void jacobi_to_v(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, const double* U, double* V, cudaStream_t s, int) { launch_jacobi_to_v_f64(A, d, b, x, wdt, U, V, s); }
 // the float32 V-cycle belongs to the mixed path, whose U and V are float-float
-void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv) { launch_jacobi_to_vdf_f32(A, d, b, x, wdt, reinterpret_cast<const float2*>(U), reinterpret_cast<float2*>(V), s, qv); }
+void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv, const float* xadd = nullptr) { launch_jacobi_to_vdf_f32(A, d, b, x, wdt, reinterpret_cast<const float2*>(U), reinterpret_cast<float2*>(V), s, qv, xadd); }
 void add_to_v(const double* U, const double* x, int rows, int q, int, double* V, cudaStream_t s) { launch_add_to_v_f64(U, x, static_cast<long long>(rows) * q, V, s); }
 void add_to_v(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t s) { launch_add_to_vdf(reinterpret_cast<const float2*>(U), x, rows, q, ldx, reinterpret_cast<float2*>(V), s); }
 void axpy(const double* x, long long c, double* y, cudaStream_t s) { launch_axpy_f64(x, c, y, s); }
@@ -418,7 +419,7 @@ int width_of(SolveWork* w, float*) { return w->ld32; }
 
 template <typename T>
 void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool to_v, const double* U, double* V,
-            cudaStream_t st) {
+            cudaStream_t st, const float* xadd = nullptr) {
   const int q = width_of(w, static_cast<T*>(nullptr));
   const int n = h->nlev;
   auto& B = VBufs<T>::B(w);
@@ -448,13 +449,20 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
     spmm(h->P[l], X[l + 1], q, X[l], true, st);
     for (int s = 0; s < post; ++s) {
       if (to_v && l == k && s == post - 1) {
-        jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt);
+        if constexpr (std::is_same<T, float>::value)
+          jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt, xadd);
+        else
+          jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt);
       } else {
         jacobi(A, d, B[l], X[l], q, Tm[l], st);
         std::swap(X[l], Tm[l]);
       }
     }
-    if (to_v && l == k && post == 0) add_to_v(U, X[l], static_cast<int>(h->sizes[l]), w->qt, q, V, st);
+    if (to_v && l == k && post == 0) {
+      if constexpr (std::is_same<T, float>::value)
+        if (xadd) axpy(xadd, h->sizes[l] * q, X[l], st);
+      add_to_v(U, X[l], static_cast<int>(h->sizes[l]), w->qt, q, V, st);
+    }
   }
 }
 
@@ -474,6 +482,23 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
   auto& E = VBufs<T>::E(w);
   const int wd = width_of(w, static_cast<T*>(nullptr));
   const long long cnt = h->sizes[k] * wd;
+  if constexpr (std::is_same<T, float>::value) {
+    // the same sums without the copies: the first cycle's result becomes E by a
+    // pointer swap, its residual goes to D and trades places with B (D then
+    // keeps the original defect), and the last cycle's final sweep writes
+    // V = U + (x + E) itself
+    vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
+    std::swap(X[k], E[k]);
+    residual(h->A[k], B[k], E[k], wd, D[k], st);
+    std::swap(B[k], D[k]);
+    for (int c = 1; c + 1 < o.v_cycles; ++c) {
+      vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
+      axpy(X[k], cnt, E[k], st);
+      residual(h->A[k], D[k], E[k], wd, B[k], st);
+    }
+    vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, true, U, V, st, E[k]);
+    return;
+  }
   cudaMemcpyAsync(D[k], B[k], sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(E[k], 0, sizeof(T) * cnt, st);
   for (int c = 0; c < o.v_cycles; ++c) {

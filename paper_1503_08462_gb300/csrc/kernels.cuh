@@ -100,7 +100,7 @@ void launch_cols_to_df(const double* src, int rows, int ld, int q, float2* dst, 
 // last float32 sweep on the working level fused with V = U + x (U, V float-float,
 // row stride qv; b and x row stride width)
 void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                              const float2* U, float2* V, cudaStream_t st, int qv);
+                              const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd = nullptr);
 // V = U + x (U, V float-float rows x q; x float32 with row stride ldx)
 void launch_add_to_vdf(const float2* U, const float* x, int rows, int q, int ldx, float2* V, cudaStream_t st);
 

@@ -1525,11 +1525,11 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const
                           : X[i * q + j];
     }
     __syncthreads();
-    // the block only has to find what the accepted vectors do not span:
-    // project them out (Mt inner product) and re-normalise
-    block_deflate(X, Sl, Yb, MY, AY, c.good, ys, m, q, cs);
-    block_cholqr(th, F, T, Sl, Yb, AY, MY, &c, m, q, cs);
     if (dup) {
+      // the block only has to find what the accepted vectors do not span:
+      // project them out (Mt inner product) and re-normalise
+      block_deflate(X, Sl, Yb, MY, AY, c.good, ys, m, q, cs);
+      block_cholqr(th, F, T, Sl, Yb, AY, MY, &c, m, q, cs);
       // shift: the mean Rayleigh quotient of the block (inside the cluster)
       pencil_apply(th, F, T, Sl, Yb, AY, MY, m, q, cs);
       for (int idx = tid; idx < 2 * cs; idx += nt) {

@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
                                                         int w4, float4* __restrict__ out1, float4* __restrict__ out2,
                                                         const double* __restrict__ U, double* __restrict__ V, int qv,
                                                         int G, const float2* __restrict__ U2 = nullptr,
-                                                        float2* __restrict__ V2 = nullptr) {
+                                                        float2* __restrict__ V2 = nullptr,
+                                                        const float4* __restrict__ xadd = nullptr) {
   const int rpb = blockDim.x / G;
   const int lane = threadIdx.x % G;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
@@ -332,9 +333,14 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
         for (int k = 0; k < 4; ++k)
           if (4 * c4 + k < qv) V[vb + k] = U[vb + k] + static_cast<double>(xs[k]);
       } else {
-        // MODE 4: float-float V = U + x
+        // MODE 4: float-float V = U + x (+ xadd: the earlier V-cycles' sum)
         const long long vb = static_cast<long long>(row) * qv + 4 * c4;
-        const float xs[4] = {xn.x, xn.y, xn.z, xn.w};
+        float4 xt = xn;
+        if (xadd) {
+          const float4 e = xadd[o];
+          xt = make_float4(xn.x + e.x, xn.y + e.y, xn.z + e.z, xn.w + e.w);
+        }
+        const float xs[4] = {xt.x, xt.y, xt.z, xt.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (4 * c4 + k < qv) {
@@ -776,15 +782,16 @@ void launch_f32_to_f64_unpad(const float* src, int rows, int q, int ld, double* 
 }
 
 void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                              const float2* U, float2* V, cudaStream_t st, int qv) {
+                              const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd) {
   if (A.rows == 0) return;
   const int w4 = width / 4, G = group_for_f4(w4);
   const double N = A.rows;
-  ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + (2.0 * 4 + 16.0) * N * width,
+  ProfScope ps(st, P_SMOOTH,
+               4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + ((xadd ? 3.0 : 2.0) * 4 + 16.0) * N * width,
                2.0 * A.nnz * width);
   k_smooth_f4<4><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
       A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
-      nullptr, nullptr, nullptr, nullptr, qv, G, U, V);
+      nullptr, nullptr, nullptr, nullptr, qv, G, U, V, reinterpret_cast<const float4*>(xadd));
 }
 
 __global__ void k_add_to_vdf(const float2* __restrict__ U, const float* __restrict__ x, int rows, int q, int ldx,
