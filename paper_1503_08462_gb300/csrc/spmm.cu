@@ -279,11 +279,47 @@ void smooth_impl(const DevCsr& A, const T* vals, const T* dinv, const T* b, cons
 // ------------------------------------------------------------------ float32, 16-byte vectors
 //
 // The float32 V-cycle works on blocks whose row stride is a multiple of 4, so
-// each thread moves one float4 (16 bytes) per gathered row: a row group is
-// G = width/4 threads (rounded up to a power of two), and a warp serves
-// 32/G rows at once, keeping more independent gathers in flight.
+// rows are moved as float4 (16 bytes).  A row group of G lanes owns a row; lane
+// l handles the float4 columns l, l + G, ... (CPT of them, 1..3), so for the
+// usual width of 24 floats two lanes take three columns each: per gathered
+// row the pair reads 32 contiguous bytes per instruction, the index and value
+// of each nonzero are loaded by two lanes instead of eight, and every lane
+// keeps three independent 16-byte gathers in flight.
 
-template <int MODE>
+struct F4Geo {
+  int G, cpt;
+};
+
+// Few lanes per row pay off only while the rows alone keep the GPU full: below
+// about four resident waves of row groups the one-column-per-lane layout (more
+// threads, shorter chains) is faster on the coarse levels.
+F4Geo f4_geo(int w4, long long rows) {
+  int G = 1;
+  while (G * 3 < w4 && G < 32) G <<= 1;
+  int cpt = (w4 + G - 1) / G;
+  while (cpt > 3) {
+    G <<= 1;
+    cpt = (w4 + G - 1) / G;
+  }
+  if (rows * G < 4LL * kNumSms * 1024) {
+    G = 1;
+    while (G < w4 && G < 32) G <<= 1;
+    cpt = (w4 + G - 1) / G;
+  }
+  return F4Geo{G, cpt};
+}
+
+__device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
+  acc.x = fmaf(s, x.x, acc.x);
+  acc.y = fmaf(s, x.y, acc.y);
+  acc.z = fmaf(s, x.z, acc.z);
+  acc.w = fmaf(s, x.w, acc.w);
+}
+
+// MODE 0: x = D^-1 b, r = b - A x (x from 0);  1: x <- x + D^-1 (b - A x);
+// 2: r = b - A x;  3: V = U + (x + D^-1 (b - A x)) in float64;  4: the same in
+// float-float, plus xadd when given (the sum of the earlier V-cycles).
+template <int MODE, int CPT>
 __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __restrict__ rp,
                                                         const int* __restrict__ ci, const float* __restrict__ a,
                                                         const float* __restrict__ dinv,
@@ -297,24 +333,31 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
   const int lane = threadIdx.x % G;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
   if (row >= n) return;
-  for (int c4 = lane; c4 < w4; c4 += G) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int p0 = rp[row], p1 = rp[row + 1];
+  float4 acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int p0 = rp[row], p1 = rp[row + 1];
+  const float4* src = MODE == 0 ? b : x;
 #pragma unroll 4
-    for (int p = p0; p < p1; ++p) {
-      const int j = ci[p];
-      float s = a[p];
-      if (MODE == 0) s *= dinv[j];
-      const float4 xv = (MODE == 0 ? b : x)[static_cast<long long>(j) * w4 + c4];
-      acc.x = fmaf(s, xv.x, acc.x);
-      acc.y = fmaf(s, xv.y, acc.y);
-      acc.z = fmaf(s, xv.z, acc.z);
-      acc.w = fmaf(s, xv.w, acc.w);
+  for (int p = p0; p < p1; ++p) {
+    const int j = ci[p];
+    float s = a[p];
+    if (MODE == 0) s *= dinv[j];
+    const float4* sr = src + static_cast<long long>(j) * w4;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c4 = lane + t * G;
+      if (c4 < w4) fma4(s, sr[c4], acc[t]);
     }
+  }
+  const float di = dinv ? dinv[row] : 0.f;
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c4 = lane + t * G;
+    if (c4 >= w4) continue;
     const long long o = static_cast<long long>(row) * w4 + c4;
     const float4 bi = b[o];
-    const float4 res = make_float4(bi.x - acc.x, bi.y - acc.y, bi.z - acc.z, bi.w - acc.w);
-    const float di = dinv ? dinv[row] : 0.f;
+    const float4 res = make_float4(bi.x - acc[t].x, bi.y - acc[t].y, bi.z - acc[t].z, bi.w - acc[t].w);
     if (MODE == 0) {
       out1[o] = make_float4(di * bi.x, di * bi.y, di * bi.z, di * bi.w);
       out2[o] = res;
@@ -353,6 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
   }
 }
 
+template <int CPT>
 __global__ void __launch_bounds__(kThreads) k_spmm_f4(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                       const float* __restrict__ v, const float4* __restrict__ X,
                                                       int w4, float4* __restrict__ Y, int G, int accumulate) {
@@ -360,34 +404,57 @@ __global__ void __launch_bounds__(kThreads) k_spmm_f4(int n, const int* __restri
   const int lane = threadIdx.x % G;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
   if (row >= n) return;
-  for (int c4 = lane; c4 < w4; c4 += G) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int p0 = rp[row], p1 = rp[row + 1];
+  float4 acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int p0 = rp[row], p1 = rp[row + 1];
 #pragma unroll 4
-    for (int p = p0; p < p1; ++p) {
-      const float s = v[p];
-      const float4 xv = X[static_cast<long long>(ci[p]) * w4 + c4];
-      acc.x = fmaf(s, xv.x, acc.x);
-      acc.y = fmaf(s, xv.y, acc.y);
-      acc.z = fmaf(s, xv.z, acc.z);
-      acc.w = fmaf(s, xv.w, acc.w);
+  for (int p = p0; p < p1; ++p) {
+    const float s = v[p];
+    const float4* xr = X + static_cast<long long>(ci[p]) * w4;
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c4 = lane + t * G;
+      if (c4 < w4) fma4(s, xr[c4], acc[t]);
     }
+  }
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    const int c4 = lane + t * G;
+    if (c4 >= w4) continue;
     const long long o = static_cast<long long>(row) * w4 + c4;
+    float4 r = acc[t];
     if (accumulate) {
       const float4 y = Y[o];
-      acc.x += y.x;
-      acc.y += y.y;
-      acc.z += y.z;
-      acc.w += y.w;
+      r = make_float4(r.x + y.x, r.y + y.y, r.z + y.z, r.w + y.w);
     }
-    Y[o] = acc;
+    Y[o] = r;
   }
 }
 
-int group_for_f4(int w4) {
-  int G = 1;
-  while (G < w4 && G < 32) G <<= 1;
-  return G;
+template <int MODE>
+void smooth_f4(const DevCsr& A, const float* dinv, const float* b, const float* x, int w4, float* out1, float* out2,
+               const double* U, double* V, int qv, const float2* U2, float2* V2, const float* xadd,
+               cudaStream_t st) {
+  const F4Geo g = f4_geo(w4, A.rows);
+  const int blocks = ceil_div(A.rows, kThreads / g.G);
+#define AMGEIG_SMOOTH(C)                                                                                        \
+  k_smooth_f4<MODE, C><<<blocks, kThreads, 0, st>>>(                                                            \
+      A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4, \
+      reinterpret_cast<float4*>(out1), reinterpret_cast<float4*>(out2), U, V, qv, g.G, U2, V2,                   \
+      reinterpret_cast<const float4*>(xadd))
+  switch (g.cpt) {
+    case 1:
+      AMGEIG_SMOOTH(1);
+      break;
+    case 2:
+      AMGEIG_SMOOTH(2);
+      break;
+    default:
+      AMGEIG_SMOOTH(3);
+      break;
+  }
+#undef AMGEIG_SMOOTH
 }
 
 // ------------------------------------------------------------------ augmentation
@@ -592,13 +659,26 @@ void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool 
     spmm_impl<float>(S, S.v32, X, width, Y, accumulate, st);
     return;
   }
-  const int w4 = width / 4, G = group_for_f4(w4);
+  const int w4 = width / 4;
+  const F4Geo g = f4_geo(w4, S.rows);
+  const int blocks = ceil_div(S.rows, kThreads / g.G);
   ProfScope ps(st, P_TRANSFER,
                4.0 * (S.rows + 1) + 8.0 * S.nnz + 4.0 * S.cols * width + 4.0 * S.rows * width * (accumulate ? 2 : 1),
                2.0 * S.nnz * width);
-  k_spmm_f4<<<ceil_div(S.rows, kThreads / G), kThreads, 0, st>>>(
-      S.rows, S.rp, S.ci, S.v32, reinterpret_cast<const float4*>(X), w4, reinterpret_cast<float4*>(Y), G,
-      accumulate ? 1 : 0);
+  const float4* X4 = reinterpret_cast<const float4*>(X);
+  float4* Y4 = reinterpret_cast<float4*>(Y);
+  const int acc = accumulate ? 1 : 0;
+  switch (g.cpt) {
+    case 1:
+      k_spmm_f4<1><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc);
+      break;
+    case 2:
+      k_spmm_f4<2><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc);
+      break;
+    default:
+      k_spmm_f4<3><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc);
+      break;
+  }
 }
 
 void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const double* b, int width, double* x,
@@ -608,13 +688,10 @@ void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const do
 void launch_presmooth_residual_f32(const DevCsr& A, const float* dinv, const float* b, int width, float* x,
                                    float* r, cudaStream_t st) {
   if (width % 4 == 0 && A.rows > 0) {
-    const int w4 = width / 4, G = group_for_f4(w4);
     const double N = A.rows;
     const double vec = 12.0 * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
-    k_smooth_f4<0><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
-        A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), nullptr, w4,
-        reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r), nullptr, nullptr, 0, G);
+    smooth_f4<0>(A, dinv, b, nullptr, width / 4, x, r, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st);
     return;
   }
   smooth_impl<float, 0>(A, A.v32, dinv, b, nullptr, width, x, r, nullptr, nullptr, st);
@@ -626,13 +703,10 @@ void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, con
 void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
                        float* x_out, cudaStream_t st) {
   if (width % 4 == 0 && A.rows > 0) {
-    const int w4 = width / 4, G = group_for_f4(w4);
     const double N = A.rows;
     const double vec = 12.0 * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
-    k_smooth_f4<1><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
-        A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
-        reinterpret_cast<float4*>(x_out), nullptr, nullptr, nullptr, 0, G);
+    smooth_f4<1>(A, dinv, b, x, width / 4, x_out, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st);
     return;
   }
   smooth_impl<float, 1>(A, A.v32, dinv, b, x, width, x_out, nullptr, nullptr, nullptr, st);
@@ -642,13 +716,10 @@ void launch_residual_f64(const DevCsr& A, const double* b, const double* x, int 
 }
 void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st) {
   if (width % 4 == 0 && A.rows > 0) {
-    const int w4 = width / 4, G = group_for_f4(w4);
     const double N = A.rows;
     const double vec = 12.0 * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 0.0 + vec, 2.0 * A.nnz * width);
-    k_smooth_f4<2><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
-        A.rows, A.rp, A.ci, A.v32, nullptr, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
-        reinterpret_cast<float4*>(r), nullptr, nullptr, nullptr, 0, G);
+    smooth_f4<2>(A, nullptr, b, x, width / 4, r, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st);
     return;
   }
   smooth_impl<float, 2>(A, A.v32, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
@@ -660,13 +731,10 @@ void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b
 void launch_jacobi_to_v_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
                             const double* U, double* V, cudaStream_t st, int qv) {
   if (width % 4 == 0 && A.rows > 0) {
-    const int w4 = width / 4, G = group_for_f4(w4);
     const double N = A.rows;
     const double vec = (2.0 * 4 + 16.0) * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
-    k_smooth_f4<3><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
-        A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
-        nullptr, nullptr, U, V, qv, G);
+    smooth_f4<3>(A, dinv, b, x, width / 4, nullptr, nullptr, U, V, qv, nullptr, nullptr, nullptr, st);
     return;
   }
   smooth_impl<float, 3>(A, A.v32, dinv, b, x, width, nullptr, nullptr, U, V, st);
@@ -784,14 +852,11 @@ void launch_f32_to_f64_unpad(const float* src, int rows, int q, int ld, double* 
 void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
                               const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd) {
   if (A.rows == 0) return;
-  const int w4 = width / 4, G = group_for_f4(w4);
   const double N = A.rows;
   ProfScope ps(st, P_SMOOTH,
                4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + ((xadd ? 3.0 : 2.0) * 4 + 16.0) * N * width,
                2.0 * A.nnz * width);
-  k_smooth_f4<4><<<ceil_div(A.rows, kThreads / G), kThreads, 0, st>>>(
-      A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4,
-      nullptr, nullptr, nullptr, nullptr, qv, G, U, V, reinterpret_cast<const float4*>(xadd));
+  smooth_f4<4>(A, dinv, b, x, width / 4, nullptr, nullptr, nullptr, nullptr, qv, U, V, xadd, st);
 }
 
 __global__ void k_add_to_vdf(const float2* __restrict__ U, const float* __restrict__ x, int rows, int q, int ldx,
