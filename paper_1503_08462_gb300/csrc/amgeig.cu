@@ -261,6 +261,7 @@ struct amgeig_hierarchy_t {
   std::vector<double*> dinv64;
   std::vector<float*> dinv32;
   std::vector<DevCsr> P, R;  // v64 and v32
+  std::vector<DevCsr> PC;    // PC[k] = I_n^k = P_k ... P_{n-2} (rows_k x d_n), float-float values
   int dn = 0;
   double *An = nullptr, *Mn = nullptr, *Z = nullptr, *theta = nullptr, *Ainv = nullptr;
   float* Ainv32 = nullptr;
@@ -565,6 +566,19 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
     launch_pencil_solve(w->pw, h->dn, modes, q, nullptr, cur, w->G, h->Zdf, h->theta, w->mu, w->Xc,
                         as_df(w->PX[n - 1]), w->Yv, h->dstatus, st, w->nfallback);
+    if (q <= 32) {
+      // U = I_n^k Xc + V Y in one pass: the composite prolongation is applied row by row
+      const DevCsr& PC = h->PC[k];
+      launch_recombine_pc_df(Nk, PC.nnz, PC.rp, PC.ci, PC.d2, as_df(w->PX[n - 1]), as_df(w->V), w->Yv, q,
+                             as_df(w->U), st);
+      CK(cudaGetLastError());
+      {
+        ProfScope ps(st, P_OTHER, 16.0 * q, 0.0);
+        k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
+      }
+      CK(cudaGetLastError());
+      return AMGEIG_OK;
+    }
     const float2* px = as_df(w->PX[n - 1]);
     for (int l = n - 2; l >= k; --l) {
       launch_spmm_df(h->P[l], px, q, as_df(w->PX[l]), false, st, P_CHAIN);
@@ -903,6 +917,66 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
       CK(m.upload(&D.v64, S.a));
       CK(m.upload(&D.v32, v32));
       CK(m.upload(&D.d2, v2));
+    }
+  }
+  // composite prolongations I_n^k (coarsest -> level k) for the recombination:
+  // PC[n-2] = P_{n-2}, PC[k] = P_k PC[k+1] (row-wise sparse products in float64)
+  h->PC.resize(n > 1 ? n - 1 : 0);
+  {
+    HostCsr next;
+    std::vector<double> acc(static_cast<size_t>(h->dn), 0.0);
+    std::vector<int32_t> mark(static_cast<size_t>(h->dn), -1), cols;
+    for (int k = n - 2; k >= 0; --k) {
+      const HostCsr& Pk = prolong[k];
+      HostCsr C;
+      C.rows = Pk.rows;
+      C.cols = h->dn;
+      C.rp.assign(static_cast<size_t>(Pk.rows) + 1, 0);
+      for (int64_t i = 0; i < Pk.rows; ++i) {
+        cols.clear();
+        for (int32_t p = Pk.rp[i]; p < Pk.rp[i + 1]; ++p) {
+          const int32_t t = Pk.ci[p];
+          const double v = Pk.a[p];
+          if (k == n - 2) {
+            if (mark[t] != static_cast<int32_t>(i)) {
+              mark[t] = static_cast<int32_t>(i);
+              acc[t] = 0.0;
+              cols.push_back(t);
+            }
+            acc[t] += v;
+            continue;
+          }
+          for (int32_t r = next.rp[t]; r < next.rp[t + 1]; ++r) {
+            const int32_t c = next.ci[r];
+            if (mark[c] != static_cast<int32_t>(i)) {
+              mark[c] = static_cast<int32_t>(i);
+              acc[c] = 0.0;
+              cols.push_back(c);
+            }
+            acc[c] += v * next.a[r];
+          }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int32_t c : cols) {
+          C.ci.push_back(c);
+          C.a.push_back(acc[c]);
+        }
+        C.rp[static_cast<size_t>(i) + 1] = static_cast<int32_t>(C.ci.size());
+      }
+      std::fill(mark.begin(), mark.end(), -1);
+      DevCsr& D = h->PC[k];
+      D.rows = static_cast<int>(C.rows);
+      D.cols = static_cast<int>(C.cols);
+      D.nnz = static_cast<int>(C.ci.size());
+      std::vector<float2> v2(C.a.size());
+      for (size_t i = 0; i < C.a.size(); ++i) {
+        const float hi = static_cast<float>(C.a[i]);
+        v2[i] = make_float2(hi, static_cast<float>(C.a[i] - static_cast<double>(hi)));
+      }
+      CK(m.upload(&D.rp, C.rp));
+      CK(m.upload(&D.ci, C.ci));
+      CK(m.upload(&D.d2, v2));
+      next = std::move(C);
     }
   }
   // dense coarsest pencil and its eigendecomposition

@@ -89,6 +89,10 @@ void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* la
 void launch_dual_spmm_df(const DevCsr& AM, const float2* V, int q, float2* W, cudaStream_t st);
 void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool accumulate, cudaStream_t st,
                     int cls);
+// U = PC Xc + V Y with PC (CSR rows x d_n, float-float values) the composite
+// prolongation I_n^k and Xc (d_n x q) float-float; q <= 32.
+void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, const float2* pv, const float2* Xc,
+                            const float2* V, const double* Y, int q, float2* U, cudaStream_t st);
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
                          cudaStream_t st);
 size_t gram_df_scratch_doubles(int rows, int q, int w);

@@ -277,6 +277,52 @@ __global__ void __launch_bounds__(kThreads) k_recombine_rows(int n, const float2
     if (c < q) st2(U, base + c, acc[c].value());
 }
 
+// U = I_n^k Xc + V Y with the composite prolongation I_n^k (CSR, float-float
+// values) applied row by row: the prolongation chain and its intermediate
+// blocks disappear; each thread owns one row and all Q accumulators.
+template <int Q>
+__global__ void __launch_bounds__(kThreads) k_recombine_pc(int n, const int* __restrict__ rp,
+                                                           const int* __restrict__ ci, const float2* __restrict__ pv,
+                                                           const float2* __restrict__ Xc,
+                                                           const float2* __restrict__ V,
+                                                           const double* __restrict__ Y, int q,
+                                                           float2* __restrict__ U) {
+  __shared__ __align__(16) float2 ys[Q * Q];
+  for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+    const int d = i / Q, c = i % Q;
+    const df v = (d < q && c < q) ? df_from_double(Y[d * q + c]) : df{0.f, 0.f};
+    ys[i] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  const long long row = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const long long base = row * q;
+  df_acc acc[Q];
+#pragma unroll
+  for (int c = 0; c < Q; ++c) acc[c] = acc_zero();
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const df w = ld2(pv, p);
+    const long long xr = static_cast<long long>(ci[p]) * q;
+#pragma unroll
+    for (int c = 0; c < Q; ++c)
+      if (c < q) acc[c].fma(w, ld2(Xc, xr + c));
+  }
+  for (int d = 0; d < q; ++d) {
+    const df v = ld2(V, base + d);
+    const float4* yr = reinterpret_cast<const float4*>(ys + d * Q);
+#pragma unroll
+    for (int c = 0; c < Q; c += 2) {
+      const float4 y2 = yr[c / 2];
+      acc[c].fma(v, df{y2.x, y2.y});
+      acc[c + 1].fma(v, df{y2.z, y2.w});
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < Q; ++c)
+    if (c < q) st2(U, base + c, acc[c].value());
+}
+
 // ---------------------------------------------------------------- Gram V^T W (df inputs)
 // G = V^T [A V | M V] (q x 2q).  Both halves are symmetric, so only the pairs
 // a <= b of each half are formed: np = q (q + 1) pairs.  A block stages a slab
@@ -583,6 +629,22 @@ void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool
                2.0 * S.nnz * width);
   AMGEIG_DISPATCH(g.cpt, k_spmm_df,
                   <<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.d2, X, width, Y, g.G, accumulate ? 1 : 0))
+}
+
+void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, const float2* pv, const float2* Xc,
+                            const float2* V, const double* Y, int q, float2* U, cudaStream_t st) {
+  if (rows <= 0 || q <= 0) return;
+  ProfScope ps(st, P_RECOMBINE, 16.0 * rows * q + 8.0 * q * q + 4.0 * (rows + 1) + 12.0 * nnz,
+               2.0 * rows * q * q + 2.0 * nnz * q);
+  const int blocks = ceil_div(rows, kThreads);
+  if (q <= 8)
+    k_recombine_pc<8><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+  else if (q <= 16)
+    k_recombine_pc<16><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+  else if (q <= 24)
+    k_recombine_pc<24><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+  else
+    k_recombine_pc<32><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
 }
 
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
