@@ -44,26 +44,35 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha, cons
   }
 }
 
-// x = A b for a dense n x n row-major A and an n x w row-major block b: each
-// thread owns one output, rows_per_block rows per block; four independent
-// accumulators break the FMA dependency chain.
+// x = A b for a dense n x n row-major A and an n x w row-major block b.  One
+// block per output row; its threads are (column, segment) pairs: each sums a
+// contiguous segment of k for one column, and the segments are added in a
+// fixed order in shared memory.  Short independent chains keep the latency of
+// this once-per-V-cycle coarse solve low.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_apply(int n, int w, const T* __restrict__ A, const T* __restrict__ b,
-                                                     T* __restrict__ x, int rows_per_block) {
-  const int rl = threadIdx.x / w, c = threadIdx.x % w;
-  const int r = blockIdx.x * rows_per_block + rl;
-  if (rl >= rows_per_block || r >= n) return;
-  const T* a = A + static_cast<long long>(r) * n;
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-  int k = 0;
-  for (; k + 4 <= n; k += 4) {
-    s0 = fma(a[k], b[static_cast<long long>(k) * w + c], s0);
-    s1 = fma(a[k + 1], b[static_cast<long long>(k + 1) * w + c], s1);
-    s2 = fma(a[k + 2], b[static_cast<long long>(k + 2) * w + c], s2);
-    s3 = fma(a[k + 3], b[static_cast<long long>(k + 3) * w + c], s3);
+                                                     T* __restrict__ x, int segs) {
+  __shared__ T part[256];
+  const int c = threadIdx.x % w, sg = threadIdx.x / w;
+  const int r = blockIdx.x;
+  T s0 = T(0), s1 = T(0);
+  if (sg < segs) {
+    const int len = (n + segs - 1) / segs, k0 = sg * len, k1 = min(n, k0 + len);
+    const T* a = A + static_cast<long long>(r) * n;
+    int k = k0;
+    for (; k + 2 <= k1; k += 2) {
+      s0 = fma(a[k], b[static_cast<long long>(k) * w + c], s0);
+      s1 = fma(a[k + 1], b[static_cast<long long>(k + 1) * w + c], s1);
+    }
+    if (k < k1) s0 = fma(a[k], b[static_cast<long long>(k) * w + c], s0);
+    part[threadIdx.x] = s0 + s1;
   }
-  for (; k < n; ++k) s0 = fma(a[k], b[static_cast<long long>(k) * w + c], s0);
-  x[static_cast<long long>(r) * w + c] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (sg == 0) {
+    T s = part[c];
+    for (int t = 1; t < segs; ++t) s += part[t * w + c];
+    x[static_cast<long long>(r) * w + c] = s;
+  }
 }
 
 // Gram partials: block (chunk, tile) accumulates out[a][b] = sum_{r in chunk} V[r][a] W[r][b]
@@ -211,10 +220,8 @@ template <typename T>
 void launch_dense_apply_t(int n, int w, const T* A, const T* b, T* x, cudaStream_t st, int cls) {
   if (n <= 0 || w <= 0) return;
   ProfScope ps(st, cls, sizeof(T) * (1.0 * n * n + 2.0 * n * w), 2.0 * n * n * w);
-  // float64 issues slowly on this part: fewer rows per block spread it over more SMs
-  const int cap = std::is_same<T, double>::value ? 2 : 8;
-  const int rpb = std::max(1, std::min(cap, 256 / w));
-  k_dense_apply<T><<<ceil_div(n, rpb), rpb * w, 0, st>>>(n, w, A, b, x, rpb);
+  const int segs = std::max(1, std::min(16, 256 / w));
+  k_dense_apply<T><<<n, segs * w, 0, st>>>(n, w, A, b, x, segs);
 }
 
 void launch_dense_apply(int n, int w, const double* A, const double* b, double* x, cudaStream_t st, int cls) {

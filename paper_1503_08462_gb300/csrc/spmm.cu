@@ -320,7 +320,7 @@ __device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
 // 2: r = b - A x;  3: V = U + (x + D^-1 (b - A x)) in float64;  4: the same in
 // float-float, plus xadd when given (the sum of the earlier V-cycles).
 template <int MODE, int CPT>
-__global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __restrict__ rp,
+__global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __restrict__ rp,
                                                         const int* __restrict__ ci, const float* __restrict__ a,
                                                         const float* __restrict__ dinv,
                                                         const float4* __restrict__ b, const float4* __restrict__ x,
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
   for (int t = 0; t < CPT; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int p0 = rp[row], p1 = rp[row + 1];
   const float4* src = MODE == 0 ? b : x;
-#pragma unroll 4
+#pragma unroll 2
   for (int p = p0; p < p1; ++p) {
     const int j = ci[p];
     float s = a[p];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_f4(int n, const int* __rest
 }
 
 template <int CPT>
-__global__ void __launch_bounds__(kThreads) k_spmm_f4(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(kThreads, 6) k_spmm_f4(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                       const float* __restrict__ v, const float4* __restrict__ X,
                                                       int w4, float4* __restrict__ Y, int G, int accumulate) {
   const int rpb = blockDim.x / G;
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_f4(int n, const int* __restri
 #pragma unroll
   for (int t = 0; t < CPT; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int p0 = rp[row], p1 = rp[row + 1];
-#pragma unroll 4
+#pragma unroll 2
   for (int p = p0; p < p1; ++p) {
     const float s = v[p];
     const float4* xr = X + static_cast<long long>(ci[p]) * w4;
