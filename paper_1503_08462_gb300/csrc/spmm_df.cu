@@ -29,20 +29,32 @@ __device__ __forceinline__ void st2(float2* p, long long i, df v) { p[i] = make_
 
 struct Geo {
   int G, rows_per_block, cpt;
+  // G need not divide kThreads: blocks get exactly G * rows_per_block threads, so
+  // every thread owns a row slot of its own block
+  int threads() const { return G * rows_per_block; }
 };
 
-// G lanes per row with CPT = ceil(width / G) <= 8 columns each: about three
-// columns per lane gives each thread independent accumulation chains and cuts
-// the redundant index / value loads of a 32-lane row group
+// G lanes per row with CPT = ceil(width / G) <= 8 columns each: about three or
+// four columns per lane gives each thread independent accumulation chains and
+// cuts the redundant index / value loads of a wide row group.  G need not be a
+// power of two (28 columns: 7 lanes x 4); the fewest idle column slots win,
+// then CPT nearest 3.5, then the larger G.
 Geo geo_for(int width) {
-  int G = 1;
-  while (G * 2 <= width / 3 && G < 32) G <<= 1;
-  int cpt = (width + G - 1) / G;
-  while (cpt > 8) {
-    G <<= 1;
-    cpt = (width + G - 1) / G;
+  int bestG = 1, bestC = width;
+  long long bestKey = -1;
+  for (int G = 1; G <= 32; ++G) {
+    const int cpt = (width + G - 1) / G;
+    if (cpt > 8) continue;
+    const int waste = G * cpt - width;
+    const int dist = cpt * 2 > 7 ? cpt * 2 - 7 : 7 - cpt * 2;  // |cpt - 3.5| * 2
+    const long long key = static_cast<long long>(waste) * 1000 + dist * 40 + (32 - G);
+    if (bestKey < 0 || key < bestKey) {
+      bestKey = key;
+      bestG = G;
+      bestC = cpt;
+    }
   }
-  return Geo{G, kThreads / G, cpt};
+  return Geo{bestG, kThreads / bestG, bestC};
 }
 
 // ---------------------------------------------------------------- defect
@@ -606,7 +618,7 @@ void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* la
   const double N = AM.rows, nnz = AM.nnz;
   ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 4.0 * N * ldr, 4.0 * nnz * q);
   AMGEIG_DISPATCH(g.cpt, k_defect_df,
-                  <<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, U, q, lam, R, ldr, g.G,
+                  <<<blocks, g.threads(), sm, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, U, q, lam, R, ldr, g.G,
                                                  partials))
 }
 
@@ -616,7 +628,7 @@ void launch_dual_spmm_df(const DevCsr& AM, const float2* V, int q, float2* W, cu
   const double N = AM.rows, nnz = AM.nnz;
   ProfScope ps(st, P_AUGMENT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 16.0 * N * q, 4.0 * nnz * q);
   AMGEIG_DISPATCH(g.cpt, k_dual_spmm_df,
-                  <<<blocks, kThreads, 0, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, V, q, W, g.G))
+                  <<<blocks, g.threads(), 0, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, V, q, W, g.G))
 }
 
 void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool accumulate, cudaStream_t st,
@@ -628,7 +640,7 @@ void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool
                4.0 * (S.rows + 1) + 12.0 * S.nnz + 8.0 * S.cols * width + 8.0 * S.rows * width * (accumulate ? 2 : 1),
                2.0 * S.nnz * width);
   AMGEIG_DISPATCH(g.cpt, k_spmm_df,
-                  <<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.d2, X, width, Y, g.G, accumulate ? 1 : 0))
+                  <<<blocks, g.threads(), 0, st>>>(S.rows, S.rp, S.ci, S.d2, X, width, Y, g.G, accumulate ? 1 : 0))
 }
 
 void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, const float2* pv, const float2* Xc,
@@ -641,8 +653,12 @@ void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, con
     k_recombine_pc<8><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
   else if (q <= 16)
     k_recombine_pc<16><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+  else if (q <= 20)
+    k_recombine_pc<20><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
   else if (q <= 24)
     k_recombine_pc<24><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+  else if (q <= 28)
+    k_recombine_pc<28><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
   else
     k_recombine_pc<32><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
 }
@@ -659,6 +675,8 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
       k_recombine_rows<16><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
     else if (q <= 24)
       k_recombine_rows<24><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    else if (q <= 28)
+      k_recombine_rows<28><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
     else
       k_recombine_rows<32><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
     return;
@@ -672,7 +690,7 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
   case C:                                                                                           \
     if (sm > 48 * 1024)                                                                             \
       cudaFuncSetAttribute(k_recombine_df2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    k_recombine_df2<C><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U, g.G);                      \
+    k_recombine_df2<C><<<blocks, g.threads(), sm, st>>>(rows, Xp, V, Y, q, U, g.G);                      \
     break;
     AMGEIG_CASE(1)
     AMGEIG_CASE(2)
