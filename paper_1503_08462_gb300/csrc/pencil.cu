@@ -87,6 +87,19 @@ __device__ __forceinline__ int sturm_count(const float* sd, const float* se2, in
   return cnt;
 }
 
+// The same count in float-float; ee2 holds e_i^2.  The reciprocal of the
+// previous pivot replaces the division (one Newton step on the float32 rcp).
+__device__ __forceinline__ int sturm_count_df(const df* dd, const df* ee2, int n, df x, float pivmin) {
+  df qv = df_sub(dd[0], x);
+  int cnt = df_lt0(qv);
+  for (int i = 1; i < n; ++i) {
+    if (fabsf(qv.hi) < pivmin) qv = df{-pivmin, 0.f};
+    qv = df_sub(df_sub(dd[i], x), df_mul(ee2[i - 1], df_recip(qv)));
+    cnt += df_lt0(qv);
+  }
+  return cnt;
+}
+
 // ------------------------------------------------------------ float-float syev
 //
 // Dynamic shared memory: v, p (df, n each), sd, se2 (float, n each), shift
@@ -115,7 +128,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   int* cstart = reinterpret_cast<int*>(shift + nwant);
   int* cpos = cstart + nwant;
   size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
-                3 * sizeof(df) * n + 15) &
+                4 * sizeof(df) * n + sizeof(df) * nwant + 15) &
                ~static_cast<size_t>(15);
   df* W = Wg;
   if (flags & kSyW) {
@@ -139,6 +152,8 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   df* dd = reinterpret_cast<df*>(cpos + nwant);
   df* ee = dd + n;
   df* tau = ee + n;
+  df* ee2 = tau + n;     // e_i^2 in float-float (Sturm counts)
+  df* shd = ee2 + n;     // float-float shifts (nwant)
   __shared__ df_acc red_sig[32], red_vp[32];
 
   for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
@@ -310,25 +325,73 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     }
     shift[j] = 0.5f * (lo + hi);
   }
+  for (int i = tid; i + 1 < n; i += nt) ee2[i] = df_mul(ee[i], ee[i]);
   __syncthreads();
-  // clusters of nearly equal shifts are iterated in rounds with Gram-Schmidt
+  // Refine each shift with float-float Sturm counts.  The float32 counts can be
+  // off by ~n 2^-24 ||T||, far more than the gaps inside a graded spectrum; with
+  // float-float shifts the inverse iteration below separates eigenvalues down to
+  // ~1e-9 ||T|| apart on its own.  One warp per eigenvalue: the bracket is first
+  // widened until its float-float counts enclose index j, then 32-point
+  // multisection shrinks it 33x per round (Golub & Van Loan 8.4.1).
+  for (int j = warp; j < nwant; j += nw) {
+    const float s0 = shift[j];
+    float w = 1.0e-4f * tnorm + 1.0e-6f * fabsf(s0) + pivmin;
+    df lo = df{s0 - w, 0.f}, hi = df{s0 + w, 0.f};
+    for (int attempt = 0; attempt < 12; ++attempt) {
+      int c = 0;
+      if (lane < 2) c = sturm_count_df(dd, ee2, n, lane == 0 ? lo : hi, pivmin);
+      const int clo = __shfl_sync(0xffffffffu, c, 0), chi = __shfl_sync(0xffffffffu, c, 1);
+      if (clo <= j && chi > j) break;
+      w *= 4.f;
+      if (attempt == 11) {
+        lo = df{gl, 0.f};
+        hi = df{gu, 0.f};
+      } else {
+        if (clo > j) lo = df{s0 - w, 0.f};
+        if (chi <= j) hi = df{s0 + w, 0.f};
+      }
+    }
+    const float tol = 1.0e-14f * tnorm + pivmin;
+    for (int round = 0; round < 12; ++round) {
+      const df width = df_sub(hi, lo);
+      if (!(width.hi > tol)) break;
+      const df x = df_add(lo, df_mul_f(width, static_cast<float>(lane + 1) * (1.f / 33.f)));
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_df(dd, ee2, n, x, pivmin) > j);
+      const int l1 = above ? __ffs(above) - 1 : 32;  // first point with more than j eigenvalues below
+      const float lhi = __shfl_sync(0xffffffffu, x.hi, l1 > 0 ? l1 - 1 : 0);
+      const float llo = __shfl_sync(0xffffffffu, x.lo, l1 > 0 ? l1 - 1 : 0);
+      const float hhi = __shfl_sync(0xffffffffu, x.hi, l1 < 32 ? l1 : 31);
+      const float hlo = __shfl_sync(0xffffffffu, x.lo, l1 < 32 ? l1 : 31);
+      if (l1 > 0) lo = df{lhi, llo};
+      if (l1 < 32) hi = df{hhi, hlo};
+    }
+    if (lane == 0) shd[j] = df_mul_f(df_add(lo, hi), 0.5f);
+  }
+  __syncthreads();
+  // Clusters of shifts closer than 1e-9 ||T|| are iterated in rounds with
+  // Gram-Schmidt; any pair closer than 1e-4 ||T|| sends the block through the
+  // Rayleigh-Ritz clean-up below (orthogonality to working accuracy).
   if (tid == 0) {
-    const float ctol = 1.0e-4f * tnorm;
-    int maxpos = 0;
+    const float ctol = 1.0e-9f * tnorm + pivmin, rtol = 1.0e-4f * tnorm;
+    int maxpos = 0, close = 0;
     for (int j = 0; j < nwant; ++j) {
-      if (j > 0 && shift[j] - shift[j - 1] <= ctol) {
+      const float gap = j > 0 ? df_float(df_sub(shd[j], shd[j - 1])) : 3.0e38f;
+      if (gap <= ctol) {
         cstart[j] = cstart[j - 1];
         cpos[j] = cpos[j - 1] + 1;
       } else {
         cstart[j] = j;
         cpos[j] = 0;
       }
+      if (gap <= rtol) close = 1;
       maxpos = max(maxpos, cpos[j]);
     }
     si[0] = maxpos;
+    si[1] = close;
   }
   __syncthreads();
   const int maxpos = si[0];
+  const bool cleanup = si[1] != 0;
 
   // ---- inverse iteration in float-float: T - s I = L D L^T -----------------
   // factor arrays (element i of eigen-index j at [i * nwant + j]):
@@ -338,7 +401,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   for (int round = 0; round <= maxpos; ++round) {
     for (int j = tid; j < nwant; j += nt) {
       if (cpos[j] != round) continue;
-      const df sg = df{shift[j], 0.f};
+      const df sg = shd[j];
       df* dinv = fac;
       df* lm = fac + N * NW;
       df d = df_sub(dd[0], sg);
@@ -394,10 +457,10 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   }
 
   df* Zn = fac;
-  if (maxpos == 0) {
-    // no two shifts within the cluster tolerance: the vectors are accurate
-    // individually (error ~ 48-bit rounding x ||T|| / gap <= 4e-11); their
-    // Rayleigh quotients are the eigenvalues, already in ascending order
+  if (!cleanup) {
+    // every gap is above 1e-4 ||T||: the vectors are accurate individually
+    // (error ~ 48-bit rounding x ||T|| / gap <= 4e-11); their Rayleigh
+    // quotients are the eigenvalues, already in ascending order
     for (long long idx = tid; idx < N * NW; idx += nt) Zn[idx] = Zt[idx];
     for (int j = tid; j < nwant; j += nt) {
       df_acc h = acc_zero();
@@ -1986,7 +2049,7 @@ __global__ void k_scale_cols_inv(int rows, int cols, const double* __restrict__ 
 
 size_t syev_smem_base(int n, int nwant) {
   return (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
-          3 * sizeof(df) * n + 15) &
+          4 * sizeof(df) * n + sizeof(df) * nwant + 15) &
          ~static_cast<size_t>(15);
 }
 
