@@ -543,7 +543,6 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
       launch_spmm_f64(h->R[l], cur, 2 * q, w->WC[l + 1], false, st, P_CHAIN);
       cur = w->WC[l + 1];
     }
-    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
     launch_pencil_solve(w->pw, h->dn, modes, q, cur, nullptr, w->G, h->Zdf, h->theta, w->mu, w->Xc, nullptr, w->Yv,
                         h->dstatus, st, w->nfallback);
     // recombination: U = I_n^k Xc + V Y
@@ -563,7 +562,6 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
       launch_spmm_df(h->R[l], cur, 2 * q, as_df(w->WC[l + 1]), false, st, P_CHAIN);
       cur = as_df(w->WC[l + 1]);
     }
-    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
     launch_pencil_solve(w->pw, h->dn, modes, q, nullptr, cur, w->G, h->Zdf, h->theta, w->mu, w->Xc,
                         as_df(w->PX[n - 1]), w->Yv, h->dstatus, st, w->nfallback);
     if (q <= 32) {
@@ -644,6 +642,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
     k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
   }
   CK(cudaMemsetAsync(w->nfallback, 0, sizeof(int), st));
+  // the pencil kernels only ever set the status (Cholesky of the Gram Schur
+  // complement failed), so one clear per solve suffices and the nested phase
+  // runs without host round trips: its status is read with the first
+  // finest-level residual
+  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
   CK(cudaGetLastError());
   int corrections = 0;
   bool converged = false;
@@ -660,10 +663,6 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
       if (rc) return rc;
       rc = correction_tail(h, w, k, o, st);
       if (rc) return rc;
-      int stt = 0;
-      CK(cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (stt) return fail(stt, "augmented pencil: Gram Schur complement not positive definite");
       continue;
     }
     for (;;) {
