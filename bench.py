@@ -55,9 +55,13 @@ WORKLOADS = {
     "lshape_h512_q20": dict(builder="lshape_2d", kw=dict(m_half=512, seed=2), q=20, qe=8, cap=400, tol=1e-4,
                             modes=64),
     "square_h32_q4": dict(builder="square_2d", kw=dict(m=32, seed=1), q=4, qe=2, cap=50, tol=1e-9, modes=0),
-    "checker_h1024_q50": dict(builder="square_2d", kw=dict(m=1024, checker=4, seed=3), q=50, qe=6, cap=400,
+    # checkerboard: a dense low spectrum (q = 50 ends at a ratio lambda_50 / lambda_51 ~ 0.98), so the
+    # buffer has to be wide: 6 extra vectors did not converge in 60 corrections, 22 take 52
+    "checker_h1024_q50": dict(builder="square_2d", kw=dict(m=1024, checker=4, seed=3), q=50, qe=22, cap=400,
                               tol=1e-6, modes=112),
-    "cube_m128_q10": dict(builder="cube_3d", kw=dict(m=128, seed=4), q=10, qe=4, cap=400, tol=1e-6, modes=64),
+    # cube: q = 10 ends after the 11 pi^2 triple; 7 extra vectors reach past the 14 pi^2 sextet
+    # (41 -> 22 corrections against 4 extra)
+    "cube_m128_q10": dict(builder="cube_3d", kw=dict(m=128, seed=4), q=10, qe=7, cap=400, tol=1e-6, modes=64),
 }
 
 
