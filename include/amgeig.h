@@ -127,10 +127,13 @@ int amgeig_solve(amgeig_hierarchy h, int q, double tol, const amgeig_options* op
                  double* eigvecs, int eigvecs_on_device, amgeig_info* info, void* stream);
 
 /* Serving: queue a solve on h and return at once with *request_id.  The options
- * are copied.  Requests run on a library thread in arrival order; each keeps
- * its hierarchy and iterate block resident on the device, and a request is
- * admitted only when its workspace fits in free device memory (ENOMEM is
- * reported through amgeig_poll if it can never fit).  Errors: EINVAL. */
+ * are copied.  Four library threads take requests in arrival order, skipping
+ * one whose hierarchy is already solving: requests on different hierarchies run
+ * at the same time on their hierarchies' streams.  Each hierarchy keeps its
+ * iterate workspace resident (sized for the widest q + q_extra it has served).
+ * A request whose workspace does not fit in free device memory waits until a
+ * running request ends (ENOMEM is reported through amgeig_poll if it cannot fit
+ * with nothing else running).  Errors: EINVAL. */
 int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* opt, uint64_t* request_id);
 
 /* Poll a request.  *done = 0 while it is queued or running.  Once done, copies

@@ -278,7 +278,8 @@ struct amgeig_hierarchy_t {
 namespace {
 
 struct SolveWork {
-  int qt = 0;
+  int qcap = 0;  // column capacity: the buffers serve any solve with q + q_extra <= qcap
+  int qt = 0;    // columns of the current solve (every block's row stride)
   int ld32 = 0;  // row stride of the float32 V-cycle blocks: qt rounded up to a multiple of 4
   int precision = -1;
   int vcycles = 1;
@@ -297,6 +298,7 @@ struct SolveWork {
 
 int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, std::unique_ptr<SolveWork>& out) {
   auto w = std::make_unique<SolveWork>();
+  w->qcap = qt;
   w->qt = qt;
   w->ld32 = (qt + 3) & ~3;
   w->precision = precision;
@@ -351,10 +353,11 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->C, static_cast<size_t>(h->dn) * 2 * qt));
   CK(m.alloc(&w->G, static_cast<size_t>(qt) * 2 * qt));
   size_t gs = 0;
-  for (int l = 0; l < n; ++l) {
-    gs = std::max(gs, gram_scratch_doubles(static_cast<int>(h->sizes[l]), qt, 2 * qt));
-    gs = std::max(gs, gram_df_scratch_doubles(static_cast<int>(h->sizes[l]), qt, 2 * qt));
-  }
+  for (int l = 0; l < n; ++l)
+    for (int qq = 1; qq <= qt; ++qq) {  // any width up to the capacity (the chunking depends on it)
+      gs = std::max(gs, gram_scratch_doubles(static_cast<int>(h->sizes[l]), qq, 2 * qq));
+      gs = std::max(gs, gram_df_scratch_doubles(static_cast<int>(h->sizes[l]), qq, 2 * qq));
+    }
   CK(m.alloc(&w->gsc, gs));
   CK(m.alloc(&w->Xc, static_cast<size_t>(h->dn) * qt));
   CK(m.alloc(&w->Yv, static_cast<size_t>(qt) * qt));
@@ -365,6 +368,25 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   w->pw = pencil_work_create(h->dn, qt, &e);
   if (!w->pw) return fail(AMGEIG_ENOMEM, std::string("pencil workspace: ") + cudaGetErrorString(e));
   out = std::move(w);
+  return AMGEIG_OK;
+}
+
+// Keep a workspace that can hold qt columns: a smaller solve reuses the buffers
+// of a larger one (all layouts follow the current qt), so a stream of requests
+// with varying q on one hierarchy allocates only when its largest width grows.
+int ensure_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles) {
+  SolveWork* w = h->ws.get();
+  if (!w || w->qcap < qt || w->precision != precision || w->vcycles < vcycles) {
+    const bool same = w && w->precision == precision;
+    const int cap = same ? std::max(qt, w->qcap) : qt;
+    const int vc = same ? std::max(vcycles, w->vcycles) : vcycles;
+    h->ws.reset();
+    const int rc = make_workspace(h, cap, precision, vc, h->ws);
+    if (rc) return rc;
+    w = h->ws.get();
+  }
+  w->qt = qt;
+  w->ld32 = (qt + 3) & ~3;
   return AMGEIG_OK;
 }
 
@@ -626,11 +648,8 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   if (qt > 128) return fail(AMGEIG_EINVAL, "q + q_extra must be at most 128");
   int rc = check_options(o);
   if (rc) return rc;
-  if (!h->ws || h->ws->qt != qt || h->ws->precision != o.precision || h->ws->vcycles < o.v_cycles) {
-    h->ws.reset();
-    rc = make_workspace(h, qt, o.precision, std::max(1, o.v_cycles), h->ws);
-    if (rc) return rc;
-  }
+  rc = ensure_workspace(h, qt, o.precision, std::max(1, o.v_cycles));
+  if (rc) return rc;
   SolveWork* w = h->ws.get();
   // step 1: initial eigenpairs on level n1 = n (the coarsest)
   if (o.precision == AMGEIG_FP64)
@@ -768,33 +787,64 @@ struct Request {
   amgeig_info info{};
 };
 
+// Continuous batching over hierarchies: kWorkers library threads take queued
+// requests in arrival order, skipping one whose hierarchy is busy (a hierarchy
+// runs one solve at a time on its own stream, so requests on different
+// hierarchies overlap on the device).  A request whose workspace does not fit
+// in free device memory waits while others run and is admitted when one ends;
+// with nothing else running it is tried anyway (and fails with ENOMEM if it
+// cannot fit at all).
+constexpr int kWorkers = 4;
+
 struct Service {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<std::shared_ptr<Request>> queue;
   std::map<uint64_t, std::shared_ptr<Request>> table;
+  std::vector<amgeig_hierarchy_t*> busy;
   uint64_t next_id = 1;
-  std::thread worker;
-  bool running = false;
+  int running_solves = 0;
+  bool started = false;
 
   void start() {
-    if (running) return;
-    running = true;
-    worker = std::thread([this] { loop(); });
-    worker.detach();
+    if (started) return;
+    started = true;
+    for (int i = 0; i < kWorkers; ++i) std::thread([this] { loop(); }).detach();
   }
+
+  bool is_busy(amgeig_hierarchy_t* h) const { return std::find(busy.begin(), busy.end(), h) != busy.end(); }
+
+  // first admissible request (caller holds mu)
+  std::shared_ptr<Request> pick() {
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      const std::shared_ptr<Request> r = *it;
+      if (is_busy(r->h)) continue;
+      if (running_solves > 0 && !fits(r.get())) continue;
+      queue.erase(it);
+      return r;
+    }
+    return nullptr;
+  }
+
+  static bool fits(const Request* r);
 
   void loop() {
     for (;;) {
       std::shared_ptr<Request> r;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait(lk, [this] { return !queue.empty(); });
-        r = queue.front();
-        queue.pop_front();
+        cv.wait(lk, [&] { return (r = pick()) != nullptr; });
+        busy.push_back(r->h);
+        ++running_solves;
       }
       run(r);
-      r->h->pending--;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        busy.erase(std::find(busy.begin(), busy.end(), r->h));
+        --running_solves;
+        r->h->pending--;
+      }
+      cv.notify_all();
     }
   }
 
@@ -1096,11 +1146,8 @@ int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_o
   std::lock_guard<std::mutex> lk(h->mu);
   CK(cudaSetDevice(h->device));
   cudaStream_t st = h->stream;
-  if (!h->ws || h->ws->qt != width || h->ws->precision != o.precision) {
-    h->ws.reset();
-    rc = make_workspace(h, width, o.precision, 1, h->ws);
-    if (rc) return rc;
-  }
+  rc = ensure_workspace(h, width, o.precision, 1);
+  if (rc) return rc;
   SolveWork* w = h->ws.get();
   const long long cnt = h->sizes[level] * static_cast<long long>(width);
   if (level == h->nlev - 1) {
@@ -1180,33 +1227,36 @@ int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs
 
 namespace {
 
-void Service::run(const std::shared_ptr<Request>& r) {
+// device bytes a request's workspace needs beyond what its hierarchy already holds
+size_t workspace_bytes(const amgeig_hierarchy_t* h, int qt) {
+  size_t per = 0;
+  for (int l = 0; l < h->nlev; ++l) per += static_cast<size_t>(h->sizes[l]) * qt * 8 * 6;
+  return per + static_cast<size_t>(h->sizes[0]) * qt * 8 * 5;
+}
+
+bool Service::fits(const Request* r) {
   amgeig_hierarchy_t* h = r->h;
   const int qt = r->q + r->opt.q_extra;
-  // admission by free device memory: the request's workspace must fit
-  size_t need = 0;
   {
-    size_t per = 0;
-    for (int l = 0; l < h->nlev; ++l) per += static_cast<size_t>(h->sizes[l]) * qt * 8 * 6;
-    need = per + static_cast<size_t>(h->sizes[0]) * qt * 8 * 5;
+    // a direct solve on this hierarchy from another thread: not now
+    std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return false;
+    if (h->ws && h->ws->qcap >= qt && h->ws->precision == r->opt.precision) return true;
   }
-  int status = AMGEIG_OK;
-  {
-    std::lock_guard<std::mutex> lk(h->mu);
-    cudaSetDevice(h->device);
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    const bool have_ws = h->ws && h->ws->qt == qt && h->ws->precision == r->opt.precision;
-    if (!have_ws && need > fr && need > tot) status = AMGEIG_ENOMEM;
-  }
-  if (status == AMGEIG_OK) {
-    r->vals.assign(r->q, 0.0);
-    r->vecs.assign(static_cast<size_t>(h->sizes[0]) * r->q, 0.0);
-    status = amgeig_solve(h, r->q, r->tol, &r->opt, r->vals.data(), r->vecs.data(), 0, &r->info, nullptr);
-    if (status != AMGEIG_OK && status != AMGEIG_ENOCONV) {
-      r->vals.clear();
-      r->vecs.clear();
-    }
+  size_t fr = 0, tot = 0;
+  cudaSetDevice(h->device);
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return true;
+  return workspace_bytes(h, qt) <= fr;
+}
+
+void Service::run(const std::shared_ptr<Request>& r) {
+  amgeig_hierarchy_t* h = r->h;
+  r->vals.assign(r->q, 0.0);
+  r->vecs.assign(static_cast<size_t>(h->sizes[0]) * r->q, 0.0);
+  int status = amgeig_solve(h, r->q, r->tol, &r->opt, r->vals.data(), r->vecs.data(), 0, &r->info, nullptr);
+  if (status != AMGEIG_OK && status != AMGEIG_ENOCONV) {
+    r->vals.clear();
+    r->vecs.clear();
   }
   r->info.status = status;
   std::lock_guard<std::mutex> lk(mu);

@@ -2132,7 +2132,7 @@ void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* ev
     sm += zb;
   }
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
-  cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_df), sm);
   k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, w->W, w->tau, w->dd, w->ee, w->fac,
                                        w->Zt, w->rr, w->perm, skip);
 }
@@ -2158,7 +2158,7 @@ void launch_syev_df_into(int n, int nwant, const double* H, double* evals, doubl
     sm += zb;
   }
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
-  cudaFuncSetAttribute(k_syev_df, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_df), sm);
   k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, W, tau, dd, ee, fac, Zt, rr, perm,
                                        nullptr);
 }
@@ -2168,7 +2168,7 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
                          float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback) {
   const int n = m + q;
   auto smem_attr = [](const void* f, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    ensure_dynamic_smem(f, bytes);
   };
   const size_t kbs = sizeof(df) * dn;
   const size_t srs = sizeof(df) * (2.0 * m + 2.0 * m * q + 3.0 * q * q + 2.0 * q + 2.0 * n);

@@ -1,6 +1,7 @@
 // Launch counter and event-based per-class timing (see prof.cuh).
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -44,6 +45,18 @@ const char* kNames[P_COUNT] = {"defect", "smooth", "transfer", "coarse_solve", "
                                "gram", "pencil", "recombine", "other", "chain"};
 
 }  // namespace
+
+void ensure_dynamic_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::map<const void*, size_t> limit;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[func];
+  if (bytes <= cur) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) ==
+      cudaSuccess)
+    cur = bytes;
+}
 
 thread_local int g_depth = 0;  // nested scopes only count launches; the outermost one is timed
 

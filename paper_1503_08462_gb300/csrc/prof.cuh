@@ -26,6 +26,12 @@ enum ProfClass {
   P_COUNT
 };
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowering it: the limit is one per function for the whole process, so solves
+// running on several host threads must not shrink it under each other's
+// launches.  Sizes up to 48 KB need no attribute.
+void ensure_dynamic_smem(const void* func, size_t bytes);
+
 class ProfScope {
  public:
   ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels = 1);

@@ -780,7 +780,7 @@ void launch_recombine(int rows, const double* Xp, const double* V, const double*
 #define AMGEIG_CASE(C)                                                                            \
   case C:                                                                                         \
     if (sm > 48 * 1024)                                                                           \
-      cudaFuncSetAttribute(k_recombine_df<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_recombine_df<C>), sm);                    \
     k_recombine_df<C><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U, g.G);                     \
     break;
       AMGEIG_CASE(1)
@@ -798,7 +798,7 @@ void launch_recombine(int rows, const double* Xp, const double* V, const double*
 #define AMGEIG_CASE(C)                                                                         \
   case C:                                                                                      \
     if (sm > 48 * 1024)                                                                        \
-      cudaFuncSetAttribute(k_recombine<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_recombine<C>), sm);                    \
     k_recombine<C><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U, g.G);                     \
     break;
     AMGEIG_CASE(1)

@@ -689,7 +689,7 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
 #define AMGEIG_CASE(C)                                                                              \
   case C:                                                                                           \
     if (sm > 48 * 1024)                                                                             \
-      cudaFuncSetAttribute(k_recombine_df2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_recombine_df2<C>), sm);            \
     k_recombine_df2<C><<<blocks, g.threads(), sm, st>>>(rows, Xp, V, Y, q, U, g.G);                      \
     break;
     AMGEIG_CASE(1)

@@ -190,6 +190,47 @@ def test_submit_poll_matches_direct():
             ae.amgeig_poll(ids[0])
 
 
+def test_request_mix_matches_alone():
+    """Requests on three hierarchies, submitted together so that they run at the same
+    time on the library's workers, give the same bits as each solve run alone."""
+    import time
+
+    cases = [problem_and_blob("square", 32, 50, 1), problem_and_blob("lshape", 16, 60, 2),
+             problem_and_blob("checker", 32, 60, 3)]
+    hs = [ae.Hierarchy(blob) for _, blob, _ in cases]
+    try:
+        plan = [(i % 3, q, prec) for i, (q, prec) in
+                enumerate([(2, ae.AMGEIG_FP64), (5, ae.AMGEIG_MIXED_FP32), (3, ae.AMGEIG_MIXED_FP32),
+                           (4, ae.AMGEIG_FP64), (6, ae.AMGEIG_MIXED_FP32), (2, ae.AMGEIG_MIXED_FP32),
+                           (7, ae.AMGEIG_FP64), (3, ae.AMGEIG_FP64), (5, ae.AMGEIG_MIXED_FP32)])]
+
+        def opt(prec):
+            return ae.options(q_extra=2, max_corrections=40, precision=prec, v_cycles=2)
+
+        alone = [hs[k].solve(q, tol=1e-8, opt=opt(prec)) for k, q, prec in plan]
+        ids = [ae.amgeig_submit(hs[k].handle, q, 1e-8, opt(prec)) for k, q, prec in plan]
+        pending = dict(zip(ids, range(len(plan))))
+        t0 = time.time()
+        while pending:
+            for rid in list(pending):
+                j = pending[rid]
+                k, q, _ = plan[j]
+                vals = np.empty(q)
+                vecs = np.empty((cases[k][0].n, q))
+                done, code = ae.amgeig_poll(rid, vals, vecs)
+                if not done:
+                    continue
+                del pending[rid]
+                assert code == alone[j][3]
+                assert np.array_equal(vals, alone[j][0]), (j, vals, alone[j][0])
+                assert np.array_equal(vecs, alone[j][1]), j
+            assert time.time() - t0 < 300
+            time.sleep(0.005)
+    finally:
+        for h in hs:
+            h.close()
+
+
 def test_multiple_vcycles_match_oracle():
     p, blob, _ = problem_and_blob("square", 32, 50, 1)
     oh = O.read_blob(blob)
