@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -220,13 +221,147 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+STREAM_DOMAINS = ("square", "lshape", "checker")
+
+
+def stream_pool(n_problems, seed=5):
+    """Seeded pool of 2D P1 problems: domain uniform over square / L-shape /
+    checkerboard-kappa, N uniform in [10k, 500k] (realised through h)."""
+    from paper_1503_08462_gb300.inputs import hierarchy, meshes
+
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(n_problems):
+        dom = STREAM_DOMAINS[int(rng.integers(0, 3))]
+        target = float(rng.uniform(10_000, 500_000))
+        t0 = time.perf_counter()
+        if dom == "lshape":
+            p = meshes.lshape_2d(m_half=max(8, int(round(math.sqrt(target / 3.0)))), seed=100 + i)
+        elif dom == "checker":
+            p = meshes.square_2d(m=4 * max(2, int(round((math.sqrt(target) + 1) / 4))), checker=4, seed=100 + i)
+        else:
+            p = meshes.square_2d(m=int(round(math.sqrt(target))) + 1, seed=100 + i)
+        blob, h = hierarchy.problem_blob(p, coarse_cap=400)
+        log(f"[stream] problem {i}: {dom} N={p.n} levels={h.sizes} setup={time.perf_counter() - t0:.1f}s")
+        pool.append((dom, p.n, blob, h.sizes[-1]))
+    return pool
+
+
+def run_stream(args):
+    """Serving stream: requests with Poisson arrivals (seeded) over a pool of
+    device-resident hierarchies, q uniform in {1..32}, mixed path; requests
+    enter through amgeig_submit and leave through amgeig_poll (host buffers),
+    so the library's workers overlap requests on different hierarchies.  The
+    arrival rate is 0.7 x the service rate measured on a saturated burst."""
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1503_08462_gb300 import amgeig as ae
+
+    pool = stream_pool(args.pool)
+    hs = [ae.Hierarchy(blob, device=local) for _, _, blob, _ in pool]
+    q_extra, tol = 4, 1e-6
+
+    def opt_for(k):
+        return ae.options(q_extra=q_extra, max_corrections=60, precision=ae.AMGEIG_MIXED_FP32, v_cycles=2,
+                          coarse_modes=min(64, pool[k][3]))
+
+    def run_batch(reqs, arrivals=None):
+        """Submit (at the given arrival times, else all at once) and poll to completion;
+        returns per-request (arrival, done) times, statuses and the wall span."""
+        n = len(reqs)
+        t_arr = np.zeros(n)
+        t_done = np.full(n, np.nan)
+        codes = [None] * n
+        outs = [(np.empty(q), np.empty((pool[k][1], q))) for k, q in reqs]
+        ids = {}
+        nxt = 0
+        t0 = time.perf_counter()
+        while nxt < n or ids:
+            now = time.perf_counter() - t0
+            while nxt < n and (arrivals is None or arrivals[nxt] <= now):
+                k, q = reqs[nxt]
+                t_arr[nxt] = arrivals[nxt] if arrivals is not None else now
+                ids[ae.amgeig_submit(hs[k].handle, q, tol, opt_for(k))] = nxt
+                nxt += 1
+            for rid in list(ids):
+                j = ids[rid]
+                done, code = ae.amgeig_poll(rid, outs[j][0], outs[j][1])
+                if done:
+                    t_done[j] = time.perf_counter() - t0
+                    codes[j] = code
+                    del ids[rid]
+            time.sleep(0.0002)
+        return t_arr, t_done, codes, float(np.nanmax(t_done))
+
+    rng = np.random.default_rng(5)
+    # warm-up: every problem once at the widest q (sizes its resident workspace)
+    run_batch([(k, 32) for k in range(len(pool))])
+    # service rate: a saturated burst
+    burst = [(int(rng.integers(0, len(pool))), int(rng.integers(1, 33))) for _ in range(4 * len(pool))]
+    _, _, _, span = run_batch(burst)
+    mu = len(burst) / span
+    lam = 0.7 * mu
+    reqs = [(int(rng.integers(0, len(pool))), int(rng.integers(1, 33))) for _ in range(args.requests)]
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, args.requests))
+    torch.cuda.synchronize()
+    launches0 = ae.amgeig_kernel_launches()
+    with ClockSampler(local) as clk:
+        t_arr, t_done, codes, span = run_batch(reqs, arrivals)
+    launches = ae.amgeig_kernel_launches() - launches0
+    lat_ms = (t_done - t_arr) * 1e3
+    pairs = sum(q for _, q in reqs)
+    span = replica_max(dist, span, f"cuda:{local}")
+    if rank == 0:
+        line = {
+            "metric": "eigenpairs/s", "value": world * pairs / span, "unit": "eigenpairs/s", "n_gpus": world,
+            "steps": args.requests, "warmup": len(pool) + len(burst), "ms_per_step": span * 1e3 / args.requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": "stream", "requests": args.requests, "q": "uniform 1..32", "q_extra": q_extra,
+                       "tol_relres": tol, "pool": [{"domain": d, "N": n} for d, n, _, _ in pool],
+                       "service_rate_req_s": mu, "arrival_rate_req_s": lam, "workers": 4,
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                           "mean": float(np.mean(lat_ms)), "max": float(np.max(lat_ms))},
+            "requests_per_s": args.requests / span,
+            "statuses": {str(c): codes.count(c) for c in set(codes)},
+            "not_ok": [{"domain": pool[k][0], "N": pool[k][1], "q": q, "status": c}
+                       for (k, q), c in zip(reqs, codes) if c != 0][:40],
+            "e2e": {"value": world * pairs / span, "unit": "eigenpairs/s",
+                    "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(np.mean([8 * q + 8 * pool[k][1] * q for k, q in reqs]))},
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    for h in hs:
+        h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lshape_h512_q20", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lshape_h512_q20", choices=sorted(WORKLOADS) + ["stream"],
+                    help="one problem solved per step, or 'stream': Poisson-arriving requests through "
+                         "amgeig_submit / amgeig_poll over a pool of problems (throughput and p50/p99 latency)")
+    ap.add_argument("--requests", type=int, default=200, help="stream: requests in the timed stream")
+    ap.add_argument("--pool", type=int, default=6, help="stream: distinct problems the requests draw from")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-corrections", type=int, default=10,
@@ -245,7 +380,15 @@ def main():
         oracle_child(args)
         return
     if args.impl == "reference":
+        if args.workload == "stream":
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is a per-problem solve; "
+                                  "the request stream has no CPU counterpart"}), flush=True)
+            return
         run_reference(args)
+        return
+    if args.workload == "stream":
+        run_stream(args)
         return
 
     import torch
