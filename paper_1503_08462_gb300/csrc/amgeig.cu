@@ -153,15 +153,43 @@ bool csr_valid(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, i
   return true;
 }
 
+// Host threads for the load-time loops over rows: one per 64k rows, at most 16.
+int host_threads(int64_t rows) {
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int64_t want = rows / 65536 + 1;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({want, 16, hc ? static_cast<int64_t>(hc) : 1})));
+}
+
+// f(t) for t in [0, T) on T threads (the calling thread runs t = 0)
+template <class F>
+void parallel_for(int T, F f) {
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back([&f, t] { f(t); });
+  f(0);
+  for (auto& x : th) x.join();
+}
+
 int parse_blob(const void* blob, size_t bytes, std::vector<HostCsr>& levels, std::vector<HostCsr>& prolong) {
   const uint8_t* b = static_cast<const uint8_t*>(blob);
   if (bytes < 24 || bytes % 8 != 0 || std::memcmp(b, "AMGEIGH1", 8) != 0)
     return fail(AMGEIG_ECORRUPT, "not a hierarchy blob (magic/length)");
   uint64_t sum = 0, stored;
-  for (size_t i = 0; i + 8 < bytes; i += 8) {
-    uint64_t w;
-    std::memcpy(&w, b + i, 8);
-    sum += w;
+  {
+    // word sum (mod 2^64) of everything before the stored checksum, in slices
+    const size_t words = (bytes - 8) / 8;
+    const int T = host_threads(static_cast<int64_t>(words / 64));
+    std::vector<uint64_t> part(T, 0);
+    parallel_for(T, [&](int t) {
+      const size_t lo = words * t / T, hi = words * (t + 1) / T;
+      uint64_t acc = 0;
+      for (size_t i = lo; i < hi; ++i) {
+        uint64_t w;
+        std::memcpy(&w, b + 8 * i, 8);
+        acc += w;
+      }
+      part[t] = acc;
+    });
+    for (uint64_t x : part) sum += x;
   }
   std::memcpy(&stored, b + bytes - 8, 8);
   if (sum != stored) return fail(AMGEIG_ECORRUPT, "hierarchy blob checksum mismatch");
@@ -973,46 +1001,66 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   h->PC.resize(n > 1 ? n - 1 : 0);
   {
     HostCsr next;
-    std::vector<double> acc(static_cast<size_t>(h->dn), 0.0);
-    std::vector<int32_t> mark(static_cast<size_t>(h->dn), -1), cols;
     for (int k = n - 2; k >= 0; --k) {
       const HostCsr& Pk = prolong[k];
       HostCsr C;
       C.rows = Pk.rows;
       C.cols = h->dn;
       C.rp.assign(static_cast<size_t>(Pk.rows) + 1, 0);
-      for (int64_t i = 0; i < Pk.rows; ++i) {
-        cols.clear();
-        for (int32_t p = Pk.rp[i]; p < Pk.rp[i + 1]; ++p) {
-          const int32_t t = Pk.ci[p];
-          const double v = Pk.a[p];
-          if (k == n - 2) {
-            if (mark[t] != static_cast<int32_t>(i)) {
-              mark[t] = static_cast<int32_t>(i);
-              acc[t] = 0.0;
-              cols.push_back(t);
+      // rows in contiguous slices, one per host thread, then concatenated in order
+      const int T = host_threads(Pk.rows);
+      std::vector<std::vector<int32_t>> pci(T), pcnt(T);
+      std::vector<std::vector<double>> pa(T);
+      parallel_for(T, [&](int t) {
+        const int64_t lo = Pk.rows * t / T, hi = Pk.rows * (t + 1) / T;
+        std::vector<double> acc(static_cast<size_t>(h->dn), 0.0);
+        std::vector<int32_t> mark(static_cast<size_t>(h->dn), -1), cols;
+        pcnt[t].resize(static_cast<size_t>(hi - lo));
+        for (int64_t i = lo; i < hi; ++i) {
+          cols.clear();
+          for (int32_t p = Pk.rp[i]; p < Pk.rp[i + 1]; ++p) {
+            const int32_t tc = Pk.ci[p];
+            const double v = Pk.a[p];
+            if (k == n - 2) {
+              if (mark[tc] != static_cast<int32_t>(i)) {
+                mark[tc] = static_cast<int32_t>(i);
+                acc[tc] = 0.0;
+                cols.push_back(tc);
+              }
+              acc[tc] += v;
+              continue;
             }
-            acc[t] += v;
-            continue;
-          }
-          for (int32_t r = next.rp[t]; r < next.rp[t + 1]; ++r) {
-            const int32_t c = next.ci[r];
-            if (mark[c] != static_cast<int32_t>(i)) {
-              mark[c] = static_cast<int32_t>(i);
-              acc[c] = 0.0;
-              cols.push_back(c);
+            for (int32_t r = next.rp[tc]; r < next.rp[tc + 1]; ++r) {
+              const int32_t c = next.ci[r];
+              if (mark[c] != static_cast<int32_t>(i)) {
+                mark[c] = static_cast<int32_t>(i);
+                acc[c] = 0.0;
+                cols.push_back(c);
+              }
+              acc[c] += v * next.a[r];
             }
-            acc[c] += v * next.a[r];
           }
+          std::sort(cols.begin(), cols.end());
+          for (int32_t c : cols) {
+            pci[t].push_back(c);
+            pa[t].push_back(acc[c]);
+          }
+          pcnt[t][static_cast<size_t>(i - lo)] = static_cast<int32_t>(cols.size());
         }
-        std::sort(cols.begin(), cols.end());
-        for (int32_t c : cols) {
-          C.ci.push_back(c);
-          C.a.push_back(acc[c]);
+      });
+      size_t total = 0;
+      for (int t = 0; t < T; ++t) total += pci[t].size();
+      C.ci.reserve(total);
+      C.a.reserve(total);
+      int64_t row = 0;
+      for (int t = 0; t < T; ++t) {
+        for (int32_t c : pcnt[t]) {
+          C.rp[static_cast<size_t>(row) + 1] = C.rp[static_cast<size_t>(row)] + c;
+          ++row;
         }
-        C.rp[static_cast<size_t>(i) + 1] = static_cast<int32_t>(C.ci.size());
+        C.ci.insert(C.ci.end(), pci[t].begin(), pci[t].end());
+        C.a.insert(C.a.end(), pa[t].begin(), pa[t].end());
       }
-      std::fill(mark.begin(), mark.end(), -1);
       DevCsr& D = h->PC[k];
       D.rows = static_cast<int>(C.rows);
       D.cols = static_cast<int>(C.cols);

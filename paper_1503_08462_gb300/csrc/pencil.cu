@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   int* cstart = reinterpret_cast<int*>(shift + nwant);
   int* cpos = cstart + nwant;
   size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
-                4 * sizeof(df) * n + sizeof(df) * nwant + 15) &
+                4 * sizeof(df) * n + sizeof(df) * nwant + 2 * sizeof(int) * nwant + 15) &
                ~static_cast<size_t>(15);
   df* W = Wg;
   if (flags & kSyW) {
@@ -154,6 +154,8 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   df* tau = ee + n;
   df* ee2 = tau + n;     // e_i^2 in float-float (Sturm counts)
   df* shd = ee2 + n;     // float-float shifts (nwant)
+  int* gs0 = reinterpret_cast<int*>(shd + nwant);  // clean-up group [gs0[j], gs1[j]) of index j
+  int* gs1 = gs0 + nwant;
   __shared__ df_acc red_sig[32], red_vp[32];
 
   for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   // Rayleigh-Ritz clean-up below (orthogonality to working accuracy).
   if (tid == 0) {
     const float ctol = 1.0e-9f * tnorm + pivmin, rtol = 1.0e-4f * tnorm;
-    int maxpos = 0, close = 0;
+    int maxpos = 0, close = 0, gstart = 0;
     for (int j = 0; j < nwant; ++j) {
       const float gap = j > 0 ? df_float(df_sub(shd[j], shd[j - 1])) : 3.0e38f;
       if (gap <= ctol) {
@@ -383,9 +385,16 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
         cstart[j] = j;
         cpos[j] = 0;
       }
-      if (gap <= rtol) close = 1;
+      if (gap <= rtol) {
+        close = 1;
+      } else if (j > 0) {
+        for (int i = gstart; i < j; ++i) gs1[i] = j;
+        gstart = j;
+      }
+      gs0[j] = gstart;
       maxpos = max(maxpos, cpos[j]);
     }
+    for (int i = gstart; i < nwant; ++i) gs1[i] = nwant;
     si[0] = maxpos;
     si[1] = close;
   }
@@ -475,216 +484,260 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     }
     __syncthreads();
   } else {
-    // ---- Rayleigh-Ritz clean-up on span(Zt): S = Z^T Z, Hq = Z^T T Z ---------
-    df* S = rrw;
-    df* Hq = rrw + NW * NW;
-    df* Qm = rrw + 2 * NW * NW;
-    df* Xm = rrw + 3 * NW * NW;
-    for (int idx = tid; idx < nwant * nwant; idx += nt) {
-      const int a0 = idx / nwant, b0 = idx % nwant;
-      if (b0 < a0) continue;
-      df_acc s = acc_zero(), h = acc_zero();
-      for (int i = 0; i < n; ++i) {
-        const df za = Zt[i * NW + a0];
-        const df zb = Zt[i * NW + b0];
-        s.fma(za, zb);
-        df_acc tz = acc_zero();
-        tz.fma(dd[i], zb);
-        if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + b0]);
-        if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + b0]);
-        h.fma(za, tz.value());
-      }
-      S[a0 * NW + b0] = S[b0 * NW + a0] = s.value();
-      Hq[a0 * NW + b0] = Hq[b0 * NW + a0] = h.value();
-    }
-    __syncthreads();
-    // Cholesky S = L L^T in place (lower), right-looking
-    for (int kk = 0; kk < nwant; ++kk) {
-      if (tid == 0) S[kk * NW + kk] = df_sqrt(S[kk * NW + kk]);
-      __syncthreads();
-      const df piv = S[kk * NW + kk];
-      for (int i = kk + 1 + tid; i < nwant; i += nt) S[i * NW + kk] = df_div(S[i * NW + kk], piv);
-      __syncthreads();
-      for (int idx = tid; idx < (nwant - kk - 1) * (nwant - kk - 1); idx += nt) {
-        const int i = kk + 1 + idx / (nwant - kk - 1), jj = kk + 1 + idx % (nwant - kk - 1);
-        if (jj <= i) S[i * NW + jj] = df_sub(S[i * NW + jj], df_mul(S[i * NW + kk], S[jj * NW + kk]));
-      }
-      __syncthreads();
-    }
-    // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int col = tid; col < nwant; col += nt) {
-        for (int i = 0; i < nwant; ++i) {
-          df s = (pass == 0) ? Hq[i * NW + col] : Xm[col * NW + i];
-          for (int kk = 0; kk < i; ++kk)
-            s = df_sub(s, df_mul(S[i * NW + kk], (pass == 0) ? Xm[kk * NW + col] : Qm[kk * NW + col]));
-          const df r = df_div(s, S[i * NW + i]);
-          if (pass == 0) Xm[i * NW + col] = r; else Qm[i * NW + col] = r;
-        }
-      }
-      __syncthreads();
-    }
-    // Qm now holds C (symmetric); move it to Hq and set Qm = I
-    for (int idx = tid; idx < nwant * nwant; idx += nt) {
-      const int a0 = idx / nwant, b0 = idx % nwant;
-      const df cab = Qm[a0 * NW + b0], cba = Qm[b0 * NW + a0];
-      Hq[idx] = df_mul_f(df_add(cab, cba), 0.5f);
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nwant * nwant; idx += nt) Qm[idx] = df{(idx / nwant == idx % nwant) ? 1.f : 0.f, 0.f};
-    __syncthreads();
-    // parallel cyclic Jacobi (round-robin pairing) on C, accumulating Q
-    {
-      const int np = (nwant + 1) & ~1;  // even player count; index nwant is a dummy
-      for (int sweep = 0; sweep < 12; ++sweep) {
-        // convergence test: largest off-diagonal entry against the largest diagonal one
-        float off = 0.f, dia = 0.f;
-        for (int idx = tid; idx < nwant * nwant; idx += nt) {
-          const int a0 = idx / nwant, b0 = idx % nwant;
-          const float x = fabsf(Hq[idx].hi);
-          if (a0 == b0) dia = fmaxf(dia, x); else off = fmaxf(off, x);
-        }
-  #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
-          dia = fmaxf(dia, __shfl_xor_sync(0xffffffffu, dia, o));
-        }
-        if (lane == 0) {
-          red[warp].s = off;
-          red[warp].c = dia;
-        }
-        __syncthreads();
-        if (tid == 0) {
-          float o2 = 0.f, d2 = 0.f;
-          for (int w2 = 0; w2 < nw; ++w2) {
-            o2 = fmaxf(o2, red[w2].s);
-            d2 = fmaxf(d2, red[w2].c);
-          }
-          sf[0] = o2;
-          sf[1] = d2;
-        }
-        __syncthreads();
-        const float offmax = sf[0], diamax = sf[1];
-        __syncthreads();
-        if (!(offmax > 1.0e-15f * fmaxf(diamax, 1.0e-30f))) break;
-        for (int r = 0; r < np - 1; ++r) {
-          // pair t: players (a, b) of the round-robin schedule
-          for (int t = tid; t < np / 2; t += nt) {
-            int a0 = (t == 0) ? 0 : 1 + (t - 1 + r) % (np - 1);
-            int b0 = 1 + (np - 2 - t + r) % (np - 1);
-            if (a0 > b0) {
-              const int tmpi = a0;
-              a0 = b0;
-              b0 = tmpi;
-            }
-            df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
-            if (b0 < nwant) {
-              const df apq = Hq[a0 * NW + b0];
-              const df app = Hq[a0 * NW + a0], aqq = Hq[b0 * NW + b0];
-              // skip entries already below the float-float resolution of the diagonal
-              const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
-              if (fabsf(apq.hi) > thr) {
-                // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
-                // and t = 1 / (2 theta) once theta^2 would leave the float range
-                const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
-                df tt;
-                if (fabsf(th.hi) > 1.0e12f) {
-                  tt = df_div(df{0.5f, 0.f}, th);
-                } else {
-                  const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
-                  tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
-                  if (df_lt0(th)) tt = df_neg(tt);
-                }
-                cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
-                sn = df_mul(tt, cs);
-              }
-            }
-            // stash rotation in Xm row 0..np/2 (cols 0..3)
-            Xm[t * 4 + 0] = cs;
-            Xm[t * 4 + 1] = sn;
-            reinterpret_cast<int*>(&Xm[t * 4 + 2])[0] = a0;
-            reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
-          }
-          __syncthreads();
-          // rows: C <- J^T C
-          for (int idx = tid; idx < (np / 2) * nwant; idx += nt) {
-            const int t = idx / nwant, col = idx % nwant;
-            const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-            const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-            if (b0 >= nwant) continue;
-            const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-            const df x = Hq[a0 * NW + col], y = Hq[b0 * NW + col];
-            Hq[a0 * NW + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
-            Hq[b0 * NW + col] = df_add(df_mul(sn, x), df_mul(cs, y));
-          }
-          __syncthreads();
-          // columns: C <- C J, Q <- Q J
-          for (int idx = tid; idx < (np / 2) * nwant; idx += nt) {
-            const int t = idx / nwant, row = idx % nwant;
-            const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-            const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-            if (b0 >= nwant) continue;
-            const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-            df x = Hq[row * NW + a0], y = Hq[row * NW + b0];
-            Hq[row * NW + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-            Hq[row * NW + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-            x = Qm[row * NW + a0];
-            y = Qm[row * NW + b0];
-            Qm[row * NW + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-            Qm[row * NW + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-          }
-          __syncthreads();
-        }
-      }
-    }
-    // order eigenvalues ascending (selection by rank; ties broken by index)
+    // ---- Rayleigh-Ritz clean-up ---------------------------------------------
+    // Shifts closer than 1e-4 ||T|| form groups (runs of consecutive indices);
+    // groups are more than 1e-4 ||T|| apart, so each vector's error outside its
+    // own group's span is below ~4e-11 and a Rayleigh-Ritz step on each group's
+    // span (S = Z_g^T Z_g, Hq = Z_g^T T Z_g) restores working accuracy.  Single
+    // vectors only need their Rayleigh quotient; the groups of two or more run
+    // one after another on windows of the workspace.
     for (int j = tid; j < nwant; j += nt) {
-      const df lj = Hq[j * NW + j];
-      int rank = 0;
-      for (int i = 0; i < nwant; ++i) {
-        const df li = Hq[i * NW + i];
-        const df dlt = df_sub(li, lj);
-        if (df_lt0(dlt) || ((dlt.hi == 0.f && dlt.lo == 0.f) && i < j)) ++rank;
+      if (gs1[j] - gs0[j] != 1) continue;
+      df_acc sq = acc_zero(), hq = acc_zero();
+      for (int i = 0; i < n; ++i) {
+        const df z = Zt[i * NW + j];
+        df_acc tz = acc_zero();
+        tz.fma(dd[i], z);
+        if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + j]);
+        if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + j]);
+        sq.fma(z, z);
+        hq.fma(z, tz.value());
       }
-      perm[rank] = j;
+      const df sv = sq.value();
+      const df inv = df_div(df{1.f, 0.f}, df_sqrt(sv));
+      for (int i = 0; i < n; ++i) Zn[i * NW + j] = df_mul(Zt[i * NW + j], inv);
+      evals[j] = df_to_double(df_div(hq.value(), sv));
     }
     __syncthreads();
-    // Xm = L^-T Q  (back substitution per column)
-    for (int col = tid; col < nwant; col += nt) {
-      for (int i = nwant - 1; i >= 0; --i) {
-        df s = Qm[i * NW + col];
-        for (int kk = i + 1; kk < nwant; ++kk) s = df_sub(s, df_mul(S[kk * NW + i], Xm[kk * NW + col]));
-        Xm[i * NW + col] = df_div(s, S[i * NW + i]);
+    for (int g0 = 0; g0 < nwant;) {
+      const int g1 = gs1[g0], G = g1 - g0;
+      if (G < 2) {
+        g0 = g1;
+        continue;
       }
+      df* S = rrw;
+      df* Hq = rrw + G * G;
+      df* Qm = rrw + 2 * G * G;
+      df* Xm = rrw + 3 * G * G;
+      for (int idx = tid; idx < G * G; idx += nt) {
+        const int a0 = idx / G, b0 = idx % G;
+        if (b0 < a0) continue;
+        df_acc sa = acc_zero(), ha = acc_zero();
+        for (int i = 0; i < n; ++i) {
+          const df za = Zt[i * NW + g0 + a0];
+          const df zb = Zt[i * NW + g0 + b0];
+          sa.fma(za, zb);
+          df_acc tz = acc_zero();
+          tz.fma(dd[i], zb);
+          if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + g0 + b0]);
+          if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + g0 + b0]);
+          ha.fma(za, tz.value());
+        }
+        S[a0 * G + b0] = S[b0 * G + a0] = sa.value();
+        Hq[a0 * G + b0] = Hq[b0 * G + a0] = ha.value();
+      }
+      __syncthreads();
+      // Cholesky S = L L^T in place (lower), right-looking
+      for (int kk = 0; kk < G; ++kk) {
+        if (tid == 0) S[kk * G + kk] = df_sqrt(S[kk * G + kk]);
+        __syncthreads();
+        const df piv = S[kk * G + kk];
+        for (int i = kk + 1 + tid; i < G; i += nt) S[i * G + kk] = df_div(S[i * G + kk], piv);
+        __syncthreads();
+        for (int idx = tid; idx < (G - kk - 1) * (G - kk - 1); idx += nt) {
+          const int i = kk + 1 + idx / (G - kk - 1), jj = kk + 1 + idx % (G - kk - 1);
+          if (jj <= i) S[i * G + jj] = df_sub(S[i * G + jj], df_mul(S[i * G + kk], S[jj * G + kk]));
+        }
+        __syncthreads();
+      }
+      // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int col = tid; col < G; col += nt) {
+          for (int i = 0; i < G; ++i) {
+            df s = (pass == 0) ? Hq[i * G + col] : Xm[col * G + i];
+            for (int kk = 0; kk < i; ++kk)
+              s = df_sub(s, df_mul(S[i * G + kk], (pass == 0) ? Xm[kk * G + col] : Qm[kk * G + col]));
+            const df r = df_div(s, S[i * G + i]);
+            if (pass == 0) Xm[i * G + col] = r; else Qm[i * G + col] = r;
+          }
+        }
+        __syncthreads();
+      }
+      // Qm now holds C (symmetric); move it to Hq and set Qm = I
+      for (int idx = tid; idx < G * G; idx += nt) {
+        const int a0 = idx / G, b0 = idx % G;
+        const df cab = Qm[a0 * G + b0], cba = Qm[b0 * G + a0];
+        Hq[idx] = df_mul_f(df_add(cab, cba), 0.5f);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < G * G; idx += nt) Qm[idx] = df{(idx / G == idx % G) ? 1.f : 0.f, 0.f};
+      __syncthreads();
+      // parallel cyclic Jacobi (round-robin pairing) on C, accumulating Q
+      {
+        const int np = (G + 1) & ~1;  // even player count; index G is a dummy
+        for (int sweep = 0; sweep < 12; ++sweep) {
+          // convergence test: largest off-diagonal entry against the largest diagonal one
+          float off = 0.f, dia = 0.f;
+          for (int idx = tid; idx < G * G; idx += nt) {
+            const int a0 = idx / G, b0 = idx % G;
+            const float x = fabsf(Hq[idx].hi);
+            if (a0 == b0) dia = fmaxf(dia, x); else off = fmaxf(off, x);
+          }
+    #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+            dia = fmaxf(dia, __shfl_xor_sync(0xffffffffu, dia, o));
+          }
+          if (lane == 0) {
+            red[warp].s = off;
+            red[warp].c = dia;
+          }
+          __syncthreads();
+          if (tid == 0) {
+            float o2 = 0.f, d2 = 0.f;
+            for (int w2 = 0; w2 < nw; ++w2) {
+              o2 = fmaxf(o2, red[w2].s);
+              d2 = fmaxf(d2, red[w2].c);
+            }
+            sf[0] = o2;
+            sf[1] = d2;
+          }
+          __syncthreads();
+          const float offmax = sf[0], diamax = sf[1];
+          __syncthreads();
+          if (!(offmax > 1.0e-15f * fmaxf(diamax, 1.0e-30f))) break;
+          for (int r = 0; r < np - 1; ++r) {
+            // pair t: players (a, b) of the round-robin schedule
+            for (int t = tid; t < np / 2; t += nt) {
+              int a0 = (t == 0) ? 0 : 1 + (t - 1 + r) % (np - 1);
+              int b0 = 1 + (np - 2 - t + r) % (np - 1);
+              if (a0 > b0) {
+                const int tmpi = a0;
+                a0 = b0;
+                b0 = tmpi;
+              }
+              df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
+              if (b0 < G) {
+                const df apq = Hq[a0 * G + b0];
+                const df app = Hq[a0 * G + a0], aqq = Hq[b0 * G + b0];
+                // skip entries already below the float-float resolution of the diagonal
+                const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
+                if (fabsf(apq.hi) > thr) {
+                  // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
+                  // and t = 1 / (2 theta) once theta^2 would leave the float range
+                  const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
+                  df tt;
+                  if (fabsf(th.hi) > 1.0e12f) {
+                    tt = df_div(df{0.5f, 0.f}, th);
+                  } else {
+                    const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
+                    tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
+                    if (df_lt0(th)) tt = df_neg(tt);
+                  }
+                  cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
+                  sn = df_mul(tt, cs);
+                }
+              }
+              // stash rotation in Xm row 0..np/2 (cols 0..3)
+              Xm[t * 4 + 0] = cs;
+              Xm[t * 4 + 1] = sn;
+              reinterpret_cast<int*>(&Xm[t * 4 + 2])[0] = a0;
+              reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
+            }
+            __syncthreads();
+            // rows: C <- J^T C
+            for (int idx = tid; idx < (np / 2) * G; idx += nt) {
+              const int t = idx / G, col = idx % G;
+              const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
+              const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
+              if (b0 >= G) continue;
+              const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+              const df x = Hq[a0 * G + col], y = Hq[b0 * G + col];
+              Hq[a0 * G + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
+              Hq[b0 * G + col] = df_add(df_mul(sn, x), df_mul(cs, y));
+            }
+            __syncthreads();
+            // columns: C <- C J, Q <- Q J
+            for (int idx = tid; idx < (np / 2) * G; idx += nt) {
+              const int t = idx / G, row = idx % G;
+              const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
+              const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
+              if (b0 >= G) continue;
+              const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+              df x = Hq[row * G + a0], y = Hq[row * G + b0];
+              Hq[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+              Hq[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+              x = Qm[row * G + a0];
+              y = Qm[row * G + b0];
+              Qm[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+              Qm[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+            }
+            __syncthreads();
+          }
+        }
+      }
+      // order eigenvalues ascending (selection by rank; ties broken by index)
+      for (int j = tid; j < G; j += nt) {
+        const df lj = Hq[j * G + j];
+        int rank = 0;
+        for (int i = 0; i < G; ++i) {
+          const df li = Hq[i * G + i];
+          const df dlt = df_sub(li, lj);
+          if (df_lt0(dlt) || ((dlt.hi == 0.f && dlt.lo == 0.f) && i < j)) ++rank;
+        }
+        perm[rank] = j;
+      }
+      __syncthreads();
+      // Xm = L^-T Q  (back substitution per column)
+      for (int col = tid; col < G; col += nt) {
+        for (int i = G - 1; i >= 0; --i) {
+          df s = Qm[i * G + col];
+          for (int kk = i + 1; kk < G; ++kk) s = df_sub(s, df_mul(S[kk * G + i], Xm[kk * G + col]));
+          Xm[i * G + col] = df_div(s, S[i * G + i]);
+        }
+      }
+      __syncthreads();
+      // group eigenvectors Zn[:, g0 + c] = Z_g Xm[:, perm[c]] (ascending within the group)
+      for (long long idx = tid; idx < N * G; idx += nt) {
+        const int i = static_cast<int>(idx / G), c = static_cast<int>(idx % G);
+        const int src = perm[c];
+        df_acc sa = acc_zero();
+        for (int kk = 0; kk < G; ++kk) sa.fma(Zt[i * NW + g0 + kk], Xm[kk * G + src]);
+        Zn[i * NW + g0 + c] = sa.value();
+      }
+      for (int c = tid; c < G; c += nt) evals[g0 + c] = df_to_double(Hq[perm[c] * G + perm[c]]);
+      __syncthreads();
+      g0 = g1;
     }
-    __syncthreads();
-    // tridiagonal eigenvectors Zt <- Zt Xm, written in sorted order into Qm-free
-    // storage: reuse fac (no longer needed) as the new block
-    for (long long idx = tid; idx < N * NW; idx += nt) {
-      const int i = static_cast<int>(idx / NW), c = static_cast<int>(idx % NW);
-      const int src = perm[c];
-      df_acc s = acc_zero();
-      for (int kk = 0; kk < nwant; ++kk) s.fma(Zt[i * NW + kk], Xm[kk * NW + src]);
-      Zn[idx] = s.value();
-    }
-    __syncthreads();
-    for (int c = tid; c < nwant; c += nt) evals[c] = df_to_double(Hq[perm[c] * NW + perm[c]]);
   }
 
   // ---- back-transformation y = H_0 H_1 ... H_{n-3} z ------------------------
+  // v_k (column k of W below the diagonal) is staged in shared memory once per
+  // step; each thread then owns whole columns of Z, so its row walks are
+  // coalesced across the threads of a warp
   for (int k = n - 3; k >= 0; --k) {
     const df t = tau[k];
     if (t.hi == 0.f) continue;
     const int m = n - k - 1;
+    for (int i = tid; i < m; i += nt) v[i] = W[(k + 1 + i) * LD + k];
+    __syncthreads();
     // for each column c: s_c = v^T z[k+1:, c]; z[k+1:, c] -= t s_c v
-    for (int c = warp; c < nwant; c += nw) {
-      df_acc s = acc_zero();
-      for (int i = lane; i < m; i += 32) s.fma(W[(k + 1 + i) * LD + k], Zn[(k + 1 + i) * NW + c]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s.merge(shfl_xor_acc(s, o));
-      const df f = df_mul(t, s.value());
-      for (int i = lane; i < m; i += 32)
-        Zn[(k + 1 + i) * NW + c] = df_sub(Zn[(k + 1 + i) * NW + c], df_mul(f, W[(k + 1 + i) * LD + k]));
+    for (int c = tid; c < nwant; c += nt) {
+      df* zc = Zn + static_cast<long long>(k + 1) * NW + c;
+      df_acc s0 = acc_zero(), s1 = acc_zero(), s2 = acc_zero(), s3 = acc_zero();
+      int i = 0;
+      for (; i + 4 <= m; i += 4) {
+        s0.fma(v[i], zc[i * NW]);
+        s1.fma(v[i + 1], zc[(i + 1) * NW]);
+        s2.fma(v[i + 2], zc[(i + 2) * NW]);
+        s3.fma(v[i + 3], zc[(i + 3) * NW]);
+      }
+      for (; i < m; ++i) s0.fma(v[i], zc[i * NW]);
+      s0.merge(s1);
+      s2.merge(s3);
+      s0.merge(s2);
+      const df f = df_mul(t, s0.value());
+      for (i = 0; i < m; ++i) zc[i * NW] = df_sub(zc[i * NW], df_mul(f, v[i]));
     }
     __syncthreads();
   }
@@ -2049,7 +2102,7 @@ __global__ void k_scale_cols_inv(int rows, int cols, const double* __restrict__ 
 
 size_t syev_smem_base(int n, int nwant) {
   return (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
-          4 * sizeof(df) * n + sizeof(df) * nwant + 15) &
+          4 * sizeof(df) * n + sizeof(df) * nwant + 2 * sizeof(int) * nwant + 15) &
          ~static_cast<size_t>(15);
 }
 
