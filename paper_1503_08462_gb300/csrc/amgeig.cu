@@ -127,29 +127,49 @@ struct HostCsr {
   std::vector<double> a, m;
 };
 
+// A CSR matrix read in place from the hierarchy blob (no copies): the arrays
+// are 8-byte aligned inside the blob, which is 8-byte aligned itself (or copied
+// once to an aligned buffer).  m is null for transfer operators.
+struct CsrView {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  const int32_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* a = nullptr;
+  const double* m = nullptr;
+};
+
 struct Reader {
   const uint8_t* p;
   size_t n, off;
-  bool ok = true;
   template <typename T>
-  bool take(std::vector<T>& out, size_t count) {
+  bool view(const T** out, size_t count) {
     const size_t bytes = count * sizeof(T);
-    if (off + bytes > n - 8 || count > (n / sizeof(T))) return ok = false;
-    out.resize(count);
-    std::memcpy(out.data(), p + off, bytes);
+    if (count > (n / sizeof(T)) || off + bytes > n - 8) return false;
+    *out = reinterpret_cast<const T*>(p + off);
     off += bytes;
     off += (8 - off % 8) % 8;
     return true;
   }
 };
 
-bool csr_valid(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, int64_t rows, int64_t cols) {
-  if (static_cast<int64_t>(rp.size()) != rows + 1 || rp[0] != 0) return false;
-  for (int64_t i = 0; i < rows; ++i)
-    if (rp[i + 1] < rp[i]) return false;
-  if (static_cast<size_t>(rp[rows]) != ci.size()) return false;
-  for (int32_t c : ci)
-    if (c < 0 || c >= cols) return false;
+int host_threads(int64_t rows);
+template <class F>
+void parallel_for(int T, F f);
+
+bool csr_valid(const CsrView& v) {
+  if (v.rp[0] != 0 || v.rp[v.rows] != v.nnz) return false;
+  const int T = host_threads(std::max(v.rows, v.nnz));
+  std::vector<char> ok(T, 1);
+  parallel_for(T, [&](int t) {
+    const int64_t r0 = v.rows * t / T, r1 = v.rows * (t + 1) / T;
+    for (int64_t i = r0; i < r1; ++i)
+      if (v.rp[i + 1] < v.rp[i]) ok[t] = 0;
+    const int64_t p0 = v.nnz * t / T, p1 = v.nnz * (t + 1) / T;
+    for (int64_t q = p0; q < p1; ++q)
+      if (v.ci[q] < 0 || v.ci[q] >= v.cols) ok[t] = 0;
+  });
+  for (char c : ok)
+    if (!c) return false;
   return true;
 }
 
@@ -163,14 +183,22 @@ int host_threads(int64_t rows) {
 // f(t) for t in [0, T) on T threads (the calling thread runs t = 0)
 template <class F>
 void parallel_for(int T, F f) {
+  if (T <= 0) return;
   std::vector<std::thread> th;
   for (int t = 1; t < T; ++t) th.emplace_back([&f, t] { f(t); });
   f(0);
   for (auto& x : th) x.join();
 }
 
-int parse_blob(const void* blob, size_t bytes, std::vector<HostCsr>& levels, std::vector<HostCsr>& prolong) {
+int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std::vector<CsrView>& prolong,
+               std::vector<uint64_t>& aligned) {
   const uint8_t* b = static_cast<const uint8_t*>(blob);
+  if (reinterpret_cast<uintptr_t>(b) % 8 != 0) {
+    // the views need 8-byte alignment: one aligned copy of an unaligned blob
+    aligned.resize(bytes / 8 + 1);
+    std::memcpy(aligned.data(), b, bytes);
+    b = reinterpret_cast<const uint8_t*>(aligned.data());
+  }
   if (bytes < 24 || bytes % 8 != 0 || std::memcmp(b, "AMGEIGH1", 8) != 0)
     return fail(AMGEIG_ECORRUPT, "not a hierarchy blob (magic/length)");
   uint64_t sum = 0, stored;
@@ -212,37 +240,39 @@ int parse_blob(const void* blob, size_t bytes, std::vector<HostCsr>& levels, std
     if (l > 0 && rows[l] >= rows[l - 1]) return fail(AMGEIG_ECORRUPT, "levels must shrink");
   }
   Reader rd{b, bytes, off};
-  levels.assign(n, HostCsr());
-  prolong.assign(n > 1 ? n - 1 : 0, HostCsr());
+  levels.assign(n, CsrView());
+  prolong.assign(n > 1 ? n - 1 : 0, CsrView());
   for (uint32_t l = 0; l < n; ++l) {
-    HostCsr& L = levels[l];
+    CsrView& L = levels[l];
     L.rows = L.cols = static_cast<int64_t>(rows[l]);
-    if (!rd.take(L.rp, rows[l] + 1) || !rd.take(L.ci, nnz[l]) || !rd.take(L.a, nnz[l]) || !rd.take(L.m, nnz[l]))
+    L.nnz = static_cast<int64_t>(nnz[l]);
+    if (!rd.view(&L.rp, rows[l] + 1) || !rd.view(&L.ci, nnz[l]) || !rd.view(&L.a, nnz[l]) || !rd.view(&L.m, nnz[l]))
       return fail(AMGEIG_ECORRUPT, "truncated level arrays");
-    if (!csr_valid(L.rp, L.ci, L.rows, L.cols)) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
+    if (!csr_valid(L)) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
   }
   for (uint32_t l = 0; l + 1 < n; ++l) {
-    HostCsr& P = prolong[l];
+    CsrView& P = prolong[l];
     P.rows = static_cast<int64_t>(rows[l]);
     P.cols = static_cast<int64_t>(rows[l + 1]);
+    P.nnz = static_cast<int64_t>(nnzp[l]);
     if (nnzp[l] >= (1ull << 31)) return fail(AMGEIG_ECORRUPT, "prolongation size out of range");
-    if (!rd.take(P.rp, rows[l] + 1) || !rd.take(P.ci, nnzp[l]) || !rd.take(P.a, nnzp[l]))
+    if (!rd.view(&P.rp, rows[l] + 1) || !rd.view(&P.ci, nnzp[l]) || !rd.view(&P.a, nnzp[l]))
       return fail(AMGEIG_ECORRUPT, "truncated prolongation arrays");
-    if (!csr_valid(P.rp, P.ci, P.rows, P.cols)) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
+    if (!csr_valid(P)) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
   }
   if (rd.off != bytes - 8) return fail(AMGEIG_ECORRUPT, "trailing bytes in blob");
   return AMGEIG_OK;
 }
 
-HostCsr transpose(const HostCsr& P) {
+HostCsr transpose(const CsrView& P) {
   HostCsr R;
   R.rows = P.cols;
   R.cols = P.rows;
   R.rp.assign(P.cols + 1, 0);
-  for (int32_t c : P.ci) R.rp[c + 1]++;
+  for (int64_t q = 0; q < P.nnz; ++q) R.rp[P.ci[q] + 1]++;
   for (int64_t j = 0; j < P.cols; ++j) R.rp[j + 1] += R.rp[j];
-  R.ci.resize(P.ci.size());
-  R.a.resize(P.ci.size());
+  R.ci.resize(static_cast<size_t>(P.nnz));
+  R.a.resize(static_cast<size_t>(P.nnz));
   std::vector<int32_t> pos(R.rp.begin(), R.rp.end() - 1);
   for (int64_t i = 0; i < P.rows; ++i)
     for (int32_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
@@ -257,6 +287,7 @@ HostCsr transpose(const HostCsr& P) {
 
 struct DeviceBuffers {
   std::vector<void*> ptrs;
+  cudaStream_t st = nullptr;  // uploads are ordered on this stream (the hierarchy's)
   ~DeviceBuffers() {
     for (void* p : ptrs) cudaFree(p);
   }
@@ -269,11 +300,15 @@ struct DeviceBuffers {
     return e;
   }
   template <typename T>
-  cudaError_t upload(T** out, const std::vector<T>& v) {
-    cudaError_t e = alloc(out, v.size());
+  cudaError_t upload(T** out, const T* src, size_t count) {
+    cudaError_t e = alloc(out, count);
     if (e != cudaSuccess) return e;
-    if (!v.empty()) e = cudaMemcpy(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    if (count) e = cudaMemcpyAsync(*out, src, sizeof(T) * count, cudaMemcpyHostToDevice, st);
     return e;
+  }
+  template <typename T>
+  cudaError_t upload(T** out, const std::vector<T>& v) {
+    return upload(out, v.data(), v.size());
   }
 };
 
@@ -926,8 +961,9 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return fail(AMGEIG_EINVAL, "no such CUDA device");
-  std::vector<HostCsr> levels, prolong;
-  int rc = parse_blob(blob, bytes, levels, prolong);
+  std::vector<CsrView> levels, prolong;
+  std::vector<uint64_t> aligned;
+  int rc = parse_blob(blob, bytes, levels, prolong, aligned);
   if (rc) return rc;
   CK(cudaSetDevice(device));
   auto h = std::make_unique<amgeig_hierarchy_t>();
@@ -939,61 +975,71 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   if (h->dn > 4096) return fail(AMGEIG_EINVAL, "coarsest level larger than 4096");
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
   auto& m = h->mem;
+  m.st = h->stream;
   h->A.resize(n);
   h->dinv64.assign(n, nullptr);
   h->dinv32.assign(n, nullptr);
+  // the blob's arrays go to the device as they are (stream-ordered copies); the
+  // float32 and float-float copies of the values are made there
+  std::vector<std::vector<double>> d64s(n);
+  std::vector<std::vector<float>> d32s(n);
   for (int l = 0; l < n; ++l) {
-    HostCsr& L = levels[l];
+    const CsrView& L = levels[l];
     DevCsr& D = h->A[l];
     D.rows = D.cols = static_cast<int>(L.rows);
-    D.nnz = static_cast<int>(L.ci.size());
-    std::vector<float> a32(L.a.begin(), L.a.end());
-    std::vector<double> d64(L.rows);
-    std::vector<float> d32(L.rows);
-    for (int64_t i = 0; i < L.rows; ++i) {
-      double s = 0.0;
-      for (int32_t p = L.rp[i]; p < L.rp[i + 1]; ++p) s += std::fabs(L.a[p]);
-      if (!(s > 0.0)) return fail(AMGEIG_ECORRUPT, "zero row in A");
-      d64[i] = 1.0 / s;
-      d32[i] = static_cast<float>(1.0 / s);
-    }
-    CK(m.upload(&D.rp, L.rp));
-    CK(m.upload(&D.ci, L.ci));
-    CK(m.upload(&D.v64, L.a));
-    CK(m.upload(&D.m64, L.m));
-    CK(m.upload(&D.v32, a32));
-    std::vector<float2> a2(L.a.size()), m2(L.m.size());
-    for (size_t i = 0; i < L.a.size(); ++i) {
-      const float hi = static_cast<float>(L.a[i]);
-      a2[i] = make_float2(hi, static_cast<float>(L.a[i] - static_cast<double>(hi)));
-      const float mh = static_cast<float>(L.m[i]);
-      m2[i] = make_float2(mh, static_cast<float>(L.m[i] - static_cast<double>(mh)));
-    }
-    CK(m.upload(&D.d2, a2));
-    CK(m.upload(&D.m2, m2));
+    D.nnz = static_cast<int>(L.nnz);
+    // l1-Jacobi inverse diagonal 1 / sum_j |a_ij| (host threads over rows)
+    std::vector<double>& d64 = d64s[l];
+    std::vector<float>& d32 = d32s[l];
+    d64.resize(static_cast<size_t>(L.rows));
+    d32.resize(static_cast<size_t>(L.rows));
+    const int T = host_threads(L.rows);
+    std::vector<char> ok(T, 1);
+    parallel_for(T, [&](int t) {
+      for (int64_t i = L.rows * t / T; i < L.rows * (t + 1) / T; ++i) {
+        double sa = 0.0;
+        for (int32_t p = L.rp[i]; p < L.rp[i + 1]; ++p) sa += std::fabs(L.a[p]);
+        if (!(sa > 0.0)) ok[t] = 0;
+        d64[i] = 1.0 / sa;
+        d32[i] = static_cast<float>(1.0 / sa);
+      }
+    });
+    for (char c : ok)
+      if (!c) return fail(AMGEIG_ECORRUPT, "zero row in A");
+    CK(m.upload(&D.rp, L.rp, static_cast<size_t>(L.rows) + 1));
+    CK(m.upload(&D.ci, L.ci, static_cast<size_t>(L.nnz)));
+    CK(m.upload(&D.v64, L.a, static_cast<size_t>(L.nnz)));
+    CK(m.upload(&D.m64, L.m, static_cast<size_t>(L.nnz)));
+    CK(m.alloc(&D.v32, static_cast<size_t>(L.nnz)));
+    CK(m.alloc(&D.d2, static_cast<size_t>(L.nnz)));
+    CK(m.alloc(&D.m2, static_cast<size_t>(L.nnz)));
+    launch_convert_f64_to_f32(D.v64, L.nnz, D.v32, h->stream);
+    launch_f64_to_df(D.v64, L.nnz, D.d2, h->stream);
+    launch_f64_to_df(D.m64, L.nnz, D.m2, h->stream);
     CK(m.upload(&h->dinv64[l], d64));
     CK(m.upload(&h->dinv32[l], d32));
   }
   h->P.resize(n - 1);
   h->R.resize(n - 1);
+  // R_l = P_l^T on host threads (one transpose per level), both uploaded
+  std::vector<HostCsr> Rt(n > 1 ? n - 1 : 0);
+  parallel_for(n > 1 ? n - 1 : 0, [&](int l) { Rt[l] = transpose(prolong[l]); });
   for (int l = 0; l + 1 < n; ++l) {
     for (int which = 0; which < 2; ++which) {
-      HostCsr S = which == 0 ? prolong[l] : transpose(prolong[l]);
+      const CsrView& P = prolong[l];
+      const HostCsr& R = Rt[l];
       DevCsr& D = which == 0 ? h->P[l] : h->R[l];
-      D.rows = static_cast<int>(S.rows);
-      D.cols = static_cast<int>(S.cols);
-      D.nnz = static_cast<int>(S.ci.size());
-      std::vector<float> v32(S.a.begin(), S.a.end());
-      std::vector<float2> v2(S.a.size());
-      for (size_t i = 0; i < S.a.size(); ++i) {
-        const float hi = static_cast<float>(S.a[i]);
-        v2[i] = make_float2(hi, static_cast<float>(S.a[i] - static_cast<double>(hi)));
-      }
-      CK(m.upload(&D.rp, S.rp));
-      CK(m.upload(&D.ci, S.ci));
-      CK(m.upload(&D.v64, S.a));
-      CK(m.upload(&D.v32, v32));
-      CK(m.upload(&D.d2, v2));
+      const int64_t rows = which == 0 ? P.rows : R.rows;
+      D.rows = static_cast<int>(rows);
+      D.cols = static_cast<int>(which == 0 ? P.cols : R.cols);
+      D.nnz = static_cast<int>(P.nnz);
+      CK(m.upload(&D.rp, which == 0 ? P.rp : R.rp.data(), static_cast<size_t>(rows) + 1));
+      CK(m.upload(&D.ci, which == 0 ? P.ci : R.ci.data(), static_cast<size_t>(P.nnz)));
+      CK(m.upload(&D.v64, which == 0 ? P.a : R.a.data(), static_cast<size_t>(P.nnz)));
+      CK(m.alloc(&D.v32, static_cast<size_t>(P.nnz)));
+      CK(m.alloc(&D.d2, static_cast<size_t>(P.nnz)));
+      launch_convert_f64_to_f32(D.v64, P.nnz, D.v32, h->stream);
+      launch_f64_to_df(D.v64, P.nnz, D.d2, h->stream);
     }
   }
   // composite prolongations I_n^k (coarsest -> level k) for the recombination:
@@ -1002,7 +1048,7 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   {
     HostCsr next;
     for (int k = n - 2; k >= 0; --k) {
-      const HostCsr& Pk = prolong[k];
+      const CsrView& Pk = prolong[k];
       HostCsr C;
       C.rows = Pk.rows;
       C.cols = h->dn;
@@ -1066,10 +1112,14 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
       D.cols = static_cast<int>(C.cols);
       D.nnz = static_cast<int>(C.ci.size());
       std::vector<float2> v2(C.a.size());
-      for (size_t i = 0; i < C.a.size(); ++i) {
-        const float hi = static_cast<float>(C.a[i]);
-        v2[i] = make_float2(hi, static_cast<float>(C.a[i] - static_cast<double>(hi)));
-      }
+      const int64_t nv = static_cast<int64_t>(C.a.size());
+      const int T2 = host_threads(nv);
+      parallel_for(T2, [&](int t) {
+        for (int64_t i = nv * t / T2; i < nv * (t + 1) / T2; ++i) {
+          const float hi = static_cast<float>(C.a[i]);
+          v2[i] = make_float2(hi, static_cast<float>(C.a[i] - static_cast<double>(hi)));
+        }
+      });
       CK(m.upload(&D.rp, C.rp));
       CK(m.upload(&D.ci, C.ci));
       CK(m.upload(&D.d2, v2));
@@ -1079,7 +1129,7 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   // dense coarsest pencil and its eigendecomposition
   const int dn = h->dn;
   std::vector<double> An(static_cast<size_t>(dn) * dn, 0.0), Mn(static_cast<size_t>(dn) * dn, 0.0);
-  const HostCsr& Lc = levels[n - 1];
+  const CsrView& Lc = levels[n - 1];
   for (int i = 0; i < dn; ++i)
     for (int32_t p = Lc.rp[i]; p < Lc.rp[i + 1]; ++p) {
       An[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.a[p];
