@@ -173,10 +173,10 @@ bool csr_valid(const CsrView& v) {
   return true;
 }
 
-// Host threads for the load-time loops over rows: one per 64k rows, at most 16.
+// Host threads for the load-time loops over rows: one per 32k rows, at most 16.
 int host_threads(int64_t rows) {
   const unsigned hc = std::thread::hardware_concurrency();
-  const int64_t want = rows / 65536 + 1;
+  const int64_t want = rows / 32768 + 1;
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({want, 16, hc ? static_cast<int64_t>(hc) : 1})));
 }
 

@@ -2042,9 +2042,9 @@ __global__ void k_chol(int n, const double* __restrict__ A, double* __restrict__
     const double piv = L[k * N + k];
     for (int i = k + 1 + tid; i < n; i += nt) L[i * N + k] /= piv;
     __syncthreads();
-    const int m = n - k - 1;
-    for (long long idx = tid; idx < static_cast<long long>(m) * m; idx += nt) {
-      const int i = k + 1 + static_cast<int>(idx / m), j = k + 1 + static_cast<int>(idx % m);
+    const int m = n - k - 1;  // n <= 4096: m * m fits in 32 bits
+    for (int idx = tid; idx < m * m; idx += nt) {
+      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
       if (j <= i) L[i * N + j] -= L[i * N + k] * L[j * N + k];
     }
     __syncthreads();
@@ -2053,22 +2053,32 @@ __global__ void k_chol(int n, const double* __restrict__ A, double* __restrict__
 }
 
 // In-place triangular solves on `ncols` columns of the row-major n x ld block X:
-// trans = 0: L Y = X (forward), trans = 1: L^T Y = X (backward).  One thread per column.
+// trans = 0: L Y = X (forward), trans = 1: L^T Y = X (backward).  One warp per
+// column: each step's inner product is spread over the lanes (fixed lane
+// partition, then a shuffle tree), so the dependent float64 chain per step is
+// ~i/32 long instead of i.
 __global__ void k_trsm(int n, const double* __restrict__ L, double* __restrict__ X, int ld, int ncols, int trans) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
-  const long long N = n;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ncols) return;  // whole warps
+  const long long N = n, LDX = ld;
   if (!trans) {
     for (int i = 0; i < n; ++i) {
-      double s = X[i * static_cast<long long>(ld) + c];
-      for (int k = 0; k < i; ++k) s -= L[i * N + k] * X[k * static_cast<long long>(ld) + c];
-      X[i * static_cast<long long>(ld) + c] = s / L[i * N + i];
+      double s = 0.0;
+      for (int k = lane; k < i; k += 32) s += L[i * N + k] * X[k * LDX + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) X[i * LDX + c] = (X[i * LDX + c] - s) / L[i * N + i];
+      __syncwarp();
     }
   } else {
     for (int i = n - 1; i >= 0; --i) {
-      double s = X[i * static_cast<long long>(ld) + c];
-      for (int k = i + 1; k < n; ++k) s -= L[k * N + i] * X[k * static_cast<long long>(ld) + c];
-      X[i * static_cast<long long>(ld) + c] = s / L[i * N + i];
+      double s = 0.0;
+      for (int k = i + 1 + lane; k < n; k += 32) s += L[k * N + i] * X[k * LDX + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) X[i * LDX + c] = (X[i * LDX + c] - s) / L[i * N + i];
+      __syncwarp();
     }
   }
 }
@@ -2268,14 +2278,14 @@ void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* M
   k_chol<<<1, 1024, 0, st>>>(dn, Mn, w->Lm, status);
   // Hs = L^-1 A_n L^-T : X = L^-1 A_n ; Hs = L^-1 X^T
   cudaMemcpyAsync(w->Hs, An, sizeof(double) * dn * dn, cudaMemcpyDeviceToDevice, st);
-  k_trsm<<<ceil_div(dn, 128), 128, 0, st>>>(dn, w->Lm, w->Hs, dn, dn, 0);
+  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, w->Hs, dn, dn, 0);
   k_transpose<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, dn, w->Hs, w->H);
-  k_trsm<<<ceil_div(dn, 128), 128, 0, st>>>(dn, w->Lm, w->H, dn, dn, 0);
+  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, w->H, dn, dn, 0);
   k_transpose_sym<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->H, w->Hs);
   // eigenpairs of Hs (all dn)
   launch_syev_df(w, dn, dn, w->Hs, theta, Z, st);
   // Z = L^-T Y
-  k_trsm<<<ceil_div(dn, 128), 128, 0, st>>>(dn, w->Lm, Z, dn, dn, 1);
+  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, Z, dn, dn, 1);
   // Ainv = Z diag(1/theta) Z^T
   k_scale_cols_inv<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, dn, Z, theta, w->H);
   launch_gemm_f64(dn, dn, dn, 1.0, w->H, dn, false, Z, dn, true, 0.0, Ainv, dn, st);
