@@ -190,6 +190,46 @@ def test_submit_poll_matches_direct():
             ae.amgeig_poll(ids[0])
 
 
+def test_blob_alignment_and_validation():
+    """The loader reads the blob in place: an unaligned blob (copied once) gives the
+    same bits as an aligned one, and an out-of-range column index behind a valid
+    checksum is rejected."""
+    import ctypes
+    import struct
+
+    p, blob, _ = problem_and_blob("square", 32, 50, 1)
+    opt = ae.options(q_extra=2, max_corrections=30, precision=ae.AMGEIG_MIXED_FP32)
+    with ae.Hierarchy(blob) as h:
+        ref = h.solve(3, tol=1e-9, opt=opt)
+    raw = ctypes.create_string_buffer(len(blob) + 8)
+    addr = ctypes.addressof(raw)
+    base = addr + 1 if (addr + 1) % 8 != 0 else addr + 2  # not 8-byte aligned
+    ctypes.memmove(base, blob, len(blob))
+    hnd = ctypes.c_void_p()
+    ae._check(ae.lib().amgeig_load_hierarchy(ctypes.c_void_p(base), len(blob), 0, ctypes.byref(hnd)), "load")
+    try:
+        vals = np.empty(3)
+        vecs = np.empty((p.n, 3))
+        ae.amgeig_solve(hnd, 3, 1e-9, opt, vals, vecs, False)
+        assert np.array_equal(vals, ref[0]) and np.array_equal(vecs, ref[1])
+    finally:
+        ae.amgeig_free_hierarchy(hnd)
+    # level 0's first column index out of range, checksum rewritten
+    n_lev = struct.unpack_from("<I", blob, 12)[0]
+    off = 16 + 8 * (3 * n_lev - 1)
+    off += (8 - off % 8) % 8
+    rows0 = struct.unpack_from("<Q", blob, 16)[0]
+    ci0 = off + 4 * (rows0 + 1)
+    ci0 += (8 - ci0 % 8) % 8
+    bad = bytearray(blob)
+    struct.pack_into("<i", bad, ci0, int(rows0) + 5)
+    words = np.frombuffer(bytes(bad[:-8]), dtype="<u8")
+    struct.pack_into("<Q", bad, len(bad) - 8, int(words.sum(dtype=np.uint64)))
+    with pytest.raises(ae.AmgEigError) as e:
+        ae.amgeig_load_hierarchy(bytes(bad))
+    assert e.value.code == ae.AMGEIG_ECORRUPT and "CSR" in str(e.value)
+
+
 def test_request_mix_matches_alone():
     """Requests on three hierarchies, submitted together so that they run at the same
     time on the library's workers, give the same bits as each solve run alone."""
