@@ -63,6 +63,8 @@ WORKLOADS = {
     # cube: q = 10 ends after the 11 pi^2 triple; 7 extra vectors reach past the 14 pi^2 sextet
     # (41 -> 22 corrections against 4 extra)
     "cube_m128_q10": dict(builder="cube_3d", kw=dict(m=128, seed=4), q=10, qe=7, cap=400, tol=1e-6, modes=64),
+    # q = 100 cuts inside the sixfold 42 pi^2 cluster (eigenvalues 97-102): the buffer covers it
+    "cube_m128_q100": dict(builder="cube_3d", kw=dict(m=128, seed=4), q=100, qe=8, cap=400, tol=1e-6, modes=64),
 }
 
 
@@ -271,10 +273,15 @@ def run_stream(args):
 
     pool = stream_pool(args.pool)
     hs = [ae.Hierarchy(blob, device=local) for _, _, blob, _ in pool]
-    q_extra, tol = 4, 1e-6
+    tol = 1e-6
 
-    def opt_for(k):
-        return ae.options(q_extra=q_extra, max_corrections=60, precision=ae.AMGEIG_MIXED_FP32, v_cycles=2,
+    def q_extra_for(q):
+        # the checkerboard's low spectrum is dense: a buffer of half the wanted
+        # count keeps its requests converging within the correction limit
+        return 4 + q // 2
+
+    def opt_for(k, q):
+        return ae.options(q_extra=q_extra_for(q), max_corrections=60, precision=ae.AMGEIG_MIXED_FP32, v_cycles=2,
                           coarse_modes=min(64, pool[k][3]))
 
     def run_batch(reqs, arrivals=None):
@@ -293,7 +300,7 @@ def run_stream(args):
             while nxt < n and (arrivals is None or arrivals[nxt] <= now):
                 k, q = reqs[nxt]
                 t_arr[nxt] = arrivals[nxt] if arrivals is not None else now
-                ids[ae.amgeig_submit(hs[k].handle, q, tol, opt_for(k))] = nxt
+                ids[ae.amgeig_submit(hs[k].handle, q, tol, opt_for(k, q))] = nxt
                 nxt += 1
             for rid in list(ids):
                 j = ids[rid]
@@ -329,7 +336,7 @@ def run_stream(args):
             "steps": args.requests, "warmup": len(pool) + len(burst), "ms_per_step": span * 1e3 / args.requests,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
-            "config": {"workload": "stream", "requests": args.requests, "q": "uniform 1..32", "q_extra": q_extra,
+            "config": {"workload": "stream", "requests": args.requests, "q": "uniform 1..32", "q_extra": "4 + q // 2",
                        "tol_relres": tol, "pool": [{"domain": d, "N": n} for d, n, _, _ in pool],
                        "service_rate_req_s": mu, "arrival_rate_req_s": lam, "workers": 4,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},

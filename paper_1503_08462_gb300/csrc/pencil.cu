@@ -1974,43 +1974,46 @@ __global__ void k_std_back(int m, int q, const df* __restrict__ L, double* __res
 // Xc = Z_m (a - B b) (d_n x q) and Y = b (q x q) from evecs = [a; b].  Every
 // block forms a - B b in shared memory (b staged there first), then its share
 // of the rows of Xc.
-__global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, const float2* __restrict__ Zdf,
-                                                    const df* __restrict__ KB, const double* __restrict__ evecs,
-                                                    double* __restrict__ Xc, float2* __restrict__ Xc2,
-                                                    double* __restrict__ Y) {
+// Xc = Z_m (a - B b) and Y = b for the columns [j0, j0 + qc) (chunks keep the
+// staged blocks within shared memory when m and q are large)
+__global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0, int qc,
+                                                    const float2* __restrict__ Zdf, const df* __restrict__ KB,
+                                                    const double* __restrict__ evecs, double* __restrict__ Xc,
+                                                    float2* __restrict__ Xc2, double* __restrict__ Y) {
   extern __shared__ __align__(16) unsigned char xraw[];
-  df* bs = reinterpret_cast<df*>(xraw);  // q x q
-  df* tmp = bs + q * q;                  // m x q
+  df* bs = reinterpret_cast<df*>(xraw);  // q x qc: b[:, j0:j0+qc]
+  df* tmp = bs + q * qc;                 // m x qc
   const int tid = threadIdx.x, nt = blockDim.x;
   const int q2 = 2 * q;
-  for (int idx = tid; idx < q * q; idx += nt) {
-    const double v = evecs[static_cast<long long>(m) * q + idx];
+  for (int idx = tid; idx < q * qc; idx += nt) {
+    const int r = idx / qc, jj = idx % qc;
+    const double v = evecs[static_cast<long long>(m + r) * q + j0 + jj];
     bs[idx] = to_df(v);
-    if (blockIdx.x == 0) Y[idx] = v;
+    if (blockIdx.x == 0) Y[r * q + j0 + jj] = v;
   }
   __syncthreads();
-  for (int idx = tid; idx < m * q; idx += nt) {
-    const int i = idx / q, j = idx % q;
+  for (int idx = tid; idx < m * qc; idx += nt) {
+    const int i = idx / qc, jj = idx % qc;
     const df* Bi = KB + static_cast<long long>(i) * q2 + q;
-    tmp[idx] = df_sub(to_df(evecs[idx]), dot4(Bi, 1, bs + j, q, q).value());
+    tmp[idx] = df_sub(to_df(evecs[static_cast<long long>(i) * q + j0 + jj]), dot4(Bi, 1, bs + jj, qc, q).value());
   }
   __syncthreads();
   const int rows = (dn + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * rows, r1 = min(dn, r0 + rows);
-  for (int idx = tid; idx < (r1 - r0) * q; idx += nt) {
-    const int l = r0 + idx / q, j = idx % q;
+  for (int idx = tid; idx < (r1 - r0) * qc; idx += nt) {
+    const int l = r0 + idx / qc, jj = idx % qc;
     const float2* zl = Zdf + static_cast<long long>(l) * dn;
     df_acc s0 = acc_zero(), s1 = acc_zero();
     int i = 0;
     for (; i + 2 <= m; i += 2) {
-      s0.fma(to_df(zl[i]), tmp[i * q + j]);
-      s1.fma(to_df(zl[i + 1]), tmp[(i + 1) * q + j]);
+      s0.fma(to_df(zl[i]), tmp[i * qc + jj]);
+      s1.fma(to_df(zl[i + 1]), tmp[(i + 1) * qc + jj]);
     }
-    if (i < m) s0.fma(to_df(zl[i]), tmp[i * q + j]);
+    if (i < m) s0.fma(to_df(zl[i]), tmp[i * qc + jj]);
     s0.merge(s1);
     const df v = s0.value();
-    Xc[static_cast<long long>(l) * q + j] = df_to_double(v);
-    if (Xc2) Xc2[static_cast<long long>(l) * q + j] = make_float2(v.hi, v.lo);
+    Xc[static_cast<long long>(l) * q + j0 + jj] = df_to_double(v);
+    if (Xc2) Xc2[static_cast<long long>(l) * q + j0 + jj] = make_float2(v.hi, v.lo);
   }
 }
 
@@ -2238,11 +2241,14 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   const size_t chs = sizeof(df) * (1.0 * n * q + 5.0 * q * q + 2.0 * m + 1.0 * m * q + 1.0 * q * (q + kMaxCluster) +
                                     3.0 * n * kMaxCluster + 1.0 * kMaxCluster * q);
   const size_t fs = sizeof(df) * q * q;
-  const size_t xs = sizeof(df) * (1.0 * m * q + 1.0 * q * q);
   const bool fast = q <= kSrqiMaxQ && srs <= 200 * 1024 && chs <= 220 * 1024;
+  // Xc = Z_m (a - B b) runs in column chunks whose staged blocks fit in 200 KB
+  const int qc = static_cast<int>(std::max<size_t>(
+      1, std::min<size_t>(q, (200 * 1024) / (sizeof(df) * static_cast<size_t>(m + q)))));
+  const int nxc = (q + qc - 1) / qc;
   // kernels launched here; the dense eigensolver's launcher counts its own
   ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * m * q + 3.0 * q * q + 1.0 * n * q), 0.0,
-               fast ? 7 : 5);
+               (fast ? 6 : 4) + nxc);
   if (Cdf) {
     smem_attr((const void*)k_kb<float2>, kbs);
     k_kb<float2><<<2 * q, kPenThreads, kbs, st>>>(dn, m, q, Zdf, Cdf, w->KB);
@@ -2267,8 +2273,12 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   launch_syev_df(w, n, q, w->H, mu, w->Yh, st, skip);
   k_std_back<<<1, kStdMaxQ, 0, st>>>(m, q, w->Lq, w->Yh, skip);
   // Xc = Z_m (a - B b), Y = b
-  smem_attr((const void*)k_xc, xs);
-  k_xc<<<16, kPenThreads, xs, st>>>(dn, m, q, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
+  for (int j0 = 0; j0 < q; j0 += qc) {
+    const int wc = std::min(qc, q - j0);
+    const size_t xsc = sizeof(df) * static_cast<size_t>(m + q) * wc;
+    smem_attr((const void*)k_xc, xsc);
+    k_xc<<<16, kPenThreads, xsc, st>>>(dn, m, q, j0, wc, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
+  }
 }
 
 void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,
