@@ -283,6 +283,22 @@ def test_multiple_vcycles_match_oracle():
     assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
 
 
+def test_wide_block_all_coarse_modes_matches_oracle():
+    """q + q_extra = 90 with the full coarse space (255 modes): the pencil goes through
+    the dense solver and the coarse reconstruction runs in column chunks."""
+    p, blob, _ = problem_and_blob("square", 64, 400, 1)
+    oh = O.read_blob(blob)
+    lam_o, U_o, _ = O.solve(oh, 80, tol=0.0, opts=O.Options(q_extra=10, fixed_corrections=2))
+    with ae.Hierarchy(blob) as h:
+        assert h.sizes[-1] >= 200
+        lam, U, info, _ = h.solve(80, tol=0.0, opt=ae.options(q_extra=10, fixed_corrections=2))
+    assert info.dense_fallbacks > 0
+    tol = eig_rel_tol(lam_o, lam_max(p))
+    assert np.all(np.abs(lam - lam_o) / lam_o < tol)
+    M = oh.M[0]
+    assert np.max(np.abs(U.T @ (M @ U) - np.eye(80))) < 1e-10
+
+
 @pytest.mark.parametrize("L", [1, 3])
 def test_coarse_modes_parity(L):
     """The truncated coarse space (coarse_modes option) matches the oracle's same option."""
