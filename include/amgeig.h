@@ -154,7 +154,19 @@ int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals, double* evecs);
 
-/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h (Algorithm
+/* The defect of Algorithm 3.1 step 1 (the right-hand side of the correction
+ * equation, Eq. Linear_Equation): r_j = lambda_j M_l u_j - A_l u_j on level
+ * `level` of h, with the relative residuals ||A u_j - lambda_j M u_j||_2 /
+ * (|lambda_j| ||M u_j||_2) from the same pass.  U (N_l x width, row-major) and
+ * lam (width) are host inputs; R (N_l x width) and relres (width, may be NULL)
+ * host outputs.  The options' precision selects the float64 kernel or the
+ * mixed path's float-float kernel, whose defect is rounded to float32 (the
+ * V-cycle's right-hand side).  1 <= width <= 128.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+int amgeig_apply_defect(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* U,
+                        const double* lam, double* R, double* relres);
+
+/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h (Algorithm
  * 3.1 step 1 with the options' pre/post l1-Jacobi sweeps and precision): b and
  * x are host buffers of N_l x width doubles (row-major), 1 <= width <= 128.
  * Errors: EINVAL, ENOMEM, ECUDA. */

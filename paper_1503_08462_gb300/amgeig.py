@@ -54,8 +54,8 @@ class amgeig_info(ctypes.Structure):
 _lib = None
 EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
-            "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_profile_enable", "amgeig_profile_read",
-            "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc"]
+            "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_apply_defect", "amgeig_profile_enable",
+            "amgeig_profile_read", "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc"]
 
 
 def library_path() -> str:
@@ -86,6 +86,7 @@ def lib():
         L.amgeig_last_error.restype = ctypes.c_char_p
         L.amgeig_sym_eigh.argtypes = [i32, i32, i32, vp, vp, vp]
         L.amgeig_apply_vcycle.argtypes = [vp, i32, i32, ctypes.POINTER(amgeig_options), vp, vp]
+        L.amgeig_apply_defect.argtypes = [vp, i32, i32, ctypes.POINTER(amgeig_options), vp, vp, vp, vp]
         L.amgeig_profile_enable.argtypes = [i32]
         L.amgeig_profile_read.argtypes = [ctypes.POINTER(amgeig_prof_entry), i32, ctypes.POINTER(i32)]
         L.amgeig_sym_eigh_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
@@ -94,7 +95,7 @@ def lib():
         L.amgeig_kernel_launches.restype = ctypes.c_uint64
         for name in ("amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
                      "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle",
-                     "amgeig_profile_enable", "amgeig_profile_read"):
+                     "amgeig_apply_defect", "amgeig_profile_enable", "amgeig_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -187,6 +188,17 @@ def amgeig_sym_eigh_noalloc(H, evals, evecs, stream: Optional[int] = None) -> No
     nwant = evals.shape[0]
     _check(lib().amgeig_sym_eigh_noalloc(n, nwant, _ptr(H), _ptr(evals), _ptr(evecs), stream),
            "amgeig_sym_eigh_noalloc")
+
+
+def amgeig_apply_defect(h, level: int, U: np.ndarray, lam: np.ndarray, opt: Optional[amgeig_options] = None):
+    """(R, relres): r_j = lam_j M u_j - A u_j on `level` and the relative residuals."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    R = np.empty_like(U)
+    rr = np.empty(U.shape[1])
+    _check(lib().amgeig_apply_defect(h, level, U.shape[1], ctypes.byref(opt) if opt is not None else None, _ptr(U),
+                                     _ptr(lam), _ptr(R), _ptr(rr)), "amgeig_apply_defect")
+    return R, rr
 
 
 def amgeig_apply_vcycle(h, level: int, b: np.ndarray, opt: Optional[amgeig_options] = None) -> np.ndarray:

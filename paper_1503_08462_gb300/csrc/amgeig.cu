@@ -1231,6 +1231,46 @@ int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals
   return AMGEIG_OK;
 }
 
+int amgeig_apply_defect(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* U,
+                        const double* lam, double* R, double* relres) {
+  g_last_error.clear();
+  if (!h || !U || !lam || !R || level < 0 || level >= h->nlev || width < 1 || width > 128)
+    return fail(AMGEIG_EINVAL, "invalid argument");
+  amgeig_options o;
+  amgeig_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->stream;
+  rc = ensure_workspace(h, width, o.precision, 1);
+  if (rc) return rc;
+  SolveWork* w = h->ws.get();
+  const int Nl = static_cast<int>(h->sizes[level]);
+  const long long cnt = static_cast<long long>(Nl) * width;
+  CK(cudaMemcpyAsync(w->V, U, sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(w->lam, lam, sizeof(double) * width, cudaMemcpyHostToDevice, st));
+  int nb = 0;
+  if (o.precision == AMGEIG_FP64) {
+    launch_defect_f64(h->A[level], w->V, width, w->lam, w->B64[level], w->partials, &nb, st);
+    CK(cudaMemcpyAsync(R, w->B64[level], sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  } else {
+    // the iterate in float-float, the defect rounded to float32 (the V-cycle's right-hand side)
+    launch_f64_to_df(w->V, cnt, as_df(w->U), st);
+    launch_defect_df(h->A[level], as_df(w->U), width, w->lam, w->B32[level], w->ld32, w->partials, &nb, st);
+    launch_f32_to_f64_unpad(w->B32[level], Nl, width, w->ld32, w->Ualt, st);
+    CK(cudaMemcpyAsync(R, w->Ualt, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  }
+  launch_sum_partials(w->partials, nb, 2 * width, w->sums, st);
+  CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
+  launch_relres(w->sums, w->lam, width, w->relres, w->flags, st);
+  CK(cudaGetLastError());
+  if (relres) CK(cudaMemcpyAsync(relres, w->relres, sizeof(double) * width, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return AMGEIG_OK;
+}
+
 int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* b,
                         double* x) {
   g_last_error.clear();

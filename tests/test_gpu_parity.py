@@ -271,6 +271,36 @@ def test_request_mix_matches_alone():
             h.close()
 
 
+@pytest.mark.parametrize("level", [0, 1])
+def test_defect_matches_oracle(level):
+    """r_j = lambda_j M u_j - A u_j and the relative residuals (Eq. Linear_Equation),
+    float64 kernel and float-float kernel, against the oracle's sparse products; near
+    eigenvectors too, where lambda M u and A u cancel to ~1e-6 of their size."""
+    p, blob, _ = problem_and_blob("lshape", 24, 60, 2)
+    oh = O.read_blob(blob)
+    A, M = oh.A[level], oh.M[level]
+    n = A.shape[0]
+    rng = np.random.default_rng(5)
+    import scipy.linalg as sla
+
+    lam_d, V_d = sla.eigh(A.toarray(), M.toarray(), subset_by_index=[0, 5])
+    cases = [(rng.standard_normal((n, 7)), rng.uniform(5.0, 200.0, 7)),
+             (V_d + 1e-6 * rng.standard_normal(V_d.shape), lam_d)]
+    with ae.Hierarchy(blob) as h:
+        for U, lam in cases:
+            ref = M @ U * lam[None, :] - A @ U
+            scale = (abs(A) @ abs(U)) + (abs(M) @ abs(U)) * abs(lam)[None, :]
+            rr_ref = np.linalg.norm(ref, axis=0) / (np.abs(lam) * np.linalg.norm(M @ U, axis=0))
+            R64, rr64 = ae.amgeig_apply_defect(h.handle, level, U, lam, ae.options(precision=ae.AMGEIG_FP64))
+            assert np.all(np.abs(R64 - ref) <= 1e-14 * scale + 1e-300)
+            np.testing.assert_allclose(rr64, rr_ref, rtol=1e-10)
+            R32, rr32 = ae.amgeig_apply_defect(h.handle, level, U, lam,
+                                              ae.options(precision=ae.AMGEIG_MIXED_FP32))
+            # float-float products (~2^-46 of the operand scale), then float32 rounding
+            assert np.all(np.abs(R32 - ref) <= 2.0 ** -23 * np.abs(ref) + 2.0 ** -42 * scale)
+            np.testing.assert_allclose(rr32, rr_ref, rtol=1e-6)
+
+
 def test_multiple_vcycles_match_oracle():
     p, blob, _ = problem_and_blob("square", 32, 50, 1)
     oh = O.read_blob(blob)
