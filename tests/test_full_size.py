@@ -50,8 +50,9 @@ def test_full_size_solve_properties(workload):
     assert code64 == ae.AMGEIG_OK
     assert np.max(np.abs(lam - lam64) / lam64) <= 1e-8
     # Ritz values bound the discrete eigenvalues from above: the less converged values
-    # cannot lie below the tightly converged ones beyond rounding
-    assert np.all(lam >= lam64 * (1.0 - 1e-12))
+    # cannot lie below the tightly converged ones beyond rounding (the float-float
+    # Rayleigh-Ritz resolves values to ~1e-11 relative)
+    assert np.all(lam >= lam64 * (1.0 - 1e-10)), np.min((lam - lam64) / lam64)
 
 
 @pytest.mark.parametrize("prec", [ae.AMGEIG_FP64, ae.AMGEIG_MIXED_FP32])
