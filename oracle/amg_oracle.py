@@ -42,7 +42,12 @@ Readings of the paper taken here (they are listed with the rest of the design):
   paper's total error e_l needs reference eigenvalues;
 * "select the desired eigenpairs" means the q + q_extra smallest Ritz values;
 * each output vector is signed so that its largest-magnitude entry (lowest
-  index on ties) is positive.
+  index on ties) is positive;
+* with ``Options.smoother = "gs"`` the V-cycle smooths with Gauss-Seidel as the
+  paper does (Sec. 4.1), made parallel by a multicolour ordering: rows are
+  coloured first-fit in row order (the smallest colour no earlier neighbour
+  holds) and one sweep visits the colours in ascending order before the coarse
+  correction and in descending order after it, so the V-cycle stays symmetric.
 """
 from __future__ import annotations
 
@@ -144,26 +149,71 @@ def jacobi_l1(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray) -> np.nd
     return x + d * (b - h.A[l] @ x)
 
 
-def vcycle(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray, pre: int = 1, post: int = 1) -> np.ndarray:
+def greedy_colours(A: sp.csr_matrix) -> np.ndarray:
+    """First-fit colouring in row order: row i takes the smallest colour that no
+    neighbour j < i (a_ij != 0) holds.  Rows of one colour are never adjacent."""
+    n = A.shape[0]
+    colour = np.full(n, -1, dtype=np.int64)
+    for i in range(n):
+        taken = set()
+        for p in range(A.indptr[i], A.indptr[i + 1]):
+            j = A.indices[p]
+            if j < i:
+                taken.add(int(colour[j]))
+        c = 0
+        while c in taken:
+            c += 1
+        colour[i] = c
+    return colour
+
+
+_COLOURS = {}
+
+
+def colours(h: OracleHierarchy, l: int) -> np.ndarray:
+    key = (id(h), l)
+    if key not in _COLOURS:
+        _COLOURS[key] = greedy_colours(h.A[l])
+    return _COLOURS[key]
+
+
+def gauss_seidel(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray, descending: bool = False) -> np.ndarray:
+    """One multicolour Gauss-Seidel sweep x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii,
+    the colours in ascending (or descending) order; rows of one colour at once."""
+    A = h.A[l]
+    col = colours(h, l)
+    diag = A.diagonal()
+    x = x.copy()
+    order = range(int(col.max()) + 1)
+    for c in (reversed(order) if descending else order):
+        rows = np.nonzero(col == c)[0]
+        d = diag[rows] if x.ndim == 1 else diag[rows][:, None]
+        x[rows] = x[rows] + (b[rows] - A[rows] @ x) / d
+    return x
+
+
+def vcycle(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray, pre: int = 1, post: int = 1,
+           smoother: str = "jacobi") -> np.ndarray:
     """One V-cycle for A_l x = b from the initial guess x."""
     if l == h.n_levels - 1:
         return sla.cho_solve(h.An_chol, b)
     for _ in range(pre):
-        x = jacobi_l1(h, l, b, x)
+        x = gauss_seidel(h, l, b, x) if smoother == "gs" else jacobi_l1(h, l, b, x)
     r = b - h.A[l] @ x
     bc = h.R[l] @ r
-    xc = vcycle(h, l + 1, bc, np.zeros_like(bc), pre, post)
+    xc = vcycle(h, l + 1, bc, np.zeros_like(bc), pre, post, smoother)
     x = x + h.P[l] @ xc
     for _ in range(post):
-        x = jacobi_l1(h, l, b, x)
+        x = gauss_seidel(h, l, b, x, descending=True) if smoother == "gs" else jacobi_l1(h, l, b, x)
     return x
 
 
-def amg(h: OracleHierarchy, k: int, b: np.ndarray, x0: np.ndarray, m: int = 1, pre: int = 1, post: int = 1):
+def amg(h: OracleHierarchy, k: int, b: np.ndarray, x0: np.ndarray, m: int = 1, pre: int = 1, post: int = 1,
+        smoother: str = "jacobi"):
     """AMG(k, b, x0, m): m V-cycles on level k from the initial guess x0."""
     x = x0
     for _ in range(m):
-        x = vcycle(h, k, b, x, pre, post)
+        x = vcycle(h, k, b, x, pre, post, smoother)
     return x
 
 
@@ -191,6 +241,7 @@ def prolong_from_coarsest(h: OracleHierarchy, k: int, Xc: np.ndarray) -> np.ndar
 
 @dataclasses.dataclass
 class Options:
+    smoother: str = "jacobi"  # "jacobi" (point l1-Jacobi) or "gs" (multicolour Gauss-Seidel)
     max_corrections: int = 20
     v_cycles: int = 1
     pre_sweeps: int = 1
@@ -230,7 +281,7 @@ def correction(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts:
     """One AMGCorrection(n, k, {lambda_j, u_j}) step; returns (lambda, U)."""
     qt = U.shape[1]
     b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
-    V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps)
+    V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
     Ahat, Mhat = augmented_pencil(h, k, V)
     dn = h.sizes[-1]
     if 0 < opts.coarse_modes < dn:

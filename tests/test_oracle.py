@@ -213,3 +213,73 @@ def test_coarse_modes_option():
     lam_ex, U_ex = dense_pairs(p, 6)
     assert np.all(np.abs(lam - lam_ex) <= 1e-10 * lam_ex)
     assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
+
+
+# ---------------------------------------------------------------- multicolour Gauss-Seidel
+
+
+def test_greedy_colours_are_a_proper_colouring():
+    """No two adjacent rows share a colour, and first-fit never needs more than
+    max-degree + 1 colours."""
+    for kind, size in (("square", 16), ("lshape", 8), ("cube", 6)):
+        p, oh = _oh(kind, size, 20)
+        A = oh.A[0]
+        col = O.greedy_colours(A)
+        rows, cols = A.nonzero()
+        off = rows != cols
+        assert np.all(col[rows[off]] != col[cols[off]])
+        deg = np.diff(A.indptr) - 1
+        assert col.max() + 1 <= deg.max() + 1
+
+
+def test_multicolour_gs_is_gauss_seidel_in_colour_order():
+    """A multicolour sweep is the textbook sequential Gauss-Seidel sweep over the rows
+    taken colour by colour (row order inside a colour), written here as a plain loop;
+    the descending sweep is the same over the reversed colour order."""
+    p, oh = _oh("lshape", 8, 20, seed=2)
+    A = oh.A[0].toarray()
+    n = A.shape[0]
+    col = O.greedy_colours(oh.A[0])
+    rng = np.random.default_rng(3)
+    b, x0 = rng.standard_normal(n), rng.standard_normal(n)
+    for descending in (False, True):
+        cs = sorted(set(col.tolist()), reverse=descending)
+        order = [i for c in cs for i in range(n) if col[i] == c]
+        x = x0.copy()
+        for i in order:
+            x[i] = (b[i] - A[i] @ x + A[i, i] * x[i]) / A[i, i]
+        np.testing.assert_allclose(O.gauss_seidel(oh, 0, b, x0, descending), x, rtol=1e-12, atol=1e-12)
+
+
+def test_gs_reduces_energy_error_and_vcycle_is_symmetric():
+    """Gauss-Seidel is an A-norm contraction for SPD A; with ascending colours before and
+    descending after the coarse correction the V-cycle operator is symmetric and its
+    error propagation contracts (faster than with l1-Jacobi)."""
+    p, oh = _oh("checker", 16, 30, seed=3)
+    A = oh.A[0]
+    e = np.random.default_rng(1).standard_normal(A.shape[0])
+    for _ in range(5):
+        e_new = O.gauss_seidel(oh, 0, np.zeros_like(e), e)
+        assert e_new @ (A @ e_new) < e @ (A @ e)
+        e = e_new
+    p, oh = _oh("square", 16, 20)
+    n = oh.sizes[0]
+    B = np.stack([O.vcycle(oh, 0, ei, np.zeros(n), smoother="gs") for ei in np.eye(n)], axis=1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    Ad = oh.A[0].toarray()
+    L = np.linalg.cholesky(Ad)
+    rho = np.linalg.norm(L.T @ (np.eye(n) - B @ Ad) @ np.linalg.inv(L.T), 2)
+    Bj = _vcycle_matrix(oh)
+    rho_j = np.linalg.norm(L.T @ (np.eye(n) - Bj @ Ad) @ np.linalg.inv(L.T), 2)
+    assert rho < rho_j < 0.7, (rho, rho_j)
+
+
+def test_gs_solve_matches_dense_definition():
+    """Pin 1 with the Gauss-Seidel smoother: the same fixed point, reached in fewer corrections."""
+    p, oh = _oh("lshape", 16, 60, 2)
+    lam_ex, _ = dense_pairs(p, 6)
+    lam, U, info = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100, smoother="gs"))
+    assert info.converged
+    assert np.all(np.abs(lam - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
+    _, _, info_j = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
+    assert info.corrections < info_j.corrections
