@@ -380,6 +380,8 @@ def main():
     ap.add_argument("--cap", type=int, default=None, help="coarse-level cap of the AMG setup")
     ap.add_argument("--sweeps", type=int, default=1, help="l1-Jacobi sweeps before and after the coarse correction")
     ap.add_argument("--v-cycles", type=int, default=2, help="V-cycles per correction (AMG iteration steps m)")
+    ap.add_argument("--smoother", choices=["l1-jacobi", "gauss-seidel"], default="l1-jacobi",
+                    help="V-cycle smoother: point l1-Jacobi, or the paper's Gauss-Seidel in multicolour order")
     ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -422,8 +424,9 @@ def main():
         qe = args.q_extra
     modes = WORKLOADS[args.workload]["modes"] if args.coarse_modes is None else args.coarse_modes
     prec = ae.AMGEIG_MIXED_FP32 if args.precision == "mixed" else ae.AMGEIG_FP64
+    smoother = ae.AMGEIG_SMOOTHER_GAUSS_SEIDEL if args.smoother == "gauss-seidel" else ae.AMGEIG_SMOOTHER_L1_JACOBI
     opt = ae.options(q_extra=qe, max_corrections=60, precision=prec, coarse_modes=modes,
-                     pre_sweeps=args.sweeps, post_sweeps=args.sweeps, v_cycles=args.v_cycles)
+                     pre_sweeps=args.sweeps, post_sweeps=args.sweeps, v_cycles=args.v_cycles, smoother=smoother)
     h = ae.Hierarchy(blob, device=local)
     N0 = h.sizes[0]
     stream = torch.cuda.Stream(device=local)
@@ -562,7 +565,7 @@ def main():
             "dtype": "f64+f32" if prec == ae.AMGEIG_MIXED_FP32 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "N": N0, "q": q, "q_extra": qe, "levels": h.sizes,
                        "precision": args.precision, "tol_relres": tol, "corrections": corrections,
-                       "coarse_modes": modes, "sweeps": args.sweeps, "v_cycles": args.v_cycles,
+                       "coarse_modes": modes, "sweeps": args.sweeps, "v_cycles": args.v_cycles, "smoother": args.smoother,
                        "rel_eig_err_vs_fp64": rel_err, "fp64_corrections": info_ref.corrections,
                        "fp64_full_pencil_s": round(t_ref, 4), "fp64_relres": info_ref.max_relres,
                        "dense_fallbacks": info.dense_fallbacks,

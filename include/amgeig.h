@@ -68,7 +68,15 @@ typedef struct {
                             the coarsest pencil (A_n, M_n) span its coarse part (an
                             option of this library: the pencil shrinks from d_n + q to
                             m + q; the fixed point, the exact eigenpairs, is unchanged) */
+  int smoother;          /* AMGEIG_SMOOTHER_L1_JACOBI (default) or AMGEIG_SMOOTHER_GAUSS_SEIDEL:
+                            the paper's Gauss-Seidel (Sec. 4.1) in a multicolour ordering --
+                            rows coloured first-fit in row order, colours ascending before the
+                            coarse correction and descending after it (a symmetric V-cycle);
+                            the colouring is computed on the first such solve */
 } amgeig_options;
+
+#define AMGEIG_SMOOTHER_L1_JACOBI 0
+#define AMGEIG_SMOOTHER_GAUSS_SEIDEL 1
 
 /* Per-solve report. */
 typedef struct {

@@ -27,6 +27,8 @@ AMGEIG_ENOTFOUND = -8
 
 AMGEIG_FP64 = 0
 AMGEIG_MIXED_FP32 = 1
+AMGEIG_SMOOTHER_L1_JACOBI = 0
+AMGEIG_SMOOTHER_GAUSS_SEIDEL = 1
 
 
 class AmgEigError(RuntimeError):
@@ -38,7 +40,7 @@ class AmgEigError(RuntimeError):
 class amgeig_options(ctypes.Structure):
     _fields_ = [("max_corrections", ctypes.c_int), ("v_cycles", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("q_extra", ctypes.c_int), ("precision", ctypes.c_int),
-                ("fixed_corrections", ctypes.c_int), ("coarse_modes", ctypes.c_int)]
+                ("fixed_corrections", ctypes.c_int), ("coarse_modes", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class amgeig_prof_entry(ctypes.Structure):

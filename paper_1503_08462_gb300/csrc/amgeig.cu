@@ -333,6 +333,14 @@ struct amgeig_hierarchy_t {
   DeviceBuffers mem;
   std::mutex mu;  // one solve at a time per hierarchy (shared workspace)
   std::unique_ptr<SolveWork> ws;
+  // multicolour Gauss-Seidel, built on the first solve that asks for it:
+  // per level below the coarsest, the rows sorted by colour (device), the
+  // colour offsets (host) and 1 / a_ii
+  bool gs_ready = false;
+  std::vector<int*> gs_rows;
+  std::vector<std::vector<int>> gs_off;
+  std::vector<double*> gs_dinv64;
+  std::vector<float*> gs_dinv32;
   cudaStream_t stream = nullptr;
   std::atomic<int> pending{0};
   ~amgeig_hierarchy_t();
@@ -341,6 +349,7 @@ struct amgeig_hierarchy_t {
 namespace {
 
 struct SolveWork {
+  int smoother = AMGEIG_SMOOTHER_L1_JACOBI;  // of the current solve
   int qcap = 0;  // column capacity: the buffers serve any solve with q + q_extra <= qcap
   int qt = 0;    // columns of the current solve (every block's row stride)
   int ld32 = 0;  // row stride of the float32 V-cycle blocks: qt rounded up to a multiple of 4
@@ -503,6 +512,78 @@ void coarse_solve(amgeig_hierarchy_t* h, const float* b, int q, float* x, cudaSt
 int width_of(SolveWork* w, double*) { return w->qt; }
 int width_of(SolveWork* w, float*) { return w->ld32; }
 
+// First-fit colouring in row order of every level below the coarsest (row i
+// takes the smallest colour no neighbour j < i holds; rows of one colour are
+// never adjacent), the rows sorted by colour and 1 / a_ii.  Runs once per
+// hierarchy, under its lock.
+int ensure_gs(amgeig_hierarchy_t* h, cudaStream_t st) {
+  if (h->gs_ready) return AMGEIG_OK;
+  const int n = h->nlev;
+  h->gs_rows.assign(n, nullptr);
+  h->gs_off.assign(n, std::vector<int>());
+  h->gs_dinv64.assign(n, nullptr);
+  h->gs_dinv32.assign(n, nullptr);
+  auto& m = h->mem;
+  for (int l = 0; l + 1 < n; ++l) {
+    const DevCsr& A = h->A[l];
+    std::vector<int32_t> rp(static_cast<size_t>(A.rows) + 1), ci(static_cast<size_t>(A.nnz));
+    std::vector<double> av(static_cast<size_t>(A.nnz));
+    CK(cudaMemcpyAsync(rp.data(), A.rp, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ci.data(), A.ci, sizeof(int32_t) * ci.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(av.data(), A.v64, sizeof(double) * av.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int32_t> col(static_cast<size_t>(A.rows), 0), seen;
+    std::vector<double> d64(static_cast<size_t>(A.rows), 0.0);
+    for (int32_t i = 0; i < A.rows; ++i) {
+      double aii = 0.0;
+      for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int32_t j = ci[p];
+        if (j == i) aii = av[p];
+        if (j < i) seen[col[j]] = i;
+      }
+      int32_t c = 0;
+      while (c < static_cast<int32_t>(seen.size()) && seen[c] == i) ++c;
+      if (c == static_cast<int32_t>(seen.size())) seen.push_back(-1);
+      col[i] = c;
+      if (!(aii > 0.0)) return fail(AMGEIG_ECORRUPT, "non-positive diagonal entry in A");
+      d64[i] = 1.0 / aii;
+    }
+    const int nc = static_cast<int>(seen.size());
+    std::vector<int>& off = h->gs_off[l];
+    off.assign(static_cast<size_t>(nc) + 1, 0);
+    for (int32_t i = 0; i < A.rows; ++i) off[col[i] + 1]++;
+    for (int c = 0; c < nc; ++c) off[c + 1] += off[c];
+    std::vector<int32_t> rows(static_cast<size_t>(A.rows)), pos(off.begin(), off.end() - 1);
+    for (int32_t i = 0; i < A.rows; ++i) rows[pos[col[i]]++] = i;
+    std::vector<float> d32(d64.begin(), d64.end());
+    CK(m.upload(&h->gs_rows[l], rows));
+    CK(m.upload(&h->gs_dinv64[l], d64));
+    CK(m.upload(&h->gs_dinv32[l], d32));
+    CK(cudaStreamSynchronize(m.st));  // the uploads run on the hierarchy's stream
+  }
+  h->gs_ready = true;
+  return AMGEIG_OK;
+}
+
+const double* gs_dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->gs_dinv64[l]; }
+const float* gs_dinv_of(amgeig_hierarchy_t* h, int l, float*) { return h->gs_dinv32[l]; }
+
+// One multicolour Gauss-Seidel sweep on level l (colours ascending, or descending)
+template <typename T>
+void gs_sweep(amgeig_hierarchy_t* h, int l, const T* b, T* x, int ld, bool descending, cudaStream_t st) {
+  const DevCsr& A = h->A[l];
+  const std::vector<int>& off = h->gs_off[l];
+  const int nc = static_cast<int>(off.size()) - 1;
+  const double N = A.rows;
+  const double sweep = 4.0 * (N + 1) + (4.0 + sizeof(T)) * A.nnz + sizeof(T) * (N + 3.0 * N * ld);
+  T* dummy = nullptr;
+  for (int k = 0; k < nc; ++k) {
+    const int c = descending ? nc - 1 - k : k;
+    const int cnt = off[c + 1] - off[c];
+    launch_gs_colour(cnt, h->gs_rows[l] + off[c], A, gs_dinv_of(h, l, dummy), b, x, ld, ld, sweep * cnt / N, st);
+  }
+}
+
 template <typename T>
 void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool to_v, const double* U, double* V,
             cudaStream_t st, const float* xadd = nullptr) {
@@ -512,10 +593,17 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
   auto& X = VBufs<T>::X(w);
   auto& Tm = VBufs<T>::Tm(w);
   T* dummy = nullptr;
+  const bool gs = w->smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL;
   for (int l = k; l < n - 1; ++l) {
     const DevCsr& A = h->A[l];
     const T* d = dinv_of(h, l, dummy);
-    if (pre >= 1) {
+    if (gs && pre >= 1) {
+      // Gauss-Seidel from x = 0, colours ascending; then the residual
+      cudaMemsetAsync(X[l], 0, sizeof(T) * h->sizes[l] * q, st);
+      for (int s = 0; s < pre; ++s) gs_sweep(h, l, B[l], X[l], q, false, st);
+      residual(A, B[l], X[l], q, Tm[l], st);
+      spmm(h->R[l], Tm[l], q, B[l + 1], false, st);
+    } else if (pre >= 1) {
       presmooth_residual(A, d, B[l], q, X[l], Tm[l], st);
       for (int s = 1; s < pre; ++s) {
         jacobi(A, d, B[l], X[l], q, Tm[l], st);
@@ -533,6 +621,16 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
     const DevCsr& A = h->A[l];
     const T* d = dinv_of(h, l, dummy);
     spmm(h->P[l], X[l + 1], q, X[l], true, st);
+    if (gs) {
+      // colours descending after the coarse correction (a symmetric cycle)
+      for (int s = 0; s < post; ++s) gs_sweep(h, l, B[l], X[l], q, true, st);
+      if (to_v && l == k) {
+        if constexpr (std::is_same<T, float>::value)
+          if (xadd) axpy(xadd, h->sizes[l] * q, X[l], st);
+        add_to_v(U, X[l], static_cast<int>(h->sizes[l]), w->qt, q, V, st);
+      }
+      continue;
+    }
     for (int s = 0; s < post; ++s) {
       if (to_v && l == k && s == post - 1) {
         if constexpr (std::is_same<T, float>::value)
@@ -697,7 +795,8 @@ int defect(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, 
 int check_options(const amgeig_options& o) {
   if (o.max_corrections < 0 || o.v_cycles < 1 || o.pre_sweeps < 0 || o.post_sweeps < 0 || o.q_extra < 0 ||
       o.fixed_corrections < 0 || o.coarse_modes < 0 ||
-      (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32))
+      (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32) ||
+      (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -714,6 +813,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   rc = ensure_workspace(h, qt, o.precision, std::max(1, o.v_cycles));
   if (rc) return rc;
   SolveWork* w = h->ws.get();
+  w->smoother = o.smoother;
+  if (o.smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL) {
+    rc = ensure_gs(h, st);
+    if (rc) return rc;
+  }
   // step 1: initial eigenpairs on level n1 = n (the coarsest)
   if (o.precision == AMGEIG_FP64)
     launch_copy_cols(h->Z, h->dn, h->dn, qt, w->U, st);
@@ -935,6 +1039,7 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->precision = AMGEIG_FP64;
   opt->fixed_corrections = 0;
   opt->coarse_modes = 0;
+  opt->smoother = AMGEIG_SMOOTHER_L1_JACOBI;
 }
 
 const char* amgeig_strerror(int code) {
@@ -1287,6 +1392,11 @@ int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_o
   rc = ensure_workspace(h, width, o.precision, 1);
   if (rc) return rc;
   SolveWork* w = h->ws.get();
+  w->smoother = o.smoother;
+  if (o.smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL) {
+    rc = ensure_gs(h, st);
+    if (rc) return rc;
+  }
   const long long cnt = h->sizes[level] * static_cast<long long>(width);
   if (level == h->nlev - 1) {
     // the coarsest level: the exact solve

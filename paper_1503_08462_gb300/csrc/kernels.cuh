@@ -80,6 +80,14 @@ void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st)
 
 // float64 -> float32 / float32 -> float64 copies
 void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st);
+// One colour of a multicolour Gauss-Seidel sweep: the cnt rows listed in `rows`
+// (no two adjacent) update x_i += (b_i - sum_j a_ij x_j) * dinv_i on w columns of
+// row-major blocks with row stride ld.  `bytes` is the launch's share of the
+// sweep's algorithmic traffic.
+void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const double* dinv, const double* b, double* x,
+                      int ld, int w, double bytes, cudaStream_t st);
+void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const float* dinv, const float* b, float* x, int ld,
+                      int w, double bytes, cudaStream_t st);
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st);
 
 // ---- float-float kernels of the mixed path (spmm_df.cu) -------------------

@@ -639,6 +639,27 @@ int grid_for(long long count) {
   return static_cast<int>(b < 1 ? 1 : b);
 }
 
+// ---------------------------------------------------------------- Gauss-Seidel
+// One colour of a multicolour Gauss-Seidel sweep.  Rows of one colour share no
+// nonzero, so they update together from the current x of the other colours:
+// x_i <- x_i + (b_i - sum_j a_ij x_j) / a_ii (the j = i term included in the sum).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gs_colour(int cnt, const int* __restrict__ rows,
+                                                        const int* __restrict__ rp, const int* __restrict__ ci,
+                                                        const T* __restrict__ a, const T* __restrict__ dinv,
+                                                        const T* __restrict__ b, T* x, int ld, int w) {
+  const long long total = static_cast<long long>(cnt) * w;
+  for (long long it = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; it < total;
+       it += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = rows[it / w], c = static_cast<int>(it % w);
+    const long long o = static_cast<long long>(i) * ld + c;
+    T s = b[o];
+    const int p1 = rp[i + 1];
+    for (int p = rp[i]; p < p1; ++p) s -= a[p] * x[static_cast<long long>(ci[p]) * ld + c];
+    x[o] += s * dinv[i];
+  }
+}
+
 }  // namespace
 
 void launch_defect_f64(const DevCsr& AM, const double* U, int q, const double* lam, double* R, double* partials,
@@ -874,6 +895,21 @@ void launch_add_to_vdf(const float2* U, const float* x, int rows, int q, int ldx
   const long long count = static_cast<long long>(rows) * q;
   ProfScope ps(st, P_SMOOTH, 20.0 * count, 1.0 * count);
   k_add_to_vdf<<<grid_for(count), kThreads, 0, st>>>(U, x, rows, q, ldx, V);
+}
+
+void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const double* dinv, const double* b, double* x,
+                      int ld, int w, double bytes, cudaStream_t st) {
+  if (cnt <= 0) return;
+  ProfScope ps(st, P_SMOOTH, bytes, 2.0 * w * cnt * (static_cast<double>(A.nnz) / A.rows));
+  k_gs_colour<double><<<grid_for(static_cast<long long>(cnt) * w), kThreads, 0, st>>>(cnt, rows, A.rp, A.ci, A.v64,
+                                                                                      dinv, b, x, ld, w);
+}
+void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const float* dinv, const float* b, float* x, int ld,
+                      int w, double bytes, cudaStream_t st) {
+  if (cnt <= 0) return;
+  ProfScope ps(st, P_SMOOTH, bytes, 2.0 * w * cnt * (static_cast<double>(A.nnz) / A.rows));
+  k_gs_colour<float><<<grid_for(static_cast<long long>(cnt) * w), kThreads, 0, st>>>(cnt, rows, A.rp, A.ci, A.v32,
+                                                                                     dinv, b, x, ld, w);
 }
 
 }  // namespace amgeig
