@@ -1148,87 +1148,62 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
     }
   }
   // composite prolongations I_n^k (coarsest -> level k) for the recombination:
-  // PC[n-2] = P_{n-2}, PC[k] = P_k PC[k+1] (row-wise sparse products in float64)
+  // PC[n-2] = P_{n-2}, PC[k] = P_k PC[k+1] -- sparse products with d_n columns,
+  // built on the GPU level by level (count pass, row offsets, fill pass) in
+  // float64 and kept as float-float pairs
   h->PC.resize(n > 1 ? n - 1 : 0);
-  {
-    HostCsr next;
-    for (int k = n - 2; k >= 0; --k) {
-      const CsrView& Pk = prolong[k];
-      HostCsr C;
-      C.rows = Pk.rows;
-      C.cols = h->dn;
-      C.rp.assign(static_cast<size_t>(Pk.rows) + 1, 0);
-      // rows in contiguous slices, one per host thread, then concatenated in order
-      const int T = host_threads(Pk.rows);
-      std::vector<std::vector<int32_t>> pci(T), pcnt(T);
-      std::vector<std::vector<double>> pa(T);
-      parallel_for(T, [&](int t) {
-        const int64_t lo = Pk.rows * t / T, hi = Pk.rows * (t + 1) / T;
-        std::vector<double> acc(static_cast<size_t>(h->dn), 0.0);
-        std::vector<int32_t> mark(static_cast<size_t>(h->dn), -1), cols;
-        pcnt[t].resize(static_cast<size_t>(hi - lo));
-        for (int64_t i = lo; i < hi; ++i) {
-          cols.clear();
-          for (int32_t p = Pk.rp[i]; p < Pk.rp[i + 1]; ++p) {
-            const int32_t tc = Pk.ci[p];
-            const double v = Pk.a[p];
-            if (k == n - 2) {
-              if (mark[tc] != static_cast<int32_t>(i)) {
-                mark[tc] = static_cast<int32_t>(i);
-                acc[tc] = 0.0;
-                cols.push_back(tc);
-              }
-              acc[tc] += v;
-              continue;
-            }
-            for (int32_t r = next.rp[tc]; r < next.rp[tc + 1]; ++r) {
-              const int32_t c = next.ci[r];
-              if (mark[c] != static_cast<int32_t>(i)) {
-                mark[c] = static_cast<int32_t>(i);
-                acc[c] = 0.0;
-                cols.push_back(c);
-              }
-              acc[c] += v * next.a[r];
-            }
-          }
-          std::sort(cols.begin(), cols.end());
-          for (int32_t c : cols) {
-            pci[t].push_back(c);
-            pa[t].push_back(acc[c]);
-          }
-          pcnt[t][static_cast<size_t>(i - lo)] = static_cast<int32_t>(cols.size());
-        }
-      });
-      size_t total = 0;
-      for (int t = 0; t < T; ++t) total += pci[t].size();
-      C.ci.reserve(total);
-      C.a.reserve(total);
-      int64_t row = 0;
-      for (int t = 0; t < T; ++t) {
-        for (int32_t c : pcnt[t]) {
-          C.rp[static_cast<size_t>(row) + 1] = C.rp[static_cast<size_t>(row)] + c;
-          ++row;
-        }
-        C.ci.insert(C.ci.end(), pci[t].begin(), pci[t].end());
-        C.a.insert(C.a.end(), pa[t].begin(), pa[t].end());
+  if (n > 1) {
+    const int dn0 = h->dn;
+    // PC[n-1] = I (the identity on the coarsest level) starts the recursion
+    std::vector<int32_t> irp(static_cast<size_t>(dn0) + 1), ici(static_cast<size_t>(dn0));
+    for (int i = 0; i <= dn0; ++i) irp[i] = i;
+    for (int i = 0; i < dn0; ++i) ici[i] = i;
+    std::vector<double> iv(static_cast<size_t>(dn0), 1.0);
+    int *nrp = nullptr, *nci = nullptr;
+    double* nv = nullptr;
+    CK(m.upload(&nrp, irp));
+    CK(m.upload(&nci, ici));
+    // float64 values of the level below (freed once the next level is built) and of this level
+    struct DeviceTemp {
+      double* p = nullptr;
+      ~DeviceTemp() {
+        if (p) cudaFree(p);
       }
+    } prev, cur;
+    CK(cudaMalloc(&prev.p, sizeof(double) * iv.size()));
+    CK(cudaMemcpyAsync(prev.p, iv.data(), sizeof(double) * iv.size(), cudaMemcpyHostToDevice, h->stream));
+    nv = prev.p;
+    int* counts = nullptr;
+    CK(m.alloc(&counts, static_cast<size_t>(h->sizes[0])));
+    for (int k = n - 2; k >= 0; --k) {
+      const DevCsr& P = h->P[k];
       DevCsr& D = h->PC[k];
-      D.rows = static_cast<int>(C.rows);
-      D.cols = static_cast<int>(C.cols);
-      D.nnz = static_cast<int>(C.ci.size());
-      std::vector<float2> v2(C.a.size());
-      const int64_t nv = static_cast<int64_t>(C.a.size());
-      const int T2 = host_threads(nv);
-      parallel_for(T2, [&](int t) {
-        for (int64_t i = nv * t / T2; i < nv * (t + 1) / T2; ++i) {
-          const float hi = static_cast<float>(C.a[i]);
-          v2[i] = make_float2(hi, static_cast<float>(C.a[i] - static_cast<double>(hi)));
-        }
-      });
-      CK(m.upload(&D.rp, C.rp));
-      CK(m.upload(&D.ci, C.ci));
-      CK(m.upload(&D.d2, v2));
-      next = std::move(C);
+      D.rows = P.rows;
+      D.cols = dn0;
+      launch_composite_rows(P, nrp, nci, nv, dn0, nullptr, counts, nullptr, nullptr, h->stream);
+      std::vector<int32_t> cnt(static_cast<size_t>(P.rows)), rp(static_cast<size_t>(P.rows) + 1, 0);
+      CK(cudaMemcpyAsync(cnt.data(), counts, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      int64_t total = 0;
+      for (int64_t i = 0; i < P.rows; ++i) {
+        total += cnt[static_cast<size_t>(i)];
+        if (total >= (1LL << 31)) return fail(AMGEIG_ENOMEM, "composite prolongation too large");
+        rp[static_cast<size_t>(i) + 1] = static_cast<int32_t>(total);
+      }
+      D.nnz = static_cast<int>(total);
+      CK(m.upload(&D.rp, rp));
+      CK(m.alloc(&D.ci, static_cast<size_t>(total)));
+      CK(cudaMalloc(&cur.p, sizeof(double) * std::max<int64_t>(total, 1)));
+      launch_composite_rows(P, nrp, nci, nv, dn0, D.rp, nullptr, D.ci, cur.p, h->stream);
+      CK(m.alloc(&D.d2, static_cast<size_t>(total)));
+      launch_f64_to_df(cur.p, total, D.d2, h->stream);
+      CK(cudaStreamSynchronize(h->stream));
+      CK(cudaFree(prev.p));
+      prev.p = cur.p;
+      cur.p = nullptr;
+      nrp = D.rp;
+      nci = D.ci;
+      nv = prev.p;
     }
   }
   // dense coarsest pencil and its eigendecomposition

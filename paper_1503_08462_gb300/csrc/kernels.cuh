@@ -80,6 +80,11 @@ void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st)
 
 // float64 -> float32 / float32 -> float64 copies
 void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st);
+// One level of the composite prolongation I_n^k = P_k I_n^{k+1} (next: CSR with
+// d_n columns, float64 values).  out_rp null: counts[i] = nonzeros of row i;
+// otherwise rows i fill out_ci / out_v from out_rp[i] in column order.
+void launch_composite_rows(const DevCsr& P, const int* nrp, const int* nci, const double* nv, int dn,
+                           const int* out_rp, int* counts, int* out_ci, double* out_v, cudaStream_t st);
 // One colour of a multicolour Gauss-Seidel sweep: the cnt rows listed in `rows`
 // (no two adjacent) update x_i += (b_i - sum_j a_ij x_j) * dinv_i on w columns of
 // row-major blocks with row stride ld.  `bytes` is the launch's share of the

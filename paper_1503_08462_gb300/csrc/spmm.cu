@@ -14,6 +14,7 @@
 //   transfers    restriction R_l = P_l^T and prolongation P_l (Sec. 2.3)
 //   augmentation A_k V and M_k V for the pencil of Algorithm 3.1 step 2
 //   recombine    u_j = I_n^k x_j(1:d_n) + V x_j(d_n+1:d_n+q)
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -660,6 +661,61 @@ __global__ void __launch_bounds__(kThreads) k_gs_colour(int cnt, const int* __re
   }
 }
 
+// ---------------------------------------------------------------- composite prolongation
+// One level of I_n^k = P_k I_n^{k+1} (a sparse product with d_n columns), one warp
+// per row: the row's entries accumulate into a dense d_n-wide float64 row in
+// shared memory (flags mark the structural nonzeros), then come out in column
+// order.  With out_rp null the pass only counts each row's nonzeros.  Each column
+// receives its terms in the order of the row of P_k, as a row-by-row host product
+// would add them.
+__global__ void __launch_bounds__(kThreads) k_pc_rows(int rows, const int* __restrict__ prp,
+                                                      const int* __restrict__ pci, const double* __restrict__ pv,
+                                                      const int* __restrict__ nrp, const int* __restrict__ nci,
+                                                      const double* __restrict__ nv, int dn,
+                                                      const int* __restrict__ out_rp, int* __restrict__ counts,
+                                                      int* __restrict__ out_ci, double* __restrict__ out_v) {
+  extern __shared__ __align__(16) unsigned char pcs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  double* acc = reinterpret_cast<double*>(pcs) + static_cast<size_t>(warp) * dn;
+  unsigned char* flag = pcs + static_cast<size_t>(wpb) * dn * sizeof(double) + static_cast<size_t>(warp) * dn;
+  for (int c = lane; c < dn; c += 32) {
+    flag[c] = 0;
+    acc[c] = 0.0;
+  }
+  __syncwarp();
+  for (int row = blockIdx.x * wpb + warp; row < rows; row += gridDim.x * wpb) {
+    const int p1 = prp[row + 1];
+    for (int p = prp[row]; p < p1; ++p) {
+      const int t = pci[p];
+      const double v = pv[p];
+      for (int r = nrp[t] + lane; r < nrp[t + 1]; r += 32) {
+        const int c = nci[r];  // distinct within one row of I_n^{k+1}
+        flag[c] = 1;
+        acc[c] += v * nv[r];
+      }
+      __syncwarp();
+    }
+    int base = out_rp ? out_rp[row] : 0;
+    for (int c0 = 0; c0 < dn; c0 += 32) {
+      const int c = c0 + lane;
+      const bool on = c < dn && flag[c];
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on && out_rp) {
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        out_ci[pos] = c;
+        out_v[pos] = acc[c];
+      }
+      base += __popc(m);
+      if (c < dn) {
+        flag[c] = 0;
+        acc[c] = 0.0;
+      }
+    }
+    if (!out_rp && lane == 0) counts[row] = base;
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 void launch_defect_f64(const DevCsr& AM, const double* U, int q, const double* lam, double* R, double* partials,
@@ -910,6 +966,19 @@ void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const float* di
   ProfScope ps(st, P_SMOOTH, bytes, 2.0 * w * cnt * (static_cast<double>(A.nnz) / A.rows));
   k_gs_colour<float><<<grid_for(static_cast<long long>(cnt) * w), kThreads, 0, st>>>(cnt, rows, A.rp, A.ci, A.v32,
                                                                                      dinv, b, x, ld, w);
+}
+
+void launch_composite_rows(const DevCsr& P, const int* nrp, const int* nci, const double* nv, int dn,
+                           const int* out_rp, int* counts, int* out_ci, double* out_v, cudaStream_t st) {
+  if (P.rows <= 0) return;
+  // warps per block: the dense rows (9 bytes per column) within 96 KB of shared memory
+  const int wpb = std::max(1, std::min(8, static_cast<int>((96 * 1024) / (9 * static_cast<size_t>(dn)))));
+  const size_t sm = static_cast<size_t>(wpb) * dn * 9;
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_pc_rows), sm);
+  int blocks = ceil_div(P.rows, wpb);
+  if (blocks > 8 * kNumSms) blocks = 8 * kNumSms;
+  ProfScope ps(st, P_OTHER, 4.0 * P.rows + 12.0 * P.nnz, 0.0);
+  k_pc_rows<<<blocks, 32 * wpb, sm, st>>>(P.rows, P.rp, P.ci, P.v64, nrp, nci, nv, dn, out_rp, counts, out_ci, out_v);
 }
 
 }  // namespace amgeig
