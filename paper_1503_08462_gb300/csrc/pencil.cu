@@ -713,8 +713,12 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
 
   // ---- back-transformation y = H_0 H_1 ... H_{n-3} z ------------------------
   // v_k (column k of W below the diagonal) is staged in shared memory once per
-  // step; each thread then owns whole columns of Z, so its row walks are
-  // coalesced across the threads of a warp
+  // step.  Each column of Z is split over S consecutive lanes (S = 1..8 threads
+  // per column, as many as the block holds): lane seg takes rows seg, seg + S, ...,
+  // the partial products meet in a shuffle tree, and the same lanes apply the
+  // update -- row walks stay coalesced across columns and each chain is m / S long.
+  int S = 1;
+  while (S < 8 && 2 * S * nwant <= nt) S <<= 1;
   for (int k = n - 3; k >= 0; --k) {
     const df t = tau[k];
     if (t.hi == 0.f) continue;
@@ -722,22 +726,31 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     for (int i = tid; i < m; i += nt) v[i] = W[(k + 1 + i) * LD + k];
     __syncthreads();
     // for each column c: s_c = v^T z[k+1:, c]; z[k+1:, c] -= t s_c v
-    for (int c = tid; c < nwant; c += nt) {
+    const int total = nwant * S;
+    for (int base = warp * 32; base < total; base += nt) {
+      const int it = base + lane;
+      const bool valid = it < total;
+      const int c = valid ? it / S : 0, seg = it % S;
       df* zc = Zn + static_cast<long long>(k + 1) * NW + c;
       df_acc s0 = acc_zero(), s1 = acc_zero(), s2 = acc_zero(), s3 = acc_zero();
-      int i = 0;
-      for (; i + 4 <= m; i += 4) {
-        s0.fma(v[i], zc[i * NW]);
-        s1.fma(v[i + 1], zc[(i + 1) * NW]);
-        s2.fma(v[i + 2], zc[(i + 2) * NW]);
-        s3.fma(v[i + 3], zc[(i + 3) * NW]);
+      if (valid) {
+        int i = seg;
+        for (; i + 3 * S < m; i += 4 * S) {
+          s0.fma(v[i], zc[i * NW]);
+          s1.fma(v[i + S], zc[(i + S) * NW]);
+          s2.fma(v[i + 2 * S], zc[(i + 2 * S) * NW]);
+          s3.fma(v[i + 3 * S], zc[(i + 3 * S) * NW]);
+        }
+        for (; i < m; i += S) s0.fma(v[i], zc[i * NW]);
       }
-      for (; i < m; ++i) s0.fma(v[i], zc[i * NW]);
       s0.merge(s1);
       s2.merge(s3);
       s0.merge(s2);
-      const df f = df_mul(t, s0.value());
-      for (i = 0; i < m; ++i) zc[i * NW] = df_sub(zc[i * NW], df_mul(f, v[i]));
+      for (int o = 1; o < S; o <<= 1) s0.merge(shfl_xor_acc(s0, o));
+      if (valid) {
+        const df f = df_mul(t, s0.value());
+        for (int i = seg; i < m; i += S) zc[i * NW] = df_sub(zc[i * NW], df_mul(f, v[i]));
+      }
     }
     __syncthreads();
   }
