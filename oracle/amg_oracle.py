@@ -76,6 +76,7 @@ class OracleHierarchy:
     An: np.ndarray  # dense coarsest A
     Mn: np.ndarray  # dense coarsest M
     An_chol: tuple  # scipy cho_factor of An
+    colour_cache: dict = dataclasses.field(default_factory=dict)  # level -> Gauss-Seidel colours
 
     @property
     def n_levels(self) -> int:
@@ -167,14 +168,11 @@ def greedy_colours(A: sp.csr_matrix) -> np.ndarray:
     return colour
 
 
-_COLOURS = {}
-
-
 def colours(h: OracleHierarchy, l: int) -> np.ndarray:
-    key = (id(h), l)
-    if key not in _COLOURS:
-        _COLOURS[key] = greedy_colours(h.A[l])
-    return _COLOURS[key]
+    """The colouring of level l, computed once per hierarchy."""
+    if l not in h.colour_cache:
+        h.colour_cache[l] = greedy_colours(h.A[l])
+    return h.colour_cache[l]
 
 
 def gauss_seidel(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray, descending: bool = False) -> np.ndarray:
