@@ -327,6 +327,10 @@ struct amgeig_hierarchy_t {
   std::vector<DevCsr> PC;    // PC[k] = I_n^k = P_k ... P_{n-2} (rows_k x d_n), float-float values
   int dn = 0;
   double *An = nullptr, *Mn = nullptr, *Z = nullptr, *theta = nullptr, *Ainv = nullptr;
+  // the coarse eigenbasis is computed on demand: modes_ready leading columns of
+  // Z (and theta) are valid; cpw keeps the M_n factor and the solver's scratch
+  int modes_ready = 0;
+  PencilWork* cpw = nullptr;
   float* Ainv32 = nullptr;
   float2* Zdf = nullptr;  // Z as float-float pairs
   int* dstatus = nullptr;
@@ -698,6 +702,7 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
 
 amgeig_hierarchy_t::~amgeig_hierarchy_t() {
   ws.reset();
+  pencil_work_destroy(cpw);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -801,6 +806,17 @@ int check_options(const amgeig_options& o) {
   return AMGEIG_OK;
 }
 
+// The leading `need` eigenpairs of the coarsest pencil (computed again, all of
+// them, when a solve asks for more than are ready).  Under the hierarchy's lock.
+int ensure_modes(amgeig_hierarchy_t* h, int need, cudaStream_t st) {
+  if (need <= h->modes_ready) return AMGEIG_OK;
+  launch_coarse_modes(h->cpw, h->dn, need, h->An, h->Z, h->theta, st);
+  launch_f64_to_df(h->Z, static_cast<long long>(h->dn) * h->dn, h->Zdf, st);
+  CK(cudaGetLastError());
+  h->modes_ready = need;
+  return AMGEIG_OK;
+}
+
 // Algorithm 3.2 on the hierarchy's stream; results stay in the workspace.
 int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o, amgeig_info* info,
                std::vector<double>& relres_host, cudaStream_t st) {
@@ -816,6 +832,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   w->smoother = o.smoother;
   if (o.smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL) {
     rc = ensure_gs(h, st);
+    if (rc) return rc;
+  }
+  {
+    const int modes = (o.coarse_modes > 0 && o.coarse_modes < h->dn) ? o.coarse_modes : h->dn;
+    rc = ensure_modes(h, std::max(modes, qt), st);
     if (rc) return rc;
   }
   // step 1: initial eigenpairs on level n1 = n (the coarsest)
@@ -1224,16 +1245,16 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   CK(m.alloc(&h->dstatus, 4));
   CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
   cudaError_t e;
-  PencilWork* pw = pencil_work_create(dn, 1, &e);
-  if (!pw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
-  launch_coarse_eigh(pw, dn, h->An, h->Mn, h->Z, h->theta, h->Ainv, h->dstatus, h->stream);
+  h->cpw = pencil_work_create(dn, 1, &e);
+  if (!h->cpw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
+  // the exact coarsest solve of the V-cycle (float64 Cholesky); the eigenbasis
+  // waits for the first solve, which asks for as many modes as it needs
+  launch_coarse_inverse(h->cpw, dn, h->An, h->Mn, h->Ainv, h->dstatus, h->stream);
   launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, h->stream);
   CK(m.alloc(&h->Zdf, static_cast<size_t>(dn) * dn));
-  launch_f64_to_df(h->Z, static_cast<long long>(dn) * dn, h->Zdf, h->stream);
   int stt = 0;
   cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
-  pencil_work_destroy(pw);
   CK(e1);
   CK(e2);
   CK(cudaGetLastError());

@@ -160,13 +160,6 @@ __global__ void __launch_bounds__(256) k_sum_partials_wide(const double* __restr
   if (threadIdx.x == 0) out[j] = sh[0];
 }
 
-__global__ void k_eye_minus(int n, double* __restrict__ T) {
-  const long long total = static_cast<long long>(n) * n;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x)
-    T[i] = ((i / n) == (i % n) ? 1.0 : 0.0) - T[i];
-}
-
 __global__ void k_relres(const double* __restrict__ sums, const double* __restrict__ lam, int q,
                          double* __restrict__ relres, int* __restrict__ flags) {
   for (int j = threadIdx.x; j < q; j += blockDim.x) {
@@ -278,18 +271,6 @@ void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, c
   long long b = (total + 255) / 256;
   if (b > 8 * kNumSms) b = 8 * kNumSms;
   k_copy_cols<<<static_cast<int>(b), 256, 0, st>>>(src, rows, ld, q, dst);
-}
-
-// One Newton-Schulz step X <- X (2I - A X) for an approximate inverse X of A
-// (n x n, row-major); T and Y are n x n scratch.  Squares the residual I - A X.
-void launch_newton_schulz(int n, const double* A, double* X, double* T, double* Y, cudaStream_t st) {
-  launch_gemm_f64(n, n, n, 1.0, A, n, false, X, n, false, 0.0, T, n, st, P_PENCIL);
-  {
-    ProfScope ps(st, P_PENCIL, 16.0 * n * n, 0.0);
-    k_eye_minus<<<ceil_div(static_cast<long long>(n) * n, 256), 256, 0, st>>>(n, T);
-  }
-  cudaMemcpyAsync(Y, X, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
-  launch_gemm_f64(n, n, n, 1.0, Y, n, false, T, n, false, 1.0, X, n, st, P_PENCIL);
 }
 
 }  // namespace amgeig

@@ -145,8 +145,6 @@ void launch_gram(int rows, const double* V, int q, const double* W, int w, doubl
 void launch_gram_strided(int rows, const double* V, int ldv, int q, const double* W, int ldw, int w, double* scratch,
                          double* G, cudaStream_t st, bool df_arith = false);
 
-// One Newton-Schulz step X <- X (2I - A X) (n x n row-major; T, Y scratch)
-void launch_newton_schulz(int n, const double* A, double* X, double* T, double* Y, cudaStream_t st);
 
 // Sum `nparts` partial rows of length `len` in fixed order: out[j] = sum_b part[b*len + j]
 void launch_sum_partials(const double* part, int nparts, int len, double* out, cudaStream_t st);
@@ -181,11 +179,19 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
                          const double* G, const float2* Zdf, const double* theta, double* mu, double* Xc,
                          float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback = nullptr);
 
-// Full eigendecomposition of the coarsest pencil (A_n, M_n), both dn x dn
-// dense row-major: Z (dn x dn) with Z^T M_n Z = I, Z^T A_n Z = diag(theta),
-// theta ascending; also Ainv = A_n^-1 = Z diag(1/theta) Z^T.  status as above.
-void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,
-                        double* Ainv, int* status, cudaStream_t st);
+// The coarsest level's exact solve: Ainv = A_n^-1 (dn x dn, row-major) from
+// the float64 Cholesky factor A_n = L L^T as L^-T L^-1; status = ENOTSPD when
+// A_n is not positive definite.  Also factors M_n = L_m L_m^T into the
+// workspace (its Cholesky is the check that M_n is positive definite and the
+// first step of launch_coarse_modes).
+void launch_coarse_inverse(PencilWork* w, int dn, const double* An, const double* Mn, double* Ainv, int* status,
+                           cudaStream_t st);
+// The nwant lowest eigenpairs of the coarsest pencil (A_n, M_n) (needs the
+// M_n factor of launch_coarse_inverse in the same workspace): the first nwant
+// columns of Z (dn x dn row-major, stride dn) with Z^T M_n Z = I and
+// Z^T A_n Z = diag(theta), theta ascending.
+void launch_coarse_modes(PencilWork* w, int dn, int nwant, const double* An, double* Z, double* theta,
+                         cudaStream_t st);
 
 // Symmetric eigensolver in float-float: the `nwant` smallest eigenpairs of the
 // symmetric n x n row-major float64 matrix H.  evals (nwant), evecs (n x nwant

@@ -2109,6 +2109,13 @@ __global__ void k_transpose_sym(int n, const double* __restrict__ X, double* __r
   }
 }
 
+__global__ void k_identity(int n, double* __restrict__ X) {
+  const long long N = n;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N * N;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    X[i] = (i / N == i % N) ? 1.0 : 0.0;
+}
+
 __global__ void k_transpose(int rows, int cols, const double* __restrict__ X, double* __restrict__ Y) {
   const long long total = static_cast<long long>(rows) * cols;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
@@ -2116,14 +2123,6 @@ __global__ void k_transpose(int rows, int cols, const double* __restrict__ X, do
     const int r = static_cast<int>(i / cols), c = static_cast<int>(i % cols);
     Y[static_cast<long long>(c) * rows + r] = X[i];
   }
-}
-
-__global__ void k_scale_cols_inv(int rows, int cols, const double* __restrict__ Z, const double* __restrict__ th,
-                                 double* __restrict__ out) {
-  const long long total = static_cast<long long>(rows) * cols;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x)
-    out[i] = Z[i] / th[i % cols];
 }
 
 size_t syev_smem_base(int n, int nwant) {
@@ -2294,27 +2293,33 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   }
 }
 
-void launch_coarse_eigh(PencilWork* w, int dn, const double* An, const double* Mn, double* Z, double* theta,
-                        double* Ainv, int* status, cudaStream_t st) {
-  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 0.0, 7);
-  // M_n = L L^T
+void launch_coarse_inverse(PencilWork* w, int dn, const double* An, const double* Mn, double* Ainv, int* status,
+                           cudaStream_t st) {
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 5, 2.0 * dn * dn * dn, 4);
+  // M_n = L_m L_m^T (kept for the eigenbasis); A_n = L L^T
   k_chol<<<1, 1024, 0, st>>>(dn, Mn, w->Lm, status);
-  // Hs = L^-1 A_n L^-T : X = L^-1 A_n ; Hs = L^-1 X^T
+  k_chol<<<1, 1024, 0, st>>>(dn, An, w->Hs, status);
+  // H = L^-1 (the identity solved in place), Ainv = H^T H = L^-T L^-1
+  k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->H);
+  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Hs, w->H, dn, dn, 0);
+  launch_gemm_f64(dn, dn, dn, 1.0, w->H, dn, true, w->H, dn, false, 0.0, Ainv, dn, st);
+}
+
+void launch_coarse_modes(PencilWork* w, int dn, int nwant, const double* An, double* Z, double* theta,
+                         cudaStream_t st) {
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 0.0, 6);
+  // Hs = L_m^-1 A_n L_m^-T : X = L_m^-1 A_n ; Hs = L_m^-1 X^T
   cudaMemcpyAsync(w->Hs, An, sizeof(double) * dn * dn, cudaMemcpyDeviceToDevice, st);
   k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, w->Hs, dn, dn, 0);
   k_transpose<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, dn, w->Hs, w->H);
   k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, w->H, dn, dn, 0);
   k_transpose_sym<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->H, w->Hs);
-  // eigenpairs of Hs (all dn)
-  launch_syev_df(w, dn, dn, w->Hs, theta, Z, st);
-  // Z = L^-T Y
-  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, Z, dn, dn, 1);
-  // Ainv = Z diag(1/theta) Z^T
-  k_scale_cols_inv<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, dn, Z, theta, w->H);
-  launch_gemm_f64(dn, dn, dn, 1.0, w->H, dn, false, Z, dn, true, 0.0, Ainv, dn, st);
-  // two Newton-Schulz steps bring the float-float-derived inverse to float64 accuracy
-  launch_newton_schulz(dn, An, Ainv, w->Hs, w->H, st);
-  launch_newton_schulz(dn, An, Ainv, w->Hs, w->H, st);
+  // the nwant lowest eigenpairs of Hs (dn x nwant into Yh), placed as Z's first columns
+  launch_syev_df(w, dn, nwant, w->Hs, theta, w->Yh, st);
+  cudaMemcpy2DAsync(Z, sizeof(double) * dn, w->Yh, sizeof(double) * nwant, sizeof(double) * nwant, dn,
+                    cudaMemcpyDeviceToDevice, st);
+  // Z = L_m^-T Y on those columns
+  k_trsm<<<ceil_div(nwant, 8), 256, 0, st>>>(dn, w->Lm, Z, dn, nwant, 1);
 }
 
 }  // namespace amgeig
