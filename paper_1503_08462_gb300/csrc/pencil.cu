@@ -241,37 +241,27 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
       for (int i = tid; i < m; i += nt) p[i] = df_sub(p[i], df_mul(kc, v[i]));  // w
     }
     __syncthreads();  // (3) w complete
-    // W22 -= v w^T + w v^T (lower triangle computed, mirrored); lane 0 of each
-    // row also accumulates the next column's norm (rows 2.. of the trailing block)
+    // W22 -= v w^T + w v^T over whole rows (coalesced; no mirrored column writes):
+    // entry (r, c) takes its two products in the order of (max, min), so both
+    // triangles stay bitwise equal.  Lane 0 of each row also accumulates the next
+    // column's norm (rows 2.. of the trailing block)
     {
       df_acc sg = acc_zero();
       for (int i = warp; i < m; i += nw) {
         const df vi = v[i], wi = p[i];
         df* rowi = W + (k + 1 + i) * LD + (k + 1);
-        int j = lane;
-        for (; j + 32 <= i; j += 64) {
-          const df a0 = rowi[j], a1 = rowi[j + 32];
-          const df pj0 = p[j], vj0 = v[j], pj1 = p[j + 32], vj1 = v[j + 32];
-          df_acc u0 = acc_zero(), u1 = acc_zero();
-          u0.fma(vi, pj0);
-          u1.fma(vi, pj1);
-          u0.fma(wi, vj0);
-          u1.fma(wi, vj1);
-          const df n0 = df_sub(a0, u0.value());
-          const df n1 = df_sub(a1, u1.value());
-          rowi[j] = n0;
-          rowi[j + 32] = n1;
-          W[(k + 1 + j) * LD + (k + 1 + i)] = n0;
-          W[(k + 1 + j + 32) * LD + (k + 1 + i)] = n1;
-          if (j == 0 && i >= 2) sg.fma(n0, n0);
-        }
-        if (j <= i) {
+#pragma unroll 2
+        for (int j = lane; j < m; j += 32) {
           df_acc u0 = acc_zero();
-          u0.fma(vi, p[j]);
-          u0.fma(wi, v[j]);
+          if (j <= i) {
+            u0.fma(vi, p[j]);
+            u0.fma(wi, v[j]);
+          } else {
+            u0.fma(v[j], wi);
+            u0.fma(p[j], vi);
+          }
           const df n0 = df_sub(rowi[j], u0.value());
           rowi[j] = n0;
-          W[(k + 1 + j) * LD + (k + 1 + i)] = n0;
           if (j == 0 && i >= 2) sg.fma(n0, n0);
         }
       }
