@@ -4,10 +4,11 @@
 // a pencil of size d_n + q, and Algorithm 3.2 step 1 solves (A_n, M_n).  The
 // paper treats these as black boxes (ARPACK, Sec. 4.1).  Here:
 //
-// * (A_n, M_n) is decomposed once per hierarchy: M_n = L L^T, H = L^-1 A_n L^-T,
-//   H = Y Theta Y^T, Z = L^-T Y.  Then Z^T M_n Z = I and Z^T A_n Z = Theta, which
-//   gives step 1 of Algorithm 3.2 (the q smallest columns of Z) and the exact
-//   coarsest-level solve A_n^-1 = Z Theta^-1 Z^T of the V-cycle.
+// * The coarsest level: at load A_n = L L^T gives the V-cycle's exact solve
+//   A_n^-1 = L^-T L^-1 (float64); M_n = L_m L_m^T, H = L_m^-1 A_n L_m^-T,
+//   H = Y Theta Y^T, Z = L_m^-T Y gives, for as many leading modes as a solve
+//   needs, Z^T M_n Z = I and Z^T A_n Z = Theta: step 1 of Algorithm 3.2 (the q
+//   smallest columns of Z) and the coarse modes of the pencil below.
 // * Each correction's pencil is written in the basis [I_n^k Z_m, V - I_n^k Z_m B]
 //   (block Gram-Schmidt of V against the first m coarse modes) with
 //   K = Z_m^T I_k^n A_k V, B = Z_m^T I_k^n M_k V: it becomes
@@ -22,12 +23,13 @@
 //   only better conditioned, and everything runs in float-float.
 // * The symmetric eigenproblem is solved in float-float (48-bit significand)
 //   by one 1024-thread block: Householder tridiagonalisation, bisection with
-//   Sturm counts for the wanted eigenvalues (float32), inverse iteration with
-//   partial pivoting in float-float (Gram-Schmidt inside clusters of nearly
-//   equal shifts), a Rayleigh-Ritz clean-up of the wanted vectors by parallel
-//   cyclic Jacobi, and back-transformation.  References: Golub & Van Loan,
-//   Matrix Computations, 4th ed., 8.3 (tridiagonalisation), 8.4.1 (Sturm
-//   bisection), 8.2.2 (inverse iteration), 8.5 (Jacobi).
+//   Sturm counts for the wanted eigenvalues (float32), each shift refined by
+//   float-float Sturm multisection, inverse iteration with partial pivoting in
+//   float-float (Gram-Schmidt inside clusters of nearly equal shifts), a
+//   Rayleigh-Ritz clean-up by parallel cyclic Jacobi on each group of close
+//   shifts, and back-transformation.  References: Golub & Van Loan, Matrix
+//   Computations, 4th ed., 8.3 (tridiagonalisation), 8.4.1 (Sturm bisection),
+//   8.2.2 (inverse iteration), 8.5 (Jacobi).
 #include <cstdio>
 
 #include "common.cuh"

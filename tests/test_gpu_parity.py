@@ -377,6 +377,29 @@ def test_wide_block_all_coarse_modes_matches_oracle():
     assert np.max(np.abs(U.T @ (M @ U) - np.eye(80))) < 1e-10
 
 
+def test_coarse_modes_on_demand():
+    """The coarse eigenbasis is computed on the first solve with only the modes it needs
+    and again, whole, when a later solve needs more: every solve gives the bits of the
+    same solve on a fresh hierarchy."""
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    few = ae.options(q_extra=2, fixed_corrections=2, coarse_modes=16)
+    full = ae.options(q_extra=2, fixed_corrections=2)
+    with ae.Hierarchy(blob) as h:
+        a_few = h.solve(6, tol=0.0, opt=few)
+        a_full = h.solve(6, tol=0.0, opt=full)
+        a_few2 = h.solve(6, tol=0.0, opt=few)
+    with ae.Hierarchy(blob) as h:
+        b_full = h.solve(6, tol=0.0, opt=full)
+        b_few = h.solve(6, tol=0.0, opt=few)
+    with ae.Hierarchy(blob) as h:
+        c_few = h.solve(6, tol=0.0, opt=few)
+    assert np.array_equal(a_full[0], b_full[0]) and np.array_equal(a_full[1], b_full[1])
+    assert np.array_equal(a_few[0], c_few[0]) and np.array_equal(a_few[1], c_few[1])
+    # a few-mode solve after the full basis exists uses its leading columns: same fixed point
+    assert np.array_equal(a_few2[0], b_few[0])
+    assert np.max(np.abs(a_few2[0] - a_few[0]) / a_few[0]) < 1e-10
+
+
 @pytest.mark.parametrize("L", [1, 3])
 def test_coarse_modes_parity(L):
     """The truncated coarse space (coarse_modes option) matches the oracle's same option."""
