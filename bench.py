@@ -369,7 +369,8 @@ def main():
                          "amgeig_submit / amgeig_poll over a pool of problems (throughput and p50/p99 latency)")
     ap.add_argument("--requests", type=int, default=200, help="stream: requests in the timed stream")
     ap.add_argument("--pool", type=int, default=6, help="stream: distinct problems the requests draw from")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "bf16", "fp64"],
+                    help="mixed: float32 V-cycle; bf16: its operators stored in bfloat16; fp64: every step in float64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-corrections", type=int, default=10,
                     help="finest-level corrections the reference arm's oracle timing is scaled to (the GPU run "
@@ -423,7 +424,7 @@ def main():
     if args.q_extra is not None:
         qe = args.q_extra
     modes = WORKLOADS[args.workload]["modes"] if args.coarse_modes is None else args.coarse_modes
-    prec = ae.AMGEIG_MIXED_FP32 if args.precision == "mixed" else ae.AMGEIG_FP64
+    prec = {"mixed": ae.AMGEIG_MIXED_FP32, "bf16": ae.AMGEIG_MIXED_BF16}.get(args.precision, ae.AMGEIG_FP64)
     smoother = ae.AMGEIG_SMOOTHER_GAUSS_SEIDEL if args.smoother == "gauss-seidel" else ae.AMGEIG_SMOOTHER_L1_JACOBI
     opt = ae.options(q_extra=qe, max_corrections=60, precision=prec, coarse_modes=modes,
                      pre_sweeps=args.sweeps, post_sweeps=args.sweeps, v_cycles=args.v_cycles, smoother=smoother)
@@ -562,7 +563,8 @@ def main():
             "metric": "eigenpairs/s", "value": value, "unit": "eigenpairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+f32" if prec == ae.AMGEIG_MIXED_FP32 else "f64", "data": "synthetic",
+            "dtype": {ae.AMGEIG_MIXED_FP32: "f64+f32", ae.AMGEIG_MIXED_BF16: "f64+f32+bf16"}.get(prec, "f64"),
+            "data": "synthetic",
             "config": {"workload": args.workload, "N": N0, "q": q, "q_extra": qe, "levels": h.sizes,
                        "precision": args.precision, "tol_relres": tol, "corrections": corrections,
                        "coarse_modes": modes, "sweeps": args.sweeps, "v_cycles": args.v_cycles, "smoother": args.smoother,

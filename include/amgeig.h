@@ -46,7 +46,10 @@ extern "C" {
 #define AMGEIG_FP64 0       /* every step in float64 */
 #define AMGEIG_MIXED_FP32 1 /* V-cycle (smoothing, transfers, coarse solve) in float32;
                                defect, Rayleigh-Ritz, Gram/cross blocks and the
-                               recombination stay in float64 */
+                               recombination in float-float (48-bit significand) */
+#define AMGEIG_MIXED_BF16 2 /* as AMGEIG_MIXED_FP32, with the V-cycle's operators (A_l, R_l,
+                               P_l) stored in bfloat16 and applied with float32
+                               accumulation; the defect keeps the exact A */
 
 typedef struct amgeig_hierarchy_t* amgeig_hierarchy;
 
@@ -60,7 +63,7 @@ typedef struct {
   int pre_sweeps;        /* l1-Jacobi sweeps before the coarse correction, >= 0 */
   int post_sweeps;       /* l1-Jacobi sweeps after the coarse correction, >= 0 */
   int q_extra;           /* extra eigenpairs carried along (Sec. 4, Examples 4-6), >= 0 */
-  int precision;         /* AMGEIG_FP64 or AMGEIG_MIXED_FP32 */
+  int precision;         /* AMGEIG_FP64, AMGEIG_MIXED_FP32 or AMGEIG_MIXED_BF16 */
   int fixed_corrections; /* > 0: run exactly this many finest-level corrections and
                             ignore tol (iteration-level parity mode) */
   int coarse_modes;      /* 0: the pencil of Algorithm 3.1 step 2 uses all of V_n (the

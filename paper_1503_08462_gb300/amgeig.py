@@ -27,6 +27,7 @@ AMGEIG_ENOTFOUND = -8
 
 AMGEIG_FP64 = 0
 AMGEIG_MIXED_FP32 = 1
+AMGEIG_MIXED_BF16 = 2
 AMGEIG_SMOOTHER_L1_JACOBI = 0
 AMGEIG_SMOOTHER_GAUSS_SEIDEL = 1
 

@@ -341,6 +341,7 @@ struct amgeig_hierarchy_t {
   // per level below the coarsest, the rows sorted by colour (device), the
   // colour offsets (host) and 1 / a_ii
   bool gs_ready = false;
+  bool bf16_ready = false;  // bfloat16 copies of the V-cycle's operators (on the first such solve)
   std::vector<int*> gs_rows;
   std::vector<std::vector<int>> gs_off;
   std::vector<double*> gs_dinv64;
@@ -354,6 +355,7 @@ namespace {
 
 struct SolveWork {
   int smoother = AMGEIG_SMOOTHER_L1_JACOBI;  // of the current solve
+  bool bf16 = false;                          // the current solve reads bfloat16 operator values
   int qcap = 0;  // column capacity: the buffers serve any solve with q + q_extra <= qcap
   int qt = 0;    // columns of the current solve (every block's row stride)
   int ld32 = 0;  // row stride of the float32 V-cycle blocks: qt rounded up to a multiple of 4
@@ -451,6 +453,8 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
 // of a larger one (all layouts follow the current qt), so a stream of requests
 // with varying q on one hierarchy allocates only when its largest width grows.
 int ensure_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles) {
+  // the bfloat16 option only swaps the V-cycle's operator values: same workspace
+  if (precision == AMGEIG_MIXED_BF16) precision = AMGEIG_MIXED_FP32;
   SolveWork* w = h->ws.get();
   if (!w || w->qcap < qt || w->precision != precision || w->vcycles < vcycles) {
     const bool same = w && w->precision == precision;
@@ -487,17 +491,18 @@ struct VBufs<float> {
   static std::vector<float*>& E(SolveWork* w) { return w->E32; }
 };
 
-void presmooth_residual(const DevCsr& A, const double* d, const double* b, int wdt, double* x, double* r, cudaStream_t s) { launch_presmooth_residual_f64(A, d, b, wdt, x, r, s); }
-void presmooth_residual(const DevCsr& A, const float* d, const float* b, int wdt, float* x, float* r, cudaStream_t s) { launch_presmooth_residual_f32(A, d, b, wdt, x, r, s); }
-void jacobi(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, double* o, cudaStream_t s) { launch_jacobi_f64(A, d, b, x, wdt, o, s); }
-void jacobi(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, float* o, cudaStream_t s) { launch_jacobi_f32(A, d, b, x, wdt, o, s); }
-void residual(const DevCsr& A, const double* b, const double* x, int wdt, double* r, cudaStream_t s) { launch_residual_f64(A, b, x, wdt, r, s); }
-void residual(const DevCsr& A, const float* b, const float* x, int wdt, float* r, cudaStream_t s) { launch_residual_f32(A, b, x, wdt, r, s); }
-void spmm(const DevCsr& S, const double* X, int wdt, double* Y, bool acc, cudaStream_t s) { launch_spmm_f64(S, X, wdt, Y, acc, s); }
-void spmm(const DevCsr& S, const float* X, int wdt, float* Y, bool acc, cudaStream_t s) { launch_spmm_f32(S, X, wdt, Y, acc, s); }
+// bf: the float32 path reads the operators' bfloat16 values (AMGEIG_MIXED_BF16)
+void presmooth_residual(const DevCsr& A, const double* d, const double* b, int wdt, double* x, double* r, cudaStream_t s, bool = false) { launch_presmooth_residual_f64(A, d, b, wdt, x, r, s); }
+void presmooth_residual(const DevCsr& A, const float* d, const float* b, int wdt, float* x, float* r, cudaStream_t s, bool bf = false) { launch_presmooth_residual_f32(A, d, b, wdt, x, r, s, bf); }
+void jacobi(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, double* o, cudaStream_t s, bool = false) { launch_jacobi_f64(A, d, b, x, wdt, o, s); }
+void jacobi(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, float* o, cudaStream_t s, bool bf = false) { launch_jacobi_f32(A, d, b, x, wdt, o, s, bf); }
+void residual(const DevCsr& A, const double* b, const double* x, int wdt, double* r, cudaStream_t s, bool = false) { launch_residual_f64(A, b, x, wdt, r, s); }
+void residual(const DevCsr& A, const float* b, const float* x, int wdt, float* r, cudaStream_t s, bool bf = false) { launch_residual_f32(A, b, x, wdt, r, s, bf); }
+void spmm(const DevCsr& S, const double* X, int wdt, double* Y, bool acc, cudaStream_t s, bool = false) { launch_spmm_f64(S, X, wdt, Y, acc, s); }
+void spmm(const DevCsr& S, const float* X, int wdt, float* Y, bool acc, cudaStream_t s, bool bf = false) { launch_spmm_f32(S, X, wdt, Y, acc, s, bf); }
 void jacobi_to_v(const DevCsr& A, const double* d, const double* b, const double* x, int wdt, const double* U, double* V, cudaStream_t s, int) { launch_jacobi_to_v_f64(A, d, b, x, wdt, U, V, s); }
 // the float32 V-cycle belongs to the mixed path, whose U and V are float-float
-void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv, const float* xadd = nullptr) { launch_jacobi_to_vdf_f32(A, d, b, x, wdt, reinterpret_cast<const float2*>(U), reinterpret_cast<float2*>(V), s, qv, xadd); }
+void jacobi_to_v(const DevCsr& A, const float* d, const float* b, const float* x, int wdt, const double* U, double* V, cudaStream_t s, int qv, const float* xadd = nullptr, bool bf = false) { launch_jacobi_to_vdf_f32(A, d, b, x, wdt, reinterpret_cast<const float2*>(U), reinterpret_cast<float2*>(V), s, qv, xadd, bf); }
 void add_to_v(const double* U, const double* x, int rows, int q, int, double* V, cudaStream_t s) { launch_add_to_v_f64(U, x, static_cast<long long>(rows) * q, V, s); }
 void add_to_v(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t s) { launch_add_to_vdf(reinterpret_cast<const float2*>(U), x, rows, q, ldx, reinterpret_cast<float2*>(V), s); }
 void axpy(const double* x, long long c, double* y, cudaStream_t s) { launch_axpy_f64(x, c, y, s); }
@@ -569,6 +574,28 @@ int ensure_gs(amgeig_hierarchy_t* h, cudaStream_t st) {
   return AMGEIG_OK;
 }
 
+// bfloat16 copies of A_l, R_l and P_l (levels below the coarsest) for
+// AMGEIG_MIXED_BF16, rounded from the float32 values on the first such solve.
+int ensure_bf16(amgeig_hierarchy_t* h, cudaStream_t st) {
+  if (h->bf16_ready) return AMGEIG_OK;
+  auto& m = h->mem;
+  auto make = [&](DevCsr& D) -> int {
+    if (D.vbf || D.nnz == 0) return AMGEIG_OK;
+    CK(m.alloc(&D.vbf, static_cast<size_t>(D.nnz)));
+    launch_f32_to_bf16(D.v32, D.nnz, D.vbf, st);
+    return AMGEIG_OK;
+  };
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    int rc = make(h->A[l]);
+    if (!rc) rc = make(h->R[l]);
+    if (!rc) rc = make(h->P[l]);
+    if (rc) return rc;
+  }
+  CK(cudaGetLastError());
+  h->bf16_ready = true;
+  return AMGEIG_OK;
+}
+
 const double* gs_dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->gs_dinv64[l]; }
 const float* gs_dinv_of(amgeig_hierarchy_t* h, int l, float*) { return h->gs_dinv32[l]; }
 
@@ -606,25 +633,25 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
       cudaMemsetAsync(X[l], 0, sizeof(T) * h->sizes[l] * q, st);
       for (int s = 0; s < pre; ++s) gs_sweep(h, l, B[l], X[l], q, false, st);
       residual(A, B[l], X[l], q, Tm[l], st);
-      spmm(h->R[l], Tm[l], q, B[l + 1], false, st);
+      spmm(h->R[l], Tm[l], q, B[l + 1], false, st, w->bf16);
     } else if (pre >= 1) {
-      presmooth_residual(A, d, B[l], q, X[l], Tm[l], st);
+      presmooth_residual(A, d, B[l], q, X[l], Tm[l], st, w->bf16);
       for (int s = 1; s < pre; ++s) {
-        jacobi(A, d, B[l], X[l], q, Tm[l], st);
+        jacobi(A, d, B[l], X[l], q, Tm[l], st, w->bf16);
         std::swap(X[l], Tm[l]);
       }
-      if (pre > 1) residual(A, B[l], X[l], q, Tm[l], st);
-      spmm(h->R[l], Tm[l], q, B[l + 1], false, st);
+      if (pre > 1) residual(A, B[l], X[l], q, Tm[l], st, w->bf16);
+      spmm(h->R[l], Tm[l], q, B[l + 1], false, st, w->bf16);
     } else {
       cudaMemsetAsync(X[l], 0, sizeof(T) * h->sizes[l] * q, st);
-      spmm(h->R[l], B[l], q, B[l + 1], false, st);
+      spmm(h->R[l], B[l], q, B[l + 1], false, st, w->bf16);
     }
   }
   coarse_solve(h, B[n - 1], q, X[n - 1], st);
   for (int l = n - 2; l >= k; --l) {
     const DevCsr& A = h->A[l];
     const T* d = dinv_of(h, l, dummy);
-    spmm(h->P[l], X[l + 1], q, X[l], true, st);
+    spmm(h->P[l], X[l + 1], q, X[l], true, st, w->bf16);
     if (gs) {
       // colours descending after the coarse correction (a symmetric cycle)
       for (int s = 0; s < post; ++s) gs_sweep(h, l, B[l], X[l], q, true, st);
@@ -638,11 +665,11 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
     for (int s = 0; s < post; ++s) {
       if (to_v && l == k && s == post - 1) {
         if constexpr (std::is_same<T, float>::value)
-          jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt, xadd);
+          jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt, xadd, w->bf16);
         else
           jacobi_to_v(A, d, B[l], X[l], q, U, V, st, w->qt);
       } else {
-        jacobi(A, d, B[l], X[l], q, Tm[l], st);
+        jacobi(A, d, B[l], X[l], q, Tm[l], st, w->bf16);
         std::swap(X[l], Tm[l]);
       }
     }
@@ -677,12 +704,12 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     // V = U + (x + E) itself
     vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
     std::swap(X[k], E[k]);
-    residual(h->A[k], B[k], E[k], wd, D[k], st);
+    residual(h->A[k], B[k], E[k], wd, D[k], st, w->bf16);
     std::swap(B[k], D[k]);
     for (int c = 1; c + 1 < o.v_cycles; ++c) {
       vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
       axpy(X[k], cnt, E[k], st);
-      residual(h->A[k], D[k], E[k], wd, B[k], st);
+      residual(h->A[k], D[k], E[k], wd, B[k], st, w->bf16);
     }
     vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, true, U, V, st, E[k]);
     return;
@@ -800,7 +827,7 @@ int defect(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, 
 int check_options(const amgeig_options& o) {
   if (o.max_corrections < 0 || o.v_cycles < 1 || o.pre_sweeps < 0 || o.post_sweeps < 0 || o.q_extra < 0 ||
       o.fixed_corrections < 0 || o.coarse_modes < 0 ||
-      (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32) ||
+      (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
       (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
@@ -832,6 +859,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   w->smoother = o.smoother;
   if (o.smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL) {
     rc = ensure_gs(h, st);
+    if (rc) return rc;
+  }
+  w->bf16 = o.precision == AMGEIG_MIXED_BF16;
+  if (w->bf16) {
+    rc = ensure_bf16(h, st);
     if (rc) return rc;
   }
   {
@@ -1393,6 +1425,11 @@ int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_o
     rc = ensure_gs(h, st);
     if (rc) return rc;
   }
+  w->bf16 = o.precision == AMGEIG_MIXED_BF16;
+  if (w->bf16) {
+    rc = ensure_bf16(h, st);
+    if (rc) return rc;
+  }
   const long long cnt = h->sizes[level] * static_cast<long long>(width);
   if (level == h->nlev - 1) {
     // the coarsest level: the exact solve
@@ -1485,7 +1522,8 @@ bool Service::fits(const Request* r) {
     // a direct solve on this hierarchy from another thread: not now
     std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
     if (!lk.owns_lock()) return false;
-    if (h->ws && h->ws->qcap >= qt && h->ws->precision == r->opt.precision) return true;
+    const int wp = r->opt.precision == AMGEIG_FP64 ? AMGEIG_FP64 : AMGEIG_MIXED_FP32;
+    if (h->ws && h->ws->qcap >= qt && h->ws->precision == wp) return true;
   }
   size_t fr = 0, tot = 0;
   cudaSetDevice(h->device);

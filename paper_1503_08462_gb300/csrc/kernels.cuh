@@ -2,6 +2,7 @@
 // family; each launcher enqueues on `st` and returns without synchronising).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -18,6 +19,7 @@ struct DevCsr {
   double* m64 = nullptr;  // second value array sharing the pattern (mass matrix)
   float2* d2 = nullptr;   // v64 as float-float pairs (hi, lo)
   float2* m2 = nullptr;   // m64 as float-float pairs
+  __nv_bfloat16* vbf = nullptr;  // v64 rounded to bfloat16 (the V-cycle's operators, AMGEIG_MIXED_BF16)
 };
 
 // ---- sparse kernels (spmm.cu) --------------------------------------------
@@ -35,22 +37,25 @@ void launch_defect_f32out(const DevCsr& AM, const double* U, int q, const double
 // Y = S X (accumulate = false) or Y += S X (accumulate = true)
 void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, bool accumulate, cudaStream_t st,
                      int cls = 2);
-void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st);
+// bf16: read the operator's bfloat16 values (vbf) instead of the float32 ones
+void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st,
+                     bool bf16 = false);
 
 // first l1-Jacobi sweep from x = 0 fused with the residual:
 //   x = D^-1 b,  r = b - A x
 void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const double* b, int width, double* x,
                                    double* r, cudaStream_t st);
 void launch_presmooth_residual_f32(const DevCsr& A, const float* dinv, const float* b, int width, float* x,
-                                   float* r, cudaStream_t st);
+                                   float* r, cudaStream_t st, bool bf16 = false);
 // one l1-Jacobi sweep x_out = x + D^-1 (b - A x) (x_out != x)
 void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
                        double* x_out, cudaStream_t st);
 void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                       float* x_out, cudaStream_t st);
+                       float* x_out, cudaStream_t st, bool bf16 = false);
 // residual r = b - A x
 void launch_residual_f64(const DevCsr& A, const double* b, const double* x, int width, double* r, cudaStream_t st);
-void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st);
+void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st,
+                         bool bf16 = false);
 // last sweep on the working level fused with V = U + x_new (float64 output)
 void launch_jacobi_to_v_f64(const DevCsr& A, const double* dinv, const double* b, const double* x, int width,
                             const double* U, double* V, cudaStream_t st);
@@ -117,7 +122,10 @@ void launch_cols_to_df(const double* src, int rows, int ld, int q, float2* dst, 
 // last float32 sweep on the working level fused with V = U + x (U, V float-float,
 // row stride qv; b and x row stride width)
 void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                              const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd = nullptr);
+                              const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd = nullptr,
+                              bool bf16 = false);
+// float32 -> bfloat16 (round to nearest even)
+void launch_f32_to_bf16(const float* x, long long count, __nv_bfloat16* y, cudaStream_t st);
 // V = U + x (U, V float-float rows x q; x float32 with row stride ldx)
 void launch_add_to_vdf(const float2* U, const float* x, int rows, int q, int ldx, float2* V, cudaStream_t st);
 

@@ -320,9 +320,12 @@ __device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
 // MODE 0: x = D^-1 b, r = b - A x (x from 0);  1: x <- x + D^-1 (b - A x);
 // 2: r = b - A x;  3: V = U + (x + D^-1 (b - A x)) in float64;  4: the same in
 // float-float, plus xadd when given (the sum of the earlier V-cycles).
-template <int MODE, int CPT>
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <int MODE, int CPT, typename TV>
 __global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __restrict__ rp,
-                                                        const int* __restrict__ ci, const float* __restrict__ a,
+                                                        const int* __restrict__ ci, const TV* __restrict__ a,
                                                         const float* __restrict__ dinv,
                                                         const float4* __restrict__ b, const float4* __restrict__ x,
                                                         int w4, float4* __restrict__ out1, float4* __restrict__ out2,
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __r
 #pragma unroll 2
   for (int p = p0; p < p1; ++p) {
     const int j = ci[p];
-    float s = a[p];
+    float s = to_f(a[p]);
     if (MODE == 0) s *= dinv[j];
     const float4* sr = src + static_cast<long long>(j) * w4;
 #pragma unroll
@@ -397,9 +400,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __r
   }
 }
 
-template <int CPT>
+template <int CPT, typename TV>
 __global__ void __launch_bounds__(kThreads, 6) k_spmm_f4(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                      const float* __restrict__ v, const float4* __restrict__ X,
+                                                      const TV* __restrict__ v, const float4* __restrict__ X,
                                                       int w4, float4* __restrict__ Y, int G, int accumulate) {
   const int rpb = blockDim.x / G;
   const int lane = threadIdx.x % G;
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_spmm_f4(int n, const int* __res
   const int p0 = rp[row], p1 = rp[row + 1];
 #pragma unroll 2
   for (int p = p0; p < p1; ++p) {
-    const float s = v[p];
+    const float s = to_f(v[p]);
     const float4* xr = X + static_cast<long long>(ci[p]) * w4;
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
@@ -436,14 +439,19 @@ __global__ void __launch_bounds__(kThreads, 6) k_spmm_f4(int n, const int* __res
 template <int MODE>
 void smooth_f4(const DevCsr& A, const float* dinv, const float* b, const float* x, int w4, float* out1, float* out2,
                const double* U, double* V, int qv, const float2* U2, float2* V2, const float* xadd,
-               cudaStream_t st) {
+               cudaStream_t st, bool bf16 = false) {
   const F4Geo g = f4_geo(w4, A.rows);
   const int blocks = ceil_div(A.rows, kThreads / g.G);
-#define AMGEIG_SMOOTH(C)                                                                                        \
-  k_smooth_f4<MODE, C><<<blocks, kThreads, 0, st>>>(                                                            \
-      A.rows, A.rp, A.ci, A.v32, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4, \
+#define AMGEIG_SMOOTH_T(C, TV, VALS)                                                                         \
+  k_smooth_f4<MODE, C, TV><<<blocks, kThreads, 0, st>>>(                                                       \
+      A.rows, A.rp, A.ci, VALS, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4, \
       reinterpret_cast<float4*>(out1), reinterpret_cast<float4*>(out2), U, V, qv, g.G, U2, V2,                   \
       reinterpret_cast<const float4*>(xadd))
+#define AMGEIG_SMOOTH(C)                                  \
+  if (bf16)                                               \
+    AMGEIG_SMOOTH_T(C, __nv_bfloat16, A.vbf);             \
+  else                                                    \
+    AMGEIG_SMOOTH_T(C, float, A.v32)
   switch (g.cpt) {
     case 1:
       AMGEIG_SMOOTH(1);
@@ -456,6 +464,7 @@ void smooth_f4(const DevCsr& A, const float* dinv, const float* b, const float* 
       break;
   }
 #undef AMGEIG_SMOOTH
+#undef AMGEIG_SMOOTH_T
 }
 
 // ------------------------------------------------------------------ augmentation
@@ -731,7 +740,8 @@ void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, boo
                      int cls) {
   spmm_impl<double>(S, S.v64, X, width, Y, accumulate, st, cls);
 }
-void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st) {
+void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st,
+                     bool bf16) {
   if (width % 4 != 0 || S.rows == 0) {
     spmm_impl<float>(S, S.v32, X, width, Y, accumulate, st);
     return;
@@ -745,17 +755,23 @@ void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool 
   const float4* X4 = reinterpret_cast<const float4*>(X);
   float4* Y4 = reinterpret_cast<float4*>(Y);
   const int acc = accumulate ? 1 : 0;
+#define AMGEIG_SPMM(C)                                                                                       \
+  if (bf16)                                                                                                  \
+    k_spmm_f4<C, __nv_bfloat16><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.vbf, X4, w4, Y4, g.G, acc); \
+  else                                                                                                       \
+    k_spmm_f4<C, float><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc)
   switch (g.cpt) {
     case 1:
-      k_spmm_f4<1><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc);
+      AMGEIG_SPMM(1);
       break;
     case 2:
-      k_spmm_f4<2><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc);
+      AMGEIG_SPMM(2);
       break;
     default:
-      k_spmm_f4<3><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc);
+      AMGEIG_SPMM(3);
       break;
   }
+#undef AMGEIG_SPMM
 }
 
 void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const double* b, int width, double* x,
@@ -763,12 +779,12 @@ void launch_presmooth_residual_f64(const DevCsr& A, const double* dinv, const do
   smooth_impl<double, 0>(A, A.v64, dinv, b, nullptr, width, x, r, nullptr, nullptr, st);
 }
 void launch_presmooth_residual_f32(const DevCsr& A, const float* dinv, const float* b, int width, float* x,
-                                   float* r, cudaStream_t st) {
+                                   float* r, cudaStream_t st, bool bf16) {
   if (width % 4 == 0 && A.rows > 0) {
     const double N = A.rows;
     const double vec = 12.0 * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
-    smooth_f4<0>(A, dinv, b, nullptr, width / 4, x, r, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st);
+    smooth_f4<0>(A, dinv, b, nullptr, width / 4, x, r, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st, bf16);
     return;
   }
   smooth_impl<float, 0>(A, A.v32, dinv, b, nullptr, width, x, r, nullptr, nullptr, st);
@@ -778,12 +794,12 @@ void launch_jacobi_f64(const DevCsr& A, const double* dinv, const double* b, con
   smooth_impl<double, 1>(A, A.v64, dinv, b, x, width, x_out, nullptr, nullptr, nullptr, st);
 }
 void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                       float* x_out, cudaStream_t st) {
+                       float* x_out, cudaStream_t st, bool bf16) {
   if (width % 4 == 0 && A.rows > 0) {
     const double N = A.rows;
     const double vec = 12.0 * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + vec, 2.0 * A.nnz * width);
-    smooth_f4<1>(A, dinv, b, x, width / 4, x_out, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st);
+    smooth_f4<1>(A, dinv, b, x, width / 4, x_out, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st, bf16);
     return;
   }
   smooth_impl<float, 1>(A, A.v32, dinv, b, x, width, x_out, nullptr, nullptr, nullptr, st);
@@ -791,12 +807,13 @@ void launch_jacobi_f32(const DevCsr& A, const float* dinv, const float* b, const
 void launch_residual_f64(const DevCsr& A, const double* b, const double* x, int width, double* r, cudaStream_t st) {
   smooth_impl<double, 2>(A, A.v64, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
 }
-void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st) {
+void launch_residual_f32(const DevCsr& A, const float* b, const float* x, int width, float* r, cudaStream_t st,
+                         bool bf16) {
   if (width % 4 == 0 && A.rows > 0) {
     const double N = A.rows;
     const double vec = 12.0 * N * width;
     ProfScope ps(st, P_SMOOTH, 4.0 * (N + 1) + 8.0 * A.nnz + 0.0 + vec, 2.0 * A.nnz * width);
-    smooth_f4<2>(A, nullptr, b, x, width / 4, r, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st);
+    smooth_f4<2>(A, nullptr, b, x, width / 4, r, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st, bf16);
     return;
   }
   smooth_impl<float, 2>(A, A.v32, nullptr, b, x, width, r, nullptr, nullptr, nullptr, st);
@@ -927,13 +944,25 @@ void launch_f32_to_f64_unpad(const float* src, int rows, int q, int ld, double* 
 }
 
 void launch_jacobi_to_vdf_f32(const DevCsr& A, const float* dinv, const float* b, const float* x, int width,
-                              const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd) {
+                              const float2* U, float2* V, cudaStream_t st, int qv, const float* xadd, bool bf16) {
   if (A.rows == 0) return;
   const double N = A.rows;
   ProfScope ps(st, P_SMOOTH,
                4.0 * (N + 1) + 8.0 * A.nnz + 4.0 * N + ((xadd ? 3.0 : 2.0) * 4 + 16.0) * N * width,
                2.0 * A.nnz * width);
-  smooth_f4<4>(A, dinv, b, x, width / 4, nullptr, nullptr, nullptr, nullptr, qv, U, V, xadd, st);
+  smooth_f4<4>(A, dinv, b, x, width / 4, nullptr, nullptr, nullptr, nullptr, qv, U, V, xadd, st, bf16);
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ x, long long count, __nv_bfloat16* __restrict__ y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+void launch_f32_to_bf16(const float* x, long long count, __nv_bfloat16* y, cudaStream_t st) {
+  if (count <= 0) return;
+  ProfScope ps(st, P_OTHER, 6.0 * count, 0.0);
+  k_f32_to_bf16<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
 }
 
 __global__ void k_add_to_vdf(const float2* __restrict__ U, const float* __restrict__ x, int rows, int q, int ldx,

@@ -118,6 +118,61 @@ def test_gs_iteration_parity_and_convergence(kind, size, cap, seed, q, qe):
         assert info_g.corrections <= info_j.corrections
 
 
+def _bf16(values):
+    """float64 -> float32 -> bfloat16 (round to nearest even), back to float64."""
+    u = np.asarray(values, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_vcycle_matches_oracle_with_rounded_operators():
+    """AMGEIG_MIXED_BF16 stores the V-cycle's operators A_l, R_l, P_l in bfloat16: its
+    float32 V-cycle equals the oracle's V-cycle run on a hierarchy whose operators hold
+    the same rounded values (the l1 diagonals and the coarsest solve stay exact)."""
+    import copy
+
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    oh = O.read_blob(blob)
+    ob = copy.copy(oh)
+    last = oh.n_levels - 1
+    ob.A = [a if l == last else a.copy() for l, a in enumerate(oh.A)]
+    ob.P = [m.copy() for m in oh.P]
+    for l in range(last):
+        ob.A[l].data = _bf16(oh.A[l].data)
+        ob.P[l].data = _bf16(oh.P[l].data)
+    ob.R = [m.T.tocsr() for m in ob.P]
+    ob.colour_cache = {}
+    rng = np.random.default_rng(9)
+    with ae.Hierarchy(blob) as h:
+        for level in range(last):
+            b = rng.standard_normal((oh.sizes[level], 8))
+            ref = O.vcycle(ob, level, b, np.zeros_like(b))
+            x = ae.amgeig_apply_vcycle(h.handle, level, b, ae.options(precision=ae.AMGEIG_MIXED_BF16))
+            assert np.abs(x - ref).max() <= 2e-5 * np.abs(ref).max()
+            # and it is a different operator from the float32 one
+            x32 = ae.amgeig_apply_vcycle(h.handle, level, b, ae.options(precision=ae.AMGEIG_MIXED_FP32))
+            assert np.abs(x - x32).max() > 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind,size,cap,seed,q,qe", [("lshape", 16, 60, 2, 6, 2), ("square", 32, 50, 1, 4, 2)])
+def test_bf16_converged_solve(kind, size, cap, seed, q, qe):
+    """The bfloat16 operators only change the correction direction: the defect uses the
+    exact A, so the converged eigenpairs are the dense ones."""
+    p, blob, _ = problem_and_blob(kind, size, cap, seed)
+    oh = O.read_blob(blob)
+    lam_ex, U_ex = dense_pairs(p, q)
+    lmax = lam_max(p)
+    ptol = max(1e-9, 4 * 2.0 ** -48 * lmax / lam_ex[0])
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, code = h.solve(q, tol=ptol, opt=ae.options(q_extra=qe, max_corrections=150,
+                                                                 precision=ae.AMGEIG_MIXED_BF16))
+    assert code == ae.AMGEIG_OK
+    prtol = np.maximum(eig_rel_tol(lam_ex, lmax), 4 * 2.0 ** -48 * lmax / lam_ex)
+    assert np.all(np.abs(lam - lam_ex) <= prtol * lam_ex)
+    assert m_subspace_angle(U, U_ex, oh.M[0]) < max(1e-8, 10 * ptol)
+    assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(q)).max() < 1e-10
+
+
 # ------------------------------------------------------------------ solver
 
 
