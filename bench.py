@@ -44,7 +44,7 @@ FP64_CLASSES = {"defect", "augment", "gram", "recombine", "chain"}
 # over the class's launches / launch count); keyed by (workload, precision,
 # v_cycles, q_extra) and valid only for the kernels it was taken on.
 DRAM_TRAFFIC_PER_LAUNCH = {
-    ("lshape_h512_q20", "mixed", 2, 8, "smooth"): 61.53e6,
+    ("lshape_h512_q20", "mixed", 2, 8, "smooth"): 61.56e6,
 }
 
 WORKLOADS = {
