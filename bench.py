@@ -504,9 +504,11 @@ def main():
         import ctypes
 
         handle = ctypes.c_void_p()
-        rc = hh.amgeig_load_hierarchy(ctypes.c_void_p(blob_pinned.data_ptr()), len(blob), local,
-                                      ctypes.byref(handle))
-        ae._check(rc, "amgeig_load_hierarchy")
+        # the load also computes the coarse modes this solve's pencil uses (on a side stream)
+        rc = hh.amgeig_load_hierarchy_modes(ctypes.c_void_p(blob_pinned.data_ptr()), len(blob), local,
+                                            0 if opt.coarse_modes == 0 else max(opt.coarse_modes, q + opt.q_extra),
+                                            ctypes.byref(handle))
+        ae._check(rc, "amgeig_load_hierarchy_modes")
         ae.amgeig_solve(handle, q, tol, opt, vals_h, vecs_h, False, None, None)
         ae.amgeig_free_hierarchy(handle)
     e2e_s = replica_max(dist, (time.perf_counter() - t0) / e2e_steps, f"cuda:{local}")

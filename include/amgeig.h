@@ -100,13 +100,27 @@ void amgeig_default_options(amgeig_options* opt);
  * `device`.  blob: host pointer to `bytes` bytes, read during the call only.
  * The library copies every level (A_k, M_k in one shared-pattern CSR, P_k and
  * its transpose R_k = P_k^T, Sec. 2.3) to the device, derives the l1-Jacobi
- * diagonals and float32 copies, and computes once, on the GPU, the
- * M_n-orthonormal eigenbasis of the coarsest pencil (A_n, M_n) used by step 1
- * of Algorithm 3.2 and by every correction.  On success *out owns all device
- * memory of the hierarchy until amgeig_free_hierarchy.  Errors: EINVAL (NULL
- * argument, bad device), ECORRUPT (validation), ENOMEM, ENOTSPD (A_n or M_n not
- * SPD), ECUDA. */
+ * diagonals and float32 copies, builds the composite prolongations I_n^k, and
+ * factors the coarsest level on the GPU (the exact coarse solve of the V-cycle).
+ * The M_n-orthonormal eigenbasis of the coarsest pencil (A_n, M_n), used by
+ * step 1 of Algorithm 3.2 and by every correction, is computed on the GPU by the
+ * first solve that needs it, only its leading modes (all d_n with coarse_modes
+ * = 0), and kept for later solves.  On success *out owns all device memory of
+ * the hierarchy until amgeig_free_hierarchy.  Errors: EINVAL (NULL argument,
+ * bad device), ECORRUPT (validation), ENOMEM, ENOTSPD (A_n or M_n not SPD),
+ * ECUDA. */
 int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hierarchy* out);
+
+/* As amgeig_load_hierarchy, and also computes the `modes` lowest eigenpairs of
+ * the coarsest pencil (A_n, M_n) (Algorithm 3.2 step 1) during the load: the
+ * coarsest level is uploaded, factored and decomposed on a second stream while
+ * the host validates and converts the finer levels, so a first solve whose
+ * pencil needs at most `modes` coarse modes (coarse_modes <= modes and q +
+ * q_extra <= modes) starts without computing them.  modes = 0 or modes > d_n:
+ * all d_n modes (the paper's pencil, coarse_modes = 0).  The modes are the same
+ * bits a first solve would compute on its own with that count.  Errors: as
+ * amgeig_load_hierarchy; EINVAL also for modes < 0. */
+int amgeig_load_hierarchy_modes(const void* blob, size_t bytes, int device, int modes, amgeig_hierarchy* out);
 
 /* Release every device and host resource of h.  NULL is accepted.  Pending
  * requests on h must have been polled to completion first (EINVAL otherwise). */

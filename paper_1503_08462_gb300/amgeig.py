@@ -55,7 +55,7 @@ class amgeig_info(ctypes.Structure):
 
 
 _lib = None
-EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
+EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_load_hierarchy_modes", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
             "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_apply_defect", "amgeig_profile_enable",
             "amgeig_profile_read", "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc"]
@@ -77,6 +77,7 @@ def lib():
         L.amgeig_default_options.argtypes = [ctypes.POINTER(amgeig_options)]
         L.amgeig_default_options.restype = None
         L.amgeig_load_hierarchy.argtypes = [vp, ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+        L.amgeig_load_hierarchy_modes.argtypes = [vp, ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
         L.amgeig_free_hierarchy.argtypes = [vp]
         L.amgeig_hierarchy_info.argtypes = [vp, ctypes.POINTER(i32), vp, i32]
         L.amgeig_solve.argtypes = [vp, i32, dbl, ctypes.POINTER(amgeig_options), vp, vp, i32,
@@ -96,7 +97,7 @@ def lib():
         L.amgeig_sym_eigh_noalloc.restype = i32
         L.amgeig_kernel_launches.argtypes = []
         L.amgeig_kernel_launches.restype = ctypes.c_uint64
-        for name in ("amgeig_load_hierarchy", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
+        for name in ("amgeig_load_hierarchy", "amgeig_load_hierarchy_modes", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
                      "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle",
                      "amgeig_apply_defect", "amgeig_profile_enable", "amgeig_profile_read"):
             getattr(L, name).restype = i32
@@ -136,6 +137,15 @@ def amgeig_load_hierarchy(blob: bytes, device: int = 0) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(blob, len(blob))
     _check(lib().amgeig_load_hierarchy(buf, len(blob), device, ctypes.byref(h)), "amgeig_load_hierarchy")
+    return h
+
+
+def amgeig_load_hierarchy_modes(blob: bytes, device: int = 0, modes: int = 0) -> ctypes.c_void_p:
+    """Load and compute the `modes` lowest coarse eigenpairs during the load (0: all)."""
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().amgeig_load_hierarchy_modes(buf, len(blob), device, modes, ctypes.byref(h)),
+           "amgeig_load_hierarchy_modes")
     return h
 
 
@@ -246,10 +256,16 @@ def options(**kw) -> amgeig_options:
 
 
 class Hierarchy:
-    """Owns a loaded hierarchy handle (amgeig_load_hierarchy / amgeig_free_hierarchy)."""
+    """Owns a loaded hierarchy handle (amgeig_load_hierarchy / amgeig_free_hierarchy).
 
-    def __init__(self, blob: bytes, device: int = 0):
-        self.handle = amgeig_load_hierarchy(blob, device)
+    modes: None computes the coarse eigenbasis on the first solve; an int computes that
+    many lowest coarse modes during the load (amgeig_load_hierarchy_modes, 0: all)."""
+
+    def __init__(self, blob: bytes, device: int = 0, modes: Optional[int] = None):
+        if modes is None:
+            self.handle = amgeig_load_hierarchy(blob, device)
+        else:
+            self.handle = amgeig_load_hierarchy_modes(blob, device, modes)
         self.sizes = amgeig_hierarchy_info(self.handle)
 
     def solve(self, q: int, tol: float = 1e-10, opt: Optional[amgeig_options] = None, vectors: bool = True):

@@ -1112,7 +1112,12 @@ const char* amgeig_strerror(int code) {
 
 const char* amgeig_last_error(void) { return g_last_error.c_str(); }
 
-int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hierarchy* out) {
+namespace {
+
+// The load behind both entry points.  modes < 0: the coarse eigenbasis waits for the
+// first solve; modes >= 0: its `modes` lowest pairs (0 or more than d_n: all) are
+// computed during the load.
+int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig_hierarchy* out) {
   g_last_error.clear();
   if (!blob || !out) return fail(AMGEIG_EINVAL, "NULL argument");
   *out = nullptr;
@@ -1134,6 +1139,54 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
   auto& m = h->mem;
   m.st = h->stream;
+  // The coarsest level goes first, on a second stream: the GPU factors it (and
+  // computes the asked-for lowest eigenpairs, Algorithm 3.2 step 1) while the
+  // host prepares the finer levels.  The stream is drained before any return.
+  struct SideStream {
+    cudaStream_t s = nullptr;
+    ~SideStream() {
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    }
+  } side;
+  CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+  const int dn = h->dn;
+  std::vector<double> An(static_cast<size_t>(dn) * dn, 0.0), Mn(static_cast<size_t>(dn) * dn, 0.0);
+  {
+    const CsrView& Lc = levels[n - 1];
+    for (int i = 0; i < dn; ++i)
+      for (int32_t p = Lc.rp[i]; p < Lc.rp[i + 1]; ++p) {
+        An[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.a[p];
+        Mn[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.m[p];
+      }
+  }
+  CK(m.alloc(&h->An, An.size()));
+  CK(m.alloc(&h->Mn, Mn.size()));
+  CK(cudaMemcpyAsync(h->An, An.data(), sizeof(double) * An.size(), cudaMemcpyHostToDevice, side.s));
+  CK(cudaMemcpyAsync(h->Mn, Mn.data(), sizeof(double) * Mn.size(), cudaMemcpyHostToDevice, side.s));
+  CK(m.alloc(&h->Z, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->theta, dn));
+  CK(m.alloc(&h->Ainv, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->Ainv32, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->Zdf, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->dstatus, 4));
+  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), side.s));
+  {
+    cudaError_t e;
+    h->cpw = pencil_work_create(dn, 1, &e);
+    if (!h->cpw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
+  }
+  // the exact coarsest solve of the V-cycle (float64 Cholesky)
+  launch_coarse_inverse(h->cpw, dn, h->An, h->Mn, h->Ainv, h->dstatus, side.s);
+  launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, side.s);
+  const int prefetch = modes < 0 ? 0 : (modes == 0 || modes > dn ? dn : modes);
+  if (prefetch > 0) {
+    launch_coarse_modes(h->cpw, dn, prefetch, h->An, h->Z, h->theta, side.s);
+    launch_f64_to_df(h->Z, static_cast<long long>(dn) * dn, h->Zdf, side.s);
+  }
+  CK(cudaGetLastError());
   h->A.resize(n);
   h->dinv64.assign(n, nullptr);
   h->dinv32.assign(n, nullptr);
@@ -1217,13 +1270,16 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
     CK(m.upload(&nrp, irp));
     CK(m.upload(&nci, ici));
     // float64 values of the level below (freed once the next level is built) and of this level
+    // (stream-ordered: a cudaFree would wait for the coarsest level's work on the side stream)
     struct DeviceTemp {
       double* p = nullptr;
+      cudaStream_t s = nullptr;
       ~DeviceTemp() {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
       }
     } prev, cur;
-    CK(cudaMalloc(&prev.p, sizeof(double) * iv.size()));
+    prev.s = cur.s = h->stream;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&prev.p), sizeof(double) * iv.size(), h->stream));
     CK(cudaMemcpyAsync(prev.p, iv.data(), sizeof(double) * iv.size(), cudaMemcpyHostToDevice, h->stream));
     nv = prev.p;
     int* counts = nullptr;
@@ -1246,12 +1302,11 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
       D.nnz = static_cast<int>(total);
       CK(m.upload(&D.rp, rp));
       CK(m.alloc(&D.ci, static_cast<size_t>(total)));
-      CK(cudaMalloc(&cur.p, sizeof(double) * std::max<int64_t>(total, 1)));
+      CK(cudaMallocAsync(reinterpret_cast<void**>(&cur.p), sizeof(double) * std::max<int64_t>(total, 1), h->stream));
       launch_composite_rows(P, nrp, nci, nv, dn0, D.rp, nullptr, D.ci, cur.p, h->stream);
       CK(m.alloc(&D.d2, static_cast<size_t>(total)));
       launch_f64_to_df(cur.p, total, D.d2, h->stream);
-      CK(cudaStreamSynchronize(h->stream));
-      CK(cudaFree(prev.p));
+      CK(cudaFreeAsync(prev.p, h->stream));
       prev.p = cur.p;
       cur.p = nullptr;
       nrp = D.rp;
@@ -1259,40 +1314,32 @@ int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hie
       nv = prev.p;
     }
   }
-  // dense coarsest pencil and its eigendecomposition
-  const int dn = h->dn;
-  std::vector<double> An(static_cast<size_t>(dn) * dn, 0.0), Mn(static_cast<size_t>(dn) * dn, 0.0);
-  const CsrView& Lc = levels[n - 1];
-  for (int i = 0; i < dn; ++i)
-    for (int32_t p = Lc.rp[i]; p < Lc.rp[i + 1]; ++p) {
-      An[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.a[p];
-      Mn[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.m[p];
-    }
-  CK(m.upload(&h->An, An));
-  CK(m.upload(&h->Mn, Mn));
-  CK(m.alloc(&h->Z, static_cast<size_t>(dn) * dn));
-  CK(m.alloc(&h->theta, dn));
-  CK(m.alloc(&h->Ainv, static_cast<size_t>(dn) * dn));
-  CK(m.alloc(&h->Ainv32, static_cast<size_t>(dn) * dn));
-  CK(m.alloc(&h->dstatus, 4));
-  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
-  cudaError_t e;
-  h->cpw = pencil_work_create(dn, 1, &e);
-  if (!h->cpw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
-  // the exact coarsest solve of the V-cycle (float64 Cholesky); the eigenbasis
-  // waits for the first solve, which asks for as many modes as it needs
-  launch_coarse_inverse(h->cpw, dn, h->An, h->Mn, h->Ainv, h->dstatus, h->stream);
-  launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, h->stream);
-  CK(m.alloc(&h->Zdf, static_cast<size_t>(dn) * dn));
   int stt = 0;
-  cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, side.s);
+  cudaError_t e2 = cudaStreamSynchronize(side.s);
+  cudaError_t e3 = cudaStreamSynchronize(h->stream);
   CK(e1);
   CK(e2);
+  CK(e3);
   CK(cudaGetLastError());
   if (stt) return fail(AMGEIG_ENOTSPD, "coarsest M_n or A_n is not positive definite");
+  h->modes_ready = prefetch;
   *out = h.release();
   return AMGEIG_OK;
+}
+
+}  // namespace
+
+int amgeig_load_hierarchy(const void* blob, size_t bytes, int device, amgeig_hierarchy* out) {
+  return load_hierarchy(blob, bytes, device, -1, out);
+}
+
+int amgeig_load_hierarchy_modes(const void* blob, size_t bytes, int device, int modes, amgeig_hierarchy* out) {
+  if (modes < 0) {
+    g_last_error.clear();
+    return fail(AMGEIG_EINVAL, "modes must be >= 0");
+  }
+  return load_hierarchy(blob, bytes, device, modes, out);
 }
 
 int amgeig_free_hierarchy(amgeig_hierarchy h) {

@@ -455,6 +455,32 @@ def test_coarse_modes_on_demand():
     assert np.max(np.abs(a_few2[0] - a_few[0]) / a_few[0]) < 1e-10
 
 
+def test_coarse_modes_during_load():
+    """amgeig_load_hierarchy_modes computes the coarse modes on a side stream during the
+    load: a solve on such a hierarchy gives the bits of the same solve on a hierarchy that
+    computes them on demand (same mode count), for a truncated and for the full pencil, and
+    a solve that needs more modes than were loaded computes them itself."""
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    few = ae.options(q_extra=2, fixed_corrections=2, coarse_modes=16)
+    full = ae.options(q_extra=2, fixed_corrections=2)
+    with ae.Hierarchy(blob) as h:
+        ref_few = h.solve(6, tol=0.0, opt=few)
+    with ae.Hierarchy(blob) as h:
+        ref_full = h.solve(6, tol=0.0, opt=full)
+    with ae.Hierarchy(blob, modes=16) as h:
+        got_few = h.solve(6, tol=0.0, opt=few)
+        # more modes than were loaded: the whole basis is computed on this solve
+        got_full_after = h.solve(6, tol=0.0, opt=full)
+    for modes in (0, 10 ** 6):  # all modes; a count above d_n is clamped to all
+        with ae.Hierarchy(blob, modes=modes) as h:
+            got_full = h.solve(6, tol=0.0, opt=full)
+        assert np.array_equal(got_full[0], ref_full[0]) and np.array_equal(got_full[1], ref_full[1])
+    assert np.array_equal(got_few[0], ref_few[0]) and np.array_equal(got_few[1], ref_few[1])
+    assert np.array_equal(got_full_after[0], ref_full[0]) and np.array_equal(got_full_after[1], ref_full[1])
+    with pytest.raises(ae.AmgEigError):
+        ae.amgeig_load_hierarchy_modes(blob, 0, -1)
+
+
 @pytest.mark.parametrize("L", [1, 3])
 def test_coarse_modes_parity(L):
     """The truncated coarse space (coarse_modes option) matches the oracle's same option."""
