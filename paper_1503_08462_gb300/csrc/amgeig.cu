@@ -285,19 +285,45 @@ HostCsr transpose(const CsrView& P) {
 
 // ------------------------------------------------------------------ device data
 
+// Device memory of one owner (a hierarchy, a solve workspace), released with it.
+// Arrays of 2 MiB and more get a cudaMalloc of their own; smaller ones are carved,
+// 256-byte aligned, from blocks (2 MiB, then 8 MiB).  A hierarchy holds ~200 arrays,
+// most of them small, and each cudaMalloc / cudaFree costs tens of microseconds (a
+// cudaFree synchronises the device), so loading and releasing one takes a few dozen
+// calls instead of hundreds.
 struct DeviceBuffers {
-  std::vector<void*> ptrs;
+  static constexpr size_t kOwn = size_t(2) << 20, kAlign = 256;
+  std::vector<void*> ptrs;  // every cudaMalloc of this owner
+  char* blk = nullptr;      // free tail of the current block of small arrays
+  size_t blk_left = 0;
   cudaStream_t st = nullptr;  // uploads are ordered on this stream (the hierarchy's)
   ~DeviceBuffers() {
     for (void* p : ptrs) cudaFree(p);
   }
   template <typename T>
   cudaError_t alloc(T** out, size_t count) {
+    const size_t bytes = (sizeof(T) * (count > 0 ? count : 1) + kAlign - 1) / kAlign * kAlign;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(T) * (count > 0 ? count : 1));
-    if (e == cudaSuccess) ptrs.push_back(p);
-    *out = static_cast<T*>(p);
-    return e;
+    *out = nullptr;
+    if (bytes >= kOwn) {
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) return e;
+      ptrs.push_back(p);
+      *out = static_cast<T*>(p);
+      return cudaSuccess;
+    }
+    if (bytes > blk_left) {
+      const size_t block = ptrs.empty() ? kOwn : size_t(8) << 20;  // > bytes
+      cudaError_t e = cudaMalloc(&p, block);
+      if (e != cudaSuccess) return e;
+      ptrs.push_back(p);
+      blk = static_cast<char*>(p);
+      blk_left = block;
+    }
+    *out = reinterpret_cast<T*>(blk);
+    blk += bytes;
+    blk_left -= bytes;
+    return cudaSuccess;
   }
   template <typename T>
   cudaError_t upload(T** out, const T* src, size_t count) {
@@ -1191,32 +1217,16 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   h->dinv64.assign(n, nullptr);
   h->dinv32.assign(n, nullptr);
   // the blob's arrays go to the device as they are (stream-ordered copies); the
-  // float32 and float-float copies of the values are made there
-  std::vector<std::vector<double>> d64s(n);
-  std::vector<std::vector<float>> d32s(n);
+  // float32 and float-float copies of the values and the l1-Jacobi inverse
+  // diagonals are made there
+  int* zero_row = nullptr;
+  CK(m.alloc(&zero_row, 1));
+  CK(cudaMemsetAsync(zero_row, 0, sizeof(int), h->stream));
   for (int l = 0; l < n; ++l) {
     const CsrView& L = levels[l];
     DevCsr& D = h->A[l];
     D.rows = D.cols = static_cast<int>(L.rows);
     D.nnz = static_cast<int>(L.nnz);
-    // l1-Jacobi inverse diagonal 1 / sum_j |a_ij| (host threads over rows)
-    std::vector<double>& d64 = d64s[l];
-    std::vector<float>& d32 = d32s[l];
-    d64.resize(static_cast<size_t>(L.rows));
-    d32.resize(static_cast<size_t>(L.rows));
-    const int T = host_threads(L.rows);
-    std::vector<char> ok(T, 1);
-    parallel_for(T, [&](int t) {
-      for (int64_t i = L.rows * t / T; i < L.rows * (t + 1) / T; ++i) {
-        double sa = 0.0;
-        for (int32_t p = L.rp[i]; p < L.rp[i + 1]; ++p) sa += std::fabs(L.a[p]);
-        if (!(sa > 0.0)) ok[t] = 0;
-        d64[i] = 1.0 / sa;
-        d32[i] = static_cast<float>(1.0 / sa);
-      }
-    });
-    for (char c : ok)
-      if (!c) return fail(AMGEIG_ECORRUPT, "zero row in A");
     CK(m.upload(&D.rp, L.rp, static_cast<size_t>(L.rows) + 1));
     CK(m.upload(&D.ci, L.ci, static_cast<size_t>(L.nnz)));
     CK(m.upload(&D.v64, L.a, static_cast<size_t>(L.nnz)));
@@ -1227,8 +1237,9 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
     launch_convert_f64_to_f32(D.v64, L.nnz, D.v32, h->stream);
     launch_f64_to_df(D.v64, L.nnz, D.d2, h->stream);
     launch_f64_to_df(D.m64, L.nnz, D.m2, h->stream);
-    CK(m.upload(&h->dinv64[l], d64));
-    CK(m.upload(&h->dinv32[l], d32));
+    CK(m.alloc(&h->dinv64[l], static_cast<size_t>(L.rows)));
+    CK(m.alloc(&h->dinv32[l], static_cast<size_t>(L.rows)));
+    launch_l1_inv_diag(D, h->dinv64[l], h->dinv32[l], zero_row, h->stream);
   }
   h->P.resize(n - 1);
   h->R.resize(n - 1);
@@ -1314,14 +1325,17 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
       nv = prev.p;
     }
   }
-  int stt = 0;
+  int stt = 0, zr = 0;
   cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, side.s);
   cudaError_t e2 = cudaStreamSynchronize(side.s);
-  cudaError_t e3 = cudaStreamSynchronize(h->stream);
+  cudaError_t e3 = cudaMemcpyAsync(&zr, zero_row, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e4 = cudaStreamSynchronize(h->stream);
   CK(e1);
   CK(e2);
   CK(e3);
+  CK(e4);
   CK(cudaGetLastError());
+  if (zr) return fail(AMGEIG_ECORRUPT, "zero row in A");
   if (stt) return fail(AMGEIG_ENOTSPD, "coarsest M_n or A_n is not positive definite");
   h->modes_ready = prefetch;
   *out = h.release();

@@ -85,6 +85,9 @@ void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st)
 
 // float64 -> float32 / float32 -> float64 copies
 void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st);
+// l1-Jacobi inverse diagonal 1 / sum_j |a_ij| of A (float64 and float32 copies);
+// *zero_row (device) is set to 1 when a row sum is not positive
+void launch_l1_inv_diag(const DevCsr& A, double* d64, float* d32, int* zero_row, cudaStream_t st);
 // One level of the composite prolongation I_n^k = P_k I_n^{k+1} (next: CSR with
 // d_n columns, float64 values).  out_rp null: counts[i] = nonzeros of row i;
 // otherwise rows i fill out_ci / out_v from out_rp[i] in column order.

@@ -45,6 +45,7 @@ constexpr int kSyThreads = AMGEIG_SY_THREADS;
 
 struct PencilWork {
   int dn = 0, qmax = 0, nmax = 0;
+  void* base = nullptr;  // one device allocation holding every array below
   // Rayleigh-Ritz pencil (float-float)
   df* KB = nullptr;   // dn x 2q   Z_m^T C = [K | B]
   df* Ft = nullptr;   // dn x q    K - Theta B
@@ -2137,46 +2138,59 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
   w->nwant_max = dn > qmax ? dn : qmax;
   const long long nm = w->nmax;
   const long long nwm = w->nwant_max;
-  cudaError_t e = cudaSuccess;
+  // two passes over the same list: sizes (256-byte aligned) into one allocation,
+  // then the arrays' places in it
+  size_t total = 0;
+  char* at = nullptr;
   auto alloc = [&](void** p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 8);
+    const size_t b = ((bytes > 0 ? bytes : 8) + 255) / 256 * 256;
+    if (at) {
+      *p = at;
+      at += b;
+    } else {
+      total += b;
+    }
   };
-  alloc((void**)&w->KB, sizeof(df) * dn * 2 * qmax);
-  alloc((void**)&w->Ft, sizeof(df) * dn * qmax);
-  alloc((void**)&w->Tt, sizeof(df) * qmax * qmax);
-  alloc((void**)&w->St, sizeof(df) * qmax * qmax);
-  alloc((void**)&w->Lq, sizeof(df) * qmax * qmax);
-  alloc((void**)&w->Xq, sizeof(df) * qmax * qmax);
-  alloc((void**)&w->H, sizeof(double) * nm * nm);
-  alloc((void**)&w->Yh, sizeof(double) * nm * nwm);
-  alloc((void**)&w->W, sizeof(df) * nm * (nm + 1));
-  alloc((void**)&w->tau, sizeof(df) * nm);
-  alloc((void**)&w->dd, sizeof(df) * nm);
-  alloc((void**)&w->ee, sizeof(df) * nm);
-  alloc((void**)&w->fac, sizeof(df) * 6 * nm * nwm);
-  alloc((void**)&w->Zt, sizeof(df) * nm * nwm);
-  alloc((void**)&w->rr, sizeof(df) * 4 * (nwm * nwm > 4 * nwm ? nwm * nwm : 4 * nwm));
-  alloc((void**)&w->perm, sizeof(int) * nwm);
-  alloc((void**)&w->Lm, sizeof(double) * dn * dn);
-  alloc((void**)&w->Hs, sizeof(double) * dn * dn);
-  alloc((void**)&w->sr_mu, sizeof(double) * qmax);
-  alloc((void**)&w->sr_X, sizeof(double) * nm * qmax);
-  alloc((void**)&w->sr_conv, sizeof(int) * qmax);
-  alloc((void**)&w->sr_flag, 4 * sizeof(int));
-  if (err) *err = e;
-  if (e != cudaSuccess) {
-    pencil_work_destroy(w);
-    return nullptr;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      cudaError_t e = cudaMalloc(&w->base, total);
+      if (err) *err = e;
+      if (e != cudaSuccess) {
+        w->base = nullptr;
+        pencil_work_destroy(w);
+        return nullptr;
+      }
+      at = static_cast<char*>(w->base);
+    }
+    alloc((void**)&w->KB, sizeof(df) * dn * 2 * qmax);
+    alloc((void**)&w->Ft, sizeof(df) * dn * qmax);
+    alloc((void**)&w->Tt, sizeof(df) * qmax * qmax);
+    alloc((void**)&w->St, sizeof(df) * qmax * qmax);
+    alloc((void**)&w->Lq, sizeof(df) * qmax * qmax);
+    alloc((void**)&w->Xq, sizeof(df) * qmax * qmax);
+    alloc((void**)&w->H, sizeof(double) * nm * nm);
+    alloc((void**)&w->Yh, sizeof(double) * nm * nwm);
+    alloc((void**)&w->W, sizeof(df) * nm * (nm + 1));
+    alloc((void**)&w->tau, sizeof(df) * nm);
+    alloc((void**)&w->dd, sizeof(df) * nm);
+    alloc((void**)&w->ee, sizeof(df) * nm);
+    alloc((void**)&w->fac, sizeof(df) * 6 * nm * nwm);
+    alloc((void**)&w->Zt, sizeof(df) * nm * nwm);
+    alloc((void**)&w->rr, sizeof(df) * 4 * (nwm * nwm > 4 * nwm ? nwm * nwm : 4 * nwm));
+    alloc((void**)&w->perm, sizeof(int) * nwm);
+    alloc((void**)&w->Lm, sizeof(double) * dn * dn);
+    alloc((void**)&w->Hs, sizeof(double) * dn * dn);
+    alloc((void**)&w->sr_mu, sizeof(double) * qmax);
+    alloc((void**)&w->sr_X, sizeof(double) * nm * qmax);
+    alloc((void**)&w->sr_conv, sizeof(int) * qmax);
+    alloc((void**)&w->sr_flag, 4 * sizeof(int));
   }
   return w;
 }
 
 void pencil_work_destroy(PencilWork* w) {
   if (!w) return;
-  void* ptrs[] = {w->KB, w->Ft, w->Tt, w->St, w->Lq, w->Xq, w->H, w->Yh, w->W, w->tau, w->dd, w->ee,
-                  w->fac, w->Zt, w->rr, w->perm, w->Lm, w->Hs, w->sr_mu, w->sr_X, w->sr_conv, w->sr_flag};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  if (w->base) cudaFree(w->base);
   delete w;
 }
 

@@ -612,6 +612,20 @@ __global__ void k_f64_to_f32(const double* __restrict__ x, long long count, floa
     y[i] = static_cast<float>(x[i]);
 }
 
+// l1-Jacobi inverse diagonal of one level: d_i = 1 / sum_j |a_ij| (the row summed in
+// order, float64), also rounded to float32; *zero_row = 1 when a row sum is not positive
+__global__ void k_l1_inv_diag(int rows, const int* __restrict__ rp, const double* __restrict__ a,
+                              double* __restrict__ d64, float* __restrict__ d32, int* __restrict__ zero_row) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+    double sa = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) sa += fabs(a[p]);
+    if (!(sa > 0.0)) *zero_row = 1;
+    const double d = 1.0 / sa;
+    d64[i] = d;
+    d32[i] = static_cast<float>(d);
+  }
+}
+
 __global__ void k_f32_to_f64(const float* __restrict__ x, long long count, double* __restrict__ y) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
@@ -917,6 +931,11 @@ void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st)
 void launch_convert_f64_to_f32(const double* x, long long count, float* y, cudaStream_t st) {
   ProfScope ps(st, P_OTHER, 12.0 * count, 0.0);
   k_f64_to_f32<<<grid_for(count), kThreads, 0, st>>>(x, count, y);
+}
+
+void launch_l1_inv_diag(const DevCsr& A, double* d64, float* d32, int* zero_row, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 4.0 * (A.rows + 1) + 8.0 * A.nnz + 12.0 * A.rows, 0.0);
+  k_l1_inv_diag<<<grid_for(A.rows), kThreads, 0, st>>>(A.rows, A.rp, A.v64, d64, d32, zero_row);
 }
 
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st) {
