@@ -190,8 +190,11 @@ void parallel_for(int T, F f) {
   for (auto& x : th) x.join();
 }
 
+// The blob's layout: magic, header and in-place views of every array, each
+// bounds-checked against the blob; *base receives the blob or its aligned copy.
+// The content (checksum, CSR structure) is checked by validate_blob.
 int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std::vector<CsrView>& prolong,
-               std::vector<uint64_t>& aligned) {
+               std::vector<uint64_t>& aligned, const uint8_t** base) {
   const uint8_t* b = static_cast<const uint8_t*>(blob);
   if (reinterpret_cast<uintptr_t>(b) % 8 != 0) {
     // the views need 8-byte alignment: one aligned copy of an unaligned blob
@@ -201,26 +204,7 @@ int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std
   }
   if (bytes < 24 || bytes % 8 != 0 || std::memcmp(b, "AMGEIGH1", 8) != 0)
     return fail(AMGEIG_ECORRUPT, "not a hierarchy blob (magic/length)");
-  uint64_t sum = 0, stored;
-  {
-    // word sum (mod 2^64) of everything before the stored checksum, in slices
-    const size_t words = (bytes - 8) / 8;
-    const int T = host_threads(static_cast<int64_t>(words / 64));
-    std::vector<uint64_t> part(T, 0);
-    parallel_for(T, [&](int t) {
-      const size_t lo = words * t / T, hi = words * (t + 1) / T;
-      uint64_t acc = 0;
-      for (size_t i = lo; i < hi; ++i) {
-        uint64_t w;
-        std::memcpy(&w, b + 8 * i, 8);
-        acc += w;
-      }
-      part[t] = acc;
-    });
-    for (uint64_t x : part) sum += x;
-  }
-  std::memcpy(&stored, b + bytes - 8, 8);
-  if (sum != stored) return fail(AMGEIG_ECORRUPT, "hierarchy blob checksum mismatch");
+  *base = b;
   uint32_t version, n;
   std::memcpy(&version, b + 8, 4);
   std::memcpy(&n, b + 12, 4);
@@ -248,7 +232,6 @@ int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std
     L.nnz = static_cast<int64_t>(nnz[l]);
     if (!rd.view(&L.rp, rows[l] + 1) || !rd.view(&L.ci, nnz[l]) || !rd.view(&L.a, nnz[l]) || !rd.view(&L.m, nnz[l]))
       return fail(AMGEIG_ECORRUPT, "truncated level arrays");
-    if (!csr_valid(L)) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
   }
   for (uint32_t l = 0; l + 1 < n; ++l) {
     CsrView& P = prolong[l];
@@ -258,9 +241,39 @@ int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std
     if (nnzp[l] >= (1ull << 31)) return fail(AMGEIG_ECORRUPT, "prolongation size out of range");
     if (!rd.view(&P.rp, rows[l] + 1) || !rd.view(&P.ci, nnzp[l]) || !rd.view(&P.a, nnzp[l]))
       return fail(AMGEIG_ECORRUPT, "truncated prolongation arrays");
-    if (!csr_valid(P)) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
   }
   if (rd.off != bytes - 8) return fail(AMGEIG_ECORRUPT, "trailing bytes in blob");
+  return AMGEIG_OK;
+}
+
+// The blob's content: the u64 word-sum checksum trailer and the CSR structure
+// (row offsets, column bounds) of every level and transfer operator.
+int validate_blob(const uint8_t* b, size_t bytes, const std::vector<CsrView>& levels,
+                  const std::vector<CsrView>& prolong) {
+  uint64_t sum = 0, stored;
+  {
+    // word sum (mod 2^64) of everything before the stored checksum, in slices
+    const size_t words = (bytes - 8) / 8;
+    const int T = host_threads(static_cast<int64_t>(words / 64));
+    std::vector<uint64_t> part(T, 0);
+    parallel_for(T, [&](int t) {
+      const size_t lo = words * t / T, hi = words * (t + 1) / T;
+      uint64_t acc = 0;
+      for (size_t i = lo; i < hi; ++i) {
+        uint64_t w;
+        std::memcpy(&w, b + 8 * i, 8);
+        acc += w;
+      }
+      part[t] = acc;
+    });
+    for (uint64_t x : part) sum += x;
+  }
+  std::memcpy(&stored, b + bytes - 8, 8);
+  if (sum != stored) return fail(AMGEIG_ECORRUPT, "hierarchy blob checksum mismatch");
+  for (const CsrView& L : levels)
+    if (!csr_valid(L)) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
+  for (const CsrView& P : prolong)
+    if (!csr_valid(P)) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
   return AMGEIG_OK;
 }
 
@@ -1152,8 +1165,13 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
     return fail(AMGEIG_EINVAL, "no such CUDA device");
   std::vector<CsrView> levels, prolong;
   std::vector<uint64_t> aligned;
-  int rc = parse_blob(blob, bytes, levels, prolong, aligned);
+  const uint8_t* base = nullptr;
+  int rc = parse_blob(blob, bytes, levels, prolong, aligned, &base);
   if (rc) return rc;
+  // the coarsest level is checked on its own: its GPU work starts before the
+  // rest of the blob is validated
+  if (levels.back().rows > 4096) return fail(AMGEIG_EINVAL, "coarsest level larger than 4096");
+  if (!csr_valid(levels.back())) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
   CK(cudaSetDevice(device));
   auto h = std::make_unique<amgeig_hierarchy_t>();
   h->device = device;
@@ -1161,13 +1179,13 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   const int n = h->nlev;
   for (auto& L : levels) h->sizes.push_back(L.rows);
   h->dn = static_cast<int>(h->sizes[n - 1]);
-  if (h->dn > 4096) return fail(AMGEIG_EINVAL, "coarsest level larger than 4096");
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
   auto& m = h->mem;
   m.st = h->stream;
-  // The coarsest level goes first, on a second stream: the GPU factors it (and
-  // computes the asked-for lowest eigenpairs, Algorithm 3.2 step 1) while the
-  // host prepares the finer levels.  The stream is drained before any return.
+  // The coarsest level goes first, on two more streams: the GPU factors M_n
+  // (and computes the asked-for lowest eigenpairs, Algorithm 3.2 step 1) on
+  // one and inverts A_n on the other while the host validates the blob and
+  // prepares the finer levels.  Both are drained before any return.
   struct SideStream {
     cudaStream_t s = nullptr;
     ~SideStream() {
@@ -1176,8 +1194,16 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
         cudaStreamDestroy(s);
       }
     }
-  } side;
+  } side, side2;
+  struct Event {
+    cudaEvent_t e = nullptr;
+    ~Event() {
+      if (e) cudaEventDestroy(e);
+    }
+  } uploaded;
   CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&side2.s, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&uploaded.e, cudaEventDisableTiming));
   const int dn = h->dn;
   std::vector<double> An(static_cast<size_t>(dn) * dn, 0.0), Mn(static_cast<size_t>(dn) * dn, 0.0);
   {
@@ -1198,21 +1224,38 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   CK(m.alloc(&h->Ainv32, static_cast<size_t>(dn) * dn));
   CK(m.alloc(&h->Zdf, static_cast<size_t>(dn) * dn));
   CK(m.alloc(&h->dstatus, 4));
-  CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), side.s));
+  CK(cudaMemsetAsync(h->dstatus, 0, 2 * sizeof(int), side.s));  // [0]: M_n factor, [1]: A_n inverse
+  CK(cudaEventRecord(uploaded.e, side.s));
+  CK(cudaStreamWaitEvent(side2.s, uploaded.e, 0));
   {
     cudaError_t e;
     h->cpw = pencil_work_create(dn, 1, &e);
     if (!h->cpw) return fail(AMGEIG_ENOMEM, std::string("coarse workspace: ") + cudaGetErrorString(e));
   }
-  // the exact coarsest solve of the V-cycle (float64 Cholesky)
-  launch_coarse_inverse(h->cpw, dn, h->An, h->Mn, h->Ainv, h->dstatus, side.s);
-  launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, side.s);
+  launch_mass_factor(h->cpw, dn, h->Mn, h->dstatus, side.s);
   const int prefetch = modes < 0 ? 0 : (modes == 0 || modes > dn ? dn : modes);
   if (prefetch > 0) {
     launch_coarse_modes(h->cpw, dn, prefetch, h->An, h->Z, h->theta, side.s);
     launch_f64_to_df(h->Z, static_cast<long long>(dn) * dn, h->Zdf, side.s);
   }
+  // the exact coarsest solve of the V-cycle (float64 Cholesky), its two dn x dn
+  // scratch matrices stream-ordered on side2
+  struct SideTemp {
+    double* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~SideTemp() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  } Lf, Li;
+  Lf.s = Li.s = side2.s;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&Lf.p), sizeof(double) * dn * dn, side2.s));
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&Li.p), sizeof(double) * dn * dn, side2.s));
+  launch_coarse_inverse(dn, h->An, Lf.p, Li.p, h->Ainv, h->dstatus + 1, side2.s);
+  launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, side2.s);
   CK(cudaGetLastError());
+  // the rest of the blob (checksum, every CSR) on host threads meanwhile
+  rc = validate_blob(base, bytes, levels, prolong);
+  if (rc) return rc;
   h->A.resize(n);
   h->dinv64.assign(n, nullptr);
   h->dinv32.assign(n, nullptr);
@@ -1325,18 +1368,20 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
       nv = prev.p;
     }
   }
-  int stt = 0, zr = 0;
-  cudaError_t e1 = cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, side.s);
-  cudaError_t e2 = cudaStreamSynchronize(side.s);
+  int stt[2] = {0, 0}, zr = 0;
+  cudaError_t e0 = cudaStreamSynchronize(side2.s);
+  cudaError_t e1 = cudaStreamSynchronize(side.s);
+  cudaError_t e2 = cudaMemcpyAsync(stt, h->dstatus, 2 * sizeof(int), cudaMemcpyDeviceToHost, side.s);
   cudaError_t e3 = cudaMemcpyAsync(&zr, zero_row, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e4 = cudaStreamSynchronize(h->stream);
+  CK(e0);
   CK(e1);
   CK(e2);
   CK(e3);
   CK(e4);
   CK(cudaGetLastError());
   if (zr) return fail(AMGEIG_ECORRUPT, "zero row in A");
-  if (stt) return fail(AMGEIG_ENOTSPD, "coarsest M_n or A_n is not positive definite");
+  if (stt[0] || stt[1]) return fail(AMGEIG_ENOTSPD, "coarsest M_n or A_n is not positive definite");
   h->modes_ready = prefetch;
   *out = h.release();
   return AMGEIG_OK;

@@ -190,15 +190,18 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
                          const double* G, const float2* Zdf, const double* theta, double* mu, double* Xc,
                          float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback = nullptr);
 
-// The coarsest level's exact solve: Ainv = A_n^-1 (dn x dn, row-major) from
-// the float64 Cholesky factor A_n = L L^T as L^-T L^-1; status = ENOTSPD when
-// A_n is not positive definite.  Also factors M_n = L_m L_m^T into the
-// workspace (its Cholesky is the check that M_n is positive definite and the
-// first step of launch_coarse_modes).
-void launch_coarse_inverse(PencilWork* w, int dn, const double* An, const double* Mn, double* Ainv, int* status,
+// The float64 Cholesky factor M_n = L_m L_m^T into the workspace (the first step
+// of launch_coarse_modes, and the check that M_n is positive definite: status =
+// ENOTSPD otherwise).
+void launch_mass_factor(PencilWork* w, int dn, const double* Mn, int* status, cudaStream_t st);
+// The coarsest level's exact solve: Ainv = A_n^-1 (dn x dn, row-major) from the
+// float64 Cholesky factor A_n = L L^T as L^-T L^-1; L and Linv are dn x dn
+// scratch; status = ENOTSPD when A_n is not positive definite.  Independent of
+// the workspace, so it can run beside launch_mass_factor / launch_coarse_modes.
+void launch_coarse_inverse(int dn, const double* An, double* L, double* Linv, double* Ainv, int* status,
                            cudaStream_t st);
 // The nwant lowest eigenpairs of the coarsest pencil (A_n, M_n) (needs the
-// M_n factor of launch_coarse_inverse in the same workspace): the first nwant
+// M_n factor of launch_mass_factor in the same workspace): the first nwant
 // columns of Z (dn x dn row-major, stride dn) with Z^T M_n Z = I and
 // Z^T A_n Z = diag(theta), theta ascending.
 void launch_coarse_modes(PencilWork* w, int dn, int nwant, const double* An, double* Z, double* theta,

@@ -2299,16 +2299,19 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   }
 }
 
-void launch_coarse_inverse(PencilWork* w, int dn, const double* An, const double* Mn, double* Ainv, int* status,
+void launch_mass_factor(PencilWork* w, int dn, const double* Mn, int* status, cudaStream_t st) {
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 2, dn * static_cast<double>(dn) * dn / 3.0, 1);
+  k_chol<<<1, 1024, 0, st>>>(dn, Mn, w->Lm, status);
+}
+
+void launch_coarse_inverse(int dn, const double* An, double* L, double* Linv, double* Ainv, int* status,
                            cudaStream_t st) {
   ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 5, 2.0 * dn * dn * dn, 4);
-  // M_n = L_m L_m^T (kept for the eigenbasis); A_n = L L^T
-  k_chol<<<1, 1024, 0, st>>>(dn, Mn, w->Lm, status);
-  k_chol<<<1, 1024, 0, st>>>(dn, An, w->Hs, status);
-  // H = L^-1 (the identity solved in place), Ainv = H^T H = L^-T L^-1
-  k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->H);
-  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Hs, w->H, dn, dn, 0);
-  launch_gemm_f64(dn, dn, dn, 1.0, w->H, dn, true, w->H, dn, false, 0.0, Ainv, dn, st);
+  // A_n = L L^T; Linv = L^-1 (the identity solved in place); Ainv = Linv^T Linv = L^-T L^-1
+  k_chol<<<1, 1024, 0, st>>>(dn, An, L, status);
+  k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, Linv);
+  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, L, Linv, dn, dn, 0);
+  launch_gemm_f64(dn, dn, dn, 1.0, Linv, dn, true, Linv, dn, false, 0.0, Ainv, dn, st);
 }
 
 void launch_coarse_modes(PencilWork* w, int dn, int nwant, const double* An, double* Z, double* theta,
