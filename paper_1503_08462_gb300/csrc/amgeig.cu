@@ -87,13 +87,17 @@ __global__ void k_col_best(const double* __restrict__ U, int rows, int ld, int q
   }
 }
 
+// stage 2: one block (kSignThreads) per column; (max |u|, lowest index) is a
+// total order, so the pick does not depend on how the slabs are split
+constexpr int kSignThreads = 128;
 __global__ void k_col_sign2(const double* __restrict__ U, int ld, int q, int nslabs, const double* __restrict__ bval,
                             const int* __restrict__ bidx, double* __restrict__ sign) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= q) return;
+  __shared__ double sb[kSignThreads];
+  __shared__ int si[kSignThreads];
+  const int c = blockIdx.x, t = threadIdx.x;
   double best = -1.0;
   int bi = 0x7fffffff;
-  for (int s = 0; s < nslabs; ++s) {
+  for (int s = t; s < nslabs; s += kSignThreads) {
     const double b2 = bval[static_cast<long long>(s) * q + c];
     const int i2 = bidx[static_cast<long long>(s) * q + c];
     if (b2 > best || (b2 == best && i2 < bi)) {
@@ -101,7 +105,21 @@ __global__ void k_col_sign2(const double* __restrict__ U, int ld, int q, int nsl
       bi = i2;
     }
   }
-  sign[c] = (bi != 0x7fffffff && U[static_cast<long long>(bi) * ld + c] < 0.0) ? -1.0 : 1.0;
+  sb[t] = best;
+  si[t] = bi;
+  __syncthreads();
+  for (int o = kSignThreads / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      const double b2 = sb[t + o];
+      const int i2 = si[t + o];
+      if (b2 > sb[t] || (b2 == sb[t] && i2 < si[t])) {
+        sb[t] = b2;
+        si[t] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (t == 0) sign[c] = (si[0] != 0x7fffffff && U[static_cast<long long>(si[0]) * ld + c] < 0.0) ? -1.0 : 1.0;
 }
 
 __global__ void k_out_vectors(const double* __restrict__ U, int rows, int ld, int q, const double* __restrict__ sign,
@@ -1016,12 +1034,12 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
     const long long total = static_cast<long long>(N0) * q;
     ProfScope ps(st, P_OTHER, 8.0 * N0 * qt + 16.0 * total, 0.0, 3);
     {
-      const int slab = 4096, nslabs = ceil_div(N0, slab);
+      const int slab = 512, nslabs = ceil_div(N0, slab);
       // the slab results live in W, free after the solve (nslabs * q <= N0 * 2q)
       double* bval = w->W;
       int* bidx = reinterpret_cast<int*>(w->W + static_cast<size_t>(nslabs) * q);
       k_col_best<<<nslabs, 256, 0, st>>>(src, N0, qt, q, slab, bval, bidx);
-      k_col_sign2<<<ceil_div(q, 128), 128, 0, st>>>(src, qt, q, nslabs, bval, bidx, w->sign);
+      k_col_sign2<<<q, kSignThreads, 0, st>>>(src, qt, q, nslabs, bval, bidx, w->sign);
     }
     k_out_vectors<<<static_cast<int>(std::min<long long>((total + 255) / 256, 8LL * kNumSms)), 256, 0, st>>>(
         src, N0, qt, q, w->sign, dst);
