@@ -2001,7 +2001,22 @@ __global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0
   for (int idx = tid; idx < m * qc; idx += nt) {
     const int i = idx / qc, jj = idx % qc;
     const df* Bi = KB + static_cast<long long>(i) * q2 + q;
-    tmp[idx] = df_sub(to_df(evecs[static_cast<long long>(i) * q + j0 + jj]), dot4(Bi, 1, bs + jj, qc, q).value());
+    // the four-accumulator dot of dot4, unrolled so that the loads of B's row
+    // (L2) are in flight together
+    df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
+    int t = 0;
+#pragma unroll 4
+    for (; t + 4 <= q; t += 4) {
+      c0.fma(Bi[t], bs[t * qc + jj]);
+      c1.fma(Bi[t + 1], bs[(t + 1) * qc + jj]);
+      c2.fma(Bi[t + 2], bs[(t + 2) * qc + jj]);
+      c3.fma(Bi[t + 3], bs[(t + 3) * qc + jj]);
+    }
+    for (; t < q; ++t) c0.fma(Bi[t], bs[t * qc + jj]);
+    c0.merge(c1);
+    c2.merge(c3);
+    c0.merge(c2);
+    tmp[idx] = df_sub(to_df(evecs[static_cast<long long>(i) * q + j0 + jj]), c0.value());
   }
   __syncthreads();
   const int rows = (dn + gridDim.x - 1) / gridDim.x;
@@ -2011,7 +2026,8 @@ __global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0
     const float2* zl = Zdf + static_cast<long long>(l) * dn;
     df_acc s0 = acc_zero(), s1 = acc_zero();
     int i = 0;
-    for (; i + 2 <= m; i += 2) {
+#pragma unroll 8
+    for (; i + 2 <= m; i += 2) {  // unrolled: the row's loads (L2) in flight together
       s0.fma(to_df(zl[i]), tmp[i * qc + jj]);
       s1.fma(to_df(zl[i + 1]), tmp[(i + 1) * qc + jj]);
     }
@@ -2295,7 +2311,7 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
     const int wc = std::min(qc, q - j0);
     const size_t xsc = sizeof(df) * static_cast<size_t>(m + q) * wc;
     smem_attr((const void*)k_xc, xsc);
-    k_xc<<<16, kPenThreads, xsc, st>>>(dn, m, q, j0, wc, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
+    k_xc<<<64, kPenThreads, xsc, st>>>(dn, m, q, j0, wc, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
   }
 }
 
