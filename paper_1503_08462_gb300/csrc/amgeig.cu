@@ -384,8 +384,9 @@ struct amgeig_hierarchy_t {
   std::vector<DevCsr> PC;    // PC[k] = I_n^k = P_k ... P_{n-2} (rows_k x d_n), float-float values
   int dn = 0;
   double *An = nullptr, *Mn = nullptr, *Z = nullptr, *theta = nullptr, *Ainv = nullptr;
-  // the coarse eigenbasis is computed on demand: modes_ready leading columns of
-  // Z (and theta) are valid; cpw keeps the M_n factor and the solver's scratch
+  // the coarse eigenbasis is computed during the load (amgeig_load_hierarchy_modes)
+  // or on the first solve that needs it: modes_ready leading columns of Z (and
+  // theta) are valid; cpw keeps the M_n factor and the solver's scratch
   int modes_ready = 0;
   PencilWork* cpw = nullptr;
   float* Ainv32 = nullptr;
