@@ -47,7 +47,14 @@ Readings of the paper taken here (they are listed with the rest of the design):
   paper does (Sec. 4.1), made parallel by a multicolour ordering: rows are
   coloured first-fit in row order (the smallest colour no earlier neighbour
   holds) and one sweep visits the colours in ascending order before the coarse
-  correction and in descending order after it, so the V-cycle stays symmetric.
+  correction and in descending order after it, so the V-cycle stays symmetric;
+* with ``Options.shift = sigma`` the linear solve of step 1 is shifted, one of
+  the strategies the remark after Algorithm 3.1 allows: m AMG iterations for
+  (A_k - sigma M_k) u~ = (lambda_j - sigma) M_k u_j from u_j, on the hierarchy
+  of A_l - sigma M_l (Galerkin-consistent, since both A and M are Galerkin
+  products), with its l1-Jacobi diagonals and an exact coarsest solve; sigma
+  must lie below the lowest eigenvalue of (A_n, M_n) so that every level's
+  operator is positive definite.  sigma = 0 is the paper's unshifted solve.
 """
 from __future__ import annotations
 
@@ -77,6 +84,7 @@ class OracleHierarchy:
     Mn: np.ndarray  # dense coarsest M
     An_chol: tuple  # scipy cho_factor of An
     colour_cache: dict = dataclasses.field(default_factory=dict)  # level -> Gauss-Seidel colours
+    shift_cache: dict = dataclasses.field(default_factory=dict)  # sigma -> shifted hierarchy
 
     @property
     def n_levels(self) -> int:
@@ -142,6 +150,26 @@ def read_blob(blob: bytes) -> OracleHierarchy:
 
 # --------------------------------------------------------------------------
 # AMG linear solver (Algorithm 3.1 step 1)
+
+
+def shifted(h: OracleHierarchy, sigma: float) -> OracleHierarchy:
+    """The hierarchy of the shifted operators A_l - sigma M_l (same pattern, same
+    transfers) with their l1-Jacobi diagonals and the Cholesky factor of the
+    shifted coarsest matrix.  Raises ValueError when that matrix is not positive
+    definite (sigma at or above the lowest eigenvalue of (A_n, M_n))."""
+    if sigma in h.shift_cache:
+        return h.shift_cache[sigma]
+    B = [sp.csr_matrix((a.data - sigma * m.data, a.indices, a.indptr), shape=a.shape) for a, m in zip(h.A, h.M)]
+    dinv = [1.0 / np.asarray(abs(b).sum(axis=1)).ravel() for b in B[:-1]]
+    Bn = B[-1].toarray()
+    try:
+        chol = sla.cho_factor(Bn, lower=True)
+    except np.linalg.LinAlgError as e:
+        raise ValueError("shift not below the lowest coarse eigenvalue") from e
+    # same sparsity pattern: the Gauss-Seidel colouring is shared
+    hs = OracleHierarchy(B, h.M, h.P, h.R, dinv, Bn, h.Mn, chol, colour_cache=h.colour_cache)
+    h.shift_cache[sigma] = hs
+    return hs
 
 
 def jacobi_l1(h: OracleHierarchy, l: int, b: np.ndarray, x: np.ndarray) -> np.ndarray:
@@ -250,6 +278,8 @@ class Options:
     # eigenvectors of (A_n, M_n) instead of all of V_n (an option of the GPU
     # library, not of the paper; 0 = the paper's pencil)
     coarse_modes: int = 0
+    # sigma of the shifted linear solve in step 1 (0 = the paper's unshifted solve)
+    shift: float = 0.0
 
 
 def augmented_pencil(h: OracleHierarchy, k: int, V: np.ndarray):
@@ -278,8 +308,14 @@ def coarse_modes_basis(h: OracleHierarchy, m: int) -> np.ndarray:
 def correction(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
     """One AMGCorrection(n, k, {lambda_j, u_j}) step; returns (lambda, U)."""
     qt = U.shape[1]
-    b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
-    V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
+    if opts.shift != 0.0:
+        # (A_k - sigma M_k) u~ = (lambda_j - sigma) M_k u_j, on the shifted hierarchy
+        hs = shifted(h, opts.shift)
+        b = h.M[k] @ U * (lam - opts.shift)[None, :]
+        V = amg(hs, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
+    else:
+        b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
+        V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
     Ahat, Mhat = augmented_pencil(h, k, V)
     dn = h.sizes[-1]
     if 0 < opts.coarse_modes < dn:

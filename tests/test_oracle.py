@@ -283,3 +283,69 @@ def test_gs_solve_matches_dense_definition():
     assert np.all(np.abs(lam - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
     _, _, info_j = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
     assert info.corrections < info_j.corrections
+
+
+# ---------------------------------------------------------------- shifted inner solve
+
+
+def test_shifted_two_level_dense():
+    """The shifted solve's two-level cycle equals the dense formula for B = A - sigma M:
+    l1-Jacobi with D = diag(sum_j |b_ij|), the exact coarse correction with P^T B P, and
+    the same sweep after it.  A wrong sign of the shift, the unshifted diagonal or an
+    unshifted coarse matrix breaks the equality."""
+    p = meshes.square_2d(8)
+    h = hierarchy.build_for_problem(p, coarse_cap=25, max_levels=2)
+    oh = O.read_blob(hierarchy.to_blob(h))
+    assert oh.n_levels == 2
+    lam1 = sla.eigh(oh.A[0].toarray(), oh.M[0].toarray(), eigvals_only=True)[0]
+    sigma = 0.7 * lam1
+    B = oh.A[0].toarray() - sigma * oh.M[0].toarray()
+    P = oh.P[0].toarray()
+    D = np.diag(np.abs(B).sum(axis=1))
+    Bc_inv = np.linalg.inv(P.T @ B @ P)
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal(B.shape[0])
+    x0 = rng.standard_normal(B.shape[0])
+    x1 = x0 + np.linalg.solve(D, b - B @ x0)
+    x2 = x1 + P @ Bc_inv @ P.T @ (b - B @ x1)
+    x3 = x2 + np.linalg.solve(D, b - B @ x2)
+    got = O.amg(O.shifted(oh, sigma), 0, b, x0, 1)
+    assert np.allclose(got, x3, rtol=1e-11, atol=1e-11 * np.abs(x3).max())
+
+
+def test_shifted_vcycle_is_symmetric_and_contracting():
+    """For sigma below the lowest eigenvalue, B = A - sigma M is SPD on every level and the
+    shifted V-cycle is a symmetric operator whose error propagation contracts in the
+    B-norm; a shift at or above the coarsest level's lowest eigenvalue is refused."""
+    p, oh = _oh("square", 16, 20)
+    lam1 = sla.eigh(oh.A[0].toarray(), oh.M[0].toarray(), eigvals_only=True)[0]
+    hs = O.shifted(oh, 0.9 * lam1)
+    n = oh.sizes[0]
+    C = np.stack([O.vcycle(hs, 0, e, np.zeros(n)) for e in np.eye(n)], axis=1)
+    assert np.abs(C - C.T).max() <= 1e-12 * np.abs(C).max()
+    B = hs.A[0].toarray()
+    L = np.linalg.cholesky(B)
+    rho = np.linalg.norm(L.T @ (np.eye(n) - C @ B) @ np.linalg.inv(L.T), 2)
+    assert rho < 1.0, rho
+    lam1_coarse = sla.eigh(oh.An, oh.Mn, eigvals_only=True)[0]
+    with pytest.raises(ValueError):
+        O.shifted(oh, 1.01 * lam1_coarse)
+
+
+def test_shifted_solve_matches_dense_definition():
+    """Pin 1 with the shifted inner solve: exact eigenpairs stay a fixed point of the
+    shifted correction and the converged iteration reproduces the dense eigenpairs;
+    shifted inverse iteration needs no more corrections than the unshifted one."""
+    p, oh = _oh("lshape", 16, 60, 2)
+    lam_ex, U_ex = dense_pairs(p, 6)
+    sigma = 0.8 * lam_ex[0]
+    mu, U1 = O.correction(oh, 0, lam_ex, U_ex, O.Options(shift=sigma))
+    assert np.allclose(mu, lam_ex, rtol=1e-11)
+    assert m_subspace_angle(U1[:, :4], U_ex[:, :4], oh.M[0]) < 1e-8
+    opts = O.Options(q_extra=2, max_corrections=100, shift=sigma)
+    lam, U, info = O.solve(oh, 6, tol=1e-10, opts=opts)
+    assert info.converged
+    assert np.all(np.abs(lam - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
+    assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
+    _, _, info0 = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
+    assert info.corrections <= info0.corrections
