@@ -54,7 +54,14 @@ Readings of the paper taken here (they are listed with the rest of the design):
   of A_l - sigma M_l (Galerkin-consistent, since both A and M are Galerkin
   products), with its l1-Jacobi diagonals and an exact coarsest solve; sigma
   must lie below the lowest eigenvalue of (A_n, M_n) so that every level's
-  operator is positive definite.  sigma = 0 is the paper's unshifted solve.
+  operator is positive definite.  sigma = 0 is the paper's unshifted solve;
+* with ``Options.krylov = s`` the correction space is V_n plus a block Krylov
+  space of step 1's inexact inverse iteration T (the remark after Algorithm 3.1
+  names "V_n + Krylov spaces"): V_1 = T U, V_i = T V_{i-1}, all with the Ritz
+  values lambda of the current step, and the pencil is taken on
+  V_n + span(V_1, ..., V_s) after the block is M-orthonormalised (directions
+  whose M-norm falls below 1e-10 of the largest are dropped).  s = 1 is the
+  paper's V_n + span(V).
 """
 from __future__ import annotations
 
@@ -280,6 +287,8 @@ class Options:
     coarse_modes: int = 0
     # sigma of the shifted linear solve in step 1 (0 = the paper's unshifted solve)
     shift: float = 0.0
+    # depth s of the block Krylov correction space V_n + span(T U, ..., T^s U) (1 = the paper's)
+    krylov: int = 1
 
 
 def augmented_pencil(h: OracleHierarchy, k: int, V: np.ndarray):
@@ -305,25 +314,48 @@ def coarse_modes_basis(h: OracleHierarchy, m: int) -> np.ndarray:
     return Z
 
 
-def correction(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
-    """One AMGCorrection(n, k, {lambda_j, u_j}) step; returns (lambda, U)."""
-    qt = U.shape[1]
+def inverse_iteration_step(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
+    """Step 1 of Algorithm 3.1, T U: m AMG iterations for A_k u~ = lambda_j M_k u_j from
+    u_j (or the shifted system when opts.shift != 0)."""
     if opts.shift != 0.0:
         # (A_k - sigma M_k) u~ = (lambda_j - sigma) M_k u_j, on the shifted hierarchy
         hs = shifted(h, opts.shift)
         b = h.M[k] @ U * (lam - opts.shift)[None, :]
-        V = amg(hs, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
-    else:
-        b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
-        V = amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
+        return amg(hs, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
+    b = h.M[k] @ U * lam[None, :]  # lambda_j M_k u_j
+    return amg(h, k, b, U, opts.v_cycles, opts.pre_sweeps, opts.post_sweeps, opts.smoother)
+
+
+def krylov_block(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
+    """[T U, T^2 U, ..., T^s U] M-orthonormalised (s = opts.krylov >= 2): eigenvectors
+    of the block's M-Gram matrix scaled by 1/sqrt(eigenvalue), directions with an
+    eigenvalue below 1e-20 of the largest (M-norm below 1e-10) dropped; done twice,
+    since the consecutive blocks are nearly parallel and one pass leaves an error of
+    the Gram matrix's condition number times the rounding unit."""
+    blocks = [inverse_iteration_step(h, k, lam, U, opts)]
+    for _ in range(opts.krylov - 1):
+        blocks.append(inverse_iteration_step(h, k, lam, blocks[-1], opts))
+    K = np.hstack(blocks)
+    for _ in range(2):
+        g, Q = np.linalg.eigh(K.T @ (h.M[k] @ K))
+        keep = g > 1e-20 * g.max()
+        K = K @ (Q[:, keep] / np.sqrt(g[keep])[None, :])
+    return K
+
+
+def correction(h: OracleHierarchy, k: int, lam: np.ndarray, U: np.ndarray, opts: Options = Options()):
+    """One AMGCorrection(n, k, {lambda_j, u_j}) step; returns (lambda, U)."""
+    qt = U.shape[1]
+    V = inverse_iteration_step(h, k, lam, U, opts) if opts.krylov <= 1 else krylov_block(h, k, lam, U, opts)
     Ahat, Mhat = augmented_pencil(h, k, V)
     dn = h.sizes[-1]
     if 0 < opts.coarse_modes < dn:
         # restrict the coarse block to span(Z_m): the pencil of B = [I_n^k Z_m, V]
         m = opts.coarse_modes
-        T = np.zeros((m + qt, dn + qt))
+        w = V.shape[1]
+        T = np.zeros((m + w, dn + w))
         T[:m, :dn] = coarse_modes_basis(h, m).T
-        T[m:, dn:] = np.eye(qt)
+        T[m:, dn:] = np.eye(w)
         mu, X = smallest_pairs(T @ Ahat @ T.T, T @ Mhat @ T.T, qt)
         X = T.T @ X
     else:

@@ -349,3 +349,38 @@ def test_shifted_solve_matches_dense_definition():
     assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
     _, _, info0 = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
     assert info.corrections <= info0.corrections
+
+
+# ---------------------------------------------------------------- Krylov-augmented correction space
+
+
+def test_krylov_block_is_m_orthonormal_and_ritz_values_fall():
+    """The depth-2 block [T U, T^2 U] comes out M-orthonormal, and since its span holds
+    the paper's span(T U), the depth-2 Ritz values of one correction lie at or below
+    the depth-1 ones (Courant-Fischer) and at or above the exact eigenvalues."""
+    p, oh = _oh("lshape", 16, 60, 2)
+    lam_ex, U_ex = dense_pairs(p, 8)
+    rng = np.random.default_rng(4)
+    U = U_ex + 1e-2 * rng.standard_normal(U_ex.shape)
+    lam = np.array([(u @ (oh.A[0] @ u)) / (u @ (oh.M[0] @ u)) for u in U.T])
+    K = O.krylov_block(oh, 0, lam, U, O.Options(krylov=2))
+    assert K.shape[1] == 16
+    assert np.abs(K.T @ (oh.M[0] @ K) - np.eye(K.shape[1])).max() < 1e-12
+    mu1, _ = O.correction(oh, 0, lam, U, O.Options())
+    mu2, _ = O.correction(oh, 0, lam, U, O.Options(krylov=2))
+    assert np.all(mu2 <= mu1 * (1 + 1e-12))
+    assert np.all(mu2 >= lam_ex * (1 - 1e-12))
+    assert np.sum(mu2 - lam_ex) < 0.5 * np.sum(mu1 - lam_ex)
+
+
+def test_krylov_solve_matches_dense_definition():
+    """Pin 1 with the Krylov-augmented space: the same fixed point, in fewer corrections."""
+    p, oh = _oh("lshape", 16, 60, 2)
+    lam_ex, U_ex = dense_pairs(p, 6)
+    lam, U, info = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100, krylov=2))
+    assert info.converged
+    assert np.all(np.abs(lam - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
+    assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-8
+    assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(6)).max() < 1e-11
+    _, _, info1 = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
+    assert info.corrections < info1.corrections
