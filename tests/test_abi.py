@@ -46,3 +46,20 @@ def test_host_only_calls_without_gpu():
     o = amgeig.amgeig_default_options()
     assert (o.max_corrections, o.v_cycles, o.pre_sweeps, o.post_sweeps) == (20, 1, 1, 1)
     assert amgeig.strerror(amgeig.AMGEIG_ENOCONV).startswith("not converged")
+
+
+def test_argument_errors_need_no_gpu():
+    """Argument checks return their error codes before any CUDA call: a negative
+    mode count and NULL pointers are EINVAL with a message, on any machine."""
+    import ctypes
+
+    from paper_1503_08462_gb300 import amgeig
+
+    with pytest.raises(amgeig.AmgEigError) as e:
+        amgeig.amgeig_load_hierarchy_modes(b"AMGEIGH1" + bytes(16), 0, -1)
+    assert e.value.code == amgeig.AMGEIG_EINVAL and "modes" in str(e.value)
+    L = amgeig.lib()
+    h = ctypes.c_void_p()
+    assert L.amgeig_load_hierarchy(None, 0, 0, ctypes.byref(h)) == amgeig.AMGEIG_EINVAL
+    assert L.amgeig_load_hierarchy_modes(None, 0, 0, 4, ctypes.byref(h)) == amgeig.AMGEIG_EINVAL
+    assert b"NULL" in L.amgeig_last_error()
