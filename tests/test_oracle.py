@@ -384,3 +384,22 @@ def test_krylov_solve_matches_dense_definition():
     assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(6)).max() < 1e-11
     _, _, info1 = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
     assert info.corrections < info1.corrections
+
+
+# ---------------------------------------------------------------- output conventions
+
+
+def test_relres_and_sign_convention():
+    """relres is zero on exact eigenpairs, invariant to scaling a column and grows with a
+    perturbation; sign_normalise makes each column's largest-magnitude entry positive,
+    the lowest index winning a tie (reading of the paper's unsigned eigenvectors)."""
+    p, oh = _oh("square", 16, 20)
+    lam, U = dense_pairs(p, 3)
+    assert np.all(O.relres(oh, lam, U) < 1e-12)
+    np.testing.assert_allclose(O.relres(oh, lam, -3.0 * U), O.relres(oh, lam, U), atol=1e-15)
+    assert np.all(O.relres(oh, lam * (1 + 1e-6), U) > 1e-7)
+    X = np.array([[1.0, -2.0, 0.0], [-2.0, 2.0, 0.0], [0.5, 1.0, 0.0]])
+    Y = O.sign_normalise(X)
+    np.testing.assert_array_equal(Y[:, 0], [-1.0, 2.0, -0.5])  # largest |.| at row 1, was negative
+    np.testing.assert_array_equal(Y[:, 1], [2.0, -2.0, -1.0])  # tie between rows 0 and 1: row 0 decides
+    np.testing.assert_array_equal(Y[:, 2], [0.0, 0.0, 0.0])
