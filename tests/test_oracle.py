@@ -384,6 +384,13 @@ def test_krylov_solve_matches_dense_definition():
     assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(6)).max() < 1e-11
     _, _, info1 = O.solve(oh, 6, tol=1e-10, opts=O.Options(q_extra=2, max_corrections=100))
     assert info.corrections < info1.corrections
+    # with the truncated coarse space of the library option the pencil border is the whole
+    # depth-2 block; the fixed point is the same
+    lam_t, U_t, info_t = O.solve(oh, 6, tol=1e-10,
+                                 opts=O.Options(q_extra=2, max_corrections=100, krylov=2, coarse_modes=16))
+    assert info_t.converged
+    assert np.all(np.abs(lam_t - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
+    assert m_subspace_angle(U_t, U_ex, oh.M[0]) < 1e-8
 
 
 # ---------------------------------------------------------------- output conventions
