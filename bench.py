@@ -36,16 +36,32 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+import hashlib  # noqa: E402
+
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 FMA/clk/SM x 2 flops x max SM clock
-FP64_CLASSES = {"defect", "augment", "gram", "recombine", "chain"}
-# DRAM bytes (read + write) per launch of the roofline kernel class, from one ncu
-# capture of the timed solve (dram__bytes_read.sum + dram__bytes_write.sum summed
-# over the class's launches / launch count); keyed by (workload, precision,
-# v_cycles, q_extra) and valid only for the kernels it was taken on.
-DRAM_TRAFFIC_PER_LAUNCH = {
-    ("lshape_h512_q20", "mixed", 2, 8, "smooth"): 61.56e6,
-}
+# Float-float kernels count the float64-equivalent flops they replace (2 per multiply-add).  Their
+# inner operation, the compensated multiply-add (TwoProduct, TwoSum, the cross terms and the
+# compensation update), issues 13 FP32 instructions, so their ALU peak in those units is the FP32
+# instruction rate x 2 / 13.
+DF_INSTR_PER_FMA = 13
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / DF_INSTR_PER_FMA / 1e12
+ACCURATE_CLASSES = {"defect", "augment", "gram", "recombine", "chain"}
+# DRAM bytes (read + write) per launch of the roofline kernel class, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum summed over the class's launches / launch count),
+# keyed by (workload, precision, v_cycles, q_extra, class) and by the SHA-256 of the source file that
+# holds the class's kernels when the counters were taken: a later change to that file makes the
+# figure stale, and the bench line then reports traffic as null.
+TRAFFIC_SOURCES = {"smooth": "paper_1503_08462_gb300/csrc/spmm.cu", "transfer": "paper_1503_08462_gb300/csrc/spmm.cu"}
+DRAM_TRAFFIC_PER_LAUNCH = {}
+
+
+def source_sha(cls):
+    path = TRAFFIC_SOURCES.get(cls)
+    if path is None:
+        return None
+    with open(os.path.join(ROOT, path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
 
 WORKLOADS = {
     # name: builder, its arguments, q, q_extra, coarse-level cap of the AMG setup,
@@ -334,7 +350,7 @@ def run_stream(args):
         line = {
             "metric": "eigenpairs/s", "value": world * pairs / span, "unit": "eigenpairs/s", "n_gpus": world,
             "steps": args.requests, "warmup": len(pool) + len(burst), "ms_per_step": span * 1e3 / args.requests,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+float-float",
             "data": "synthetic",
             "config": {"workload": "stream", "requests": args.requests, "q": "uniform 1..32", "q_extra": "4 + q // 2",
                        "tol_relres": tol, "pool": [{"domain": d, "N": n} for d, n, _, _ in pool],
@@ -356,6 +372,39 @@ def run_stream(args):
         h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_profile_case(args):
+    """--profile-case vcycle|defect: a short, fixed launch sequence for single-kernel profiler captures.
+
+    Builds the L-shape workload (h = 1/512, N = 784,385, seed 2, 400-row coarse cap), loads it and runs
+    ONE V-cycle from --level on a seeded N_level x --width block through amgeig_apply_vcycle (28 columns
+    by default: the 20 wanted pairs plus 8 buffer vectors of the timed solve), or the defect
+    r_j = lambda_j M u_j - A u_j of that block through amgeig_apply_defect.  The first k_smooth_f4 launch
+    of the process is the level's first pre-smoothing sweep and the first k_spmm_f4 its restriction (one
+    k_defect_df launch for the defect), with only a format conversion before them, so a profiler can take
+    them with -k regex:<kernel> -c 1 and nothing else in flight."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1503_08462_gb300 import amgeig as ae
+    from paper_1503_08462_gb300.inputs import hierarchy, meshes
+
+    p = meshes.lshape_2d(m_half=512, seed=2)
+    blob, _ = hierarchy.problem_blob(p, coarse_cap=400)
+    prec = ae.AMGEIG_FP64 if args.precision == "fp64" else ae.AMGEIG_MIXED_FP32
+    with ae.Hierarchy(blob) as hh:
+        if not 0 <= args.level < len(hh.sizes):
+            raise SystemExit(f"level must be in [0, {len(hh.sizes) - 1}]")
+        n = hh.sizes[args.level]
+        b = np.random.default_rng(0).standard_normal((n, args.width))
+        if args.profile_case == "defect":
+            lam = np.linspace(10.0, 400.0, args.width)
+            r, _ = ae.amgeig_apply_defect(hh.handle, args.level, b, lam, ae.options(precision=prec))
+            log(f"defect level {args.level}: {n} rows x {args.width} columns, |r| = {float(np.linalg.norm(r)):.6e}")
+            return
+        x = ae.amgeig_apply_vcycle(hh.handle, args.level, b, ae.options(precision=prec))
+        log(f"vcycle level {args.level}: {n} rows x {args.width} columns, |x| = {float(np.linalg.norm(x)):.6e}")
 
 
 def main():
@@ -384,7 +433,15 @@ def main():
     ap.add_argument("--smoother", choices=["l1-jacobi", "gauss-seidel"], default="l1-jacobi",
                     help="V-cycle smoother: point l1-Jacobi, or the paper's Gauss-Seidel in multicolour order")
     ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-case", choices=["vcycle", "defect"], default=None,
+                    help="run one V-cycle (or one defect) from --level on the L-shape workload for a "
+                         "single-kernel profiler capture, and nothing else")
+    ap.add_argument("--level", type=int, default=0, help="--profile-case: the level")
+    ap.add_argument("--width", type=int, default=28, help="--profile-case: block columns")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
 
     if args.oracle_child:
         oracle_child(args)
@@ -525,23 +582,27 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     cands = {k: v for k, v in prof.items() if k not in ("pencil", "other")}
     name, d = max(cands.items(), key=lambda kv: kv[1]["total_ms"])
-    fp64_kernel = name in FP64_CLASSES or prec == ae.AMGEIG_FP64
-    alu_peak = FP64_PEAK_TFLOPS if fp64_kernel else FP32_PEAK_TFLOPS
+    if prec == ae.AMGEIG_FP64:
+        alu_peak, alu_src = FP64_PEAK_TFLOPS, "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz (derived)"
+    elif name in ACCURATE_CLASSES:
+        alu_peak = DF_PEAK_TFLOPS
+        alu_src = (f"float-float multiply-add: 152 SMs x 128 FP32 instr/clk x 2070 MHz / {DF_INSTR_PER_FMA} "
+                   f"instr x 2 float64-equivalent flops (derived)")
+    else:
+        alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 FMA/clk x 2 flops x 2070 MHz (derived)"
     t_s = d["total_ms"] / 1e3
     gbs = d["bytes"] / t_s / 1e9
     tfl = d["flops"] / t_s / 1e12
     per_launch_ms = d["total_ms"] / d["launches"]
     if d["flops"] / (alu_peak * 1e12) > d["bytes"] / (hbm_peak * 1e9):
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
-                "traffic": None, "kernel": name,
-                "peak_source": ("FP64" if fp64_kernel else "FP32") + " FMA: 152 SMs x "
-                               + ("2" if fp64_kernel else "128") + " FMA/clk x 2 x 2070 MHz (derived)",
-                "ms_per_launch": per_launch_ms}
+                "traffic": None, "kernel": name, "peak_source": alu_src, "ms_per_launch": per_launch_ms}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": None, "kernel": name, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "ms_per_launch": per_launch_ms}
-    roof["traffic"] = DRAM_TRAFFIC_PER_LAUNCH.get((args.workload, args.precision, args.v_cycles, qe, name))
+    cap_rec = DRAM_TRAFFIC_PER_LAUNCH.get((args.workload, args.precision, args.v_cycles, qe, name))
+    roof["traffic"] = cap_rec[0] if cap_rec and cap_rec[1] == source_sha(name) else None
     roof["algorithmic_bytes_per_launch"] = d["bytes"] / max(d["launches"], 1)
     roof["timed_in"] = (f"second {args.steps}-step region with per-launch CUDA events "
                         f"({ms_profiled:.3f} ms per step there)")
@@ -565,7 +626,8 @@ def main():
             "metric": "eigenpairs/s", "value": value, "unit": "eigenpairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {ae.AMGEIG_MIXED_FP32: "f64+f32", ae.AMGEIG_MIXED_BF16: "f64+f32+bf16"}.get(prec, "f64"),
+            "dtype": {ae.AMGEIG_MIXED_FP32: "f32+float-float",
+                      ae.AMGEIG_MIXED_BF16: "bf16-storage f32+float-float"}.get(prec, "f64"),
             "data": "synthetic",
             "config": {"workload": args.workload, "N": N0, "q": q, "q_extra": qe, "levels": h.sizes,
                        "precision": args.precision, "tol_relres": tol, "corrections": corrections,

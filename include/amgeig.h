@@ -168,6 +168,22 @@ int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* o
  * released id. */
 int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs, amgeig_info* info);
 
+/* Serving: cap the device memory the request service keeps in iterate
+ * workspaces (the workspaces of hierarchies it has served stay resident between
+ * requests).  bytes = 0 (the default): no cap beyond free device memory.  Under
+ * a cap, a request whose workspace does not fit first releases the workspaces
+ * of idle hierarchies, least recently used first; if it still does not fit it
+ * waits for running requests to end, and a request whose workspace alone
+ * exceeds the cap (or that cannot fit with nothing else running) ends with
+ * ENOMEM, reported by amgeig_poll.  Takes effect for the next admission
+ * decision.  Returns AMGEIG_OK. */
+int amgeig_service_set_memory_limit(uint64_t bytes);
+
+/* Serving: the bytes the service's resident workspaces hold now, and how many
+ * workspaces it has released to admit other requests so far (either pointer
+ * may be NULL, not both).  Errors: EINVAL. */
+int amgeig_service_memory(uint64_t* resident_bytes, uint64_t* evictions);
+
 /* ---- building blocks, exposed for verification -------------------------- */
 
 /* The nwant smallest eigenpairs of the symmetric n x n matrix H (host, row-major,
@@ -191,7 +207,7 @@ int amgeig_sym_eigh(int device, int n, int nwant, const double* H, double* evals
 int amgeig_apply_defect(amgeig_hierarchy h, int level, int width, const amgeig_options* opt, const double* U,
                         const double* lam, double* R, double* relres);
 
-/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h (Algorithm
+/* One AMG V-cycle for A_l x = b from x = 0 on level `level` of h (Algorithm
  * 3.1 step 1 with the options' pre/post l1-Jacobi sweeps and precision): b and
  * x are host buffers of N_l x width doubles (row-major), 1 <= width <= 128.
  * Errors: EINVAL, ENOMEM, ECUDA. */

@@ -58,7 +58,8 @@ _lib = None
 EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_load_hierarchy_modes", "amgeig_free_hierarchy", "amgeig_hierarchy_info",
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
             "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_apply_defect", "amgeig_profile_enable",
-            "amgeig_profile_read", "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc"]
+            "amgeig_profile_read", "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc",
+            "amgeig_service_set_memory_limit", "amgeig_service_memory"]
 
 
 def library_path() -> str:
@@ -95,11 +96,14 @@ def lib():
         L.amgeig_profile_read.argtypes = [ctypes.POINTER(amgeig_prof_entry), i32, ctypes.POINTER(i32)]
         L.amgeig_sym_eigh_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
         L.amgeig_sym_eigh_noalloc.restype = i32
+        L.amgeig_service_set_memory_limit.argtypes = [ctypes.c_uint64]
+        L.amgeig_service_memory.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
         L.amgeig_kernel_launches.argtypes = []
         L.amgeig_kernel_launches.restype = ctypes.c_uint64
         for name in ("amgeig_load_hierarchy", "amgeig_load_hierarchy_modes", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
                      "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle",
-                     "amgeig_apply_defect", "amgeig_profile_enable", "amgeig_profile_read"):
+                     "amgeig_apply_defect", "amgeig_profile_enable", "amgeig_profile_read",
+                     "amgeig_service_set_memory_limit", "amgeig_service_memory"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -186,6 +190,18 @@ def amgeig_poll(request_id: int, eigvals=None, eigvecs=None, info: Optional[amge
     return True, code
 
 
+def amgeig_service_set_memory_limit(nbytes: int) -> None:
+    _check(lib().amgeig_service_set_memory_limit(nbytes), "amgeig_service_set_memory_limit")
+
+
+def amgeig_service_memory() -> Tuple[int, int]:
+    """(bytes held by the service's resident workspaces, workspaces released so far to admit others)."""
+    rb = ctypes.c_uint64()
+    ev = ctypes.c_uint64()
+    _check(lib().amgeig_service_memory(ctypes.byref(rb), ctypes.byref(ev)), "amgeig_service_memory")
+    return int(rb.value), int(ev.value)
+
+
 def amgeig_sym_eigh(H: np.ndarray, nwant: int, device: int = 0):
     H = np.ascontiguousarray(H, dtype=np.float64)
     n = H.shape[0]
@@ -196,9 +212,25 @@ def amgeig_sym_eigh(H: np.ndarray, nwant: int, device: int = 0):
 
 
 def amgeig_sym_eigh_noalloc(H, evals, evecs, stream: Optional[int] = None) -> None:
-    """Device-pointer form without allocation: H (n x n), evals (nwant), evecs (n x nwant) CUDA float64 tensors."""
+    """Device-pointer form without allocation: H (n x n), evals (nwant), evecs (n x nwant) CUDA float64 tensors
+    on the current CUDA device.  Shapes and devices are checked here, before any pointer reaches the library:
+    a mis-shaped output would be written out of bounds on the device."""
+    import torch
+
+    tensors = (H, evals, evecs)
+    if not all(isinstance(t, torch.Tensor) for t in tensors):
+        raise AmgEigError(AMGEIG_EINVAL, "amgeig_sym_eigh_noalloc", "H, evals and evecs must be torch tensors")
+    if H.dim() != 2 or H.shape[0] != H.shape[1] or evals.dim() != 1 or evecs.dim() != 2:
+        raise AmgEigError(AMGEIG_EINVAL, "amgeig_sym_eigh_noalloc", "H must be n x n, evals 1-D, evecs 2-D")
     n = H.shape[0]
     nwant = evals.shape[0]
+    if tuple(evecs.shape) != (n, nwant):
+        raise AmgEigError(AMGEIG_EINVAL, "amgeig_sym_eigh_noalloc",
+                          f"evecs has shape {tuple(evecs.shape)}, expected ({n}, {nwant})")
+    cur = torch.cuda.current_device()
+    if not all(t.is_cuda and t.device.index == cur for t in tensors):
+        raise AmgEigError(AMGEIG_EINVAL, "amgeig_sym_eigh_noalloc",
+                          f"H, evals and evecs must be CUDA tensors on the current device cuda:{cur}")
     _check(lib().amgeig_sym_eigh_noalloc(n, nwant, _ptr(H), _ptr(evals), _ptr(evecs), stream),
            "amgeig_sym_eigh_noalloc")
 

@@ -325,6 +325,7 @@ HostCsr transpose(const CsrView& P) {
 struct DeviceBuffers {
   static constexpr size_t kOwn = size_t(2) << 20, kAlign = 256;
   std::vector<void*> ptrs;  // every cudaMalloc of this owner
+  size_t held = 0;          // bytes of those allocations
   char* blk = nullptr;      // free tail of the current block of small arrays
   size_t blk_left = 0;
   cudaStream_t st = nullptr;  // uploads are ordered on this stream (the hierarchy's)
@@ -340,6 +341,7 @@ struct DeviceBuffers {
       cudaError_t e = cudaMalloc(&p, bytes);
       if (e != cudaSuccess) return e;
       ptrs.push_back(p);
+      held += bytes;
       *out = static_cast<T*>(p);
       return cudaSuccess;
     }
@@ -348,6 +350,7 @@ struct DeviceBuffers {
       cudaError_t e = cudaMalloc(&p, block);
       if (e != cudaSuccess) return e;
       ptrs.push_back(p);
+      held += block;
       blk = static_cast<char*>(p);
       blk_left = block;
     }
@@ -1080,6 +1083,11 @@ struct Service {
   std::deque<std::shared_ptr<Request>> queue;
   std::map<uint64_t, std::shared_ptr<Request>> table;
   std::vector<amgeig_hierarchy_t*> busy;
+  // hierarchies whose workspace the service has used, least recently used first;
+  // under a memory limit, idle ones give their workspace back to admit others
+  std::vector<amgeig_hierarchy_t*> resident;
+  size_t mem_limit = 0;  // bytes of resident workspaces the service may hold (0: no limit)
+  uint64_t evictions = 0;
   uint64_t next_id = 1;
   int running_solves = 0;
   bool started = false;
@@ -1092,19 +1100,48 @@ struct Service {
 
   bool is_busy(amgeig_hierarchy_t* h) const { return std::find(busy.begin(), busy.end(), h) != busy.end(); }
 
-  // first admissible request (caller holds mu)
+  // first admissible request (caller holds mu).  A request that cannot fit
+  // under the memory limit even with every idle workspace released, while
+  // nothing else runs, is refused here with ENOMEM.
   std::shared_ptr<Request> pick() {
-    for (auto it = queue.begin(); it != queue.end(); ++it) {
+    for (auto it = queue.begin(); it != queue.end();) {
       const std::shared_ptr<Request> r = *it;
-      if (is_busy(r->h)) continue;
-      if (running_solves > 0 && !fits(r.get())) continue;
+      if (is_busy(r->h)) {
+        ++it;
+        continue;
+      }
+      const int f = fits(r.get());
+      if (f == kRefuse && running_solves == 0) {
+        it = queue.erase(it);
+        r->status = AMGEIG_ENOMEM;
+        r->info.status = AMGEIG_ENOMEM;
+        r->done = true;
+        r->h->pending--;
+        continue;
+      }
+      if (running_solves > 0 && f != kFits) {
+        ++it;
+        continue;
+      }
       queue.erase(it);
+      touch(r->h);
       return r;
     }
     return nullptr;
   }
 
-  static bool fits(const Request* r);
+  static constexpr int kFits = 0, kWait = 1, kRefuse = 2;
+  int fits(const Request* r);
+  size_t resident_bytes() const;
+  void touch(amgeig_hierarchy_t* h) {
+    auto it = std::find(resident.begin(), resident.end(), h);
+    if (it != resident.end()) resident.erase(it);
+    resident.push_back(h);
+  }
+  void forget(amgeig_hierarchy_t* h) {
+    auto it = std::find(resident.begin(), resident.end(), h);
+    if (it != resident.end()) resident.erase(it);
+  }
 
   void loop() {
     for (;;) {
@@ -1170,6 +1207,18 @@ const char* amgeig_strerror(int code) {
 
 const char* amgeig_last_error(void) { return g_last_error.c_str(); }
 
+}  // extern "C"
+
+int amgeig::set_last_error(int code, const char* msg) {
+  if (code == AMGEIG_OK)
+    g_last_error.clear();
+  else
+    g_last_error = msg ? msg : "";
+  return code;
+}
+
+extern "C" {
+
 namespace {
 
 // The load behind both entry points.  modes < 0: the coarse eigenbasis waits for the
@@ -1179,9 +1228,8 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   g_last_error.clear();
   if (!blob || !out) return fail(AMGEIG_EINVAL, "NULL argument");
   *out = nullptr;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
-    return fail(AMGEIG_EINVAL, "no such CUDA device");
+  // the blob's layout first (host only: a malformed blob is reported as such
+  // whatever the device argument)
   std::vector<CsrView> levels, prolong;
   std::vector<uint64_t> aligned;
   const uint8_t* base = nullptr;
@@ -1191,6 +1239,9 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   // rest of the blob is validated
   if (levels.back().rows > 4096) return fail(AMGEIG_EINVAL, "coarsest level larger than 4096");
   if (!csr_valid(levels.back())) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(AMGEIG_EINVAL, "no such CUDA device");
   CK(cudaSetDevice(device));
   auto h = std::make_unique<amgeig_hierarchy_t>();
   h->device = device;
@@ -1423,6 +1474,11 @@ int amgeig_load_hierarchy_modes(const void* blob, size_t bytes, int device, int 
 int amgeig_free_hierarchy(amgeig_hierarchy h) {
   if (!h) return AMGEIG_OK;
   if (h->pending.load() != 0) return fail(AMGEIG_EINVAL, "hierarchy has pending requests");
+  {
+    Service& s = service();
+    std::lock_guard<std::mutex> lk(s.mu);
+    s.forget(h);
+  }
   cudaSetDevice(h->device);
   delete h;
   return AMGEIG_OK;
@@ -1607,6 +1663,25 @@ int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* o
   return AMGEIG_OK;
 }
 
+int amgeig_service_set_memory_limit(uint64_t bytes) {
+  Service& s = service();
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    s.mem_limit = static_cast<size_t>(bytes);
+  }
+  s.cv.notify_all();
+  return AMGEIG_OK;
+}
+
+int amgeig_service_memory(uint64_t* resident_bytes, uint64_t* evictions) {
+  if (!resident_bytes && !evictions) return fail(AMGEIG_EINVAL, "NULL arguments");
+  Service& s = service();
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (resident_bytes) *resident_bytes = s.resident_bytes();
+  if (evictions) *evictions = s.evictions;
+  return AMGEIG_OK;
+}
+
 int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs, amgeig_info* info) {
   if (!done) return fail(AMGEIG_EINVAL, "NULL argument");
   Service& s = service();
@@ -1640,20 +1715,53 @@ size_t workspace_bytes(const amgeig_hierarchy_t* h, int qt) {
   return per + static_cast<size_t>(h->sizes[0]) * qt * 8 * 5;
 }
 
-bool Service::fits(const Request* r) {
+size_t ws_held(const amgeig_hierarchy_t* h) { return h->ws ? h->ws->mem.held : 0; }
+
+// Bytes held by the workspaces of the hierarchies the service has used (caller holds mu).
+size_t Service::resident_bytes() const {
+  size_t b = 0;
+  for (const amgeig_hierarchy_t* x : resident) b += ws_held(x);
+  return b;
+}
+
+// Admission (caller holds mu): kFits when the request's workspace is resident or
+// can be made (under the memory limit, after releasing idle workspaces of other
+// hierarchies, least recently used first, and within free device memory); kWait
+// when it may fit once running requests end; kRefuse when it cannot fit under
+// the limit at all.
+int Service::fits(const Request* r) {
   amgeig_hierarchy_t* h = r->h;
   const int qt = r->q + r->opt.q_extra;
+  size_t own = 0;
   {
     // a direct solve on this hierarchy from another thread: not now
     std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
-    if (!lk.owns_lock()) return false;
+    if (!lk.owns_lock()) return kWait;
     const int wp = r->opt.precision == AMGEIG_FP64 ? AMGEIG_FP64 : AMGEIG_MIXED_FP32;
-    if (h->ws && h->ws->qcap >= qt && h->ws->precision == wp) return true;
+    if (h->ws && h->ws->qcap >= qt && h->ws->precision == wp) return kFits;
+    own = ws_held(h);
+  }
+  const size_t need = workspace_bytes(h, qt);
+  if (mem_limit > 0) {
+    if (need > mem_limit) return kRefuse;
+    // the request's own (too small) workspace is replaced, so it does not count
+    size_t held = resident_bytes() - std::min(resident_bytes(), own);
+    for (size_t i = 0; i < resident.size() && held + need > mem_limit; ++i) {
+      amgeig_hierarchy_t* x = resident[i];
+      if (x == h || is_busy(x)) continue;
+      std::unique_lock<std::mutex> lk(x->mu, std::try_to_lock);
+      if (!lk.owns_lock() || !x->ws) continue;
+      held -= std::min(held, ws_held(x));
+      cudaSetDevice(x->device);
+      x->ws.reset();  // its last solve synchronised its stream: nothing in flight
+      ++evictions;
+    }
+    if (held + need > mem_limit) return kWait;
   }
   size_t fr = 0, tot = 0;
   cudaSetDevice(h->device);
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return true;
-  return workspace_bytes(h, qt) <= fr;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return kFits;
+  return need <= fr ? kFits : kWait;
 }
 
 void Service::run(const std::shared_ptr<Request>& r) {

@@ -23,6 +23,7 @@
 #include "amgeig.h"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace amgeig {
 namespace {
@@ -37,19 +38,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-thread_local std::string g_err;
-
 // Device address of the scratch array on the current device (looked up once per device).
 int scratch_address(int device, void** out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (device < 0 || device >= kMaxDevices) return AMGEIG_EINVAL;
+  if (device < 0 || device >= kMaxDevices) return set_last_error(AMGEIG_EINVAL, "device ordinal beyond 63");
   if (!g_scratch_ptr[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) {
-      g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return AMGEIG_ECUDA;
-    }
+    if (e != cudaSuccess)
+      return set_last_error(AMGEIG_ECUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
     g_scratch_ptr[device] = p;
   }
   *out = g_scratch_ptr[device];
@@ -69,10 +66,15 @@ using namespace amgeig;
 
 extern "C" int amgeig_sym_eigh_noalloc(int n, int nwant, const double* H, double* evals, double* evecs,
                                        void* stream) {
-  if (!H || !evals || !evecs || n < 1 || nwant < 1 || nwant > n) return AMGEIG_EINVAL;
-  if (n > kNoAllocMaxN || nwant > kNoAllocMaxWant) return AMGEIG_EINVAL;
+  set_last_error(AMGEIG_OK, nullptr);
+  if (!H || !evals || !evecs) return set_last_error(AMGEIG_EINVAL, "NULL pointer");
+  if (n < 1 || nwant < 1 || nwant > n) return set_last_error(AMGEIG_EINVAL, "need 1 <= nwant <= n");
+  if (n > kNoAllocMaxN || nwant > kNoAllocMaxWant)
+    return set_last_error(AMGEIG_EINVAL, "n > 128 or nwant > 64: beyond the fixed scratch array");
   int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) return AMGEIG_ECUDA;
+  cudaError_t ge = cudaGetDevice(&device);
+  if (ge != cudaSuccess)
+    return set_last_error(AMGEIG_ECUDA, (std::string("cudaGetDevice: ") + cudaGetErrorString(ge)).c_str());
   void* base = nullptr;
   int rc = scratch_address(device, &base);
   if (rc) return rc;
@@ -88,12 +90,14 @@ extern "C" int amgeig_sym_eigh_noalloc(int n, int nwant, const double* H, double
   const size_t rrn = nw * nw > 4 * nw ? nw * nw : 4 * nw;
   const size_t oR = carve(&off, sizeof(df) * 4 * rrn);
   const size_t oP = carve(&off, sizeof(int) * nw);
-  if (off > kNoAllocScratchBytes) return AMGEIG_EINVAL;
+  if (off > kNoAllocScratchBytes) return set_last_error(AMGEIG_EINVAL, "scratch layout exceeds 512 KiB");
   unsigned char* b = static_cast<unsigned char*>(base);
   launch_syev_df_into(n, nwant, H, evals, evecs, reinterpret_cast<df*>(b + oW), reinterpret_cast<df*>(b + oTau),
                       reinterpret_cast<df*>(b + oD), reinterpret_cast<df*>(b + oE), reinterpret_cast<df*>(b + oF),
                       reinterpret_cast<df*>(b + oZ), reinterpret_cast<df*>(b + oR), reinterpret_cast<int*>(b + oP),
                       static_cast<cudaStream_t>(stream));
-  if (cudaGetLastError() != cudaSuccess) return AMGEIG_ECUDA;
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess)
+    return set_last_error(AMGEIG_ECUDA, (std::string("eigensolver launch: ") + cudaGetErrorString(le)).c_str());
   return AMGEIG_OK;
 }

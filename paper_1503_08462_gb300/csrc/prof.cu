@@ -3,6 +3,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "amgeig.h"
@@ -48,10 +49,14 @@ const char* kNames[P_COUNT] = {"defect", "smooth", "transfer", "coarse_solve", "
 
 void ensure_dynamic_smem(const void* func, size_t bytes) {
   if (bytes <= 48 * 1024) return;
+  // the attribute belongs to the current device's copy of the function: one
+  // record per (device, function)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
   static std::mutex mu;
-  static std::map<const void*, size_t> limit;
+  static std::map<std::pair<int, const void*>, size_t> limit;
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = limit[func];
+  size_t& cur = limit[std::make_pair(dev, func)];
   if (bytes <= cur) return;
   if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) ==
       cudaSuccess)

@@ -29,8 +29,13 @@ enum ProfClass {
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
 // lowering it: the limit is one per function for the whole process, so solves
 // running on several host threads must not shrink it under each other's
-// launches.  Sizes up to 48 KB need no attribute.
+// launches.  Sizes up to 48 KB need no attribute.  The attribute is set on
+// the current device, and recorded per (device, function).
 void ensure_dynamic_smem(const void* func, size_t bytes);
+
+// Record `msg` as the calling thread's last failure (amgeig_last_error) and
+// return `code`; code == AMGEIG_OK clears the record.
+int set_last_error(int code, const char* msg);
 
 class ProfScope {
  public:

@@ -63,3 +63,30 @@ def test_argument_errors_need_no_gpu():
     assert L.amgeig_load_hierarchy(None, 0, 0, ctypes.byref(h)) == amgeig.AMGEIG_EINVAL
     assert L.amgeig_load_hierarchy_modes(None, 0, 0, 4, ctypes.byref(h)) == amgeig.AMGEIG_EINVAL
     assert b"NULL" in L.amgeig_last_error()
+
+
+def test_malformed_blobs_are_refused_by_the_loader_without_a_gpu():
+    """The loader checks the blob's layout on the host before it touches a device: a truncated blob, a
+    wrong magic, a bad version and trailing bytes are ECORRUPT on any machine (the checksum and every
+    level's CSR are checked by the GPU loader, in the GPU tests)."""
+    import ctypes
+
+    from paper_1503_08462_gb300 import amgeig
+    from paper_1503_08462_gb300.inputs import hierarchy, meshes
+
+    blob, _ = hierarchy.problem_blob(meshes.square_2d(8, seed=1), coarse_cap=10)
+    L = amgeig.lib()
+    h = ctypes.c_void_p()
+
+    def load(b):
+        buf = ctypes.create_string_buffer(b, len(b))
+        return L.amgeig_load_hierarchy(buf, len(b), 0, ctypes.byref(h))
+
+    cut = len(blob) // 2 // 8 * 8
+    assert load(blob[:cut]) == amgeig.AMGEIG_ECORRUPT
+    assert b"truncated" in L.amgeig_last_error()
+    assert load(b"AMGEIGH0" + blob[8:]) == amgeig.AMGEIG_ECORRUPT
+    bad_version = blob[:8] + (7).to_bytes(4, "little") + blob[12:]
+    assert load(bad_version) == amgeig.AMGEIG_ECORRUPT
+    assert load(blob[:-8] + bytes(8) + blob[-8:]) == amgeig.AMGEIG_ECORRUPT
+    assert load(blob[:-3]) == amgeig.AMGEIG_ECORRUPT  # not a whole number of words
