@@ -76,6 +76,17 @@ typedef struct {
                             rows coloured first-fit in row order, colours ascending before the
                             coarse correction and descending after it (a symmetric V-cycle);
                             the colouring is computed on the first such solve */
+  int n1;                /* initial level of Algorithm 3.2 step 1, 0-based (level 0 the finest):
+                            -1 (default) = the coarsest level with at least q + q_extra rows (the
+                            paper's n1 = n whenever the coarsest level is large enough, Sec. 4.1);
+                            otherwise a level with q + q_extra <= N_n1 <= 2048.  The initial
+                            eigenproblem (A_n1, M_n1) is solved densely on the GPU; the pencils
+                            of every correction still use the coarsest space V_n */
+  int refine;            /* mixed precisions only: 1 (default) = after the last correction, each
+                            vector's Rayleigh quotient u^T A u / u^T M u and relative residual are
+                            recomputed in float64 with the exact operator values; those are the
+                            returned eigenvalues (ascending, vectors permuted alike) and residuals.
+                            0 = return the float-float Ritz values and residuals */
 } amgeig_options;
 
 #define AMGEIG_SMOOTHER_L1_JACOBI 0
@@ -131,8 +142,11 @@ int amgeig_free_hierarchy(amgeig_hierarchy h);
 int amgeig_hierarchy_info(amgeig_hierarchy h, int* n_levels, int64_t* sizes, int max_sizes);
 
 /* Algorithm 3.2 with Algorithm 3.1 on the GPU.
- *   q         number of wanted eigenpairs, 1 <= q, q + q_extra <= N_{n-1} (the
- *             coarsest dimension must hold the initial eigenproblem, n1 = n).
+ *   q         number of wanted eigenpairs, 1 <= q, q + q_extra <= min(128, N_0).
+ *             The initial eigenproblem (Algorithm 3.2 step 1) is solved on level
+ *             n1 (options.n1; by default the coarsest level with at least
+ *             q + q_extra rows), which must hold at most 2048 rows when it is
+ *             not the coarsest; EINVAL otherwise.
  *   tol       stopping test max_j relres_j <= tol on the finest level (the paper
  *             stops on the total error against reference eigenvalues, Sec. 4.1,
  *             which a solver cannot know).

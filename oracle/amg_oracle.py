@@ -289,6 +289,9 @@ class Options:
     shift: float = 0.0
     # depth s of the block Krylov correction space V_n + span(T U, ..., T^s U) (1 = the paper's)
     krylov: int = 1
+    # initial level of Algorithm 3.2 step 1 (0-based); -1: the coarsest level with at least
+    # q + q_extra rows (n1 = n whenever the coarsest level is large enough, Sec. 4.1)
+    n1: int = -1
 
 
 def augmented_pencil(h: OracleHierarchy, k: int, V: np.ndarray):
@@ -376,7 +379,8 @@ def relres(h: OracleHierarchy, lam: np.ndarray, U: np.ndarray, k: int = 0) -> np
 
 
 def initial_level(h: OracleHierarchy, qt: int) -> int:
-    """n1: the coarsest level with at least qt dofs."""
+    """n1: the coarsest level with at least qt dofs (Algorithm 3.2 step 1 allows any
+    n1 <= n; the paper takes n1 = n, Sec. 4.1, which needs d_n >= qt)."""
     for l in range(h.n_levels - 1, -1, -1):
         if h.sizes[l] >= qt:
             return l
@@ -402,7 +406,9 @@ class Info:
 def solve(h: OracleHierarchy, q: int, tol: float = 1e-10, opts: Options = Options()):
     """Algorithm 3.2.  Returns (lambda[q] ascending, U[N_0, q], Info)."""
     qt = q + opts.q_extra
-    n1 = initial_level(h, qt)
+    n1 = initial_level(h, qt) if opts.n1 < 0 else opts.n1
+    if not 0 <= n1 < h.n_levels or h.sizes[n1] < qt:
+        raise ValueError("n1 must be a level with at least q + q_extra rows")
     An1 = h.A[n1].toarray()
     Mn1 = h.M[n1].toarray()
     lam, U = smallest_pairs(An1, Mn1, qt)

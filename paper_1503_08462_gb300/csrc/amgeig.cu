@@ -326,6 +326,8 @@ struct DeviceBuffers {
   static constexpr size_t kOwn = size_t(2) << 20, kAlign = 256;
   std::vector<void*> ptrs;  // every cudaMalloc of this owner
   size_t held = 0;          // bytes of those allocations
+  size_t mallocs = 0;       // allocation calls made (or, when dry, that would be made)
+  bool dry = false;         // count the bytes a sequence of allocs would take, allocate nothing
   char* blk = nullptr;      // free tail of the current block of small arrays
   size_t blk_left = 0;
   cudaStream_t st = nullptr;  // uploads are ordered on this stream (the hierarchy's)
@@ -338,24 +340,32 @@ struct DeviceBuffers {
     void* p = nullptr;
     *out = nullptr;
     if (bytes >= kOwn) {
-      cudaError_t e = cudaMalloc(&p, bytes);
-      if (e != cudaSuccess) return e;
-      ptrs.push_back(p);
+      if (!dry) {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(p);
+      }
+      ++mallocs;
       held += bytes;
       *out = static_cast<T*>(p);
       return cudaSuccess;
     }
     if (bytes > blk_left) {
-      const size_t block = ptrs.empty() ? kOwn : size_t(8) << 20;  // > bytes
-      cudaError_t e = cudaMalloc(&p, block);
-      if (e != cudaSuccess) return e;
-      ptrs.push_back(p);
+      const size_t block = mallocs == 0 ? kOwn : size_t(8) << 20;  // > bytes
+      if (!dry) {
+        cudaError_t e = cudaMalloc(&p, block);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(p);
+        blk = static_cast<char*>(p);
+      }
+      ++mallocs;
       held += block;
-      blk = static_cast<char*>(p);
       blk_left = block;
     }
-    *out = reinterpret_cast<T*>(blk);
-    blk += bytes;
+    if (!dry) {
+      *out = reinterpret_cast<T*>(blk);
+      blk += bytes;
+    }
     blk_left -= bytes;
     return cudaSuccess;
   }
@@ -407,6 +417,14 @@ struct amgeig_hierarchy_t {
   std::vector<std::vector<int>> gs_off;
   std::vector<double*> gs_dinv64;
   std::vector<float*> gs_dinv32;
+  // Algorithm 3.2 step 1 on a level n1 above the coarsest (when q + q_extra
+  // exceeds d_n, or the caller asks for it): the dense pencil (A_n1, M_n1), its
+  // M_n1 factor's workspace and its `count` lowest eigenpairs, kept for later solves
+  struct Initial {
+    int level = -1, count = 0, d = 0;
+    double *A = nullptr, *M = nullptr, *Z = nullptr, *theta = nullptr;
+    PencilWork* pw = nullptr;
+  } init;
   cudaStream_t stream = nullptr;
   std::atomic<int> pending{0};
   ~amgeig_hierarchy_t();
@@ -430,13 +448,20 @@ struct SolveWork {
   double *partials = nullptr, *sums = nullptr, *relres = nullptr, *lam = nullptr, *mu = nullptr;
   double *C = nullptr, *G = nullptr, *gsc = nullptr, *Xc = nullptr, *Yv = nullptr, *sign = nullptr;
   int* flags = nullptr;
+  int* perm = nullptr;     // output column c is column perm[c] of the iterate (after the refinement)
+  bool permuted = false;   // perm applies to the current solve's outputs
   int* nfallback = nullptr;  // corrections that needed the dense eigensolver
   PencilWork* pw = nullptr;
+  size_t pw_bytes = 0;  // device bytes of pw
   ~SolveWork() { pencil_work_destroy(pw); }
 };
 
-int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, std::unique_ptr<SolveWork>& out) {
+// dry: allocate nothing, only add up in w->mem.held (and pw_bytes) what the
+// workspace would hold
+int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, std::unique_ptr<SolveWork>& out,
+                   bool dry = false) {
   auto w = std::make_unique<SolveWork>();
+  w->mem.dry = dry;
   w->qcap = qt;
   w->qt = qt;
   w->ld32 = (qt + 3) & ~3;
@@ -502,10 +527,14 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->Yv, static_cast<size_t>(qt) * qt));
   CK(m.alloc(&w->sign, qt));
   CK(m.alloc(&w->flags, 4));
+  CK(m.alloc(&w->perm, qt));
   CK(m.alloc(&w->nfallback, 1));
-  cudaError_t e;
-  w->pw = pencil_work_create(h->dn, qt, &e);
-  if (!w->pw) return fail(AMGEIG_ENOMEM, std::string("pencil workspace: ") + cudaGetErrorString(e));
+  w->pw_bytes = pencil_work_bytes(h->dn, qt);
+  if (!dry) {
+    cudaError_t e;
+    w->pw = pencil_work_create(h->dn, qt, &e);
+    if (!w->pw) return fail(AMGEIG_ENOMEM, std::string("pencil workspace: ") + cudaGetErrorString(e));
+  }
   out = std::move(w);
   return AMGEIG_OK;
 }
@@ -791,6 +820,7 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
 amgeig_hierarchy_t::~amgeig_hierarchy_t() {
   ws.reset();
   pencil_work_destroy(cpw);
+  pencil_work_destroy(init.pw);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -889,7 +919,8 @@ int check_options(const amgeig_options& o) {
   if (o.max_corrections < 0 || o.v_cycles < 1 || o.pre_sweeps < 0 || o.post_sweeps < 0 || o.q_extra < 0 ||
       o.fixed_corrections < 0 || o.coarse_modes < 0 ||
       (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
-      (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL))
+      (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL) || o.n1 < -1 ||
+      (o.refine != 0 && o.refine != 1))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -905,18 +936,93 @@ int ensure_modes(amgeig_hierarchy_t* h, int need, cudaStream_t st) {
   return AMGEIG_OK;
 }
 
+// The `count` lowest eigenpairs of (A_l, M_l) on level l (above the coarsest),
+// Algorithm 3.2 step 1 with n1 = l: the level's dense pencil, the Cholesky
+// factor of M_l and the float-float eigensolver of the coarse modes.  Kept for
+// later solves; under the hierarchy's lock.
+int ensure_initial(amgeig_hierarchy_t* h, int l, int count, cudaStream_t st) {
+  auto& I = h->init;
+  if (I.level == l && I.count >= count) return AMGEIG_OK;
+  const int d = static_cast<int>(h->sizes[l]);
+  if (I.level != l) {
+    // arrays of an earlier level stay in the hierarchy's allocations until it is freed
+    const size_t dd = static_cast<size_t>(d) * d;
+    CK(h->mem.alloc(&I.A, dd));
+    CK(h->mem.alloc(&I.M, dd));
+    CK(h->mem.alloc(&I.Z, dd));
+    CK(h->mem.alloc(&I.theta, static_cast<size_t>(d)));
+    pencil_work_destroy(I.pw);
+    cudaError_t e;
+    I.pw = pencil_work_create(d, 1, &e);
+    if (!I.pw) {
+      I.level = -1;
+      return fail(AMGEIG_ENOMEM, std::string("initial-level workspace: ") + cudaGetErrorString(e));
+    }
+    I.level = l;
+    I.d = d;
+    I.count = 0;
+    const DevCsr& L = h->A[l];
+    launch_csr_to_dense(d, L.rp, L.ci, L.v64, L.m64, I.A, I.M, st);
+  }
+  CK(cudaMemsetAsync(h->dstatus + 2, 0, sizeof(int), st));
+  launch_mass_factor(I.pw, d, I.M, h->dstatus + 2, st);
+  launch_coarse_modes(I.pw, d, count, I.A, I.Z, I.theta, st);
+  CK(cudaGetLastError());
+  int stt = 0;
+  CK(cudaMemcpyAsync(&stt, h->dstatus + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (stt) {
+    I.count = 0;
+    return fail(AMGEIG_ENOTSPD, "M on the initial level is not positive definite");
+  }
+  I.count = count;
+  return AMGEIG_OK;
+}
+
+// Mixed path, after the last correction: float64 Rayleigh quotients and
+// relative residuals of the finest-level vectors with the exact operator values
+// (V receives the iterate in float64, W the residual block); lam receives the
+// quotients in ascending order, perm the matching columns, relres the residual
+// of each column (unpermuted).
+int refine_fp64(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
+  const int qt = w->qt;
+  const long long cnt = h->sizes[0] * static_cast<long long>(qt);
+  launch_df_to_f64(as_df(w->U), cnt, w->V, st);
+  int nb = 0;
+  launch_rayleigh_f64(h->A[0], w->V, qt, w->partials, &nb, st);
+  launch_sum_partials(w->partials, nb, 2 * qt, w->sums, st);
+  launch_rq_finish(w->sums, qt, w->mu, w->lam, w->perm, st);
+  launch_defect_f64(h->A[0], w->V, qt, w->mu, w->W, w->partials, &nb, st);
+  launch_sum_partials(w->partials, nb, 2 * qt, w->sums, st);
+  CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
+  launch_relres(w->sums, w->mu, qt, w->relres, w->flags, st);
+  CK(cudaGetLastError());
+  w->permuted = true;
+  return AMGEIG_OK;
+}
+
 // Algorithm 3.2 on the hierarchy's stream; results stay in the workspace.
 int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o, amgeig_info* info,
                std::vector<double>& relres_host, cudaStream_t st) {
   const int qt = q + o.q_extra;
   const int n = h->nlev;
-  if (q < 1 || qt > h->dn) return fail(AMGEIG_EINVAL, "q + q_extra must be in [1, coarsest dimension]");
-  if (qt > 128) return fail(AMGEIG_EINVAL, "q + q_extra must be at most 128");
   int rc = check_options(o);
   if (rc) return rc;
+  if (q < 1 || qt > h->sizes[0]) return fail(AMGEIG_EINVAL, "q + q_extra must be in [1, finest dimension]");
+  if (qt > 128) return fail(AMGEIG_EINVAL, "q + q_extra must be at most 128");
+  // n1: the coarsest level that holds q + q_extra pairs (n1 = n when d_n suffices)
+  int n1 = o.n1;
+  if (n1 < 0) {
+    n1 = n - 1;
+    while (n1 > 0 && h->sizes[n1] < qt) --n1;
+  }
+  if (n1 >= n || h->sizes[n1] < qt) return fail(AMGEIG_EINVAL, "n1 must be a level with at least q + q_extra rows");
+  if (n1 < n - 1 && h->sizes[n1] > 2048)
+    return fail(AMGEIG_EINVAL, "the initial level above the coarsest must have at most 2048 rows");
   rc = ensure_workspace(h, qt, o.precision, std::max(1, o.v_cycles));
   if (rc) return rc;
   SolveWork* w = h->ws.get();
+  w->permuted = false;
   w->smoother = o.smoother;
   if (o.smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL) {
     rc = ensure_gs(h, st);
@@ -929,17 +1035,27 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   }
   {
     const int modes = (o.coarse_modes > 0 && o.coarse_modes < h->dn) ? o.coarse_modes : h->dn;
-    rc = ensure_modes(h, std::max(modes, qt), st);
+    rc = ensure_modes(h, n1 == n - 1 ? std::max(modes, qt) : modes, st);
     if (rc) return rc;
   }
-  // step 1: initial eigenpairs on level n1 = n (the coarsest)
+  // step 1: initial eigenpairs on level n1 (the coarsest unless it is too small)
+  const double* Z0 = h->Z;
+  const double* theta0 = h->theta;
+  int d0 = h->dn;
+  if (n1 < n - 1) {
+    rc = ensure_initial(h, n1, qt, st);
+    if (rc) return rc;
+    Z0 = h->init.Z;
+    theta0 = h->init.theta;
+    d0 = h->init.d;
+  }
   if (o.precision == AMGEIG_FP64)
-    launch_copy_cols(h->Z, h->dn, h->dn, qt, w->U, st);
+    launch_copy_cols(Z0, d0, d0, qt, w->U, st);
   else
-    launch_cols_to_df(h->Z, h->dn, h->dn, qt, as_df(w->U), st);
+    launch_cols_to_df(Z0, d0, d0, qt, as_df(w->U), st);
   {
     ProfScope ps(st, P_OTHER, 16.0 * qt, 0.0);
-    k_copy_d<<<1, 128, 0, st>>>(h->theta, qt, w->lam);
+    k_copy_d<<<1, 128, 0, st>>>(theta0, qt, w->lam);
   }
   CK(cudaMemsetAsync(w->nfallback, 0, sizeof(int), st));
   // the pencil kernels only ever set the status (Cholesky of the Gram Schur
@@ -951,8 +1067,8 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   int corrections = 0;
   bool converged = false;
   relres_host.assign(qt, 0.0);
-  // step 2: k = n1-1 .. 1 (0-based n-2 .. 1) one correction each, then the finest level
-  for (int k = n - 2; k >= 0; --k) {
+  // step 2: k = n1-1 .. 1 (0-based n1-1 .. 1) one correction each, then the finest level
+  for (int k = n1 - 1; k >= 0; --k) {
     if (o.precision == AMGEIG_FP64)
       launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st, P_CHAIN);
     else
@@ -995,12 +1111,31 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
       ++corrections;
     }
   }
-  if (n == 1) {
-    // single level: the coarse eigenpairs are the answer; report their residual
+  if (n1 == 0) {
+    // the initial level is the finest: its eigenpairs are the answer; report their residual
     rc = defect(h, w, 0, o, true, st);
     if (rc) return rc;
     CK(cudaMemcpyAsync(relres_host.data(), w->relres, sizeof(double) * qt, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
+    converged = mx <= tol;
+  }
+  if (o.precision != AMGEIG_FP64 && o.refine) {
+    // the returned values and residuals: float64 Rayleigh quotients of the
+    // final vectors; the stopping decision above stands unless the float64
+    // residuals contradict it
+    rc = refine_fp64(h, w, st);
+    if (rc) return rc;
+    std::vector<int> perm(qt);
+    std::vector<double> rr(qt);
+    int flags = 0;
+    CK(cudaMemcpyAsync(rr.data(), w->relres, sizeof(double) * qt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(perm.data(), w->perm, sizeof(int) * qt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&flags, w->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flags) return fail(AMGEIG_ENAN, "NaN or Inf in the refined Rayleigh quotients");
+    for (int c = 0; c < qt; ++c) relres_host[c] = rr[perm[c]];
     double mx = 0.0;
     for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
     converged = mx <= tol;
@@ -1014,7 +1149,7 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
     info->dense_fallbacks = nfb;
     info->corrections = corrections;
     info->converged = converged ? 1 : 0;
-    info->n1 = n - 1;
+    info->n1 = n1;
     info->max_relres = mx;
     info->status = converged ? AMGEIG_OK : AMGEIG_ENOCONV;
   }
@@ -1029,7 +1164,14 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
   if (eigvals) CK(cudaMemcpyAsync(eigvals, w->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st));
   if (eigvecs) {
     const double* src = w->U;
-    if (w->precision != AMGEIG_FP64) {
+    int ld = qt;
+    if (w->permuted) {
+      // the refinement left the iterate in float64 in V: its columns perm[0..q)
+      // gathered into U (free after the solve)
+      launch_gather_cols(w->V, N0, qt, w->perm, q, w->U, st);
+      src = w->U;
+      ld = q;
+    } else if (w->precision != AMGEIG_FP64) {
       // float-float iterate -> float64 (V is free after the solve)
       launch_df_to_f64(as_df(w->U), static_cast<long long>(N0) * qt, w->V, st);
       src = w->V;
@@ -1042,11 +1184,11 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
       // the slab results live in W, free after the solve (nslabs * q <= N0 * 2q)
       double* bval = w->W;
       int* bidx = reinterpret_cast<int*>(w->W + static_cast<size_t>(nslabs) * q);
-      k_col_best<<<nslabs, 256, 0, st>>>(src, N0, qt, q, slab, bval, bidx);
-      k_col_sign2<<<q, kSignThreads, 0, st>>>(src, qt, q, nslabs, bval, bidx, w->sign);
+      k_col_best<<<nslabs, 256, 0, st>>>(src, N0, ld, q, slab, bval, bidx);
+      k_col_sign2<<<q, kSignThreads, 0, st>>>(src, ld, q, nslabs, bval, bidx, w->sign);
     }
     k_out_vectors<<<static_cast<int>(std::min<long long>((total + 255) / 256, 8LL * kNumSms)), 256, 0, st>>>(
-        src, N0, qt, q, w->sign, dst);
+        src, N0, ld, q, w->sign, dst);
     CK(cudaGetLastError());
     if (!on_device) CK(cudaMemcpyAsync(eigvecs, dst, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
   }
@@ -1188,6 +1330,8 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->fixed_corrections = 0;
   opt->coarse_modes = 0;
   opt->smoother = AMGEIG_SMOOTHER_L1_JACOBI;
+  opt->n1 = -1;
+  opt->refine = 1;
 }
 
 const char* amgeig_strerror(int code) {
@@ -1643,7 +1787,7 @@ int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* o
   if (opt) o = *opt;
   int rc = check_options(o);
   if (rc) return rc;
-  if (q < 1 || q + o.q_extra > h->dn || q + o.q_extra > 128) return fail(AMGEIG_EINVAL, "q out of range");
+  if (q < 1 || q + o.q_extra > h->sizes[0] || q + o.q_extra > 128) return fail(AMGEIG_EINVAL, "q out of range");
   auto r = std::make_shared<Request>();
   r->h = h;
   r->q = q;
@@ -1708,14 +1852,17 @@ int amgeig_poll(uint64_t request_id, int* done, double* eigvals, double* eigvecs
 
 namespace {
 
-// device bytes a request's workspace needs beyond what its hierarchy already holds
-size_t workspace_bytes(const amgeig_hierarchy_t* h, int qt) {
-  size_t per = 0;
-  for (int l = 0; l < h->nlev; ++l) per += static_cast<size_t>(h->sizes[l]) * qt * 8 * 6;
-  return per + static_cast<size_t>(h->sizes[0]) * qt * 8 * 5;
+// device bytes of the workspace a request needs (the allocations make_workspace
+// would make for it, counted without allocating)
+size_t workspace_bytes(amgeig_hierarchy_t* h, const Request* r) {
+  const int qt = r->q + r->opt.q_extra;
+  const int prec = r->opt.precision == AMGEIG_FP64 ? AMGEIG_FP64 : AMGEIG_MIXED_FP32;
+  std::unique_ptr<SolveWork> w;
+  if (make_workspace(h, qt, prec, std::max(1, r->opt.v_cycles), w, true) != AMGEIG_OK || !w) return 0;
+  return w->mem.held + w->pw_bytes;
 }
 
-size_t ws_held(const amgeig_hierarchy_t* h) { return h->ws ? h->ws->mem.held : 0; }
+size_t ws_held(const amgeig_hierarchy_t* h) { return h->ws ? h->ws->mem.held + h->ws->pw_bytes : 0; }
 
 // Bytes held by the workspaces of the hierarchies the service has used (caller holds mu).
 size_t Service::resident_bytes() const {
@@ -1741,7 +1888,7 @@ int Service::fits(const Request* r) {
     if (h->ws && h->ws->qcap >= qt && h->ws->precision == wp) return kFits;
     own = ws_held(h);
   }
-  const size_t need = workspace_bytes(h, qt);
+  const size_t need = workspace_bytes(h, r);
   if (mem_limit > 0) {
     if (need > mem_limit) return kRefuse;
     // the request's own (too small) workspace is replaced, so it does not count

@@ -178,6 +178,20 @@ __global__ void k_copy_cols(const double* __restrict__ src, int rows, int ld, in
   }
 }
 
+// dense (rows x rows, row-major, zeroed beforehand) from a square CSR; one
+// thread per row writes that row's entries of both value arrays
+__global__ void k_csr_to_dense(int rows, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const double* __restrict__ a, const double* __restrict__ m, double* __restrict__ Ad,
+                               double* __restrict__ Md) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const long long at = static_cast<long long>(i) * rows + ci[p];
+    Ad[at] = a[p];
+    Md[at] = m[p];
+  }
+}
+
 int gram_chunks(int rows, int q, int w, int* chunk_rows) {
   const int tiles = ceil_div(q, kGT) * ceil_div(w, kGT);
   int chunks = ceil_div(rows, 256);
@@ -271,6 +285,15 @@ void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, c
   long long b = (total + 255) / 256;
   if (b > 8 * kNumSms) b = 8 * kNumSms;
   k_copy_cols<<<static_cast<int>(b), 256, 0, st>>>(src, rows, ld, q, dst);
+}
+
+void launch_csr_to_dense(int rows, const int* rp, const int* ci, const double* a, const double* m, double* Ad,
+                         double* Md, cudaStream_t st) {
+  const double bytes = 16.0 * rows * static_cast<double>(rows);
+  ProfScope ps(st, P_OTHER, bytes, 0.0, 3);
+  cudaMemsetAsync(Ad, 0, sizeof(double) * rows * static_cast<size_t>(rows), st);
+  cudaMemsetAsync(Md, 0, sizeof(double) * rows * static_cast<size_t>(rows), st);
+  k_csr_to_dense<<<ceil_div(rows, 128), 128, 0, st>>>(rows, rp, ci, a, m, Ad, Md);
 }
 
 }  // namespace amgeig

@@ -103,6 +103,16 @@ void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const float* di
                       int w, double bytes, cudaStream_t st);
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st);
 
+// ---- final float64 Rayleigh-quotient refinement (refine.cu) --------------
+// partials[block][2q]: per-block sums of u_c (A u)_c and u_c (M u)_c (float64,
+// exact operator values); q <= 128.
+void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, double* partials, int* nblocks_out,
+                         cudaStream_t st);
+// theta_j = sums[j] / sums[q+j]; lam = theta sorted ascending, perm[c] = column of the c-th smallest
+void launch_rq_finish(const double* sums, int q, double* theta, double* lam, int* perm, cudaStream_t st);
+// dst (rows x q) = columns perm[0..q) of src (rows x ld)
+void launch_gather_cols(const double* src, int rows, int ld, const int* perm, int q, double* dst, cudaStream_t st);
+
 // ---- float-float kernels of the mixed path (spmm_df.cu) -------------------
 // Blocks are float2 (hi, lo) pairs, row-major like the float64 blocks.
 void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* lam, float* R, int ldr,
@@ -164,6 +174,10 @@ void launch_sum_partials(const double* part, int nparts, int len, double* out, c
 // writes relres[q] and flags[0] = 1 if any value is NaN/Inf.
 void launch_relres(const double* sums, const double* lam, int q, double* relres, int* flags, cudaStream_t st);
 
+// Dense copies (rows x rows, row-major) of a square CSR's two value arrays
+void launch_csr_to_dense(int rows, const int* rp, const int* ci, const double* a, const double* m, double* Ad,
+                         double* Md, cudaStream_t st);
+
 // Copy the first q columns of a row-major (rows x ld) matrix into a rows x q block
 void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, cudaStream_t st);
 
@@ -172,7 +186,10 @@ void launch_copy_cols(const double* src, int rows, int ld, int q, double* dst, c
 struct PencilWork;  // opaque device workspace, sized by pencil_work_create
 
 // Workspace for pencils of coarse size dn with up to qmax border vectors.
-PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err);
+// dry: size the workspace (PencilWork::bytes) without allocating it
+PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err, bool dry = false);
+// device bytes pencil_work_create(dn, qmax) allocates
+size_t pencil_work_bytes(int dn, int qmax);
 void pencil_work_destroy(PencilWork* w);
 
 // One Rayleigh-Ritz step on V_n + span(V) (Algorithm 3.1 step 2) in the

@@ -46,6 +46,7 @@ constexpr int kSyThreads = AMGEIG_SY_THREADS;
 struct PencilWork {
   int dn = 0, qmax = 0, nmax = 0;
   void* base = nullptr;  // one device allocation holding every array below
+  size_t bytes = 0;      // its size
   // Rayleigh-Ritz pencil (float-float)
   df* KB = nullptr;   // dn x 2q   Z_m^T C = [K | B]
   df* Ft = nullptr;   // dn x q    K - Theta B
@@ -2146,7 +2147,14 @@ constexpr size_t kSmemBudget = 225 * 1024;
 
 // ------------------------------------------------------------ host side
 
-PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
+size_t pencil_work_bytes(int dn, int qmax) {
+  PencilWork* w = pencil_work_create(dn, qmax, nullptr, true);
+  const size_t b = w ? w->bytes : 0;
+  pencil_work_destroy(w);
+  return b;
+}
+
+PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err, bool dry) {
   auto* w = new PencilWork();
   w->dn = dn;
   w->qmax = qmax;
@@ -2169,6 +2177,8 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err) {
   };
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {
+      w->bytes = total;
+      if (dry) return w;
       cudaError_t e = cudaMalloc(&w->base, total);
       if (err) *err = e;
       if (e != cudaSuccess) {

@@ -90,9 +90,10 @@ def _poll_all(ids, sizes, timeout=300):
 
 def test_service_memory_cap_refuses_and_evicts():
     """Under the service's memory cap a request whose workspace alone exceeds the cap is refused with
-    ENOMEM; requests alternating between two hierarchies whose workspaces do not fit together each
-    release the other's idle workspace and give the same bits as a solve run alone."""
-    cases = [problem_and_blob("square", 32, 50, 1), problem_and_blob("lshape", 16, 60, 2)]
+    ENOMEM; requests alternating between two hierarchies (two handles of one problem, so that their
+    workspaces are alike) whose workspaces do not fit together each release the other's idle workspace
+    and give the same bits as a solve run alone."""
+    cases = [problem_and_blob("lshape", 16, 60, 2), problem_and_blob("lshape", 16, 60, 2)]
     hs = [ae.Hierarchy(blob) for _, blob, _ in cases]
     opt = ae.options(q_extra=2, max_corrections=40, precision=ae.AMGEIG_MIXED_FP32)
     try:

@@ -491,3 +491,43 @@ def test_coarse_modes_parity(L):
         lam, U, info, _ = h.solve(6, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=L, coarse_modes=16))
     assert np.max(np.abs(lam - lam_o) / lam_o) < 1e-10
     assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
+
+
+# ------------------------------------------------------------------ initial level n1 < n
+
+
+@pytest.mark.parametrize("L", [1, 2])
+def test_initial_level_above_coarsest_matches_oracle(L):
+    """q + q_extra above the coarsest dimension: both sides start on the coarsest level that holds the
+    pairs (Algorithm 3.2 step 1 with n1 < n) and agree after L finest-level corrections."""
+    p, blob, _ = problem_and_blob("square", 32, 20, 1)
+    oh = O.read_blob(blob)
+    q, qe = oh.sizes[-1] + 2, 3
+    lam_o, U_o, info_o = O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=L))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, code = h.solve(q, tol=0.0, opt=ae.options(q_extra=qe, fixed_corrections=L))
+    assert info.n1 == info_o.n1 < len(oh.sizes) - 1
+    tol = eig_rel_tol(lam_o, lam_max(p))
+    assert np.all(np.abs(lam - lam_o) <= tol * lam_o), np.max(np.abs(lam - lam_o) / lam_o)
+    assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
+
+
+def test_initial_level_finest_and_converged_mixed():
+    """n1 = 0 is the finest level's dense eigensolution; the mixed path from the default n1 < n
+    converges to the dense eigenpairs."""
+    p, blob, _ = problem_and_blob("square", 32, 20, 1)
+    oh = O.read_blob(blob)
+    lam_ex, U_ex = dense_pairs(p, 24)
+    with ae.Hierarchy(blob) as h:
+        lam0, U0, info0, _ = h.solve(4, tol=1e-8, opt=ae.options(n1=0))
+        assert info0.n1 == 0 and info0.corrections == 0
+        assert np.all(np.abs(lam0 - lam_ex[:4]) <= 1e-11 * lam_ex[:4])
+        assert m_subspace_angle(U0, U_ex[:, :4], oh.M[0]) < 1e-8
+        q = oh.sizes[-1] + 2
+        lam, U, info, code = h.solve(q, tol=1e-9, opt=ae.options(q_extra=3, max_corrections=150,
+                                                                 precision=ae.AMGEIG_MIXED_FP32))
+        assert code == ae.AMGEIG_OK and info.n1 < len(oh.sizes) - 1
+        assert np.all(np.abs(lam - lam_ex[:q]) <= 1e-10 * lam_ex[:q]), np.max(np.abs(lam - lam_ex[:q]) / lam_ex[:q])
+        with pytest.raises(ae.AmgEigError) as e:
+            h.solve(q, opt=ae.options(q_extra=3, n1=len(oh.sizes) - 1))
+        assert e.value.code == ae.AMGEIG_EINVAL

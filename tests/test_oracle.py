@@ -186,6 +186,39 @@ def test_single_level_hierarchy_is_dense_solve():
     assert info.corrections == 0 and info.n1 == 0
 
 
+def test_initial_level_above_the_coarsest():
+    """Algorithm 3.2 step 1 with n1 < n: when q + q_extra exceeds the coarsest dimension the oracle
+    starts on the coarsest level that holds that many pairs, and its initial pairs there are the dense
+    eigenpairs of (A_n1, M_n1); with n1 = 0 the solve is the finest level's dense eigensolution (no
+    correction runs); and the converged solve from an intermediate n1 equals the finest level's dense
+    eigenpairs (the fixed point)."""
+    p, oh = _oh("square", 32, 20, 1)  # coarsest level below 20 rows
+    dn = oh.sizes[-1]
+    q, qe = dn + 2, 3
+    qt = q + qe
+    n1 = O.initial_level(oh, qt)
+    assert n1 < oh.n_levels - 1 and oh.sizes[n1] >= qt and oh.sizes[n1 + 1] < qt
+    # initial pairs on level n1: exact for the level's own pencil (one Rayleigh quotient per pair)
+    lam1, U1 = O.smallest_pairs(oh.A[n1].toarray(), oh.M[n1].toarray(), qt)
+    A1, M1 = oh.A[n1], oh.M[n1]
+    assert np.abs(U1.T @ (M1 @ U1) - np.eye(qt)).max() < 1e-12
+    assert np.abs(A1 @ U1 - (M1 @ U1) * lam1).max() < 1e-10 * lam1.max()
+    # n1 = 0 is the dense finest-level solve
+    lam0, U0, info0 = O.solve(oh, 4, opts=O.Options(n1=0))
+    lam_ex, U_ex = dense_pairs(p, 4)
+    assert info0.n1 == 0 and info0.corrections == 0
+    assert np.allclose(lam0, lam_ex, rtol=1e-12)
+    # the default n1 for q + q_extra > d_n, converged: the dense eigenpairs
+    lam, U, info = O.solve(oh, q, tol=1e-10, opts=O.Options(q_extra=qe, max_corrections=150))
+    assert info.n1 == n1 and info.converged
+    lam_ex, U_ex = dense_pairs(p, q)
+    assert np.all(np.abs(lam - lam_ex) <= eig_rel_tol(lam_ex, lam_max(p)) * lam_ex)
+    assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(q)).max() < 1e-11
+    # an explicit n1 that cannot hold q + q_extra pairs is refused
+    with pytest.raises(ValueError):
+        O.solve(oh, q, opts=O.Options(q_extra=qe, n1=oh.n_levels - 1))
+
+
 def test_closed_form_unit_square():
     """The converged solver approaches pi^2 (2, 5, 5, 8) at O(h^2) (Example 1)."""
     exact = np.pi ** 2 * np.array([2.0, 5.0, 5.0, 8.0])
