@@ -87,6 +87,10 @@ typedef struct {
                             recomputed in float64 with the exact operator values; those are the
                             returned eigenvalues (ascending, vectors permuted alike) and residuals.
                             0 = return the float-float Ritz values and residuals */
+  int graphs;            /* 1 (default): the nested phase and each finest-level correction are
+                            captured once as CUDA graphs (per settings) and replayed; 0: every
+                            kernel launched directly.  Same arithmetic, same bits.  Not used
+                            while profiling is enabled or when the caller's stream is capturing */
 } amgeig_options;
 
 #define AMGEIG_SMOOTHER_L1_JACOBI 0

@@ -42,7 +42,7 @@ class amgeig_options(ctypes.Structure):
     _fields_ = [("max_corrections", ctypes.c_int), ("v_cycles", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("q_extra", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fixed_corrections", ctypes.c_int), ("coarse_modes", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("n1", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("n1", ctypes.c_int), ("refine", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class amgeig_prof_entry(ctypes.Structure):

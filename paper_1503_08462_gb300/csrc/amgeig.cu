@@ -453,7 +453,19 @@ struct SolveWork {
   int* nfallback = nullptr;  // corrections that needed the dense eigensolver
   PencilWork* pw = nullptr;
   size_t pw_bytes = 0;  // device bytes of pw
-  ~SolveWork() { pencil_work_destroy(pw); }
+  // captured CUDA graphs of launch segments (see run_segment), keyed by the
+  // segment, the settings and the buffer roles on entry
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> post;  // buffer roles after the segment
+    unsigned long long kernels = 0;
+  };
+  std::map<std::string, Graph> graphs;
+  ~SolveWork() {
+    for (auto& g : graphs)
+      if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    pencil_work_destroy(pw);
+  }
 };
 
 // dry: allocate nothing, only add up in w->mem.held (and pw_bytes) what the
@@ -920,7 +932,7 @@ int check_options(const amgeig_options& o) {
       o.fixed_corrections < 0 || o.coarse_modes < 0 ||
       (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
       (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL) || o.n1 < -1 ||
-      (o.refine != 0 && o.refine != 1))
+      (o.refine != 0 && o.refine != 1) || (o.graphs != 0 && o.graphs != 1))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -933,6 +945,79 @@ int ensure_modes(amgeig_hierarchy_t* h, int need, cudaStream_t st) {
   launch_f64_to_df(h->Z, static_cast<long long>(h->dn) * h->dn, h->Zdf, st);
   CK(cudaGetLastError());
   h->modes_ready = need;
+  return AMGEIG_OK;
+}
+
+// ------------------------------------------------------------------ CUDA graphs
+
+// Which buffer plays which role: the workspace swaps buffer pointers between
+// launches (the iterate and its copy, smoothing in/out, defect and residual),
+// so a captured launch sequence is valid only from the roles it was captured in.
+std::vector<void*> roles(SolveWork* w) {
+  std::vector<void*> r = {w->U, w->Ualt, w->V, w->W};
+  for (auto* v : {&w->B64, &w->X64, &w->T64, &w->D64, &w->E64})
+    for (double* p : *v) r.push_back(p);
+  for (auto* v : {&w->B32, &w->X32, &w->T32, &w->D32, &w->E32})
+    for (float* p : *v) r.push_back(p);
+  return r;
+}
+
+void set_roles(SolveWork* w, const std::vector<void*>& r) {
+  size_t i = 0;
+  w->U = static_cast<double*>(r[i++]);
+  w->Ualt = static_cast<double*>(r[i++]);
+  w->V = static_cast<double*>(r[i++]);
+  w->W = static_cast<double*>(r[i++]);
+  for (auto* v : {&w->B64, &w->X64, &w->T64, &w->D64, &w->E64})
+    for (double*& p : *v) p = static_cast<double*>(r[i++]);
+  for (auto* v : {&w->B32, &w->X32, &w->T32, &w->D32, &w->E32})
+    for (float*& p : *v) p = static_cast<float*>(r[i++]);
+}
+
+// Run the launch sequence `body` on st.  With graphs on (and no profiling, and
+// st not already capturing), the first run of a (segment, settings, roles)
+// combination captures the sequence as a CUDA graph and later runs replay it:
+// one launch instead of the sequence's hundred-odd, with no host work between
+// kernels.  body must only enqueue work (no host synchronisation).
+template <class F>
+int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, cudaStream_t st, F body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!o.graphs || profiling_on() || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone)
+    return body();
+  std::vector<void*> pre = roles(w);
+  std::string key = seg;
+  const int cfg[] = {w->qt, w->ld32, o.precision, o.v_cycles, o.pre_sweeps, o.post_sweeps, o.smoother,
+                     o.coarse_modes, w->bf16 ? 1 : 0};
+  key.append(reinterpret_cast<const char*>(cfg), sizeof(cfg));
+  key.append(reinterpret_cast<const char*>(pre.data()), sizeof(void*) * pre.size());
+  auto it = w->graphs.find(key);
+  if (it == w->graphs.end()) {
+    const unsigned long long k0 = launch_count();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    const int rc = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != AMGEIG_OK) {
+      if (g) cudaGraphDestroy(g);
+      set_roles(w, pre);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(AMGEIG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    SolveWork::Graph rec;
+    const cudaError_t ei = cudaGraphInstantiate(&rec.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(AMGEIG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    rec.post = roles(w);
+    // the kernels were counted when captured; the launch below runs them
+    rec.kernels = launch_count() - k0;
+    it = w->graphs.emplace(key, std::move(rec)).first;
+    CK(cudaGraphLaunch(it->second.exec, st));
+    return AMGEIG_OK;
+  }
+  CK(cudaGraphLaunch(it->second.exec, st));
+  add_launches(it->second.kernels);
+  set_roles(w, it->second.post);
   return AMGEIG_OK;
 }
 
@@ -1067,23 +1152,29 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   int corrections = 0;
   bool converged = false;
   relres_host.assign(qt, 0.0);
-  // step 2: k = n1-1 .. 1 (0-based n1-1 .. 1) one correction each, then the finest level
-  for (int k = n1 - 1; k >= 0; --k) {
-    if (o.precision == AMGEIG_FP64)
-      launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st, P_CHAIN);
-    else
-      launch_spmm_df(h->P[k], as_df(w->U), qt, as_df(w->Ualt), false, st, P_CHAIN);
-    std::swap(w->U, w->Ualt);
-    if (k >= 1) {
-      rc = defect(h, w, k, o, false, st);
-      if (rc) return rc;
-      rc = correction_tail(h, w, k, o, st);
-      if (rc) return rc;
-      continue;
-    }
+  // step 2: k = n1-1 .. 1 (0-based) one correction each after the prolongation,
+  // then the prolongation to the finest level and its first defect (one launch
+  // segment), then the finest level's corrections (one segment each: the
+  // correction and the next defect) until the stopping test
+  if (n1 > 0) {
+    rc = run_segment(w, o, "nested " + std::to_string(n1), st, [&]() -> int {
+      for (int k = n1 - 1; k >= 0; --k) {
+        if (o.precision == AMGEIG_FP64)
+          launch_spmm_f64(h->P[k], w->U, qt, w->Ualt, false, st, P_CHAIN);
+        else
+          launch_spmm_df(h->P[k], as_df(w->U), qt, as_df(w->Ualt), false, st, P_CHAIN);
+        std::swap(w->U, w->Ualt);
+        int r = defect(h, w, k, o, k == 0, st);
+        if (r) return r;
+        if (k >= 1) {
+          r = correction_tail(h, w, k, o, st);
+          if (r) return r;
+        }
+      }
+      return AMGEIG_OK;
+    });
+    if (rc) return rc;
     for (;;) {
-      rc = defect(h, w, 0, o, true, st);
-      if (rc) return rc;
       int flags = 0;
       CK(cudaMemcpyAsync(relres_host.data(), w->relres, sizeof(double) * qt, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(&flags, w->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1106,7 +1197,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
         }
         if (corrections == o.max_corrections) break;
       }
-      rc = correction_tail(h, w, 0, o, st);
+      rc = run_segment(w, o, "finest", st, [&]() -> int {
+        const int r = correction_tail(h, w, 0, o, st);
+        if (r) return r;
+        return defect(h, w, 0, o, true, st);
+      });
       if (rc) return rc;
       ++corrections;
     }
@@ -1332,6 +1427,7 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->smoother = AMGEIG_SMOOTHER_L1_JACOBI;
   opt->n1 = -1;
   opt->refine = 1;
+  opt->graphs = 1;
 }
 
 const char* amgeig_strerror(int code) {

@@ -63,6 +63,10 @@ void ensure_dynamic_smem(const void* func, size_t bytes) {
     cur = bytes;
 }
 
+unsigned long long launch_count() { return prof().launches.load(); }
+void add_launches(unsigned long long n) { prof().launches += n; }
+bool profiling_on() { return prof().on.load(std::memory_order_relaxed); }
+
 thread_local int g_depth = 0;  // nested scopes only count launches; the outermost one is timed
 
 ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels) : st_(st), slot_(-1) {

@@ -37,6 +37,13 @@ void ensure_dynamic_smem(const void* func, size_t bytes);
 // return `code`; code == AMGEIG_OK clears the record.
 int set_last_error(int code, const char* msg);
 
+// The process-wide kernel count (what amgeig_kernel_launches returns), a way
+// to add the kernels of a replayed CUDA graph to it (their ProfScopes ran once,
+// when the graph was captured), and whether per-launch event timing is on.
+unsigned long long launch_count();
+void add_launches(unsigned long long n);
+bool profiling_on();
+
 class ProfScope {
  public:
   ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels = 1);

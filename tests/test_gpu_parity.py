@@ -531,3 +531,49 @@ def test_initial_level_finest_and_converged_mixed():
         with pytest.raises(ae.AmgEigError) as e:
             h.solve(q, opt=ae.options(q_extra=3, n1=len(oh.sizes) - 1))
         assert e.value.code == ae.AMGEIG_EINVAL
+
+
+# ------------------------------------------------------------------ mixed path against the oracle
+
+
+@pytest.mark.parametrize("L", [1, 2])
+def test_mixed_iteration_parity_multilane(L):
+    """The mixed path (float32 V-cycle, float-float Rayleigh-Ritz, float64 Rayleigh quotients at the end)
+    against the oracle's iterates after L finest-level corrections, on an L-shape with 247,681 rows:
+    the finest level takes the multi-lane layout of the timed workload (4 lanes per row, 2 float4 groups
+    per lane), the levels below 155,648 rows 8 lanes per row.  Tolerances as for the full-size check
+    of the timed settings: the float32 V-cycle moves each correction by <= 2e-5 of its column, hence
+    the subspace by an angle of order 1e-5 and the Ritz values by about twice that times the relative
+    residual."""
+    p, blob, _ = problem_and_blob("lshape", 288, 400, 2)
+    oh = O.read_blob(blob)
+    assert oh.sizes[0] >= 200_000
+    q, qe = 12, 4
+    kw = dict(q_extra=qe, fixed_corrections=L, v_cycles=2)
+    lam_o, U_o, info_o = O.solve(oh, q, tol=0.0, opts=O.Options(**kw))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, _ = h.solve(q, tol=0.0, opt=ae.options(precision=ae.AMGEIG_MIXED_FP32, **kw))
+    rel = np.max(np.abs(lam - lam_o) / lam_o)
+    ang = m_subspace_angle(U, U_o, oh.M[0])
+    assert rel <= 1e-6 and ang <= 1e-4, (rel, ang, info_o.relres.max())
+    assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(q)).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", [ae.AMGEIG_FP64, ae.AMGEIG_MIXED_FP32])
+def test_graph_replay_gives_the_same_bits(prec):
+    """The nested phase and the finest-level corrections replayed from captured CUDA graphs give the bits of
+    direct launches, on the first (capturing) solve and on later (replaying) ones, and count the same
+    kernels; the buffer roles alternate between corrections, so both capture states are exercised."""
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    base = dict(q_extra=2, max_corrections=40, precision=prec, v_cycles=2)
+    with ae.Hierarchy(blob) as h:
+        k0 = ae.amgeig_kernel_launches()
+        direct = h.solve(5, tol=1e-9, opt=ae.options(graphs=0, **base))
+        k1 = ae.amgeig_kernel_launches()
+        runs = [h.solve(5, tol=1e-9, opt=ae.options(graphs=1, **base)) for _ in range(3)]
+        k2 = ae.amgeig_kernel_launches()
+    assert direct[2].corrections >= 3
+    for lam, U, info, code in runs:
+        assert code == direct[3] and info.corrections == direct[2].corrections
+        assert np.array_equal(lam, direct[0]) and np.array_equal(U, direct[1])
+    assert k2 - k1 == 3 * (k1 - k0)
