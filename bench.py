@@ -581,8 +581,10 @@ def main():
     pv1.record(stream)
     pv1.synchronize()
     ms_profiled = pv0.elapsed_time(pv1) / max(args.steps, 1)
-    prof = ae.amgeig_profile_read()
+    prof_all = ae.amgeig_profile_read()
     ae.amgeig_profile_enable(False)
+    prof = {k: v for k, v in prof_all.items() if "@" not in k}
+    per_level = {k: v for k, v in prof_all.items() if "@" in k}
     ms_total = replica_max(dist, ms_total, f"cuda:{local}")
     ms_per_step = ms_total / args.steps
     value = world * q * args.steps / (ms_total / 1e3)
@@ -644,6 +646,17 @@ def main():
     roof["algorithmic_bytes_per_launch"] = d["bytes"] / max(d["launches"], 1)
     roof["timed_in"] = (f"second {args.steps}-step region with per-launch CUDA events "
                         f"({ms_profiled:.3f} ms per step there)")
+    # the V-cycle's HBM-bound classes level by level (algorithmic bytes / event time / measured peak)
+    levels_tab = {}
+    for key, v in per_level.items():
+        cls, lev = key.split("@")
+        if cls not in ("smooth", "transfer") or v["total_ms"] <= 0:
+            continue
+        gbs_l = v["bytes"] / (v["total_ms"] / 1e3) / 1e9
+        levels_tab.setdefault(int(lev), {})[cls] = {
+            "frac": round(gbs_l / hbm_peak, 4), "GB/s": round(gbs_l, 1), "ms": round(v["total_ms"], 3),
+            "launches": v["launches"], "us_per_launch": round(v["total_ms"] / v["launches"] * 1e3, 2)}
+    roof["per_level"] = {str(k): levels_tab[k] for k in sorted(levels_tab)}
     kernels = {k: {"launches": v["launches"], "kernels": v["kernels"], "ms": round(v["total_ms"], 3),
                    "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
                    "GB/s": round(v["bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1),

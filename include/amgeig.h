@@ -272,8 +272,9 @@ typedef struct {
 int amgeig_profile_enable(int enable);
 
 /* Synchronise on the recorded events and write up to max_entries per-class
- * totals (classes with no launches are skipped) into out; *n_entries receives
- * the count.  Errors: EINVAL, ECUDA. */
+ * totals (classes with no launches are skipped) into out, followed by the
+ * classes of the V-cycle per level (names "<class>@<level>", levels 0-based);
+ * *n_entries receives the count.  Errors: EINVAL, ECUDA. */
 int amgeig_profile_read(amgeig_prof_entry* out, int max_entries, int* n_entries);
 
 /* Cumulative number of kernels this library has launched in this process. */

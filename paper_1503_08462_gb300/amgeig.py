@@ -261,9 +261,9 @@ def amgeig_profile_enable(enable: bool) -> None:
 
 def amgeig_profile_read():
     """Per kernel class totals: {name: dict(launches, kernels, total_ms, bytes, flops)}."""
-    buf = (amgeig_prof_entry * 16)()
+    buf = (amgeig_prof_entry * 512)()
     n = ctypes.c_int()
-    _check(lib().amgeig_profile_read(buf, 16, ctypes.byref(n)), "amgeig_profile_read")
+    _check(lib().amgeig_profile_read(buf, 512, ctypes.byref(n)), "amgeig_profile_read")
     return {buf[i].name.decode(): dict(launches=buf[i].launches, kernels=buf[i].kernels, total_ms=buf[i].total_ms,
                                        bytes=buf[i].bytes, flops=buf[i].flops) for i in range(n.value)}
 

@@ -728,6 +728,7 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
   T* dummy = nullptr;
   const bool gs = w->smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL;
   for (int l = k; l < n - 1; ++l) {
+    LevelTag tag(l);
     const DevCsr& A = h->A[l];
     const T* d = dinv_of(h, l, dummy);
     if (gs && pre >= 1) {
@@ -749,8 +750,12 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
       spmm(h->R[l], B[l], q, B[l + 1], false, st, w->bf16);
     }
   }
-  coarse_solve(h, B[n - 1], q, X[n - 1], st);
+  {
+    LevelTag tag(n - 1);
+    coarse_solve(h, B[n - 1], q, X[n - 1], st);
+  }
   for (int l = n - 2; l >= k; --l) {
+    LevelTag tag(l);
     const DevCsr& A = h->A[l];
     const T* d = dinv_of(h, l, dummy);
     spmm(h->P[l], X[l + 1], q, X[l], true, st, w->bf16);
@@ -799,6 +804,7 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
   auto& E = VBufs<T>::E(w);
   const int wd = width_of(w, static_cast<T*>(nullptr));
   const long long cnt = h->sizes[k] * wd;
+  LevelTag tag(k);
   if constexpr (std::is_same<T, float>::value) {
     // the same sums without the copies: the first cycle's result becomes E by a
     // pointer swap, its residual goes to D and trades places with B (D then

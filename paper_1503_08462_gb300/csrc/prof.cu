@@ -1,5 +1,6 @@
 // Launch counter and event-based per-class timing (see prof.cuh).
 #include <atomic>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -14,6 +15,7 @@ namespace {
 
 struct Rec {
   int cls;
+  int level;  // hierarchy level of the launch (-1: untagged)
   double bytes, flops;
   int kernels;
   cudaEvent_t e0, e1;
@@ -68,6 +70,10 @@ void add_launches(unsigned long long n) { prof().launches += n; }
 bool profiling_on() { return prof().on.load(std::memory_order_relaxed); }
 
 thread_local int g_depth = 0;  // nested scopes only count launches; the outermost one is timed
+thread_local int g_level = -1;  // level tag of the launches in flight (LevelTag)
+
+LevelTag::LevelTag(int level) : prev_(g_level) { g_level = level; }
+LevelTag::~LevelTag() { g_level = prev_; }
 
 ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels) : st_(st), slot_(-1) {
   Profiler& p = prof();
@@ -75,7 +81,7 @@ ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int k
   if (g_depth++ > 0) return;
   if (!p.on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(p.mu);
-  Rec r{cls, bytes, flops, kernels, p.take(), p.take()};
+  Rec r{cls, g_level, bytes, flops, kernels, p.take(), p.take()};
   if (!r.e0 || !r.e1) return;
   cudaEventRecord(r.e0, st);
   slot_ = static_cast<int>(p.recs.size());
@@ -111,23 +117,32 @@ int amgeig_profile_read(amgeig_prof_entry* out, int max_entries, int* n_entries)
   if (!out || !n_entries || max_entries < 0) return AMGEIG_EINVAL;
   Profiler& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
-  amgeig_prof_entry tab[P_COUNT];
-  std::memset(tab, 0, sizeof(tab));
-  for (int c = 0; c < P_COUNT; ++c) std::strncpy(tab[c].name, kNames[c], sizeof(tab[c].name) - 1);
+  constexpr int kLevels = 64;
+  std::vector<amgeig_prof_entry> tab(static_cast<size_t>(P_COUNT) * (kLevels + 1));
+  std::memset(tab.data(), 0, sizeof(amgeig_prof_entry) * tab.size());
+  // slot c: the class total; slot P_COUNT * (1 + l) + c: the class on level l
+  for (int c = 0; c < P_COUNT; ++c) {
+    std::strncpy(tab[c].name, kNames[c], sizeof(tab[c].name) - 1);
+    for (int l = 0; l < kLevels; ++l)
+      std::snprintf(tab[P_COUNT * (1 + l) + c].name, sizeof(tab[0].name), "%s@%d", kNames[c], l);
+  }
   for (const Rec& r : p.recs) {
     if (cudaEventSynchronize(r.e1) != cudaSuccess) return AMGEIG_ECUDA;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return AMGEIG_ECUDA;
-    amgeig_prof_entry& t = tab[r.cls];
-    t.launches += 1;
-    t.kernels += r.kernels;
-    t.total_ms += ms;
-    t.bytes += r.bytes;
-    t.flops += r.flops;
+    for (int slot : {r.cls, (r.level >= 0 && r.level < kLevels) ? P_COUNT * (1 + r.level) + r.cls : -1}) {
+      if (slot < 0) continue;
+      amgeig_prof_entry& t = tab[slot];
+      t.launches += 1;
+      t.kernels += r.kernels;
+      t.total_ms += ms;
+      t.bytes += r.bytes;
+      t.flops += r.flops;
+    }
   }
   int n = 0;
-  for (int c = 0; c < P_COUNT && n < max_entries; ++c)
-    if (tab[c].launches > 0) out[n++] = tab[c];
+  for (size_t i = 0; i < tab.size() && n < max_entries; ++i)
+    if (tab[i].launches > 0) out[n++] = tab[i];
   *n_entries = n;
   return AMGEIG_OK;
 }

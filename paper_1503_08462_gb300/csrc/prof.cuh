@@ -44,6 +44,19 @@ unsigned long long launch_count();
 void add_launches(unsigned long long n);
 bool profiling_on();
 
+// Tags the launches made while it lives with a hierarchy level, so that the
+// timing table also reports each class per level.
+class LevelTag {
+ public:
+  explicit LevelTag(int level);
+  ~LevelTag();
+  LevelTag(const LevelTag&) = delete;
+  LevelTag& operator=(const LevelTag&) = delete;
+
+ private:
+  int prev_;
+};
+
 class ProfScope {
  public:
   ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels = 1);
