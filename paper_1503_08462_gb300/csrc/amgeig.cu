@@ -521,8 +521,9 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
     CK(m.alloc(&w->PX[l], Nl * qt));
   }
   const int blocks_max = ceil_div(N0, 8) + 1;  // defect launches use >= 8 rows per block
-  CK(m.alloc(&w->partials, static_cast<size_t>(blocks_max) * 2 * qt));
-  CK(m.alloc(&w->sums, 2 * qt));
+  CK(m.alloc(&w->partials, std::max(static_cast<size_t>(blocks_max) * 2 * qt,
+                                     static_cast<size_t>(rayleigh_blocks(qt)) * 5 * qt)));
+  CK(m.alloc(&w->sums, 5 * qt));
   CK(m.alloc(&w->relres, qt));
   CK(m.alloc(&w->lam, qt));
   CK(m.alloc(&w->mu, qt));
@@ -1081,12 +1082,19 @@ int refine_fp64(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
   launch_df_to_f64(as_df(w->U), cnt, w->V, st);
   int nb = 0;
   launch_rayleigh_f64(h->A[0], w->V, qt, w->partials, &nb, st);
-  launch_sum_partials(w->partials, nb, 2 * qt, w->sums, st);
-  launch_rq_finish(w->sums, qt, w->mu, w->lam, w->perm, st);
-  launch_defect_f64(h->A[0], w->V, qt, w->mu, w->W, w->partials, &nb, st);
-  launch_sum_partials(w->partials, nb, 2 * qt, w->sums, st);
-  CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
-  launch_relres(w->sums, w->mu, qt, w->relres, w->flags, st);
+  launch_sum_partials(w->partials, nb, 5 * qt, w->sums, st);
+  launch_rq_finish(w->sums, qt, w->mu, w->lam, w->perm, w->relres, w->flags, st);
+  int redo = 0;
+  CK(cudaMemcpyAsync(&redo, w->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (redo == 2) return fail(AMGEIG_ENAN, "NaN or Inf in the refined Rayleigh quotients");
+  if (redo) {
+    // small residuals: form them explicitly with the refined quotients
+    launch_defect_f64(h->A[0], w->V, qt, w->mu, w->W, w->partials, &nb, st);
+    launch_sum_partials(w->partials, nb, 2 * qt, w->sums, st);
+    CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
+    launch_relres(w->sums, w->mu, qt, w->relres, w->flags, st);
+  }
   CK(cudaGetLastError());
   w->permuted = true;
   return AMGEIG_OK;
@@ -1329,6 +1337,8 @@ struct Service {
   // hierarchies whose workspace the service has used, least recently used first;
   // under a memory limit, idle ones give their workspace back to admit others
   std::vector<amgeig_hierarchy_t*> resident;
+  // admitted requests whose workspace is being made: the bytes it will hold
+  std::map<amgeig_hierarchy_t*, size_t> reserved;
   size_t mem_limit = 0;  // bytes of resident workspaces the service may hold (0: no limit)
   uint64_t evictions = 0;
   uint64_t next_id = 1;
@@ -1399,6 +1409,7 @@ struct Service {
       {
         std::lock_guard<std::mutex> lk(mu);
         busy.erase(std::find(busy.begin(), busy.end(), r->h));
+        reserved.erase(r->h);
         --running_solves;
         r->h->pending--;
       }
@@ -1966,10 +1977,14 @@ size_t workspace_bytes(amgeig_hierarchy_t* h, const Request* r) {
 
 size_t ws_held(const amgeig_hierarchy_t* h) { return h->ws ? h->ws->mem.held + h->ws->pw_bytes : 0; }
 
-// Bytes held by the workspaces of the hierarchies the service has used (caller holds mu).
+// Bytes held by the workspaces of the hierarchies the service has used, or
+// about to be held by the ones being made for admitted requests (caller holds mu).
 size_t Service::resident_bytes() const {
   size_t b = 0;
-  for (const amgeig_hierarchy_t* x : resident) b += ws_held(x);
+  for (amgeig_hierarchy_t* x : resident) {
+    auto it = reserved.find(x);
+    b += it != reserved.end() ? it->second : ws_held(x);
+  }
   return b;
 }
 
@@ -1997,7 +2012,7 @@ int Service::fits(const Request* r) {
     size_t held = resident_bytes() - std::min(resident_bytes(), own);
     for (size_t i = 0; i < resident.size() && held + need > mem_limit; ++i) {
       amgeig_hierarchy_t* x = resident[i];
-      if (x == h || is_busy(x)) continue;
+      if (x == h || is_busy(x) || reserved.count(x)) continue;
       std::unique_lock<std::mutex> lk(x->mu, std::try_to_lock);
       if (!lk.owns_lock() || !x->ws) continue;
       held -= std::min(held, ws_held(x));
@@ -2009,8 +2024,10 @@ int Service::fits(const Request* r) {
   }
   size_t fr = 0, tot = 0;
   cudaSetDevice(h->device);
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return kFits;
-  return need <= fr ? kFits : kWait;
+  const bool ok = cudaMemGetInfo(&fr, &tot) != cudaSuccess || need <= fr;
+  if (!ok) return kWait;
+  reserved[h] = need;  // admitted (pick takes it now): counted until its workspace exists
+  return kFits;
 }
 
 void Service::run(const std::shared_ptr<Request>& r) {

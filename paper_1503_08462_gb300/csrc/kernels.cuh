@@ -104,12 +104,17 @@ void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const float* di
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st);
 
 // ---- final float64 Rayleigh-quotient refinement (refine.cu) --------------
-// partials[block][2q]: per-block sums of u_c (A u)_c and u_c (M u)_c (float64,
-// exact operator values); q <= 128.
+// partials[block][5q]: per-block sums of u^T A u, u^T M u, |Au|^2, (Au)^T Mu and
+// |Mu|^2 per column (float64, exact operator values), over at most
+// rayleigh_blocks() blocks; q <= 128.
+int rayleigh_blocks(int q);
 void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, double* partials, int* nblocks_out,
                          cudaStream_t st);
-// theta_j = sums[j] / sums[q+j]; lam = theta sorted ascending, perm[c] = column of the c-th smallest
-void launch_rq_finish(const double* sums, int q, double* theta, double* lam, int* perm, cudaStream_t st);
+// theta_j = u^T A u / u^T M u; lam = theta sorted ascending, perm[c] = column of the c-th smallest;
+// relres_j from the expanded residual norm; flag[0] = 1 when the expansion cancelled too far to be
+// trusted (form the residual explicitly), 2 on a NaN or Inf
+void launch_rq_finish(const double* sums, int q, double* theta, double* lam, int* perm, double* relres, int* flag,
+                      cudaStream_t st);
 // dst (rows x q) = columns perm[0..q) of src (rows x ld)
 void launch_gather_cols(const double* src, int rows, int ld, const int* perm, int q, double* dst, cudaStream_t st);
 

@@ -264,7 +264,10 @@ def test_errors_are_reported():
     assert e.value.code == ae.AMGEIG_ECORRUPT
     with ae.Hierarchy(blob) as h:
         with pytest.raises(ae.AmgEigError) as e:
-            h.solve(h.sizes[-1] + 1)
+            h.solve(h.sizes[0] + 1)
+        assert e.value.code == ae.AMGEIG_EINVAL
+        with pytest.raises(ae.AmgEigError) as e:
+            h.solve(120, opt=ae.options(q_extra=9))  # q + q_extra above 128
         assert e.value.code == ae.AMGEIG_EINVAL
         with pytest.raises(ae.AmgEigError):
             h.solve(2, opt=ae.options(v_cycles=0))
