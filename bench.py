@@ -657,6 +657,16 @@ def main():
             "frac": round(gbs_l / hbm_peak, 4), "GB/s": round(gbs_l, 1), "ms": round(v["total_ms"], 3),
             "launches": v["launches"], "us_per_launch": round(v["total_ms"] / v["launches"] * 1e3, 2)}
     roof["per_level"] = {str(k): levels_tab[k] for k in sorted(levels_tab)}
+    try:
+        tune = ae.amgeig_tuning_report(h.handle)
+    except Exception:  # the report is informational
+        tune = []
+    roof["autotune"] = {"entries": len(tune), "changed_from_rule": sum(1 for e in tune if (e["G"], e["cpt"]) !=
+                                                                      (e["rule_G"], e["rule_cpt"])),
+                        "us_tuned": round(sum(e["us"] for e in tune), 2),
+                        "us_rule": round(sum(e["rule_us"] for e in tune), 2),
+                        "levels": [{k: e[k] for k in ("level", "kernel", "G", "cpt", "us", "rule_G", "rule_cpt",
+                                                       "rule_us")} for e in tune]}
     kernels = {k: {"launches": v["launches"], "kernels": v["kernels"], "ms": round(v["total_ms"], 3),
                    "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
                    "GB/s": round(v["bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1),

@@ -91,6 +91,11 @@ typedef struct {
                             captured once as CUDA graphs (per settings) and replayed; 0: every
                             kernel launched directly.  Same arithmetic, same bits.  Not used
                             while profiling is enabled or when the caller's stream is capturing */
+  int autotune;          /* mixed precisions: 1 (default) = the first solve at each block width times
+                            every lane layout of the float32 smoothing and transfer kernels on each
+                            level's operators and keeps the fastest in the hierarchy (same bits:
+                            the layout does not change the order of any sum); 0 = no tuning now
+                            (layouts tuned by earlier solves stay in use) */
 } amgeig_options;
 
 #define AMGEIG_SMOOTHER_L1_JACOBI 0
@@ -254,6 +259,13 @@ int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_o
 int amgeig_sym_eigh_noalloc(int n, int nwant, const double* H, double* evals, double* evecs, void* stream);
 
 /* ---- measurement ---------------------------------------------------------- */
+
+/* The launch-shape tuner's choices on h so far, as JSON text: a list of
+ * {"level", "kernel" (smooth | restrict | prolong), "w4" (block width in float4
+ * columns), "G" (lanes per row), "cpt" (float4 columns per lane), "us" (its
+ * time), "rule_G", "rule_cpt", "rule_us" (the fixed rule's shape and time)}.
+ * Errors: EINVAL (NULL argument, buffer too small; the text is truncated). */
+int amgeig_tuning_report(amgeig_hierarchy h, char* buf, size_t len);
 
 /* Per kernel class totals recorded while profiling is enabled. */
 typedef struct {

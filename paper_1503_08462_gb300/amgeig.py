@@ -42,7 +42,8 @@ class amgeig_options(ctypes.Structure):
     _fields_ = [("max_corrections", ctypes.c_int), ("v_cycles", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("q_extra", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fixed_corrections", ctypes.c_int), ("coarse_modes", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("n1", ctypes.c_int), ("refine", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("n1", ctypes.c_int), ("refine", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class amgeig_prof_entry(ctypes.Structure):
@@ -60,7 +61,7 @@ EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_load_hier
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
             "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_apply_defect", "amgeig_profile_enable",
             "amgeig_profile_read", "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc",
-            "amgeig_service_set_memory_limit", "amgeig_service_memory"]
+            "amgeig_service_set_memory_limit", "amgeig_service_memory", "amgeig_tuning_report"]
 
 
 def library_path() -> str:
@@ -98,13 +99,14 @@ def lib():
         L.amgeig_sym_eigh_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
         L.amgeig_sym_eigh_noalloc.restype = i32
         L.amgeig_service_set_memory_limit.argtypes = [ctypes.c_uint64]
+        L.amgeig_tuning_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         L.amgeig_service_memory.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
         L.amgeig_kernel_launches.argtypes = []
         L.amgeig_kernel_launches.restype = ctypes.c_uint64
         for name in ("amgeig_load_hierarchy", "amgeig_load_hierarchy_modes", "amgeig_free_hierarchy", "amgeig_hierarchy_info", "amgeig_solve",
                      "amgeig_submit", "amgeig_poll", "amgeig_sym_eigh", "amgeig_apply_vcycle",
                      "amgeig_apply_defect", "amgeig_profile_enable", "amgeig_profile_read",
-                     "amgeig_service_set_memory_limit", "amgeig_service_memory"):
+                     "amgeig_service_set_memory_limit", "amgeig_service_memory", "amgeig_tuning_report"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -193,6 +195,15 @@ def amgeig_poll(request_id: int, eigvals=None, eigvecs=None, info: Optional[amge
 
 def amgeig_service_set_memory_limit(nbytes: int) -> None:
     _check(lib().amgeig_service_set_memory_limit(nbytes), "amgeig_service_set_memory_limit")
+
+
+def amgeig_tuning_report(h) -> list:
+    """The launch-shape tuner's choices on hierarchy h (parsed JSON)."""
+    import json
+
+    buf = ctypes.create_string_buffer(1 << 20)
+    _check(lib().amgeig_tuning_report(h, buf, len(buf)), "amgeig_tuning_report")
+    return json.loads(buf.value.decode())
 
 
 def amgeig_service_memory() -> Tuple[int, int]:

@@ -425,6 +425,9 @@ struct amgeig_hierarchy_t {
     double *A = nullptr, *M = nullptr, *Z = nullptr, *theta = nullptr;
     PencilWork* pw = nullptr;
   } init;
+  // float32 V-cycle widths (float4 columns) whose launch shapes are tuned, and the tuner's log
+  bool tuned_w4[33] = {};
+  std::string tune_log;
   cudaStream_t stream = nullptr;
   std::atomic<int> pending{0};
   ~amgeig_hierarchy_t();
@@ -939,7 +942,7 @@ int check_options(const amgeig_options& o) {
       o.fixed_corrections < 0 || o.coarse_modes < 0 ||
       (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
       (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL) || o.n1 < -1 ||
-      (o.refine != 0 && o.refine != 1) || (o.graphs != 0 && o.graphs != 1))
+      (o.refine != 0 && o.refine != 1) || (o.graphs != 0 && o.graphs != 1) || (o.autotune != 0 && o.autotune != 1))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -1025,6 +1028,41 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
   CK(cudaGraphLaunch(it->second.exec, st));
   add_launches(it->second.kernels);
   set_roles(w, it->second.post);
+  return AMGEIG_OK;
+}
+
+// Launch shapes of the float32 V-cycle kernels for this solve's width, tuned on
+// its first mixed solve at that width (smoothing on every A_l, restriction R_l
+// and prolongation P_l): every lane layout is timed on the level's own
+// operator and the fastest is kept in the hierarchy.  The layout does not
+// change the arithmetic (each column's sum runs over the row in the same
+// order), so results keep their bits.  Before any capture; under the lock.
+int ensure_tuned(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
+  const int w4 = w->ld32 / 4;
+  if (w4 < 1 || w4 > 32 || h->tuned_w4[w4]) return AMGEIG_OK;
+  const int n = h->nlev;
+  for (int l = 0; l + 1 < n; ++l) {
+    const size_t cl = static_cast<size_t>(h->sizes[l]) * w->ld32, cn = static_cast<size_t>(h->sizes[l + 1]) * w->ld32;
+    CK(cudaMemsetAsync(w->X32[l], 0, sizeof(float) * cl, st));
+    CK(cudaMemsetAsync(w->B32[l], 0, sizeof(float) * cl, st));
+    CK(cudaMemsetAsync(w->X32[l + 1], 0, sizeof(float) * cn, st));
+    const TuneResult a = autotune_f4(h->A[l], 0, w4, h->dinv32[l], w->X32[l], w->B32[l], w->T32[l], st);
+    const TuneResult r = autotune_f4(h->R[l], 1, w4, nullptr, w->T32[l], nullptr, w->B32[l + 1], st);
+    const TuneResult p = autotune_f4(h->P[l], 1, w4, nullptr, w->X32[l + 1], nullptr, w->T32[l], st);
+    char line[512];
+    const TuneResult* tr[3] = {&a, &r, &p};
+    const char* nm[3] = {"smooth", "restrict", "prolong"};
+    for (int i = 0; i < 3; ++i) {
+      std::snprintf(line, sizeof(line),
+                    "%s{\"level\": %d, \"kernel\": \"%s\", \"w4\": %d, \"G\": %d, \"cpt\": %d, \"us\": %.2f, "
+                    "\"rule_G\": %d, \"rule_cpt\": %d, \"rule_us\": %.2f}",
+                    h->tune_log.empty() ? "" : ", ", l, nm[i], w4, tr[i]->G, tr[i]->cpt, tr[i]->us, tr[i]->rule_G,
+                    tr[i]->rule_cpt, tr[i]->rule_us);
+      h->tune_log += line;
+    }
+  }
+  CK(cudaGetLastError());
+  h->tuned_w4[w4] = true;
   return AMGEIG_OK;
 }
 
@@ -1130,6 +1168,10 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   w->bf16 = o.precision == AMGEIG_MIXED_BF16;
   if (w->bf16) {
     rc = ensure_bf16(h, st);
+    if (rc) return rc;
+  }
+  if (o.precision != AMGEIG_FP64 && o.autotune) {
+    rc = ensure_tuned(h, w, st);
     if (rc) return rc;
   }
   {
@@ -1445,6 +1487,7 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->n1 = -1;
   opt->refine = 1;
   opt->graphs = 1;
+  opt->autotune = 1;
 }
 
 const char* amgeig_strerror(int code) {
@@ -1917,6 +1960,15 @@ int amgeig_submit(amgeig_hierarchy h, int q, double tol, const amgeig_options* o
   }
   s.cv.notify_one();
   *request_id = r->id;
+  return AMGEIG_OK;
+}
+
+int amgeig_tuning_report(amgeig_hierarchy h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return fail(AMGEIG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  const std::string txt = "[" + h->tune_log + "]";
+  std::snprintf(buf, len, "%s", txt.c_str());
+  if (txt.size() + 1 > len) return fail(AMGEIG_EINVAL, "buffer too small for the tuning report");
   return AMGEIG_OK;
 }
 

@@ -20,7 +20,23 @@ struct DevCsr {
   float2* d2 = nullptr;   // v64 as float-float pairs (hi, lo)
   float2* m2 = nullptr;   // m64 as float-float pairs
   __nv_bfloat16* vbf = nullptr;  // v64 rounded to bfloat16 (the V-cycle's operators, AMGEIG_MIXED_BF16)
+  // launch shape of the float32 V-cycle kernels on this operator, per block width in float4
+  // columns w4 <= 32, chosen by the autotuner: (log2 G) * 4 + cpt; 0 = not tuned (the rule applies)
+  unsigned char tuned[33] = {};
 };
+
+// ---- launch-shape autotuning of the float32 V-cycle kernels (spmm.cu) -------
+// Times every lane layout (G lanes per row, cpt float4 columns per lane) of the
+// smoothing sweep on A (kind 0: x_out = x + D^-1 (b - A x)) or of the transfer
+// SpMM on S (kind 1: Y = S X) at width 4 * w4, and records the fastest in the
+// operator's `tuned` table.  x / b / X and out / Y are device scratch of the
+// operator's rows (or columns) x 4 w4 floats; their contents are overwritten.
+struct TuneResult {
+  int G = 0, cpt = 0, rule_G = 0, rule_cpt = 0;
+  float us = 0.f, rule_us = 0.f;
+};
+TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const float* x, const float* b, float* out,
+                       cudaStream_t st);
 
 // ---- sparse kernels (spmm.cu) --------------------------------------------
 // All blocks of vectors are row-major [rows][width].

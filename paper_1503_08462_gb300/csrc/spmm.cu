@@ -310,6 +310,15 @@ F4Geo f4_geo(int w4, long long rows) {
   return F4Geo{G, cpt};
 }
 
+// the operator's tuned shape at this width, else the rule
+F4Geo geo_of(const DevCsr& S, int w4) {
+  if (w4 >= 1 && w4 <= 32 && S.tuned[w4]) {
+    const int v = S.tuned[w4];
+    return F4Geo{1 << (v >> 2), v & 3};
+  }
+  return f4_geo(w4, S.rows);
+}
+
 __device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
   acc.x = fmaf(s, x.x, acc.x);
   acc.y = fmaf(s, x.y, acc.y);
@@ -439,8 +448,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_spmm_f4(int n, const int* __res
 template <int MODE>
 void smooth_f4(const DevCsr& A, const float* dinv, const float* b, const float* x, int w4, float* out1, float* out2,
                const double* U, double* V, int qv, const float2* U2, float2* V2, const float* xadd,
-               cudaStream_t st, bool bf16 = false) {
-  const F4Geo g = f4_geo(w4, A.rows);
+               cudaStream_t st, bool bf16 = false, const F4Geo* force = nullptr) {
+  const F4Geo g = force ? *force : geo_of(A, w4);
   const int blocks = ceil_div(A.rows, kThreads / g.G);
 #define AMGEIG_SMOOTH_T(C, TV, VALS)                                                                         \
   k_smooth_f4<MODE, C, TV><<<blocks, kThreads, 0, st>>>(                                                       \
@@ -754,6 +763,9 @@ void launch_spmm_f64(const DevCsr& S, const double* X, int width, double* Y, boo
                      int cls) {
   spmm_impl<double>(S, S.v64, X, width, Y, accumulate, st, cls);
 }
+static void spmm_f4_geo(const DevCsr& S, const float* X, int w4, float* Y, bool accumulate, cudaStream_t st,
+                        bool bf16, F4Geo g);
+
 void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool accumulate, cudaStream_t st,
                      bool bf16) {
   if (width % 4 != 0 || S.rows == 0) {
@@ -761,7 +773,13 @@ void launch_spmm_f32(const DevCsr& S, const float* X, int width, float* Y, bool 
     return;
   }
   const int w4 = width / 4;
-  const F4Geo g = f4_geo(w4, S.rows);
+  const F4Geo g = geo_of(S, w4);
+  spmm_f4_geo(S, X, w4, Y, accumulate, st, bf16, g);
+}
+
+static void spmm_f4_geo(const DevCsr& S, const float* X, int w4, float* Y, bool accumulate, cudaStream_t st,
+                        bool bf16, F4Geo g) {
+  const int width = 4 * w4;
   const int blocks = ceil_div(S.rows, kThreads / g.G);
   ProfScope ps(st, P_TRANSFER,
                4.0 * (S.rows + 1) + 8.0 * S.nnz + 4.0 * S.cols * width + 4.0 * S.rows * width * (accumulate ? 2 : 1),
@@ -1027,6 +1045,62 @@ void launch_composite_rows(const DevCsr& P, const int* nrp, const int* nci, cons
   if (blocks > 8 * kNumSms) blocks = 8 * kNumSms;
   ProfScope ps(st, P_OTHER, 4.0 * P.rows + 12.0 * P.nnz, 0.0);
   k_pc_rows<<<blocks, 32 * wpb, sm, st>>>(P.rows, P.rp, P.ci, P.v64, nrp, nci, nv, dn, out_rp, counts, out_ci, out_v);
+}
+
+TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const float* x, const float* b, float* out,
+                       cudaStream_t st) {
+  TuneResult r;
+  const F4Geo rule = f4_geo(w4, S.rows);
+  r.rule_G = rule.G;
+  r.rule_cpt = rule.cpt;
+  if (w4 < 1 || w4 > 32 || S.rows == 0) return r;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return r;
+  }
+  auto run = [&](F4Geo g) {
+    if (kind == 0)
+      smooth_f4<1>(S, dinv, b, x, w4, out, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, st, false, &g);
+    else
+      spmm_f4_geo(S, x, w4, out, false, st, false, g);
+  };
+  auto time_us = [&](F4Geo g) -> float {
+    ProfScope ps(st, P_OTHER, 0.0, 0.0, 4);
+    run(g);  // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      run(g);
+      cudaEventRecord(e1, st);
+      float ms = 1e30f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        best = best < ms ? best : ms;
+    }
+    return best * 1000.f;
+  };
+  // every power-of-two lane count whose column share per lane is 1..3 float4s
+  float best = 1e30f;
+  for (int G = 1, lg = 0; G <= 32; G <<= 1, ++lg) {
+    const int cpt = (w4 + G - 1) / G;
+    if (cpt > 3 || (G > 1 && G / 2 >= w4)) continue;
+    const float us = time_us(F4Geo{G, cpt});
+    if (us < best) {
+      best = us;
+      r.G = G;
+      r.cpt = cpt;
+    }
+  }
+  r.us = best;
+  r.rule_us = time_us(rule);
+  if (r.G > 0 && cudaGetLastError() == cudaSuccess) {
+    int lg = 0;
+    while ((1 << lg) < r.G) ++lg;
+    S.tuned[w4] = static_cast<unsigned char>(lg * 4 + r.cpt);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
 }
 
 }  // namespace amgeig
