@@ -416,7 +416,7 @@ def main():
     ap.add_argument("--workload", default="lshape_h512_q20", choices=sorted(WORKLOADS) + ["stream"],
                     help="one problem solved per step, or 'stream': Poisson-arriving requests through "
                          "amgeig_submit / amgeig_poll over a pool of problems (throughput and p50/p99 latency)")
-    ap.add_argument("--requests", type=int, default=200, help="stream: requests in the timed stream")
+    ap.add_argument("--requests", type=int, default=2000, help="stream: requests in the timed stream")
     ap.add_argument("--pool", type=int, default=6, help="stream: distinct problems the requests draw from")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "bf16", "fp64"],
                     help="mixed: float32 V-cycle; bf16: its operators stored in bfloat16; fp64: every step in float64")

@@ -82,11 +82,16 @@ typedef struct {
                             otherwise a level with q + q_extra <= N_n1 <= 2048.  The initial
                             eigenproblem (A_n1, M_n1) is solved densely on the GPU; the pencils
                             of every correction still use the coarsest space V_n */
-  int refine;            /* mixed precisions only: 1 (default) = after the last correction, each
-                            vector's Rayleigh quotient u^T A u / u^T M u and relative residual are
-                            recomputed in float64 with the exact operator values; those are the
-                            returned eigenvalues (ascending, vectors permuted alike) and residuals.
-                            0 = return the float-float Ritz values and residuals */
+  int refine;            /* 0 (default): the eigenvalues are the last Rayleigh-Ritz step's values.
+                            1: after the last correction each vector's Rayleigh quotient
+                            u^T A u / u^T M u and relative residual are recomputed in float64 with
+                            the exact operator values (for the mixed path, whose Ritz data use A
+                            and M rounded to 48 bits); 2: the same with the quotient's sums
+                            accumulated in compensated float64 (as if in twice the precision),
+                            so that the returned eigenvalues are those of the returned vectors
+                            to a few units of float64 rounding, where plain float64 sums lose
+                            ~u * lambda_max / lambda_j to cancellation.  With 1 or 2 the values are
+                            sorted ascending and the vectors permuted alike */
   int graphs;            /* 1 (default): the nested phase and each finest-level correction are
                             captured once as CUDA graphs (per settings) and replayed; 0: every
                             kernel launched directly.  Same arithmetic, same bits.  Not used
@@ -96,6 +101,11 @@ typedef struct {
                             level's operators and keeps the fastest in the hierarchy (same bits:
                             the layout does not change the order of any sum); 0 = no tuning now
                             (layouts tuned by earlier solves stay in use) */
+  int batch;             /* amgeig_submit only: 1 (default) = the request may share one solve with
+                            other queued requests on the same hierarchy whose options agree but for
+                            q, q_extra, tol and max_corrections (the shared solve takes the widest
+                            and the tightest of each; every request receives its own leading q
+                            pairs and its own residual test); 0 = always solved on its own */
 } amgeig_options;
 
 #define AMGEIG_SMOOTHER_L1_JACOBI 0
@@ -177,7 +187,9 @@ int amgeig_solve(amgeig_hierarchy h, int q, double tol, const amgeig_options* op
 /* Serving: queue a solve on h and return at once with *request_id.  The options
  * are copied.  Four library threads take requests in arrival order, skipping
  * one whose hierarchy is already solving: requests on different hierarchies run
- * at the same time on their hierarchies' streams.  Each hierarchy keeps its
+ * at the same time on their hierarchies' streams, and queued requests on the
+ * taken request's hierarchy join its solve (options.batch) when their width
+ * fits its workspace.  Each hierarchy keeps its
  * iterate workspace resident (sized for the widest q + q_extra it has served).
  * A request whose workspace does not fit in free device memory waits until a
  * running request ends (ENOMEM is reported through amgeig_poll if it cannot fit

@@ -453,6 +453,7 @@ struct SolveWork {
   int* flags = nullptr;
   int* perm = nullptr;     // output column c is column perm[c] of the iterate (after the refinement)
   bool permuted = false;   // perm applies to the current solve's outputs
+  double* refined = nullptr;  // the refined iterate in float64 (U or V)
   int* nfallback = nullptr;  // corrections that needed the dense eigensolver
   PencilWork* pw = nullptr;
   size_t pw_bytes = 0;  // device bytes of pw
@@ -525,7 +526,7 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   }
   const int blocks_max = ceil_div(N0, 8) + 1;  // defect launches use >= 8 rows per block
   CK(m.alloc(&w->partials, std::max(static_cast<size_t>(blocks_max) * 2 * qt,
-                                     static_cast<size_t>(rayleigh_blocks(qt)) * 5 * qt)));
+                                     static_cast<size_t>(rayleigh_blocks(qt)) * 7 * qt)));
   CK(m.alloc(&w->sums, 5 * qt));
   CK(m.alloc(&w->relres, qt));
   CK(m.alloc(&w->lam, qt));
@@ -942,7 +943,8 @@ int check_options(const amgeig_options& o) {
       o.fixed_corrections < 0 || o.coarse_modes < 0 ||
       (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
       (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL) || o.n1 < -1 ||
-      (o.refine != 0 && o.refine != 1) || (o.graphs != 0 && o.graphs != 1) || (o.autotune != 0 && o.autotune != 1))
+      (o.refine < 0 || o.refine > 2) || (o.graphs != 0 && o.graphs != 1) || (o.autotune != 0 && o.autotune != 1) ||
+      (o.batch != 0 && o.batch != 1))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -1114,13 +1116,15 @@ int ensure_initial(amgeig_hierarchy_t* h, int l, int count, cudaStream_t st) {
 // (V receives the iterate in float64, W the residual block); lam receives the
 // quotients in ascending order, perm the matching columns, relres the residual
 // of each column (unpermuted).
-int refine_fp64(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
+int refine_fp64(amgeig_hierarchy_t* h, SolveWork* w, bool compensated, bool fp64_path, cudaStream_t st) {
   const int qt = w->qt;
   const long long cnt = h->sizes[0] * static_cast<long long>(qt);
-  launch_df_to_f64(as_df(w->U), cnt, w->V, st);
-  int nb = 0;
-  launch_rayleigh_f64(h->A[0], w->V, qt, w->partials, &nb, st);
-  launch_sum_partials(w->partials, nb, 5 * qt, w->sums, st);
+  double* X = w->U;
+  if (!fp64_path) {
+    launch_df_to_f64(as_df(w->U), cnt, w->V, st);
+    X = w->V;
+  }
+  launch_rayleigh_f64(h->A[0], X, qt, compensated, w->partials, w->sums, st);
   launch_rq_finish(w->sums, qt, w->mu, w->lam, w->perm, w->relres, w->flags, st);
   int redo = 0;
   CK(cudaMemcpyAsync(&redo, w->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1128,12 +1132,14 @@ int refine_fp64(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
   if (redo == 2) return fail(AMGEIG_ENAN, "NaN or Inf in the refined Rayleigh quotients");
   if (redo) {
     // small residuals: form them explicitly with the refined quotients
-    launch_defect_f64(h->A[0], w->V, qt, w->mu, w->W, w->partials, &nb, st);
+    int nb = 0;
+    launch_defect_f64(h->A[0], X, qt, w->mu, w->W, w->partials, &nb, st);
     launch_sum_partials(w->partials, nb, 2 * qt, w->sums, st);
     CK(cudaMemsetAsync(w->flags, 0, sizeof(int), st));
     launch_relres(w->sums, w->mu, qt, w->relres, w->flags, st);
   }
   CK(cudaGetLastError());
+  w->refined = X;
   w->permuted = true;
   return AMGEIG_OK;
 }
@@ -1272,11 +1278,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
     for (int j = 0; j < q; ++j) mx = std::max(mx, relres_host[j]);
     converged = mx <= tol;
   }
-  if (o.precision != AMGEIG_FP64 && o.refine) {
-    // the returned values and residuals: float64 Rayleigh quotients of the
-    // final vectors; the stopping decision above stands unless the float64
-    // residuals contradict it
-    rc = refine_fp64(h, w, st);
+  if (o.refine) {
+    // the returned values and residuals: float64 (or compensated float64)
+    // Rayleigh quotients of the final vectors; the stopping decision above
+    // stands unless the float64 residuals contradict it
+    rc = refine_fp64(h, w, o.refine == 2, o.precision == AMGEIG_FP64, st);
     if (rc) return rc;
     std::vector<int> perm(qt);
     std::vector<double> rr(qt);
@@ -1317,10 +1323,11 @@ int write_outputs(amgeig_hierarchy_t* h, int q, double* eigvals, double* eigvecs
     const double* src = w->U;
     int ld = qt;
     if (w->permuted) {
-      // the refinement left the iterate in float64 in V: its columns perm[0..q)
-      // gathered into U (free after the solve)
-      launch_gather_cols(w->V, N0, qt, w->perm, q, w->U, st);
-      src = w->U;
+      // the refined float64 iterate's columns perm[0..q) gathered into the other
+      // of U and V (both free after the solve)
+      double* g = w->refined == w->U ? w->V : w->U;
+      launch_gather_cols(w->refined, N0, qt, w->perm, q, g, st);
+      src = g;
       ld = q;
     } else if (w->precision != AMGEIG_FP64) {
       // float-float iterate -> float64 (V is free after the solve)
@@ -1359,7 +1366,20 @@ struct Request {
   int status = AMGEIG_OK;
   std::vector<double> vals, vecs;
   amgeig_info info{};
+  // queued requests on the same hierarchy that share this request's solve
+  std::vector<std::shared_ptr<Request>> riders;
 };
+
+// Two requests can share one solve when everything but the wanted count, the
+// buffer and the tolerance agrees (the shared solve takes the widest of each
+// and the tightest tolerance).
+bool can_share(const Request& a, const Request& b) {
+  const amgeig_options &x = a.opt, &y = b.opt;
+  return a.h == b.h && x.batch && y.batch && x.fixed_corrections == 0 && y.fixed_corrections == 0 &&
+         x.precision == y.precision && x.v_cycles == y.v_cycles && x.pre_sweeps == y.pre_sweeps &&
+         x.post_sweeps == y.post_sweeps && x.coarse_modes == y.coarse_modes && x.smoother == y.smoother &&
+         x.n1 == y.n1 && x.refine == y.refine && x.graphs == y.graphs && x.autotune == y.autotune;
+}
 
 // Continuous batching over hierarchies: kWorkers library threads take queued
 // requests in arrival order, skipping one whose hierarchy is busy (a hierarchy
@@ -1420,9 +1440,35 @@ struct Service {
       }
       queue.erase(it);
       touch(r->h);
+      gather_riders(r);
       return r;
     }
     return nullptr;
+  }
+
+  // Queued requests on r's hierarchy that can share its solve ride along, as
+  // long as the shared width (the widest q + q_extra of the group) stays within
+  // r's workspace, or the workspace admitted for r (caller holds mu).
+  void gather_riders(const std::shared_ptr<Request>& r) {
+    r->riders.clear();
+    if (!r->opt.batch) return;
+    int width = r->q + r->opt.q_extra;
+    {
+      std::unique_lock<std::mutex> lk(r->h->mu, std::try_to_lock);
+      if (lk.owns_lock() && r->h->ws) width = std::max(width, r->h->ws->qcap);
+    }
+    int qm = r->q, qe = r->opt.q_extra;
+    for (auto it = queue.begin(); it != queue.end();) {
+      const std::shared_ptr<Request>& x = *it;
+      if (can_share(*r, *x) && std::max(qm, x->q) + std::max(qe, x->opt.q_extra) <= width) {
+        qm = std::max(qm, x->q);
+        qe = std::max(qe, x->opt.q_extra);
+        r->riders.push_back(x);
+        it = queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
   }
 
   static constexpr int kFits = 0, kWait = 1, kRefuse = 2;
@@ -1453,7 +1499,8 @@ struct Service {
         busy.erase(std::find(busy.begin(), busy.end(), r->h));
         reserved.erase(r->h);
         --running_solves;
-        r->h->pending--;
+        r->h->pending -= 1 + static_cast<int>(r->riders.size());
+        r->riders.clear();
       }
       cv.notify_all();
     }
@@ -1485,9 +1532,10 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->coarse_modes = 0;
   opt->smoother = AMGEIG_SMOOTHER_L1_JACOBI;
   opt->n1 = -1;
-  opt->refine = 1;
+  opt->refine = 0;
   opt->graphs = 1;
   opt->autotune = 1;
+  opt->batch = 1;
 }
 
 const char* amgeig_strerror(int code) {
@@ -2084,17 +2132,74 @@ int Service::fits(const Request* r) {
 
 void Service::run(const std::shared_ptr<Request>& r) {
   amgeig_hierarchy_t* h = r->h;
-  r->vals.assign(r->q, 0.0);
-  r->vecs.assign(static_cast<size_t>(h->sizes[0]) * r->q, 0.0);
-  int status = amgeig_solve(h, r->q, r->tol, &r->opt, r->vals.data(), r->vecs.data(), 0, &r->info, nullptr);
-  if (status != AMGEIG_OK && status != AMGEIG_ENOCONV) {
-    r->vals.clear();
-    r->vecs.clear();
+  if (r->riders.empty()) {
+    r->vals.assign(r->q, 0.0);
+    r->vecs.assign(static_cast<size_t>(h->sizes[0]) * r->q, 0.0);
+    int status = amgeig_solve(h, r->q, r->tol, &r->opt, r->vals.data(), r->vecs.data(), 0, &r->info, nullptr);
+    if (status != AMGEIG_OK && status != AMGEIG_ENOCONV) {
+      r->vals.clear();
+      r->vecs.clear();
+    }
+    r->info.status = status;
+    std::lock_guard<std::mutex> lk(mu);
+    r->status = status;
+    r->done = true;
+    return;
   }
-  r->info.status = status;
+  // One solve for the group: the widest wanted count and buffer, the tightest
+  // tolerance, the largest correction limit.  Every member wants the lowest
+  // eigenpairs of the same pencil, so each takes the leading columns it asked
+  // for, with its own residual test over them.
+  std::vector<Request*> grp = {r.get()};
+  for (auto& x : r->riders) grp.push_back(x.get());
+  int qm = 0, qe = 0, mc = 0;
+  double tol = r->tol;
+  for (Request* x : grp) {
+    qm = std::max(qm, x->q);
+    qe = std::max(qe, x->opt.q_extra);
+    mc = std::max(mc, x->opt.max_corrections);
+    tol = std::min(tol, x->tol);
+  }
+  amgeig_options o = r->opt;
+  o.q_extra = qe;
+  o.max_corrections = mc;
+  const int64_t N0 = h->sizes[0];
+  std::vector<double> vals(qm), vecs(static_cast<size_t>(N0) * qm), rr;
+  amgeig_info info{};
+  int status;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    g_last_error.clear();
+    cudaSetDevice(h->device);
+    status = solve_impl(h, qm, tol, o, &info, rr, h->stream);
+    if (status == AMGEIG_OK || status == AMGEIG_ENOCONV) {
+      const int rc2 = write_outputs(h, qm, vals.data(), vecs.data(), 0, h->stream);
+      if (rc2) status = rc2;
+    }
+  }
+  for (Request* x : grp) {
+    x->info = info;
+    if (status == AMGEIG_OK || status == AMGEIG_ENOCONV) {
+      x->vals.assign(vals.begin(), vals.begin() + x->q);
+      x->vecs.resize(static_cast<size_t>(N0) * x->q);
+      for (int64_t i = 0; i < N0; ++i)
+        std::memcpy(x->vecs.data() + i * x->q, vecs.data() + i * qm, sizeof(double) * x->q);
+      double mx = 0.0;
+      for (int j = 0; j < x->q && j < static_cast<int>(rr.size()); ++j) mx = std::max(mx, rr[j]);
+      x->info.max_relres = mx;
+      x->info.converged = mx <= x->tol ? 1 : 0;
+      x->info.status = x->info.converged ? AMGEIG_OK : AMGEIG_ENOCONV;
+    } else {
+      x->vals.clear();
+      x->vecs.clear();
+      x->info.status = status;
+    }
+  }
   std::lock_guard<std::mutex> lk(mu);
-  r->status = status;
-  r->done = true;
+  for (Request* x : grp) {
+    x->status = x->info.status;
+    x->done = true;
+  }
 }
 
 }  // namespace

@@ -120,12 +120,13 @@ void launch_gs_colour(int cnt, const int* rows, const DevCsr& A, const float* di
 void launch_convert_f32_to_f64(const float* x, long long count, double* y, cudaStream_t st);
 
 // ---- final float64 Rayleigh-quotient refinement (refine.cu) --------------
-// partials[block][5q]: per-block sums of u^T A u, u^T M u, |Au|^2, (Au)^T Mu and
-// |Mu|^2 per column (float64, exact operator values), over at most
-// rayleigh_blocks() blocks; q <= 128.
+// sums[5q]: per column u^T A u, u^T M u, |Au|^2, (Au)^T Mu and |Mu|^2 (float64,
+// exact operator values; `compensated`: the first two accumulated in
+// compensated arithmetic, as if in twice the working precision), through
+// per-block partials (scratch of rayleigh_blocks() x 7q doubles); q <= 128.
 int rayleigh_blocks(int q);
-void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, double* partials, int* nblocks_out,
-                         cudaStream_t st);
+void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, bool compensated, double* partials,
+                         double* sums, cudaStream_t st);
 // theta_j = u^T A u / u^T M u; lam = theta sorted ascending, perm[c] = column of the c-th smallest;
 // relres_j from the expanded residual norm; flag[0] = 1 when the expansion cancelled too far to be
 // trusted (form the residual explicitly), 2 on a NaN or Inf

@@ -23,29 +23,58 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Error-free float64 transformations for the compensated sums: Knuth's TwoSum
+// and the FMA form of Dekker's TwoProduct; a running sum carries its rounding
+// errors in a second word, as in Ogita, Rump and Oishi's Dot2 (2005, "Accurate
+// sum and dot product"), so the result is as if accumulated in twice the
+// working precision.
+struct dd {
+  double hi, lo;
+};
+// (explicitly rounded operations: no contraction into FMAs may change them)
+__device__ __forceinline__ void dd_add(dd& s, double x) {
+  const double t = __dadd_rn(s.hi, x);
+  const double z = __dsub_rn(t, s.hi);
+  s.lo = __dadd_rn(s.lo, __dadd_rn(__dsub_rn(s.hi, __dsub_rn(t, z)), __dsub_rn(x, z)));
+  s.hi = t;
+}
+__device__ __forceinline__ void dd_fma(dd& s, double a, double b) {
+  const double p = __dmul_rn(a, b);
+  const double e = fma(a, b, -p);
+  dd_add(s, p);
+  s.lo = __dadd_rn(s.lo, e);
+}
+
 // Per block and column, over the rows the block visits (a fixed grid striding
 // over the rows, so the sums are taken in a fixed order): u_c (A u)_c,
 // u_c (M u)_c, (A u)_c^2, (A u)_c (M u)_c and (M u)_c^2, in float64 with the
-// exact operator values.  A group of G threads owns one row at a time; thread t
-// of the group holds columns t, t+G, ...
-template <int CPT>
+// exact operator values.  COMP: the first two (the Rayleigh quotient's
+// numerator and denominator) in compensated arithmetic, row sums and the sum
+// over rows alike, written as (hi, lo) pairs: partials[block][7q] = hi0, lo0,
+// hi1, lo1, s2, s3, s4 per column; otherwise partials[block][5q].  A group of
+// G threads owns one row at a time; thread t of the group holds columns t,
+// t+G, ...
+template <int CPT, bool COMP>
 __global__ void __launch_bounds__(kThreads) k_rayleigh(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                        const double* __restrict__ a, const double* __restrict__ m,
                                                        const double* __restrict__ U, int q, int G,
                                                        double* __restrict__ partials) {
-  extern __shared__ double sred[];  // [rows_per_block][5 * G * CPT]
+  extern __shared__ double sred[];  // [rows_per_block][NS * G * CPT]
+  constexpr int NS = COMP ? 7 : 5;
   const int rpb = blockDim.x / G;
   const int g = threadIdx.x / G;
   const int lane = threadIdx.x % G;
-  double s[5][CPT];
+  dd s01[2][CPT];
+  double s[3][CPT];
 #pragma unroll
-  for (int k = 0; k < 5; ++k)
-#pragma unroll
-    for (int t = 0; t < CPT; ++t) s[k][t] = 0.0;
+  for (int t = 0; t < CPT; ++t) {
+    s01[0][t] = s01[1][t] = dd{0.0, 0.0};
+    s[0][t] = s[1][t] = s[2][t] = 0.0;
+  }
   for (int row = blockIdx.x * rpb + g; row < n; row += gridDim.x * rpb) {
-    double aa[CPT], mm[CPT];
+    dd aa[CPT], mm[CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = 0.0;
+    for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = dd{0.0, 0.0};
     const int p0 = rp[row], p1 = rp[row + 1];
     for (int p = p0; p < p1; ++p) {
       const int j = ci[p];
@@ -56,8 +85,13 @@ __global__ void __launch_bounds__(kThreads) k_rayleigh(int n, const int* __restr
         const int c = lane + t * G;
         if (c < q) {
           const double u = uj[c];
-          aa[t] = fma(av, u, aa[t]);
-          mm[t] = fma(mv, u, mm[t]);
+          if (COMP) {
+            dd_fma(aa[t], av, u);
+            dd_fma(mm[t], mv, u);
+          } else {
+            aa[t].hi = fma(av, u, aa[t].hi);
+            mm[t].hi = fma(mv, u, mm[t].hi);
+          }
         }
       }
     }
@@ -65,24 +99,82 @@ __global__ void __launch_bounds__(kThreads) k_rayleigh(int n, const int* __restr
     for (int t = 0; t < CPT; ++t) {
       const int c = lane + t * G;
       const double ui = c < q ? U[static_cast<long long>(row) * q + c] : 0.0;
-      s[0][t] = fma(ui, aa[t], s[0][t]);
-      s[1][t] = fma(ui, mm[t], s[1][t]);
-      s[2][t] = fma(aa[t], aa[t], s[2][t]);
-      s[3][t] = fma(aa[t], mm[t], s[3][t]);
-      s[4][t] = fma(mm[t], mm[t], s[4][t]);
+      if (COMP) {
+        dd_fma(s01[0][t], ui, aa[t].hi);
+        s01[0][t].lo = fma(ui, aa[t].lo, s01[0][t].lo);
+        dd_fma(s01[1][t], ui, mm[t].hi);
+        s01[1][t].lo = fma(ui, mm[t].lo, s01[1][t].lo);
+      } else {
+        s01[0][t].hi = fma(ui, aa[t].hi, s01[0][t].hi);
+        s01[1][t].hi = fma(ui, mm[t].hi, s01[1][t].hi);
+      }
+      const double ah = aa[t].hi + aa[t].lo, mh = mm[t].hi + mm[t].lo;
+      s[0][t] = fma(ah, ah, s[0][t]);
+      s[1][t] = fma(ah, mh, s[1][t]);
+      s[2][t] = fma(mh, mh, s[2][t]);
     }
   }
   const int W = G * CPT;
 #pragma unroll
-  for (int k = 0; k < 5; ++k)
-#pragma unroll
-    for (int t = 0; t < CPT; ++t) sred[(g * 5 + k) * W + lane + t * G] = s[k][t];
+  for (int t = 0; t < CPT; ++t) {
+    const int col = lane + t * G;
+    double* r = sred + g * NS * W + col;
+    if (COMP) {
+      r[0 * W] = s01[0][t].hi;
+      r[1 * W] = s01[0][t].lo;
+      r[2 * W] = s01[1][t].hi;
+      r[3 * W] = s01[1][t].lo;
+      r[4 * W] = s[0][t];
+      r[5 * W] = s[1][t];
+      r[6 * W] = s[2][t];
+    } else {
+      r[0 * W] = s01[0][t].hi;
+      r[1 * W] = s01[1][t].hi;
+      r[2 * W] = s[0][t];
+      r[3 * W] = s[1][t];
+      r[4 * W] = s[2][t];
+    }
+  }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 5 * q; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < NS * q; idx += blockDim.x) {
     const int k = idx / q, c = idx % q;
+    if (COMP && (k == 0 || k == 2)) {
+      // the compensated pairs: hi words summed with TwoSum, lo words added
+      dd acc{0.0, 0.0};
+      for (int r = 0; r < rpb; ++r) {
+        dd_add(acc, sred[(r * NS + k) * W + c]);
+        acc.lo += sred[(r * NS + k + 1) * W + c];
+      }
+      partials[static_cast<long long>(blockIdx.x) * NS * q + k * q + c] = acc.hi;
+      partials[static_cast<long long>(blockIdx.x) * NS * q + (k + 1) * q + c] = acc.lo;
+    } else if (COMP && (k == 1 || k == 3)) {
+      continue;  // written with its hi word
+    } else {
+      double v = 0.0;
+      for (int r = 0; r < rpb; ++r) v += sred[(r * NS + k) * W + c];
+      partials[static_cast<long long>(blockIdx.x) * NS * q + idx] = v;
+    }
+  }
+}
+
+// Compensated partials (7q per block) to the 5q sums the finish reads: the
+// numerator and denominator summed over blocks in compensated arithmetic
+// (rounded once at the end), the norms plainly; fixed order.
+__global__ void k_sum_rayleigh_comp(const double* __restrict__ part, int nparts, int q, double* __restrict__ sums) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 5 * q) return;
+  const int k = idx / q, c = idx % q;
+  if (k < 2) {
+    dd acc{0.0, 0.0};
+    for (int b = 0; b < nparts; ++b) {
+      dd_add(acc, part[static_cast<long long>(b) * 7 * q + (2 * k) * q + c]);
+      acc.lo += part[static_cast<long long>(b) * 7 * q + (2 * k + 1) * q + c];
+    }
+    sums[idx] = acc.hi + acc.lo;
+  } else {
     double v = 0.0;
-    for (int r = 0; r < rpb; ++r) v += sred[(r * 5 + k) * W + c];
-    partials[static_cast<long long>(blockIdx.x) * 5 * q + idx] = v;
+    for (int b = 0; b < nparts; ++b) v += part[static_cast<long long>(b) * 7 * q + (k + 2) * q + c];
+    sums[idx] = v;
   }
 }
 
@@ -144,22 +236,37 @@ void launch_gather_cols(const double* src, int rows, int ld, const int* perm, in
 
 int rayleigh_blocks(int) { return 4 * kNumSms; }
 
-void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, double* partials, int* nblocks_out,
-                         cudaStream_t st) {
+void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, bool compensated, double* partials,
+                         double* sums, cudaStream_t st) {
   int G = 1;
   while (G < q && G < 32) G <<= 1;
   int cpt = 1;
   while (cpt * G < q) cpt <<= 1;
   const int rpb = kThreads / G;
   const int blocks = std::min(ceil_div(AM.rows, rpb), rayleigh_blocks(q));
-  *nblocks_out = blocks;
+  const int ns = compensated ? 7 : 5;
   const double N = AM.rows, nnz = AM.nnz;
-  ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q, 4.0 * nnz * q + 10.0 * N * q);
-  const size_t sm = sizeof(double) * rpb * 5 * G * cpt;
+  // float64 operations: two FMAs per (nonzero, column), or the compensated
+  // product-sums (about eight operations each)
+  ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q,
+               (compensated ? 16.0 : 4.0) * nnz * q + 10.0 * N * q, 2);
+  const size_t sm = sizeof(double) * rpb * ns * G * cpt;
+  if (sm > 48 * 1024) {
+    if (compensated) {
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_rayleigh<1, true>), sm);
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_rayleigh<2, true>), sm);
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_rayleigh<4, true>), sm);
+    }
+  }
   switch (cpt) {
-#define AMGEIG_CASE(C)                                                                                           \
-  case C:                                                                                                        \
-    k_rayleigh<C><<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, U, q, G, partials); \
+#define AMGEIG_CASE(C)                                                                                        \
+  case C:                                                                                                     \
+    if (compensated)                                                                                          \
+      k_rayleigh<C, true><<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, U, q, G,     \
+                                                        partials);                                            \
+    else                                                                                                      \
+      k_rayleigh<C, false><<<blocks, kThreads, sm, st>>>(AM.rows, AM.rp, AM.ci, AM.v64, AM.m64, U, q, G,    \
+                                                         partials);                                           \
     break;
     AMGEIG_CASE(1)
     AMGEIG_CASE(2)
@@ -168,6 +275,10 @@ void launch_rayleigh_f64(const DevCsr& AM, const double* U, int q, double* parti
     default:
       break;
   }
+  if (compensated)
+    k_sum_rayleigh_comp<<<ceil_div(5 * q, 128), 128, 0, st>>>(partials, blocks, q, sums);
+  else
+    launch_sum_partials(partials, blocks, 5 * q, sums, st);
 }
 
 void launch_rq_finish(const double* sums, int q, double* theta, double* lam, int* perm, double* relres, int* flag,
