@@ -106,6 +106,13 @@ typedef struct {
                             q, q_extra, tol and max_corrections (the shared solve takes the widest
                             and the tightest of each; every request receives its own leading q
                             pairs and its own residual test); 0 = always solved on its own */
+  double shift;          /* sigma of a shifted inner solve (the remark after Algorithm 3.1): 0
+                            (default) = the paper's step 1; otherwise step 1 runs its V-cycles on
+                            (A_k - sigma M_k) u~ = (lambda_j - sigma) M_k u_j from u_j, on the
+                            hierarchy of A_l - sigma M_l (made on the GPU for the last sigma used;
+                            the defect is unchanged, lambda M u - A u).  sigma must lie below the
+                            lowest eigenvalue of (A_n, M_n) (EINVAL otherwise); with the
+                            l1-Jacobi smoother only, not with AMGEIG_MIXED_BF16 */
 } amgeig_options;
 
 #define AMGEIG_SMOOTHER_L1_JACOBI 0

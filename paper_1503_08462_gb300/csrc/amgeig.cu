@@ -425,6 +425,18 @@ struct amgeig_hierarchy_t {
     double *A = nullptr, *M = nullptr, *Z = nullptr, *theta = nullptr;
     PencilWork* pw = nullptr;
   } init;
+  // the shifted inner solve (options.shift = sigma): the V-cycle's operators
+  // A_l - sigma M_l (same pattern and transfers), their l1-Jacobi diagonals and the
+  // exact coarsest solve (A_n - sigma M_n)^-1, made for the last sigma asked for
+  struct Shifted {
+    bool ready = false;
+    double sigma = 0.0;
+    std::vector<DevCsr> A;
+    std::vector<double*> dinv64;
+    std::vector<float*> dinv32;
+    double *Bn = nullptr, *L = nullptr, *Linv = nullptr, *Ainv = nullptr;
+    float* Ainv32 = nullptr;
+  } sh;
   // float32 V-cycle widths (float4 columns) whose launch shapes are tuned, and the tuner's log
   bool tuned_w4[33] = {};
   std::string tune_log;
@@ -437,6 +449,7 @@ namespace {
 
 struct SolveWork {
   int smoother = AMGEIG_SMOOTHER_L1_JACOBI;  // of the current solve
+  bool shifted = false;                       // the current solve's V-cycle runs on A_l - sigma M_l
   bool bf16 = false;                          // the current solve reads bfloat16 operator values
   int qcap = 0;  // column capacity: the buffers serve any solve with q + q_extra <= qcap
   int qt = 0;    // columns of the current solve (every block's row stride)
@@ -614,13 +627,20 @@ void add_to_v(const double* U, const double* x, int rows, int q, int, double* V,
 void add_to_v(const double* U, const float* x, int rows, int q, int ldx, double* V, cudaStream_t s) { launch_add_to_vdf(reinterpret_cast<const float2*>(U), x, rows, q, ldx, reinterpret_cast<float2*>(V), s); }
 void axpy(const double* x, long long c, double* y, cudaStream_t s) { launch_axpy_f64(x, c, y, s); }
 void axpy(const float* x, long long c, float* y, cudaStream_t s) { launch_axpy_f32(x, c, y, s); }
-const double* dinv_of(amgeig_hierarchy_t* h, int l, double*) { return h->dinv64[l]; }
-const float* dinv_of(amgeig_hierarchy_t* h, int l, float*) { return h->dinv32[l]; }
-void coarse_solve(amgeig_hierarchy_t* h, const double* b, int q, double* x, cudaStream_t s) {
-  launch_dense_apply(h->dn, q, h->Ainv, b, x, s, P_COARSE);
+// the V-cycle's operator, l1-Jacobi diagonal and coarsest solve: the
+// hierarchy's own, or the shifted ones when the solve asks for a shift
+const DevCsr& vop(amgeig_hierarchy_t* h, SolveWork* w, int l) { return w->shifted ? h->sh.A[l] : h->A[l]; }
+const double* dinv_of(amgeig_hierarchy_t* h, SolveWork* w, int l, double*) {
+  return w->shifted ? h->sh.dinv64[l] : h->dinv64[l];
 }
-void coarse_solve(amgeig_hierarchy_t* h, const float* b, int q, float* x, cudaStream_t s) {
-  launch_dense_apply(h->dn, q, h->Ainv32, b, x, s, P_COARSE);
+const float* dinv_of(amgeig_hierarchy_t* h, SolveWork* w, int l, float*) {
+  return w->shifted ? h->sh.dinv32[l] : h->dinv32[l];
+}
+void coarse_solve(amgeig_hierarchy_t* h, SolveWork* w, const double* b, int q, double* x, cudaStream_t s) {
+  launch_dense_apply(h->dn, q, w->shifted ? h->sh.Ainv : h->Ainv, b, x, s, P_COARSE);
+}
+void coarse_solve(amgeig_hierarchy_t* h, SolveWork* w, const float* b, int q, float* x, cudaStream_t s) {
+  launch_dense_apply(h->dn, q, w->shifted ? h->sh.Ainv32 : h->Ainv32, b, x, s, P_COARSE);
 }
 
 // One V-cycle for A_k x = B[k] from x = 0; the result is left in X[k] unless
@@ -734,8 +754,8 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
   const bool gs = w->smoother == AMGEIG_SMOOTHER_GAUSS_SEIDEL;
   for (int l = k; l < n - 1; ++l) {
     LevelTag tag(l);
-    const DevCsr& A = h->A[l];
-    const T* d = dinv_of(h, l, dummy);
+    const DevCsr& A = vop(h, w, l);
+    const T* d = dinv_of(h, w, l, dummy);
     if (gs && pre >= 1) {
       // Gauss-Seidel from x = 0, colours ascending; then the residual
       cudaMemsetAsync(X[l], 0, sizeof(T) * h->sizes[l] * q, st);
@@ -757,12 +777,12 @@ void vcycle(amgeig_hierarchy_t* h, SolveWork* w, int k, int pre, int post, bool 
   }
   {
     LevelTag tag(n - 1);
-    coarse_solve(h, B[n - 1], q, X[n - 1], st);
+    coarse_solve(h, w, B[n - 1], q, X[n - 1], st);
   }
   for (int l = n - 2; l >= k; --l) {
     LevelTag tag(l);
-    const DevCsr& A = h->A[l];
-    const T* d = dinv_of(h, l, dummy);
+    const DevCsr& A = vop(h, w, l);
+    const T* d = dinv_of(h, w, l, dummy);
     spmm(h->P[l], X[l + 1], q, X[l], true, st, w->bf16);
     if (gs) {
       // colours descending after the coarse correction (a symmetric cycle)
@@ -817,12 +837,12 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     // V = U + (x + E) itself
     vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
     std::swap(X[k], E[k]);
-    residual(h->A[k], B[k], E[k], wd, D[k], st, w->bf16);
+    residual(vop(h, w, k), B[k], E[k], wd, D[k], st, w->bf16);
     std::swap(B[k], D[k]);
     for (int c = 1; c + 1 < o.v_cycles; ++c) {
       vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
       axpy(X[k], cnt, E[k], st);
-      residual(h->A[k], D[k], E[k], wd, B[k], st, w->bf16);
+      residual(vop(h, w, k), D[k], E[k], wd, B[k], st, w->bf16);
     }
     vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, true, U, V, st, E[k]);
     return;
@@ -833,7 +853,7 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, U, V, st);
     // E += X[k]
     axpy(X[k], cnt, E[k], st);
-    if (c + 1 < o.v_cycles) residual(h->A[k], D[k], E[k], wd, B[k], st);
+    if (c + 1 < o.v_cycles) residual(vop(h, w, k), D[k], E[k], wd, B[k], st);
   }
   add_to_v(U, E[k], static_cast<int>(h->sizes[k]), q, wd, V, st);
 }
@@ -944,7 +964,8 @@ int check_options(const amgeig_options& o) {
       (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
       (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL) || o.n1 < -1 ||
       (o.refine < 0 || o.refine > 2) || (o.graphs != 0 && o.graphs != 1) || (o.autotune != 0 && o.autotune != 1) ||
-      (o.batch != 0 && o.batch != 1))
+      (o.batch != 0 && o.batch != 1) || !std::isfinite(o.shift) ||
+      (o.shift != 0.0 && (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI || o.precision == AMGEIG_MIXED_BF16)))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
 }
@@ -1000,8 +1021,9 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
   std::vector<void*> pre = roles(w);
   std::string key = seg;
   const int cfg[] = {w->qt, w->ld32, o.precision, o.v_cycles, o.pre_sweeps, o.post_sweeps, o.smoother,
-                     o.coarse_modes, w->bf16 ? 1 : 0};
+                     o.coarse_modes, w->bf16 ? 1 : 0, w->shifted ? 1 : 0};
   key.append(reinterpret_cast<const char*>(cfg), sizeof(cfg));
+  key.append(reinterpret_cast<const char*>(&o.shift), sizeof(o.shift));
   key.append(reinterpret_cast<const char*>(pre.data()), sizeof(void*) * pre.size());
   auto it = w->graphs.find(key);
   if (it == w->graphs.end()) {
@@ -1030,6 +1052,65 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
   CK(cudaGraphLaunch(it->second.exec, st));
   add_launches(it->second.kernels);
   set_roles(w, it->second.post);
+  return AMGEIG_OK;
+}
+
+// The shifted operators for sigma (Algorithm 3.1's remark: a shifted linear
+// solve in step 1), made on the GPU: A_l - sigma M_l on every level below the
+// coarsest (float64 and float32 values on the shared pattern), their l1
+// diagonals, and (A_n - sigma M_n)^-1 from its float64 Cholesky factor.
+// EINVAL when A_n - sigma M_n is not positive definite (sigma not below the
+// coarsest pencil's lowest eigenvalue).  Under the hierarchy's lock.
+int ensure_shift(amgeig_hierarchy_t* h, double sigma, cudaStream_t st) {
+  auto& S = h->sh;
+  const int n = h->nlev, dn = h->dn;
+  if (S.ready && S.sigma == sigma) return AMGEIG_OK;
+  auto& m = h->mem;
+  if (S.A.empty()) {
+    S.A.assign(n > 1 ? n - 1 : 0, DevCsr());
+    S.dinv64.assign(n, nullptr);
+    S.dinv32.assign(n, nullptr);
+    for (int l = 0; l + 1 < n; ++l) {
+      const DevCsr& A = h->A[l];
+      DevCsr& D = S.A[l];
+      D.rows = A.rows;
+      D.cols = A.cols;
+      D.nnz = A.nnz;
+      D.rp = A.rp;
+      D.ci = A.ci;
+      D.m64 = A.m64;
+      CK(m.alloc(&D.v64, static_cast<size_t>(A.nnz)));
+      CK(m.alloc(&D.v32, static_cast<size_t>(A.nnz)));
+      CK(m.alloc(&S.dinv64[l], static_cast<size_t>(A.rows)));
+      CK(m.alloc(&S.dinv32[l], static_cast<size_t>(A.rows)));
+    }
+    const size_t dd = static_cast<size_t>(dn) * dn;
+    CK(m.alloc(&S.Bn, dd));
+    CK(m.alloc(&S.L, dd));
+    CK(m.alloc(&S.Linv, dd));
+    CK(m.alloc(&S.Ainv, dd));
+    CK(m.alloc(&S.Ainv32, dd));
+  }
+  S.ready = false;
+  int* flag = h->dstatus + 3;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  for (int l = 0; l + 1 < n; ++l) {
+    DevCsr& D = S.A[l];
+    std::memcpy(D.tuned, h->A[l].tuned, sizeof(D.tuned));
+    launch_axpby_f64(h->A[l].v64, -sigma, h->A[l].m64, D.nnz, D.v64, st);
+    launch_convert_f64_to_f32(D.v64, D.nnz, D.v32, st);
+    launch_l1_inv_diag(D, S.dinv64[l], S.dinv32[l], flag, st);
+  }
+  launch_axpby_f64(h->An, -sigma, h->Mn, static_cast<long long>(dn) * dn, S.Bn, st);
+  launch_coarse_inverse(dn, S.Bn, S.L, S.Linv, S.Ainv, flag, st);
+  launch_convert_f64_to_f32(S.Ainv, static_cast<long long>(dn) * dn, S.Ainv32, st);
+  CK(cudaGetLastError());
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return fail(AMGEIG_EINVAL, "shift not below the lowest eigenvalue of the coarsest pencil");
+  S.sigma = sigma;
+  S.ready = true;
   return AMGEIG_OK;
 }
 
@@ -1174,6 +1255,11 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   w->bf16 = o.precision == AMGEIG_MIXED_BF16;
   if (w->bf16) {
     rc = ensure_bf16(h, st);
+    if (rc) return rc;
+  }
+  w->shifted = o.shift != 0.0;
+  if (w->shifted) {
+    rc = ensure_shift(h, o.shift, st);
     if (rc) return rc;
   }
   if (o.precision != AMGEIG_FP64 && o.autotune) {
@@ -1378,7 +1464,8 @@ bool can_share(const Request& a, const Request& b) {
   return a.h == b.h && x.batch && y.batch && x.fixed_corrections == 0 && y.fixed_corrections == 0 &&
          x.precision == y.precision && x.v_cycles == y.v_cycles && x.pre_sweeps == y.pre_sweeps &&
          x.post_sweeps == y.post_sweeps && x.coarse_modes == y.coarse_modes && x.smoother == y.smoother &&
-         x.n1 == y.n1 && x.refine == y.refine && x.graphs == y.graphs && x.autotune == y.autotune;
+         x.n1 == y.n1 && x.refine == y.refine && x.graphs == y.graphs && x.autotune == y.autotune &&
+         x.shift == y.shift;
 }
 
 // Continuous batching over hierarchies: kWorkers library threads take queued
@@ -1536,6 +1623,7 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->graphs = 1;
   opt->autotune = 1;
   opt->batch = 1;
+  opt->shift = 0.0;
 }
 
 const char* amgeig_strerror(int code) {
@@ -1959,11 +2047,17 @@ int amgeig_apply_vcycle(amgeig_hierarchy h, int level, int width, const amgeig_o
     rc = ensure_bf16(h, st);
     if (rc) return rc;
   }
+  w->shifted = o.shift != 0.0;
+  if (w->shifted) {
+    rc = ensure_shift(h, o.shift, st);
+    if (rc) return rc;
+  }
   const long long cnt = h->sizes[level] * static_cast<long long>(width);
   if (level == h->nlev - 1) {
     // the coarsest level: the exact solve
     CK(cudaMemcpyAsync(w->V, b, sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
-    launch_gemm_f64(h->dn, width, h->dn, 1.0, h->Ainv, h->dn, false, w->V, width, false, 0.0, w->U, width, st);
+    launch_gemm_f64(h->dn, width, h->dn, 1.0, w->shifted ? h->sh.Ainv : h->Ainv, h->dn, false, w->V, width, false,
+                    0.0, w->U, width, st);
     CK(cudaMemcpyAsync(x, w->U, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return AMGEIG_OK;

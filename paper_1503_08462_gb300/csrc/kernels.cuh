@@ -95,6 +95,8 @@ void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaS
 void launch_recombine(int rows, const double* Xp, const double* V, const double* Y, int q, double* U,
                       cudaStream_t st, bool df_arith = false);
 
+// z = x + alpha y (elementwise; z may alias neither)
+void launch_axpby_f64(const double* x, double alpha, const double* y, long long count, double* z, cudaStream_t st);
 // y += x
 void launch_axpy_f64(const double* x, long long count, double* y, cudaStream_t st);
 void launch_axpy_f32(const float* x, long long count, float* y, cudaStream_t st);

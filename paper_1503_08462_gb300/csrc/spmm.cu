@@ -1103,4 +1103,18 @@ TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const flo
   return r;
 }
 
+namespace {
+__global__ void k_axpby_f64(const double* __restrict__ x, double alpha, const double* __restrict__ y, long long n,
+                            double* __restrict__ z) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    z[i] = fma(alpha, y[i], x[i]);
+}
+}  // namespace
+
+void launch_axpby_f64(const double* x, double alpha, const double* y, long long count, double* z, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 24.0 * count, 2.0 * count);
+  k_axpby_f64<<<grid_for(count), kThreads, 0, st>>>(x, alpha, y, count, z);
+}
+
 }  // namespace amgeig

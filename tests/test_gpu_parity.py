@@ -684,3 +684,64 @@ def test_compensated_refinement_gives_exact_rayleigh_quotients(prec):
     assert np.all(np.abs(lam - exact) <= 8 * 2.0 ** -53 * exact), np.max(np.abs(lam - exact) / exact)
     rr = O.relres(oh, lam, U)
     assert np.allclose(info.max_relres, rr.max(), rtol=1e-6)
+
+
+# ------------------------------------------------------------------ shifted inner solve
+
+
+def _safe_shift(oh, frac=0.5):
+    """A shift below the coarsest pencil's lowest eigenvalue (so every level's A - sigma M stays SPD)."""
+    import scipy.linalg as sla
+
+    lo = sla.eigh(oh.An, oh.Mn, eigvals_only=True, subset_by_index=[0, 0])[0]
+    return frac * float(lo)
+
+
+@pytest.mark.parametrize("prec,rtol", [(ae.AMGEIG_FP64, 1e-11), (ae.AMGEIG_MIXED_FP32, 2e-5)])
+def test_shifted_vcycle_matches_oracle(prec, rtol):
+    """One V-cycle on the hierarchy of A_l - sigma M_l (shifted values, their l1 diagonals, the shifted exact
+    coarsest solve) against the oracle's shifted V-cycle, every level, element by element."""
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    oh = O.read_blob(blob)
+    sigma = _safe_shift(oh)
+    hs = O.shifted(oh, sigma)
+    with ae.Hierarchy(blob) as h:
+        for level in range(len(oh.sizes)):
+            n = oh.sizes[level]
+            b = np.random.default_rng(level).standard_normal((n, 6))
+            x = ae.amgeig_apply_vcycle(h.handle, level, b, ae.options(precision=prec, shift=sigma))
+            xo = O.vcycle(hs, level, b, np.zeros_like(b))
+            err = np.abs(x - xo).max(axis=0) / np.abs(xo).max(axis=0)
+            assert np.all(err <= rtol), (level, err.max())
+
+
+@pytest.mark.parametrize("L", [1, 2])
+def test_shifted_iteration_parity(L):
+    """L finest-level corrections with the shifted inner solve: the GPU float64 path against the oracle's."""
+    p, blob, _ = problem_and_blob("square", 32, 50, 1)
+    oh = O.read_blob(blob)
+    sigma = _safe_shift(oh, 0.9)
+    lam_o, U_o, _ = O.solve(oh, 4, tol=0.0, opts=O.Options(q_extra=2, fixed_corrections=L, shift=sigma))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, _ = h.solve(4, tol=0.0, opt=ae.options(q_extra=2, fixed_corrections=L, shift=sigma))
+    assert np.all(np.abs(lam - lam_o) <= eig_rel_tol(lam_o, lam_max(p)) * lam_o)
+    assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
+
+
+def test_shifted_mixed_solve_converges_and_refuses_a_large_shift():
+    p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
+    oh = O.read_blob(blob)
+    lam_ex, U_ex = dense_pairs(p, 6)
+    sigma = _safe_shift(oh, 0.9)
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, code = h.solve(6, tol=1e-9, opt=ae.options(q_extra=2, max_corrections=100, v_cycles=2,
+                                                                 precision=ae.AMGEIG_MIXED_FP32, shift=sigma))
+        assert code == ae.AMGEIG_OK
+        assert np.all(np.abs(lam - lam_ex) <= 1e-10 * lam_ex)
+        assert m_subspace_angle(U, U_ex, oh.M[0]) < 1e-7
+        with pytest.raises(ae.AmgEigError) as e:
+            h.solve(6, tol=1e-9, opt=ae.options(q_extra=2, shift=2.0 * _safe_shift(oh, 1.0)))
+        assert e.value.code == ae.AMGEIG_EINVAL
+        # after a refused shift the hierarchy still solves (unshifted and shifted)
+        lam2, _, _, code2 = h.solve(6, tol=1e-9, opt=ae.options(q_extra=2, max_corrections=100))
+        assert code2 == ae.AMGEIG_OK and np.all(np.abs(lam2 - lam_ex) <= 1e-10 * lam_ex)
