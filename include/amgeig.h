@@ -281,8 +281,10 @@ int amgeig_sym_eigh_noalloc(int n, int nwant, const double* H, double* evals, do
 
 /* The launch-shape tuner's choices on h so far, as JSON text: a list of
  * {"level", "kernel" (smooth | restrict | prolong), "w4" (block width in float4
- * columns), "G" (lanes per row), "cpt" (float4 columns per lane), "us" (its
- * time), "rule_G", "rule_cpt", "rule_us" (the fixed rule's shape and time)}.
+ * columns), "G" (lanes per row), "cpt" (float4 columns per lane), "S" (streams
+ * the row's nonzeros are split over: G / S lanes each; set by the rule, kept by
+ * the tuner), "us" (its time), "rule_G", "rule_cpt", "rule_us" (the fixed
+ * rule's shape and time)}.
  * Errors: EINVAL (NULL argument, buffer too small; the text is truncated). */
 int amgeig_tuning_report(amgeig_hierarchy h, char* buf, size_t len);
 

@@ -1137,10 +1137,10 @@ int ensure_tuned(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
     const char* nm[3] = {"smooth", "restrict", "prolong"};
     for (int i = 0; i < 3; ++i) {
       std::snprintf(line, sizeof(line),
-                    "%s{\"level\": %d, \"kernel\": \"%s\", \"w4\": %d, \"G\": %d, \"cpt\": %d, \"us\": %.2f, "
-                    "\"rule_G\": %d, \"rule_cpt\": %d, \"rule_us\": %.2f}",
-                    h->tune_log.empty() ? "" : ", ", l, nm[i], w4, tr[i]->G, tr[i]->cpt, tr[i]->us, tr[i]->rule_G,
-                    tr[i]->rule_cpt, tr[i]->rule_us);
+                    "%s{\"level\": %d, \"kernel\": \"%s\", \"w4\": %d, \"G\": %d, \"cpt\": %d, \"S\": %d, "
+                    "\"us\": %.2f, \"rule_G\": %d, \"rule_cpt\": %d, \"rule_us\": %.2f}",
+                    h->tune_log.empty() ? "" : ", ", l, nm[i], w4, tr[i]->G, tr[i]->cpt, tr[i]->S, tr[i]->us,
+                    tr[i]->rule_G, tr[i]->rule_cpt, tr[i]->rule_us);
       h->tune_log += line;
     }
   }

@@ -21,7 +21,8 @@ struct DevCsr {
   float2* m2 = nullptr;   // m64 as float-float pairs
   __nv_bfloat16* vbf = nullptr;  // v64 rounded to bfloat16 (the V-cycle's operators, AMGEIG_MIXED_BF16)
   // launch shape of the float32 V-cycle kernels on this operator, per block width in float4
-  // columns w4 <= 32, chosen by the autotuner: (log2 G) * 4 + cpt; 0 = not tuned (the rule applies)
+  // columns w4 <= 32, chosen by the autotuner: (log2 column lanes) * 4 + cpt (the nonzero
+  // streams per row stay the rule's); 0 = not tuned (the rule applies)
   unsigned char tuned[33] = {};
 };
 
@@ -32,7 +33,7 @@ struct DevCsr {
 // operator's `tuned` table.  x / b / X and out / Y are device scratch of the
 // operator's rows (or columns) x 4 w4 floats; their contents are overwritten.
 struct TuneResult {
-  int G = 0, cpt = 0, rule_G = 0, rule_cpt = 0;
+  int G = 0, cpt = 0, rule_G = 0, rule_cpt = 0, S = 1;
   float us = 0.f, rule_us = 0.f;
 };
 TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const float* x, const float* b, float* out,

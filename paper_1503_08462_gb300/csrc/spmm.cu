@@ -289,12 +289,14 @@ void smooth_impl(const DevCsr& A, const T* vals, const T* dinv, const T* b, cons
 
 struct F4Geo {
   int G, cpt;
+  int S = 1;  // nonzero streams per row: the row's G lanes form S groups of G / S column lanes, group k
+              // takes the nonzeros p0 + k, p0 + k + S, ... and the groups' sums are added at the end
 };
 
 // Few lanes per row pay off only while the rows alone keep the GPU full: below
 // about four resident waves of row groups the one-column-per-lane layout (more
 // threads, shorter chains) is faster on the coarse levels.
-F4Geo f4_geo(int w4, long long rows) {
+F4Geo f4_geo(int w4, long long rows, long long nnz = 0) {
   int G = 1;
   while (G * 3 < w4 && G < 32) G <<= 1;
   int cpt = (w4 + G - 1) / G;
@@ -306,17 +308,26 @@ F4Geo f4_geo(int w4, long long rows) {
     G = 1;
     while (G < w4 && G < 32) G <<= 1;
     cpt = (w4 + G - 1) / G;
+    // Small levels with long rows (the Galerkin coarse operators keep 25-35 nonzeros a
+    // row): the chain of dependent gathers along a row, not bandwidth, sets the time, so
+    // the row's nonzeros are split over S streams of lanes (a warp per row at most)
+    if (nnz >= 12 * rows && rows < 65536 && G < 32) {
+      const int S = std::min(4, 32 / G);
+      return F4Geo{G * S, cpt, S};
+    }
   }
-  return F4Geo{G, cpt};
+  return F4Geo{G, cpt, 1};
 }
 
 // the operator's tuned shape at this width, else the rule
 F4Geo geo_of(const DevCsr& S, int w4) {
+  const F4Geo rule = f4_geo(w4, S.rows, S.nnz);
   if (w4 >= 1 && w4 <= 32 && S.tuned[w4]) {
     const int v = S.tuned[w4];
-    return F4Geo{1 << (v >> 2), v & 3};
+    // tuned: the lane count per stream and the columns per lane; the streams stay the rule's
+    return F4Geo{(1 << (v >> 2)) * rule.S, v & 3, rule.S};
   }
-  return f4_geo(w4, S.rows);
+  return rule;
 }
 
 __device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
@@ -332,6 +343,21 @@ __device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
 __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
+// the S streams' partial sums of a row added into stream 0's lanes (the row's
+// G = S * (G / S) lanes are consecutive in a warp; every lane of the warp takes part)
+template <int CPT>
+__device__ __forceinline__ void reduce_streams(float4 (&acc)[CPT], int S, int gs) {
+  for (int o = gs; o < gs * S; o <<= 1) {
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      acc[t].x += __shfl_down_sync(0xffffffffu, acc[t].x, o);
+      acc[t].y += __shfl_down_sync(0xffffffffu, acc[t].y, o);
+      acc[t].z += __shfl_down_sync(0xffffffffu, acc[t].z, o);
+      acc[t].w += __shfl_down_sync(0xffffffffu, acc[t].w, o);
+    }
+  }
+}
+
 template <int MODE, int CPT, typename TV>
 __global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __restrict__ rp,
                                                         const int* __restrict__ ci, const TV* __restrict__ a,
@@ -341,32 +367,38 @@ __global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __r
                                                         const double* __restrict__ U, double* __restrict__ V, int qv,
                                                         int G, const float2* __restrict__ U2 = nullptr,
                                                         float2* __restrict__ V2 = nullptr,
-                                                        const float4* __restrict__ xadd = nullptr) {
+                                                        const float4* __restrict__ xadd = nullptr, int S = 1) {
   const int rpb = blockDim.x / G;
-  const int lane = threadIdx.x % G;
+  const int gs = G / S;  // column lanes per stream
+  const int lane = threadIdx.x % gs;
+  const int sub = (threadIdx.x % G) / gs;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
-  if (row >= n) return;
+  if (S == 1 && row >= n) return;
   float4 acc[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int p0 = rp[row], p1 = rp[row + 1];
+  const int p0 = row < n ? rp[row] : 0, p1 = row < n ? rp[row + 1] : 0;
   const float4* src = MODE == 0 ? b : x;
 #pragma unroll 2
-  for (int p = p0; p < p1; ++p) {
+  for (int p = p0 + sub; p < p1; p += S) {
     const int j = ci[p];
     float s = to_f(a[p]);
     if (MODE == 0) s *= dinv[j];
     const float4* sr = src + static_cast<long long>(j) * w4;
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
-      const int c4 = lane + t * G;
+      const int c4 = lane + t * gs;
       if (c4 < w4) fma4(s, sr[c4], acc[t]);
     }
+  }
+  if (S > 1) {
+    reduce_streams(acc, S, gs);
+    if (sub != 0 || row >= n) return;
   }
   const float di = dinv ? dinv[row] : 0.f;
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
-    const int c4 = lane + t * G;
+    const int c4 = lane + t * gs;
     if (c4 >= w4) continue;
     const long long o = static_cast<long long>(row) * w4 + c4;
     const float4 bi = b[o];
@@ -412,28 +444,35 @@ __global__ void __launch_bounds__(kThreads, 6) k_smooth_f4(int n, const int* __r
 template <int CPT, typename TV>
 __global__ void __launch_bounds__(kThreads, 6) k_spmm_f4(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                       const TV* __restrict__ v, const float4* __restrict__ X,
-                                                      int w4, float4* __restrict__ Y, int G, int accumulate) {
+                                                      int w4, float4* __restrict__ Y, int G, int accumulate,
+                                                      int S = 1) {
   const int rpb = blockDim.x / G;
-  const int lane = threadIdx.x % G;
+  const int gs = G / S;
+  const int lane = threadIdx.x % gs;
+  const int sub = (threadIdx.x % G) / gs;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
-  if (row >= n) return;
+  if (S == 1 && row >= n) return;
   float4 acc[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int p0 = rp[row], p1 = rp[row + 1];
+  const int p0 = row < n ? rp[row] : 0, p1 = row < n ? rp[row + 1] : 0;
 #pragma unroll 2
-  for (int p = p0; p < p1; ++p) {
+  for (int p = p0 + sub; p < p1; p += S) {
     const float s = to_f(v[p]);
     const float4* xr = X + static_cast<long long>(ci[p]) * w4;
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
-      const int c4 = lane + t * G;
+      const int c4 = lane + t * gs;
       if (c4 < w4) fma4(s, xr[c4], acc[t]);
     }
   }
+  if (S > 1) {
+    reduce_streams(acc, S, gs);
+    if (sub != 0 || row >= n) return;
+  }
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
-    const int c4 = lane + t * G;
+    const int c4 = lane + t * gs;
     if (c4 >= w4) continue;
     const long long o = static_cast<long long>(row) * w4 + c4;
     float4 r = acc[t];
@@ -455,7 +494,7 @@ void smooth_f4(const DevCsr& A, const float* dinv, const float* b, const float* 
   k_smooth_f4<MODE, C, TV><<<blocks, kThreads, 0, st>>>(                                                       \
       A.rows, A.rp, A.ci, VALS, dinv, reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(x), w4, \
       reinterpret_cast<float4*>(out1), reinterpret_cast<float4*>(out2), U, V, qv, g.G, U2, V2,                   \
-      reinterpret_cast<const float4*>(xadd))
+      reinterpret_cast<const float4*>(xadd), g.S)
 #define AMGEIG_SMOOTH(C)                                  \
   if (bf16)                                               \
     AMGEIG_SMOOTH_T(C, __nv_bfloat16, A.vbf);             \
@@ -789,9 +828,10 @@ static void spmm_f4_geo(const DevCsr& S, const float* X, int w4, float* Y, bool 
   const int acc = accumulate ? 1 : 0;
 #define AMGEIG_SPMM(C)                                                                                       \
   if (bf16)                                                                                                  \
-    k_spmm_f4<C, __nv_bfloat16><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.vbf, X4, w4, Y4, g.G, acc); \
+    k_spmm_f4<C, __nv_bfloat16><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.vbf, X4, w4, Y4, g.G, acc, \
+                                                             g.S);                                            \
   else                                                                                                       \
-    k_spmm_f4<C, float><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc)
+    k_spmm_f4<C, float><<<blocks, kThreads, 0, st>>>(S.rows, S.rp, S.ci, S.v32, X4, w4, Y4, g.G, acc, g.S)
   switch (g.cpt) {
     case 1:
       AMGEIG_SPMM(1);
@@ -1050,9 +1090,10 @@ void launch_composite_rows(const DevCsr& P, const int* nrp, const int* nci, cons
 TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const float* x, const float* b, float* out,
                        cudaStream_t st) {
   TuneResult r;
-  const F4Geo rule = f4_geo(w4, S.rows);
+  const F4Geo rule = f4_geo(w4, S.rows, S.nnz);
   r.rule_G = rule.G;
   r.rule_cpt = rule.cpt;
+  r.S = rule.S;
   if (w4 < 1 || w4 > 32 || S.rows == 0) return r;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1079,15 +1120,16 @@ TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const flo
     }
     return best * 1000.f;
   };
-  // every power-of-two lane count whose column share per lane is 1..3 float4s
+  // every power-of-two column-lane count whose share per lane is 1..3 float4s, with the
+  // rule's nonzero streams (which fix the order of each row's sums: the bits stay the rule's)
   float best = 1e30f;
-  for (int G = 1, lg = 0; G <= 32; G <<= 1, ++lg) {
-    const int cpt = (w4 + G - 1) / G;
-    if (cpt > 3 || (G > 1 && G / 2 >= w4)) continue;
-    const float us = time_us(F4Geo{G, cpt});
+  for (int gc = 1; gc * rule.S <= 32; gc <<= 1) {
+    const int cpt = (w4 + gc - 1) / gc;
+    if (cpt > 3 || (gc > 1 && gc / 2 >= w4)) continue;
+    const float us = time_us(F4Geo{gc * rule.S, cpt, rule.S});
     if (us < best) {
       best = us;
-      r.G = G;
+      r.G = gc * rule.S;
       r.cpt = cpt;
     }
   }
@@ -1095,7 +1137,7 @@ TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const flo
   r.rule_us = time_us(rule);
   if (r.G > 0 && cudaGetLastError() == cudaSuccess) {
     int lg = 0;
-    while ((1 << lg) < r.G) ++lg;
+    while ((1 << lg) < r.G / rule.S) ++lg;
     S.tuned[w4] = static_cast<unsigned char>(lg * 4 + r.cpt);
   }
   cudaEventDestroy(e0);
