@@ -1533,9 +1533,10 @@ struct Service {
     return nullptr;
   }
 
-  // Queued requests on r's hierarchy that can share its solve ride along, as
-  // long as the shared width (the widest q + q_extra of the group) stays within
-  // r's workspace, or the workspace admitted for r (caller holds mu).
+  // Queued requests on r's hierarchy that can share its solve ride along.  The
+  // shared solve takes the group's widest q and q_extra: up to the width of r's
+  // workspace (or the one admitted for r), or wider when a workspace of the
+  // wider width is admissible now (caller holds mu).
   void gather_riders(const std::shared_ptr<Request>& r) {
     r->riders.clear();
     if (!r->opt.batch) return;
@@ -1543,6 +1544,23 @@ struct Service {
     {
       std::unique_lock<std::mutex> lk(r->h->mu, std::try_to_lock);
       if (lk.owns_lock() && r->h->ws) width = std::max(width, r->h->ws->qcap);
+    }
+    {
+      // the widest group the queue offers, if its workspace fits
+      int wq = 0, we = 0;
+      for (const auto& x : queue)
+        if (can_share(*r, *x)) {
+          wq = std::max(wq, x->q);
+          we = std::max(we, x->opt.q_extra);
+        }
+      const int wide = std::min(128, std::max(r->q, wq) + std::max(r->opt.q_extra, we));
+      if (wide > width) {
+        Request probe = *r;
+        probe.riders.clear();
+        probe.q = std::max(r->q, wq);
+        probe.opt.q_extra = wide - probe.q;
+        if (probe.opt.q_extra >= 0 && fits(&probe) == kFits) width = wide;
+      }
     }
     int qm = r->q, qe = r->opt.q_extra;
     for (auto it = queue.begin(); it != queue.end();) {

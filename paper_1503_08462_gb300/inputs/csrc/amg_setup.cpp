@@ -355,6 +355,24 @@ int amgsetup_build(int64_t n, const int32_t* rp, const int32_t* ci, const double
   return 0;
 }
 
+// The C/F splitting alone (the first step of each level's setup), for a setup
+// whose other steps run elsewhere: state[i] = 1 for a C point, 2 for an F point.
+// Returns 0, or -1 on invalid input.
+int amgsetup_cf_split(int64_t n, const int32_t* rp, const int32_t* ci, const double* a, double theta,
+                      int8_t* state) {
+  if (n <= 0 || !rp || !ci || !a || !state || theta <= 0.0 || theta >= 1.0) return -1;
+  Csr A;
+  A.rows = A.cols = n;
+  A.rp.assign(rp, rp + n + 1);
+  const int64_t nnz = A.rp[n];
+  A.ci.assign(ci, ci + nnz);
+  A.a.assign(a, a + nnz);
+  std::vector<int8_t> st;
+  rs_split(A, theta, st);
+  std::memcpy(state, st.data(), static_cast<size_t>(n));
+  return 0;
+}
+
 int32_t amgsetup_num_levels(void* hp) { return static_cast<int32_t>(static_cast<Hierarchy*>(hp)->levels.size()); }
 
 // Sizes of level l: rows, nnz of (A,M), nnz of P_l (0 for the coarsest level).

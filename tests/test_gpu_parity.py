@@ -278,8 +278,10 @@ def test_submit_poll_matches_direct():
 
     p, blob, _ = problem_and_blob("lshape", 16, 60, 2)
     with ae.Hierarchy(blob) as h:
+        # batch = 0: each request runs its own solve (a shared solve gives equal results within tolerance, not bits)
         direct = [h.solve(q, tol=1e-9, opt=ae.options(q_extra=2, max_corrections=60)) for q in (3, 6)]
-        ids = [ae.amgeig_submit(h.handle, q, 1e-9, ae.options(q_extra=2, max_corrections=60)) for q in (3, 6)]
+        ids = [ae.amgeig_submit(h.handle, q, 1e-9, ae.options(q_extra=2, max_corrections=60, batch=0))
+               for q in (3, 6)]
         for rid, q, d in zip(ids, (3, 6), direct):
             vals = np.empty(q)
             vecs = np.empty((p.n, q))
