@@ -107,6 +107,9 @@ def replica_max(dist, seconds_or_ms, device):
     return float(t.item())
 
 
+SETUP_TIMES = {}
+
+
 def build_workload(name, cap=None):
     from paper_1503_08462_gb300.inputs import hierarchy, meshes
 
@@ -114,10 +117,33 @@ def build_workload(name, cap=None):
     q, qe, tol = wl["q"], wl["qe"], wl["tol"]
     t0 = time.perf_counter()
     p = getattr(meshes, wl["builder"])(**wl["kw"])
+    t1 = time.perf_counter()
     blob, h = hierarchy.problem_blob(p, coarse_cap=cap or wl["cap"])
+    t2 = time.perf_counter()
+    SETUP_TIMES.update(mesh_s=t1 - t0, host_setup_s=t2 - t1)
     log(f"[bench] {name}: N={p.n} levels={h.sizes} op.complexity={h.operator_complexity():.2f} "
-        f"blob={len(blob) / 1e6:.1f} MB setup={time.perf_counter() - t0:.1f}s")
+        f"blob={len(blob) / 1e6:.1f} MB mesh={t1 - t0:.1f}s setup={t2 - t1:.1f}s")
     return p, blob, h, q, qe, tol
+
+
+def device_setup(ae, p, blob, cap, device):
+    """The device AMG setup of the same problem: its time beside the host setup's, and whether it
+    reproduces the host hierarchy's levels (sizes and sparsity)."""
+    import struct
+
+    try:
+        ae.amgeig_setup_blob(p.row_ptr, p.col_idx, p.a_vals, p.m_vals, coarse_cap=cap, device=device)  # warm
+        t0 = time.perf_counter()
+        blob_d, secs, split_s = ae.amgeig_setup_blob(p.row_ptr, p.col_idx, p.a_vals, p.m_vals, coarse_cap=cap,
+                                                     device=device)
+        wall = time.perf_counter() - t0
+    except Exception as exc:  # reported, never hides the solve's result
+        return {"error": str(exc)}
+    n_h = struct.unpack_from("<I", blob, 12)[0]
+    n_d = struct.unpack_from("<I", blob_d, 12)[0]
+    same = n_h == n_d and blob[16:16 + 8 * (3 * n_h - 1)] == blob_d[16:16 + 8 * (3 * n_d - 1)]
+    return {"device_setup_s": wall, "device_cf_split_host_s": split_s, "same_level_sizes_and_nnz": bool(same),
+            **{k: round(v, 4) for k, v in SETUP_TIMES.items()}}
 
 
 class ClockSampler:
@@ -450,6 +476,7 @@ def main():
     ap.add_argument("--ref-max", type=int, default=None,
                     help="corrections the float64 reference may take (workload default, 150)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip the float64 path at the same settings")
+    ap.add_argument("--no-device-setup", action="store_true", help="skip timing the device AMG setup")
     ap.add_argument("--refine", type=int, default=None, choices=[0, 1, 2],
                     help="Rayleigh quotients of the final vectors: 1 float64, 2 compensated float64 "
                          "(workload default)")
@@ -693,6 +720,8 @@ def main():
                    "GB/s": round(v["bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1),
                    "TFLOP/s": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 4)} for k, v in prof.items()}
 
+    setup_info = device_setup(ae, p, blob, args.cap or wl["cap"], local) if not args.no_device_setup else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -722,7 +751,7 @@ def main():
                        "dense_fallbacks": info.dense_fallbacks,
                        "l2": "inputs larger than L2 (hierarchy + blocks > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "setup": setup_info,
             "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": len(blob),
                     "d2h_bytes_per_step": 8 * q + 8 * N0 * q},
             "gpu_launches": int(launches), "launches_before_timed": int(launches0), "clocks": clk.summary(),

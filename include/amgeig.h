@@ -226,6 +226,32 @@ int amgeig_service_set_memory_limit(uint64_t bytes);
  * may be NULL, not both).  Errors: EINVAL. */
 int amgeig_service_memory(uint64_t* resident_bytes, uint64_t* evictions);
 
+/* ---- AMG setup ------------------------------------------------------------ */
+
+/* Build the AMG hierarchy of Sec. 2 for the pencil (A, M), A and M given as one
+ * shared-pattern CSR (host arrays: rp int32[n+1], ci int32[nnz], a and m
+ * float64[nnz]), and return it as a hierarchy blob for amgeig_load_hierarchy.
+ * Per level: strength theta on the negative couplings (Sec. 2.1; 0.25 in
+ * Sec. 4.1) and the classical Ruge-Stueben C/F splitting on the host; direct
+ * interpolation (Eqs. Interpolation_Def, Interpolation_Dir) and the Galerkin
+ * products A_{k+1} = P^T A_k P, M_{k+1} = P^T M_k P (Eq. Coarse_Matrices) on
+ * device `device`; levels until the coarsest has at most coarse_cap rows or
+ * max_levels are made.  The same hierarchy as the package's host setup
+ * (inputs/hierarchy.py): identical levels, splittings and sparsity patterns,
+ * values equal up to the rounding of sums taken in another order.
+ *   blob, bytes   receive a library-allocated host buffer (free it with
+ *                 amgeig_free_blob) and its size.
+ *   seconds       may be NULL; else seconds[0] = the whole setup, seconds[1] =
+ *                 its host C/F splitting.
+ * Errors: EINVAL (NULL argument, bad CSR, theta outside (0, 1), bad device),
+ * ENOMEM (a sparse product row beyond 8192 terms, or allocation), ECUDA. */
+int amgeig_setup_blob(int64_t n, const int32_t* rp, const int32_t* ci, const double* a, const double* m,
+                      double theta, int64_t coarse_cap, int max_levels, int device, void** blob, size_t* bytes,
+                      double* seconds);
+
+/* Release a blob returned by amgeig_setup_blob (NULL is accepted). */
+void amgeig_free_blob(void* blob);
+
 /* ---- building blocks, exposed for verification -------------------------- */
 
 /* The nwant smallest eigenpairs of the symmetric n x n matrix H (host, row-major,

@@ -52,7 +52,8 @@ def build_setup_lib(force: bool = False) -> Path:
 
 
 def cuda_sources():
-    return sorted(CUDA_DIR.glob("*.cu"))
+    # the CUDA translation units, and the host setup library's C/F splitting (used by the device setup)
+    return sorted(CUDA_DIR.glob("*.cu")) + [SETUP_SRC]
 
 
 def cuda_headers():
@@ -75,7 +76,11 @@ def build_cuda_lib(force: bool = False, jobs: int | None = None) -> Path:
     for s in srcs:
         o = objdir / (s.stem + ".o")
         objs.append(o)
-        procs.append(subprocess.Popen(["nvcc", *flags, "-c", str(s), "-o", str(o)]))
+        if s.suffix == ".cpp":
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", str(s), "-o", str(o)]
+        else:
+            cmd = ["nvcc", *flags, "-c", str(s), "-o", str(o)]
+        procs.append(subprocess.Popen(cmd))
         if jobs and len([p for p in procs if p.poll() is None]) >= jobs:
             procs[0].wait()
     rc = [p.wait() for p in procs]

@@ -61,7 +61,8 @@ EXPORTED = ["amgeig_default_options", "amgeig_load_hierarchy", "amgeig_load_hier
             "amgeig_solve", "amgeig_submit", "amgeig_poll", "amgeig_strerror", "amgeig_last_error",
             "amgeig_sym_eigh", "amgeig_apply_vcycle", "amgeig_apply_defect", "amgeig_profile_enable",
             "amgeig_profile_read", "amgeig_kernel_launches", "amgeig_sym_eigh_noalloc",
-            "amgeig_service_set_memory_limit", "amgeig_service_memory", "amgeig_tuning_report"]
+            "amgeig_service_set_memory_limit", "amgeig_service_memory", "amgeig_tuning_report",
+            "amgeig_setup_blob", "amgeig_free_blob"]
 
 
 def library_path() -> str:
@@ -100,6 +101,11 @@ def lib():
         L.amgeig_sym_eigh_noalloc.restype = i32
         L.amgeig_service_set_memory_limit.argtypes = [ctypes.c_uint64]
         L.amgeig_tuning_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.amgeig_setup_blob.argtypes = [ctypes.c_int64, vp, vp, vp, vp, dbl, ctypes.c_int64, i32, i32,
+                                        ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_size_t), vp]
+        L.amgeig_setup_blob.restype = i32
+        L.amgeig_free_blob.argtypes = [vp]
+        L.amgeig_free_blob.restype = None
         L.amgeig_service_memory.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
         L.amgeig_kernel_launches.argtypes = []
         L.amgeig_kernel_launches.restype = ctypes.c_uint64
@@ -204,6 +210,27 @@ def amgeig_tuning_report(h) -> list:
     buf = ctypes.create_string_buffer(1 << 20)
     _check(lib().amgeig_tuning_report(h, buf, len(buf)), "amgeig_tuning_report")
     return json.loads(buf.value.decode())
+
+
+def amgeig_setup_blob(row_ptr, col_idx, a_vals, m_vals, theta: float = 0.25, coarse_cap: int = 50,
+                      max_levels: int = 25, device: int = 0):
+    """The hierarchy blob of (A, M) built by the device setup; returns (blob bytes, total s, C/F split s)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    av = np.ascontiguousarray(a_vals, dtype=np.float64)
+    mv = np.ascontiguousarray(m_vals, dtype=np.float64)
+    out = ctypes.c_void_p()
+    nbytes = ctypes.c_size_t()
+    secs = np.zeros(2)
+    L = lib()
+    _check(L.amgeig_setup_blob(rp.shape[0] - 1, rp.ctypes.data, ci.ctypes.data, av.ctypes.data, mv.ctypes.data,
+                               theta, coarse_cap, max_levels, device, ctypes.byref(out), ctypes.byref(nbytes),
+                               secs.ctypes.data), "amgeig_setup_blob")
+    try:
+        blob = ctypes.string_at(out, nbytes.value)
+    finally:
+        L.amgeig_free_blob(out)
+    return blob, float(secs[0]), float(secs[1])
 
 
 def amgeig_service_memory() -> Tuple[int, int]:
