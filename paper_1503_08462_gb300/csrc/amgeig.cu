@@ -1027,7 +1027,7 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
   key.append(reinterpret_cast<const char*>(pre.data()), sizeof(void*) * pre.size());
   auto it = w->graphs.find(key);
   if (it == w->graphs.end()) {
-    const unsigned long long k0 = launch_count();
+    const unsigned long long k0 = thread_launch_count();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     const int rc = body();
     cudaGraph_t g = nullptr;
@@ -1043,8 +1043,9 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return fail(AMGEIG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
     rec.post = roles(w);
-    // the kernels were counted when captured; the launch below runs them
-    rec.kernels = launch_count() - k0;
+    // the kernels were counted when captured (on this thread; other threads
+    // launch meanwhile); the launch below runs them
+    rec.kernels = thread_launch_count() - k0;
     it = w->graphs.emplace(key, std::move(rec)).first;
     CK(cudaGraphLaunch(it->second.exec, st));
     return AMGEIG_OK;

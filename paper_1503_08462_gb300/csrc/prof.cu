@@ -65,7 +65,10 @@ void ensure_dynamic_smem(const void* func, size_t bytes) {
     cur = bytes;
 }
 
+thread_local unsigned long long g_thread_launches = 0;  // kernels launched by the calling thread
+
 unsigned long long launch_count() { return prof().launches.load(); }
+unsigned long long thread_launch_count() { return g_thread_launches; }
 void add_launches(unsigned long long n) { prof().launches += n; }
 bool profiling_on() { return prof().on.load(std::memory_order_relaxed); }
 
@@ -78,6 +81,7 @@ LevelTag::~LevelTag() { g_level = prev_; }
 ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int kernels) : st_(st), slot_(-1) {
   Profiler& p = prof();
   p.launches += static_cast<unsigned long long>(kernels);
+  g_thread_launches += static_cast<unsigned long long>(kernels);
   if (g_depth++ > 0) return;
   if (!p.on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(p.mu);

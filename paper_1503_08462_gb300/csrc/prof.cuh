@@ -41,6 +41,8 @@ int set_last_error(int code, const char* msg);
 // to add the kernels of a replayed CUDA graph to it (their ProfScopes ran once,
 // when the graph was captured), and whether per-launch event timing is on.
 unsigned long long launch_count();
+// kernels launched by the calling thread so far (what a capture on this thread records)
+unsigned long long thread_launch_count();
 void add_launches(unsigned long long n);
 bool profiling_on();
 
