@@ -380,6 +380,7 @@ def run_stream(args):
         t_arr, t_done, codes, span = run_batch(reqs, arrivals)
     launches = ae.amgeig_kernel_launches() - launches0
     lat_ms = (t_done - t_arr) * 1e3
+    kk = np.array([k for k, _ in reqs])
     pairs = sum(q for _, q in reqs)
     span = replica_max(dist, span, f"cuda:{local}")
     if rank == 0:
@@ -397,6 +398,10 @@ def run_stream(args):
             "p99_target_ms": P99_TARGET_MS, "p99_met": bool(np.percentile(lat_ms, 99) <= P99_TARGET_MS),
             "batching": bool(args.batch),
             "requests_per_s": args.requests / span,
+            "by_problem": [{"domain": pool[k][0], "N": pool[k][1], "requests": int(np.sum(kk == k)),
+                            "p50_ms": float(np.percentile(lat_ms[kk == k], 50)) if np.any(kk == k) else None,
+                            "p99_ms": float(np.percentile(lat_ms[kk == k], 99)) if np.any(kk == k) else None}
+                           for k in range(len(pool))],
             "statuses": {str(c): codes.count(c) for c in set(codes)},
             "not_ok": [{"domain": pool[k][0], "N": pool[k][1], "q": q, "status": c}
                        for (k, q), c in zip(reqs, codes) if c != 0][:40],
