@@ -98,9 +98,11 @@ typedef struct {
                             while profiling is enabled or when the caller's stream is capturing */
   int autotune;          /* mixed precisions: 1 (default) = the first solve at each block width times
                             every lane layout of the float32 smoothing and transfer kernels on each
-                            level's operators and keeps the fastest in the hierarchy (same bits:
-                            the layout does not change the order of any sum); 0 = no tuning now
-                            (layouts tuned by earlier solves stay in use) */
+                            level's operators (lanes per row, columns per lane, nonzero streams per
+                            row) and keeps the fastest in the hierarchy; layouts with another stream
+                            count add a row's terms in another order (float32 rounding in the
+                            V-cycle; later solves on the hierarchy repeat bit for bit); 0 = no
+                            tuning now (layouts tuned by earlier solves stay in use) */
   int batch;             /* amgeig_submit only: 1 (default) = the request may share one solve with
                             other queued requests on the same hierarchy whose options agree but for
                             q, q_extra, tol and max_corrections (the shared solve takes the widest

@@ -1118,9 +1118,11 @@ int ensure_shift(amgeig_hierarchy_t* h, double sigma, cudaStream_t st) {
 // Launch shapes of the float32 V-cycle kernels for this solve's width, tuned on
 // its first mixed solve at that width (smoothing on every A_l, restriction R_l
 // and prolongation P_l): every lane layout is timed on the level's own
-// operator and the fastest is kept in the hierarchy.  The layout does not
-// change the arithmetic (each column's sum runs over the row in the same
-// order), so results keep their bits.  Before any capture; under the lock.
+// operator and the fastest is kept in the hierarchy.  Layouts that split a
+// row's nonzeros over several lane streams add its terms in another order, so
+// tuned solves can differ from untuned ones by float32 rounding in the V-cycle
+// (the fixed point is the same); a hierarchy keeps its choice, so its solves
+// repeat bit for bit.  Before any capture; under the lock.
 int ensure_tuned(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
   const int w4 = w->ld32 / 4;
   if (w4 < 1 || w4 > 32 || h->tuned_w4[w4]) return AMGEIG_OK;

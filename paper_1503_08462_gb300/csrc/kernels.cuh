@@ -21,8 +21,8 @@ struct DevCsr {
   float2* m2 = nullptr;   // m64 as float-float pairs
   __nv_bfloat16* vbf = nullptr;  // v64 rounded to bfloat16 (the V-cycle's operators, AMGEIG_MIXED_BF16)
   // launch shape of the float32 V-cycle kernels on this operator, per block width in float4
-  // columns w4 <= 32, chosen by the autotuner: (log2 column lanes) * 4 + cpt (the nonzero
-  // streams per row stay the rule's); 0 = not tuned (the rule applies)
+  // columns w4 <= 32, chosen by the autotuner: (log2 streams) << 5 | (log2 column lanes per
+  // stream) << 2 | columns per lane; 0 = not tuned (the rule applies)
   unsigned char tuned[33] = {};
 };
 

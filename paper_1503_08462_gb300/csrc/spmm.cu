@@ -321,13 +321,13 @@ F4Geo f4_geo(int w4, long long rows, long long nnz = 0) {
 
 // the operator's tuned shape at this width, else the rule
 F4Geo geo_of(const DevCsr& S, int w4) {
-  const F4Geo rule = f4_geo(w4, S.rows, S.nnz);
   if (w4 >= 1 && w4 <= 32 && S.tuned[w4]) {
     const int v = S.tuned[w4];
-    // tuned: the lane count per stream and the columns per lane; the streams stay the rule's
-    return F4Geo{(1 << (v >> 2)) * rule.S, v & 3, rule.S};
+    // tuned: column lanes per stream (log2, bits 2-4), columns per lane (bits 0-1), streams (log2, bits 5-6)
+    const int streams = 1 << ((v >> 5) & 3);
+    return F4Geo{(1 << ((v >> 2) & 7)) * streams, v & 3, streams};
   }
-  return rule;
+  return f4_geo(w4, S.rows, S.nnz);
 }
 
 __device__ __forceinline__ void fma4(float s, const float4& x, float4& acc) {
@@ -1120,25 +1120,30 @@ TuneResult autotune_f4(DevCsr& S, int kind, int w4, const float* dinv, const flo
     }
     return best * 1000.f;
   };
-  // every power-of-two column-lane count whose share per lane is 1..3 float4s, with the
-  // rule's nonzero streams (which fix the order of each row's sums: the bits stay the rule's)
+  // every power-of-two column-lane count whose share per lane is 1..3 float4s, times 1, 2
+  // or 4 nonzero streams per row (at most a warp per row).  The streams change the order
+  // in which a row's terms are added, so a tuned shape can round differently from the
+  // rule's (a float32 rounding difference); a given shape always gives the same bits.
   float best = 1e30f;
-  for (int gc = 1; gc * rule.S <= 32; gc <<= 1) {
-    const int cpt = (w4 + gc - 1) / gc;
-    if (cpt > 3 || (gc > 1 && gc / 2 >= w4)) continue;
-    const float us = time_us(F4Geo{gc * rule.S, cpt, rule.S});
-    if (us < best) {
-      best = us;
-      r.G = gc * rule.S;
-      r.cpt = cpt;
+  for (int streams = 1; streams <= 4; streams <<= 1)
+    for (int gc = 1; gc * streams <= 32; gc <<= 1) {
+      const int cpt = (w4 + gc - 1) / gc;
+      if (cpt > 3 || (gc > 1 && gc / 2 >= w4)) continue;
+      const float us = time_us(F4Geo{gc * streams, cpt, streams});
+      if (us < best) {
+        best = us;
+        r.G = gc * streams;
+        r.cpt = cpt;
+        r.S = streams;
+      }
     }
-  }
   r.us = best;
   r.rule_us = time_us(rule);
   if (r.G > 0 && cudaGetLastError() == cudaSuccess) {
-    int lg = 0;
-    while ((1 << lg) < r.G / rule.S) ++lg;
-    S.tuned[w4] = static_cast<unsigned char>(lg * 4 + r.cpt);
+    int lg = 0, ls = 0;
+    while ((1 << lg) < r.G / r.S) ++lg;
+    while ((1 << ls) < r.S) ++ls;
+    S.tuned[w4] = static_cast<unsigned char>((ls << 5) | (lg << 2) | r.cpt);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
