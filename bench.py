@@ -52,16 +52,33 @@ ACCURATE_CLASSES = {"defect", "augment", "gram", "recombine", "chain"}
 # keyed by (workload, precision, v_cycles, q_extra, class) and by the SHA-256 of the source file that
 # holds the class's kernels when the counters were taken: a later change to that file makes the
 # figure stale, and the bench line then reports traffic as null.
-TRAFFIC_SOURCES = {"smooth": "paper_1503_08462_gb300/csrc/spmm.cu", "transfer": "paper_1503_08462_gb300/csrc/spmm.cu"}
-DRAM_TRAFFIC_PER_LAUNCH = {}
+# The source text a class's kernels are defined by: (file, first line of the span, first line after it).
+TRAFFIC_SOURCES = {
+    "smooth": ("paper_1503_08462_gb300/csrc/spmm.cu", "__device__ __forceinline__ void reduce_streams",
+               "__global__ void __launch_bounds__(kThreads, 6) k_spmm_f4"),
+}
+# smooth: the 16 k_smooth_f4 launches of one 28-column V-cycle from the finest level of the L-shape
+# h = 1/512 hierarchy (bench.py --profile-case vcycle --level 0), 62.78 MB per launch on average
+# (profiles/k_smooth_f4_level0_lshape_h512.md)
+DRAM_TRAFFIC_PER_LAUNCH = {
+    ("lshape_h512_q20", "mixed", 2, 8, "smooth"):
+        (62.78e6, "b3dd21e339d3608462668e9f7edfff202524a1ff8f244cc127f32cc415bba1a9"),
+}
 
 
 def source_sha(cls):
-    path = TRAFFIC_SOURCES.get(cls)
-    if path is None:
+    """SHA-256 of the source span that defines a class's kernels (None if unknown or not found)."""
+    spec = TRAFFIC_SOURCES.get(cls)
+    if spec is None:
         return None
-    with open(os.path.join(ROOT, path), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+    path, first, after = spec
+    with open(os.path.join(ROOT, path)) as fh:
+        text = fh.read()
+    i = text.find(first)
+    j = text.find(after, i + 1) if i >= 0 else -1
+    if i < 0 or j < 0:
+        return None
+    return hashlib.sha256(text[i:j].encode()).hexdigest()
 
 WORKLOADS = {
     # name: builder, its arguments, q, q_extra, coarse-level cap of the AMG setup,
@@ -332,11 +349,11 @@ def run_stream(args):
         # count keeps its requests converging within the correction limit
         return 4 + q // 2
 
-    def opt_for(k, q):
+    def opt_for(k, q, batch=None):
         return ae.options(q_extra=q_extra_for(q), max_corrections=60, precision=ae.AMGEIG_MIXED_FP32, v_cycles=2,
-                          coarse_modes=min(64, pool[k][3]), batch=args.batch)
+                          coarse_modes=min(64, pool[k][3]), batch=args.batch if batch is None else batch)
 
-    def run_batch(reqs, arrivals=None):
+    def run_batch(reqs, arrivals=None, batch=None):
         """Submit (at the given arrival times, else all at once) and poll to completion;
         returns per-request (arrival, done) times, statuses and the wall span."""
         n = len(reqs)
@@ -352,7 +369,7 @@ def run_stream(args):
             while nxt < n and (arrivals is None or arrivals[nxt] <= now):
                 k, q = reqs[nxt]
                 t_arr[nxt] = arrivals[nxt] if arrivals is not None else now
-                ids[ae.amgeig_submit(hs[k].handle, q, tol, opt_for(k, q))] = nxt
+                ids[ae.amgeig_submit(hs[k].handle, q, tol, opt_for(k, q, batch))] = nxt
                 nxt += 1
             for rid in list(ids):
                 j = ids[rid]
@@ -368,8 +385,10 @@ def run_stream(args):
     # warm-up: every problem once at the widest q (sizes its resident workspace)
     run_batch([(k, 32) for k in range(len(pool))])
     # service rate: a saturated burst
+    # the service rate on a saturated burst of requests each solved on its own (no shared solves: the
+    # rate a stream sustains without counting on requests to coincide); arrivals at 70% of it
     burst = [(int(rng.integers(0, len(pool))), int(rng.integers(1, 33))) for _ in range(4 * len(pool))]
-    _, _, _, span = run_batch(burst)
+    _, _, _, span = run_batch(burst, batch=0)
     mu = len(burst) / span
     lam = 0.7 * mu
     reqs = [(int(rng.integers(0, len(pool))), int(rng.integers(1, 33))) for _ in range(args.requests)]

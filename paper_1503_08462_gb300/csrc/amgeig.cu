@@ -1706,7 +1706,17 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   const int n = h->nlev;
   for (auto& L : levels) h->sizes.push_back(L.rows);
   h->dn = static_cast<int>(h->sizes[n - 1]);
-  CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  {
+    // small hierarchies get the higher stream priority: when solves on several
+    // hierarchies share the GPU (the request service), the short kernels of a
+    // small problem are scheduled ahead of a large problem's long ones, which
+    // keeps small requests' latency near their own solve time
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));  // hi is the numerically smallest, the highest priority
+    const int64_t N0 = h->sizes[0];
+    const int prio = N0 <= 65536 ? hi : (N0 <= 262144 ? (lo + hi) / 2 : lo);
+    CK(cudaStreamCreateWithPriority(&h->stream, cudaStreamNonBlocking, prio));
+  }
   auto& m = h->mem;
   m.st = h->stream;
   // The coarsest level goes first, on two more streams: the GPU factors M_n
