@@ -219,17 +219,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(blob, q, qe, n_corr, sample_corr=2):
-    """The CPU oracle on the same hierarchy: the nested phase plus `sample_corr`
-    finest-level corrections, scaled to `n_corr` corrections.  Runs in the calling
-    process; oracle_samples() runs it single-threaded in a child."""
+def oracle_sample(blob, q, qe, n_corr, full=True, v_cycles=2, modes=0, sample_corr=2):
+    """The CPU oracle on the same hierarchy with the GPU run's settings (buffer vectors, V-cycles per
+    correction, coarse modes).  full: one complete solve with exactly n_corr finest-level corrections
+    after the nested phase, timed; otherwise the nested phase plus `sample_corr` corrections, scaled to
+    n_corr.  Runs in the calling process; oracle_samples() runs it in a child with fixed thread counts.
+    Returns (eigenpairs/s, seconds per solve, nested-phase s, s per correction, wall s)."""
     from oracle import amg_oracle as O
 
     oh = O.read_blob(blob)
+    kw = dict(q_extra=qe, v_cycles=v_cycles, coarse_modes=modes)
+    if full:
+        t0 = time.perf_counter()
+        O.solve(oh, q, tol=0.0, opts=O.Options(fixed_corrections=n_corr, **kw))
+        wall = time.perf_counter() - t0
+        return q / wall, wall, None, None, wall
     t0 = time.perf_counter()
-    O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1))
+    O.solve(oh, q, tol=0.0, opts=O.Options(fixed_corrections=1, **kw))
     t1 = time.perf_counter()
-    O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=1 + sample_corr))
+    O.solve(oh, q, tol=0.0, opts=O.Options(fixed_corrections=1 + sample_corr, **kw))
     t2 = time.perf_counter()
     per_corr = (t2 - t1 - (t1 - t0)) / sample_corr
     nested = (t1 - t0) - per_corr
@@ -241,18 +249,23 @@ SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_N
                      "VECLIB_MAXIMUM_THREADS": "1", "NUMEXPR_NUM_THREADS": "1"}
 
 
-def oracle_samples(workload, cap, qe, n_corr, count):
-    """`count` oracle samples in a fresh single-threaded interpreter (BLAS thread
-    counts are fixed by the environment before numpy loads; the child builds the
-    same seeded workload and never touches the GPU).  Returns a list of
-    oracle_sample() tuples."""
+def all_threads_env():
+    n = str(os.cpu_count() or 1)
+    return {k: n for k in SINGLE_THREAD_ENV}
+
+
+def oracle_samples(workload, cap, qe, n_corr, count, full=True, threads=1, v_cycles=2, modes=0):
+    """`count` oracle samples in a fresh interpreter whose BLAS / OpenMP thread counts are fixed by the
+    environment before numpy loads (1, or every core); the child builds the same seeded workload and
+    never touches the GPU.  Returns a list of oracle_sample() tuples."""
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--workload", workload,
-           "--reference-corrections", str(n_corr), "--steps", str(count), "--warmup", "0"]
+           "--reference-corrections", str(n_corr), "--steps", str(count), "--warmup", "0",
+           "--v-cycles", str(v_cycles), "--coarse-modes", str(modes), "--oracle-mode", "full" if full else "sample"]
     if cap is not None:
         cmd += ["--cap", str(cap)]
     if qe is not None:
         cmd += ["--q-extra", str(qe)]
-    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    env = dict(os.environ, **(SINGLE_THREAD_ENV if threads == 1 else all_threads_env()))
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True, timeout=1800)
     return [tuple(x) for x in json.loads(out.stdout.strip().splitlines()[-1])]
 
@@ -262,28 +275,39 @@ def oracle_child(args):
     p, blob, h, q, qe, tol = build_workload(args.workload, args.cap)
     if args.q_extra is not None:
         qe = args.q_extra
-    res = [oracle_sample(blob, q, qe, args.reference_corrections) for _ in range(args.steps)]
+    modes = args.coarse_modes if args.coarse_modes is not None else WORKLOADS[args.workload]["modes"]
+    res = [oracle_sample(blob, q, qe, args.reference_corrections, full=args.oracle_mode == "full",
+                         v_cycles=args.v_cycles, modes=modes) for _ in range(args.steps)]
     print(json.dumps(res), flush=True)
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle (as it stands) on this workload, rank 0 only."""
+    """--impl reference: the CPU oracle (as it stands) on this workload, rank 0 only: each timed step one
+    complete oracle solve with the GPU run's settings and correction count (one thread); the warm-up steps
+    run the short sample instead (the oracle has nothing to warm up)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     p, blob, h, q, qe, tol = build_workload(args.workload)
     n_corr = args.reference_corrections
-    samples = oracle_samples(args.workload, None, qe, n_corr, args.warmup + args.steps)
-    vals = [smp[0] for smp in samples[args.warmup:]]
+    modes = WORKLOADS[args.workload]["modes"]
+    if args.warmup:
+        oracle_samples(args.workload, None, qe, n_corr, args.warmup, full=False, v_cycles=args.v_cycles,
+                       modes=modes)
+    samples = oracle_samples(args.workload, None, qe, n_corr, args.steps, full=True, v_cycles=args.v_cycles,
+                             modes=modes)
+    vals = [smp[0] for smp in samples]
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": "eigenpairs/s", "value": value, "unit": "eigenpairs/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": p.n, "q": q, "q_extra": qe, "levels": h.sizes},
+        "config": {"workload": args.workload, "N": p.n, "q": q, "q_extra": qe, "levels": h.sizes,
+                   "v_cycles": args.v_cycles, "coarse_modes": modes, "corrections": n_corr},
         "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: nested phase + 2 finest corrections of the FP64 oracle "
-                                   f"(one thread), scaled to {n_corr} corrections"},
+                         "sample": f"per timed step: one complete FP64 oracle solve (one thread), nested phase "
+                                   f"+ {n_corr} finest corrections, {args.v_cycles} V-cycles each, "
+                                   f"{modes or 'all'} coarse modes"},
         "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -505,6 +529,7 @@ def main():
                     help="Rayleigh quotients of the final vectors: 1 float64, 2 compensated float64 "
                          "(workload default)")
     ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-mode", choices=["full", "sample"], default="full", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["vcycle", "defect"], default=None,
                     help="run one V-cycle (or one defect) from --level on the L-shape workload for a "
                          "single-kernel profiler capture, and nothing else")
@@ -749,10 +774,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            v, est, nested, per_corr, wall_c = oracle_samples(args.workload, args.cap, qe, corrections, 1)[0]
+            v, wall_c, _, _, _ = oracle_samples(args.workload, args.cap, qe, corrections, 1, full=True,
+                                                v_cycles=args.v_cycles, modes=modes)[0]
+            ncores = os.cpu_count() or 1
+            va, wall_a, _, _, _ = oracle_samples(args.workload, args.cap, qe, corrections, 1, full=True,
+                                                 threads=ncores, v_cycles=args.v_cycles, modes=modes)[0]
             cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-                   "sample": f"FP64 oracle, 1 thread: nested phase ({nested:.1f}s) + 2 finest corrections "
-                             f"({per_corr:.1f}s each) measured, scaled to the {corrections} corrections of this run"}
+                   "sample": f"one complete FP64 oracle solve with this run's settings and its {corrections} "
+                             f"finest corrections ({wall_c:.1f} s), one thread",
+                   "all_cores": {"value": va, "cores": ncores, "seconds": wall_a,
+                                 "note": "BLAS/OpenMP threads on every core (the oracle's sparse products "
+                                         "stay single-threaded)"}}
         except Exception as exc:  # the baseline must not hide the GPU result
             cpu = {"value": None, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
