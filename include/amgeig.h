@@ -115,6 +115,12 @@ typedef struct {
                             the defect is unchanged, lambda M u - A u).  sigma must lie below the
                             lowest eigenvalue of (A_n, M_n) (EINVAL otherwise); with the
                             l1-Jacobi smoother only, not with AMGEIG_MIXED_BF16 */
+  int krylov;            /* depth s of the correction space (the remark after Algorithm 3.1, "V_n +
+                            Krylov spaces"): 1 (default) = the paper's V_n + span(V); 2 = V_n +
+                            span(T U, T^2 U), T the step's inexact inverse iteration (m V-cycles on
+                            the defect with the step's Ritz values), the pencil on the block
+                            [T U | T^2 U - T U] of 2 (q + q_extra) columns; needs 2 (q + q_extra) <=
+                            128, and q + q_extra <= 32 on the mixed paths (EINVAL otherwise) */
 } amgeig_options;
 
 #define AMGEIG_SMOOTHER_L1_JACOBI 0

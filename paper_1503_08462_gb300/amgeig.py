@@ -43,7 +43,8 @@ class amgeig_options(ctypes.Structure):
                 ("post_sweeps", ctypes.c_int), ("q_extra", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fixed_corrections", ctypes.c_int), ("coarse_modes", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("n1", ctypes.c_int), ("refine", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("batch", ctypes.c_int), ("shift", ctypes.c_double)]
+                ("autotune", ctypes.c_int), ("batch", ctypes.c_int), ("shift", ctypes.c_double),
+                ("krylov", ctypes.c_int)]
 
 
 class amgeig_prof_entry(ctypes.Structure):

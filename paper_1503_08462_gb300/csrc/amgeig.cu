@@ -452,12 +452,14 @@ struct SolveWork {
   bool shifted = false;                       // the current solve's V-cycle runs on A_l - sigma M_l
   bool bf16 = false;                          // the current solve reads bfloat16 operator values
   int qcap = 0;  // column capacity: the buffers serve any solve with q + q_extra <= qcap
+  int bcap = 0;  // augmentation width capacity (qcap, or a Krylov block's 2 (q + q_extra))
   int qt = 0;    // columns of the current solve (every block's row stride)
   int ld32 = 0;  // row stride of the float32 V-cycle blocks: qt rounded up to a multiple of 4
   int precision = -1;
   int vcycles = 1;
   DeviceBuffers mem;
   double *U = nullptr, *Ualt = nullptr, *V = nullptr, *W = nullptr;
+  double* K = nullptr;  // the Krylov block [V1 | E] (rows x 2 qt), when the capacity allows one
   std::vector<double*> B64, X64, T64, D64, E64;  // per level (FP64 V-cycle)
   std::vector<float*> B32, X32, T32, D32, E32;   // per level (FP32 V-cycle)
   std::vector<double*> WC, PX;                   // restriction chain [N][2q], prolongation chain [N][q]
@@ -488,9 +490,12 @@ struct SolveWork {
 // dry: allocate nothing, only add up in w->mem.held (and pw_bytes) what the
 // workspace would hold
 int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, std::unique_ptr<SolveWork>& out,
-                   bool dry = false) {
+                   bool dry = false, int border = 0) {
   auto w = std::make_unique<SolveWork>();
   w->mem.dry = dry;
+  // the augmentation's width: the iterate's qt columns, or a Krylov block of up to 2 qt
+  const int bw = std::max(qt, border);
+  w->bcap = bw;
   w->qcap = qt;
   w->qt = qt;
   w->ld32 = (qt + 3) & ~3;
@@ -502,7 +507,8 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->U, N0 * qt));
   CK(m.alloc(&w->Ualt, N0 * qt));
   CK(m.alloc(&w->V, N0 * qt));
-  CK(m.alloc(&w->W, N0 * 2 * qt));
+  CK(m.alloc(&w->W, N0 * 2 * bw));
+  if (bw > qt) CK(m.alloc(&w->K, N0 * bw));
   w->B64.assign(n, nullptr);
   w->X64.assign(n, nullptr);
   w->T64.assign(n, nullptr);
@@ -534,7 +540,7 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
         CK(m.alloc(&w->E32[l], Nl * w->ld32));
       }
     }
-    if (l > 0) CK(m.alloc(&w->WC[l], Nl * 2 * qt));
+    if (l > 0) CK(m.alloc(&w->WC[l], Nl * 2 * bw));
     CK(m.alloc(&w->PX[l], Nl * qt));
   }
   const int blocks_max = ceil_div(N0, 8) + 1;  // defect launches use >= 8 rows per block
@@ -544,25 +550,25 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->relres, qt));
   CK(m.alloc(&w->lam, qt));
   CK(m.alloc(&w->mu, qt));
-  CK(m.alloc(&w->C, static_cast<size_t>(h->dn) * 2 * qt));
-  CK(m.alloc(&w->G, static_cast<size_t>(qt) * 2 * qt));
+  CK(m.alloc(&w->C, static_cast<size_t>(h->dn) * 2 * bw));
+  CK(m.alloc(&w->G, static_cast<size_t>(bw) * 2 * bw));
   size_t gs = 0;
   for (int l = 0; l < n; ++l)
-    for (int qq = 1; qq <= qt; ++qq) {  // any width up to the capacity (the chunking depends on it)
+    for (int qq = 1; qq <= bw; ++qq) {  // any width up to the capacity (the chunking depends on it)
       gs = std::max(gs, gram_scratch_doubles(static_cast<int>(h->sizes[l]), qq, 2 * qq));
       gs = std::max(gs, gram_df_scratch_doubles(static_cast<int>(h->sizes[l]), qq, 2 * qq));
     }
   CK(m.alloc(&w->gsc, gs));
   CK(m.alloc(&w->Xc, static_cast<size_t>(h->dn) * qt));
-  CK(m.alloc(&w->Yv, static_cast<size_t>(qt) * qt));
+  CK(m.alloc(&w->Yv, static_cast<size_t>(bw) * qt));
   CK(m.alloc(&w->sign, qt));
   CK(m.alloc(&w->flags, 4));
   CK(m.alloc(&w->perm, qt));
   CK(m.alloc(&w->nfallback, 1));
-  w->pw_bytes = pencil_work_bytes(h->dn, qt);
+  w->pw_bytes = pencil_work_bytes(h->dn, bw);
   if (!dry) {
     cudaError_t e;
-    w->pw = pencil_work_create(h->dn, qt, &e);
+    w->pw = pencil_work_create(h->dn, bw, &e);
     if (!w->pw) return fail(AMGEIG_ENOMEM, std::string("pencil workspace: ") + cudaGetErrorString(e));
   }
   out = std::move(w);
@@ -572,16 +578,18 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
 // Keep a workspace that can hold qt columns: a smaller solve reuses the buffers
 // of a larger one (all layouts follow the current qt), so a stream of requests
 // with varying q on one hierarchy allocates only when its largest width grows.
-int ensure_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles) {
+int ensure_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, int border = 0) {
   // the bfloat16 option only swaps the V-cycle's operator values: same workspace
   if (precision == AMGEIG_MIXED_BF16) precision = AMGEIG_MIXED_FP32;
   SolveWork* w = h->ws.get();
-  if (!w || w->qcap < qt || w->precision != precision || w->vcycles < vcycles) {
+  const int bw = std::max(qt, border);
+  if (!w || w->qcap < qt || w->bcap < bw || w->precision != precision || w->vcycles < vcycles) {
     const bool same = w && w->precision == precision;
     const int cap = same ? std::max(qt, w->qcap) : qt;
+    const int bcap = same ? std::max(bw, w->bcap) : bw;
     const int vc = same ? std::max(vcycles, w->vcycles) : vcycles;
     h->ws.reset();
-    const int rc = make_workspace(h, cap, precision, vc, h->ws);
+    const int rc = make_workspace(h, cap, precision, vc, h->ws, false, bcap);
     if (rc) return rc;
     w = h->ws.get();
   }
@@ -858,6 +866,32 @@ void amg_correction(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
   add_to_v(U, E[k], static_cast<int>(h->sizes[k]), q, wd, V, st);
 }
 
+// The correction of m V-cycles for A_k x = B[k] from x = 0 (defect form, as in
+// amg_correction, without adding it to an iterate): the pointer to x (row
+// stride width_of).  B[k] holds the defect on entry.
+template <typename T>
+const T* amg_x(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, cudaStream_t st) {
+  auto& B = VBufs<T>::B(w);
+  auto& X = VBufs<T>::X(w);
+  auto& D = VBufs<T>::D(w);
+  auto& E = VBufs<T>::E(w);
+  if (o.v_cycles <= 1) {
+    vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, nullptr, nullptr, st);
+    return X[k];
+  }
+  const int wd = width_of(w, static_cast<T*>(nullptr));
+  const long long cnt = h->sizes[k] * wd;
+  LevelTag tag(k);
+  cudaMemcpyAsync(D[k], B[k], sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(E[k], 0, sizeof(T) * cnt, st);
+  for (int c = 0; c < o.v_cycles; ++c) {
+    vcycle<T>(h, w, k, o.pre_sweeps, o.post_sweeps, false, nullptr, nullptr, st);
+    axpy(X[k], cnt, E[k], st);
+    if (c + 1 < o.v_cycles) residual(vop(h, w, k), D[k], E[k], wd, B[k], st, w->bf16);
+  }
+  return E[k];
+}
+
 }  // namespace
 
 amgeig_hierarchy_t::~amgeig_hierarchy_t() {
@@ -877,7 +911,65 @@ namespace {
 // pair is already in B[k] (float64 or float32 by precision).
 float2* as_df(double* p) { return reinterpret_cast<float2*>(p); }
 
+// Step 2 on the depth-2 Krylov space (the remark after Algorithm 3.1): V_n +
+// span(T U, T^2 U) = V_n + span(V1, E) with V1 = T U (step 1) and E the
+// correction T V1 - V1 (m V-cycles on the defect of V1 with the same lambda);
+// the pencil is taken on the block K = [V1 | E] (Rayleigh-Ritz depends only on
+// the span) and its q + q_extra smallest pairs recombined as I_n^k Xc + K Y.
+int correction_tail_krylov(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, cudaStream_t st) {
+  const int q = w->qt, nb = 2 * q;
+  const int n = h->nlev;
+  const int Nk = static_cast<int>(h->sizes[k]);
+  const int modes = (o.coarse_modes > 0 && o.coarse_modes < h->dn) ? o.coarse_modes : h->dn;
+  int nbk = 0;
+  if (o.precision == AMGEIG_FP64) {
+    amg_correction<double>(h, w, k, o, w->U, w->V, st);
+    launch_defect_f64(h->A[k], w->V, q, w->lam, w->B64[k], nullptr, &nbk, st);
+    const double* E = amg_x<double>(h, w, k, o, st);
+    launch_pack_krylov_f64(Nk, w->V, E, q, q, w->K, st);
+    launch_dual_spmm(h->A[k], w->K, nb, w->W, st);
+    launch_gram(Nk, w->K, nb, w->W, 2 * nb, w->gsc, w->G, st, false);
+    const double* cur = w->W;
+    for (int l = k; l < n - 1; ++l) {
+      launch_spmm_f64(h->R[l], cur, 2 * nb, w->WC[l + 1], false, st, P_CHAIN);
+      cur = w->WC[l + 1];
+    }
+    launch_pencil_solve(w->pw, h->dn, modes, nb, cur, nullptr, w->G, h->Zdf, h->theta, w->mu, w->Xc, nullptr,
+                        w->Yv, h->dstatus, st, w->nfallback, q);
+    const double* px = w->Xc;
+    for (int l = n - 2; l >= k; --l) {
+      launch_spmm_f64(h->P[l], px, q, w->PX[l], false, st, P_CHAIN);
+      px = w->PX[l];
+    }
+    launch_recombine_wide(Nk, px, w->K, nb, w->Yv, q, w->U, st);
+  } else {
+    amg_correction<float>(h, w, k, o, w->U, w->V, st);
+    launch_defect_df(h->A[k], as_df(w->V), q, w->lam, w->B32[k], w->ld32, nullptr, &nbk, st);
+    const float* E = amg_x<float>(h, w, k, o, st);
+    launch_pack_krylov_df(Nk, as_df(w->V), E, w->ld32, q, as_df(w->K), st);
+    launch_dual_spmm_df(h->A[k], as_df(w->K), nb, as_df(w->W), st);
+    launch_gram_df(Nk, as_df(w->K), nb, as_df(w->W), 2 * nb, w->gsc, w->G, st);
+    const float2* cur = as_df(w->W);
+    for (int l = k; l < n - 1; ++l) {
+      launch_spmm_df(h->R[l], cur, 2 * nb, as_df(w->WC[l + 1]), false, st, P_CHAIN);
+      cur = as_df(w->WC[l + 1]);
+    }
+    launch_pencil_solve(w->pw, h->dn, modes, nb, nullptr, cur, w->G, h->Zdf, h->theta, w->mu, w->Xc,
+                        as_df(w->PX[n - 1]), w->Yv, h->dstatus, st, w->nfallback, q);
+    const DevCsr& PC = h->PC[k];
+    launch_recombine_pc_df(Nk, PC.nnz, PC.rp, PC.ci, PC.d2, as_df(w->PX[n - 1]), as_df(w->K), w->Yv, q,
+                           as_df(w->U), st, nb);
+  }
+  {
+    ProfScope ps(st, P_OTHER, 16.0 * q, 0.0);
+    k_copy_d<<<1, 128, 0, st>>>(w->mu, q, w->lam);
+  }
+  CK(cudaGetLastError());
+  return AMGEIG_OK;
+}
+
 int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options& o, cudaStream_t st) {
+  if (o.krylov == 2) return correction_tail_krylov(h, w, k, o, st);
   const int q = w->qt;
   const int n = h->nlev;
   const int Nk = static_cast<int>(h->sizes[k]);
@@ -964,7 +1056,7 @@ int check_options(const amgeig_options& o) {
       (o.precision != AMGEIG_FP64 && o.precision != AMGEIG_MIXED_FP32 && o.precision != AMGEIG_MIXED_BF16) ||
       (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI && o.smoother != AMGEIG_SMOOTHER_GAUSS_SEIDEL) || o.n1 < -1 ||
       (o.refine < 0 || o.refine > 2) || (o.graphs != 0 && o.graphs != 1) || (o.autotune != 0 && o.autotune != 1) ||
-      (o.batch != 0 && o.batch != 1) || !std::isfinite(o.shift) ||
+      (o.batch != 0 && o.batch != 1) || !std::isfinite(o.shift) || (o.krylov != 1 && o.krylov != 2) ||
       (o.shift != 0.0 && (o.smoother != AMGEIG_SMOOTHER_L1_JACOBI || o.precision == AMGEIG_MIXED_BF16)))
     return fail(AMGEIG_EINVAL, "invalid options");
   return AMGEIG_OK;
@@ -1021,7 +1113,7 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
   std::vector<void*> pre = roles(w);
   std::string key = seg;
   const int cfg[] = {w->qt, w->ld32, o.precision, o.v_cycles, o.pre_sweeps, o.post_sweeps, o.smoother,
-                     o.coarse_modes, w->bf16 ? 1 : 0, w->shifted ? 1 : 0};
+                     o.coarse_modes, w->bf16 ? 1 : 0, w->shifted ? 1 : 0, o.krylov};
   key.append(reinterpret_cast<const char*>(cfg), sizeof(cfg));
   key.append(reinterpret_cast<const char*>(&o.shift), sizeof(o.shift));
   key.append(reinterpret_cast<const char*>(pre.data()), sizeof(void*) * pre.size());
@@ -1246,7 +1338,9 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
   if (n1 >= n || h->sizes[n1] < qt) return fail(AMGEIG_EINVAL, "n1 must be a level with at least q + q_extra rows");
   if (n1 < n - 1 && h->sizes[n1] > 2048)
     return fail(AMGEIG_EINVAL, "the initial level above the coarsest must have at most 2048 rows");
-  rc = ensure_workspace(h, qt, o.precision, std::max(1, o.v_cycles));
+  if (o.krylov == 2 && (2 * qt > 128 || (o.precision != AMGEIG_FP64 && qt > 32)))
+    return fail(AMGEIG_EINVAL, "the Krylov space needs 2 (q + q_extra) <= 128 (and q + q_extra <= 32 when mixed)");
+  rc = ensure_workspace(h, qt, o.precision, std::max(1, o.v_cycles), o.krylov == 2 ? 2 * qt : 0);
   if (rc) return rc;
   SolveWork* w = h->ws.get();
   w->permuted = false;
@@ -1468,7 +1562,7 @@ bool can_share(const Request& a, const Request& b) {
          x.precision == y.precision && x.v_cycles == y.v_cycles && x.pre_sweeps == y.pre_sweeps &&
          x.post_sweeps == y.post_sweeps && x.coarse_modes == y.coarse_modes && x.smoother == y.smoother &&
          x.n1 == y.n1 && x.refine == y.refine && x.graphs == y.graphs && x.autotune == y.autotune &&
-         x.shift == y.shift;
+         x.shift == y.shift && x.krylov == y.krylov;
 }
 
 // Continuous batching over hierarchies: kWorkers library threads take queued
@@ -1645,6 +1739,7 @@ void amgeig_default_options(amgeig_options* opt) {
   opt->autotune = 1;
   opt->batch = 1;
   opt->shift = 0.0;
+  opt->krylov = 1;
 }
 
 const char* amgeig_strerror(int code) {
@@ -2196,7 +2291,10 @@ size_t workspace_bytes(amgeig_hierarchy_t* h, const Request* r) {
   const int qt = r->q + r->opt.q_extra;
   const int prec = r->opt.precision == AMGEIG_FP64 ? AMGEIG_FP64 : AMGEIG_MIXED_FP32;
   std::unique_ptr<SolveWork> w;
-  if (make_workspace(h, qt, prec, std::max(1, r->opt.v_cycles), w, true) != AMGEIG_OK || !w) return 0;
+  if (make_workspace(h, qt, prec, std::max(1, r->opt.v_cycles), w, true, r->opt.krylov == 2 ? 2 * qt : 0) !=
+          AMGEIG_OK ||
+      !w)
+    return 0;
   return w->mem.held + w->pw_bytes;
 }
 

@@ -95,6 +95,12 @@ void launch_dual_spmm(const DevCsr& AM, const double* V, int q, double* W, cudaS
 // U = Xp + V Y   (Y: q x q row-major); df_arith as for the Gram
 void launch_recombine(int rows, const double* Xp, const double* V, const double* Y, int q, double* U,
                       cudaStream_t st, bool df_arith = false);
+// the same with V of nv columns (a Krylov block) and Y nv x q (float64)
+void launch_recombine_wide(int rows, const double* Xp, const double* V, int nv, const double* Y, int q, double* U,
+                           cudaStream_t st);
+// Krylov block K = [V1 | E] (rows x 2q) from V1 (rows x q) and the correction E (rows x q, row stride lde)
+void launch_pack_krylov_f64(int rows, const double* V1, const double* E, int lde, int q, double* K, cudaStream_t st);
+void launch_pack_krylov_df(int rows, const float2* V1, const float* E, int lde, int q, float2* K, cudaStream_t st);
 
 // z = x + alpha y (elementwise; z may alias neither)
 void launch_axpby_f64(const double* x, double alpha, const double* y, long long count, double* z, cudaStream_t st);
@@ -146,9 +152,10 @@ void launch_dual_spmm_df(const DevCsr& AM, const float2* V, int q, float2* W, cu
 void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool accumulate, cudaStream_t st,
                     int cls);
 // U = PC Xc + V Y with PC (CSR rows x d_n, float-float values) the composite
-// prolongation I_n^k and Xc (d_n x q) float-float; q <= 32.
+// prolongation I_n^k and Xc (d_n x q) float-float; q <= 32.  V has nv columns
+// (0: q; a Krylov block: up to 2q) and Y is nv x q.
 void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, const float2* pv, const float2* Xc,
-                            const float2* V, const double* Y, int q, float2* U, cudaStream_t st);
+                            const float2* V, const double* Y, int q, float2* U, cudaStream_t st, int nv = 0);
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
                          cudaStream_t st);
 size_t gram_df_scratch_doubles(int rows, int q, int w);
@@ -228,9 +235,12 @@ void pencil_work_destroy(PencilWork* w);
 // vectors are I_n^k Xc + V Y.  status[0] receives AMGEIG_ENOTSPD when the Gram
 // Schur complement is not positive definite.  nfallback (device, may be null)
 // is incremented when the dense eigensolver had to run.
+// p > 0 and p < q: a border of q columns (C: dn x 2q, G: q x 2q) of which the p smallest pairs are wanted
+// (mu: p, Xc: dn x p, Y: q x p); the structured iteration is then not used.
 void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64, const float2* Cdf,
                          const double* G, const float2* Zdf, const double* theta, double* mu, double* Xc,
-                         float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback = nullptr);
+                         float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback = nullptr,
+                         int p = 0);
 
 // The float64 Cholesky factor M_n = L_m L_m^T into the workspace (the first step
 // of launch_coarse_modes, and the check that M_n is positive definite: status =

@@ -1964,18 +1964,20 @@ __global__ void __launch_bounds__(512) k_std_form(int m, int q, const double* __
 }
 
 // Fallback back-map: b = L^-T b_std in place (rows m.. of evecs, n x q).
-__global__ void k_std_back(int m, int q, const df* __restrict__ L, double* __restrict__ evecs, const int* skip) {
+// b = L^-T b_std for the p wanted columns of evecs ((m + q) x p; L is the border's q x q factor)
+__global__ void k_std_back(int m, int q, int p, const df* __restrict__ L, double* __restrict__ evecs,
+                           const int* skip) {
   if (skip && *skip) return;
   const int c = threadIdx.x;
-  if (c >= q) return;
+  if (c >= p) return;
   df b[kStdMaxQ];
   for (int i = q - 1; i >= 0; --i) {
     df_acc s = acc_zero();
-    s.add(to_df(evecs[(m + i) * static_cast<long long>(q) + c]));
+    s.add(to_df(evecs[(m + i) * static_cast<long long>(p) + c]));
     for (int k = i + 1; k < q; ++k) s.fma(df_neg(L[k * q + i]), b[k]);
     b[i] = df_div(s.value(), L[i * q + i]);
   }
-  for (int i = 0; i < q; ++i) evecs[(m + i) * static_cast<long long>(q) + c] = df_to_double(b[i]);
+  for (int i = 0; i < q; ++i) evecs[(m + i) * static_cast<long long>(p) + c] = df_to_double(b[i]);
 }
 
 // Xc = Z_m (a - B b) (d_n x q) and Y = b (q x q) from evecs = [a; b].  Every
@@ -1983,7 +1985,8 @@ __global__ void k_std_back(int m, int q, const df* __restrict__ L, double* __res
 // of the rows of Xc.
 // Xc = Z_m (a - B b) and Y = b for the columns [j0, j0 + qc) (chunks keep the
 // staged blocks within shared memory when m and q are large)
-__global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0, int qc,
+// q: the border (columns of V), p: the pairs (columns of evecs, Xc and Y)
+__global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int p, int j0, int qc,
                                                     const float2* __restrict__ Zdf, const df* __restrict__ KB,
                                                     const double* __restrict__ evecs, double* __restrict__ Xc,
                                                     float2* __restrict__ Xc2, double* __restrict__ Y) {
@@ -1994,9 +1997,9 @@ __global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0
   const int q2 = 2 * q;
   for (int idx = tid; idx < q * qc; idx += nt) {
     const int r = idx / qc, jj = idx % qc;
-    const double v = evecs[static_cast<long long>(m + r) * q + j0 + jj];
+    const double v = evecs[static_cast<long long>(m + r) * p + j0 + jj];
     bs[idx] = to_df(v);
-    if (blockIdx.x == 0) Y[r * q + j0 + jj] = v;
+    if (blockIdx.x == 0) Y[r * p + j0 + jj] = v;
   }
   __syncthreads();
   for (int idx = tid; idx < m * qc; idx += nt) {
@@ -2017,7 +2020,7 @@ __global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0
     c0.merge(c1);
     c2.merge(c3);
     c0.merge(c2);
-    tmp[idx] = df_sub(to_df(evecs[static_cast<long long>(i) * q + j0 + jj]), c0.value());
+    tmp[idx] = df_sub(to_df(evecs[static_cast<long long>(i) * p + j0 + jj]), c0.value());
   }
   __syncthreads();
   const int rows = (dn + gridDim.x - 1) / gridDim.x;
@@ -2035,8 +2038,8 @@ __global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int j0
     if (i < m) s0.fma(to_df(zl[i]), tmp[i * qc + jj]);
     s0.merge(s1);
     const df v = s0.value();
-    Xc[static_cast<long long>(l) * q + j0 + jj] = df_to_double(v);
-    if (Xc2) Xc2[static_cast<long long>(l) * q + j0 + jj] = make_float2(v.hi, v.lo);
+    Xc[static_cast<long long>(l) * p + j0 + jj] = df_to_double(v);
+    if (Xc2) Xc2[static_cast<long long>(l) * p + j0 + jj] = make_float2(v.hi, v.lo);
   }
 }
 
@@ -2275,7 +2278,8 @@ void launch_syev_df_into(int n, int nwant, const double* H, double* evals, doubl
 
 void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64, const float2* Cdf,
                          const double* G, const float2* Zdf, const double* theta, double* mu, double* Xc,
-                         float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback) {
+                         float2* Xcdf, double* Y, int* status, cudaStream_t st, int* nfallback, int p) {
+  if (p <= 0) p = q;  // pairs wanted: the border's width unless a wider border was given
   const int n = m + q;
   auto smem_attr = [](const void* f, size_t bytes) {
     ensure_dynamic_smem(f, bytes);
@@ -2285,11 +2289,12 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   const size_t chs = sizeof(df) * (1.0 * n * q + 5.0 * q * q + 2.0 * m + 1.0 * m * q + 1.0 * q * (q + kMaxCluster) +
                                     3.0 * n * kMaxCluster + 1.0 * kMaxCluster * q);
   const size_t fs = sizeof(df) * q * q;
-  const bool fast = q <= kSrqiMaxQ && srs <= 200 * 1024 && chs <= 220 * 1024;
+  // the structured iteration finds one pair per border column: a wider border (p < q) takes the dense path
+  const bool fast = p == q && q <= kSrqiMaxQ && srs <= 200 * 1024 && chs <= 220 * 1024;
   // Xc = Z_m (a - B b) runs in column chunks whose staged blocks fit in 200 KB
   const int qc = static_cast<int>(std::max<size_t>(
-      1, std::min<size_t>(q, (200 * 1024) / (sizeof(df) * static_cast<size_t>(m + q)))));
-  const int nxc = (q + qc - 1) / qc;
+      1, std::min<size_t>(p, (200 * 1024) / (sizeof(df) * static_cast<size_t>(m + q)))));
+  const int nxc = (p + qc - 1) / qc;
   // kernels launched here; the dense eigensolver's launcher counts its own
   ProfScope ps(st, P_PENCIL, 8.0 * (2.0 * dn * m + 2.0 * dn * q + 2.0 * m * q + 3.0 * q * q + 1.0 * n * q), 0.0,
                (fast ? 6 : 4) + nxc);
@@ -2314,14 +2319,14 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
   }
   smem_attr((const void*)k_std_form, fs);
   k_std_form<<<1, 512, fs, st>>>(m, q, theta, w->Ft, w->Tt, w->St, w->Lq, w->Xq, w->H, status, skip, nfallback);
-  launch_syev_df(w, n, q, w->H, mu, w->Yh, st, skip);
-  k_std_back<<<1, kStdMaxQ, 0, st>>>(m, q, w->Lq, w->Yh, skip);
+  launch_syev_df(w, n, p, w->H, mu, w->Yh, st, skip);
+  k_std_back<<<1, kStdMaxQ, 0, st>>>(m, q, p, w->Lq, w->Yh, skip);
   // Xc = Z_m (a - B b), Y = b
-  for (int j0 = 0; j0 < q; j0 += qc) {
-    const int wc = std::min(qc, q - j0);
+  for (int j0 = 0; j0 < p; j0 += qc) {
+    const int wc = std::min(qc, p - j0);
     const size_t xsc = sizeof(df) * static_cast<size_t>(m + q) * wc;
     smem_attr((const void*)k_xc, xsc);
-    k_xc<<<64, kPenThreads, xsc, st>>>(dn, m, q, j0, wc, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
+    k_xc<<<64, kPenThreads, xsc, st>>>(dn, m, q, p, j0, wc, Zdf, w->KB, w->Yh, Xc, Xcdf, Y);
   }
 }
 

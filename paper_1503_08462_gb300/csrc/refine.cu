@@ -287,4 +287,65 @@ void launch_rq_finish(const double* sums, int q, double* theta, double* lam, int
   k_rq_finish<<<1, 32, 0, st>>>(sums, q, theta, lam, perm, relres, flag);
 }
 
+// ---------------------------------------------------------------- Krylov block helpers
+
+namespace {
+
+template <typename TV, typename TE>
+__global__ void k_pack_krylov(int rows, const TV* __restrict__ V1, const TE* __restrict__ E, int lde, int q,
+                              TV* __restrict__ K) {
+  const long long total = static_cast<long long>(rows) * 2 * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / (2 * q);
+    const int c = static_cast<int>(i % (2 * q));
+    if (c < q) {
+      K[i] = V1[r * q + c];
+    } else {
+      if constexpr (sizeof(TV) == sizeof(double) && sizeof(TE) == sizeof(double)) {
+        K[i] = E[r * lde + c - q];
+      } else {
+        K[i] = make_float2(E[r * lde + c - q], 0.f);
+      }
+    }
+  }
+}
+
+// U = Xp + V Y with V rows x nv and Y nv x q (float64), one thread per (row, column)
+__global__ void k_recombine_wide(int rows, const double* __restrict__ Xp, const double* __restrict__ V, int nv,
+                                 const double* __restrict__ Y, int q, double* __restrict__ U) {
+  const long long total = static_cast<long long>(rows) * q;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / q;
+    const int c = static_cast<int>(i % q);
+    double acc = Xp[i];
+    for (int d = 0; d < nv; ++d) acc = fma(V[r * nv + d], Y[d * q + c], acc);
+    U[i] = acc;
+  }
+}
+
+int grid_of(long long n) { return static_cast<int>(std::min<long long>((n + kThreads - 1) / kThreads, 8LL * kNumSms)); }
+
+}  // namespace
+
+void launch_pack_krylov_f64(int rows, const double* V1, const double* E, int lde, int q, double* K, cudaStream_t st) {
+  const long long n = static_cast<long long>(rows) * 2 * q;
+  ProfScope ps(st, P_OTHER, 24.0 * rows * q, 0.0);
+  k_pack_krylov<double, double><<<grid_of(n), kThreads, 0, st>>>(rows, V1, E, lde, q, K);
+}
+
+void launch_pack_krylov_df(int rows, const float2* V1, const float* E, int lde, int q, float2* K, cudaStream_t st) {
+  const long long n = static_cast<long long>(rows) * 2 * q;
+  ProfScope ps(st, P_OTHER, 20.0 * rows * q + 4.0 * rows * lde, 0.0);
+  k_pack_krylov<float2, float><<<grid_of(n), kThreads, 0, st>>>(rows, V1, E, lde, q, K);
+}
+
+void launch_recombine_wide(int rows, const double* Xp, const double* V, int nv, const double* Y, int q, double* U,
+                           cudaStream_t st) {
+  const long long n = static_cast<long long>(rows) * q;
+  ProfScope ps(st, P_RECOMBINE, 8.0 * rows * (2.0 * q + nv) + 8.0 * nv * q, 2.0 * rows * nv * q);
+  k_recombine_wide<<<grid_of(n), kThreads, 0, st>>>(rows, Xp, V, nv, Y, q, U);
+}
+
 }  // namespace amgeig

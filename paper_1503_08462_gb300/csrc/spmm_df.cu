@@ -292,17 +292,18 @@ __global__ void __launch_bounds__(kThreads) k_recombine_rows(int n, const float2
 // U = I_n^k Xc + V Y with the composite prolongation I_n^k (CSR, float-float
 // values) applied row by row: the prolongation chain and its intermediate
 // blocks disappear; each thread owns one row and all Q accumulators.
+// V has nv >= q columns (a Krylov block wider than the pairs: nv <= 2 Q) and Y is nv x q
 template <int Q>
 __global__ void __launch_bounds__(kThreads) k_recombine_pc(int n, const int* __restrict__ rp,
                                                            const int* __restrict__ ci, const float2* __restrict__ pv,
                                                            const float2* __restrict__ Xc,
                                                            const float2* __restrict__ V,
                                                            const double* __restrict__ Y, int q,
-                                                           float2* __restrict__ U) {
-  __shared__ __align__(16) float2 ys[Q * Q];
-  for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+                                                           float2* __restrict__ U, int nv) {
+  __shared__ __align__(16) float2 ys[2 * Q * Q];
+  for (int i = threadIdx.x; i < nv * Q; i += blockDim.x) {
     const int d = i / Q, c = i % Q;
-    const df v = (d < q && c < q) ? df_from_double(Y[d * q + c]) : df{0.f, 0.f};
+    const df v = (c < q) ? df_from_double(Y[d * q + c]) : df{0.f, 0.f};
     ys[i] = make_float2(v.hi, v.lo);
   }
   __syncthreads();
@@ -320,8 +321,8 @@ __global__ void __launch_bounds__(kThreads) k_recombine_pc(int n, const int* __r
     for (int c = 0; c < Q; ++c)
       if (c < q) acc[c].fma(w, ld2(Xc, xr + c));
   }
-  for (int d = 0; d < q; ++d) {
-    const df v = ld2(V, base + d);
+  for (int d = 0; d < nv; ++d) {
+    const df v = ld2(V, row * nv + d);
     const float4* yr = reinterpret_cast<const float4*>(ys + d * Q);
 #pragma unroll
     for (int c = 0; c < Q; c += 2) {
@@ -644,23 +645,24 @@ void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool
 }
 
 void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, const float2* pv, const float2* Xc,
-                            const float2* V, const double* Y, int q, float2* U, cudaStream_t st) {
+                            const float2* V, const double* Y, int q, float2* U, cudaStream_t st, int nv) {
   if (rows <= 0 || q <= 0) return;
-  ProfScope ps(st, P_RECOMBINE, 16.0 * rows * q + 8.0 * q * q + 4.0 * (rows + 1) + 12.0 * nnz,
-               2.0 * rows * q * q + 2.0 * nnz * q);
+  if (nv <= 0) nv = q;
+  ProfScope ps(st, P_RECOMBINE, 8.0 * rows * (q + nv) + 8.0 * nv * q + 4.0 * (rows + 1) + 12.0 * nnz,
+               2.0 * rows * nv * q + 2.0 * nnz * q);
   const int blocks = ceil_div(rows, kThreads);
   if (q <= 8)
-    k_recombine_pc<8><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+    k_recombine_pc<8><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U, nv);
   else if (q <= 16)
-    k_recombine_pc<16><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+    k_recombine_pc<16><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U, nv);
   else if (q <= 20)
-    k_recombine_pc<20><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+    k_recombine_pc<20><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U, nv);
   else if (q <= 24)
-    k_recombine_pc<24><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+    k_recombine_pc<24><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U, nv);
   else if (q <= 28)
-    k_recombine_pc<28><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+    k_recombine_pc<28><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U, nv);
   else
-    k_recombine_pc<32><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U);
+    k_recombine_pc<32><<<blocks, kThreads, 0, st>>>(rows, rp, ci, pv, Xc, V, Y, q, U, nv);
 }
 
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,

@@ -754,3 +754,40 @@ def test_shifted_mixed_solve_converges_and_refuses_a_large_shift():
         # after a refused shift the hierarchy still solves (unshifted and shifted)
         lam2, _, _, code2 = h.solve(6, tol=1e-9, opt=ae.options(q_extra=2, max_corrections=100))
         assert code2 == ae.AMGEIG_OK and np.all(np.abs(lam2 - lam_ex) <= 1e-10 * lam_ex)
+
+
+# ------------------------------------------------------------------ Krylov-augmented correction space
+
+
+@pytest.mark.parametrize("kind,size,cap,seed,q,qe", [("lshape", 16, 60, 2, 6, 2), ("square", 32, 50, 1, 4, 2)])
+@pytest.mark.parametrize("L,m", [(1, 1), (2, 1), (3, 1), (2, 2)])
+def test_krylov_iteration_parity(kind, size, cap, seed, q, qe, L, m):
+    """Depth-2 Krylov space (V_n + span(TU, T^2 U)) on the GPU float64 path against the oracle's, after L
+    finest-level corrections with m V-cycles per inverse-iteration step: the GPU takes the pencil on
+    [TU | T^2 U - TU], the oracle on the M-orthonormalised [TU, T^2 U]; Rayleigh-Ritz depends only on the
+    span, so the bounds are the float64 parity bounds."""
+    p, blob, _ = problem_and_blob(kind, size, cap, seed)
+    oh = O.read_blob(blob)
+    lam_o, U_o, _ = O.solve(oh, q, tol=0.0, opts=O.Options(q_extra=qe, fixed_corrections=L, krylov=2, v_cycles=m))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, _ = h.solve(q, tol=0.0, opt=ae.options(q_extra=qe, fixed_corrections=L, krylov=2, v_cycles=m))
+    rel = np.max(np.abs(lam - lam_o) / lam_o)
+    assert np.all(np.abs(lam - lam_o) <= eig_rel_tol(lam_o, lam_max(p)) * lam_o), rel
+    assert m_subspace_angle(U, U_o, oh.M[0]) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [ae.AMGEIG_FP64, ae.AMGEIG_MIXED_FP32])
+def test_krylov_converged_solve_and_fewer_corrections(prec):
+    """The Krylov space converges to the dense eigenpairs in fewer corrections than the paper's space."""
+    p, blob, _ = problem_and_blob("lshape", 24, 60, 2)
+    oh = O.read_blob(blob)
+    lam_ex, U_ex = dense_pairs(p, 6)
+    with ae.Hierarchy(blob) as h:
+        base = dict(q_extra=2, max_corrections=100, precision=prec)
+        l1, _, i1, c1 = h.solve(6, tol=1e-9, opt=ae.options(krylov=1, **base))
+        l2, U2, i2, c2 = h.solve(6, tol=1e-9, opt=ae.options(krylov=2, **base))
+    assert c1 == c2 == ae.AMGEIG_OK
+    assert i2.corrections < i1.corrections, (i2.corrections, i1.corrections)
+    assert np.all(np.abs(l2 - lam_ex) <= 1e-10 * lam_ex)
+    assert m_subspace_angle(U2, U_ex, oh.M[0]) < 1e-7
+    assert np.abs(U2.T @ (oh.M[0] @ U2) - np.eye(6)).max() < 1e-10
