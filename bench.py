@@ -525,6 +525,8 @@ def main():
                     help="corrections the float64 reference may take (workload default, 150)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip the float64 path at the same settings")
     ap.add_argument("--no-device-setup", action="store_true", help="skip timing the device AMG setup")
+    ap.add_argument("--krylov", type=int, default=1, choices=[1, 2],
+                    help="correction space: 1 = V_n + span(V) (the paper's), 2 = V_n + span(TU, T^2 U)")
     ap.add_argument("--refine", type=int, default=None, choices=[0, 1, 2],
                     help="Rayleigh quotients of the final vectors: 1 float64, 2 compensated float64 "
                          "(workload default)")
@@ -586,7 +588,7 @@ def main():
     smoother = ae.AMGEIG_SMOOTHER_GAUSS_SEIDEL if args.smoother == "gauss-seidel" else ae.AMGEIG_SMOOTHER_L1_JACOBI
     opt = ae.options(q_extra=qe, max_corrections=max_corr, precision=prec, coarse_modes=modes,
                      pre_sweeps=args.sweeps, post_sweeps=args.sweeps, v_cycles=args.v_cycles, smoother=smoother,
-                     refine=refine)
+                     refine=refine, krylov=args.krylov)
     h = ae.Hierarchy(blob, device=local)
     N0 = h.sizes[0]
     stream = torch.cuda.Stream(device=local)
@@ -799,6 +801,7 @@ def main():
             "config": {"workload": args.workload, "N": N0, "q": q, "q_extra": qe, "levels": h.sizes,
                        "precision": args.precision, "tol_relres": tol, "corrections": corrections,
                        "coarse_modes": modes, "sweeps": args.sweeps, "v_cycles": args.v_cycles, "smoother": args.smoother,
+                       "krylov": args.krylov,
                        "rel_eig_err_vs_fp64": rel_err, "fp64_corrections": info_ref.corrections,
                        "fp64_full_pencil_s": round(t_ref, 4), "fp64_relres": info_ref.max_relres,
                        "fp64_ref_converged": bool(info_ref.converged), "fp64_ref_drift_last10": ref_drift,
