@@ -95,7 +95,9 @@ def test_service_memory_cap_refuses_and_evicts():
     and give the same bits as a solve run alone."""
     cases = [problem_and_blob("lshape", 16, 60, 2), problem_and_blob("lshape", 16, 60, 2)]
     hs = [ae.Hierarchy(blob) for _, blob, _ in cases]
-    opt = ae.options(q_extra=2, max_corrections=40, precision=ae.AMGEIG_MIXED_FP32)
+    # autotune = 0: each handle would tune its own launch shapes, which may add a row's terms in another
+    # order; with the rule's shapes every handle of the blob gives the same bits
+    opt = ae.options(q_extra=2, max_corrections=40, precision=ae.AMGEIG_MIXED_FP32, autotune=0)
     try:
         alone = [h.solve(4, tol=1e-8, opt=opt) for h in hs]
         # a fresh pair of handles, so that no workspace is resident yet

@@ -306,7 +306,8 @@ def test_blob_alignment_and_validation():
     import struct
 
     p, blob, _ = problem_and_blob("square", 32, 50, 1)
-    opt = ae.options(q_extra=2, max_corrections=30, precision=ae.AMGEIG_MIXED_FP32)
+    # autotune = 0: the two handles compared bit for bit use the rule's launch shapes
+    opt = ae.options(q_extra=2, max_corrections=30, precision=ae.AMGEIG_MIXED_FP32, autotune=0)
     with ae.Hierarchy(blob) as h:
         ref = h.solve(3, tol=1e-9, opt=opt)
     raw = ctypes.create_string_buffer(len(blob) + 8)
