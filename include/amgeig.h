@@ -101,8 +101,11 @@ typedef struct {
                             level's operators (lanes per row, columns per lane, nonzero streams per
                             row) and keeps the fastest in the hierarchy; layouts with another stream
                             count add a row's terms in another order (float32 rounding in the
-                            V-cycle; later solves on the hierarchy repeat bit for bit); 0 = no
-                            tuning now (layouts tuned by earlier solves stay in use) */
+                            V-cycle; later solves on the hierarchy repeat bit for bit); the choices
+                            are also kept for the process, keyed by each operator's role, size and
+                            nonzero count, so a hierarchy of the same problem loaded again reuses
+                            them without timing; 0 = no tuning now (layouts tuned by earlier solves
+                            stay in use) */
   int batch;             /* amgeig_submit only: 1 (default) = the request may share one solve with
                             other queued requests on the same hierarchy whose options agree but for
                             q, q_extra, tol and max_corrections (the shared solve takes the widest
@@ -252,7 +255,7 @@ int amgeig_service_memory(uint64_t* resident_bytes, uint64_t* evictions);
  *   seconds       may be NULL; else seconds[0] = the whole setup, seconds[1] =
  *                 its host C/F splitting.
  * Errors: EINVAL (NULL argument, bad CSR, theta outside (0, 1), bad device),
- * ENOMEM (a sparse product row beyond 8192 terms, or allocation), ECUDA. */
+ * ENOMEM (allocation), ECUDA. */
 int amgeig_setup_blob(int64_t n, const int32_t* rp, const int32_t* ci, const double* a, const double* m,
                       double theta, int64_t coarse_cap, int max_levels, int device, void** blob, size_t* bytes,
                       double* seconds);

@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -1215,6 +1216,38 @@ int ensure_shift(amgeig_hierarchy_t* h, double sigma, cudaStream_t st) {
 // tuned solves can differ from untuned ones by float32 rounding in the V-cycle
 // (the fixed point is the same); a hierarchy keeps its choice, so its solves
 // repeat bit for bit.  Before any capture; under the lock.
+// Tuned shapes are also kept per process, keyed by the operator's role, shape
+// and nonzero count and the width: a hierarchy loaded again (the same problem)
+// takes them without timing anything.
+struct TuneKey {
+  int role, w4;
+  int64_t rows, cols, nnz;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(role, w4, rows, cols, nnz) < std::tie(o.role, o.w4, o.rows, o.cols, o.nnz);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<unsigned char, TuneResult>> g_tuned;
+
+TuneResult tune_or_reuse(DevCsr& S, int role, int kind, int w4, const float* dinv, const float* x, const float* b,
+                         float* out, cudaStream_t st) {
+  const TuneKey key{role, w4, S.rows, S.cols, S.nnz};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      S.tuned[w4] = it->second.first;
+      return it->second.second;
+    }
+  }
+  const TuneResult r = autotune_f4(S, kind, w4, dinv, x, b, out, st);
+  if (S.tuned[w4]) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = std::make_pair(S.tuned[w4], r);
+  }
+  return r;
+}
+
 int ensure_tuned(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
   const int w4 = w->ld32 / 4;
   if (w4 < 1 || w4 > 32 || h->tuned_w4[w4]) return AMGEIG_OK;
@@ -1224,9 +1257,9 @@ int ensure_tuned(amgeig_hierarchy_t* h, SolveWork* w, cudaStream_t st) {
     CK(cudaMemsetAsync(w->X32[l], 0, sizeof(float) * cl, st));
     CK(cudaMemsetAsync(w->B32[l], 0, sizeof(float) * cl, st));
     CK(cudaMemsetAsync(w->X32[l + 1], 0, sizeof(float) * cn, st));
-    const TuneResult a = autotune_f4(h->A[l], 0, w4, h->dinv32[l], w->X32[l], w->B32[l], w->T32[l], st);
-    const TuneResult r = autotune_f4(h->R[l], 1, w4, nullptr, w->T32[l], nullptr, w->B32[l + 1], st);
-    const TuneResult p = autotune_f4(h->P[l], 1, w4, nullptr, w->X32[l + 1], nullptr, w->T32[l], st);
+    const TuneResult a = tune_or_reuse(h->A[l], 0, 0, w4, h->dinv32[l], w->X32[l], w->B32[l], w->T32[l], st);
+    const TuneResult r = tune_or_reuse(h->R[l], 1, 1, w4, nullptr, w->T32[l], nullptr, w->B32[l + 1], st);
+    const TuneResult p = tune_or_reuse(h->P[l], 2, 1, w4, nullptr, w->X32[l + 1], nullptr, w->T32[l], st);
     char line[512];
     const TuneResult* tr[3] = {&a, &r, &p};
     const char* nm[3] = {"smooth", "restrict", "prolong"};

@@ -150,6 +150,12 @@ __global__ void k_spgemm_rows(int n, const int* __restrict__ xrp, const int* __r
   const int row = blockIdx.x * warps + wid;
   if (row >= n) return;  // whole warps leave together
   const bool fill = crp != nullptr;
+  {
+    // a row beyond the staging capacity is the long-row kernel's (whole warp leaves)
+    int total = 0;
+    for (int p = xrp[row]; p < xrp[row + 1]; ++p) total += yrp[xci[p] + 1] - yrp[xci[p]];
+    if (total > cap) return;
+  }
   // gather: the (p, r) loop in order; position m is the candidate's order
   int m0 = 0;
   for (int p = xrp[row]; p < xrp[row + 1]; ++p) {
@@ -220,6 +226,55 @@ __global__ void k_spgemm_rows(int n, const int* __restrict__ xrp, const int* __r
   }
 }
 
+// Rows with more candidate terms than the shared staging holds (dense rows of
+// the coarse 3D Galerkin levels): one thread per such row accumulates its terms
+// in candidate order into a dense row of scratch (marker, two sums per column of
+// C), then walks the columns in order.  Pass 1 (crp null) counts, pass 2
+// writes.  Same sums in the same order as the sorted path.
+__global__ void k_spgemm_long(int nlong, const int* __restrict__ rows, int ncols, const int* __restrict__ xrp,
+                              const int* __restrict__ xci, const double* __restrict__ xa,
+                              const double* __restrict__ xm, const int* __restrict__ yrp,
+                              const int* __restrict__ yci, const double* __restrict__ ya,
+                              const double* __restrict__ ym, int* __restrict__ mark, double* __restrict__ sa,
+                              double* __restrict__ sm, int* __restrict__ cnt, const int* __restrict__ crp,
+                              int* __restrict__ cci, double* __restrict__ ca, double* __restrict__ cm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlong) return;
+  const int row = rows[t];
+  int* mk = mark + static_cast<long long>(t) * ncols;
+  double* a = sa + static_cast<long long>(t) * ncols;
+  double* m = sm + static_cast<long long>(t) * ncols;
+  for (int j = 0; j < ncols; ++j) mk[j] = 0;
+  for (int p = xrp[row]; p < xrp[row + 1]; ++p) {
+    const int k = xci[p];
+    const double s1 = xa[p], s2 = xm ? xm[p] : xa[p];
+    for (int r = yrp[k]; r < yrp[k + 1]; ++r) {
+      const int j = yci[r];
+      if (!mk[j]) {
+        mk[j] = 1;
+        a[j] = 0.0;
+        m[j] = 0.0;
+      }
+      a[j] = __dadd_rn(a[j], s1 * ya[r]);
+      m[j] = __dadd_rn(m[j], s2 * (ym ? ym[r] : ya[r]));
+    }
+  }
+  if (!crp) {
+    int c = 0;
+    for (int j = 0; j < ncols; ++j) c += mk[j];
+    cnt[row] = c;
+    return;
+  }
+  int w = crp[row];
+  for (int j = 0; j < ncols; ++j)
+    if (mk[j]) {
+      cci[w] = j;
+      ca[w] = a[j];
+      cm[w] = m[j];
+      ++w;
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 struct Csr {
@@ -275,10 +330,11 @@ int scan_counts(const std::vector<int32_t>& cnt, std::vector<int32_t>& rp) {
   return AMGEIG_OK;
 }
 
-// C = X Y on the device (see k_spgemm_rows); C's arrays in pool, its row
-// offsets also on the host (crp_host).
-int spgemm(Pool& pool, int nrows, const DevMat& X, const DevMat& Y, DevMat& C, std::vector<int32_t>& crp_host,
-           int* d_cnt, cudaStream_t st) {
+// C = X Y on the device (see k_spgemm_rows; rows beyond 8192 candidate terms:
+// k_spgemm_long); C's arrays in pool, its row offsets also on the host
+// (crp_host).  ncols: the columns of Y.
+int spgemm(Pool& pool, int nrows, int ncols, const DevMat& X, const DevMat& Y, DevMat& C,
+           std::vector<int32_t>& crp_host, int* d_cnt, cudaStream_t st) {
   if (nrows == 0) return set_last_error(AMGEIG_EINVAL, "setup: empty product");
   {
     ProfScope ps(st, P_OTHER, 0.0, 0.0);
@@ -287,12 +343,29 @@ int spgemm(Pool& pool, int nrows, const DevMat& X, const DevMat& Y, DevMat& C, s
   std::vector<int32_t> cnt(static_cast<size_t>(nrows));
   SCK(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nrows, cudaMemcpyDeviceToHost, st));
   SCK(cudaStreamSynchronize(st));
+  constexpr int kCap = 8192;
   int mx = 1;
-  for (int32_t c : cnt) mx = std::max(mx, static_cast<int>(c));
+  std::vector<int32_t> longrows;
+  for (int i = 0; i < nrows; ++i) {
+    if (cnt[i] > kCap)
+      longrows.push_back(i);
+    else
+      mx = std::max(mx, static_cast<int>(cnt[i]));
+  }
   int cap = 32;
   while (cap < mx) cap <<= 1;
-  if (cap > 8192 || mx >= (1 << 20))
-    return set_last_error(AMGEIG_ENOMEM, "setup: a sparse product row has more than 8192 terms");
+  int* d_long = nullptr;
+  int* d_mark = nullptr;
+  double *d_sa = nullptr, *d_sm = nullptr;
+  const int nlong = static_cast<int>(longrows.size());
+  if (nlong > 0) {
+    // dense scratch rows for the long rows (freed with the setup's other arrays)
+    const size_t cells = static_cast<size_t>(nlong) * static_cast<size_t>(ncols);
+    SCK(pool.upload(&d_long, longrows, st));
+    SCK(pool.alloc(&d_mark, cells));
+    SCK(pool.alloc(&d_sa, cells));
+    SCK(pool.alloc(&d_sm, cells));
+  }
   const size_t per_warp = static_cast<size_t>(cap) * (8 + 16);
   const int warps = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp)));
   const size_t sm = per_warp * warps;
@@ -302,6 +375,12 @@ int spgemm(Pool& pool, int nrows, const DevMat& X, const DevMat& Y, DevMat& C, s
     ProfScope ps(st, P_OTHER, 0.0, 0.0);
     k_spgemm_rows<<<blocks, 32 * warps, sm, st>>>(nrows, X.rp, X.ci, X.a, X.m, Y.rp, Y.ci, Y.a, Y.m, cap, d_cnt,
                                                   nullptr, nullptr, nullptr, nullptr);
+  }
+  if (nlong > 0) {
+    ProfScope ps(st, P_OTHER, 0.0, 0.0);
+    k_spgemm_long<<<ceil_div(nlong, 64), 64, 0, st>>>(nlong, d_long, ncols, X.rp, X.ci, X.a, X.m, Y.rp, Y.ci, Y.a,
+                                                     Y.m, d_mark, d_sa, d_sm, d_cnt, nullptr, nullptr, nullptr,
+                                                     nullptr);
   }
   SCK(cudaGetLastError());
   SCK(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nrows, cudaMemcpyDeviceToHost, st));
@@ -317,6 +396,11 @@ int spgemm(Pool& pool, int nrows, const DevMat& X, const DevMat& Y, DevMat& C, s
     ProfScope ps(st, P_OTHER, 0.0, 0.0);
     k_spgemm_rows<<<blocks, 32 * warps, sm, st>>>(nrows, X.rp, X.ci, X.a, X.m, Y.rp, Y.ci, Y.a, Y.m, cap, d_cnt,
                                                   C.rp, C.ci, C.a, C.m);
+  }
+  if (nlong > 0) {
+    ProfScope ps(st, P_OTHER, 0.0, 0.0);
+    k_spgemm_long<<<ceil_div(nlong, 64), 64, 0, st>>>(nlong, d_long, ncols, X.rp, X.ci, X.a, X.m, Y.rp, Y.ci, Y.a,
+                                                     Y.m, d_mark, d_sa, d_sm, nullptr, C.rp, C.ci, C.a, C.m);
   }
   SCK(cudaGetLastError());
   return AMGEIG_OK;
@@ -501,9 +585,9 @@ extern "C" int amgeig_setup_blob(int64_t n, const int32_t* rp, const int32_t* ci
     // A P (both value arrays), then R (A P)
     DevMat dAP, dC;
     std::vector<int32_t> aprp, crp;
-    rc = spgemm(pool, nf, dA, dP, dAP, aprp, d_cnt, st);
+    rc = spgemm(pool, nf, nc, dA, dP, dAP, aprp, d_cnt, st);
     if (rc) return rc;
-    rc = spgemm(pool, nc, dR, dAP, dC, crp, d_cnt, st);
+    rc = spgemm(pool, nc, nc, dR, dAP, dC, crp, d_cnt, st);
     if (rc) return rc;
     Csr Ac;
     Ac.rows = Ac.cols = nc;

@@ -19,7 +19,9 @@ def _built():
 
 
 CASES = [("square", dict(m=32, seed=1), 50), ("lshape", dict(m_half=24, seed=2), 60),
-         ("checker", dict(m=48, checker=4, seed=3), 60), ("cube", dict(m=12, seed=4), 40)]
+         ("checker", dict(m=48, checker=4, seed=3), 60), ("cube", dict(m=12, seed=4), 40),
+         # dense Galerkin rows on the coarse 3D levels: products with rows beyond the shared staging
+         ("cube", dict(m=40, seed=4), 60)]
 
 
 def _problem(kind, kw):
