@@ -93,9 +93,10 @@ typedef struct {
                             ~u * lambda_max / lambda_j to cancellation.  With 1 or 2 the values are
                             sorted ascending and the vectors permuted alike */
   int graphs;            /* 1 (default): the nested phase and each finest-level correction are
-                            captured once as CUDA graphs (per settings) and replayed; 0: every
-                            kernel launched directly.  Same arithmetic, same bits.  Not used
-                            while profiling is enabled or when the caller's stream is capturing */
+                            captured as CUDA graphs (per settings and buffer roles) the second time
+                            they run, and replayed from then on; 0: every kernel launched directly.
+                            Same arithmetic, same bits.  Not used while profiling is enabled or
+                            when the caller's stream is capturing */
   int autotune;          /* mixed precisions: 1 (default) = the first solve at each block width times
                             every lane layout of the float32 smoothing and transfer kernels on each
                             level's operators (lanes per row, columns per lane, nonzero streams per

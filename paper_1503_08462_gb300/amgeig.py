@@ -228,7 +228,9 @@ def amgeig_setup_blob(row_ptr, col_idx, a_vals, m_vals, theta: float = 0.25, coa
                                theta, coarse_cap, max_levels, device, ctypes.byref(out), ctypes.byref(nbytes),
                                secs.ctypes.data), "amgeig_setup_blob")
     try:
-        blob = ctypes.string_at(out, nbytes.value)
+        # numpy view of the library's buffer, copied once (ctypes.string_at cannot take 2 GB and more)
+        view = np.ctypeslib.as_array((ctypes.c_uint8 * nbytes.value).from_address(out.value))
+        blob = view.tobytes()
     finally:
         L.amgeig_free_blob(out)
     return blob, float(secs[0]), float(secs[1])

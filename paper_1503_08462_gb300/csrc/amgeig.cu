@@ -481,6 +481,7 @@ struct SolveWork {
     unsigned long long kernels = 0;
   };
   std::map<std::string, Graph> graphs;
+  std::map<std::string, int> graph_seen;  // segments run so far without a graph
   ~SolveWork() {
     for (auto& g : graphs)
       if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
@@ -1101,7 +1102,7 @@ void set_roles(SolveWork* w, const std::vector<void*>& r) {
 }
 
 // Run the launch sequence `body` on st.  With graphs on (and no profiling, and
-// st not already capturing), the first run of a (segment, settings, roles)
+// st not already capturing), the second run of a (segment, settings, roles)
 // combination captures the sequence as a CUDA graph and later runs replay it:
 // one launch instead of the sequence's hundred-odd, with no host work between
 // kernels.  body must only enqueue work (no host synchronisation).
@@ -1120,6 +1121,9 @@ int run_segment(SolveWork* w, const amgeig_options& o, const std::string& seg, c
   key.append(reinterpret_cast<const char*>(pre.data()), sizeof(void*) * pre.size());
   auto it = w->graphs.find(key);
   if (it == w->graphs.end()) {
+    // capture only a combination seen before: a one-off solve (a freshly loaded
+    // hierarchy solved once) does not pay for capturing and instantiating
+    if (w->graph_seen[key]++ == 0) return body();
     const unsigned long long k0 = thread_launch_count();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     const int rc = body();
