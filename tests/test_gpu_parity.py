@@ -792,3 +792,22 @@ def test_krylov_converged_solve_and_fewer_corrections(prec):
     assert np.all(np.abs(l2 - lam_ex) <= 1e-10 * lam_ex)
     assert m_subspace_angle(U2, U_ex, oh.M[0]) < 1e-7
     assert np.abs(U2.T @ (oh.M[0] @ U2) - np.eye(6)).max() < 1e-10
+
+
+def test_checkerboard_mixed_eigenvalues_at_the_metric_bound():
+    """The C3 family (10^(+-3) checkerboard coefficient, dense low spectrum): the mixed path with compensated
+    Rayleigh quotients gives each of its eigenvalues within 1e-8 (the metric's bound) of the dense generalized
+    eigenvalue.  LAPACK's own eigenvalues carry ~u lambda_max / lambda_j of rounding on this pencil (~1e-8
+    for the smallest), so the reference is the exact Rayleigh quotient of LAPACK's eigenvector, which is the
+    eigenvalue to second order in that vector's error."""
+    p, blob, _ = problem_and_blob("checker", 24, 40, 3)
+    oh = O.read_blob(blob)
+    q = 8
+    lam_ex, U_ex = dense_pairs(p, q)
+    ref = np.array([_exact_rayleigh(oh.A[0], oh.M[0], U_ex[:, j]) for j in range(q)])
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, code = h.solve(q, tol=1e-8, opt=ae.options(q_extra=6, max_corrections=200, v_cycles=2,
+                                                                 precision=ae.AMGEIG_MIXED_FP32, refine=2))
+    assert code == ae.AMGEIG_OK
+    rel = np.abs(lam - ref) / ref
+    assert np.all(rel <= 1e-8), rel.max()
