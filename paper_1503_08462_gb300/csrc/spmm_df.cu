@@ -250,6 +250,66 @@ __global__ void __launch_bounds__(kThreads) k_recombine_df2(int n, const float2*
   }
 }
 
+// Register-tiled form for wide blocks (32 < q <= 128): a block of 256 threads
+// takes 32 rows; thread t computes 2 rows (t / 16 and t / 16 + 16) times the
+// columns t % 16, t % 16 + 16, ... (CJ of them), so each Y value read from
+// shared memory feeds two compensated products and each V value CJ: 2 CJ
+// independent accumulators per thread hide the float-float dependency chains.
+// Same sums in the same order (Xp, then d = 0 .. q-1) as k_recombine_df2.
+constexpr int kRtRows = 32, kRtCols = 16;
+template <int CJ>
+__global__ void __launch_bounds__(kThreads) k_recombine_tiled(int n, const float2* __restrict__ Xp,
+                                                              const float2* __restrict__ V,
+                                                              const double* __restrict__ Y, int q,
+                                                              float2* __restrict__ U) {
+  extern __shared__ __align__(16) df tsm[];  // Y (q x q) then the block's V rows (kRtRows x q)
+  df* ys = tsm;
+  df* vs = tsm + q * q;
+  for (int i = threadIdx.x; i < q * q; i += blockDim.x) ys[i] = df_from_double(Y[i]);
+  const long long row0 = static_cast<long long>(blockIdx.x) * kRtRows;
+  for (int i = threadIdx.x; i < kRtRows * q; i += blockDim.x) {
+    const long long r = row0 + i / q;
+    vs[i] = (r < n) ? ld2(V, r * q + i % q) : df{0.f, 0.f};
+  }
+  __syncthreads();
+  const int cg = threadIdx.x % kRtCols, rp = threadIdx.x / kRtCols;
+  const int ra = rp, rb = rp + kRtRows / 2;
+  const long long rowa = row0 + ra, rowb = row0 + rb;
+  df_acc acc[2][CJ];
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) {
+    const int c = cg + j * kRtCols;
+    acc[0][j] = acc_zero();
+    acc[1][j] = acc_zero();
+    if (c < q) {
+      if (rowa < n) acc[0][j].add(ld2(Xp, rowa * q + c));
+      if (rowb < n) acc[1][j].add(ld2(Xp, rowb * q + c));
+    }
+  }
+  const df* va = vs + ra * q;
+  const df* vb = vs + rb * q;
+  for (int d = 0; d < q; ++d) {
+    const df x0 = va[d], x1 = vb[d];
+    const df* yr = ys + d * q;
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+      const int c = cg + j * kRtCols;
+      if (c < q) {
+        const df y = yr[c];
+        acc[0][j].fma(x0, y);
+        acc[1][j].fma(x1, y);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) {
+    const int c = cg + j * kRtCols;
+    if (c >= q) continue;
+    if (rowa < n) st2(U, rowa * q + c, acc[0][j].value());
+    if (rowb < n) st2(U, rowb * q + c, acc[1][j].value());
+  }
+}
+
 // Row-per-thread form for q <= Q <= 32: each thread keeps all Q accumulators of
 // its row in registers, so one V value feeds Q compensated products and the
 // rows of Y (zero-padded to Q columns, shared) are read as 16-byte broadcasts.
@@ -681,6 +741,23 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
       k_recombine_rows<28><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
     else
       k_recombine_rows<32><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    return;
+  }
+  if (q <= 128) {
+    const int blocks = ceil_div(rows, kRtRows);
+    ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
+    const size_t sm = sizeof(df) * (static_cast<size_t>(q) * q + static_cast<size_t>(kRtRows) * q);
+#define AMGEIG_TILED(CJ)                                                                     \
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_recombine_tiled<CJ>), sm);             \
+  k_recombine_tiled<CJ><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Y, q, U)
+    if (q <= 3 * kRtCols) {
+      AMGEIG_TILED(3);
+    } else if (q <= 5 * kRtCols) {
+      AMGEIG_TILED(5);
+    } else {
+      AMGEIG_TILED(8);
+    }
+#undef AMGEIG_TILED
     return;
   }
   Geo g = geo_for(q);
