@@ -21,13 +21,14 @@
 //   L^-T, T = L^-1 (...) L^-T, solved by the dense eigensolver below.  Both are
 //   the same Rayleigh-Ritz problem (same eigenvalues as the paper's pencil),
 //   only better conditioned, and everything runs in float-float.
-// * The symmetric eigenproblem is solved in float-float (48-bit significand)
-//   by one 1024-thread block: Householder tridiagonalisation, bisection with
+// * The symmetric eigenproblem is solved in float-float (48-bit significand):
+//   Householder tridiagonalisation (one 1024-thread block), bisection with
 //   Sturm counts for the wanted eigenvalues (float32), each shift refined by
-//   float-float Sturm multisection, inverse iteration with partial pivoting in
-//   float-float (Gram-Schmidt inside clusters of nearly equal shifts), a
-//   Rayleigh-Ritz clean-up by parallel cyclic Jacobi on each group of close
-//   shifts, and back-transformation.  References: Golub & Van Loan, Matrix
+//   float-float Sturm multisection, inverse iteration in float-float
+//   (Gram-Schmidt inside clusters of nearly equal shifts), a Rayleigh-Ritz
+//   clean-up by parallel cyclic Jacobi on each group of close shifts, and
+//   back-transformation; the phases after the tridiagonalisation run one warp
+//   or one block per eigenvalue, group or eigenvector.  References: Golub & Van Loan, Matrix
 //   Computations, 4th ed., 8.3 (tridiagonalisation), 8.4.1 (Sturm bisection),
 //   8.2.2 (inverse iteration), 8.5 (Jacobi).
 #include <cstdio>
@@ -65,6 +66,9 @@ struct PencilWork {
   df* Zt = nullptr;    // nmax x nwant_max
   df* rr = nullptr;    // 4 x nwant_max^2 (Rayleigh-Ritz clean-up)
   int* perm = nullptr; // nwant_max
+  df* hv = nullptr;    // nmax x nmax reflectors (split path)
+  df* shd = nullptr;   // nwant_max refined shifts (split path)
+  float* bounds = nullptr;  // 4: Gershgorin bounds, ||T||, pivot floor (split path)
   int nwant_max = 0;
   // coarse decomposition
   double* Lm = nullptr;  // dn x dn
@@ -106,64 +110,24 @@ __device__ __forceinline__ int sturm_count_df(const df* dd, const df* ee2, int n
 
 // ------------------------------------------------------------ float-float syev
 //
-// Dynamic shared memory: v, p (df, n each), sd, se2 (float, n each), shift
-// (float, nwant), cstart, cpos (int, nwant), d, e, tau (df, n each), then --
-// when they fit -- the
-// working matrix W (n x ldw df), the inverse-iteration factors (2 x n x nwant
-// df) and the tridiagonal eigenvectors Zt (n x nwant df).  `flags` bit 0/1/2
-// says which of W / factors / Zt live in shared memory; the others use the
-// global workspace (same layout), so one code path serves every size.
-constexpr int kSyW = 1, kSyF = 2, kSyZ = 4;
+// The phases of the solver are device functions with two drivers: k_syev_df
+// runs all of them in one block (the allocation-free entry point), the split
+// path runs the tridiagonalisation in one block (k_syev_tri) and spreads the
+// per-eigenvalue phases over many: the shifts one warp each (k_syev_vals),
+// inverse iteration and clean-up one block per group of close shifts
+// (k_syev_vecs) and the back-transformation one warp per eigenvector
+// (k_syev_back).  Each eigenvalue's phases do the same arithmetic on both.
 
-__global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ldw, int flags,
-                                                        const double* __restrict__ H, double* __restrict__ evals,
-                                                        double* __restrict__ evecs, df* __restrict__ Wg,
-                                                        df* __restrict__ tau_g, df* __restrict__ dd_g,
-                                                        df* __restrict__ ee_g, df* __restrict__ facg,
-                                                        df* __restrict__ Ztg, df* __restrict__ rrw,
-                                                        int* __restrict__ perm, const int* __restrict__ skip) {
-  if (skip != nullptr && *skip != 0) return;  // the structured fast path already produced the pairs
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  df* v = reinterpret_cast<df*>(smem_raw);
-  df* p = v + n;
-  float* sd = reinterpret_cast<float*>(p + n);
-  float* se2 = sd + n;
-  float* shift = se2 + n;
-  int* cstart = reinterpret_cast<int*>(shift + nwant);
-  int* cpos = cstart + nwant;
-  size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
-                4 * sizeof(df) * n + sizeof(df) * nwant + 2 * sizeof(int) * nwant + 15) &
-               ~static_cast<size_t>(15);
-  df* W = Wg;
-  if (flags & kSyW) {
-    W = reinterpret_cast<df*>(smem_raw + off);
-    off += sizeof(df) * static_cast<size_t>(n) * ldw;
-  }
-  df* fac = facg;
-  if (flags & kSyF) {
-    fac = reinterpret_cast<df*>(smem_raw + off);
-    off += sizeof(df) * 2 * static_cast<size_t>(n) * nwant;
-  }
-  df* Zt = Ztg;
-  if (flags & kSyZ) Zt = reinterpret_cast<df*>(smem_raw + off);
-  __shared__ df_acc red[32];
-  __shared__ float sf[4];
-  __shared__ int si[4];
-
+// Householder tridiagonalisation of the symmetric W (n x n, row stride LD,
+// full storage) by the whole block.  Four barriers per step: the norm of the
+// next column and v^T p are formed from per-warp partial sums written in the
+// preceding phase.  On return dd, ee hold the tridiagonal, tau the reflector
+// scalars and column k of W below the diagonal the reflector v_k, which is
+// also written to hv[k n + i] (i < n - k - 1) when hv is given.  v, p: n df of
+// scratch each; red_sig, red_vp: 32 per-warp partial sums each.
+__device__ void syev_tridiagonalise(int n, df* W, long long LD, df* v, df* p, df* dd, df* ee, df* tau,
+                                    df_acc* red_sig, df_acc* red_vp, df* hv) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const long long N = n, LD = ldw;
-  // the tridiagonal (d, e) and the Householder scalars live in shared memory
-  df* dd = reinterpret_cast<df*>(cpos + nwant);
-  df* ee = dd + n;
-  df* tau = ee + n;
-  df* ee2 = tau + n;     // e_i^2 in float-float (Sturm counts)
-  df* shd = ee2 + n;     // float-float shifts (nwant)
-  int* gs0 = reinterpret_cast<int*>(shd + nwant);  // clean-up group [gs0[j], gs1[j]) of index j
-  int* gs1 = gs0 + nwant;
-  __shared__ df_acc red_sig[32], red_vp[32];
-
-  for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
-  __syncthreads();
   // sigma partials of column 0 (rows 2..n-1)
   {
     df_acc a = acc_zero();
@@ -172,10 +136,6 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     if (lane == 0) red_sig[warp] = a;
   }
   __syncthreads();
-
-  // ---- Householder tridiagonalisation (full symmetric storage) -------------
-  // Four barriers per step: the norm of the next column and v^T p are formed
-  // from per-warp partial sums written in the preceding phase.
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
     df_acc sa = lane < nw ? red_sig[lane] : acc_zero();
@@ -235,6 +195,8 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
       }
       if (lane == 0) red_vp[warp] = pv;
       for (int i = tid; i < m; i += nt) W[(k + 1 + i) * LD + k] = v[i];
+      if (hv != nullptr)
+        for (int i = tid; i < m; i += nt) hv[static_cast<long long>(k) * n + i] = v[i];
     }
     __syncthreads();  // (2) p and v^T p partials complete
     {
@@ -285,8 +247,486 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     if (n >= 1) tau[n - 1] = df{0.f, 0.f};
   }
   __syncthreads();
+}
 
-  // ---- bisection (float32) for the nwant smallest eigenvalues -------------
+// Gershgorin interval of the tridiagonal (float32 diagonal sd, squared
+// off-diagonal se2), padded, by one thread: sf = {lower, upper, ||T|| bound,
+// pivot floor of the Sturm recurrences}.
+__device__ void syev_bounds(const float* sd, const float* se2, int n, float* sf) {
+  float gl = 3.0e38f, gu = -3.0e38f, emax2 = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const float r = (i > 0 ? sqrtf(se2[i - 1]) : 0.f) + (i + 1 < n ? sqrtf(se2[i]) : 0.f);
+    gl = fminf(gl, sd[i] - r);
+    gu = fmaxf(gu, sd[i] + r);
+    if (i + 1 < n) emax2 = fmaxf(emax2, se2[i]);
+  }
+  const float tn = fmaxf(fabsf(gl), fabsf(gu));
+  const float pad = 2.0e-6f * tn + 1.0e-30f;
+  sf[0] = gl - pad;
+  sf[1] = gu + pad;
+  sf[2] = tn;
+  sf[3] = fmaxf(1.0e-30f, 1.0e-35f * fmaxf(emax2, 1.f));
+}
+
+// float32 bisection for the (j+1)-th smallest eigenvalue, one thread.
+__device__ float syev_bisect(int j, const float* sd, const float* se2, int n, float gl, float gu, float pivmin) {
+  float lo = gl, hi = gu;
+  for (int it = 0; it < 80; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(sd, se2, n, mid, pivmin) > j) hi = mid; else lo = mid;
+  }
+  return 0.5f * (lo + hi);
+}
+
+// The same bracket by one warp: 32-point multisection, 33x narrower per round
+// (Golub & Van Loan 8.4.1), until the float32 points stop separating.
+__device__ float syev_multisect(int j, const float* sd, const float* se2, int n, float gl, float gu, float pivmin) {
+  const int lane = threadIdx.x & 31;
+  float lo = gl, hi = gu;
+  for (int round = 0; round < 40; ++round) {
+    const float mid = 0.5f * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    const float x = lo + (hi - lo) * (static_cast<float>(lane + 1) * (1.f / 33.f));
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_count(sd, se2, n, x, pivmin) > j);
+    const int l1 = above ? __ffs(above) - 1 : 32;  // first point with more than j eigenvalues below
+    const float xlo = __shfl_sync(0xffffffffu, x, l1 > 0 ? l1 - 1 : 0);
+    const float xhi = __shfl_sync(0xffffffffu, x, l1 < 32 ? l1 : 31);
+    if (l1 > 0) lo = fmaxf(lo, xlo);
+    if (l1 < 32) hi = fminf(hi, xhi);
+  }
+  return 0.5f * (lo + hi);
+}
+
+// Refine the float32 shift s0 of index j with float-float Sturm counts (one
+// warp; ee2 holds e_i^2).  The float32 counts can be off by ~n 2^-24 ||T||,
+// far more than the gaps inside a graded spectrum; with float-float shifts the
+// inverse iteration separates eigenvalues down to ~1e-9 ||T|| apart on its
+// own.  The bracket is first widened until its float-float counts enclose
+// index j, then 32-point multisection shrinks it 33x per round.  Returns the
+// midpoint of the final bracket (the same on every lane).
+__device__ df syev_refine_shift(int j, float s0, const df* dd, const df* ee2, int n, float gl, float gu,
+                                float tnorm, float pivmin) {
+  const int lane = threadIdx.x & 31;
+  float w = 1.0e-4f * tnorm + 1.0e-6f * fabsf(s0) + pivmin;
+  df lo = df{s0 - w, 0.f}, hi = df{s0 + w, 0.f};
+  for (int attempt = 0; attempt < 12; ++attempt) {
+    int c = 0;
+    if (lane < 2) c = sturm_count_df(dd, ee2, n, lane == 0 ? lo : hi, pivmin);
+    const int clo = __shfl_sync(0xffffffffu, c, 0), chi = __shfl_sync(0xffffffffu, c, 1);
+    if (clo <= j && chi > j) break;
+    w *= 4.f;
+    if (attempt == 11) {
+      lo = df{gl, 0.f};
+      hi = df{gu, 0.f};
+    } else {
+      if (clo > j) lo = df{s0 - w, 0.f};
+      if (chi <= j) hi = df{s0 + w, 0.f};
+    }
+  }
+  const float tol = 1.0e-14f * tnorm + pivmin;
+  for (int round = 0; round < 12; ++round) {
+    const df width = df_sub(hi, lo);
+    if (!(width.hi > tol)) break;
+    const df x = df_add(lo, df_mul_f(width, static_cast<float>(lane + 1) * (1.f / 33.f)));
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_count_df(dd, ee2, n, x, pivmin) > j);
+    const int l1 = above ? __ffs(above) - 1 : 32;  // first point with more than j eigenvalues below
+    const float lhi = __shfl_sync(0xffffffffu, x.hi, l1 > 0 ? l1 - 1 : 0);
+    const float llo = __shfl_sync(0xffffffffu, x.lo, l1 > 0 ? l1 - 1 : 0);
+    const float hhi = __shfl_sync(0xffffffffu, x.hi, l1 < 32 ? l1 : 31);
+    const float hlo = __shfl_sync(0xffffffffu, x.lo, l1 < 32 ? l1 : 31);
+    if (l1 > 0) lo = df{lhi, llo};
+    if (l1 < 32) hi = df{hhi, hlo};
+  }
+  return df_mul_f(df_add(lo, hi), 0.5f);
+}
+
+// Gap between consecutive refined shifts, compared in float32 against the
+// cluster and group thresholds below.
+__device__ __forceinline__ float shift_gap(const df* shd, int j) {
+  return j > 0 ? df_float(df_sub(shd[j], shd[j - 1])) : 3.0e38f;
+}
+
+// Clusters and clean-up groups of the ascending shifts, by one thread.  Shifts
+// closer than 1e-9 ||T|| form clusters, iterated in rounds with Gram-Schmidt
+// (cpos[j]: position of j in its cluster, which starts at cstart[j]); runs of
+// shifts closer than 1e-4 ||T|| form the groups [gs0[j], gs1[j]) of the
+// Rayleigh-Ritz clean-up.  si[0] = the largest cluster position, si[1] = 1 if
+// any two shifts are closer than 1e-4 ||T||.
+__device__ void syev_groups(const df* shd, int nwant, float tnorm, float pivmin, int* cstart, int* cpos, int* gs0,
+                            int* gs1, int* si) {
+  const float ctol = 1.0e-9f * tnorm + pivmin, rtol = 1.0e-4f * tnorm;
+  int maxpos = 0, close = 0, gstart = 0;
+  for (int j = 0; j < nwant; ++j) {
+    const float gap = shift_gap(shd, j);
+    if (gap <= ctol) {
+      cstart[j] = cstart[j - 1];
+      cpos[j] = cpos[j - 1] + 1;
+    } else {
+      cstart[j] = j;
+      cpos[j] = 0;
+    }
+    if (gap <= rtol) {
+      close = 1;
+    } else if (j > 0) {
+      for (int i = gstart; i < j; ++i) gs1[i] = j;
+      gstart = j;
+    }
+    gs0[j] = gstart;
+    maxpos = max(maxpos, cpos[j]);
+  }
+  for (int i = gstart; i < nwant; ++i) gs1[i] = nwant;
+  si[0] = maxpos;
+  si[1] = close;
+}
+
+// Inverse iteration in float-float for the shift sg of index j, one thread:
+// T - sg I = L D L^T (pivots kept at least pv in magnitude), three solves from
+// a fixed start vector, each followed by Gram-Schmidt against the finished
+// members c0 .. jj-1 of its cluster and a normalisation.  Element i of the
+// vector, of 1/d and of l is at [i ld + jj] of Z, dinv and lm.
+__device__ void syev_inverse_iteration(int j, int jj, int c0, df sg, const df* dd, const df* ee, int n, df pv,
+                                       df* dinv, df* lm, df* Z, long long ld) {
+  df d = df_sub(dd[0], sg);
+  if (fabsf(d.hi) < pv.hi) d = df_lt0(d) ? df_neg(pv) : pv;
+  df di = df_div(df{1.f, 0.f}, d);
+  dinv[jj] = di;
+  for (int i = 1; i < n; ++i) {
+    const df e = ee[i - 1];
+    const df l = df_mul(e, di);
+    lm[(i - 1) * ld + jj] = l;
+    d = df_sub(df_sub(dd[i], sg), df_mul(l, e));
+    if (fabsf(d.hi) < pv.hi) d = df_lt0(d) ? df_neg(pv) : pv;
+    di = df_div(df{1.f, 0.f}, d);
+    dinv[i * ld + jj] = di;
+  }
+  // start vector
+  for (int i = 0; i < n; ++i) Z[i * ld + jj] = df{1.f + 0.37f * (float)((i * 7 + j * 13) % 11) / 11.f, 0.f};
+  for (int it = 0; it < 3; ++it) {
+    // L w = x ; z = D^-1 w ; L^T y = z
+    df prev = Z[jj];
+    for (int i = 1; i < n; ++i) {
+      prev = df_sub(Z[i * ld + jj], df_mul(lm[(i - 1) * ld + jj], prev));
+      Z[i * ld + jj] = prev;
+    }
+    df nxt = df_mul(Z[(n - 1) * ld + jj], dinv[(n - 1) * ld + jj]);
+    Z[(n - 1) * ld + jj] = nxt;
+    for (int i = n - 2; i >= 0; --i) {
+      nxt = df_sub(df_mul(Z[i * ld + jj], dinv[i * ld + jj]), df_mul(lm[i * ld + jj], nxt));
+      Z[i * ld + jj] = nxt;
+    }
+    // Gram-Schmidt against finished members of the cluster
+    for (int jp = c0; jp < jj; ++jp) {
+      df_acc dt = acc_zero();
+      for (int i = 0; i < n; ++i) dt.fma(Z[i * ld + jp], Z[i * ld + jj]);
+      const df dv = dt.value();
+      for (int i = 0; i < n; ++i) Z[i * ld + jj] = df_sub(Z[i * ld + jj], df_mul(dv, Z[i * ld + jp]));
+    }
+    // normalise (scale first by the largest entry to stay in range)
+    float amax = 0.f;
+    for (int i = 0; i < n; ++i) amax = fmaxf(amax, fabsf(Z[i * ld + jj].hi));
+    const float sc1 = amax > 0.f ? 1.f / amax : 1.f;
+    df_acc dn = acc_zero();
+    for (int i = 0; i < n; ++i) {
+      const df z = df_mul_f(Z[i * ld + jj], sc1);
+      Z[i * ld + jj] = z;
+      dn.fma(z, z);
+    }
+    const df inv = df_div(df{1.f, 0.f}, df_sqrt(dn.value()));
+    for (int i = 0; i < n; ++i) Z[i * ld + jj] = df_mul(Z[i * ld + jj], inv);
+  }
+}
+
+// A vector alone in its group, one thread: its Rayleigh quotient with T goes
+// to *eval and the vector, normalised, to Zn (element i at [i ldn]).  Z holds
+// element i at [i ldz].
+__device__ void syev_single(const df* Z, long long ldz, const df* dd, const df* ee, int n, df* Zn, long long ldn,
+                            double* eval) {
+  df_acc sq = acc_zero(), hq = acc_zero();
+  for (int i = 0; i < n; ++i) {
+    const df z = Z[i * ldz];
+    df_acc tz = acc_zero();
+    tz.fma(dd[i], z);
+    if (i > 0) tz.fma(ee[i - 1], Z[(i - 1) * ldz]);
+    if (i + 1 < n) tz.fma(ee[i], Z[(i + 1) * ldz]);
+    sq.fma(z, z);
+    hq.fma(z, tz.value());
+  }
+  const df sv = sq.value();
+  const df inv = df_div(df{1.f, 0.f}, df_sqrt(sv));
+  for (int i = 0; i < n; ++i) Zn[i * ldn] = df_mul(Z[i * ldz], inv);
+  *eval = df_to_double(df_div(hq.value(), sv));
+}
+
+// Rayleigh-Ritz clean-up of one group of G >= 2 vectors by the whole block.
+// The group's shifts are more than 1e-4 ||T|| from every other group's, so each
+// vector's error outside its own group's span is below ~4e-11, and a
+// Rayleigh-Ritz step on the span (S = Z_g^T Z_g, Hq = Z_g^T T Z_g) restores
+// working accuracy: S = L L^T, C = L^-1 Hq L^-T by parallel cyclic Jacobi,
+// vectors Z_g L^-T Q in ascending order.  Column c of the group is at
+// Z[i ldz + c] and goes to Zn[i ldn + c], its eigenvalue to evals[c].  rrw:
+// 4 G^2 df, perm: G ints, red, sf: block reduction scratch (shared).
+__device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, const df* ee, int n, df* rrw,
+                              int* perm, df_acc* red, float* sf, df* Zn, long long ldn, double* evals) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const long long N = n;
+  df* S = rrw;
+  df* Hq = rrw + G * G;
+  df* Qm = rrw + 2 * G * G;
+  df* Xm = rrw + 3 * G * G;
+  for (int idx = tid; idx < G * G; idx += nt) {
+    const int a0 = idx / G, b0 = idx % G;
+    if (b0 < a0) continue;
+    df_acc sa = acc_zero(), ha = acc_zero();
+    for (int i = 0; i < n; ++i) {
+      const df za = Z[i * ldz + a0];
+      const df zb = Z[i * ldz + b0];
+      sa.fma(za, zb);
+      df_acc tz = acc_zero();
+      tz.fma(dd[i], zb);
+      if (i > 0) tz.fma(ee[i - 1], Z[(i - 1) * ldz + b0]);
+      if (i + 1 < n) tz.fma(ee[i], Z[(i + 1) * ldz + b0]);
+      ha.fma(za, tz.value());
+    }
+    S[a0 * G + b0] = S[b0 * G + a0] = sa.value();
+    Hq[a0 * G + b0] = Hq[b0 * G + a0] = ha.value();
+  }
+  __syncthreads();
+  // Cholesky S = L L^T in place (lower), right-looking
+  for (int kk = 0; kk < G; ++kk) {
+    if (tid == 0) S[kk * G + kk] = df_sqrt(S[kk * G + kk]);
+    __syncthreads();
+    const df piv = S[kk * G + kk];
+    for (int i = kk + 1 + tid; i < G; i += nt) S[i * G + kk] = df_div(S[i * G + kk], piv);
+    __syncthreads();
+    for (int idx = tid; idx < (G - kk - 1) * (G - kk - 1); idx += nt) {
+      const int i = kk + 1 + idx / (G - kk - 1), jj = kk + 1 + idx % (G - kk - 1);
+      if (jj <= i) S[i * G + jj] = df_sub(S[i * G + jj], df_mul(S[i * G + kk], S[jj * G + kk]));
+    }
+    __syncthreads();
+  }
+  // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int col = tid; col < G; col += nt) {
+      for (int i = 0; i < G; ++i) {
+        df s = (pass == 0) ? Hq[i * G + col] : Xm[col * G + i];
+        for (int kk = 0; kk < i; ++kk)
+          s = df_sub(s, df_mul(S[i * G + kk], (pass == 0) ? Xm[kk * G + col] : Qm[kk * G + col]));
+        const df r = df_div(s, S[i * G + i]);
+        if (pass == 0) Xm[i * G + col] = r; else Qm[i * G + col] = r;
+      }
+    }
+    __syncthreads();
+  }
+  // Qm now holds C (symmetric); move it to Hq and set Qm = I
+  for (int idx = tid; idx < G * G; idx += nt) {
+    const int a0 = idx / G, b0 = idx % G;
+    const df cab = Qm[a0 * G + b0], cba = Qm[b0 * G + a0];
+    Hq[idx] = df_mul_f(df_add(cab, cba), 0.5f);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < G * G; idx += nt) Qm[idx] = df{(idx / G == idx % G) ? 1.f : 0.f, 0.f};
+  __syncthreads();
+  // parallel cyclic Jacobi (round-robin pairing) on C, accumulating Q
+  {
+    const int np = (G + 1) & ~1;  // even player count; index G is a dummy
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      // convergence test: largest off-diagonal entry against the largest diagonal one
+      float off = 0.f, dia = 0.f;
+      for (int idx = tid; idx < G * G; idx += nt) {
+        const int a0 = idx / G, b0 = idx % G;
+        const float x = fabsf(Hq[idx].hi);
+        if (a0 == b0) dia = fmaxf(dia, x); else off = fmaxf(off, x);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+        dia = fmaxf(dia, __shfl_xor_sync(0xffffffffu, dia, o));
+      }
+      if (lane == 0) {
+        red[warp].s = off;
+        red[warp].c = dia;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float o2 = 0.f, d2 = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) {
+          o2 = fmaxf(o2, red[w2].s);
+          d2 = fmaxf(d2, red[w2].c);
+        }
+        sf[0] = o2;
+        sf[1] = d2;
+      }
+      __syncthreads();
+      const float offmax = sf[0], diamax = sf[1];
+      __syncthreads();
+      if (!(offmax > 1.0e-15f * fmaxf(diamax, 1.0e-30f))) break;
+      for (int r = 0; r < np - 1; ++r) {
+        // pair t: players (a, b) of the round-robin schedule
+        for (int t = tid; t < np / 2; t += nt) {
+          int a0 = (t == 0) ? 0 : 1 + (t - 1 + r) % (np - 1);
+          int b0 = 1 + (np - 2 - t + r) % (np - 1);
+          if (a0 > b0) {
+            const int tmpi = a0;
+            a0 = b0;
+            b0 = tmpi;
+          }
+          df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
+          if (b0 < G) {
+            const df apq = Hq[a0 * G + b0];
+            const df app = Hq[a0 * G + a0], aqq = Hq[b0 * G + b0];
+            // skip entries already below the float-float resolution of the diagonal
+            const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
+            if (fabsf(apq.hi) > thr) {
+              // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
+              // and t = 1 / (2 theta) once theta^2 would leave the float range
+              const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
+              df tt;
+              if (fabsf(th.hi) > 1.0e12f) {
+                tt = df_div(df{0.5f, 0.f}, th);
+              } else {
+                const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
+                tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
+                if (df_lt0(th)) tt = df_neg(tt);
+              }
+              cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
+              sn = df_mul(tt, cs);
+            }
+          }
+          // stash rotation in Xm row 0..np/2 (cols 0..3)
+          Xm[t * 4 + 0] = cs;
+          Xm[t * 4 + 1] = sn;
+          reinterpret_cast<int*>(&Xm[t * 4 + 2])[0] = a0;
+          reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
+        }
+        __syncthreads();
+        // rows: C <- J^T C
+        for (int idx = tid; idx < (np / 2) * G; idx += nt) {
+          const int t = idx / G, col = idx % G;
+          const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
+          const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
+          if (b0 >= G) continue;
+          const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+          const df x = Hq[a0 * G + col], y = Hq[b0 * G + col];
+          Hq[a0 * G + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
+          Hq[b0 * G + col] = df_add(df_mul(sn, x), df_mul(cs, y));
+        }
+        __syncthreads();
+        // columns: C <- C J, Q <- Q J
+        for (int idx = tid; idx < (np / 2) * G; idx += nt) {
+          const int t = idx / G, row = idx % G;
+          const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
+          const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
+          if (b0 >= G) continue;
+          const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+          df x = Hq[row * G + a0], y = Hq[row * G + b0];
+          Hq[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+          Hq[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+          x = Qm[row * G + a0];
+          y = Qm[row * G + b0];
+          Qm[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+          Qm[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // order eigenvalues ascending (selection by rank; ties broken by index)
+  for (int j = tid; j < G; j += nt) {
+    const df lj = Hq[j * G + j];
+    int rank = 0;
+    for (int i = 0; i < G; ++i) {
+      const df li = Hq[i * G + i];
+      const df dlt = df_sub(li, lj);
+      if (df_lt0(dlt) || ((dlt.hi == 0.f && dlt.lo == 0.f) && i < j)) ++rank;
+    }
+    perm[rank] = j;
+  }
+  __syncthreads();
+  // Xm = L^-T Q  (back substitution per column)
+  for (int col = tid; col < G; col += nt) {
+    for (int i = G - 1; i >= 0; --i) {
+      df s = Qm[i * G + col];
+      for (int kk = i + 1; kk < G; ++kk) s = df_sub(s, df_mul(S[kk * G + i], Xm[kk * G + col]));
+      Xm[i * G + col] = df_div(s, S[i * G + i]);
+    }
+  }
+  __syncthreads();
+  // group eigenvectors Zn[:, c] = Z_g Xm[:, perm[c]] (ascending within the group)
+  for (long long idx = tid; idx < N * G; idx += nt) {
+    const int i = static_cast<int>(idx / G), c = static_cast<int>(idx % G);
+    const int src = perm[c];
+    df_acc sa = acc_zero();
+    for (int kk = 0; kk < G; ++kk) sa.fma(Z[i * ldz + kk], Xm[kk * G + src]);
+    Zn[i * ldn + c] = sa.value();
+  }
+  for (int c = tid; c < G; c += nt) evals[c] = df_to_double(Hq[perm[c] * G + perm[c]]);
+  __syncthreads();
+}
+
+// ---- one-block driver
+//
+// Dynamic shared memory: v, p (df, n each), sd, se2 (float, n each), shift
+// (float, nwant), cstart, cpos (int, nwant), d, e, tau, e^2 (df, n each),
+// shifts (df, nwant), gs0, gs1 (int, nwant), then -- when they fit -- the
+// working matrix W (n x ldw df), the inverse-iteration factors (2 x n x nwant
+// df) and the tridiagonal eigenvectors Zt (n x nwant df).  `flags` bit 0/1/2
+// says which of W / factors / Zt live in shared memory; the others use the
+// global workspace (same layout), so one code path serves every size.
+constexpr int kSyW = 1, kSyF = 2, kSyZ = 4;
+
+__global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ldw, int flags,
+                                                        const double* __restrict__ H, double* __restrict__ evals,
+                                                        double* __restrict__ evecs, df* __restrict__ Wg,
+                                                        df* __restrict__ tau_g, df* __restrict__ dd_g,
+                                                        df* __restrict__ ee_g, df* __restrict__ facg,
+                                                        df* __restrict__ Ztg, df* __restrict__ rrw,
+                                                        int* __restrict__ perm, const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;  // the structured fast path already produced the pairs
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df* v = reinterpret_cast<df*>(smem_raw);
+  df* p = v + n;
+  float* sd = reinterpret_cast<float*>(p + n);
+  float* se2 = sd + n;
+  float* shift = se2 + n;
+  int* cstart = reinterpret_cast<int*>(shift + nwant);
+  int* cpos = cstart + nwant;
+  size_t off = (2 * sizeof(df) * n + 2 * sizeof(float) * n + sizeof(float) * nwant + 2 * sizeof(int) * nwant +
+                4 * sizeof(df) * n + sizeof(df) * nwant + 2 * sizeof(int) * nwant + 15) &
+               ~static_cast<size_t>(15);
+  df* W = Wg;
+  if (flags & kSyW) {
+    W = reinterpret_cast<df*>(smem_raw + off);
+    off += sizeof(df) * static_cast<size_t>(n) * ldw;
+  }
+  df* fac = facg;
+  if (flags & kSyF) {
+    fac = reinterpret_cast<df*>(smem_raw + off);
+    off += sizeof(df) * 2 * static_cast<size_t>(n) * nwant;
+  }
+  df* Zt = Ztg;
+  if (flags & kSyZ) Zt = reinterpret_cast<df*>(smem_raw + off);
+  __shared__ df_acc red[32];
+  __shared__ float sf[4];
+  __shared__ int si[4];
+
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const long long N = n, LD = ldw;
+  // the tridiagonal (d, e) and the Householder scalars live in shared memory
+  df* dd = reinterpret_cast<df*>(cpos + nwant);
+  df* ee = dd + n;
+  df* tau = ee + n;
+  df* ee2 = tau + n;     // e_i^2 in float-float (Sturm counts)
+  df* shd = ee2 + n;     // float-float shifts (nwant)
+  int* gs0 = reinterpret_cast<int*>(shd + nwant);  // clean-up group [gs0[j], gs1[j]) of index j
+  int* gs1 = gs0 + nwant;
+  __shared__ df_acc red_sig[32], red_vp[32];
+
+  for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
+  __syncthreads();
+  syev_tridiagonalise(n, W, LD, v, p, dd, ee, tau, red_sig, red_vp, nullptr);
+
+  // ---- bisection (float32) for the nwant smallest eigenvalues, refined in float-float
   for (int i = tid; i < n; i += nt) {
     sd[i] = df_float(dd[i]);
     if (i + 1 < n) {
@@ -295,103 +735,18 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    float gl = 3.0e38f, gu = -3.0e38f, emax2 = 0.f;
-    for (int i = 0; i < n; ++i) {
-      const float r = (i > 0 ? sqrtf(se2[i - 1]) : 0.f) + (i + 1 < n ? sqrtf(se2[i]) : 0.f);
-      gl = fminf(gl, sd[i] - r);
-      gu = fmaxf(gu, sd[i] + r);
-      if (i + 1 < n) emax2 = fmaxf(emax2, se2[i]);
-    }
-    const float tn = fmaxf(fabsf(gl), fabsf(gu));
-    const float pad = 2.0e-6f * tn + 1.0e-30f;
-    sf[0] = gl - pad;
-    sf[1] = gu + pad;
-    sf[2] = tn;
-    sf[3] = fmaxf(1.0e-30f, 1.0e-35f * fmaxf(emax2, 1.f));
-  }
+  if (tid == 0) syev_bounds(sd, se2, n, sf);
   __syncthreads();
   const float gl = sf[0], gu = sf[1], tnorm = sf[2], pivmin = sf[3];
-  for (int j = tid; j < nwant; j += nt) {
-    float lo = gl, hi = gu;
-    for (int it = 0; it < 80; ++it) {
-      const float mid = 0.5f * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (sturm_count(sd, se2, n, mid, pivmin) > j) hi = mid; else lo = mid;
-    }
-    shift[j] = 0.5f * (lo + hi);
-  }
+  for (int j = tid; j < nwant; j += nt) shift[j] = syev_bisect(j, sd, se2, n, gl, gu, pivmin);
   for (int i = tid; i + 1 < n; i += nt) ee2[i] = df_mul(ee[i], ee[i]);
   __syncthreads();
-  // Refine each shift with float-float Sturm counts.  The float32 counts can be
-  // off by ~n 2^-24 ||T||, far more than the gaps inside a graded spectrum; with
-  // float-float shifts the inverse iteration below separates eigenvalues down to
-  // ~1e-9 ||T|| apart on its own.  One warp per eigenvalue: the bracket is first
-  // widened until its float-float counts enclose index j, then 32-point
-  // multisection shrinks it 33x per round (Golub & Van Loan 8.4.1).
   for (int j = warp; j < nwant; j += nw) {
-    const float s0 = shift[j];
-    float w = 1.0e-4f * tnorm + 1.0e-6f * fabsf(s0) + pivmin;
-    df lo = df{s0 - w, 0.f}, hi = df{s0 + w, 0.f};
-    for (int attempt = 0; attempt < 12; ++attempt) {
-      int c = 0;
-      if (lane < 2) c = sturm_count_df(dd, ee2, n, lane == 0 ? lo : hi, pivmin);
-      const int clo = __shfl_sync(0xffffffffu, c, 0), chi = __shfl_sync(0xffffffffu, c, 1);
-      if (clo <= j && chi > j) break;
-      w *= 4.f;
-      if (attempt == 11) {
-        lo = df{gl, 0.f};
-        hi = df{gu, 0.f};
-      } else {
-        if (clo > j) lo = df{s0 - w, 0.f};
-        if (chi <= j) hi = df{s0 + w, 0.f};
-      }
-    }
-    const float tol = 1.0e-14f * tnorm + pivmin;
-    for (int round = 0; round < 12; ++round) {
-      const df width = df_sub(hi, lo);
-      if (!(width.hi > tol)) break;
-      const df x = df_add(lo, df_mul_f(width, static_cast<float>(lane + 1) * (1.f / 33.f)));
-      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_df(dd, ee2, n, x, pivmin) > j);
-      const int l1 = above ? __ffs(above) - 1 : 32;  // first point with more than j eigenvalues below
-      const float lhi = __shfl_sync(0xffffffffu, x.hi, l1 > 0 ? l1 - 1 : 0);
-      const float llo = __shfl_sync(0xffffffffu, x.lo, l1 > 0 ? l1 - 1 : 0);
-      const float hhi = __shfl_sync(0xffffffffu, x.hi, l1 < 32 ? l1 : 31);
-      const float hlo = __shfl_sync(0xffffffffu, x.lo, l1 < 32 ? l1 : 31);
-      if (l1 > 0) lo = df{lhi, llo};
-      if (l1 < 32) hi = df{hhi, hlo};
-    }
-    if (lane == 0) shd[j] = df_mul_f(df_add(lo, hi), 0.5f);
+    const df s = syev_refine_shift(j, shift[j], dd, ee2, n, gl, gu, tnorm, pivmin);
+    if (lane == 0) shd[j] = s;
   }
   __syncthreads();
-  // Clusters of shifts closer than 1e-9 ||T|| are iterated in rounds with
-  // Gram-Schmidt; any pair closer than 1e-4 ||T|| sends the block through the
-  // Rayleigh-Ritz clean-up below (orthogonality to working accuracy).
-  if (tid == 0) {
-    const float ctol = 1.0e-9f * tnorm + pivmin, rtol = 1.0e-4f * tnorm;
-    int maxpos = 0, close = 0, gstart = 0;
-    for (int j = 0; j < nwant; ++j) {
-      const float gap = j > 0 ? df_float(df_sub(shd[j], shd[j - 1])) : 3.0e38f;
-      if (gap <= ctol) {
-        cstart[j] = cstart[j - 1];
-        cpos[j] = cpos[j - 1] + 1;
-      } else {
-        cstart[j] = j;
-        cpos[j] = 0;
-      }
-      if (gap <= rtol) {
-        close = 1;
-      } else if (j > 0) {
-        for (int i = gstart; i < j; ++i) gs1[i] = j;
-        gstart = j;
-      }
-      gs0[j] = gstart;
-      maxpos = max(maxpos, cpos[j]);
-    }
-    for (int i = gstart; i < nwant; ++i) gs1[i] = nwant;
-    si[0] = maxpos;
-    si[1] = close;
-  }
+  if (tid == 0) syev_groups(shd, nwant, tnorm, pivmin, cstart, cpos, gs0, gs1, si);
   __syncthreads();
   const int maxpos = si[0];
   const bool cleanup = si[1] != 0;
@@ -404,57 +759,7 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
   for (int round = 0; round <= maxpos; ++round) {
     for (int j = tid; j < nwant; j += nt) {
       if (cpos[j] != round) continue;
-      const df sg = shd[j];
-      df* dinv = fac;
-      df* lm = fac + N * NW;
-      df d = df_sub(dd[0], sg);
-      if (fabsf(d.hi) < pv.hi) d = df_lt0(d) ? df_neg(pv) : pv;
-      df di = df_div(df{1.f, 0.f}, d);
-      dinv[j] = di;
-      for (int i = 1; i < n; ++i) {
-        const df e = ee[i - 1];
-        const df l = df_mul(e, di);
-        lm[(i - 1) * NW + j] = l;
-        d = df_sub(df_sub(dd[i], sg), df_mul(l, e));
-        if (fabsf(d.hi) < pv.hi) d = df_lt0(d) ? df_neg(pv) : pv;
-        di = df_div(df{1.f, 0.f}, d);
-        dinv[i * NW + j] = di;
-      }
-      // start vector
-      for (int i = 0; i < n; ++i) Zt[i * NW + j] = df{1.f + 0.37f * (float)((i * 7 + j * 13) % 11) / 11.f, 0.f};
-      for (int it = 0; it < 3; ++it) {
-        // L w = x ; z = D^-1 w ; L^T y = z
-        df prev = Zt[j];
-        for (int i = 1; i < n; ++i) {
-          prev = df_sub(Zt[i * NW + j], df_mul(lm[(i - 1) * NW + j], prev));
-          Zt[i * NW + j] = prev;
-        }
-        df nxt = df_mul(Zt[(n - 1) * NW + j], dinv[(n - 1) * NW + j]);
-        Zt[(n - 1) * NW + j] = nxt;
-        for (int i = n - 2; i >= 0; --i) {
-          nxt = df_sub(df_mul(Zt[i * NW + j], dinv[i * NW + j]), df_mul(lm[i * NW + j], nxt));
-          Zt[i * NW + j] = nxt;
-        }
-        // Gram-Schmidt against finished members of the cluster
-        for (int jp = cstart[j]; jp < j; ++jp) {
-          df_acc dt = acc_zero();
-          for (int i = 0; i < n; ++i) dt.fma(Zt[i * NW + jp], Zt[i * NW + j]);
-          const df dv = dt.value();
-          for (int i = 0; i < n; ++i) Zt[i * NW + j] = df_sub(Zt[i * NW + j], df_mul(dv, Zt[i * NW + jp]));
-        }
-        // normalise (scale first by the largest entry to stay in range)
-        float amax = 0.f;
-        for (int i = 0; i < n; ++i) amax = fmaxf(amax, fabsf(Zt[i * NW + j].hi));
-        const float sc1 = amax > 0.f ? 1.f / amax : 1.f;
-        df_acc dn = acc_zero();
-        for (int i = 0; i < n; ++i) {
-          const df z = df_mul_f(Zt[i * NW + j], sc1);
-          Zt[i * NW + j] = z;
-          dn.fma(z, z);
-        }
-        const df inv = df_div(df{1.f, 0.f}, df_sqrt(dn.value()));
-        for (int i = 0; i < n; ++i) Zt[i * NW + j] = df_mul(Zt[i * NW + j], inv);
-      }
+      syev_inverse_iteration(j, j, cstart[j], shd[j], dd, ee, n, pv, fac, fac + N * NW, Zt, NW);
     }
     __syncthreads();
   }
@@ -478,229 +783,16 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     }
     __syncthreads();
   } else {
-    // ---- Rayleigh-Ritz clean-up ---------------------------------------------
-    // Shifts closer than 1e-4 ||T|| form groups (runs of consecutive indices);
-    // groups are more than 1e-4 ||T|| apart, so each vector's error outside its
-    // own group's span is below ~4e-11 and a Rayleigh-Ritz step on each group's
-    // span (S = Z_g^T Z_g, Hq = Z_g^T T Z_g) restores working accuracy.  Single
-    // vectors only need their Rayleigh quotient; the groups of two or more run
-    // one after another on windows of the workspace.
+    // single vectors only need their Rayleigh quotient; the groups of two or
+    // more run one after another on windows of the workspace
     for (int j = tid; j < nwant; j += nt) {
       if (gs1[j] - gs0[j] != 1) continue;
-      df_acc sq = acc_zero(), hq = acc_zero();
-      for (int i = 0; i < n; ++i) {
-        const df z = Zt[i * NW + j];
-        df_acc tz = acc_zero();
-        tz.fma(dd[i], z);
-        if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + j]);
-        if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + j]);
-        sq.fma(z, z);
-        hq.fma(z, tz.value());
-      }
-      const df sv = sq.value();
-      const df inv = df_div(df{1.f, 0.f}, df_sqrt(sv));
-      for (int i = 0; i < n; ++i) Zn[i * NW + j] = df_mul(Zt[i * NW + j], inv);
-      evals[j] = df_to_double(df_div(hq.value(), sv));
+      syev_single(Zt + j, NW, dd, ee, n, Zn + j, NW, evals + j);
     }
     __syncthreads();
     for (int g0 = 0; g0 < nwant;) {
       const int g1 = gs1[g0], G = g1 - g0;
-      if (G < 2) {
-        g0 = g1;
-        continue;
-      }
-      df* S = rrw;
-      df* Hq = rrw + G * G;
-      df* Qm = rrw + 2 * G * G;
-      df* Xm = rrw + 3 * G * G;
-      for (int idx = tid; idx < G * G; idx += nt) {
-        const int a0 = idx / G, b0 = idx % G;
-        if (b0 < a0) continue;
-        df_acc sa = acc_zero(), ha = acc_zero();
-        for (int i = 0; i < n; ++i) {
-          const df za = Zt[i * NW + g0 + a0];
-          const df zb = Zt[i * NW + g0 + b0];
-          sa.fma(za, zb);
-          df_acc tz = acc_zero();
-          tz.fma(dd[i], zb);
-          if (i > 0) tz.fma(ee[i - 1], Zt[(i - 1) * NW + g0 + b0]);
-          if (i + 1 < n) tz.fma(ee[i], Zt[(i + 1) * NW + g0 + b0]);
-          ha.fma(za, tz.value());
-        }
-        S[a0 * G + b0] = S[b0 * G + a0] = sa.value();
-        Hq[a0 * G + b0] = Hq[b0 * G + a0] = ha.value();
-      }
-      __syncthreads();
-      // Cholesky S = L L^T in place (lower), right-looking
-      for (int kk = 0; kk < G; ++kk) {
-        if (tid == 0) S[kk * G + kk] = df_sqrt(S[kk * G + kk]);
-        __syncthreads();
-        const df piv = S[kk * G + kk];
-        for (int i = kk + 1 + tid; i < G; i += nt) S[i * G + kk] = df_div(S[i * G + kk], piv);
-        __syncthreads();
-        for (int idx = tid; idx < (G - kk - 1) * (G - kk - 1); idx += nt) {
-          const int i = kk + 1 + idx / (G - kk - 1), jj = kk + 1 + idx % (G - kk - 1);
-          if (jj <= i) S[i * G + jj] = df_sub(S[i * G + jj], df_mul(S[i * G + kk], S[jj * G + kk]));
-        }
-        __syncthreads();
-      }
-      // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int col = tid; col < G; col += nt) {
-          for (int i = 0; i < G; ++i) {
-            df s = (pass == 0) ? Hq[i * G + col] : Xm[col * G + i];
-            for (int kk = 0; kk < i; ++kk)
-              s = df_sub(s, df_mul(S[i * G + kk], (pass == 0) ? Xm[kk * G + col] : Qm[kk * G + col]));
-            const df r = df_div(s, S[i * G + i]);
-            if (pass == 0) Xm[i * G + col] = r; else Qm[i * G + col] = r;
-          }
-        }
-        __syncthreads();
-      }
-      // Qm now holds C (symmetric); move it to Hq and set Qm = I
-      for (int idx = tid; idx < G * G; idx += nt) {
-        const int a0 = idx / G, b0 = idx % G;
-        const df cab = Qm[a0 * G + b0], cba = Qm[b0 * G + a0];
-        Hq[idx] = df_mul_f(df_add(cab, cba), 0.5f);
-      }
-      __syncthreads();
-      for (int idx = tid; idx < G * G; idx += nt) Qm[idx] = df{(idx / G == idx % G) ? 1.f : 0.f, 0.f};
-      __syncthreads();
-      // parallel cyclic Jacobi (round-robin pairing) on C, accumulating Q
-      {
-        const int np = (G + 1) & ~1;  // even player count; index G is a dummy
-        for (int sweep = 0; sweep < 12; ++sweep) {
-          // convergence test: largest off-diagonal entry against the largest diagonal one
-          float off = 0.f, dia = 0.f;
-          for (int idx = tid; idx < G * G; idx += nt) {
-            const int a0 = idx / G, b0 = idx % G;
-            const float x = fabsf(Hq[idx].hi);
-            if (a0 == b0) dia = fmaxf(dia, x); else off = fmaxf(off, x);
-          }
-    #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
-            dia = fmaxf(dia, __shfl_xor_sync(0xffffffffu, dia, o));
-          }
-          if (lane == 0) {
-            red[warp].s = off;
-            red[warp].c = dia;
-          }
-          __syncthreads();
-          if (tid == 0) {
-            float o2 = 0.f, d2 = 0.f;
-            for (int w2 = 0; w2 < nw; ++w2) {
-              o2 = fmaxf(o2, red[w2].s);
-              d2 = fmaxf(d2, red[w2].c);
-            }
-            sf[0] = o2;
-            sf[1] = d2;
-          }
-          __syncthreads();
-          const float offmax = sf[0], diamax = sf[1];
-          __syncthreads();
-          if (!(offmax > 1.0e-15f * fmaxf(diamax, 1.0e-30f))) break;
-          for (int r = 0; r < np - 1; ++r) {
-            // pair t: players (a, b) of the round-robin schedule
-            for (int t = tid; t < np / 2; t += nt) {
-              int a0 = (t == 0) ? 0 : 1 + (t - 1 + r) % (np - 1);
-              int b0 = 1 + (np - 2 - t + r) % (np - 1);
-              if (a0 > b0) {
-                const int tmpi = a0;
-                a0 = b0;
-                b0 = tmpi;
-              }
-              df cs = df{1.f, 0.f}, sn = df{0.f, 0.f};
-              if (b0 < G) {
-                const df apq = Hq[a0 * G + b0];
-                const df app = Hq[a0 * G + a0], aqq = Hq[b0 * G + b0];
-                // skip entries already below the float-float resolution of the diagonal
-                const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
-                if (fabsf(apq.hi) > thr) {
-                  // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
-                  // and t = 1 / (2 theta) once theta^2 would leave the float range
-                  const df th = df_div(df_sub(aqq, app), df_mul_f(apq, 2.f));
-                  df tt;
-                  if (fabsf(th.hi) > 1.0e12f) {
-                    tt = df_div(df{0.5f, 0.f}, th);
-                  } else {
-                    const df rt = df_sqrt(df_add(df_mul(th, th), df{1.f, 0.f}));
-                    tt = df_div(df{1.f, 0.f}, df_add(df_abs(th), rt));
-                    if (df_lt0(th)) tt = df_neg(tt);
-                  }
-                  cs = df_div(df{1.f, 0.f}, df_sqrt(df_add(df_mul(tt, tt), df{1.f, 0.f})));
-                  sn = df_mul(tt, cs);
-                }
-              }
-              // stash rotation in Xm row 0..np/2 (cols 0..3)
-              Xm[t * 4 + 0] = cs;
-              Xm[t * 4 + 1] = sn;
-              reinterpret_cast<int*>(&Xm[t * 4 + 2])[0] = a0;
-              reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
-            }
-            __syncthreads();
-            // rows: C <- J^T C
-            for (int idx = tid; idx < (np / 2) * G; idx += nt) {
-              const int t = idx / G, col = idx % G;
-              const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-              const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-              if (b0 >= G) continue;
-              const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-              const df x = Hq[a0 * G + col], y = Hq[b0 * G + col];
-              Hq[a0 * G + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
-              Hq[b0 * G + col] = df_add(df_mul(sn, x), df_mul(cs, y));
-            }
-            __syncthreads();
-            // columns: C <- C J, Q <- Q J
-            for (int idx = tid; idx < (np / 2) * G; idx += nt) {
-              const int t = idx / G, row = idx % G;
-              const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-              const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-              if (b0 >= G) continue;
-              const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-              df x = Hq[row * G + a0], y = Hq[row * G + b0];
-              Hq[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-              Hq[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-              x = Qm[row * G + a0];
-              y = Qm[row * G + b0];
-              Qm[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-              Qm[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-            }
-            __syncthreads();
-          }
-        }
-      }
-      // order eigenvalues ascending (selection by rank; ties broken by index)
-      for (int j = tid; j < G; j += nt) {
-        const df lj = Hq[j * G + j];
-        int rank = 0;
-        for (int i = 0; i < G; ++i) {
-          const df li = Hq[i * G + i];
-          const df dlt = df_sub(li, lj);
-          if (df_lt0(dlt) || ((dlt.hi == 0.f && dlt.lo == 0.f) && i < j)) ++rank;
-        }
-        perm[rank] = j;
-      }
-      __syncthreads();
-      // Xm = L^-T Q  (back substitution per column)
-      for (int col = tid; col < G; col += nt) {
-        for (int i = G - 1; i >= 0; --i) {
-          df s = Qm[i * G + col];
-          for (int kk = i + 1; kk < G; ++kk) s = df_sub(s, df_mul(S[kk * G + i], Xm[kk * G + col]));
-          Xm[i * G + col] = df_div(s, S[i * G + i]);
-        }
-      }
-      __syncthreads();
-      // group eigenvectors Zn[:, g0 + c] = Z_g Xm[:, perm[c]] (ascending within the group)
-      for (long long idx = tid; idx < N * G; idx += nt) {
-        const int i = static_cast<int>(idx / G), c = static_cast<int>(idx % G);
-        const int src = perm[c];
-        df_acc sa = acc_zero();
-        for (int kk = 0; kk < G; ++kk) sa.fma(Zt[i * NW + g0 + kk], Xm[kk * G + src]);
-        Zn[i * NW + g0 + c] = sa.value();
-      }
-      for (int c = tid; c < G; c += nt) evals[g0 + c] = df_to_double(Hq[perm[c] * G + perm[c]]);
-      __syncthreads();
+      if (G >= 2) syev_group_rr(G, Zt + g0, NW, dd, ee, n, rrw, perm, red, sf, Zn + g0, NW, evals + g0);
       g0 = g1;
     }
   }
@@ -749,6 +841,228 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     __syncthreads();
   }
   for (long long idx = tid; idx < N * NW; idx += nt) evecs[idx] = df_to_double(Zn[idx]);
+}
+
+// ---- split driver
+//
+// Global workspace: W (n x ldw df) unless it fits in shared memory, the
+// reflectors hv (v_k at hv[k n ..]), dd, ee, tau (df, n each), the shifts shd
+// (df, nwant) and their bounds (4 floats), the factors and working vectors of
+// groups too wide for shared memory (fac: 3 n nwant df) and the tridiagonal
+// eigenvectors Zg (n x nwant df).
+constexpr int kSvWarps = 4;  // shifts per block of k_syev_vals
+constexpr int kSvecThreads = 512;
+constexpr int kSbWarps = 8;  // eigenvectors per block of k_syev_back
+constexpr int kSbChunk = 8;  // reflectors staged per barrier in k_syev_back
+
+// Tridiagonalisation, one block: W in shared memory when `inshared`, else the
+// global Wg.  Writes dd, ee, tau and the reflectors hv to global memory.
+__global__ void __launch_bounds__(kSyThreads) k_syev_tri(int n, int ldw, int inshared, const double* __restrict__ H,
+                                                         df* __restrict__ Wg, df* __restrict__ hv,
+                                                         df* __restrict__ dd_g, df* __restrict__ ee_g,
+                                                         df* __restrict__ tau_g, const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df* v = reinterpret_cast<df*>(smem_raw);
+  df* p = v + n;
+  df* dd = p + n;
+  df* ee = dd + n;
+  df* tau = ee + n;
+  const size_t off = (5 * sizeof(df) * static_cast<size_t>(n) + 15) & ~static_cast<size_t>(15);
+  df* W = inshared ? reinterpret_cast<df*>(smem_raw + off) : Wg;
+  __shared__ df_acc red_sig[32], red_vp[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long N = n, LD = ldw;
+  for (long long i = tid; i < N * N; i += nt) W[(i / N) * LD + (i % N)] = df_from_double(H[i]);
+  __syncthreads();
+  syev_tridiagonalise(n, W, LD, v, p, dd, ee, tau, red_sig, red_vp, hv);
+  for (int i = tid; i < n; i += nt) {
+    dd_g[i] = dd[i];
+    tau_g[i] = tau[i];
+    if (i + 1 < n) ee_g[i] = ee[i];
+  }
+}
+
+// The refined shifts, one warp each (kSvWarps per block): float32 multisection
+// then float-float refinement.  Block 0 also writes the bounds.  Shared: dd,
+// ee2 (df, n each), sd, se2 (float, n each).
+__global__ void __launch_bounds__(32 * kSvWarps) k_syev_vals(int n, int nwant, const df* __restrict__ dd_g,
+                                                             const df* __restrict__ ee_g, df* __restrict__ shd,
+                                                             float* __restrict__ bounds,
+                                                             const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df* dd = reinterpret_cast<df*>(smem_raw);
+  df* ee2 = dd + n;
+  float* sd = reinterpret_cast<float*>(ee2 + n);
+  float* se2 = sd + n;
+  __shared__ float sf[4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const df d = dd_g[i];
+    dd[i] = d;
+    sd[i] = df_float(d);
+    if (i + 1 < n) {
+      const df e = ee_g[i];
+      const float ef = df_float(e);
+      se2[i] = ef * ef;
+      ee2[i] = df_mul(e, e);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) syev_bounds(sd, se2, n, sf);
+  __syncthreads();
+  if (blockIdx.x == 0 && tid < 4) bounds[tid] = sf[tid];
+  const int j = blockIdx.x * kSvWarps + warp;
+  if (j >= nwant) return;  // whole warps: no block barrier below
+  const float gl = sf[0], gu = sf[1], tnorm = sf[2], pivmin = sf[3];
+  const float s0 = syev_multisect(j, sd, se2, n, gl, gu, pivmin);
+  const df s = syev_refine_shift(j, s0, dd, ee2, n, gl, gu, tnorm, pivmin);
+  if (lane == 0) shd[j] = s;
+}
+
+// Bytes of shared memory k_syev_vecs keeps for a group of G vectors: d, e
+// (2n df), cluster data (2G ints), perm (G ints), and -- in shared memory when
+// they fit -- the factors and vectors (3 n G df) and the clean-up matrices (4 G^2 df).
+__host__ __device__ inline size_t syev_vecs_base(int n, int G) {
+  return (2 * sizeof(df) * static_cast<size_t>(n) + 3 * sizeof(int) * static_cast<size_t>(G) + 15) &
+         ~static_cast<size_t>(15);
+}
+__host__ __device__ inline size_t syev_vecs_work(int n, int G) {
+  return sizeof(df) * (3 * static_cast<size_t>(n) * G + 4 * static_cast<size_t>(G) * G);
+}
+
+// Inverse iteration and clean-up, one block per group of close shifts: block b
+// takes the group that starts at index b (the others exit at once).  A group's
+// clusters lie inside it (1e-9 ||T|| < 1e-4 ||T||), so every block runs alone.
+// Writes the tridiagonal eigenvectors Zg (n x nwant) and the eigenvalues.
+__global__ void __launch_bounds__(kSvecThreads) k_syev_vecs(int n, int nwant, size_t smem_bytes,
+                                                            const df* __restrict__ dd_g, const df* __restrict__ ee_g,
+                                                            const df* __restrict__ shd, const float* __restrict__ bounds,
+                                                            df* __restrict__ facg, df* __restrict__ rrg,
+                                                            df* __restrict__ Zg, double* __restrict__ evals,
+                                                            const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const float tnorm = bounds[2], pivmin = bounds[3];
+  const float ctol = 1.0e-9f * tnorm + pivmin, rtol = 1.0e-4f * tnorm;
+  const int b = blockIdx.x;
+  if (b > 0 && shift_gap(shd, b) <= rtol) return;  // not the first index of a group
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ df_acc red[32];
+  __shared__ float sf[4];
+  __shared__ int sg[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    int g1 = b + 1;
+    while (g1 < nwant && shift_gap(shd, g1) <= rtol) ++g1;
+    sg[0] = g1 - b;
+  }
+  __syncthreads();
+  const int G = sg[0];
+  df* dd = reinterpret_cast<df*>(smem_raw);
+  df* ee = dd + n;
+  int* cst = reinterpret_cast<int*>(ee + n);  // cluster start, local index
+  int* cps = cst + G;                         // position in the cluster
+  int* perm = cps + G;
+  for (int i = tid; i < n; i += nt) {
+    dd[i] = dd_g[i];
+    if (i + 1 < n) ee[i] = ee_g[i];
+  }
+  if (tid == 0) {
+    int maxpos = 0;
+    for (int jj = 0; jj < G; ++jj) {
+      if (jj == 0 || !(shift_gap(shd, b + jj) <= ctol)) {
+        cst[jj] = jj;
+        cps[jj] = 0;
+      } else {
+        cst[jj] = cst[jj - 1];
+        cps[jj] = cps[jj - 1] + 1;
+      }
+      maxpos = max(maxpos, cps[jj]);
+    }
+    sg[1] = maxpos;
+  }
+  __syncthreads();
+  const int maxpos = sg[1];
+  const long long N = n, NW = nwant;
+  // working storage: shared memory when the group fits, else its columns of the global workspace
+  const size_t base = syev_vecs_base(n, G);
+  const bool local = base + syev_vecs_work(n, G) <= smem_bytes;
+  df *dinv, *lm, *Z, *rrw;
+  long long ld;
+  if (local) {
+    dinv = reinterpret_cast<df*>(smem_raw + base);
+    lm = dinv + N * G;
+    Z = lm + N * G;
+    rrw = Z + N * G;
+    ld = G;
+  } else {
+    dinv = facg + b;
+    lm = facg + N * NW + b;
+    Z = facg + 2 * N * NW + b;
+    rrw = rrg + 4LL * b * NW;  // 4 G^2 <= 4 NW (NW - b): the groups' windows do not overlap
+    ld = NW;
+  }
+  const df pv = df{fmaxf(3.6e-15f * tnorm, 1.0e-30f), 0.f};
+  for (int round = 0; round <= maxpos; ++round) {
+    for (int jj = tid; jj < G; jj += nt)
+      if (cps[jj] == round) syev_inverse_iteration(b + jj, jj, cst[jj], shd[b + jj], dd, ee, n, pv, dinv, lm, Z, ld);
+    __syncthreads();
+  }
+  if (G == 1) {
+    if (tid == 0) syev_single(Z, ld, dd, ee, n, Zg + b, NW, evals + b);
+  } else {
+    syev_group_rr(G, Z, ld, dd, ee, n, rrw, perm, red, sf, Zg + b, NW, evals + b);
+  }
+}
+
+// Back-transformation y = H_0 H_1 ... H_{n-3} z, one warp per eigenvector
+// (column c of Zg), held in shared memory; the block stages kSbChunk
+// reflectors at a time (chunk = reflectors k0, k0 - 1, ...) and each warp then
+// applies them to its own column without further barriers.  Writes evecs
+// (n x nwant float64).
+__global__ void __launch_bounds__(32 * kSbWarps) k_syev_back(int n, int nwant, int chunk, const df* __restrict__ hv,
+                                                             const df* __restrict__ tau_g,
+                                                             const df* __restrict__ Zg, double* __restrict__ evecs,
+                                                             const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wpb = blockDim.x >> 5;
+  const long long NW = nwant;
+  df* zs = reinterpret_cast<df*>(smem_raw);  // wpb x n
+  df* vs = zs + static_cast<long long>(wpb) * n;  // chunk x n
+  const int c = blockIdx.x * wpb + warp;
+  const bool live = c < nwant;
+  df* z = zs + static_cast<long long>(warp) * n;
+  if (live)
+    for (int i = lane; i < n; i += 32) z[i] = Zg[i * NW + c];
+  for (int k0 = n - 3; k0 >= 0; k0 -= chunk) {
+    const int nk = min(chunk, k0 + 1);
+    __syncthreads();  // the previous chunk is no longer read
+    for (long long idx = tid; idx < static_cast<long long>(nk) * n; idx += blockDim.x) {
+      const int r = static_cast<int>(idx / n), i = static_cast<int>(idx % n);
+      const int k = k0 - r, m = n - k - 1;
+      vs[idx] = i < m ? hv[static_cast<long long>(k) * n + i] : df{0.f, 0.f};
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int r = 0; r < nk; ++r) {
+      const int k = k0 - r;
+      const df t = tau_g[k];
+      if (t.hi == 0.f) continue;
+      const int m = n - k - 1;
+      const df* v = vs + static_cast<long long>(r) * n;
+      df_acc s = acc_zero();
+      for (int i = lane; i < m; i += 32) s.fma(v[i], z[k + 1 + i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s.merge(shfl_xor_acc(s, o));
+      const df f = df_mul(t, s.value());
+      for (int i = lane; i < m; i += 32) z[k + 1 + i] = df_sub(z[k + 1 + i], df_mul(f, v[i]));
+      __syncwarp();
+    }
+  }
+  if (live)
+    for (int i = lane; i < n; i += 32) evecs[i * NW + c] = df_to_double(z[i]);
 }
 
 // ------------------------------------------------------------ Rayleigh-Ritz pencil
@@ -2207,6 +2521,9 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err, bool dry) {
     alloc((void**)&w->Zt, sizeof(df) * nm * nwm);
     alloc((void**)&w->rr, sizeof(df) * 4 * (nwm * nwm > 4 * nwm ? nwm * nwm : 4 * nwm));
     alloc((void**)&w->perm, sizeof(int) * nwm);
+    alloc((void**)&w->hv, sizeof(df) * nm * nm);
+    alloc((void**)&w->shd, sizeof(df) * nwm);
+    alloc((void**)&w->bounds, sizeof(float) * 4);
     alloc((void**)&w->Lm, sizeof(double) * dn * dn);
     alloc((void**)&w->Hs, sizeof(double) * dn * dn);
     alloc((void**)&w->sr_mu, sizeof(double) * qmax);
@@ -2225,29 +2542,34 @@ void pencil_work_destroy(PencilWork* w) {
 
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
                     cudaStream_t st, const int* skip) {
-  // place W, the factors and Zt in shared memory when they fit (in that order of benefit)
+  if (n <= 0 || nwant <= 0) return;
+  // tridiagonalisation: W in shared memory when it fits beside v, p, d, e, tau
   const int ldw = n | 1;  // odd row stride: column walks of W hit different banks
-  size_t sm = syev_smem_base(n, nwant);
-  int flags = 0;
+  const size_t tb = (5 * sizeof(df) * static_cast<size_t>(n) + 15) & ~static_cast<size_t>(15);
   const size_t wb = sizeof(df) * static_cast<size_t>(n) * ldw;
-  const size_t fb = sizeof(df) * 2 * static_cast<size_t>(n) * nwant;
-  const size_t zb = sizeof(df) * static_cast<size_t>(n) * nwant;
-  if (sm + wb <= kSmemBudget) {
-    flags |= kSyW;
-    sm += wb;
-  }
-  if (sm + fb <= kSmemBudget) {
-    flags |= kSyF;
-    sm += fb;
-  }
-  if (sm + zb <= kSmemBudget) {
-    flags |= kSyZ;
-    sm += zb;
-  }
-  ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0);
-  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_df), sm);
-  k_syev_df<<<1, kSyThreads, sm, st>>>(n, nwant, ldw, flags, H, evals, evecs, w->W, w->tau, w->dd, w->ee, w->fac,
-                                       w->Zt, w->rr, w->perm, skip);
+  const int inshared = tb + wb <= kSmemBudget;
+  const size_t sm_tri = tb + (inshared ? wb : 0);
+  const size_t sm_val = 2 * sizeof(df) * static_cast<size_t>(n) + 2 * sizeof(float) * static_cast<size_t>(n);
+  // groups keep their vectors in shared memory up to the budget (the widest possible group: all nwant)
+  const size_t sm_vec = std::min(kSmemBudget, syev_vecs_base(n, nwant) + syev_vecs_work(n, nwant));
+  // back-transformation: kSbWarps columns and kSbChunk staged reflectors of n df, fewer when n is large
+  int wpb = kSbWarps;
+  while (wpb > 1 && sizeof(df) * static_cast<size_t>(wpb + 1) * n > kSmemBudget) --wpb;
+  const int chunk = static_cast<int>(std::max<size_t>(
+      1, std::min<size_t>(kSbChunk, (kSmemBudget - sizeof(df) * static_cast<size_t>(wpb) * n) /
+                                        (sizeof(df) * static_cast<size_t>(n)))));
+  const size_t sm_back = sizeof(df) * static_cast<size_t>(wpb + chunk) * n;
+  ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0, 4);
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_tri), sm_tri);
+  k_syev_tri<<<1, kSyThreads, sm_tri, st>>>(n, ldw, inshared, H, w->W, w->hv, w->dd, w->ee, w->tau, skip);
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_vals), sm_val);
+  k_syev_vals<<<ceil_div(nwant, kSvWarps), 32 * kSvWarps, sm_val, st>>>(n, nwant, w->dd, w->ee, w->shd, w->bounds,
+                                                                        skip);
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_vecs), sm_vec);
+  k_syev_vecs<<<nwant, kSvecThreads, sm_vec, st>>>(n, nwant, sm_vec, w->dd, w->ee, w->shd, w->bounds, w->fac, w->rr,
+                                                   w->Zt, evals, skip);
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_back), sm_back);
+  k_syev_back<<<ceil_div(nwant, wpb), 32 * wpb, sm_back, st>>>(n, nwant, chunk, w->hv, w->tau, w->Zt, evecs, skip);
 }
 
 void launch_syev_df_into(int n, int nwant, const double* H, double* evals, double* evecs, df* W, df* tau, df* dd,

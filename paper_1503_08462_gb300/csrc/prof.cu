@@ -73,6 +73,7 @@ void add_launches(unsigned long long n) { prof().launches += n; }
 bool profiling_on() { return prof().on.load(std::memory_order_relaxed); }
 
 thread_local int g_depth = 0;  // nested scopes only count launches; the outermost one is timed
+thread_local int g_outer = -1;  // record of the open outermost scope (nested scopes add their kernels to it)
 thread_local int g_level = -1;  // level tag of the launches in flight (LevelTag)
 
 LevelTag::LevelTag(int level) : prev_(g_level) { g_level = level; }
@@ -82,7 +83,13 @@ ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int k
   Profiler& p = prof();
   p.launches += static_cast<unsigned long long>(kernels);
   g_thread_launches += static_cast<unsigned long long>(kernels);
-  if (g_depth++ > 0) return;
+  if (g_depth++ > 0) {
+    if (g_outer >= 0) {
+      std::lock_guard<std::mutex> lk(p.mu);
+      if (g_outer < static_cast<int>(p.recs.size())) p.recs[g_outer].kernels += kernels;
+    }
+    return;
+  }
   if (!p.on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(p.mu);
   Rec r{cls, g_level, bytes, flops, kernels, p.take(), p.take()};
@@ -90,11 +97,13 @@ ProfScope::ProfScope(cudaStream_t st, int cls, double bytes, double flops, int k
   cudaEventRecord(r.e0, st);
   slot_ = static_cast<int>(p.recs.size());
   p.recs.push_back(r);
+  g_outer = slot_;
 }
 
 ProfScope::~ProfScope() {
   --g_depth;
   if (slot_ < 0) return;
+  g_outer = -1;
   Profiler& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   if (slot_ < static_cast<int>(p.recs.size())) cudaEventRecord(p.recs[slot_].e1, st_);
