@@ -576,7 +576,7 @@ __device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, c
             const df apq = Hq[a0 * G + b0];
             const df app = Hq[a0 * G + a0], aqq = Hq[b0 * G + b0];
             // skip entries already below the float-float resolution of the diagonal
-            const float thr = 1.0e-17f * sqrtf(fabsf(app.hi) * fabsf(aqq.hi)) + 1.0e-37f;
+            const float thr = 1.0e-17f * (sqrtf(fabsf(app.hi)) * sqrtf(fabsf(aqq.hi))) + 1.0e-37f;
             if (fabsf(apq.hi) > thr) {
               // theta = (aqq - app) / (2 apq); t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
               // and t = 1 / (2 theta) once theta^2 would leave the float range
