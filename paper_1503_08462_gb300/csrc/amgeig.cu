@@ -950,7 +950,7 @@ int correction_tail_krylov(amgeig_hierarchy_t* h, SolveWork* w, int k, const amg
     const float* E = amg_x<float>(h, w, k, o, st);
     launch_pack_krylov_df(Nk, as_df(w->V), E, w->ld32, q, as_df(w->K), st);
     launch_dual_spmm_df(h->A[k], as_df(w->K), nb, as_df(w->W), st);
-    launch_gram_df(Nk, as_df(w->K), nb, as_df(w->W), 2 * nb, w->gsc, w->G, st);
+    launch_gram_df(Nk, as_df(w->K), nb, as_df(w->W), 2 * nb, w->gsc, w->G, st, h->dstatus);
     const float2* cur = as_df(w->W);
     for (int l = k; l < n - 1; ++l) {
       launch_spmm_df(h->R[l], cur, 2 * nb, as_df(w->WC[l + 1]), false, st, P_CHAIN);
@@ -999,7 +999,7 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
     // mixed path: float32 V-cycle; U, V, W and the chains in float-float
     amg_correction<float>(h, w, k, o, w->U, w->V, st);
     launch_dual_spmm_df(h->A[k], as_df(w->V), q, as_df(w->W), st);
-    launch_gram_df(Nk, as_df(w->V), q, as_df(w->W), 2 * q, w->gsc, w->G, st);
+    launch_gram_df(Nk, as_df(w->V), q, as_df(w->W), 2 * q, w->gsc, w->G, st, h->dstatus);
     const float2* cur = as_df(w->W);
     for (int l = k; l < n - 1; ++l) {
       launch_spmm_df(h->R[l], cur, 2 * q, as_df(w->WC[l + 1]), false, st, P_CHAIN);
@@ -1463,6 +1463,7 @@ int solve_impl(amgeig_hierarchy_t* h, int q, double tol, const amgeig_options& o
       int stt = 0;
       CK(cudaMemcpyAsync(&stt, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
+      if (stt == AMGEIG_ECUDA) return fail(stt, "a bulk copy into shared memory did not complete in time");
       if (stt) return fail(stt, "augmented pencil: Gram Schur complement not positive definite");
       if (flags) return fail(AMGEIG_ENAN, "NaN or Inf in the iterates");
       double mx = 0.0;

@@ -159,8 +159,10 @@ void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, con
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
                          cudaStream_t st);
 size_t gram_df_scratch_doubles(int rows, int q, int w);
+// status (may be null): set to AMGEIG_ECUDA when a bulk copy into shared memory did not complete
+// within the kernel's bounded wait
 void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, double* scratch, double* G,
-                    cudaStream_t st);
+                    cudaStream_t st, int* status = nullptr);
 void launch_f64_to_df(const double* x, long long count, float2* y, cudaStream_t st);
 void launch_df_to_f64(const float2* x, long long count, double* y, cudaStream_t st);
 void launch_cols_to_df(const double* src, int rows, int ld, int q, float2* dst, cudaStream_t st);

@@ -11,6 +11,7 @@
 // operation; the cancellation in lambda M u - A u raises the floor of the
 // relative residual to ~2^-48 lambda_max / lambda (float64: 2^-53 times the same).
 #include <algorithm>
+#include <cstdint>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -564,6 +565,163 @@ int gram_chunks_df(int rows, int* chunk_rows) {
   return ceil_div(rows, cr) > 0 ? ceil_div(rows, cr) : 1;
 }
 
+// ---- bulk-copy pipeline (sm_90+ TMA engine, used here on sm_103a)
+//
+// One elected thread starts cp.async.bulk copies of whole contiguous row slabs
+// into shared memory; each copy signals a shared-memory mbarrier with its byte
+// count (complete_tx), and the block waits on the barrier's phase parity.  The
+// waits are bounded: a copy that has not landed after kBulkSpins polls sets the
+// status word and the block stops (no kernel spins forever).
+constexpr int kBulkSpins = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < kBulkSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// k_gram_df_tiled with its slabs staged by bulk copies, two slabs in flight:
+// the copy of slab i + 2 starts as soon as the block has finished with slab i.
+// Slabs keep the global row layout (V rows of q, W rows of 2q float-float
+// values), so q must be even (16-byte rows pairs) and V, W 16-byte aligned;
+// the tile loads of a ragged last column tile read into the next row (or the
+// 4-value pad after the slab) and feed only accumulators that are discarded.
+// Same products in the same order as k_gram_df_tiled.
+__global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const float2* __restrict__ V, int q,
+                                                             const float2* __restrict__ W, int chunk_rows, int T,
+                                                             int rg, int slab, double* __restrict__ part,
+                                                             int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char graw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int ok_s;
+  const int stride = slab * 3 * q + 8;  // float2 per stage: V slab, W slab, pad
+  float2* stage0 = reinterpret_cast<float2*>(graw);
+  const int ntiles = T * (T + 1);
+  const int tid = threadIdx.x;
+  const int t = tid % ntiles, g = tid / ntiles;
+  const bool active = g < rg;
+  const int half = t >= T * (T + 1) / 2;
+  int r = t - half * (T * (T + 1) / 2), ta = 0;
+  while (r >= T - ta) {
+    r -= T - ta;
+    ++ta;
+  }
+  const int tb = ta + r;
+  df_acc acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = acc_zero();
+  const int r0 = blockIdx.x * chunk_rows;
+  const int r1 = min(rows, r0 + chunk_rows);
+  const int nslab = r1 > r0 ? (r1 - r0 + slab - 1) / slab : 0;
+  auto issue = [&](int i) {  // thread 0: slab i into stage i % 2
+    const int rb = r0 + i * slab, nr = min(slab, r1 - rb);
+    float2* Vs = stage0 + (i & 1) * stride;
+    float2* Ws = Vs + slab * q;
+    const unsigned bv = static_cast<unsigned>(sizeof(float2) * nr * q);
+    mbar_expect_tx(&bar[i & 1], 3 * bv);
+    bulk_g2s(Vs, V + static_cast<long long>(rb) * q, bv, &bar[i & 1]);
+    bulk_g2s(Ws, W + static_cast<long long>(rb) * 2 * q, 2 * bv, &bar[i & 1]);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    ok_s = 1;
+    for (int i = 0; i < 2 && i < nslab; ++i) issue(i);
+  }
+  __syncthreads();
+  int failed = -1;
+  for (int i = 0; i < nslab; ++i) {
+    const unsigned parity = static_cast<unsigned>((i >> 1) & 1);
+    if (tid == 0 && !mbar_wait_bounded(&bar[i & 1], parity)) ok_s = 0;
+    __syncthreads();
+    if (!ok_s) {
+      failed = i;
+      break;
+    }
+    mbar_try_wait(&bar[i & 1], parity);  // completed: each thread's own acquire of the copied bytes
+    const int nr = min(slab, r1 - (r0 + i * slab));
+    const float2* Vs = stage0 + (i & 1) * stride;
+    const float2* Ws = Vs + slab * q;
+    if (active)
+      for (int rr = g; rr < nr; rr += rg) {
+        const float4* vp = reinterpret_cast<const float4*>(Vs + rr * q + 4 * ta);
+        const float4* wp = reinterpret_cast<const float4*>(Ws + rr * 2 * q + half * q + 4 * tb);
+        const float4 v01 = vp[0], v23 = vp[1], w01 = wp[0], w23 = wp[1];
+        const df v[4] = {df{v01.x, v01.y}, df{v01.z, v01.w}, df{v23.x, v23.y}, df{v23.z, v23.w}};
+        const df w[4] = {df{w01.x, w01.y}, df{w01.z, w01.w}, df{w23.x, w23.y}, df{w23.z, w23.w}};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a * 4 + b].fma(v[a], w[b]);
+      }
+    __syncthreads();  // stage i % 2 is free again
+    if (tid == 0 && i + 2 < nslab) issue(i + 2);
+  }
+  if (failed >= 0) {
+    // a copy did not land in time: report it, give the copies still in flight (slabs failed and
+    // failed + 1) another bounded wait, and stop
+    if (tid == 0) {
+      if (status) atomicExch(status, AMGEIG_ECUDA);
+      for (int i = failed; i < failed + 2 && i < nslab; ++i)
+        mbar_wait_bounded(&bar[i & 1], static_cast<unsigned>((i >> 1) & 1));
+    }
+    return;
+  }
+  // merge the rg row groups (shared memory reused; fixed order)
+  df_acc* red = reinterpret_cast<df_acc*>(graw);  // rg x ntiles x 16
+  if (active)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) red[(g * ntiles + t) * 16 + i] = acc[i];
+  __syncthreads();
+  if (g == 0) {
+    const int np = q * (q + 1);
+    const int Tq = q * (q + 1) / 2;
+    for (int i = 0; i < 16; ++i) {
+      const int a = 4 * ta + i / 4, b = 4 * tb + i % 4;
+      if (a >= q || b >= q || a > b) continue;
+      df_acc s2 = red[t * 16 + i];
+      for (int h = 1; h < rg; ++h) s2.merge(red[(h * ntiles + t) * 16 + i]);
+      const int idx = half * Tq + a * q - a * (a - 1) / 2 + (b - a);
+      part[static_cast<long long>(blockIdx.x) * np + idx] = df_to_double(s2.value());
+    }
+  }
+}
+
 // general (non-symmetric-friendly) fallback for q > 35: 32 x 32 output tiles
 constexpr int kGT = 32;
 __global__ void __launch_bounds__(256) k_gram_df(int rows, const float2* __restrict__ V, int q,
@@ -793,7 +951,7 @@ size_t gram_df_scratch_doubles(int rows, int q, int w) {
 }
 
 void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, double* scratch, double* G,
-                    cudaStream_t st) {
+                    cudaStream_t st, int* status) {
   if (q <= 0 || w <= 0) return;
   int cr;
   const int chunks = gram_chunks_df(rows, &cr);
@@ -812,10 +970,20 @@ void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, do
     chunks2 = ceil_div(rows, cr2);
     const int np = q * (q + 1);
     ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks2 * np, 1.0 * rows * np * 2.0);
-    const size_t stage = sizeof(float2) * slab * 3 * 4 * T;
     const size_t merge = sizeof(df_acc) * rg * ntiles * 16;
-    const size_t sm = stage > merge ? stage : merge;
-    k_gram_df_tiled<<<chunks2, kGtThreads, sm, st>>>(rows, V, q, W, cr2, T, rg, slab, scratch);
+    // bulk-copy staging keeps the global row layout: even q and 16-byte aligned V, W
+    const bool bulk = q % 2 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+    if (bulk) {
+      const size_t stages = sizeof(float2) * 2 * (static_cast<size_t>(slab) * 3 * q + 8);
+      const size_t sm = stages > merge ? stages : merge;
+      ensure_dynamic_smem(reinterpret_cast<const void*>(k_gram_df_bulk), sm);
+      k_gram_df_bulk<<<chunks2, kGtThreads, sm, st>>>(rows, V, q, W, cr2, T, rg, slab, scratch, status);
+    } else {
+      const size_t stage = sizeof(float2) * slab * 3 * 4 * T;
+      const size_t sm = stage > merge ? stage : merge;
+      k_gram_df_tiled<<<chunks2, kGtThreads, sm, st>>>(rows, V, q, W, cr2, T, rg, slab, scratch);
+    }
     double* sums = scratch + static_cast<size_t>(chunks2) * np;
     launch_sum_partials(scratch, chunks2, np, sums, st);
     k_gram_unpack<<<ceil_div(np, 256), 256, 0, st>>>(sums, q, G);
