@@ -616,6 +616,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 
 // k_gram_df_tiled with its slabs staged by bulk copies, two slabs in flight:
 // the copy of slab i + 2 starts as soon as the block has finished with slab i.
+// Up to 32 columns one block holds every tile (rg row groups); wider blocks
+// (up to 128 columns) give each thread one tile, tpb tiles per block and the
+// tile list split over blockIdx.x; the blocks of one row chunk (blockIdx.y)
+// are neighbours in launch order and stage the same slabs, mostly from L2.
 // Slabs keep the global row layout (V rows of q, W rows of 2q float-float
 // values), so q must be even (16-byte rows pairs) and V, W 16-byte aligned;
 // the tile loads of a ragged last column tile read into the next row (or the
@@ -623,7 +627,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // Same products in the same order as k_gram_df_tiled.
 __global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const float2* __restrict__ V, int q,
                                                              const float2* __restrict__ W, int chunk_rows, int T,
-                                                             int rg, int slab, double* __restrict__ part,
+                                                             int tpb, int rg, int slab, double* __restrict__ part,
                                                              int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char graw[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -632,10 +636,12 @@ __global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const 
   float2* stage0 = reinterpret_cast<float2*>(graw);
   const int ntiles = T * (T + 1);
   const int tid = threadIdx.x;
-  const int t = tid % ntiles, g = tid / ntiles;
-  const bool active = g < rg;
+  // rows: chunk blockIdx.y; tiles blockIdx.x * tpb .. + tpb; rg row groups of tpb threads
+  const int lt = tid % tpb, g = tid / tpb;
+  const int t = blockIdx.x * tpb + lt;
+  const bool active = g < rg && t < ntiles;
   const int half = t >= T * (T + 1) / 2;
-  int r = t - half * (T * (T + 1) / 2), ta = 0;
+  int r = active ? t - half * (T * (T + 1) / 2) : 0, ta = 0;
   while (r >= T - ta) {
     r -= T - ta;
     ++ta;
@@ -644,7 +650,7 @@ __global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const 
   df_acc acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = acc_zero();
-  const int r0 = blockIdx.x * chunk_rows;
+  const int r0 = blockIdx.y * chunk_rows;
   const int r1 = min(rows, r0 + chunk_rows);
   const int nslab = r1 > r0 ? (r1 - r0 + slab - 1) / slab : 0;
   auto issue = [&](int i) {  // thread 0: slab i into stage i % 2
@@ -703,21 +709,21 @@ __global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const 
     return;
   }
   // merge the rg row groups (shared memory reused; fixed order)
-  df_acc* red = reinterpret_cast<df_acc*>(graw);  // rg x ntiles x 16
+  df_acc* red = reinterpret_cast<df_acc*>(graw);  // rg x tpb x 16
   if (active)
 #pragma unroll
-    for (int i = 0; i < 16; ++i) red[(g * ntiles + t) * 16 + i] = acc[i];
+    for (int i = 0; i < 16; ++i) red[(g * tpb + lt) * 16 + i] = acc[i];
   __syncthreads();
-  if (g == 0) {
+  if (g == 0 && active) {
     const int np = q * (q + 1);
     const int Tq = q * (q + 1) / 2;
     for (int i = 0; i < 16; ++i) {
       const int a = 4 * ta + i / 4, b = 4 * tb + i % 4;
       if (a >= q || b >= q || a > b) continue;
-      df_acc s2 = red[t * 16 + i];
-      for (int h = 1; h < rg; ++h) s2.merge(red[(h * ntiles + t) * 16 + i]);
+      df_acc s2 = red[lt * 16 + i];
+      for (int h = 1; h < rg; ++h) s2.merge(red[(h * tpb + lt) * 16 + i]);
       const int idx = half * Tq + a * q - a * (a - 1) / 2 + (b - a);
-      part[static_cast<long long>(blockIdx.x) * np + idx] = df_to_double(s2.value());
+      part[static_cast<long long>(blockIdx.y) * np + idx] = df_to_double(s2.value());
     }
   }
 }
@@ -955,12 +961,25 @@ void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, do
   if (q <= 0 || w <= 0) return;
   int cr;
   const int chunks = gram_chunks_df(rows, &cr);
-  if (w == 2 * q && q <= 32) {
+  // bulk-copy staging keeps the global row layout: even q and 16-byte aligned V, W
+  const bool bulk = q % 2 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+  if (w == 2 * q && (q <= 32 || (bulk && q <= 128))) {
     const int T = (q + 3) / 4, ntiles = T * (T + 1);
-    const int rg = kGtThreads / ntiles;
-    // up to 8 rows per group, staged slab within 40 KB of shared memory
-    const int rpg = std::max(1, std::min(8, 40960 / (rg * 96 * T)));
-    const int slab = rg * rpg;
+    int tpb, rg, ny, slab;
+    if (q <= 32) {
+      tpb = ntiles;
+      rg = kGtThreads / ntiles;
+      ny = 1;
+      // up to 8 rows per group, staged slab within 40 KB of shared memory
+      const int rpg = std::max(1, std::min(8, 40960 / (rg * 96 * T)));
+      slab = rg * rpg;
+    } else {
+      tpb = kGtThreads;
+      rg = 1;
+      ny = ceil_div(ntiles, tpb);
+      slab = std::max(8, std::min(32, 24576 / (24 * q)));  // about 24 KB of rows per stage
+    }
     int chunks2 = ceil_div(rows, slab);
     if (chunks2 > 3 * kNumSms) chunks2 = 3 * kNumSms;
     int cr2 = ceil_div(ceil_div(rows, chunks2), slab) * slab;
@@ -970,15 +989,13 @@ void launch_gram_df(int rows, const float2* V, int q, const float2* W, int w, do
     chunks2 = ceil_div(rows, cr2);
     const int np = q * (q + 1);
     ProfScope ps(st, P_GRAM, 8.0 * rows * (q + w) + 16.0 * chunks2 * np, 1.0 * rows * np * 2.0);
-    const size_t merge = sizeof(df_acc) * rg * ntiles * 16;
-    // bulk-copy staging keeps the global row layout: even q and 16-byte aligned V, W
-    const bool bulk = q % 2 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 &&
-                      (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+    const size_t merge = sizeof(df_acc) * rg * tpb * 16;
     if (bulk) {
       const size_t stages = sizeof(float2) * 2 * (static_cast<size_t>(slab) * 3 * q + 8);
       const size_t sm = stages > merge ? stages : merge;
       ensure_dynamic_smem(reinterpret_cast<const void*>(k_gram_df_bulk), sm);
-      k_gram_df_bulk<<<chunks2, kGtThreads, sm, st>>>(rows, V, q, W, cr2, T, rg, slab, scratch, status);
+      k_gram_df_bulk<<<dim3(ny, chunks2), kGtThreads, sm, st>>>(rows, V, q, W, cr2, T, tpb, rg, slab, scratch,
+                                                                status);
     } else {
       const size_t stage = sizeof(float2) * slab * 3 * 4 * T;
       const size_t sm = stage > merge ? stage : merge;
