@@ -466,6 +466,7 @@ struct SolveWork {
   std::vector<double*> WC, PX;                   // restriction chain [N][2q], prolongation chain [N][q]
   double *partials = nullptr, *sums = nullptr, *relres = nullptr, *lam = nullptr, *mu = nullptr;
   double *C = nullptr, *G = nullptr, *gsc = nullptr, *Xc = nullptr, *Yv = nullptr, *sign = nullptr;
+  double* Ydf = nullptr;   // Yv in float-float (two floats per value), streamed by the wide recombination
   int* flags = nullptr;
   int* perm = nullptr;     // output column c is column perm[c] of the iterate (after the refinement)
   bool permuted = false;   // perm applies to the current solve's outputs
@@ -563,6 +564,7 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
   CK(m.alloc(&w->gsc, gs));
   CK(m.alloc(&w->Xc, static_cast<size_t>(h->dn) * qt));
   CK(m.alloc(&w->Yv, static_cast<size_t>(bw) * qt));
+  CK(m.alloc(&w->Ydf, static_cast<size_t>(qt) * qt));
   CK(m.alloc(&w->sign, qt));
   CK(m.alloc(&w->flags, 4));
   CK(m.alloc(&w->perm, qt));
@@ -1025,7 +1027,7 @@ int correction_tail(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_opt
       launch_spmm_df(h->P[l], px, q, as_df(w->PX[l]), false, st, P_CHAIN);
       px = as_df(w->PX[l]);
     }
-    launch_recombine_df(Nk, px, as_df(w->V), w->Yv, q, as_df(w->U), st);
+    launch_recombine_df(Nk, px, as_df(w->V), w->Yv, q, as_df(w->U), st, as_df(w->Ydf), h->dstatus);
   }
   {
     ProfScope ps(st, P_OTHER, 16.0 * q, 0.0);

@@ -156,8 +156,10 @@ void launch_spmm_df(const DevCsr& S, const float2* X, int width, float2* Y, bool
 // (0: q; a Krylov block: up to 2q) and Y is nv x q.
 void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, const float2* pv, const float2* Xc,
                             const float2* V, const double* Y, int q, float2* U, cudaStream_t st, int nv = 0);
+// Ydf (q x q float-float, may be null): scratch for Y in float-float, which lets 32 < q <= 128 stream
+// Y through shared memory; status as for launch_gram_df
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
-                         cudaStream_t st);
+                         cudaStream_t st, float2* Ydf = nullptr, int* status = nullptr);
 size_t gram_df_scratch_doubles(int rows, int q, int w);
 // status (may be null): set to AMGEIG_ECUDA when a bulk copy into shared memory did not complete
 // within the kernel's bounded wait

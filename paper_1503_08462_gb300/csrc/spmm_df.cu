@@ -28,6 +28,56 @@ __device__ __forceinline__ df ld2(const float2* p, long long i) {
 }
 __device__ __forceinline__ void st2(float2* p, long long i, df v) { p[i] = make_float2(v.hi, v.lo); }
 
+// ---- bulk-copy pipeline (sm_90+ TMA engine, used here on sm_103a)
+//
+// One elected thread starts cp.async.bulk copies of whole contiguous row slabs
+// into shared memory; each copy signals a shared-memory mbarrier with its byte
+// count (complete_tx), and the block waits on the barrier's phase parity.  The
+// waits are bounded: a copy that has not landed after kBulkSpins polls sets the
+// status word and the block stops (no kernel spins forever).
+constexpr int kBulkSpins = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < kBulkSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+
 struct Geo {
   int G, rows_per_block, cpt;
   // G need not divide kThreads: blocks get exactly G * rows_per_block threads, so
@@ -311,6 +361,113 @@ __global__ void __launch_bounds__(kThreads) k_recombine_tiled(int n, const float
   }
 }
 
+// The same product with Y streamed: Y (already float-float, q x q) passes
+// through shared memory in chunks of kKbChunk rows by bulk copies, two chunks
+// in flight, and the block's 32 rows of V arrive by one bulk copy, so a block
+// holds 32 q + 32 q values instead of q^2 + 32 q and three blocks share an SM.
+// Needs even q and 16-byte aligned V, Ydf.  Same thread layout, same sums in
+// the same order (Xp, then d = 0 .. q-1) as k_recombine_tiled.
+constexpr int kKbChunk = 16;
+template <int CJ>
+__global__ void __launch_bounds__(kThreads, 3) k_recombine_kb(int n, const float2* __restrict__ Xp,
+                                                              const float2* __restrict__ V,
+                                                              const float2* __restrict__ Ydf, int q,
+                                                              float2* __restrict__ U, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char kraw[];
+  __shared__ __align__(8) unsigned long long bar[3];  // [0], [1]: chunks of Y; [2]: the rows of V
+  __shared__ int ok_s;
+  float2* vs = reinterpret_cast<float2*>(kraw);  // kRtRows x q
+  float2* ys = vs + kRtRows * q;                 // 2 x kKbChunk x q
+  const int tid = threadIdx.x;
+  const long long row0 = static_cast<long long>(blockIdx.x) * kRtRows;
+  const int nr = static_cast<int>(min(static_cast<long long>(kRtRows), n - row0));
+  const int nch = (q + kKbChunk - 1) / kKbChunk;
+  auto issue = [&](int c) {  // thread 0: chunk c of Y into buffer c % 2
+    const int d0 = c * kKbChunk, dk = min(kKbChunk, q - d0);
+    const unsigned bytes = static_cast<unsigned>(sizeof(float2) * dk * q);
+    mbar_expect_tx(&bar[c & 1], bytes);
+    bulk_g2s(ys + (c & 1) * kKbChunk * q, Ydf + static_cast<long long>(d0) * q, bytes, &bar[c & 1]);
+  };
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
+    mbar_init_fence();
+    ok_s = 1;
+    const unsigned vb = static_cast<unsigned>(sizeof(float2) * nr * q);
+    mbar_expect_tx(&bar[2], vb);
+    bulk_g2s(vs, V + row0 * q, vb, &bar[2]);
+    for (int c = 0; c < 2 && c < nch; ++c) issue(c);
+  }
+  __syncthreads();
+  const int cg = tid % kRtCols, rp = tid / kRtCols;
+  const int ra = rp, rb = rp + kRtRows / 2;
+  const long long rowa = row0 + ra, rowb = row0 + rb;
+  df_acc acc[2][CJ];
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) {
+    const int c = cg + j * kRtCols;
+    acc[0][j] = acc_zero();
+    acc[1][j] = acc_zero();
+    if (c < q) {
+      if (rowa < n) acc[0][j].add(ld2(Xp, rowa * q + c));
+      if (rowb < n) acc[1][j].add(ld2(Xp, rowb * q + c));
+    }
+  }
+  int failed = -1;  // first wait that expired: -2 the rows of V, c >= 0 chunk c
+  if (tid == 0 && !mbar_wait_bounded(&bar[2], 0u)) ok_s = 0;
+  __syncthreads();
+  if (!ok_s) {
+    failed = -2;
+  } else {
+    mbar_try_wait(&bar[2], 0u);
+    for (int c = 0; c < nch; ++c) {
+      const unsigned parity = static_cast<unsigned>((c >> 1) & 1);
+      if (tid == 0 && !mbar_wait_bounded(&bar[c & 1], parity)) ok_s = 0;
+      __syncthreads();
+      if (!ok_s) {
+        failed = c;
+        break;
+      }
+      mbar_try_wait(&bar[c & 1], parity);
+      const float2* yc = ys + (c & 1) * kKbChunk * q;
+      const int d0 = c * kKbChunk, dk = min(kKbChunk, q - d0);
+      for (int dd = 0; dd < dk; ++dd) {
+        const int d = d0 + dd;
+        const df x0 = ld2(vs, ra * q + d), x1 = ld2(vs, rb * q + d);
+        const float2* yr = yc + dd * q;
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+          const int c2 = cg + j * kRtCols;
+          if (c2 < q) {
+            const df y = ld2(yr, c2);
+            acc[0][j].fma(x0, y);
+            acc[1][j].fma(x1, y);
+          }
+        }
+      }
+      __syncthreads();  // buffer c % 2 is free again
+      if (tid == 0 && c + 2 < nch) issue(c + 2);
+    }
+  }
+  if (failed != -1) {
+    // a copy did not land in time: report it, give the copies still in flight another bounded wait, stop
+    if (tid == 0) {
+      if (status) atomicExch(status, AMGEIG_ECUDA);
+      if (failed == -2) mbar_wait_bounded(&bar[2], 0u);
+      const int c0 = failed == -2 ? 0 : failed;
+      for (int c = c0; c < c0 + 2 && c < nch; ++c)
+        mbar_wait_bounded(&bar[c & 1], static_cast<unsigned>((c >> 1) & 1));
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) {
+    const int c = cg + j * kRtCols;
+    if (c >= q) continue;
+    if (rowa < n) st2(U, rowa * q + c, acc[0][j].value());
+    if (rowb < n) st2(U, rowb * q + c, acc[1][j].value());
+  }
+}
+
 // Row-per-thread form for q <= Q <= 32: each thread keeps all Q accumulators of
 // its row in registers, so one V value feeds Q compensated products and the
 // rows of Y (zero-padded to Q columns, shared) are read as 16-byte broadcasts.
@@ -563,55 +720,6 @@ int gram_chunks_df(int rows, int* chunk_rows) {
   cr = ceil_div(cr, kGramRows) * kGramRows;
   *chunk_rows = cr;
   return ceil_div(rows, cr) > 0 ? ceil_div(rows, cr) : 1;
-}
-
-// ---- bulk-copy pipeline (sm_90+ TMA engine, used here on sm_103a)
-//
-// One elected thread starts cp.async.bulk copies of whole contiguous row slabs
-// into shared memory; each copy signals a shared-memory mbarrier with its byte
-// count (complete_tx), and the block waits on the barrier's phase parity.  The
-// waits are bounded: a copy that has not landed after kBulkSpins polls sets the
-// status word and the block stops (no kernel spins forever).
-constexpr int kBulkSpins = 1 << 22;
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n"
-      "  .reg .pred p;\n"
-      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "  selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (int i = 0; i < kBulkSpins; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
 }
 
 // k_gram_df_tiled with its slabs staged by bulk copies, two slabs in flight:
@@ -890,7 +998,7 @@ void launch_recombine_pc_df(int rows, int nnz, const int* rp, const int* ci, con
 }
 
 void launch_recombine_df(int rows, const float2* Xp, const float2* V, const double* Y, int q, float2* U,
-                         cudaStream_t st) {
+                         cudaStream_t st, float2* Ydf, int* status) {
   if (rows <= 0 || q <= 0) return;
   if (q <= 32) {
     ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q);
@@ -905,6 +1013,27 @@ void launch_recombine_df(int rows, const float2* Xp, const float2* V, const doub
       k_recombine_rows<28><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
     else
       k_recombine_rows<32><<<blocks, kThreads, 0, st>>>(rows, Xp, V, Y, q, U);
+    return;
+  }
+  if (q <= 128 && Ydf != nullptr && q % 2 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(Ydf) & 15) == 0) {
+    // Y to float-float once, then streamed through shared memory by the blocks
+    const int blocks = ceil_div(rows, kRtRows);
+    ProfScope ps(st, P_RECOMBINE, 24.0 * rows * q + 8.0 * q * q, 2.0 * rows * q * q, 2);
+    const long long qq = static_cast<long long>(q) * q;
+    k_f64_to_df<<<ceil_div(qq, kThreads), kThreads, 0, st>>>(Y, qq, Ydf);
+    const size_t sm = sizeof(float2) * (static_cast<size_t>(kRtRows) * q + 2 * static_cast<size_t>(kKbChunk) * q);
+#define AMGEIG_KB(CJ)                                                                     \
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_recombine_kb<CJ>), sm);             \
+  k_recombine_kb<CJ><<<blocks, kThreads, sm, st>>>(rows, Xp, V, Ydf, q, U, status)
+    if (q <= 3 * kRtCols) {
+      AMGEIG_KB(3);
+    } else if (q <= 5 * kRtCols) {
+      AMGEIG_KB(5);
+    } else {
+      AMGEIG_KB(8);
+    }
+#undef AMGEIG_KB
     return;
   }
   if (q <= 128) {
