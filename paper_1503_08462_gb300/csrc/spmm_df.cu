@@ -113,7 +113,10 @@ Geo geo_for(int width) {
 // per-block sums of r^2 and (Mu)^2 (fixed order).  The sums accumulate in
 // float-float: float64 arithmetic here, once per row and column, cost more
 // than the whole sparse product on this GPU.
-template <int CPT>
+// PW = 2 (even q, 16-byte aligned U): each lane's unit is a pair of adjacent
+// columns fetched by one 16-byte load; unit u covers columns PW u .. PW u + PW - 1.
+// Every column's sums run over the same nonzeros in the same order for PW = 1, 2.
+template <int CPT, int PW>
 __global__ void __launch_bounds__(kThreads, 4) k_defect_df(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                         const float2* __restrict__ a, const float2* __restrict__ m,
                                                         const float2* __restrict__ U, int q,
@@ -122,21 +125,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_defect_df(int n, const int* __r
   // grid-stride over row groups; each thread keeps its columns' sums of r^2 and
   // (Mu)^2 in registers, so a block writes one row of partials
   extern __shared__ df_acc sred[];
+  constexpr int K = CPT * PW;  // columns per thread
   const int rpb = blockDim.x / G;
   const int g = threadIdx.x / G;
   const int lane = threadIdx.x % G;
-  df_acc rr[CPT], m2[CPT];
-  df lamc[CPT];
+  df_acc rr[K], m2[K];
+  df lamc[K];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) {
-    rr[t] = m2[t] = acc_zero();
-    const int c = lane + t * G;
-    lamc[t] = c < q ? df_from_double(lam[c]) : df{0.f, 0.f};
-  }
+  for (int t = 0; t < CPT; ++t)
+#pragma unroll
+    for (int e = 0; e < PW; ++e) {
+      const int k = t * PW + e, c = (lane + t * G) * PW + e;
+      rr[k] = m2[k] = acc_zero();
+      lamc[k] = c < q ? df_from_double(lam[c]) : df{0.f, 0.f};
+    }
   for (int row = blockIdx.x * rpb + g; row < n; row += gridDim.x * rpb) {
-    df_acc aa[CPT], mm[CPT];
+    df_acc aa[K], mm[K];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
+    for (int k = 0; k < K; ++k) aa[k] = mm[k] = acc_zero();
     const int p0 = rp[row], p1 = rp[row + 1];
 #pragma unroll 4
     for (int p = p0; p < p1; ++p) {
@@ -145,35 +151,49 @@ __global__ void __launch_bounds__(kThreads, 4) k_defect_df(int n, const int* __r
       const long long base = static_cast<long long>(j) * q;
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
-        const int c = lane + t * G;
+        const int c = (lane + t * G) * PW;
         if (c < q) {
-          const df u = ld2(U, base + c);
-          aa[t].fma(av, u);
-          mm[t].fma(mv, u);
+          if (PW == 2) {
+            const float4 u2 = *reinterpret_cast<const float4*>(U + base + c);
+            const df u0 = df{u2.x, u2.y}, u1 = df{u2.z, u2.w};
+            aa[t * PW].fma(av, u0);
+            mm[t * PW].fma(mv, u0);
+            aa[t * PW + PW - 1].fma(av, u1);
+            mm[t * PW + PW - 1].fma(mv, u1);
+          } else {
+            const df u = ld2(U, base + c);
+            aa[t].fma(av, u);
+            mm[t].fma(mv, u);
+          }
         }
       }
     }
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) {
-      const int c = lane + t * G;
-      if (c < q) {
-        const df mu = mm[t].value();
-        const df r = df_sub(df_mul(lamc[t], mu), aa[t].value());
-        const float rf = df_float(r);
-        R[static_cast<long long>(row) * ldr + c] = rf;
-        rr[t].fma(df{rf, 0.f}, df{rf, 0.f});
-        m2[t].fma(mu, mu);
+    for (int t = 0; t < CPT; ++t)
+#pragma unroll
+      for (int e = 0; e < PW; ++e) {
+        const int k = t * PW + e, c = (lane + t * G) * PW + e;
+        if (c < q) {
+          const df mu = mm[k].value();
+          const df r = df_sub(df_mul(lamc[k], mu), aa[k].value());
+          const float rf = df_float(r);
+          R[static_cast<long long>(row) * ldr + c] = rf;
+          rr[k].fma(df{rf, 0.f}, df{rf, 0.f});
+          m2[k].fma(mu, mu);
+        }
       }
-    }
     for (int c = q + lane; c < ldr; c += G) R[static_cast<long long>(row) * ldr + c] = 0.f;
   }
   if (partials == nullptr) return;
-  const int W = G * CPT;
+  const int W = G * K;
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) {
-    sred[g * 2 * W + lane + t * G] = rr[t];
-    sred[g * 2 * W + W + lane + t * G] = m2[t];
-  }
+  for (int t = 0; t < CPT; ++t)
+#pragma unroll
+    for (int e = 0; e < PW; ++e) {
+      const int k = t * PW + e, c = (lane + t * G) * PW + e;
+      sred[g * 2 * W + c] = rr[k];
+      sred[g * 2 * W + W + c] = m2[k];
+    }
   __syncthreads();
   for (int idx = threadIdx.x; idx < 2 * q; idx += blockDim.x) {
     const int which = idx / q, c = idx % q;
@@ -184,19 +204,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_defect_df(int n, const int* __r
 }
 
 // ---------------------------------------------------------------- W = [A V | M V]
-template <int CPT>
+template <int CPT, int PW>
 __global__ void __launch_bounds__(kThreads) k_dual_spmm_df(int n, const int* __restrict__ rp,
                                                            const int* __restrict__ ci, const float2* __restrict__ a,
                                                            const float2* __restrict__ m,
                                                            const float2* __restrict__ V, int q,
                                                            float2* __restrict__ W, int G) {
+  constexpr int K = CPT * PW;
   const int rpb = blockDim.x / G;
   const int lane = threadIdx.x % G;
   const int row = blockIdx.x * rpb + threadIdx.x / G;
   if (row >= n) return;
-  df_acc aa[CPT], mm[CPT];
+  df_acc aa[K], mm[K];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) aa[t] = mm[t] = acc_zero();
+  for (int k = 0; k < K; ++k) aa[k] = mm[k] = acc_zero();
   const int p0 = rp[row], p1 = rp[row + 1];
   for (int p = p0; p < p1; ++p) {
     const int j = ci[p];
@@ -204,19 +225,34 @@ __global__ void __launch_bounds__(kThreads) k_dual_spmm_df(int n, const int* __r
     const long long base = static_cast<long long>(j) * q;
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
-      const int c = lane + t * G;
+      const int c = (lane + t * G) * PW;
       if (c < q) {
-        const df v = ld2(V, base + c);
-        aa[t].fma(av, v);
-        mm[t].fma(mv, v);
+        if (PW == 2) {
+          const float4 v2 = *reinterpret_cast<const float4*>(V + base + c);
+          const df v0 = df{v2.x, v2.y}, v1 = df{v2.z, v2.w};
+          aa[t * PW].fma(av, v0);
+          mm[t * PW].fma(mv, v0);
+          aa[t * PW + PW - 1].fma(av, v1);
+          mm[t * PW + PW - 1].fma(mv, v1);
+        } else {
+          const df v = ld2(V, base + c);
+          aa[t].fma(av, v);
+          mm[t].fma(mv, v);
+        }
       }
     }
   }
   const long long o = static_cast<long long>(row) * 2 * q;
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
-    const int c = lane + t * G;
-    if (c < q) {
+    const int c = (lane + t * G) * PW;
+    if (c >= q) continue;
+    if (PW == 2) {
+      const df a0 = aa[t * PW].value(), a1 = aa[t * PW + PW - 1].value();
+      const df m0 = mm[t * PW].value(), m1 = mm[t * PW + PW - 1].value();
+      *reinterpret_cast<float4*>(W + o + c) = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
+      *reinterpret_cast<float4*>(W + o + q + c) = make_float4(m0.hi, m0.lo, m1.hi, m1.lo);
+    } else {
       st2(W, o + c, aa[t].value());
       st2(W, o + q + c, mm[t].value());
     }
@@ -938,29 +974,82 @@ int grid_for(long long count) {
       break;                              \
   }
 
+// the same for kernels with a second template parameter PW = 1
+#define AMGEIG_DISPATCH1(cpt, KERNEL, ...) \
+  switch (cpt) {                          \
+    case 1:                               \
+      KERNEL<1, 1> __VA_ARGS__;              \
+      break;                              \
+    case 2:                               \
+      KERNEL<2, 1> __VA_ARGS__;              \
+      break;                              \
+    case 3:                               \
+      KERNEL<3, 1> __VA_ARGS__;              \
+      break;                              \
+    case 4:                               \
+      KERNEL<4, 1> __VA_ARGS__;              \
+      break;                              \
+    case 5:                               \
+      KERNEL<5, 1> __VA_ARGS__;              \
+      break;                              \
+    case 6:                               \
+      KERNEL<6, 1> __VA_ARGS__;              \
+      break;                              \
+    case 7:                               \
+      KERNEL<7, 1> __VA_ARGS__;              \
+      break;                              \
+    case 8:                               \
+      KERNEL<8, 1> __VA_ARGS__;              \
+      break;                              \
+    default:                              \
+      break;                              \
+  }
+
 }  // namespace
+
+// Even q up to 128 with 16-byte aligned blocks: pairs of columns per 16-byte load, two pairs
+// per lane, ceil(q / 4) lanes per row (pw = 2); otherwise the single-column layout of geo_for.
+Geo geo_paired(int q, const void* X, const void* Y, int* pw) {
+  const bool pair = q % 2 == 0 && q <= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  *pw = pair ? 2 : 1;
+  if (!pair) return geo_for(q);
+  const int G = (q + 3) / 4;
+  return Geo{G, kThreads / G, 2};
+}
 
 void launch_defect_df(const DevCsr& AM, const float2* U, int q, const double* lam, float* R, int ldr,
                       double* partials, int* nblocks_out, cudaStream_t st) {
-  Geo g = geo_for(q);
+  int pw;
+  Geo g = geo_paired(q, U, U, &pw);
   // one wave: four resident blocks per SM (the kernel's launch bound), grid-stride beyond
   int blocks = ceil_div(AM.rows, g.rows_per_block);
   if (blocks > 4 * kNumSms) blocks = 4 * kNumSms;
   if (nblocks_out) *nblocks_out = blocks;
-  const size_t sm = partials ? sizeof(df_acc) * g.rows_per_block * 2 * g.G * g.cpt : 0;
+  const size_t sm = partials ? sizeof(df_acc) * g.rows_per_block * 2 * g.G * g.cpt * pw : 0;
   const double N = AM.rows, nnz = AM.nnz;
   ProfScope ps(st, P_DEFECT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 4.0 * N * ldr, 4.0 * nnz * q);
-  AMGEIG_DISPATCH(g.cpt, k_defect_df,
+  if (pw == 2) {
+    k_defect_df<2, 2><<<blocks, g.threads(), sm, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, U, q, lam, R, ldr, g.G,
+                                                       partials);
+    return;
+  }
+  AMGEIG_DISPATCH1(g.cpt, k_defect_df,
                   <<<blocks, g.threads(), sm, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, U, q, lam, R, ldr, g.G,
-                                                 partials))
+                                                      partials))
 }
 
 void launch_dual_spmm_df(const DevCsr& AM, const float2* V, int q, float2* W, cudaStream_t st) {
-  Geo g = geo_for(q);
+  int pw;
+  Geo g = geo_paired(q, V, W, &pw);
   const int blocks = ceil_div(AM.rows, g.rows_per_block);
   const double N = AM.rows, nnz = AM.nnz;
   ProfScope ps(st, P_AUGMENT, 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * q + 16.0 * N * q, 4.0 * nnz * q);
-  AMGEIG_DISPATCH(g.cpt, k_dual_spmm_df,
+  if (pw == 2) {
+    k_dual_spmm_df<2, 2><<<blocks, g.threads(), 0, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, V, q, W, g.G);
+    return;
+  }
+  AMGEIG_DISPATCH1(g.cpt, k_dual_spmm_df,
                   <<<blocks, g.threads(), 0, st>>>(AM.rows, AM.rp, AM.ci, AM.d2, AM.m2, V, q, W, g.G))
 }
 
