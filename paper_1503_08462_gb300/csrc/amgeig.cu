@@ -140,12 +140,6 @@ __global__ void k_copy_d(const double* __restrict__ a, int n, double* __restrict
 
 // ------------------------------------------------------------------ blob parsing
 
-struct HostCsr {
-  int64_t rows = 0, cols = 0;
-  std::vector<int32_t> rp, ci;
-  std::vector<double> a, m;
-};
-
 // A CSR matrix read in place from the hierarchy blob (no copies): the arrays
 // are 8-byte aligned inside the blob, which is 8-byte aligned itself (or copied
 // once to an aligned buffer).  m is null for transfer operators.
@@ -265,66 +259,18 @@ int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std
   return AMGEIG_OK;
 }
 
-// The blob's content: the u64 word-sum checksum trailer and the CSR structure
-// (row offsets, column bounds) of every level and transfer operator.
-int validate_blob(const uint8_t* b, size_t bytes, const std::vector<CsrView>& levels,
-                  const std::vector<CsrView>& prolong) {
-  uint64_t sum = 0, stored;
-  {
-    // word sum (mod 2^64) of everything before the stored checksum, in slices
-    const size_t words = (bytes - 8) / 8;
-    const int T = host_threads(static_cast<int64_t>(words / 64));
-    std::vector<uint64_t> part(T, 0);
-    parallel_for(T, [&](int t) {
-      const size_t lo = words * t / T, hi = words * (t + 1) / T;
-      uint64_t acc = 0;
-      for (size_t i = lo; i < hi; ++i) {
-        uint64_t w;
-        std::memcpy(&w, b + 8 * i, 8);
-        acc += w;
-      }
-      part[t] = acc;
-    });
-    for (uint64_t x : part) sum += x;
-  }
-  std::memcpy(&stored, b + bytes - 8, 8);
-  if (sum != stored) return fail(AMGEIG_ECORRUPT, "hierarchy blob checksum mismatch");
-  for (const CsrView& L : levels)
-    if (!csr_valid(L)) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
-  for (const CsrView& P : prolong)
-    if (!csr_valid(P)) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
-  return AMGEIG_OK;
-}
-
-HostCsr transpose(const CsrView& P) {
-  HostCsr R;
-  R.rows = P.cols;
-  R.cols = P.rows;
-  R.rp.assign(P.cols + 1, 0);
-  for (int64_t q = 0; q < P.nnz; ++q) R.rp[P.ci[q] + 1]++;
-  for (int64_t j = 0; j < P.cols; ++j) R.rp[j + 1] += R.rp[j];
-  R.ci.resize(static_cast<size_t>(P.nnz));
-  R.a.resize(static_cast<size_t>(P.nnz));
-  std::vector<int32_t> pos(R.rp.begin(), R.rp.end() - 1);
-  for (int64_t i = 0; i < P.rows; ++i)
-    for (int32_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
-      const int32_t k = pos[P.ci[p]]++;
-      R.ci[k] = static_cast<int32_t>(i);
-      R.a[k] = P.a[p];
-    }
-  return R;
-}
-
 // ------------------------------------------------------------------ device data
 
 // Device memory of one owner (a hierarchy, a solve workspace), released with it.
-// Arrays of 2 MiB and more get a cudaMalloc of their own; smaller ones are carved,
-// 256-byte aligned, from blocks (2 MiB, then 8 MiB).  A hierarchy holds ~200 arrays,
-// most of them small, and each cudaMalloc / cudaFree costs tens of microseconds (a
-// cudaFree synchronises the device), so loading and releasing one takes a few dozen
-// calls instead of hundreds.
+// Arrays of 64 MiB and more get a cudaMalloc of their own; smaller ones are carved,
+// 256-byte aligned, from blocks whose size doubles from 2 MiB up to 64 MiB (a block
+// is at least as large as the array that opens it).  A hierarchy holds ~200 arrays
+// and each cudaMalloc / cudaFree costs tens of microseconds (a cudaFree synchronises
+// the device), so loading and releasing one takes about ten calls, while a small
+// owner still holds only a few MiB.
 struct DeviceBuffers {
-  static constexpr size_t kOwn = size_t(2) << 20, kAlign = 256;
+  static constexpr size_t kOwn = size_t(64) << 20, kFirst = size_t(2) << 20, kAlign = 256;
+  size_t next_block = kFirst;  // size of the next block of carved arrays
   std::vector<void*> ptrs;  // every cudaMalloc of this owner
   size_t held = 0;          // bytes of those allocations
   size_t mallocs = 0;       // allocation calls made (or, when dry, that would be made)
@@ -352,7 +298,8 @@ struct DeviceBuffers {
       return cudaSuccess;
     }
     if (bytes > blk_left) {
-      const size_t block = mallocs == 0 ? kOwn : size_t(8) << 20;  // > bytes
+      const size_t block = std::max(next_block, bytes);  // < kOwn
+      next_block = std::min(kOwn, 2 * block);
       if (!dry) {
         cudaError_t e = cudaMalloc(&p, block);
         if (e != cudaSuccess) return e;
@@ -1872,24 +1819,45 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
     ~Event() {
       if (e) cudaEventDestroy(e);
     }
-  } uploaded;
+  } uploaded, copied;
   CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&side2.s, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&uploaded.e, cudaEventDisableTiming));
+  // The rest of the blob goes to the device in one copy, first, and its arrays are
+  // used in place; its checksum and every CSR structure are checked there, and the
+  // results read back (after the coarsest level's work is queued) before any kernel
+  // follows one of its column indices.
+  uint8_t* dblob = nullptr;
+  unsigned long long* dsum = nullptr;
+  int* dbad = nullptr;
+  CK(m.alloc(&dblob, bytes));
+  CK(m.alloc(&dsum, 1));
+  CK(m.alloc(&dbad, 2));
+  CK(cudaMemcpyAsync(dblob, base, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaEventCreateWithFlags(&copied.e, cudaEventDisableTiming));
+  CK(cudaEventRecord(copied.e, h->stream));
+  auto dev = [&](const void* hp) { return dblob + (static_cast<const uint8_t*>(hp) - base); };
+  CK(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(dbad, 0, 2 * sizeof(int), h->stream));
+  launch_blob_checksum(dblob, bytes - 8, dsum, h->stream);
+  for (const CsrView& L : levels)
+    launch_csr_check(reinterpret_cast<const int*>(dev(L.rp)), reinterpret_cast<const int*>(dev(L.ci)), L.rows,
+                     L.cols, L.nnz, dbad, h->stream);
+  for (const CsrView& P : prolong)
+    launch_csr_check(reinterpret_cast<const int*>(dev(P.rp)), reinterpret_cast<const int*>(dev(P.ci)), P.rows,
+                     P.cols, P.nnz, dbad + 1, h->stream);
   const int dn = h->dn;
-  std::vector<double> An(static_cast<size_t>(dn) * dn, 0.0), Mn(static_cast<size_t>(dn) * dn, 0.0);
+  // the coarsest level's dense A_n and M_n, formed on the device from its arrays in the
+  // blob (checked on the host above) as soon as the copy has landed
+  CK(m.alloc(&h->An, static_cast<size_t>(dn) * dn));
+  CK(m.alloc(&h->Mn, static_cast<size_t>(dn) * dn));
+  CK(cudaStreamWaitEvent(side.s, copied.e, 0));
   {
     const CsrView& Lc = levels[n - 1];
-    for (int i = 0; i < dn; ++i)
-      for (int32_t p = Lc.rp[i]; p < Lc.rp[i + 1]; ++p) {
-        An[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.a[p];
-        Mn[static_cast<size_t>(i) * dn + Lc.ci[p]] = Lc.m[p];
-      }
+    launch_csr_to_dense(dn, reinterpret_cast<const int*>(dev(Lc.rp)), reinterpret_cast<const int*>(dev(Lc.ci)),
+                        reinterpret_cast<const double*>(dev(Lc.a)), reinterpret_cast<const double*>(dev(Lc.m)),
+                        h->An, h->Mn, side.s);
   }
-  CK(m.alloc(&h->An, An.size()));
-  CK(m.alloc(&h->Mn, Mn.size()));
-  CK(cudaMemcpyAsync(h->An, An.data(), sizeof(double) * An.size(), cudaMemcpyHostToDevice, side.s));
-  CK(cudaMemcpyAsync(h->Mn, Mn.data(), sizeof(double) * Mn.size(), cudaMemcpyHostToDevice, side.s));
   CK(m.alloc(&h->Z, static_cast<size_t>(dn) * dn));
   CK(m.alloc(&h->theta, dn));
   CK(m.alloc(&h->Ainv, static_cast<size_t>(dn) * dn));
@@ -1925,15 +1893,24 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   launch_coarse_inverse(dn, h->An, Lf.p, Li.p, h->Ainv, h->dstatus + 1, side2.s);
   launch_convert_f64_to_f32(h->Ainv, static_cast<long long>(dn) * dn, h->Ainv32, side2.s);
   CK(cudaGetLastError());
-  // the rest of the blob (checksum, every CSR) on host threads meanwhile
-  rc = validate_blob(base, bytes, levels, prolong);
-  if (rc) return rc;
+  // the checks' results (enqueued at the start) are read before any kernel follows a column index
+  {
+    unsigned long long sum = 0;
+    int bad[2] = {0, 0};
+    CK(cudaMemcpyAsync(&sum, dsum, sizeof(sum), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    uint64_t stored;
+    std::memcpy(&stored, base + bytes - 8, 8);
+    if (sum != stored) return fail(AMGEIG_ECORRUPT, "hierarchy blob checksum mismatch");
+    if (bad[0]) return fail(AMGEIG_ECORRUPT, "invalid level CSR");
+    if (bad[1]) return fail(AMGEIG_ECORRUPT, "invalid prolongation CSR");
+  }
   h->A.resize(n);
   h->dinv64.assign(n, nullptr);
   h->dinv32.assign(n, nullptr);
-  // the blob's arrays go to the device as they are (stream-ordered copies); the
-  // float32 and float-float copies of the values and the l1-Jacobi inverse
-  // diagonals are made there
+  // the float32 and float-float copies of the values and the l1-Jacobi inverse
+  // diagonals are made on the device
   int* zero_row = nullptr;
   CK(m.alloc(&zero_row, 1));
   CK(cudaMemsetAsync(zero_row, 0, sizeof(int), h->stream));
@@ -1942,10 +1919,10 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
     DevCsr& D = h->A[l];
     D.rows = D.cols = static_cast<int>(L.rows);
     D.nnz = static_cast<int>(L.nnz);
-    CK(m.upload(&D.rp, L.rp, static_cast<size_t>(L.rows) + 1));
-    CK(m.upload(&D.ci, L.ci, static_cast<size_t>(L.nnz)));
-    CK(m.upload(&D.v64, L.a, static_cast<size_t>(L.nnz)));
-    CK(m.upload(&D.m64, L.m, static_cast<size_t>(L.nnz)));
+    D.rp = reinterpret_cast<int*>(dev(L.rp));
+    D.ci = reinterpret_cast<int*>(dev(L.ci));
+    D.v64 = reinterpret_cast<double*>(dev(L.a));
+    D.m64 = reinterpret_cast<double*>(dev(L.m));
     CK(m.alloc(&D.v32, static_cast<size_t>(L.nnz)));
     CK(m.alloc(&D.d2, static_cast<size_t>(L.nnz)));
     CK(m.alloc(&D.m2, static_cast<size_t>(L.nnz)));
@@ -1958,25 +1935,28 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   }
   h->P.resize(n - 1);
   h->R.resize(n - 1);
-  // R_l = P_l^T on host threads (one transpose per level), both uploaded
-  std::vector<HostCsr> Rt(n > 1 ? n - 1 : 0);
-  parallel_for(n > 1 ? n - 1 : 0, [&](int l) { Rt[l] = transpose(prolong[l]); });
+  // P_l in place; R_l = P_l^T formed on the device (rows in ascending column order)
+  int* tscratch = nullptr;
+  if (n > 1) CK(m.alloc(&tscratch, static_cast<size_t>(h->sizes[1])));
   for (int l = 0; l + 1 < n; ++l) {
-    for (int which = 0; which < 2; ++which) {
-      const CsrView& P = prolong[l];
-      const HostCsr& R = Rt[l];
-      DevCsr& D = which == 0 ? h->P[l] : h->R[l];
-      const int64_t rows = which == 0 ? P.rows : R.rows;
-      D.rows = static_cast<int>(rows);
-      D.cols = static_cast<int>(which == 0 ? P.cols : R.cols);
-      D.nnz = static_cast<int>(P.nnz);
-      CK(m.upload(&D.rp, which == 0 ? P.rp : R.rp.data(), static_cast<size_t>(rows) + 1));
-      CK(m.upload(&D.ci, which == 0 ? P.ci : R.ci.data(), static_cast<size_t>(P.nnz)));
-      CK(m.upload(&D.v64, which == 0 ? P.a : R.a.data(), static_cast<size_t>(P.nnz)));
-      CK(m.alloc(&D.v32, static_cast<size_t>(P.nnz)));
-      CK(m.alloc(&D.d2, static_cast<size_t>(P.nnz)));
-      launch_convert_f64_to_f32(D.v64, P.nnz, D.v32, h->stream);
-      launch_f64_to_df(D.v64, P.nnz, D.d2, h->stream);
+    const CsrView& P = prolong[l];
+    DevCsr& Dp = h->P[l];
+    DevCsr& Dr = h->R[l];
+    Dp.rows = Dr.cols = static_cast<int>(P.rows);
+    Dp.cols = Dr.rows = static_cast<int>(P.cols);
+    Dp.nnz = Dr.nnz = static_cast<int>(P.nnz);
+    Dp.rp = reinterpret_cast<int*>(dev(P.rp));
+    Dp.ci = reinterpret_cast<int*>(dev(P.ci));
+    Dp.v64 = reinterpret_cast<double*>(dev(P.a));
+    CK(m.alloc(&Dr.rp, static_cast<size_t>(P.cols) + 1));
+    CK(m.alloc(&Dr.ci, static_cast<size_t>(P.nnz)));
+    CK(m.alloc(&Dr.v64, static_cast<size_t>(P.nnz)));
+    launch_transpose_csr(P.rows, P.cols, P.nnz, Dp.rp, Dp.ci, Dp.v64, Dr.rp, Dr.ci, Dr.v64, tscratch, h->stream);
+    for (DevCsr* D : {&Dp, &Dr}) {
+      CK(m.alloc(&D->v32, static_cast<size_t>(P.nnz)));
+      CK(m.alloc(&D->d2, static_cast<size_t>(P.nnz)));
+      launch_convert_f64_to_f32(D->v64, P.nnz, D->v32, h->stream);
+      launch_f64_to_df(D->v64, P.nnz, D->d2, h->stream);
     }
   }
   // composite prolongations I_n^k (coarsest -> level k) for the recombination:

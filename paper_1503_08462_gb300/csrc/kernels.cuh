@@ -276,4 +276,14 @@ struct df;
 void launch_syev_df_into(int n, int nwant, const double* H, double* evals, double* evecs, df* W, df* tau, df* dd,
                          df* ee, df* fac, df* Zt, df* rr, int* perm, cudaStream_t st);
 
+// Hierarchy load on the device (the blob copied in one piece): *out += the word sum (mod 2^64) of
+// `bytes` (a multiple of 8) at blob; *bad |= 1 unless (rp, ci) is a valid CSR structure of a
+// rows x cols matrix with nnz entries; R = P^T (rows x cols P in, cols x rows R out, rows of R in
+// ascending column order), scratch: cols ints.
+void launch_blob_checksum(const void* blob, size_t bytes, unsigned long long* out, cudaStream_t st);
+void launch_csr_check(const int* rp, const int* ci, long long rows, long long cols, long long nnz, int* bad,
+                      cudaStream_t st);
+void launch_transpose_csr(long long rows, long long cols, long long nnz, const int* rp, const int* ci,
+                          const double* v, int* rrp, int* rci, double* rv, int* scratch, cudaStream_t st);
+
 }  // namespace amgeig

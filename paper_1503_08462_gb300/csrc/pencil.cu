@@ -31,7 +31,11 @@
 //   or one block per eigenvalue, group or eigenvector.  References: Golub & Van Loan, Matrix
 //   Computations, 4th ed., 8.3 (tridiagonalisation), 8.4.1 (Sturm bisection),
 //   8.2.2 (inverse iteration), 8.5 (Jacobi).
+#include <cooperative_groups.h>
+
 #include <cstdio>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -881,6 +885,183 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_tri(int n, int ldw, int ins
     tau_g[i] = tau[i];
     if (i + 1 < n) ee_g[i] = ee[i];
   }
+}
+
+// The same tridiagonalisation by a thread-block cluster of CS CTAs (2, 4 or 8)
+// when W is too large for one block's shared memory: CTA r keeps rows
+// r R .. r R + R - 1 of W (full rows, stride ldw) in its own shared memory.
+// Per step k the owners of column k's entries below the diagonal write them,
+// with their partial sums of squares, into every CTA's copy of v (distributed
+// shared memory); after a cluster barrier every CTA forms the same reflector
+// from the same partials (merged in rank order), computes p = t W22 v for its
+// own rows and sends them, with its partial v^T p, to every CTA; after a
+// second barrier each CTA forms w = p - (t/2)(v^T p) v and updates its own rows
+// (both triangles in the (max, min) product order, so W stays bitwise
+// symmetric).  v, p and the partials are double-buffered by the parity of k:
+// a CTA that reaches step k + 1 writes buffers that no CTA still reads.
+constexpr int kTriMaxCluster = 8;
+
+__device__ __forceinline__ df_acc block_merge(df_acc a, df_acc* red) {
+  // every thread's partial merged: warps by shuffles, then warp 0 over the warps (result in lane 0 of warp 0)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a.merge(shfl_xor_acc(a, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) red[warp] = a;
+  __syncthreads();
+  df_acc b = acc_zero();
+  if (warp == 0) {
+    b = lane < nw ? red[lane] : acc_zero();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b.merge(shfl_xor_acc(b, o));
+  }
+  __syncthreads();
+  return b;
+}
+
+__global__ void __launch_bounds__(kSyThreads) k_syev_tri_cl(int n, int ldw, int R, const double* __restrict__ H,
+                                                            df* __restrict__ hv, df* __restrict__ dd_g,
+                                                            df* __restrict__ ee_g, df* __restrict__ tau_g,
+                                                            const int* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;  // every CTA of the cluster returns here alike
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = static_cast<int>(cl.num_blocks()), rank = static_cast<int>(cl.block_rank());
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df* W = reinterpret_cast<df*>(smem_raw);  // R x ldw: rows r0 .. r1-1
+  df* vb = W + static_cast<long long>(R) * ldw;  // 2 x n
+  df* pb = vb + 2 * n;                            // 2 x n
+  __shared__ df_acc sigp[2][kTriMaxCluster], vpp[2][kTriMaxCluster], red[32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int r0 = rank * R, r1 = min(n, r0 + R);
+  const long long LD = ldw;
+  for (long long idx = tid; idx < static_cast<long long>(r1 - r0) * n; idx += nt) {
+    const int i = static_cast<int>(idx / n), j = static_cast<int>(idx % n);
+    W[i * LD + j] = df_from_double(H[static_cast<long long>(r0 + i) * n + j]);
+  }
+  __syncthreads();
+  // column c's entries below the diagonal (own rows) into every CTA's v buffer, and
+  // the partial sum of squares of rows c + 2 .. into every CTA's partials
+  auto send_column = [&](int c) {
+    const int buf = c & 1;
+    df_acc a = acc_zero();
+    for (int i = max(r0, c + 1) + tid; i < r1; i += nt) {
+      const df x = W[(i - r0) * LD + c];
+      for (int r = 0; r < CS; ++r) cl.map_shared_rank(vb + buf * n, r)[i - c - 1] = x;
+      if (i >= c + 2) a.fma(x, x);
+    }
+    const df_acc s = block_merge(a, red);
+    if (tid == 0)
+      for (int r = 0; r < CS; ++r) cl.map_shared_rank(&sigp[buf][0], r)[rank] = s;
+  };
+  send_column(0);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int buf = k & 1, m = n - k - 1;
+    cl.sync();  // (1) column k and its partials are everywhere
+    df_acc sa = sigp[buf][0];
+    for (int r = 1; r < CS; ++r) sa.merge(sigp[buf][r]);
+    const df sigma = sa.value();
+    df* v = vb + buf * n;
+    df* p = pb + buf * n;
+    const df x0 = v[0];
+    const bool own_k = k >= r0 && k < r1;
+    if (sigma.hi == 0.f) {
+      if (own_k) {
+        if (tid == 0) {
+          tau_g[k] = df{0.f, 0.f};
+          dd_g[k] = W[(k - r0) * LD + k];
+          ee_g[k] = x0;
+        }
+      }
+      cl.sync();  // (2) the same barrier count as a reflecting step
+      send_column(k + 1);
+      continue;
+    }
+    const df nrm = df_sqrt(df_add(df_mul(x0, x0), sigma));
+    const df alpha = df_lt0(x0) ? nrm : df_neg(nrm);
+    const df v0 = df_sub(x0, alpha);
+    const df vtv = df_add(sigma, df_mul(v0, v0));
+    const df t = df_div(df{2.f, 0.f}, vtv);
+    __syncthreads();  // every thread has read v[0]
+    if (tid == 0) {
+      v[0] = v0;
+      if (own_k) {
+        tau_g[k] = t;
+        dd_g[k] = W[(k - r0) * LD + k];
+        ee_g[k] = alpha;
+      }
+    }
+    __syncthreads();
+    if (rank == 0)
+      for (int i = tid; i < m; i += nt) hv[static_cast<long long>(k) * n + i] = v[i];
+    // p_i = t (W22 v)_i for the own trailing rows, one warp per row; partial v^T p
+    {
+      df_acc pv = acc_zero();
+      for (int i = max(r0, k + 1) + warp; i < r1; i += nw) {
+        const df* row = W + (i - r0) * LD + (k + 1);
+        df_acc b0 = acc_zero(), b1 = acc_zero();
+        int j = lane;
+        for (; j + 32 < m; j += 64) {
+          b0.fma(row[j], v[j]);
+          b1.fma(row[j + 32], v[j + 32]);
+        }
+        if (j < m) b0.fma(row[j], v[j]);
+        b0.merge(b1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b0.merge(shfl_xor_acc(b0, o));
+        if (lane == 0) {
+          const df pi = df_mul(t, b0.value());
+          for (int r = 0; r < CS; ++r) cl.map_shared_rank(pb + buf * n, r)[i - k - 1] = pi;
+          pv.fma(v[i - k - 1], pi);
+        }
+      }
+      const df_acc s = block_merge(pv, red);
+      if (tid == 0)
+        for (int r = 0; r < CS; ++r) cl.map_shared_rank(&vpp[buf][0], r)[rank] = s;
+    }
+    cl.sync();  // (2) every p_i and partial v^T p are everywhere
+    {
+      df_acc c = vpp[buf][0];
+      for (int r = 1; r < CS; ++r) c.merge(vpp[buf][r]);
+      const df kc = df_mul(df_mul_f(t, 0.5f), c.value());
+      for (int i = tid; i < m; i += nt) p[i] = df_sub(p[i], df_mul(kc, v[i]));  // w
+    }
+    __syncthreads();
+    // own rows: W22 -= v w^T + w v^T (column k keeps the entries of the reduced matrix)
+    const int i0 = max(r0, k + 1);
+    const long long cnt = static_cast<long long>(max(0, r1 - i0)) * m;
+    for (long long idx = tid; idx < cnt; idx += nt) {
+      const int ii = static_cast<int>(idx / m), j = static_cast<int>(idx % m);
+      const int i = i0 + ii - k - 1;  // trailing index of the row
+      const df vi = v[i], wi = p[i];
+      df_acc u0 = acc_zero();
+      if (j <= i) {
+        u0.fma(vi, p[j]);
+        u0.fma(wi, v[j]);
+      } else {
+        u0.fma(v[j], wi);
+        u0.fma(p[j], vi);
+      }
+      df* e = W + (i0 + ii - r0) * LD + (k + 1 + j);
+      *e = df_sub(*e, u0.value());
+    }
+    __syncthreads();
+    send_column(k + 1);
+  }
+  // the last 2 x 2 block
+  if (tid == 0) {
+    if (n >= 2) {
+      if (n - 2 >= r0 && n - 2 < r1) dd_g[n - 2] = W[(n - 2 - r0) * LD + (n - 2)];
+      if (n - 1 >= r0 && n - 1 < r1) {
+        dd_g[n - 1] = W[(n - 1 - r0) * LD + (n - 1)];
+        ee_g[n - 2] = W[(n - 1 - r0) * LD + (n - 2)];
+      }
+      if (rank == 0) tau_g[n - 2] = df{0.f, 0.f};
+    } else if (rank == 0) {
+      dd_g[0] = W[0];
+    }
+    if (rank == 0 && n >= 1) tau_g[n - 1] = df{0.f, 0.f};
+  }
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
 // The refined shifts, one warp each (kSvWarps per block): float32 multisection
@@ -2540,6 +2721,36 @@ void pencil_work_destroy(PencilWork* w) {
   delete w;
 }
 
+// Whether a cluster of c blocks of k_syev_tri_cl with `bytes` of shared memory each can be
+// resident on this device (asked once per device and size class; the answer is kept).
+bool cluster_fits(int c, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, bool> known;  // (device, c * 1024 + KiB)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int key = c * 1024 + static_cast<int>((bytes + 1023) / 1024);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find({dev, key});
+  if (it != known.end()) return it->second;
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_tri_cl), bytes);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c);
+  cfg.blockDim = dim3(kSyThreads);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&clusters, k_syev_tri_cl, &cfg) == cudaSuccess && clusters > 0;
+  if (!ok) cudaGetLastError();
+  known[{dev, key}] = ok;
+  return ok;
+}
+
 void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* evals, double* evecs,
                     cudaStream_t st, const int* skip) {
   if (n <= 0 || nwant <= 0) return;
@@ -2560,8 +2771,33 @@ void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* ev
                                         (sizeof(df) * static_cast<size_t>(n)))));
   const size_t sm_back = sizeof(df) * static_cast<size_t>(wpb + chunk) * n;
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0, 4);
-  ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_tri), sm_tri);
-  k_syev_tri<<<1, kSyThreads, sm_tri, st>>>(n, ldw, inshared, H, w->W, w->hv, w->dd, w->ee, w->tau, skip);
+  // W too large for one block: a cluster of 2, 4 or 8 blocks holding its rows, when one can be scheduled
+  int cs = 0, rows_per = 0;
+  size_t sm_cl = 0;
+  if (!inshared)
+    for (int c = 2; c <= kTriMaxCluster && cs == 0; c *= 2) {
+      rows_per = (n + c - 1) / c;
+      sm_cl = sizeof(df) * (static_cast<size_t>(rows_per) * ldw + 4 * static_cast<size_t>(n));
+      if (sm_cl <= kSmemBudget && cluster_fits(c, sm_cl)) cs = c;
+    }
+  if (cs > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kSyThreads);
+    cfg.dynamicSmemBytes = sm_cl;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_syev_tri_cl, n, ldw, rows_per, H, w->hv, w->dd, w->ee, w->tau, skip);
+  } else {
+    ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_tri), sm_tri);
+    k_syev_tri<<<1, kSyThreads, sm_tri, st>>>(n, ldw, inshared, H, w->W, w->hv, w->dd, w->ee, w->tau, skip);
+  }
   ensure_dynamic_smem(reinterpret_cast<const void*>(k_syev_vals), sm_val);
   k_syev_vals<<<ceil_div(nwant, kSvWarps), 32 * kSvWarps, sm_val, st>>>(n, nwant, w->dd, w->ee, w->shd, w->bounds,
                                                                         skip);

@@ -462,6 +462,136 @@ double now_s() {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ blob checks and transposes at load
+//
+// The loader copies a hierarchy blob to the device in one piece and uses its
+// arrays in place; these kernels check it there (the word-sum checksum and
+// every CSR structure) before any kernel follows a column index, and form the
+// restrictions R = P^T.
+
+namespace {
+
+// sum (mod 2^64) of n 64-bit words
+__global__ void k_word_sum(const unsigned long long* __restrict__ w, long long n, unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    acc += w[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// *bad = 1 unless rp[0] = 0, rp[rows] = nnz, rp non-decreasing and 0 <= ci < cols
+__global__ void k_csr_check(const int* __restrict__ rp, const int* __restrict__ ci, long long rows, long long cols,
+                            long long nnz, int* bad) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  const long long t0 = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  int ok = 1;
+  if (t0 == 0 && (rp[0] != 0 || static_cast<long long>(rp[rows]) != nnz)) ok = 0;
+  for (long long i = t0; i < rows; i += stride)
+    if (rp[i + 1] < rp[i]) ok = 0;
+  for (long long p = t0; p < nnz; p += stride)
+    if (ci[p] < 0 || static_cast<long long>(ci[p]) >= cols) ok = 0;
+  if (!ok) atomicOr(bad, 1);
+}
+
+__global__ void k_count_cols(const int* __restrict__ ci, long long nnz, int* __restrict__ cnt) {
+  for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < nnz;
+       p += static_cast<long long>(gridDim.x) * blockDim.x)
+    atomicAdd(&cnt[ci[p]], 1);
+}
+
+// out[0] = 0, out[i + 1] = cnt[0] + .. + cnt[i] (one block: each thread sums a slice,
+// the slice totals are scanned in shared memory, each thread then writes its slice)
+__global__ void __launch_bounds__(1024) k_scan_counts(const int* __restrict__ cnt, long long n, int* __restrict__ out) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const long long per = (n + blockDim.x - 1) / blockDim.x;
+  const long long b = t * per, e = b + per < n ? b + per : n;
+  long long s = 0;
+  for (long long i = b; i < e; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {
+    const long long v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  long long run = part[t] - s;
+  if (t == 0) out[0] = 0;
+  for (long long i = b; i < e; ++i) {
+    run += cnt[i];
+    out[i + 1] = static_cast<int>(run);
+  }
+}
+
+// R entries at atomically taken positions of their rows (next: the rows' running offsets)
+__global__ void k_transpose_fill(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                                 long long rows, int* __restrict__ next, int* __restrict__ rci,
+                                 double* __restrict__ rv) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < rows;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int k = atomicAdd(&next[ci[p]], 1);
+      rci[k] = static_cast<int>(i);
+      rv[k] = v[p];
+    }
+}
+
+// each row of R sorted by column (insertion sort: a few entries per row), so that R is
+// the same whatever order the atomics took
+__global__ void k_sort_rows(const int* __restrict__ rp, long long rows, int* __restrict__ ci, double* __restrict__ v) {
+  for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < rows;
+       r += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int b = rp[r], e = rp[r + 1];
+    for (int p = b + 1; p < e; ++p) {
+      const int c = ci[p];
+      const double x = v[p];
+      int k = p - 1;
+      while (k >= b && ci[k] > c) {
+        ci[k + 1] = ci[k];
+        v[k + 1] = v[k];
+        --k;
+      }
+      ci[k + 1] = c;
+      v[k + 1] = x;
+    }
+  }
+}
+
+int load_grid(long long n) {
+  const long long b = (n + 255) / 256;
+  return static_cast<int>(b < 4 * kNumSms ? (b > 0 ? b : 1) : 4 * kNumSms);
+}
+
+}  // namespace
+
+void launch_blob_checksum(const void* blob, size_t bytes, unsigned long long* out, cudaStream_t st) {
+  const long long words = static_cast<long long>(bytes / 8);
+  ProfScope ps(st, P_OTHER, 1.0 * bytes, 0.0);
+  k_word_sum<<<load_grid(words), 256, 0, st>>>(static_cast<const unsigned long long*>(blob), words, out);
+}
+
+void launch_csr_check(const int* rp, const int* ci, long long rows, long long cols, long long nnz, int* bad,
+                      cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 4.0 * (rows + 1) + 4.0 * nnz, 0.0);
+  k_csr_check<<<load_grid(rows > nnz ? rows : nnz), 256, 0, st>>>(rp, ci, rows, cols, nnz, bad);
+}
+
+void launch_transpose_csr(long long rows, long long cols, long long nnz, const int* rp, const int* ci,
+                          const double* v, int* rrp, int* rci, double* rv, int* scratch, cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 4.0 * (rows + 1) + 24.0 * nnz + 8.0 * (cols + 1), 0.0, 4);
+  cudaMemsetAsync(scratch, 0, sizeof(int) * static_cast<size_t>(cols), st);
+  k_count_cols<<<load_grid(nnz), 256, 0, st>>>(ci, nnz, scratch);
+  k_scan_counts<<<1, 1024, 0, st>>>(scratch, cols, rrp);
+  cudaMemcpyAsync(scratch, rrp, sizeof(int) * static_cast<size_t>(cols), cudaMemcpyDeviceToDevice, st);
+  k_transpose_fill<<<load_grid(rows), 256, 0, st>>>(rp, ci, v, rows, scratch, rci, rv);
+  k_sort_rows<<<load_grid(cols), 256, 0, st>>>(rrp, cols, rci, rv);
+}
+
 }  // namespace amgeig
 
 using namespace amgeig;
