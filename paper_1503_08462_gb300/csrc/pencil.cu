@@ -2540,40 +2540,136 @@ __global__ void __launch_bounds__(kPenThreads) k_xc(int dn, int m, int q, int p,
 
 // ------------------------------------------------------------ small FP64 kernels
 
-// Cholesky of a symmetric positive definite n x n row-major matrix into L
-// (lower, row-major; upper part zeroed).  status[0] = ENOTSPD on failure.
-__global__ void k_chol(int n, const double* __restrict__ A, double* __restrict__ L, int* status) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+// Float64 Cholesky A = L L^T (row-major, L lower, zero above) of the
+// symmetric part of A, right-looking in panels of 32 columns so that the work
+// spreads over many blocks (float64 runs at a fraction of the float32 rate):
+// per panel the 32 x 32 diagonal block is factored by one block, the rows
+// below it solve x L11^T = a one thread each, and the trailing lower triangle
+// takes the rank-32 update in 32 x 32 tiles, one block each.  A pivot <= 0
+// sets *status = ENOTSPD (and is replaced by 1 so the factorisation finishes).
+constexpr int kCb = 32;
+
+__global__ void k_sym_lower(int n, const double* __restrict__ A, double* __restrict__ L) {
   const long long N = n;
-  for (long long i = tid; i < N * N; i += nt) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N * N;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int r = static_cast<int>(i / N), c = static_cast<int>(i % N);
     L[i] = (c <= r) ? 0.5 * (A[r * N + c] + A[c * N + r]) : 0.0;
   }
+}
+
+__global__ void __launch_bounds__(1024) k_chol_diag(int n, int j0, int nb, double* __restrict__ L, int* status) {
+  __shared__ double T[kCb][kCb + 1];
   __shared__ int bad;
+  const int tid = threadIdx.x;
+  const long long N = n;
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    T[i][j] = j <= i ? L[(j0 + i) * N + j0 + j] : 0.0;
+  }
   if (tid == 0) bad = 0;
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
+  for (int k = 0; k < nb; ++k) {
     if (tid == 0) {
-      const double d = L[k * N + k];
+      const double d = T[k][k];
       if (!(d > 0.0)) {
         bad = 1;
-        L[k * N + k] = 1.0;
+        T[k][k] = 1.0;
       } else {
-        L[k * N + k] = sqrt(d);
+        T[k][k] = sqrt(d);
       }
     }
     __syncthreads();
-    const double piv = L[k * N + k];
-    for (int i = k + 1 + tid; i < n; i += nt) L[i * N + k] /= piv;
+    if (tid > k && tid < nb) T[tid][k] /= T[k][k];
     __syncthreads();
-    const int m = n - k - 1;  // n <= 4096: m * m fits in 32 bits
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-      if (j <= i) L[i * N + j] -= L[i * N + k] * L[j * N + k];
+    const int m = nb - k - 1;
+    if (tid < m * m) {
+      const int i = k + 1 + tid / m, j = k + 1 + tid % m;
+      if (j <= i) T[i][j] -= T[i][k] * T[j][k];
     }
     __syncthreads();
   }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    if (j <= i) L[(j0 + i) * N + j0 + j] = T[i][j];
+  }
   if (tid == 0 && bad && status) status[0] = AMGEIG_ENOTSPD;
+}
+
+__global__ void __launch_bounds__(128) k_chol_panel(int n, int j0, int nb, double* __restrict__ L) {
+  __shared__ double T[kCb][kCb + 1];
+  const long long N = n;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    T[i][j] = L[(j0 + i) * N + j0 + j];
+  }
+  __syncthreads();
+  const long long r = j0 + nb + blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (r >= n) return;
+  double x[kCb];
+#pragma unroll
+  for (int j = 0; j < kCb; ++j) x[j] = j < nb ? L[r * N + j0 + j] : 0.0;
+#pragma unroll
+  for (int j = 0; j < kCb; ++j) {
+    if (j < nb) {
+      double s = x[j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) s -= x[t] * T[j][t];
+      x[j] = s / T[j][j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kCb; ++j)
+    if (j < nb) L[r * N + j0 + j] = x[j];
+}
+
+// lower-triangle tile (ti, tj), tj <= ti, of the trailing block from the block index
+__global__ void __launch_bounds__(256) k_chol_syrk(int n, int j0, int nb, double* __restrict__ L) {
+  __shared__ double Ai[kCb][kCb + 1], Aj[kCb][kCb + 1];
+  int ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= static_cast<int>(blockIdx.x)) ++ti;
+  const int tj = blockIdx.x - ti * (ti + 1) / 2;
+  const int base = j0 + nb, i0 = base + ti * kCb, c0 = base + tj * kCb;
+  const long long N = n;
+  for (int e = threadIdx.x; e < kCb * kCb; e += blockDim.x) {
+    const int r = e / kCb, t = e % kCb;
+    Ai[r][t] = (i0 + r < n && t < nb) ? L[(i0 + r) * N + j0 + t] : 0.0;
+    Aj[r][t] = (c0 + r < n && t < nb) ? L[(c0 + r) * N + j0 + t] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x / 8, cb = (threadIdx.x % 8) * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+  for (int t = 0; t < kCb; ++t) {
+    const double a = Ai[r][t];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] = fma(a, Aj[cb + e][t], acc[e]);
+  }
+  const int i = i0 + r;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int j = c0 + cb + e;
+    if (i < n && j < n && j <= i) L[i * N + j] -= acc[e];
+  }
+}
+
+void launch_chol_f64(int n, const double* A, double* L, int* status, cudaStream_t st) {
+  k_sym_lower<<<ceil_div(static_cast<long long>(n) * n, 256), 256, 0, st>>>(n, A, L);
+  for (int j0 = 0; j0 < n; j0 += kCb) {
+    const int nb = std::min(kCb, n - j0), rest = n - j0 - nb;
+    k_chol_diag<<<1, 1024, 0, st>>>(n, j0, nb, L, status);
+    if (rest > 0) {
+      k_chol_panel<<<ceil_div(rest, 128), 128, 0, st>>>(n, j0, nb, L);
+      const int T = ceil_div(rest, kCb);
+      k_chol_syrk<<<T * (T + 1) / 2, 256, 0, st>>>(n, j0, nb, L);
+    }
+  }
+}
+
+int chol_launches(int n) {
+  int c = 1;
+  for (int j0 = 0; j0 < n; j0 += kCb) c += (n - j0 > kCb) ? 3 : 1;
+  return c;
 }
 
 // In-place triangular solves on `ncols` columns of the row-major n x ld block X:
@@ -2622,15 +2718,6 @@ __global__ void k_identity(int n, double* __restrict__ X) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N * N;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
     X[i] = (i / N == i % N) ? 1.0 : 0.0;
-}
-
-__global__ void k_transpose(int rows, int cols, const double* __restrict__ X, double* __restrict__ Y) {
-  const long long total = static_cast<long long>(rows) * cols;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int r = static_cast<int>(i / cols), c = static_cast<int>(i % cols);
-    Y[static_cast<long long>(c) * rows + r] = X[i];
-  }
 }
 
 size_t syev_smem_base(int n, int nwant) {
@@ -2889,15 +2976,15 @@ void launch_pencil_solve(PencilWork* w, int dn, int m, int q, const double* C64,
 }
 
 void launch_mass_factor(PencilWork* w, int dn, const double* Mn, int* status, cudaStream_t st) {
-  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 2, dn * static_cast<double>(dn) * dn / 3.0, 1);
-  k_chol<<<1, 1024, 0, st>>>(dn, Mn, w->Lm, status);
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 2, dn * static_cast<double>(dn) * dn / 3.0, chol_launches(dn));
+  launch_chol_f64(dn, Mn, w->Lm, status, st);
 }
 
 void launch_coarse_inverse(int dn, const double* An, double* L, double* Linv, double* Ainv, int* status,
                            cudaStream_t st) {
-  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 5, 2.0 * dn * dn * dn, 4);
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 5, 2.0 * dn * dn * dn, chol_launches(dn) + 3);
   // A_n = L L^T; Linv = L^-1 (the identity solved in place); Ainv = Linv^T Linv = L^-T L^-1
-  k_chol<<<1, 1024, 0, st>>>(dn, An, L, status);
+  launch_chol_f64(dn, An, L, status, st);
   k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, Linv);
   k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, L, Linv, dn, dn, 0);
   launch_gemm_f64(dn, dn, dn, 1.0, Linv, dn, true, Linv, dn, false, 0.0, Ainv, dn, st);
@@ -2905,19 +2992,19 @@ void launch_coarse_inverse(int dn, const double* An, double* L, double* Linv, do
 
 void launch_coarse_modes(PencilWork* w, int dn, int nwant, const double* An, double* Z, double* theta,
                          cudaStream_t st) {
-  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 0.0, 6);
-  // Hs = L_m^-1 A_n L_m^-T : X = L_m^-1 A_n ; Hs = L_m^-1 X^T
-  cudaMemcpyAsync(w->Hs, An, sizeof(double) * dn * dn, cudaMemcpyDeviceToDevice, st);
-  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, w->Hs, dn, dn, 0);
-  k_transpose<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, dn, w->Hs, w->H);
-  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, w->H, dn, dn, 0);
-  k_transpose_sym<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->H, w->Hs);
-  // the nwant lowest eigenpairs of Hs (dn x nwant into Yh), placed as Z's first columns
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 4.0 * dn * dn * static_cast<double>(dn), 6);
+  // Li = L_m^-1 (the identity solved in place, in H); Hs = sym(Li A_n Li^T) by two float64
+  // products (scratch: the eigensolver's W, free until the eigensolver runs, and Yh)
+  double* Li = w->H;
+  double* T = reinterpret_cast<double*>(w->W);
+  k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, Li);
+  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, Li, dn, dn, 0);
+  launch_gemm_f64(dn, dn, dn, 1.0, Li, dn, false, An, dn, false, 0.0, T, dn, st);
+  launch_gemm_f64(dn, dn, dn, 1.0, T, dn, false, Li, dn, true, 0.0, w->Yh, dn, st);
+  k_transpose_sym<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->Yh, w->Hs);
+  // the nwant lowest eigenpairs of Hs (dn x nwant into Yh); Z's first columns = L_m^-T Y = Li^T Y
   launch_syev_df(w, dn, nwant, w->Hs, theta, w->Yh, st);
-  cudaMemcpy2DAsync(Z, sizeof(double) * dn, w->Yh, sizeof(double) * nwant, sizeof(double) * nwant, dn,
-                    cudaMemcpyDeviceToDevice, st);
-  // Z = L_m^-T Y on those columns
-  k_trsm<<<ceil_div(nwant, 8), 256, 0, st>>>(dn, w->Lm, Z, dn, nwant, 1);
+  launch_gemm_f64(dn, nwant, dn, 1.0, Li, dn, true, w->Yh, nwant, false, 0.0, Z, dn, st);
 }
 
 }  // namespace amgeig
