@@ -271,15 +271,18 @@ int parse_blob(const void* blob, size_t bytes, std::vector<CsrView>& levels, std
 struct DeviceBuffers {
   static constexpr size_t kOwn = size_t(64) << 20, kFirst = size_t(2) << 20, kAlign = 256;
   size_t next_block = kFirst;  // size of the next block of carved arrays
-  std::vector<void*> ptrs;  // every cudaMalloc of this owner
+  std::vector<void*> ptrs;  // every block of this owner
+  std::vector<size_t> sizes;  // and its size
   size_t held = 0;          // bytes of those allocations
   size_t mallocs = 0;       // allocation calls made (or, when dry, that would be made)
   bool dry = false;         // count the bytes a sequence of allocs would take, allocate nothing
   char* blk = nullptr;      // free tail of the current block of small arrays
   size_t blk_left = 0;
-  cudaStream_t st = nullptr;  // uploads are ordered on this stream (the hierarchy's)
+  cudaStream_t st = nullptr;  // the owner's work (and uploads) run on this stream
+  // the owner's stream is drained first: the blocks go back to the device cache for the next owner
   ~DeviceBuffers() {
-    for (void* p : ptrs) cudaFree(p);
+    if (st) cudaStreamSynchronize(st);
+    for (size_t i = 0; i < ptrs.size(); ++i) dev_release(ptrs[i], sizes[i]);
   }
   template <typename T>
   cudaError_t alloc(T** out, size_t count) {
@@ -288,9 +291,10 @@ struct DeviceBuffers {
     *out = nullptr;
     if (bytes >= kOwn) {
       if (!dry) {
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = dev_alloc(&p, bytes);
         if (e != cudaSuccess) return e;
         ptrs.push_back(p);
+        sizes.push_back(bytes);
       }
       ++mallocs;
       held += bytes;
@@ -301,9 +305,10 @@ struct DeviceBuffers {
       const size_t block = std::max(next_block, bytes);  // < kOwn
       next_block = std::min(kOwn, 2 * block);
       if (!dry) {
-        cudaError_t e = cudaMalloc(&p, block);
+        cudaError_t e = dev_alloc(&p, block);
         if (e != cudaSuccess) return e;
         ptrs.push_back(p);
+        sizes.push_back(block);
         blk = static_cast<char*>(p);
       }
       ++mallocs;
@@ -431,6 +436,7 @@ struct SolveWork {
   std::map<std::string, Graph> graphs;
   std::map<std::string, int> graph_seen;  // segments run so far without a graph
   ~SolveWork() {
+    if (mem.st) cudaStreamSynchronize(mem.st);  // its solves' work is done before its blocks are released
     for (auto& g : graphs)
       if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
     pencil_work_destroy(pw);
@@ -443,6 +449,7 @@ int make_workspace(amgeig_hierarchy_t* h, int qt, int precision, int vcycles, st
                    bool dry = false, int border = 0) {
   auto w = std::make_unique<SolveWork>();
   w->mem.dry = dry;
+  w->mem.st = dry ? nullptr : h->stream;
   // the augmentation's width: the iterate's qt columns, or a Krylov block of up to 2 qt
   const int bw = std::max(qt, border);
   w->bcap = bw;
@@ -846,9 +853,11 @@ const T* amg_x(amgeig_hierarchy_t* h, SolveWork* w, int k, const amgeig_options&
 }  // namespace
 
 amgeig_hierarchy_t::~amgeig_hierarchy_t() {
+  if (stream) cudaStreamSynchronize(stream);  // nothing in flight uses the blocks released below
   ws.reset();
   pencil_work_destroy(cpw);
   pencil_work_destroy(init.pw);
+  mem.st = nullptr;  // drained above; the stream goes before the member buffers are released
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -2367,7 +2376,8 @@ int Service::fits(const Request* r) {
   }
   size_t fr = 0, tot = 0;
   cudaSetDevice(h->device);
-  const bool ok = cudaMemGetInfo(&fr, &tot) != cudaSuccess || need <= fr;
+  bool ok = cudaMemGetInfo(&fr, &tot) != cudaSuccess || need <= fr;
+  if (!ok && dev_cache_trim() > 0) ok = cudaMemGetInfo(&fr, &tot) != cudaSuccess || need <= fr;
   if (!ok) return kWait;
   reserved[h] = need;  // admitted (pick takes it now): counted until its workspace exists
   return kFits;

@@ -2764,7 +2764,7 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err, bool dry) {
     if (pass == 1) {
       w->bytes = total;
       if (dry) return w;
-      cudaError_t e = cudaMalloc(&w->base, total);
+      cudaError_t e = dev_alloc(&w->base, total);
       if (err) *err = e;
       if (e != cudaSuccess) {
         w->base = nullptr;
@@ -2804,7 +2804,7 @@ PencilWork* pencil_work_create(int dn, int qmax, cudaError_t* err, bool dry) {
 
 void pencil_work_destroy(PencilWork* w) {
   if (!w) return;
-  if (w->base) cudaFree(w->base);
+  if (w->base) dev_release(w->base, w->bytes);  // the caller's work using it has completed
   delete w;
 }
 

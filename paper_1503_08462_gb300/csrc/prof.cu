@@ -11,6 +11,67 @@
 #include "prof.cuh"
 
 namespace amgeig {
+
+namespace {
+struct DevCache {
+  std::mutex mu;
+  std::multimap<std::pair<int, size_t>, void*> kept;  // (device, bytes) -> block
+  size_t bytes = 0;
+};
+DevCache& dev_cache() {
+  static DevCache* c = new DevCache();  // never destroyed: blocks outlive static destructors safely
+  return *c;
+}
+}  // namespace
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    DevCache& c = dev_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.kept.find({dev, bytes});
+    if (it != c.kept.end()) {
+      *p = it->second;
+      c.kept.erase(it);
+      c.bytes -= bytes;
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    if (dev_cache_trim() > 0) e = cudaMalloc(p, bytes);
+  }
+  return e;
+}
+
+void dev_release(void* p, size_t bytes) {
+  if (!p) return;
+  int dev = 0;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) == cudaSuccess) dev = at.device;
+  {
+    DevCache& c = dev_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.bytes + bytes <= kDevCacheBytes) {
+      c.kept.emplace(std::make_pair(dev, bytes), p);
+      c.bytes += bytes;
+      return;
+    }
+  }
+  cudaFree(p);
+}
+
+size_t dev_cache_trim() {
+  DevCache& c = dev_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  const size_t freed = c.bytes;
+  for (auto& kv : c.kept) cudaFree(kv.second);
+  c.kept.clear();
+  c.bytes = 0;
+  return freed;
+}
 namespace {
 
 struct Rec {

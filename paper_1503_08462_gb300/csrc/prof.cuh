@@ -33,6 +33,18 @@ enum ProfClass {
 // the current device, and recorded per (device, function).
 void ensure_dynamic_smem(const void* func, size_t bytes);
 
+// Device blocks released by owners (hierarchies, workspaces) are kept, per device
+// and size, for the next owner: a load after a free then maps nothing new.
+// dev_alloc takes a kept block of exactly `bytes` on the current device or calls
+// cudaMalloc (after giving every kept block back to the device once, if that
+// fails); dev_release keeps the block while at most kDevCacheBytes are kept, else
+// frees it -- the caller guarantees that no work in flight still uses it;
+// dev_cache_trim frees every kept block (returns the bytes freed).
+constexpr size_t kDevCacheBytes = size_t(16) << 30;
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_release(void* p, size_t bytes);
+size_t dev_cache_trim();
+
 // Record `msg` as the calling thread's last failure (amgeig_last_error) and
 // return `code`; code == AMGEIG_OK clears the record.
 int set_last_error(int code, const char* msg);
