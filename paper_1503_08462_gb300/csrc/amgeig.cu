@@ -1946,6 +1946,8 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
   h->R.resize(n - 1);
   // P_l in place; R_l = P_l^T formed on the device (rows in ascending column order)
   int* tscratch = nullptr;
+  long long* scan_tmp = nullptr;
+  CK(m.alloc(&scan_tmp, 1024));
   if (n > 1) CK(m.alloc(&tscratch, static_cast<size_t>(h->sizes[1])));
   for (int l = 0; l + 1 < n; ++l) {
     const CsrView& P = prolong[l];
@@ -1960,7 +1962,8 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
     CK(m.alloc(&Dr.rp, static_cast<size_t>(P.cols) + 1));
     CK(m.alloc(&Dr.ci, static_cast<size_t>(P.nnz)));
     CK(m.alloc(&Dr.v64, static_cast<size_t>(P.nnz)));
-    launch_transpose_csr(P.rows, P.cols, P.nnz, Dp.rp, Dp.ci, Dp.v64, Dr.rp, Dr.ci, Dr.v64, tscratch, h->stream);
+    launch_transpose_csr(P.rows, P.cols, P.nnz, Dp.rp, Dp.ci, Dp.v64, Dr.rp, Dr.ci, Dr.v64, tscratch, scan_tmp,
+                         h->stream);
     for (DevCsr* D : {&Dp, &Dr}) {
       CK(m.alloc(&D->v32, static_cast<size_t>(P.nnz)));
       CK(m.alloc(&D->d2, static_cast<size_t>(P.nnz)));
@@ -1998,24 +2001,23 @@ int load_hierarchy(const void* blob, size_t bytes, int device, int modes, amgeig
     CK(cudaMemcpyAsync(prev.p, iv.data(), sizeof(double) * iv.size(), cudaMemcpyHostToDevice, h->stream));
     nv = prev.p;
     int* counts = nullptr;
+    long long* dtotal = nullptr;
     CK(m.alloc(&counts, static_cast<size_t>(h->sizes[0])));
+    CK(m.alloc(&dtotal, 1));
     for (int k = n - 2; k >= 0; --k) {
       const DevCsr& P = h->P[k];
       DevCsr& D = h->PC[k];
       D.rows = P.rows;
       D.cols = dn0;
+      // row counts, their offsets on the device; only the total comes back (to size the arrays)
       launch_composite_rows(P, nrp, nci, nv, dn0, nullptr, counts, nullptr, nullptr, h->stream);
-      std::vector<int32_t> cnt(static_cast<size_t>(P.rows)), rp(static_cast<size_t>(P.rows) + 1, 0);
-      CK(cudaMemcpyAsync(cnt.data(), counts, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(m.alloc(&D.rp, static_cast<size_t>(P.rows) + 1));
+      launch_exclusive_scan(counts, P.rows, D.rp, scan_tmp, dtotal, h->stream);
+      long long total = 0;
+      CK(cudaMemcpyAsync(&total, dtotal, sizeof(total), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
-      int64_t total = 0;
-      for (int64_t i = 0; i < P.rows; ++i) {
-        total += cnt[static_cast<size_t>(i)];
-        if (total >= (1LL << 31)) return fail(AMGEIG_ENOMEM, "composite prolongation too large");
-        rp[static_cast<size_t>(i) + 1] = static_cast<int32_t>(total);
-      }
+      if (total >= (1LL << 31)) return fail(AMGEIG_ENOMEM, "composite prolongation too large");
       D.nnz = static_cast<int>(total);
-      CK(m.upload(&D.rp, rp));
       CK(m.alloc(&D.ci, static_cast<size_t>(total)));
       CK(cudaMallocAsync(reinterpret_cast<void**>(&cur.p), sizeof(double) * std::max<int64_t>(total, 1), h->stream));
       launch_composite_rows(P, nrp, nci, nv, dn0, D.rp, nullptr, D.ci, cur.p, h->stream);

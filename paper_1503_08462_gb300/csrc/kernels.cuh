@@ -283,7 +283,12 @@ void launch_syev_df_into(int n, int nwant, const double* H, double* evals, doubl
 void launch_blob_checksum(const void* blob, size_t bytes, unsigned long long* out, cudaStream_t st);
 void launch_csr_check(const int* rp, const int* ci, long long rows, long long cols, long long nnz, int* bad,
                       cudaStream_t st);
+// out[0] = 0, out[i + 1] = cnt[0] + .. + cnt[i] (int32; the exact total in *total when given);
+// tmp: 1024 int64 of scratch (also for the transpose)
+void launch_exclusive_scan(const int* cnt, long long n, int* out, long long* tmp, long long* total,
+                           cudaStream_t st);
 void launch_transpose_csr(long long rows, long long cols, long long nnz, const int* rp, const int* ci,
-                          const double* v, int* rrp, int* rci, double* rv, int* scratch, cudaStream_t st);
+                          const double* v, int* rrp, int* rci, double* rv, int* scratch, long long* tmp,
+                          cudaStream_t st);
 
 }  // namespace amgeig

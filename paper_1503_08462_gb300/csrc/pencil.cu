@@ -1026,23 +1026,24 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_tri_cl(int n, int ldw, int 
       for (int i = tid; i < m; i += nt) p[i] = df_sub(p[i], df_mul(kc, v[i]));  // w
     }
     __syncthreads();
-    // own rows: W22 -= v w^T + w v^T (column k keeps the entries of the reduced matrix)
-    const int i0 = max(r0, k + 1);
-    const long long cnt = static_cast<long long>(max(0, r1 - i0)) * m;
-    for (long long idx = tid; idx < cnt; idx += nt) {
-      const int ii = static_cast<int>(idx / m), j = static_cast<int>(idx % m);
-      const int i = i0 + ii - k - 1;  // trailing index of the row
+    // own rows: W22 -= v w^T + w v^T, one warp per row, lanes along it (column k keeps
+    // the entries of the reduced matrix)
+    for (int row = max(r0, k + 1) + warp; row < r1; row += nw) {
+      const int i = row - k - 1;  // trailing index of the row
       const df vi = v[i], wi = p[i];
-      df_acc u0 = acc_zero();
-      if (j <= i) {
-        u0.fma(vi, p[j]);
-        u0.fma(wi, v[j]);
-      } else {
-        u0.fma(v[j], wi);
-        u0.fma(p[j], vi);
+      df* rowp = W + (row - r0) * LD + (k + 1);
+#pragma unroll 2
+      for (int j = lane; j < m; j += 32) {
+        df_acc u0 = acc_zero();
+        if (j <= i) {
+          u0.fma(vi, p[j]);
+          u0.fma(wi, v[j]);
+        } else {
+          u0.fma(v[j], wi);
+          u0.fma(p[j], vi);
+        }
+        rowp[j] = df_sub(rowp[j], u0.value());
       }
-      df* e = W + (i0 + ii - r0) * LD + (k + 1 + j);
-      *e = df_sub(*e, u0.value());
     }
     __syncthreads();
     send_column(k + 1);

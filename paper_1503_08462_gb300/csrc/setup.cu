@@ -503,29 +503,79 @@ __global__ void k_count_cols(const int* __restrict__ ci, long long nnz, int* __r
     atomicAdd(&cnt[ci[p]], 1);
 }
 
-// out[0] = 0, out[i + 1] = cnt[0] + .. + cnt[i] (one block: each thread sums a slice,
-// the slice totals are scanned in shared memory, each thread then writes its slice)
-__global__ void __launch_bounds__(1024) k_scan_counts(const int* __restrict__ cnt, long long n, int* __restrict__ out) {
-  __shared__ long long part[1024];
-  const int t = threadIdx.x;
-  const long long per = (n + blockDim.x - 1) / blockDim.x;
-  const long long b = t * per, e = b + per < n ? b + per : n;
+// Exclusive scan of n int counts in three passes over up to 1024 blocks: the
+// blocks' chunk sums, one block scanning those (int64), then each block
+// scanning its chunk from its offset (inside a block each thread sums a slice,
+// the slice totals are scanned in shared memory, each thread writes its slice).
+constexpr int kScanThreads = 1024, kScanBlocks = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ cnt, long long n, long long chunk,
+                                                            long long* __restrict__ bsum) {
+  __shared__ long long red[32];
+  const long long b0 = blockIdx.x * chunk, b1 = b0 + chunk < n ? b0 + chunk : n;
   long long s = 0;
-  for (long long i = b; i < e; ++i) s += cnt[i];
-  part[t] = s;
+  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += cnt[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// inclusive scan of part[0 .. blockDim) in place (Hillis-Steele)
+__device__ void block_scan_inclusive(long long* part) {
+  const int t = threadIdx.x;
   for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {
     const long long v = t >= o ? part[t - o] : 0;
     __syncthreads();
     part[t] += v;
     __syncthreads();
   }
-  long long run = part[t] - s;
-  if (t == 0) out[0] = 0;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_offsets(long long* __restrict__ bsum, int nb,
+                                                               long long* __restrict__ total) {
+  __shared__ long long part[kScanThreads];
+  const int t = threadIdx.x;
+  const long long v = t < nb ? bsum[t] : 0;
+  part[t] = v;
+  __syncthreads();
+  block_scan_inclusive(part);
+  if (t < nb) bsum[t] = part[t] - v;  // exclusive offsets
+  if (t == blockDim.x - 1 && total) *total = part[t];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const int* __restrict__ cnt, long long n, long long chunk,
+                                                              const long long* __restrict__ boff, int* __restrict__ out) {
+  __shared__ long long part[kScanThreads];
+  const int t = threadIdx.x;
+  const long long c0 = blockIdx.x * chunk, c1 = c0 + chunk < n ? c0 + chunk : n;
+  const long long per = (chunk + blockDim.x - 1) / blockDim.x;
+  const long long b = c0 + t * per, e = b + per < c1 ? b + per : c1;
+  long long s = 0;
+  for (long long i = b; i < e; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  block_scan_inclusive(part);
+  long long run = boff[blockIdx.x] + part[t] - s;
+  if (blockIdx.x == 0 && t == 0) out[0] = 0;
   for (long long i = b; i < e; ++i) {
     run += cnt[i];
     out[i + 1] = static_cast<int>(run);
   }
+}
+
+void scan_counts(const int* cnt, long long n, int* out, long long* tmp, long long* total, cudaStream_t st) {
+  long long chunk = (n + kScanBlocks - 1) / kScanBlocks;
+  if (chunk < kScanThreads) chunk = kScanThreads;
+  const int nb = static_cast<int>((n + chunk - 1) / chunk > 0 ? (n + chunk - 1) / chunk : 1);
+  k_scan_sums<<<nb, kScanThreads, 0, st>>>(cnt, n, chunk, tmp);
+  k_scan_offsets<<<1, kScanThreads, 0, st>>>(tmp, nb, total);
+  k_scan_chunks<<<nb, kScanThreads, 0, st>>>(cnt, n, chunk, tmp, out);
 }
 
 // R entries at atomically taken positions of their rows (next: the rows' running offsets)
@@ -581,12 +631,19 @@ void launch_csr_check(const int* rp, const int* ci, long long rows, long long co
   k_csr_check<<<load_grid(rows > nnz ? rows : nnz), 256, 0, st>>>(rp, ci, rows, cols, nnz, bad);
 }
 
+void launch_exclusive_scan(const int* cnt, long long n, int* out, long long* tmp, long long* total,
+                           cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 8.0 * n, 0.0, 3);
+  scan_counts(cnt, n, out, tmp, total, st);
+}
+
 void launch_transpose_csr(long long rows, long long cols, long long nnz, const int* rp, const int* ci,
-                          const double* v, int* rrp, int* rci, double* rv, int* scratch, cudaStream_t st) {
-  ProfScope ps(st, P_OTHER, 4.0 * (rows + 1) + 24.0 * nnz + 8.0 * (cols + 1), 0.0, 4);
+                          const double* v, int* rrp, int* rci, double* rv, int* scratch, long long* tmp,
+                          cudaStream_t st) {
+  ProfScope ps(st, P_OTHER, 4.0 * (rows + 1) + 24.0 * nnz + 8.0 * (cols + 1), 0.0, 6);
   cudaMemsetAsync(scratch, 0, sizeof(int) * static_cast<size_t>(cols), st);
   k_count_cols<<<load_grid(nnz), 256, 0, st>>>(ci, nnz, scratch);
-  k_scan_counts<<<1, 1024, 0, st>>>(scratch, cols, rrp);
+  scan_counts(scratch, cols, rrp, tmp, nullptr, st);
   cudaMemcpyAsync(scratch, rrp, sizeof(int) * static_cast<size_t>(cols), cudaMemcpyDeviceToDevice, st);
   k_transpose_fill<<<load_grid(rows), 256, 0, st>>>(rp, ci, v, rows, scratch, rci, rv);
   k_sort_rows<<<load_grid(cols), 256, 0, st>>>(rrp, cols, rci, rv);
