@@ -493,6 +493,25 @@ def run_profile_case(args):
         log(f"vcycle level {args.level}: {n} rows x {args.width} columns, |x| = {float(np.linalg.norm(x)):.6e}")
 
 
+def run_profile_solve(args):
+    """--profile-case solve: two solves with the timed workload's settings (q = 20 + 8 buffer vectors, mixed, two
+    V-cycles, 64 coarse modes, relative residual 1e-4) on the L-shape with --m-half (384 by default: 440,833
+    rows, blocks of 99 / 198 MB, above L2 and a few hundred MB on the device), for full-set captures of one of the
+    solve's kernels (-k regex:<kernel> -s <launches to skip> -c 1) on a case smaller than the timed one."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1503_08462_gb300 import amgeig as ae
+    from paper_1503_08462_gb300.inputs import hierarchy, meshes
+
+    blob, hinfo = hierarchy.problem_blob(meshes.lshape_2d(m_half=args.m_half, seed=2), coarse_cap=400)
+    opt = ae.options(q_extra=8, max_corrections=60, precision=ae.AMGEIG_MIXED_FP32, v_cycles=2, coarse_modes=64)
+    with ae.Hierarchy(blob) as hh:
+        for _ in range(2):
+            lam, _, info, code = hh.solve(20, tol=1e-4, opt=opt, vectors=False)
+        log(f"solve: levels {hinfo.sizes}, corrections {info.corrections}, status {code}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,12 +551,16 @@ def main():
                          "(workload default)")
     ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-mode", choices=["full", "sample"], default="full", help=argparse.SUPPRESS)
-    ap.add_argument("--profile-case", choices=["vcycle", "defect"], default=None,
-                    help="run one V-cycle (or one defect) from --level on the L-shape workload for a "
-                         "single-kernel profiler capture, and nothing else")
+    ap.add_argument("--profile-case", choices=["vcycle", "defect", "solve"], default=None,
+                    help="run one V-cycle (or one defect) from --level on the L-shape workload, or two solves "
+                         "with its settings on a smaller L-shape (--m-half), for a single-kernel profiler capture")
+    ap.add_argument("--m-half", type=int, default=384, help="--profile-case solve: the L-shape's half width")
     ap.add_argument("--level", type=int, default=0, help="--profile-case: the level")
     ap.add_argument("--width", type=int, default=28, help="--profile-case: block columns")
     args = ap.parse_args()
+    if args.profile_case == "solve":
+        run_profile_solve(args)
+        return
     if args.profile_case:
         run_profile_case(args)
         return
