@@ -2859,11 +2859,12 @@ void launch_syev_df(PencilWork* w, int n, int nwant, const double* H, double* ev
                                         (sizeof(df) * static_cast<size_t>(n)))));
   const size_t sm_back = sizeof(df) * static_cast<size_t>(wpb + chunk) * n;
   ProfScope ps(st, P_PENCIL, 8.0 * n * n + 8.0 * n * nwant, 0.0, 4);
-  // W too large for one block: a cluster of 2, 4 or 8 blocks holding its rows, when one can be scheduled
+  // W too large for one block: a cluster holding its rows, the largest of 8, 4, 2 blocks that can be scheduled
+  // (each block's work per step is its rows times the trailing row length: more blocks, shorter steps)
   int cs = 0, rows_per = 0;
   size_t sm_cl = 0;
   if (!inshared)
-    for (int c = 2; c <= kTriMaxCluster && cs == 0; c *= 2) {
+    for (int c = kTriMaxCluster; c >= 2 && cs == 0; c /= 2) {
       rows_per = (n + c - 1) / c;
       sm_cl = sizeof(df) * (static_cast<size_t>(rows_per) * ldw + 4 * static_cast<size_t>(n));
       if (sm_cl <= kSmemBudget && cluster_fits(c, sm_cl)) cs = c;
