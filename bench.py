@@ -718,7 +718,12 @@ def main():
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    # one untimed step first (like the device-timed region's warm-up): the timed steps then reuse device
+    # blocks released by the previous step, as a serving loop does
+    for it in range(-1, e2e_steps):
+        if it == 0:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
         hh = ae.lib()
         import ctypes
 

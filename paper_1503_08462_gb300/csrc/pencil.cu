@@ -2673,34 +2673,44 @@ int chol_launches(int n) {
   return c;
 }
 
-// In-place triangular solves on `ncols` columns of the row-major n x ld block X:
-// trans = 0: L Y = X (forward), trans = 1: L^T Y = X (backward).  One warp per
-// column: each step's inner product is spread over the lanes (fixed lane
-// partition, then a shuffle tree), so the dependent float64 chain per step is
-// ~i/32 long instead of i.
-__global__ void k_trsm(int n, const double* __restrict__ L, double* __restrict__ X, int ld, int ncols, int trans) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (c >= ncols) return;  // whole warps
+// L Y = X in place on ncols columns of the row-major n x ld block X, blocked by 32 rows: rows
+// b0 .. b0+31 first take X[b0..] -= L[b0.., 0..b0) X[0..b0) (a float64 product over many blocks), then
+// the 32 x 32 diagonal triangle is solved one thread per column (kernel below).
+__global__ void __launch_bounds__(128) k_trsm_diag(int n, int b0, int nb, const double* __restrict__ L,
+                                                   double* __restrict__ X, int ld, int ncols) {
+  __shared__ double T[kCb][kCb + 1];
   const long long N = n, LDX = ld;
-  if (!trans) {
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int k = lane; k < i; k += 32) s += L[i * N + k] * X[k * LDX + c];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    T[i][j] = j <= i ? L[(b0 + i) * N + b0 + j] : 0.0;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  double x[kCb];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) X[i * LDX + c] = (X[i * LDX + c] - s) / L[i * N + i];
-      __syncwarp();
-    }
-  } else {
-    for (int i = n - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1 + lane; k < n; k += 32) s += L[k * N + i] * X[k * LDX + c];
+  for (int r = 0; r < kCb; ++r) x[r] = r < nb ? X[(b0 + r) * LDX + c] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) X[i * LDX + c] = (X[i * LDX + c] - s) / L[i * N + i];
-      __syncwarp();
+  for (int r = 0; r < kCb; ++r) {
+    if (r < nb) {
+      double s = x[r];
+#pragma unroll
+      for (int t = 0; t < r; ++t) s -= T[r][t] * x[t];
+      x[r] = s / T[r][r];
     }
+  }
+#pragma unroll
+  for (int r = 0; r < kCb; ++r)
+    if (r < nb) X[(b0 + r) * LDX + c] = x[r];
+}
+
+void launch_trsm_lower(int n, const double* L, double* X, int ld, int ncols, cudaStream_t st) {
+  for (int b0 = 0; b0 < n; b0 += kCb) {
+    const int nb = std::min(kCb, n - b0);
+    if (b0 > 0)
+      launch_gemm_f64(nb, ncols, b0, -1.0, L + static_cast<long long>(b0) * n, n, false, X, ld, false, 1.0,
+                      X + static_cast<long long>(b0) * ld, ld, st);
+    k_trsm_diag<<<ceil_div(ncols, 128), 128, 0, st>>>(n, b0, nb, L, X, ld, ncols);
   }
 }
 
@@ -2984,23 +2994,25 @@ void launch_mass_factor(PencilWork* w, int dn, const double* Mn, int* status, cu
 
 void launch_coarse_inverse(int dn, const double* An, double* L, double* Linv, double* Ainv, int* status,
                            cudaStream_t st) {
-  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 5, 2.0 * dn * dn * dn, chol_launches(dn) + 3);
+  // the products count their own launches
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 5, 2.0 * dn * dn * dn, chol_launches(dn) + 1 + ceil_div(dn, kCb));
   // A_n = L L^T; Linv = L^-1 (the identity solved in place); Ainv = Linv^T Linv = L^-T L^-1
   launch_chol_f64(dn, An, L, status, st);
   k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, Linv);
-  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, L, Linv, dn, dn, 0);
+  launch_trsm_lower(dn, L, Linv, dn, dn, st);
   launch_gemm_f64(dn, dn, dn, 1.0, Linv, dn, true, Linv, dn, false, 0.0, Ainv, dn, st);
 }
 
 void launch_coarse_modes(PencilWork* w, int dn, int nwant, const double* An, double* Z, double* theta,
                          cudaStream_t st) {
-  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 4.0 * dn * dn * static_cast<double>(dn), 6);
+  // the products and the eigensolver count their own launches
+  ProfScope ps(st, P_PENCIL, 8.0 * dn * dn * 6, 4.0 * dn * dn * static_cast<double>(dn), 2 + ceil_div(dn, kCb));
   // Li = L_m^-1 (the identity solved in place, in H); Hs = sym(Li A_n Li^T) by two float64
   // products (scratch: the eigensolver's W, free until the eigensolver runs, and Yh)
   double* Li = w->H;
   double* T = reinterpret_cast<double*>(w->W);
   k_identity<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, Li);
-  k_trsm<<<ceil_div(dn, 8), 256, 0, st>>>(dn, w->Lm, Li, dn, dn, 0);
+  launch_trsm_lower(dn, w->Lm, Li, dn, dn, st);
   launch_gemm_f64(dn, dn, dn, 1.0, Li, dn, false, An, dn, false, 0.0, T, dn, st);
   launch_gemm_f64(dn, dn, dn, 1.0, T, dn, false, Li, dn, true, 0.0, w->Yh, dn, st);
   k_transpose_sym<<<ceil_div(static_cast<long long>(dn) * dn, 256), 256, 0, st>>>(dn, w->Yh, w->Hs);
