@@ -818,3 +818,47 @@ def test_checkerboard_mixed_eigenvalues_at_the_metric_bound():
     assert code == ae.AMGEIG_OK
     rel = np.abs(lam - ref) / ref
     assert np.all(rel <= 1e-8), rel.max()
+
+
+@pytest.mark.parametrize("q,qe", [(60, 12), (59, 12)])
+def test_mixed_wide_border_parity(q, qe):
+    """Mixed path with a border of 72 (even: the Gram's tile list split over two blocks per row chunk with
+    bulk-copied slabs, the recombination streaming Y through shared memory) or 71 columns (odd: the
+    register-staged fallbacks) against the oracle's iterates after 2 finest corrections; every pencil takes
+    the dense path.  Tolerances as for the multi-lane check (the float32 V-cycle moves each correction by
+    <= 2e-5 of its column); the subspace is compared on its leading columns up to a gap of at least 1e-3."""
+    p, blob, _ = problem_and_blob("square", 64, 400, 5)
+    oh = O.read_blob(blob)
+    kw = dict(q_extra=qe, fixed_corrections=2, v_cycles=2)
+    lam_o, U_o, info_o = O.solve(oh, q, tol=0.0, opts=O.Options(**kw))
+    with ae.Hierarchy(blob) as h:
+        lam, U, info, code = h.solve(q, tol=0.0, opt=ae.options(precision=ae.AMGEIG_MIXED_FP32, **kw))
+    assert info.corrections == 2
+    rel = np.max(np.abs(lam - lam_o) / lam_o)
+    gaps = np.diff(lam_o) / lam_o[1:]
+    k = int(np.nonzero(gaps > 1e-3)[0].max()) + 1  # columns 0..k-1 end at a gap
+    assert k >= q // 2
+    ang = m_subspace_angle(U[:, :k], U_o[:, :k], oh.M[0])
+    assert rel <= 1e-6 and ang <= 1e-4, (rel, ang, k, info_o.relres.max())
+    assert np.abs(U.T @ (oh.M[0] @ U) - np.eye(q)).max() < 1e-10
+
+
+def test_reload_into_kept_blocks_gives_the_same_bits():
+    """Device blocks released with a hierarchy are kept and handed to the next load: a hierarchy loaded into
+    blocks that still hold another hierarchy's data (here the same problem's, then a different one's) solves to
+    the same bits as on its first load, for both precisions."""
+    _, blob, _ = problem_and_blob("lshape", 24, 60, 2)
+    _, other, _ = problem_and_blob("square", 40, 60, 3)
+    opts = [ae.options(q_extra=2, max_corrections=40, precision=prec, v_cycles=2)
+            for prec in (ae.AMGEIG_FP64, ae.AMGEIG_MIXED_FP32)]
+
+    def run(b):
+        with ae.Hierarchy(b) as h:
+            return [h.solve(5, tol=1e-9, opt=o) for o in opts]
+
+    first = run(blob)
+    run(other)
+    for again in (run(blob), run(blob)):
+        for (l0, u0, i0, c0), (l1, u1, i1, c1) in zip(first, again):
+            assert c0 == c1 and i0.corrections == i1.corrections
+            assert np.array_equal(l0, l1) and np.array_equal(u0, u1)
