@@ -88,6 +88,42 @@ namespace {
 
 // ------------------------------------------------------------ block helpers
 
+// sum_i a[i sa] b[i sb] (i < len) in float-float with four interleaved
+// accumulators: independent chains keep the float32 pipes busy in these
+// latency-bound single-block kernels
+__device__ __forceinline__ df_acc dot4(const df* a, int sa, const df* b, int sb, int len) {
+  df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
+  int i = 0;
+  for (; i + 4 <= len; i += 4) {
+    c0.fma(a[i * sa], b[i * sb]);
+    c1.fma(a[(i + 1) * sa], b[(i + 1) * sb]);
+    c2.fma(a[(i + 2) * sa], b[(i + 2) * sb]);
+    c3.fma(a[(i + 3) * sa], b[(i + 3) * sb]);
+  }
+  for (; i < len; ++i) c0.fma(a[i * sa], b[i * sb]);
+  c0.merge(c1);
+  c2.merge(c3);
+  c0.merge(c2);
+  return c0;
+}
+
+// the same with weights: sum_i a[i sa] w[i] b[i sb]
+__device__ __forceinline__ df_acc dot4w(const df* a, int sa, const df* w, const df* b, int sb, int len) {
+  df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
+  int i = 0;
+  for (; i + 4 <= len; i += 4) {
+    c0.fma(df_mul(a[i * sa], w[i]), b[i * sb]);
+    c1.fma(df_mul(a[(i + 1) * sa], w[i + 1]), b[(i + 1) * sb]);
+    c2.fma(df_mul(a[(i + 2) * sa], w[i + 2]), b[(i + 2) * sb]);
+    c3.fma(df_mul(a[(i + 3) * sa], w[i + 3]), b[(i + 3) * sb]);
+  }
+  for (; i < len; ++i) c0.fma(df_mul(a[i * sa], w[i]), b[i * sb]);
+  c0.merge(c1);
+  c2.merge(c3);
+  c0.merge(c2);
+  return c0;
+}
+
 __device__ __forceinline__ int sturm_count(const float* sd, const float* se2, int n, float x, float pivmin) {
   float qv = sd[0] - x;
   int cnt = qv < 0.f;
@@ -469,31 +505,75 @@ __device__ void syev_single(const df* Z, long long ldz, const df* dd, const df* 
 // working accuracy: S = L L^T, C = L^-1 Hq L^-T by parallel cyclic Jacobi,
 // vectors Z_g L^-T Q in ascending order.  Column c of the group is at
 // Z[i ldz + c] and goes to Zn[i ldn + c], its eigenvalue to evals[c].  rrw:
-// 4 G^2 df, perm: G ints, red, sf: block reduction scratch (shared).
-__device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, const df* ee, int n, df* rrw,
-                              int* perm, df_acc* red, float* sf, df* Zn, long long ldn, double* evals) {
+// 4 G^2 df, perm: G ints, red, sf: block reduction scratch (shared).  TZ: n x G
+// df scratch with Z's row stride (T Z, formed once).  TA x TB: the register
+// tile of S and Hq per thread.
+template <int TA, int TB>
+__device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, const df* ee, int n, df* TZ,
+                              df* rrw, int* perm, df_acc* red, float* sf, df* Zn, long long ldn, double* evals) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const long long N = n;
   df* S = rrw;
   df* Hq = rrw + G * G;
   df* Qm = rrw + 2 * G * G;
   df* Xm = rrw + 3 * G * G;
-  for (int idx = tid; idx < G * G; idx += nt) {
-    const int a0 = idx / G, b0 = idx % G;
-    if (b0 < a0) continue;
-    df_acc sa = acc_zero(), ha = acc_zero();
-    for (int i = 0; i < n; ++i) {
-      const df za = Z[i * ldz + a0];
-      const df zb = Z[i * ldz + b0];
-      sa.fma(za, zb);
+  for (int i = warp; i < n; i += nw)
+    for (int c = lane; c < G; c += 32) {
       df_acc tz = acc_zero();
-      tz.fma(dd[i], zb);
-      if (i > 0) tz.fma(ee[i - 1], Z[(i - 1) * ldz + b0]);
-      if (i + 1 < n) tz.fma(ee[i], Z[(i + 1) * ldz + b0]);
-      ha.fma(za, tz.value());
+      tz.fma(dd[i], Z[i * ldz + c]);
+      if (i > 0) tz.fma(ee[i - 1], Z[(i - 1) * ldz + c]);
+      if (i + 1 < n) tz.fma(ee[i], Z[(i + 1) * ldz + c]);
+      TZ[i * ldz + c] = tz.value();
     }
-    S[a0 * G + b0] = S[b0 * G + a0] = sa.value();
-    Hq[a0 * G + b0] = Hq[b0 * G + a0] = ha.value();
+  __syncthreads();
+  // S = Z^T Z and Hq = Z^T (T Z): the upper triangle by TA x TB tiles, one
+  // compensated sum per entry over the rows in order; the lower triangle mirrors it
+  {
+    // tile row ta starts at tile column (ta TA) / TB, the first that reaches the diagonal
+    const int na = (G + TA - 1) / TA, nbt = (G + TB - 1) / TB;
+    int ntile = 0;
+    for (int ta = 0; ta < na; ++ta) ntile += nbt - (ta * TA) / TB;
+    for (int tix = tid; tix < ntile; tix += nt) {
+      int ta = 0, rem = tix;
+      while (rem >= nbt - (ta * TA) / TB) {
+        rem -= nbt - (ta * TA) / TB;
+        ++ta;
+      }
+      const int a0 = ta * TA, b0 = ((ta * TA) / TB + rem) * TB;
+      df_acc sa[TA][TB], ha[TA][TB];
+#pragma unroll
+      for (int u = 0; u < TA; ++u)
+#pragma unroll
+        for (int v = 0; v < TB; ++v) sa[u][v] = ha[u][v] = acc_zero();
+      for (int i = 0; i < n; ++i) {
+        df za[TA], zb[TB], tb[TB];
+#pragma unroll
+        for (int u = 0; u < TA; ++u) za[u] = a0 + u < G ? Z[i * ldz + a0 + u] : df{0.f, 0.f};
+#pragma unroll
+        for (int v = 0; v < TB; ++v) {
+          const bool ib = b0 + v < G;
+          zb[v] = ib ? Z[i * ldz + b0 + v] : df{0.f, 0.f};
+          tb[v] = ib ? TZ[i * ldz + b0 + v] : df{0.f, 0.f};
+        }
+#pragma unroll
+        for (int u = 0; u < TA; ++u)
+#pragma unroll
+          for (int v = 0; v < TB; ++v) {
+            sa[u][v].fma(za[u], zb[v]);
+            ha[u][v].fma(za[u], tb[v]);
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < TA; ++u)
+#pragma unroll
+        for (int v = 0; v < TB; ++v) {
+          const int a = a0 + u, b = b0 + v;
+          if (a <= b && b < G) {
+            S[a * G + b] = S[b * G + a] = sa[u][v].value();
+            Hq[a * G + b] = Hq[b * G + a] = ha[u][v].value();
+          }
+        }
+    }
   }
   __syncthreads();
   // Cholesky S = L L^T in place (lower), right-looking
@@ -509,15 +589,15 @@ __device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, c
     }
     __syncthreads();
   }
-  // C = L^-1 Hq L^-T  (two column-parallel forward substitutions)
+  // C = L^-1 Hq L^-T  (two column-parallel forward substitutions; each row's
+  // sum over the solved rows in four compensated chains)
   for (int pass = 0; pass < 2; ++pass) {
+    df* out = pass == 0 ? Xm : Qm;
     for (int col = tid; col < G; col += nt) {
       for (int i = 0; i < G; ++i) {
-        df s = (pass == 0) ? Hq[i * G + col] : Xm[col * G + i];
-        for (int kk = 0; kk < i; ++kk)
-          s = df_sub(s, df_mul(S[i * G + kk], (pass == 0) ? Xm[kk * G + col] : Qm[kk * G + col]));
-        const df r = df_div(s, S[i * G + i]);
-        if (pass == 0) Xm[i * G + col] = r; else Qm[i * G + col] = r;
+        const df rhs = (pass == 0) ? Hq[i * G + col] : Xm[col * G + i];
+        const df s = df_sub(rhs, dot4(S + i * G, 1, out + col, G, i).value());
+        out[i * G + col] = df_div(s, S[i * G + i]);
       }
     }
     __syncthreads();
@@ -604,32 +684,78 @@ __device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, c
           reinterpret_cast<int*>(&Xm[t * 4 + 3])[0] = b0;
         }
         __syncthreads();
-        // rows: C <- J^T C
-        for (int idx = tid; idx < (np / 2) * G; idx += nt) {
-          const int t = idx / G, col = idx % G;
-          const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-          const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-          if (b0 >= G) continue;
-          const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-          const df x = Hq[a0 * G + col], y = Hq[b0 * G + col];
-          Hq[a0 * G + col] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          Hq[b0 * G + col] = df_add(df_mul(sn, x), df_mul(cs, y));
-        }
-        __syncthreads();
-        // columns: C <- C J, Q <- Q J
-        for (int idx = tid; idx < (np / 2) * G; idx += nt) {
-          const int t = idx / G, row = idx % G;
-          const int a0 = reinterpret_cast<int*>(&Xm[t * 4 + 2])[0];
-          const int b0 = reinterpret_cast<int*>(&Xm[t * 4 + 3])[0];
-          if (b0 >= G) continue;
-          const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
-          df x = Hq[row * G + a0], y = Hq[row * G + b0];
-          Hq[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          Hq[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
-          x = Qm[row * G + a0];
-          y = Qm[row * G + b0];
-          Qm[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
-          Qm[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+        // C <- J^T C J by 2 x 2 blocks (pair s, pair t), s <= t, the lower
+        // triangle mirrored; the rows of each block turn first, then its columns.
+        // The triangle of pair blocks is folded (row s with row P - 1 - s) so
+        // that every thread gets the same share.  Q <- Q J alongside.
+        {
+          const int P = np / 2, half = (P + 1) / 2;
+          for (int idx = tid; idx < half * (P + 1); idx += nt) {
+            const int fr = idx / (P + 1), cc = idx - fr * (P + 1);
+            int ps, pt;
+            if (cc < P - fr) {
+              ps = fr;
+              pt = fr + cc;
+            } else {
+              ps = P - 1 - fr;
+              if (ps == fr) continue;
+              pt = ps + (cc - (P - fr));
+            }
+            const int as = reinterpret_cast<const int*>(&Xm[ps * 4 + 2])[0];
+            const int bs = reinterpret_cast<const int*>(&Xm[ps * 4 + 3])[0];
+            const int at = reinterpret_cast<const int*>(&Xm[pt * 4 + 2])[0];
+            const int bt = reinterpret_cast<const int*>(&Xm[pt * 4 + 3])[0];
+            const df css = Xm[ps * 4 + 0], sns = Xm[ps * 4 + 1];
+            const df cst = Xm[pt * 4 + 0], snt = Xm[pt * 4 + 1];
+            const bool rs = bs < G, rt = bt < G;
+            const df zero = df{0.f, 0.f};
+            df x00 = Hq[as * G + at], x01 = rt ? Hq[as * G + bt] : zero;
+            df x10 = rs ? Hq[bs * G + at] : zero, x11 = (rs && rt) ? Hq[bs * G + bt] : zero;
+            if (rs) {
+              const df y00 = df_sub(df_mul(css, x00), df_mul(sns, x10));
+              const df y10 = df_add(df_mul(sns, x00), df_mul(css, x10));
+              const df y01 = df_sub(df_mul(css, x01), df_mul(sns, x11));
+              const df y11 = df_add(df_mul(sns, x01), df_mul(css, x11));
+              x00 = y00;
+              x10 = y10;
+              x01 = y01;
+              x11 = y11;
+            }
+            if (rt) {
+              const df y00 = df_sub(df_mul(cst, x00), df_mul(snt, x01));
+              const df y01 = df_add(df_mul(snt, x00), df_mul(cst, x01));
+              const df y10 = df_sub(df_mul(cst, x10), df_mul(snt, x11));
+              const df y11 = df_add(df_mul(snt, x10), df_mul(cst, x11));
+              x00 = y00;
+              x01 = y01;
+              x10 = y10;
+              x11 = y11;
+            }
+            if (ps == pt) {
+              // diagonal block: (as, bs) and (bs, as) take the same value
+              Hq[as * G + as] = x00;
+              if (rs) {
+                Hq[as * G + bs] = Hq[bs * G + as] = x01;
+                Hq[bs * G + bs] = x11;
+              }
+            } else {
+              Hq[as * G + at] = Hq[at * G + as] = x00;
+              if (rt) Hq[as * G + bt] = Hq[bt * G + as] = x01;
+              if (rs) Hq[bs * G + at] = Hq[at * G + bs] = x10;
+              if (rs && rt) Hq[bs * G + bt] = Hq[bt * G + bs] = x11;
+            }
+          }
+          for (int t = warp; t < P; t += nw) {
+            const int a0 = reinterpret_cast<const int*>(&Xm[t * 4 + 2])[0];
+            const int b0 = reinterpret_cast<const int*>(&Xm[t * 4 + 3])[0];
+            if (b0 >= G) continue;
+            const df cs = Xm[t * 4 + 0], sn = Xm[t * 4 + 1];
+            for (int row = lane; row < G; row += 32) {
+              const df x = Qm[row * G + a0], y = Qm[row * G + b0];
+              Qm[row * G + a0] = df_sub(df_mul(cs, x), df_mul(sn, y));
+              Qm[row * G + b0] = df_add(df_mul(sn, x), df_mul(cs, y));
+            }
+          }
         }
         __syncthreads();
       }
@@ -650,8 +776,7 @@ __device__ void syev_group_rr(int G, const df* Z, long long ldz, const df* dd, c
   // Xm = L^-T Q  (back substitution per column)
   for (int col = tid; col < G; col += nt) {
     for (int i = G - 1; i >= 0; --i) {
-      df s = Qm[i * G + col];
-      for (int kk = i + 1; kk < G; ++kk) s = df_sub(s, df_mul(S[kk * G + i], Xm[kk * G + col]));
+      const df s = df_sub(Qm[i * G + col], dot4(S + (i + 1) * G + i, G, Xm + (i + 1) * G + col, G, G - 1 - i).value());
       Xm[i * G + col] = df_div(s, S[i * G + i]);
     }
   }
@@ -796,7 +921,9 @@ __global__ void __launch_bounds__(kSyThreads) k_syev_df(int n, int nwant, int ld
     __syncthreads();
     for (int g0 = 0; g0 < nwant;) {
       const int g1 = gs1[g0], G = g1 - g0;
-      if (G >= 2) syev_group_rr(G, Zt + g0, NW, dd, ee, n, rrw, perm, red, sf, Zn + g0, NW, evals + g0);
+      if (G >= 2)
+        syev_group_rr<2, 2>(G, Zt + g0, NW, dd, ee, n, fac + N * NW + g0, rrw, perm, red, sf, Zn + g0, NW,
+                            evals + g0);
       g0 = g1;
     }
   }
@@ -1194,7 +1321,7 @@ __global__ void __launch_bounds__(kSvecThreads) k_syev_vecs(int n, int nwant, si
   if (G == 1) {
     if (tid == 0) syev_single(Z, ld, dd, ee, n, Zg + b, NW, evals + b);
   } else {
-    syev_group_rr(G, Z, ld, dd, ee, n, rrw, perm, red, sf, Zg + b, NW, evals + b);
+    syev_group_rr<4, 2>(G, Z, ld, dd, ee, n, dinv, rrw, perm, red, sf, Zg + b, NW, evals + b);
   }
 }
 
@@ -1277,42 +1404,6 @@ constexpr int kStdMaxQ = 128;  // largest border the solver accepts (q + q_extra
 
 __device__ __forceinline__ df to_df(double v) { return df_from_double(v); }
 __device__ __forceinline__ df to_df(float2 v) { return df{v.x, v.y}; }
-
-// sum_i a[i sa] b[i sb] (i < len) in float-float with four interleaved
-// accumulators: independent chains keep the float32 pipes busy in these
-// latency-bound single-block kernels
-__device__ __forceinline__ df_acc dot4(const df* a, int sa, const df* b, int sb, int len) {
-  df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
-  int i = 0;
-  for (; i + 4 <= len; i += 4) {
-    c0.fma(a[i * sa], b[i * sb]);
-    c1.fma(a[(i + 1) * sa], b[(i + 1) * sb]);
-    c2.fma(a[(i + 2) * sa], b[(i + 2) * sb]);
-    c3.fma(a[(i + 3) * sa], b[(i + 3) * sb]);
-  }
-  for (; i < len; ++i) c0.fma(a[i * sa], b[i * sb]);
-  c0.merge(c1);
-  c2.merge(c3);
-  c0.merge(c2);
-  return c0;
-}
-
-// the same with weights: sum_i a[i sa] w[i] b[i sb]
-__device__ __forceinline__ df_acc dot4w(const df* a, int sa, const df* w, const df* b, int sb, int len) {
-  df_acc c0 = acc_zero(), c1 = acc_zero(), c2 = acc_zero(), c3 = acc_zero();
-  int i = 0;
-  for (; i + 4 <= len; i += 4) {
-    c0.fma(df_mul(a[i * sa], w[i]), b[i * sb]);
-    c1.fma(df_mul(a[(i + 1) * sa], w[i + 1]), b[(i + 1) * sb]);
-    c2.fma(df_mul(a[(i + 2) * sa], w[i + 2]), b[(i + 2) * sb]);
-    c3.fma(df_mul(a[(i + 3) * sa], w[i + 3]), b[(i + 3) * sb]);
-  }
-  for (; i < len; ++i) c0.fma(df_mul(a[i * sa], w[i]), b[i * sb]);
-  c0.merge(c1);
-  c2.merge(c3);
-  c0.merge(c2);
-  return c0;
-}
 
 // Solve S y = r (S: q x (q+1) augmented, row-major, shared) by Gauss-Jordan
 // elimination with partial pivoting, by the whole block: per column, warp 0
@@ -2165,6 +2256,7 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const
     }
     // block inverse iteration, the shift moved to the mean Ritz value after each
     // step, until the Ritz values settle (at most kRepairRounds steps)
+    bool settled = false;
     for (int round = 0; dup && round < kRepairRounds; ++round) {
       // (At - s Mt) Y = Mt Yb through the Schur complement at s, all columns at
       // once; s sits 2^-30 (relative) off the mean Ritz value so that a cluster
@@ -2216,20 +2308,26 @@ __global__ void __launch_bounds__(kSrqiThreads) k_srqi_check(int m, int q, const
       }
       __syncthreads();
       ritz_residual(AY, MY, c.Wc, c.evc, n, cs, &c.res);
-      if (c.res <= kRepairResidual) break;
+      if (c.res <= kRepairResidual) {
+        settled = true;
+        break;
+      }
     }
-    // Rayleigh-Ritz on span(Yb)
-    pencil_apply(th, F, T, Sl, Yb, AY, MY, m, q, cs);
-    for (int idx = tid; idx < 2 * cs * cs; idx += nt) {
-      const int which = idx / (cs * cs), e = idx % (cs * cs), a = e / cs, b = e % cs;
-      const df v = dot4(Yb + a, L, (which ? MY : AY) + b, L, n).value();
-      (which ? c.Mc : c.Ac)[a * L + b] = v;
+    // Rayleigh-Ritz on span(Yb); a block that settled in its last round holds
+    // it already (Wc, evc and res of this Yb)
+    if (!settled) {
+      pencil_apply(th, F, T, Sl, Yb, AY, MY, m, q, cs);
+      for (int idx = tid; idx < 2 * cs * cs; idx += nt) {
+        const int which = idx / (cs * cs), e = idx % (cs * cs), a = e / cs, b = e % cs;
+        const df v = dot4(Yb + a, L, (which ? MY : AY) + b, L, n).value();
+        (which ? c.Mc : c.Ac)[a * L + b] = v;
+      }
+      __syncthreads();
+      if (tid == 0) small_rr(c.Ac, c.Mc, c.Wc, c.evc, cs);
+      __syncthreads();
+      ritz_residual(AY, MY, c.Wc, c.evc, n, cs, &c.res);
     }
-    __syncthreads();
-    if (tid == 0) small_rr(c.Ac, c.Mc, c.Wc, c.evc, cs);
-    __syncthreads();
     // the repaired pairs must be eigenpairs of the pencil to working accuracy
-    ritz_residual(AY, MY, c.Wc, c.evc, n, cs, &c.res);
     if (!(c.res <= kRepairResidual)) {
       if (tid == 0) {
         flag[0] = 0;

@@ -773,11 +773,11 @@ __global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const 
                                                              const float2* __restrict__ W, int chunk_rows, int T,
                                                              int tpb, int rg, int slab, double* __restrict__ part,
                                                              int* __restrict__ status) {
-  extern __shared__ __align__(128) unsigned char graw[];
+  extern __shared__ __align__(128) unsigned char gbraw[];
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ int ok_s;
   const int stride = slab * 3 * q + 8;  // float2 per stage: V slab, W slab, pad
-  float2* stage0 = reinterpret_cast<float2*>(graw);
+  float2* stage0 = reinterpret_cast<float2*>(gbraw);
   const int ntiles = T * (T + 1);
   const int tid = threadIdx.x;
   // rows: chunk blockIdx.y; tiles blockIdx.x * tpb .. + tpb; rg row groups of tpb threads
@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(kGtThreads, 3) k_gram_df_bulk(int rows, const 
     return;
   }
   // merge the rg row groups (shared memory reused; fixed order)
-  df_acc* red = reinterpret_cast<df_acc*>(graw);  // rg x tpb x 16
+  df_acc* red = reinterpret_cast<df_acc*>(gbraw);  // rg x tpb x 16
   if (active)
 #pragma unroll
     for (int i = 0; i < 16; ++i) red[(g * tpb + lt) * 16 + i] = acc[i];
