@@ -57,6 +57,34 @@ def test_noalloc_matches_allocating_entry_point_twice():
         assert np.abs(H @ V - V * w).max() <= 1e-11 * scale
 
 
+def test_noalloc_clean_up_group_matches_lapack():
+    """41 wanted eigenvalues within 1e-4 ||H|| of each other: one clean-up group of odd width inside the
+    one-block solver (its Rayleigh-Ritz step, with a dummy player in every Jacobi round)."""
+    import torch
+
+    from paper_1503_08462_gb300 import amgeig as ae
+
+    dev = torch.device("cuda:0")
+    n, nwant = 120, 41
+    rng = np.random.default_rng(11)
+    spec = np.sort(np.concatenate([rng.uniform(1.0, 1.5, nwant), rng.uniform(10.0, 1e4, n - nwant)]))
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    H = (Q * spec) @ Q.T
+    H = 0.5 * (H + H.T)
+    Hd = torch.tensor(H, dtype=torch.float64, device=dev)
+    vals = torch.empty(nwant, dtype=torch.float64, device=dev)
+    vecs = torch.empty((n, nwant), dtype=torch.float64, device=dev)
+    ae.amgeig_sym_eigh_noalloc(Hd, vals, vecs)
+    torch.cuda.synchronize()
+    w = vals.cpu().numpy()
+    V = vecs.cpu().numpy()
+    ref = np.linalg.eigvalsh(H)[:nwant]
+    scale = np.abs(spec).max()
+    assert np.all(np.abs(w - ref) <= 1e-12 * scale), np.abs(w - ref).max() / scale
+    assert np.abs(V.T @ V - np.eye(nwant)).max() < 1e-12
+    assert np.abs(H @ V - V * w).max() <= 1e-11 * scale
+
+
 def test_noalloc_on_a_side_stream():
     """The call only enqueues on the given stream; its results are read after that stream synchronises."""
     import torch
